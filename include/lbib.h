@@ -1,0 +1,229 @@
+/*
+ * lbib.h -- C ABI of the GB300 capillary solver: one time step of the hybrid
+ * lattice-Boltzmann / immersed-boundary method of Coclite, Pascazio,
+ * de Tullio and Decuzzi ("Predicting the vascular adhesion of deformable drug
+ * carriers in narrow capillaries traversed by blood cells", J. Fluids Struct.)
+ * run as hand-written CUDA kernels for sm_103a.
+ *
+ * What one step computes, in order (each item names the passage it follows):
+ *   1. streaming of the D2Q9 populations (Eq. 1 left-hand side, Eq. 3) with
+ *      halfway bounce-back walls and Zou-He inlet/outlet (Sec. 2.2, Sec. 3.1);
+ *   2. moments with the half-force shift (Eqs. 5-6) and BGK collision with the
+ *      Hermite equilibrium and Guo's forcing term (Eqs. 1, 2, 4);
+ *   3. the Lagrangian update of every membrane from that velocity: Peskin
+ *      interpolation (Sec. 2.2, Sec. 2.9), ligand-receptor kinetics and force
+ *      (Sec. 2.5, Eq. 13), membrane forces (Eqs. 8, 10, 11), repulsion
+ *      (Eq. 12), probe tractions (Eqs. 14-15), Verlet + BDF2 (Eqs. 17-18) or
+ *      rigid BDF2 (Eq. 19);
+ *   4. direct forcing at the element centroids, spread to the lattice as the
+ *      body force of the next collision (Sec. 2.2).
+ * Readings where the paper is silent: stencil nodes beyond a wall are wall
+ * nodes (velocity interpolation and spreading are truncated, density
+ * interpolation is renormalised); a marker within half a spacing of a wall is
+ * held by the wall and not forced; a traction probe that would cross a wall
+ * stops at it; Eq. 6's garbled term is the body force (Guo et al. 2002).
+ *
+ * Conventions for every call:
+ *   - Every call returns lbib_status; on failure lbib_last_error(ctx) gives a
+ *     message.  No exception and no exit() crosses this boundary.
+ *   - A context is used by one host thread at a time.
+ *   - The library owns all device memory of a context and frees it only in
+ *     lbib_destroy.  Host inputs are copied during the call; output buffers
+ *     belong to the caller.  A caller buffer smaller than needed gives
+ *     LBIB_ERR_INVALID_ARG and nothing is written.
+ *   - Lattice units: dx = dt = 1, rho_ref = 1, c_s^2 = 1/3.  Node (i, j) sits at
+ *     (x, y) = (i, j + 1/2); the walls are the lines y = 0 and y = ny.
+ *   - Population and field arrays on the host are row-major [ny][nx]
+ *     (populations [9][ny][nx], directions in the order of Eq. 3: rest, +x, +y,
+ *     -x, -y, (+1,+1), (-1,+1), (-1,-1), (+1,-1)).
+ *   - Work is enqueued on the context's stream; errors detected on the device
+ *     (divergence, a body leaving the region the solver tracks) are reported
+ *     by the next lbib_sync or read call.
+ */
+#ifndef LBIB_H
+#define LBIB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lbib_status {
+    LBIB_OK = 0,
+    LBIB_ERR_INVALID_ARG = 1, /* a parameter is out of range or a buffer too small */
+    LBIB_ERR_UNSUPPORTED = 2, /* valid request this build does not implement */
+    LBIB_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    LBIB_ERR_OOM = 4,         /* device or host allocation failed */
+    LBIB_ERR_DIVERGED = 5,    /* non-finite or non-positive state detected */
+    LBIB_ERR_TIMEOUT = 6,     /* a bounded device wait gave up */
+    LBIB_ERR_STATE = 7        /* call not valid in the context's current state */
+} lbib_status;
+
+typedef enum { LBIB_BC_INLET_OUTLET = 0, LBIB_BC_PERIODIC_FORCE = 1 } lbib_bc_mode;
+typedef enum { LBIB_STORE_FP64 = 0, LBIB_STORE_FP32 = 1, LBIB_STORE_BF16 = 2, LBIB_STORE_FP16 = 3 } lbib_storage;
+typedef enum { LBIB_CELL = 0, LBIB_PARTICLE = 1 } lbib_body_kind;
+typedef enum { LBIB_DEFORMABLE = 0, LBIB_RIGID = 1, LBIB_FIXED = 2 } lbib_motion;
+
+typedef struct lbib_ctx lbib_ctx;
+
+/* Lattice and fluid (Sec. 2.1, Sec. 3.1). */
+typedef struct lbib_fluid_params {
+    int32_t nx;          /* nodes along the channel (>= 3) */
+    int32_t ny;          /* nodes across it; the channel height H = ny dx (>= 2) */
+    double tau;          /* BGK relaxation time, > 1/2; nu = (tau - 1/2) / 3 */
+    double re;           /* Reynolds number u_max H / nu (Sec. 3.1) */
+    double rho_out;      /* outlet density (p = rho_out / 3), usually 1 */
+    double gx, gy;       /* uniform body force, PERIODIC_FORCE mode */
+    int32_t bc_mode;     /* lbib_bc_mode */
+    int32_t storage;     /* lbib_storage of the populations */
+    int32_t device;      /* CUDA device ordinal */
+    int32_t obs_capacity;/* observables ring-buffer records (0: 4096) */
+    void* cuda_stream;   /* borrowed cudaStream_t to enqueue on, or NULL */
+    uint64_t seed;       /* Philox key of the bond kinetics */
+} lbib_fluid_params;
+
+/* A closed membrane chain (Sec. 2.2-2.3); nv vertices joined by nv elements. */
+typedef struct lbib_membrane_desc {
+    int32_t kind;          /* lbib_body_kind */
+    int32_t motion;        /* lbib_motion */
+    int32_t nv;            /* vertices, 3 <= nv <= 1024 */
+    int32_t reserved;
+    const double* xy;      /* host, 2 nv doubles (x0, y0, x1, ...), counter-clockwise; copied */
+    const double* xy_ref;  /* stress-free shape, same layout, or NULL for xy */
+    double ca;             /* capillary number rho nu u_max / k_s (Sec. 3.1); > 0 if DEFORMABLE */
+    double beta;           /* k_b / k_s (Sec. 2.3) */
+    double ka;             /* area penalty coefficient k_a (Eq. 11) */
+    double density_ratio;  /* rho_body / rho (vertex mass rho_body A_0 / nv) */
+} lbib_membrane_desc;
+
+/* Ligand-receptor model of one particle (Sec. 2.5, Sec. 3.1). */
+typedef struct lbib_adhesion_params {
+    int32_t n_ligands;  /* sites equally spaced in arc length along the chain */
+    int32_t reserved;
+    double sigma;       /* spring constant in units rho nu^2 / H; INFINITY: particle fixed to the wall */
+    double y_cr;        /* critical gap for bond formation (lattice units) */
+    double y_eq;        /* equilibrium bond length (lattice units) */
+    double kf_dt;       /* k_f dt: P_f = 1 - exp(-k_f dt) */
+    double kr0_dt;      /* k_r0 dt: P_r = 1 - exp(-k_r0 dt exp(xi (y - y_eq)^2)) */
+    double xi;          /* force sensitivity of the reverse rate (1 / lattice length^2) */
+} lbib_adhesion_params;
+
+/* One observables record (Sec. 3.1), written after every completed step. */
+typedef struct lbib_obs {
+    int64_t step;     /* completed steps */
+    double t_star;    /* step u_max / H */
+    double delta_p;   /* (p - p0) / p0 of the first cell; NaN without a cell */
+    double r;         /* centroid distance, first cell to first particle; NaN if absent */
+    double n_l;       /* engaged bonds / bonds engaged at t = 0; NaN if none */
+    int32_t n_bound;  /* engaged bonds */
+    int32_t status;   /* device status bits seen when the record was written */
+} lbib_obs;
+
+/* Per-vertex arrays readable with lbib_read_body_field (values of the last step). */
+typedef enum {
+    LBIB_FIELD_X = 0, LBIB_FIELD_Y = 1,          /* positions X^n */
+    LBIB_FIELD_XPREV = 2, LBIB_FIELD_YPREV = 3,  /* positions X^{n-1} */
+    LBIB_FIELD_UVX = 4, LBIB_FIELD_UVY = 5,      /* fluid velocity interpolated at the vertex (Eq. 17) */
+    LBIB_FIELD_FSX = 6, LBIB_FIELD_FSY = 7,      /* stretching, Eq. 8 */
+    LBIB_FIELD_FBX = 8, LBIB_FIELD_FBY = 9,      /* bending, Eq. 10 */
+    LBIB_FIELD_FAX = 10, LBIB_FIELD_FAY = 11,    /* area penalty, Eq. 11 */
+    LBIB_FIELD_FPX = 12, LBIB_FIELD_FPY = 13,    /* repulsion, Eq. 12 */
+    LBIB_FIELD_FWX = 14, LBIB_FIELD_FWY = 15,    /* bonds, Eq. 13 */
+    LBIB_FIELD_FHX = 16, LBIB_FIELD_FHY = 17,    /* tractions, Eqs. 14-15 */
+    LBIB_FIELD_FTX = 18, LBIB_FIELD_FTY = 19,    /* total, Eq. 16 */
+    LBIB_FIELD_VX = 20, LBIB_FIELD_VY = 21,      /* structure velocity after the update */
+    LBIB_FIELD_MX = 22, LBIB_FIELD_MY = 23,      /* element centroid (marker) after the update */
+    LBIB_FIELD_MFX = 24, LBIB_FIELD_MFY = 25,    /* direct-forcing force density at the marker */
+    LBIB_FIELD_MDS = 26,                         /* element length ds used in spreading */
+    LBIB_FIELD_COUNT = 27
+} lbib_body_field;
+
+/* Creates a context on params->device: allocates the lattice and initialises
+ * the populations to the equilibrium at rho = 1 with the inlet profile
+ * (INLET_OUTLET) or at rest (PERIODIC_FORCE).  *out receives the handle. */
+lbib_status lbib_create(const lbib_fluid_params* params, lbib_ctx** out);
+
+/* Adds a membrane before the first lbib_advance; *id_out its index (may be NULL). */
+lbib_status lbib_add_membrane(lbib_ctx* ctx, const lbib_membrane_desc* desc, int32_t* id_out);
+
+/* Decorates body `body` with ligands (before the first lbib_advance).  Sites
+ * within y_cr of a wall start bound. */
+lbib_status lbib_set_adhesion(lbib_ctx* ctx, int32_t body, const lbib_adhesion_params* params);
+
+/* Enqueues nsteps >= 0 time steps on the context stream and returns without
+ * waiting.  The last step's Lagrangian update may stay pending (overlapped
+ * with the next call's lattice update); every read call completes it. */
+lbib_status lbib_advance(lbib_ctx* ctx, int64_t nsteps);
+
+/* Completes pending work, waits for the stream and reports device-side errors. */
+lbib_status lbib_sync(lbib_ctx* ctx);
+
+/* Number of completed steps (after completing pending work). */
+lbib_status lbib_step_count(lbib_ctx* ctx, int64_t* steps);
+
+/* Velocity u^n of the last completed step (Eq. 6) into caller host arrays of
+ * n >= nx ny doubles each, row-major [ny][nx]. */
+lbib_status lbib_read_velocity(lbib_ctx* ctx, double* ux, double* uy, size_t n);
+
+/* Density rho^n of the last completed step, host, n >= nx ny doubles. */
+lbib_status lbib_read_density(lbib_ctx* ctx, double* rho, size_t n);
+
+/* Velocity into caller DEVICE memory: dst_ux, dst_uy of n >= nx ny elements of
+ * `dtype` (0: float, 1: double), row-major; enqueued on the context stream. */
+lbib_status lbib_read_velocity_device(lbib_ctx* ctx, void* dst_ux, void* dst_uy, size_t n, int32_t dtype);
+
+/* Post-collision populations f*(x, t) of the last completed step as absolute
+ * values, host, n >= 9 nx ny doubles, [9][ny][nx]. */
+lbib_status lbib_read_populations(lbib_ctx* ctx, double* f, size_t n);
+
+/* Overwrites the stored post-collision populations (absolute values, layout as
+ * above); only before the first lbib_advance. */
+lbib_status lbib_write_populations(lbib_ctx* ctx, const double* f, size_t n);
+
+/* Copies up to `cap` observables records, oldest first, of the steps completed
+ * since the previous call (or since creation); *n_out receives the count. */
+lbib_status lbib_read_observables(lbib_ctx* ctx, lbib_obs* out, size_t cap, size_t* n_out);
+
+/* Vertex positions of body `id` after the last completed step, host,
+ * 2 nv doubles interleaved (x0, y0, x1, ...). */
+lbib_status lbib_read_markers(lbib_ctx* ctx, int32_t id, double* xy, size_t n);
+
+/* One per-vertex array (lbib_body_field) of body `id`, host, nv doubles. */
+lbib_status lbib_read_body_field(lbib_ctx* ctx, int32_t id, int32_t field, double* out, size_t n);
+
+/* Ligand states of body `id`: bound flag, anchor, and |u - P| of the last
+ * decision per site (host arrays of n >= n_ligands). */
+lbib_status lbib_read_bonds(lbib_ctx* ctx, int32_t id, int32_t* bound, double* ax, double* ay, double* margin,
+                            size_t n);
+
+/* Checkpoint: bytes needed, then save into / load from a caller host buffer.
+ * A restored context continues bit-identically (the random stream is
+ * counter-based). */
+lbib_status lbib_state_size(lbib_ctx* ctx, size_t* bytes);
+lbib_status lbib_save_state(lbib_ctx* ctx, void* buf, size_t bytes);
+lbib_status lbib_load_state(lbib_ctx* ctx, const void* buf, size_t bytes);
+
+/* Profiling: when enabled, the step graphs also record CUDA events around
+ * each kernel; lbib_read_kernel_times gives the device times (ms) of the last
+ * step's lattice kernel over the bulk, Lagrangian kernel and near-membrane
+ * lattice kernel (0 where a kernel did not run). */
+lbib_status lbib_set_profiling(lbib_ctx* ctx, int32_t enable);
+lbib_status lbib_read_kernel_times(lbib_ctx* ctx, float* bulk_ms, float* lagr_ms, float* near_ms);
+
+/* Launch counts per step and geometry the bench reports. */
+lbib_status lbib_describe(lbib_ctx* ctx, int32_t* kernels_per_step, int32_t* near_tiles, int32_t* tiles);
+
+/* Message of the last failed call on ctx (or of the last failed lbib_create
+ * when ctx is NULL).  Valid until the next call on ctx. */
+const char* lbib_last_error(lbib_ctx* ctx);
+
+/* Releases every resource of ctx (NULL is ignored). */
+void lbib_destroy(lbib_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBIB_H */

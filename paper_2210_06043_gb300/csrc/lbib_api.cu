@@ -1,0 +1,1014 @@
+// lbib_api.cu -- host runtime behind include/lbib.h: contexts, device memory,
+// streams, CUDA graphs of the time step and the C ABI.
+//
+// Time-step pipeline.  Lattice step m (bulk + near kernels) must follow the
+// Lagrangian step m - 1 only on near tiles, so the bulk lattice update of step
+// m runs on a forked stream concurrently with the Lagrangian step m - 1:
+//
+//     [Lagrangian(m-1) || bulk lattice(m)] -> near lattice(m)
+//
+// is one captured graph per parity of m.  A context keeps the last Lagrangian
+// step pending after lbib_advance (so back-to-back calls overlap it with the
+// next lattice step); every call that reads Lagrangian state completes it.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbib_internal.cuh"
+
+using namespace lbib;
+
+namespace {
+
+struct HostBody {
+    int kind = 0, motion = 0, nv = 0;
+    std::vector<double> xy, xy_ref;
+    double ca = 0, beta = 0, ka = 0, dens = 1;
+    bool adhesive = false;
+    lbib_adhesion_params adh{};
+};
+
+thread_local std::string g_create_error;
+
+// polygon measures of a closed chain: area, perimeter, area centroid, polar
+// moment about the centroid
+struct Poly {
+    double A, P, cx, cy, Jc;
+};
+
+Poly polygon(const std::vector<double>& xy)
+{
+    const size_t nv = xy.size() / 2;
+    double a2 = 0, per = 0, sx = 0, sy = 0, j = 0;
+    for (size_t v = 0; v < nv; ++v) {
+        size_t w = (v + 1) % nv;
+        double x0 = xy[2 * v], y0 = xy[2 * v + 1], x1 = xy[2 * w], y1 = xy[2 * w + 1];
+        double c = x0 * y1 - x1 * y0;
+        a2 += c;
+        per += std::sqrt((x1 - x0) * (x1 - x0) + (y1 - y0) * (y1 - y0));
+        sx += (x0 + x1) * c;
+        sy += (y0 + y1) * c;
+        j += c * (x0 * x0 + x0 * x1 + x1 * x1 + y0 * y0 + y0 * y1 + y1 * y1);
+    }
+    Poly p;
+    p.A = 0.5 * a2;
+    p.P = per;
+    p.cx = sx / (3.0 * a2);
+    p.cy = sy / (3.0 * a2);
+    p.Jc = j / 12.0 - p.A * (p.cx * p.cx + p.cy * p.cy);
+    return p;
+}
+
+template <typename T>
+cudaError_t dalloc(std::vector<void*>& reg, T** p, size_t n)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+    if (e == cudaSuccess) {
+        reg.push_back(q);
+        *p = static_cast<T*>(q);
+    }
+    return e;
+}
+
+}  // namespace
+
+struct lbib_ctx {
+    std::string err;
+    lbib_fluid_params P{};
+    int prec = PREC_F64;
+    size_t rsz = 8;  // bytes of one stored population / compute value
+    Dev d{};
+    std::vector<HostBody> bodies;
+    bool finalized = false;
+    int64_t s_f = 0, s_l = 0;  // lattice and Lagrangian steps done
+    cudaStream_t stream = nullptr, side = nullptr, cap = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t unit[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [profiling][parity]
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t pe[6] = {};
+    bool profiling = false, profiled_last = false;
+    int near_grid = 1;
+    int64_t obs_consumed = 0;
+    std::vector<void*> allocs;
+    double* macro_buf = nullptr;
+    int device = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+lbib_status fail(lbib_ctx* c, lbib_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+lbib_status cuda_fail(lbib_ctx* c, cudaError_t e, const char* what)
+{
+    cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? LBIB_ERR_OOM : LBIB_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                     \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);     \
+    } while (0)
+
+lbib_status check_status(lbib_ctx* ctx)
+{
+    uint32_t st = 0;
+    CK(cudaMemcpy(&st, ctx->d.status, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st & ST_DIVERGED) return fail(ctx, LBIB_ERR_DIVERGED, "non-finite or non-positive state on the device");
+    if (st & ST_LIST_OVERFLOW) return fail(ctx, LBIB_ERR_STATE, "near-tile list overflow");
+    if (st & ST_READ_MISS)
+        return fail(ctx, LBIB_ERR_STATE, "an interpolation stencil left the tiles updated as near-membrane");
+    if (st & ST_SPREAD_MISS)
+        return fail(ctx, LBIB_ERR_STATE, "a spreading stencil left the tiles scheduled as near-membrane");
+    return LBIB_OK;
+}
+
+lbib_status finish_pending(lbib_ctx* ctx)
+{
+    if (ctx->d.nbodies > 0 && ctx->s_l < ctx->s_f) {
+        CK(launch_lagrangian(ctx->d, ctx->prec, (int)((ctx->s_l + 1) & 1), ctx->stream));
+        ctx->s_l += 1;
+    }
+    return LBIB_OK;
+}
+
+lbib_status capture_unit(lbib_ctx* ctx, int prof, int p)
+{
+    Dev& d = ctx->d;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    auto rec = [&](int i, cudaStream_t s) {
+        if (prof && e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->pe[i], s, cudaEventRecordExternal);
+    };
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, ctx->cap);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+    rec(0, ctx->side);
+    if (e == cudaSuccess) e = launch_lbm_bulk(d, ctx->prec, p, ctx->side);
+    rec(1, ctx->side);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
+    rec(2, ctx->cap);
+    if (e == cudaSuccess) e = launch_lagrangian(d, ctx->prec, p, ctx->cap);
+    rec(3, ctx->cap);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap, ctx->ev_join, 0);
+    rec(4, ctx->cap);
+    if (e == cudaSuccess) e = launch_lbm_near(d, ctx->prec, p, ctx->near_grid, ctx->cap);
+    rec(5, ctx->cap);
+    cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(ctx, e, "capturing the step graph");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&ctx->unit[prof][p], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+    return LBIB_OK;
+}
+
+lbib_status ensure_graphs(lbib_ctx* ctx)
+{
+    int prof = ctx->profiling ? 1 : 0;
+    for (int p = 0; p < 2; ++p)
+        if (!ctx->unit[prof][p]) {
+            lbib_status s = capture_unit(ctx, prof, p);
+            if (s != LBIB_OK) return s;
+        }
+    return LBIB_OK;
+}
+
+// Builds the device Lagrangian arrays from the host bodies (first advance).
+lbib_status finalize(lbib_ctx* ctx)
+{
+    if (ctx->finalized) return LBIB_OK;
+    Dev& d = ctx->d;
+    const Lattice& L = d.L;
+    const int nb = (int)ctx->bodies.size();
+    d.nbodies = nb;
+    std::vector<BodyConst> bc(nb);
+    int nmark = 0, nlig = 0, nv_max = 0;
+    for (int b = 0; b < nb; ++b) {
+        nmark += ctx->bodies[b].nv;
+        nv_max = std::max(nv_max, ctx->bodies[b].nv);
+        if (ctx->bodies[b].adhesive) nlig += ctx->bodies[b].adh.n_ligands;
+    }
+    d.nmark = nmark;
+    d.nlig = nlig;
+    d.nv_max = std::max(nv_max, 1);
+    d.mw = std::max(1, (nmark + 31) / 32);
+    std::vector<double> pos(2 * (size_t)std::max(nmark, 1)), rref(2 * (size_t)std::max(nmark, 1));
+    std::vector<double> l0(std::max(nmark, 1)), th0(std::max(nmark, 1));
+    std::vector<double> rig((size_t)std::max(nb, 1) * RG_N, 0.0), bobs((size_t)std::max(nb, 1) * BO_N, 0.0);
+    std::vector<int32_t> lig_el(std::max(nlig, 1)), bound(std::max(nlig, 1), 0), site_off(nmark + 1, 0);
+    std::vector<double> lig_t(std::max(nlig, 1)), anchor(2 * (size_t)std::max(nlig, 1), 0.0);
+    const double nu = L.nu, umax = L.umax;
+    double lmax = 0.0;
+    int off = 0, loff = 0;
+    d.first_cell = d.first_particle = -1;
+    for (int b = 0; b < nb; ++b) {
+        const HostBody& h = ctx->bodies[b];
+        BodyConst& B = bc[b];
+        std::memset(&B, 0, sizeof(B));
+        B.kind = h.kind;
+        B.motion = h.motion;
+        B.nv = h.nv;
+        B.off = off;
+        if (h.kind == LBIB_CELL && d.first_cell < 0) d.first_cell = b;
+        if (h.kind == LBIB_PARTICLE && d.first_particle < 0) d.first_particle = b;
+        const std::vector<double>& ref = h.xy_ref.empty() ? h.xy : h.xy_ref;
+        const int nv = h.nv;
+        // stress-free lengths and turning angles
+        for (int l = 0; l < nv; ++l) {
+            int w = (l + 1) % nv, lm = (l + nv - 1) % nv;
+            double dx = ref[2 * w] - ref[2 * l], dy = ref[2 * w + 1] - ref[2 * l + 1];
+            l0[off + l] = std::sqrt(dx * dx + dy * dy);
+            double ax = ref[2 * l] - ref[2 * lm], ay = ref[2 * l + 1] - ref[2 * lm + 1];
+            th0[off + l] = std::atan2(ax * dy - ay * dx, ax * dx + ay * dy);
+            double cx = h.xy[2 * w] - h.xy[2 * l], cy = h.xy[2 * w + 1] - h.xy[2 * l + 1];
+            lmax = std::max(lmax, std::sqrt(cx * cx + cy * cy));
+        }
+        Poly pr = polygon(ref), pc = polygon(h.xy);
+        B.A0 = pr.A;
+        B.P0 = pr.P;
+        B.ks = (h.motion == LBIB_DEFORMABLE) ? 1.0 * nu * umax / h.ca : 0.0;  // Ca = rho nu u_max / k_s
+        B.kb = h.beta * B.ks;
+        B.ka = h.ka;
+        B.mv = h.dens * pr.A / nv;
+        B.mass = h.dens * pc.A;
+        B.inertia = h.dens * pc.Jc;
+        double* rs = &rig[(size_t)b * RG_N];
+        rs[RG_XC] = pc.cx;
+        rs[RG_YC] = pc.cy;
+        for (int v = 0; v < nv; ++v) {
+            pos[off + v] = h.xy[2 * v];
+            pos[nmark + off + v] = h.xy[2 * v + 1];
+            rref[off + v] = h.xy[2 * v] - pc.cx;
+            rref[nmark + off + v] = h.xy[2 * v + 1] - pc.cy;
+        }
+        double* bo = &bobs[(size_t)b * BO_N];
+        bo[BO_AREA] = pc.A;
+        bo[BO_PERIM] = pc.P;
+        bo[BO_CX] = pc.cx;
+        bo[BO_CY] = pc.cy;
+        bo[BO_XMIN] = bo[BO_YMIN] = 1e300;
+        bo[BO_XMAX] = bo[BO_YMAX] = -1e300;
+        for (int v = 0; v < nv; ++v) {
+            bo[BO_XMIN] = std::min(bo[BO_XMIN], h.xy[2 * v]);
+            bo[BO_XMAX] = std::max(bo[BO_XMAX], h.xy[2 * v]);
+            bo[BO_YMIN] = std::min(bo[BO_YMIN], h.xy[2 * v + 1]);
+            bo[BO_YMAX] = std::max(bo[BO_YMAX], h.xy[2 * v + 1]);
+        }
+        if (h.adhesive) {
+            const lbib_adhesion_params& a = h.adh;
+            B.adhesive = 1;
+            B.nlig = a.n_ligands;
+            B.lig_off = loff;
+            B.sigma_inf = std::isinf(a.sigma) ? 1 : 0;
+            B.sigma = B.sigma_inf ? 0.0 : a.sigma * 1.0 * nu * nu / L.ny;  // units rho nu^2 / H
+            B.ycr = a.y_cr;
+            B.yeq = a.y_eq;
+            B.Pf = 1.0 - std::exp(-a.kf_dt);
+            B.kr0_dt = a.kr0_dt;
+            B.xi = a.xi;
+            // sites at arc lengths (k + 1/2) P / n along the current chain
+            std::vector<double> cum(nv + 1, 0.0);
+            for (int l = 0; l < nv; ++l) {
+                int w = (l + 1) % nv;
+                double dx = h.xy[2 * w] - h.xy[2 * l], dy = h.xy[2 * w + 1] - h.xy[2 * l + 1];
+                cum[l + 1] = cum[l] + std::sqrt(dx * dx + dy * dy);
+            }
+            int l = 0;
+            for (int k = 0; k < a.n_ligands; ++k) {
+                double s = (k + 0.5) * cum[nv] / a.n_ligands;
+                while (l < nv - 1 && s > cum[l + 1]) ++l;
+                double t = (s - cum[l]) / (cum[l + 1] - cum[l]);
+                t = std::min(1.0, std::max(0.0, t));
+                int w = (l + 1) % nv;
+                double px = h.xy[2 * l] + t * (h.xy[2 * w] - h.xy[2 * l]);
+                double py = h.xy[2 * l + 1] + t * (h.xy[2 * w + 1] - h.xy[2 * l + 1]);
+                lig_el[loff + k] = off + l;
+                lig_t[loff + k] = t;
+                site_off[off + l + 1] += 1;
+                if (std::min(py, (double)L.ny - py) < a.y_cr) {
+                    bound[loff + k] = 1;
+                    anchor[loff + k] = px;
+                    anchor[nlig + loff + k] = (py < (double)L.ny - py) ? 0.0 : (double)L.ny;
+                    B.nl0 += 1;
+                }
+            }
+            bo[BO_NBOUND] = B.nl0;
+            loff += a.n_ligands;
+        }
+        off += nv;
+    }
+    for (int e = 0; e < nmark; ++e) site_off[e + 1] += site_off[e];
+    d.r_act = 2.0 + std::max(1.2, 0.75 * lmax) + 1.0;
+    d.ring_cap = ctx->P.obs_capacity > 0 ? ctx->P.obs_capacity : 4096;
+
+    // device arrays
+    auto& reg = ctx->allocs;
+    const size_t rs = ctx->rsz;
+    const size_t nm1 = std::max(nmark, 1), nl1 = std::max(nlig, 1);
+    BodyConst* dbody = nullptr;
+    void *dl0 = nullptr, *dth0 = nullptr, *dligt = nullptr;
+    double* drref = nullptr;
+    int32_t *dligel = nullptr, *dsite = nullptr;
+    CK(dalloc(reg, &d.pos[0], 2 * nm1));
+    CK(dalloc(reg, &d.pos[1], 2 * nm1));
+    CK(dalloc(reg, &dbody, std::max(nb, 1)));
+    CK(dalloc(reg, &d.rigid, (size_t)std::max(nb, 1) * RG_N));
+    CK(dalloc(reg, reinterpret_cast<char**>(&dl0), nm1 * rs));
+    CK(dalloc(reg, reinterpret_cast<char**>(&dth0), nm1 * rs));
+    CK(dalloc(reg, &drref, 2 * nm1));
+    CK(dalloc(reg, &dligel, nl1));
+    CK(dalloc(reg, reinterpret_cast<char**>(&dligt), nl1 * rs));
+    CK(dalloc(reg, &d.bound, nl1));
+    CK(dalloc(reg, &d.anchor, 2 * nl1));
+    CK(dalloc(reg, reinterpret_cast<char**>(&d.margin), nl1 * rs));
+    CK(dalloc(reg, &dsite, (size_t)nmark + 1));
+    CK(dalloc(reg, reinterpret_cast<char**>(&d.diag), (size_t)NDIAG * nm1 * rs));
+    CK(dalloc(reg, &d.body_obs[0], (size_t)std::max(nb, 1) * BO_N));
+    CK(dalloc(reg, &d.body_obs[1], (size_t)std::max(nb, 1) * BO_N));
+    CK(dalloc(reg, &d.ring, (size_t)d.ring_cap));
+    CK(dalloc(reg, reinterpret_cast<char**>(&d.mk[0]), 4 * nm1 * rs));
+    CK(dalloc(reg, reinterpret_cast<char**>(&d.mk[1]), 4 * nm1 * rs));
+    CK(dalloc(reg, &d.mask[0], (size_t)L.ntiles * d.mw));
+    CK(dalloc(reg, &d.mask[1], (size_t)L.ntiles * d.mw));
+    d.body = dbody;
+    d.l0 = dl0;
+    d.th0 = dth0;
+    d.rref = drref;
+    d.lig_el = dligel;
+    d.lig_t = dligt;
+    d.site_off = dsite;
+
+    auto up_real = [&](void* dst, const std::vector<double>& src) -> cudaError_t {
+        if (ctx->prec == PREC_F64) return cudaMemcpy(dst, src.data(), src.size() * 8, cudaMemcpyHostToDevice);
+        std::vector<float> t(src.begin(), src.end());
+        return cudaMemcpy(dst, t.data(), t.size() * 4, cudaMemcpyHostToDevice);
+    };
+    CK(cudaMemcpy(d.pos[0], pos.data(), pos.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.pos[1], pos.data(), pos.size() * 8, cudaMemcpyHostToDevice));
+    if (nb) CK(cudaMemcpy(dbody, bc.data(), bc.size() * sizeof(BodyConst), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.rigid, rig.data(), rig.size() * 8, cudaMemcpyHostToDevice));
+    CK(up_real(dl0, l0));
+    CK(up_real(dth0, th0));
+    CK(cudaMemcpy(drref, rref.data(), rref.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dligel, lig_el.data(), lig_el.size() * 4, cudaMemcpyHostToDevice));
+    CK(up_real(dligt, lig_t));
+    CK(cudaMemcpy(d.bound, bound.data(), bound.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.anchor, anchor.data(), anchor.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemset(d.margin, 0, nl1 * rs));
+    CK(cudaMemcpy(dsite, site_off.data(), site_off.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemset(d.diag, 0, (size_t)NDIAG * nm1 * rs));
+    CK(cudaMemcpy(d.body_obs[0], bobs.data(), bobs.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.body_obs[1], bobs.data(), bobs.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemset(d.ring, 0, (size_t)d.ring_cap * sizeof(lbib_obs)));
+    CK(cudaMemset(d.mk[0], 0, 4 * nm1 * rs));
+    CK(cudaMemset(d.mk[1], 0, 4 * nm1 * rs));
+    CK(cudaMemset(d.mask[0], 0, (size_t)L.ntiles * d.mw * 4));
+    CK(cudaMemset(d.mask[1], 0, (size_t)L.ntiles * d.mw * 4));
+    if (nb) {
+        if (lagrangian_smem_bytes(ctx->prec, d.nv_max) > 227 * 1024)
+            return fail(ctx, LBIB_ERR_UNSUPPORTED, "membrane too large for one block's shared memory");
+        CK(configure_kernels(ctx->prec, d.nv_max));
+        CK(launch_activate(d, ctx->prec, ctx->s_f, 3, ctx->stream));
+    }
+    ctx->near_grid = std::max(1, std::min(L.ntiles, 4 * 152));
+    ctx->finalized = true;
+    if (nb) {
+        lbib_status s = ensure_graphs(ctx);
+        if (s != LBIB_OK) return s;
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBIB_OK;
+}
+
+lbib_status pre_read(lbib_ctx* ctx)
+{
+    lbib_status s = finalize(ctx);
+    if (s != LBIB_OK) return s;
+    s = finish_pending(ctx);
+    if (s != LBIB_OK) return s;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return check_status(ctx);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+const char* lbib_last_error(lbib_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+lbib_status lbib_create(const lbib_fluid_params* P, lbib_ctx** out)
+{
+    lbib_ctx* ctx = nullptr;
+    if (!P || !out) return fail(nullptr, LBIB_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (P->nx < 3 || P->ny < 2) return fail(nullptr, LBIB_ERR_INVALID_ARG, "need nx >= 3 and ny >= 2");
+    if (!(P->tau > 0.5)) return fail(nullptr, LBIB_ERR_INVALID_ARG, "tau must exceed 1/2");
+    if (!(P->re >= 0.0) || !(P->rho_out > 0.0)) return fail(nullptr, LBIB_ERR_INVALID_ARG, "re >= 0 and rho_out > 0");
+    if (P->bc_mode != LBIB_BC_INLET_OUTLET && P->bc_mode != LBIB_BC_PERIODIC_FORCE)
+        return fail(nullptr, LBIB_ERR_INVALID_ARG, "unknown bc_mode");
+    if (P->storage == LBIB_STORE_BF16 || P->storage == LBIB_STORE_FP16)
+        return fail(nullptr, LBIB_ERR_UNSUPPORTED, "16-bit population storage is not built");
+    if (P->storage != LBIB_STORE_FP64 && P->storage != LBIB_STORE_FP32)
+        return fail(nullptr, LBIB_ERR_INVALID_ARG, "unknown storage");
+    if (P->obs_capacity < 0) return fail(nullptr, LBIB_ERR_INVALID_ARG, "obs_capacity < 0");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || P->device < 0 || P->device >= ndev) {
+        cudaGetLastError();
+        return fail(nullptr, LBIB_ERR_CUDA, "no CUDA device with that ordinal");
+    }
+    ctx = new (std::nothrow) lbib_ctx();
+    if (!ctx) return fail(nullptr, LBIB_ERR_OOM, "host allocation failed");
+    ctx->P = *P;
+    ctx->device = P->device;
+    DeviceGuard guard(ctx->device);
+    ctx->prec = (P->storage == LBIB_STORE_FP64) ? PREC_F64 : PREC_F32;
+    ctx->rsz = (ctx->prec == PREC_F64) ? 8 : 4;
+    Lattice& L = ctx->d.L;
+    L.nx = P->nx;
+    L.ny = P->ny;
+    L.ntx = (P->nx + TX - 1) / TX;
+    L.nty = (P->ny + TY - 1) / TY;
+    L.nxp = L.ntx * TX;
+    L.ntiles = L.ntx * L.nty;
+    L.bc = P->bc_mode;
+    long long qs = (long long)L.nxp * L.ny;
+    if (qs * 9 >= (1LL << 31)) {
+        delete ctx;
+        return fail(nullptr, LBIB_ERR_UNSUPPORTED, "lattice too large for 32-bit indexing");
+    }
+    L.qstride = (int)qs;
+    L.tau = P->tau;
+    L.omega = 1.0 / P->tau;
+    L.nu = (P->tau - 0.5) / 3.0;
+    L.umax = P->re * L.nu / P->ny;  // Re = u_max H / nu
+    L.rho_out = P->rho_out;
+    L.gx = P->gx;
+    L.gy = P->gy;
+    Dev& d = ctx->d;
+    d.list_cap = L.ntiles;
+    d.dcut = 2.0;
+    d.probe = 1.2;
+    d.uscale = L.umax / P->ny;
+    d.seed = P->seed;
+    d.ring_cap = 1;
+    auto bail = [&](lbib_status s) {
+        std::string m = ctx->err;
+        lbib_destroy(ctx);
+        g_create_error = m;
+        return s;
+    };
+#define CKC(call)                                                           \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return bail(cuda_fail(ctx, e_, #call));      \
+    } while (0)
+    auto& reg = ctx->allocs;
+    size_t nq = (size_t)9 * qs, nn = (size_t)qs;
+    CKC(dalloc(reg, reinterpret_cast<char**>(&d.f[0]), nq * ctx->rsz));
+    CKC(dalloc(reg, reinterpret_cast<char**>(&d.f[1]), nq * ctx->rsz));
+    CKC(dalloc(reg, reinterpret_cast<char**>(&d.drho), nn * ctx->rsz));
+    CKC(dalloc(reg, reinterpret_cast<char**>(&d.ux), nn * ctx->rsz));
+    CKC(dalloc(reg, reinterpret_cast<char**>(&d.uy), nn * ctx->rsz));
+    CKC(dalloc(reg, &d.fresh, L.ntiles));
+    CKC(dalloc(reg, &d.nearflag[0], L.ntiles));
+    CKC(dalloc(reg, &d.nearflag[1], L.ntiles));
+    for (int i = 0; i < 3; ++i) CKC(dalloc(reg, &d.list[i], d.list_cap));
+    CKC(dalloc(reg, &d.count, 3));
+    CKC(dalloc(reg, &d.step, 1));
+    CKC(dalloc(reg, &d.status, 1));
+    CKC(dalloc(reg, &d.ticket, 1));
+    CKC(cudaMemset(d.f[1], 0, nq * ctx->rsz));
+    CKC(cudaMemset(d.drho, 0, nn * ctx->rsz));
+    CKC(cudaMemset(d.ux, 0, nn * ctx->rsz));
+    CKC(cudaMemset(d.uy, 0, nn * ctx->rsz));
+    CKC(cudaMemset(d.fresh, 0x80, L.ntiles * 4));  // matches no step
+    CKC(cudaMemset(d.nearflag[0], 0, L.ntiles * 4));
+    CKC(cudaMemset(d.nearflag[1], 0, L.ntiles * 4));
+    CKC(cudaMemset(d.count, 0, 12));
+    CKC(cudaMemset(d.step, 0, 8));
+    CKC(cudaMemset(d.status, 0, 4));
+    CKC(cudaMemset(d.ticket, 0, 4));
+    if (P->cuda_stream) {
+        ctx->stream = static_cast<cudaStream_t>(P->cuda_stream);
+    } else {
+        CKC(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    }
+    CKC(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    CKC(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+    CKC(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    CKC(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    for (int i = 0; i < 6; ++i) CKC(cudaEventCreate(&ctx->pe[i]));
+    CKC(launch_init_populations(d, ctx->prec, 0, ctx->stream));
+    CKC(cudaStreamSynchronize(ctx->stream));
+#undef CKC
+    *out = ctx;
+    return LBIB_OK;
+}
+
+lbib_status lbib_add_membrane(lbib_ctx* ctx, const lbib_membrane_desc* m, int32_t* id_out)
+{
+    if (!ctx || !m) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    if (ctx->finalized) return fail(ctx, LBIB_ERR_STATE, "membranes must be added before the first advance");
+    if ((int)ctx->bodies.size() >= MAX_BODIES) return fail(ctx, LBIB_ERR_UNSUPPORTED, "too many bodies");
+    if (m->nv < 3 || m->nv > MAX_NV || !m->xy) return fail(ctx, LBIB_ERR_INVALID_ARG, "need 3 <= nv <= 1024 and xy");
+    if (m->kind != LBIB_CELL && m->kind != LBIB_PARTICLE) return fail(ctx, LBIB_ERR_INVALID_ARG, "unknown kind");
+    if (m->motion < LBIB_DEFORMABLE || m->motion > LBIB_FIXED) return fail(ctx, LBIB_ERR_INVALID_ARG, "unknown motion");
+    if (m->motion == LBIB_DEFORMABLE && !(m->ca > 0.0))
+        return fail(ctx, LBIB_ERR_INVALID_ARG, "a deformable membrane needs Ca > 0");
+    if (!(m->density_ratio > 0.0)) return fail(ctx, LBIB_ERR_INVALID_ARG, "density_ratio must be > 0");
+    HostBody h;
+    h.kind = m->kind;
+    h.motion = m->motion;
+    h.nv = m->nv;
+    h.xy.assign(m->xy, m->xy + 2 * (size_t)m->nv);
+    if (m->xy_ref) h.xy_ref.assign(m->xy_ref, m->xy_ref + 2 * (size_t)m->nv);
+    for (double v : h.xy)
+        if (!std::isfinite(v)) return fail(ctx, LBIB_ERR_INVALID_ARG, "non-finite vertex");
+    if (polygon(h.xy).A <= 0.0 || (!h.xy_ref.empty() && polygon(h.xy_ref).A <= 0.0))
+        return fail(ctx, LBIB_ERR_INVALID_ARG, "chains must be counter-clockwise with positive area");
+    h.ca = m->ca;
+    h.beta = m->beta;
+    h.ka = m->ka;
+    h.dens = m->density_ratio;
+    ctx->bodies.push_back(h);
+    if (id_out) *id_out = (int32_t)ctx->bodies.size() - 1;
+    return LBIB_OK;
+}
+
+lbib_status lbib_set_adhesion(lbib_ctx* ctx, int32_t body, const lbib_adhesion_params* a)
+{
+    if (!ctx || !a) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    if (ctx->finalized) return fail(ctx, LBIB_ERR_STATE, "adhesion must be set before the first advance");
+    if (body < 0 || body >= (int)ctx->bodies.size()) return fail(ctx, LBIB_ERR_INVALID_ARG, "no such body");
+    if (a->n_ligands <= 0 || !(a->y_cr >= 0) || !(a->kf_dt >= 0) || !(a->kr0_dt >= 0) || std::isnan(a->sigma))
+        return fail(ctx, LBIB_ERR_INVALID_ARG, "invalid adhesion parameters");
+    if (std::isinf(a->sigma) && ctx->bodies[body].motion != LBIB_FIXED)
+        return fail(ctx, LBIB_ERR_INVALID_ARG, "sigma = inf requires a FIXED particle");
+    ctx->bodies[body].adhesive = true;
+    ctx->bodies[body].adh = *a;
+    return LBIB_OK;
+}
+
+lbib_status lbib_advance(lbib_ctx* ctx, int64_t nsteps)
+{
+    if (!ctx) return fail(ctx, LBIB_ERR_INVALID_ARG, "null context");
+    if (nsteps < 0) return fail(ctx, LBIB_ERR_INVALID_ARG, "nsteps < 0");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = finalize(ctx);
+    if (s != LBIB_OK) return s;
+    Dev& d = ctx->d;
+    if (d.nbodies == 0) {
+        for (int64_t k = 0; k < nsteps; ++k) {
+            CK(launch_lbm_bulk(d, ctx->prec, (int)(ctx->s_f & 1), ctx->stream));
+            ctx->s_f += 1;
+        }
+        ctx->s_l = ctx->s_f;
+        return LBIB_OK;
+    }
+    if (nsteps == 0) return LBIB_OK;
+    s = ensure_graphs(ctx);
+    if (s != LBIB_OK) return s;
+    if (ctx->s_l == ctx->s_f) {  // open the pipeline: lattice step s_f alone
+        int p = (int)(ctx->s_f & 1);
+        CK(launch_lbm_bulk(d, ctx->prec, p, ctx->stream));
+        CK(launch_lbm_near(d, ctx->prec, p, ctx->near_grid, ctx->stream));
+        ctx->s_f += 1;
+        nsteps -= 1;
+        ctx->profiled_last = false;
+    }
+    const int prof = ctx->profiling ? 1 : 0;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        CK(cudaGraphLaunch(ctx->unit[prof][ctx->s_f & 1], ctx->stream));
+        ctx->s_f += 1;
+        ctx->s_l += 1;
+        ctx->profiled_last = (prof != 0);
+    }
+    return LBIB_OK;
+}
+
+lbib_status lbib_sync(lbib_ctx* ctx)
+{
+    if (!ctx) return fail(ctx, LBIB_ERR_INVALID_ARG, "null context");
+    DeviceGuard guard(ctx->device);
+    return pre_read(ctx);
+}
+
+lbib_status lbib_step_count(lbib_ctx* ctx, int64_t* steps)
+{
+    if (!ctx || !steps) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = pre_read(ctx);
+    *steps = ctx->s_f;
+    return s;
+}
+
+static lbib_status read_macro(lbib_ctx* ctx, double* rho, double* ux, double* uy, size_t n)
+{
+    const Lattice& L = ctx->d.L;
+    size_t nn = (size_t)L.nx * L.ny;
+    if (n < nn) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than nx * ny");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = pre_read(ctx);
+    if (s != LBIB_OK) return s;
+    if (!ctx->macro_buf) CK(dalloc(ctx->allocs, &ctx->macro_buf, 3 * nn));
+    int64_t m = ctx->s_f - 1;
+    CK(launch_macro(ctx->d, ctx->prec, (int)(ctx->s_f & 1), m, ctx->macro_buf, ctx->macro_buf + nn,
+                    ctx->macro_buf + 2 * nn, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (rho) CK(cudaMemcpy(rho, ctx->macro_buf, nn * 8, cudaMemcpyDeviceToHost));
+    if (ux) CK(cudaMemcpy(ux, ctx->macro_buf + nn, nn * 8, cudaMemcpyDeviceToHost));
+    if (uy) CK(cudaMemcpy(uy, ctx->macro_buf + 2 * nn, nn * 8, cudaMemcpyDeviceToHost));
+    return LBIB_OK;
+}
+
+lbib_status lbib_read_velocity(lbib_ctx* ctx, double* ux, double* uy, size_t n)
+{
+    if (!ctx || !ux || !uy) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    return read_macro(ctx, nullptr, ux, uy, n);
+}
+
+lbib_status lbib_read_density(lbib_ctx* ctx, double* rho, size_t n)
+{
+    if (!ctx || !rho) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    return read_macro(ctx, rho, nullptr, nullptr, n);
+}
+
+lbib_status lbib_read_velocity_device(lbib_ctx* ctx, void* dux, void* duy, size_t n, int32_t dtype)
+{
+    if (!ctx || !dux || !duy) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    if (dtype != 0 && dtype != 1) return fail(ctx, LBIB_ERR_INVALID_ARG, "dtype must be 0 (float) or 1 (double)");
+    const Lattice& L = ctx->d.L;
+    if (n < (size_t)L.nx * L.ny) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than nx * ny");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = finalize(ctx);
+    if (s != LBIB_OK) return s;
+    s = finish_pending(ctx);
+    if (s != LBIB_OK) return s;
+    CK(launch_macro_typed(ctx->d, ctx->prec, (int)(ctx->s_f & 1), ctx->s_f - 1, dux, duy, dtype, ctx->stream));
+    return LBIB_OK;
+}
+
+static double wrest(int q) { return q == 0 ? 4.0 / 9.0 : (q < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+
+lbib_status lbib_read_populations(lbib_ctx* ctx, double* f, size_t n)
+{
+    if (!ctx || !f) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    const Lattice& L = ctx->d.L;
+    size_t nn = (size_t)L.nx * L.ny;
+    if (n < 9 * nn) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than 9 nx ny");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = pre_read(ctx);
+    if (s != LBIB_OK) return s;
+    size_t nq = (size_t)9 * L.qstride;
+    std::vector<char> raw(nq * ctx->rsz);
+    CK(cudaMemcpy(raw.data(), ctx->d.f[ctx->s_f & 1], raw.size(), cudaMemcpyDeviceToHost));
+    for (int q = 0; q < 9; ++q)
+        for (int y = 0; y < L.ny; ++y)
+            for (int x = 0; x < L.nx; ++x) {
+                size_t i = (size_t)q * L.qstride + (size_t)y * L.nxp + x;
+                double v = ctx->prec == PREC_F64 ? reinterpret_cast<double*>(raw.data())[i]
+                                                 : (double)reinterpret_cast<float*>(raw.data())[i];
+                f[((size_t)q * L.ny + y) * L.nx + x] = v + wrest(q);
+            }
+    return LBIB_OK;
+}
+
+lbib_status lbib_write_populations(lbib_ctx* ctx, const double* f, size_t n)
+{
+    if (!ctx || !f) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    const Lattice& L = ctx->d.L;
+    size_t nn = (size_t)L.nx * L.ny;
+    if (n < 9 * nn) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than 9 nx ny");
+    if (ctx->s_f != 0) return fail(ctx, LBIB_ERR_STATE, "populations can only be written before the first step");
+    DeviceGuard guard(ctx->device);
+    size_t nq = (size_t)9 * L.qstride;
+    std::vector<char> raw(nq * ctx->rsz, 0);
+    for (int q = 0; q < 9; ++q)
+        for (int y = 0; y < L.ny; ++y)
+            for (int x = 0; x < L.nx; ++x) {
+                size_t i = (size_t)q * L.qstride + (size_t)y * L.nxp + x;
+                double v = f[((size_t)q * L.ny + y) * L.nx + x] - wrest(q);
+                if (ctx->prec == PREC_F64) reinterpret_cast<double*>(raw.data())[i] = v;
+                else reinterpret_cast<float*>(raw.data())[i] = (float)v;
+            }
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(ctx->d.f[0], raw.data(), raw.size(), cudaMemcpyHostToDevice));
+    return LBIB_OK;
+}
+
+lbib_status lbib_read_observables(lbib_ctx* ctx, lbib_obs* out, size_t cap, size_t* n_out)
+{
+    if (!ctx || !n_out || (cap && !out)) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    *n_out = 0;
+    DeviceGuard guard(ctx->device);
+    lbib_status s = pre_read(ctx);
+    if (ctx->d.nbodies == 0) return s;
+    const int64_t last = ctx->s_l, rc = ctx->d.ring_cap;
+    int64_t first = std::max<int64_t>(ctx->obs_consumed + 1, last - rc + 1);
+    int64_t cnt = std::min<int64_t>((int64_t)cap, last - first + 1);
+    for (int64_t k = 0; k < cnt; ++k)
+        CK(cudaMemcpy(out + k, ctx->d.ring + ((first + k) % rc), sizeof(lbib_obs), cudaMemcpyDeviceToHost));
+    if (cnt > 0) ctx->obs_consumed = first + cnt - 1;
+    *n_out = (size_t)std::max<int64_t>(cnt, 0);
+    return s;
+}
+
+lbib_status lbib_read_markers(lbib_ctx* ctx, int32_t id, double* xy, size_t n)
+{
+    if (!ctx || !xy) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    if (id < 0 || id >= (int)ctx->bodies.size()) return fail(ctx, LBIB_ERR_INVALID_ARG, "no such body");
+    const int nv = ctx->bodies[id].nv;
+    if (n < 2 * (size_t)nv) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than 2 nv");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = pre_read(ctx);
+    if (s != LBIB_OK && s != LBIB_ERR_DIVERGED) return s;
+    const Dev& d = ctx->d;
+    int off = 0;
+    for (int b = 0; b < id; ++b) off += ctx->bodies[b].nv;
+    std::vector<double> x(nv), y(nv);
+    const double* P = d.pos[ctx->s_l & 1];
+    CK(cudaMemcpy(x.data(), P + off, nv * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(y.data(), P + d.nmark + off, nv * 8, cudaMemcpyDeviceToHost));
+    for (int v = 0; v < nv; ++v) {
+        xy[2 * v] = x[v];
+        xy[2 * v + 1] = y[v];
+    }
+    return s;
+}
+
+lbib_status lbib_read_body_field(lbib_ctx* ctx, int32_t id, int32_t field, double* out, size_t n)
+{
+    if (!ctx || !out) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    if (id < 0 || id >= (int)ctx->bodies.size()) return fail(ctx, LBIB_ERR_INVALID_ARG, "no such body");
+    if (field < 0 || field >= LBIB_FIELD_COUNT) return fail(ctx, LBIB_ERR_INVALID_ARG, "unknown field");
+    const int nv = ctx->bodies[id].nv;
+    if (n < (size_t)nv) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than nv");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = pre_read(ctx);
+    if (s != LBIB_OK && s != LBIB_ERR_DIVERGED) return s;
+    const Dev& d = ctx->d;
+    int off = 0;
+    for (int b = 0; b < id; ++b) off += ctx->bodies[b].nv;
+    if (field <= LBIB_FIELD_YPREV) {
+        int64_t k = (field <= LBIB_FIELD_Y) ? ctx->s_l : ctx->s_l - 1;
+        const double* P = d.pos[k & 1];
+        size_t o = (field == LBIB_FIELD_X || field == LBIB_FIELD_XPREV) ? off : (size_t)d.nmark + off;
+        CK(cudaMemcpy(out, P + o, nv * 8, cudaMemcpyDeviceToHost));
+        return s;
+    }
+    size_t o = (size_t)field * d.nmark + off;
+    if (ctx->prec == PREC_F64) {
+        CK(cudaMemcpy(out, static_cast<double*>(d.diag) + o, nv * 8, cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<float> t(nv);
+        CK(cudaMemcpy(t.data(), static_cast<float*>(d.diag) + o, nv * 4, cudaMemcpyDeviceToHost));
+        for (int v = 0; v < nv; ++v) out[v] = t[v];
+    }
+    return s;
+}
+
+lbib_status lbib_read_bonds(lbib_ctx* ctx, int32_t id, int32_t* bound, double* ax, double* ay, double* margin,
+                            size_t n)
+{
+    if (!ctx) return fail(ctx, LBIB_ERR_INVALID_ARG, "null context");
+    if (id < 0 || id >= (int)ctx->bodies.size()) return fail(ctx, LBIB_ERR_INVALID_ARG, "no such body");
+    const HostBody& h = ctx->bodies[id];
+    if (!h.adhesive) return fail(ctx, LBIB_ERR_INVALID_ARG, "body has no ligands");
+    const int nl = h.adh.n_ligands;
+    if (n < (size_t)nl) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than n_ligands");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = pre_read(ctx);
+    if (s != LBIB_OK && s != LBIB_ERR_DIVERGED) return s;
+    const Dev& d = ctx->d;
+    int loff = 0;
+    for (int b = 0; b < id; ++b)
+        if (ctx->bodies[b].adhesive) loff += ctx->bodies[b].adh.n_ligands;
+    if (bound) CK(cudaMemcpy(bound, d.bound + loff, nl * 4, cudaMemcpyDeviceToHost));
+    if (ax) CK(cudaMemcpy(ax, d.anchor + loff, nl * 8, cudaMemcpyDeviceToHost));
+    if (ay) CK(cudaMemcpy(ay, d.anchor + d.nlig + loff, nl * 8, cudaMemcpyDeviceToHost));
+    if (margin) {
+        if (ctx->prec == PREC_F64) {
+            CK(cudaMemcpy(margin, static_cast<double*>(d.margin) + loff, nl * 8, cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> t(nl);
+            CK(cudaMemcpy(t.data(), static_cast<float*>(d.margin) + loff, nl * 4, cudaMemcpyDeviceToHost));
+            for (int k = 0; k < nl; ++k) margin[k] = t[k];
+        }
+    }
+    return s;
+}
+
+// ------------------------------------------------------------- checkpoints
+// layout: header | populations f*^{s-1} | X^s | X^{s-1} | rigid | bonds |
+//         anchors | markers for lattice step s | extents of X^s
+namespace {
+struct CkHeader {
+    uint64_t magic;
+    int32_t nx, ny, nbodies, nmark, nlig, prec;
+    int64_t steps;
+    uint64_t seed;
+};
+constexpr uint64_t kMagic = 0x314b4350424942ULL;  // "LBIBPCK1"
+
+size_t state_bytes(const lbib_ctx* ctx)
+{
+    const Dev& d = ctx->d;
+    size_t nq = (size_t)9 * d.L.qstride;
+    size_t nm = std::max(d.nmark, 1), nl = std::max(d.nlig, 1), nb = std::max(d.nbodies, 1);
+    return sizeof(CkHeader) + nq * ctx->rsz + 4 * nm * 8 + nb * RG_N * 8 + nl * 4 + 2 * nl * 8 +
+           4 * nm * ctx->rsz + nb * BO_N * 8;
+}
+}  // namespace
+
+lbib_status lbib_state_size(lbib_ctx* ctx, size_t* bytes)
+{
+    if (!ctx || !bytes) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = finalize(ctx);
+    if (s != LBIB_OK) return s;
+    *bytes = state_bytes(ctx);
+    return LBIB_OK;
+}
+
+lbib_status lbib_save_state(lbib_ctx* ctx, void* buf, size_t bytes)
+{
+    if (!ctx || !buf) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = pre_read(ctx);
+    if (s != LBIB_OK) return s;
+    if (bytes < state_bytes(ctx)) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than lbib_state_size");
+    const Dev& d = ctx->d;
+    const int64_t st = ctx->s_f;
+    char* p = static_cast<char*>(buf);
+    CkHeader h{kMagic, d.L.nx, d.L.ny, d.nbodies, d.nmark, d.nlig, ctx->prec, st, d.seed};
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    size_t nq = (size_t)9 * d.L.qstride;
+    size_t nm = std::max(d.nmark, 1), nl = std::max(d.nlig, 1), nb = std::max(d.nbodies, 1);
+    CK(cudaMemcpy(p, d.f[st & 1], nq * ctx->rsz, cudaMemcpyDeviceToHost));
+    p += nq * ctx->rsz;
+    CK(cudaMemcpy(p, d.pos[st & 1], 2 * nm * 8, cudaMemcpyDeviceToHost));
+    p += 2 * nm * 8;
+    CK(cudaMemcpy(p, d.pos[(st + 1) & 1], 2 * nm * 8, cudaMemcpyDeviceToHost));
+    p += 2 * nm * 8;
+    CK(cudaMemcpy(p, d.rigid, nb * RG_N * 8, cudaMemcpyDeviceToHost));
+    p += nb * RG_N * 8;
+    CK(cudaMemcpy(p, d.bound, nl * 4, cudaMemcpyDeviceToHost));
+    p += nl * 4;
+    CK(cudaMemcpy(p, d.anchor, 2 * nl * 8, cudaMemcpyDeviceToHost));
+    p += 2 * nl * 8;
+    CK(cudaMemcpy(p, d.mk[st & 1], 4 * nm * ctx->rsz, cudaMemcpyDeviceToHost));
+    p += 4 * nm * ctx->rsz;
+    CK(cudaMemcpy(p, d.body_obs[st & 1], nb * BO_N * 8, cudaMemcpyDeviceToHost));
+    return LBIB_OK;
+}
+
+lbib_status lbib_load_state(lbib_ctx* ctx, const void* buf, size_t bytes)
+{
+    if (!ctx || !buf) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = pre_read(ctx);
+    if (s != LBIB_OK && s != LBIB_ERR_DIVERGED && s != LBIB_ERR_STATE) return s;
+    if (bytes < state_bytes(ctx)) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than lbib_state_size");
+    Dev& d = ctx->d;
+    const char* p = static_cast<const char*>(buf);
+    CkHeader h;
+    std::memcpy(&h, p, sizeof(h));
+    p += sizeof(h);
+    if (h.magic != kMagic || h.nx != d.L.nx || h.ny != d.L.ny || h.nbodies != d.nbodies || h.nmark != d.nmark ||
+        h.nlig != d.nlig || h.prec != ctx->prec || h.steps < 0)
+        return fail(ctx, LBIB_ERR_INVALID_ARG, "checkpoint does not match this context");
+    const int64_t st = h.steps;
+    size_t nq = (size_t)9 * d.L.qstride;
+    size_t nm = std::max(d.nmark, 1), nl = std::max(d.nlig, 1), nb = std::max(d.nbodies, 1);
+    CK(cudaMemcpy(d.f[st & 1], p, nq * ctx->rsz, cudaMemcpyHostToDevice));
+    p += nq * ctx->rsz;
+    CK(cudaMemcpy(d.pos[st & 1], p, 2 * nm * 8, cudaMemcpyHostToDevice));
+    p += 2 * nm * 8;
+    CK(cudaMemcpy(d.pos[(st + 1) & 1], p, 2 * nm * 8, cudaMemcpyHostToDevice));
+    p += 2 * nm * 8;
+    CK(cudaMemcpy(d.rigid, p, nb * RG_N * 8, cudaMemcpyHostToDevice));
+    p += nb * RG_N * 8;
+    CK(cudaMemcpy(d.bound, p, nl * 4, cudaMemcpyHostToDevice));
+    p += nl * 4;
+    CK(cudaMemcpy(d.anchor, p, 2 * nl * 8, cudaMemcpyHostToDevice));
+    p += 2 * nl * 8;
+    CK(cudaMemcpy(d.mk[st & 1], p, 4 * nm * ctx->rsz, cudaMemcpyHostToDevice));
+    p += 4 * nm * ctx->rsz;
+    CK(cudaMemcpy(d.body_obs[st & 1], p, nb * BO_N * 8, cudaMemcpyHostToDevice));
+    // scheduling state is rebuilt from the restored positions and markers
+    const Lattice& L = d.L;
+    CK(cudaMemset(d.nearflag[0], 0, L.ntiles * 4));
+    CK(cudaMemset(d.nearflag[1], 0, L.ntiles * 4));
+    CK(cudaMemset(d.mask[0], 0, (size_t)L.ntiles * d.mw * 4));
+    CK(cudaMemset(d.mask[1], 0, (size_t)L.ntiles * d.mw * 4));
+    CK(cudaMemset(d.fresh, 0x80, L.ntiles * 4));
+    CK(cudaMemset(d.count, 0, 12));
+    CK(cudaMemset(d.status, 0, 4));
+    CK(cudaMemset(d.ticket, 0, 4));
+    CK(cudaMemcpy(d.step, &st, 8, cudaMemcpyHostToDevice));
+    ctx->s_f = ctx->s_l = st;
+    ctx->obs_consumed = st;
+    if (d.nbodies) {
+        CK(launch_activate(d, ctx->prec, st, 3, ctx->stream));
+        CK(launch_rebuild_mask(d, ctx->prec, (int)(st & 1), ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return check_status(ctx);
+}
+
+lbib_status lbib_set_profiling(lbib_ctx* ctx, int32_t enable)
+{
+    if (!ctx) return fail(ctx, LBIB_ERR_INVALID_ARG, "null context");
+    ctx->profiling = enable != 0;
+    return LBIB_OK;
+}
+
+lbib_status lbib_read_kernel_times(lbib_ctx* ctx, float* bulk_ms, float* lagr_ms, float* near_ms)
+{
+    if (!ctx) return fail(ctx, LBIB_ERR_INVALID_ARG, "null context");
+    DeviceGuard guard(ctx->device);
+    float t[3] = {0, 0, 0};
+    if (ctx->profiled_last) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaEventElapsedTime(&t[0], ctx->pe[0], ctx->pe[1]));
+        CK(cudaEventElapsedTime(&t[1], ctx->pe[2], ctx->pe[3]));
+        CK(cudaEventElapsedTime(&t[2], ctx->pe[4], ctx->pe[5]));
+    }
+    if (bulk_ms) *bulk_ms = t[0];
+    if (lagr_ms) *lagr_ms = t[1];
+    if (near_ms) *near_ms = t[2];
+    return LBIB_OK;
+}
+
+lbib_status lbib_describe(lbib_ctx* ctx, int32_t* kernels_per_step, int32_t* near_tiles, int32_t* tiles)
+{
+    if (!ctx) return fail(ctx, LBIB_ERR_INVALID_ARG, "null context");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = finalize(ctx);
+    if (s != LBIB_OK) return s;
+    if (kernels_per_step) *kernels_per_step = ctx->d.nbodies ? 3 : 1;
+    if (tiles) *tiles = ctx->d.L.ntiles;
+    if (near_tiles) {
+        int32_t c[3] = {0, 0, 0};
+        CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaMemcpy(c, ctx->d.count, 12, cudaMemcpyDeviceToHost));
+        *near_tiles = c[ctx->s_f % 3];
+    }
+    return LBIB_OK;
+}
+
+void lbib_destroy(lbib_ctx* ctx)
+{
+    if (!ctx) return;
+    DeviceGuard guard(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto& row : ctx->unit)
+        for (auto& g : row)
+            if (g) cudaGraphExecDestroy(g);
+    for (void* p : ctx->allocs) cudaFree(p);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    for (auto& e : ctx->pe)
+        if (e) cudaEventDestroy(e);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    cudaGetLastError();
+    delete ctx;
+}
+
+}  // extern "C"

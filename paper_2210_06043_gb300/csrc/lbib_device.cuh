@@ -1,0 +1,162 @@
+// lbib_device.cuh -- device helpers shared by the library's kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lbib_internal.cuh"
+
+namespace lbib {
+
+// D2Q9 weights printed after Eq. 3 (rest 4/9, axis 1/9, diagonal 1/36).
+template <typename R>
+__device__ __forceinline__ R wq(int q)
+{
+    return q == 0 ? R(4) / R(9) : (q < 5 ? R(1) / R(9) : R(1) / R(36));
+}
+
+// ------------------------------------------------------------ storage types
+template <typename S, typename R>
+__device__ __forceinline__ R ld(const S* p)
+{
+    return static_cast<R>(__ldg(p));
+}
+template <typename S, typename R>
+__device__ __forceinline__ void st(S* p, R v)
+{
+    *p = static_cast<S>(v);
+}
+
+// ------------------------------------------------------- Peskin 4-point kernel
+// phi(a), a = |r|: (3 - 2a + sqrt(2 - 4 (a - 1/2)^2)) / 8 on [0, 1],
+// (5 - 2a - sqrt(2 - 4 (a - 3/2)^2)) / 8 on (1, 2], zero beyond (Peskin 2002).
+template <typename R>
+__device__ __forceinline__ R peskin(R r)
+{
+    R a = fabs(r);
+    if (a <= R(1)) {
+        R t = a - R(0.5);
+        return (R(3) - R(2) * a + sqrt(R(2) - R(4) * t * t)) * R(0.125);
+    }
+    if (a <= R(2)) {
+        R t = a - R(1.5);
+        return (R(5) - R(2) * a - sqrt(R(2) - R(4) * t * t)) * R(0.125);
+    }
+    return R(0);
+}
+
+// d phi / d r
+template <typename R>
+__device__ __forceinline__ R peskin_d(R r)
+{
+    R a = fabs(r);
+    R g;
+    if (a <= R(1)) {
+        R t = a - R(0.5);
+        g = (R(-2) - R(4) * t / sqrt(R(2) - R(4) * t * t)) * R(0.125);
+    } else if (a <= R(2)) {
+        R t = a - R(1.5);
+        g = (R(-2) + R(4) * t / sqrt(R(2) - R(4) * t * t)) * R(0.125);
+    } else {
+        g = R(0);
+    }
+    return r < R(0) ? -g : g;
+}
+
+// ------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror & Shaw (SC'11): counter-based generator, 10 rounds.
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t a = 0xD2511F53u * c.x, ah = __umulhi(0xD2511F53u, c.x);
+        uint32_t b = 0xCD9E8D57u * c.z, bh = __umulhi(0xCD9E8D57u, c.z);
+        c = U4{bh ^ c.y ^ k0, b, ah ^ c.w ^ k1, a};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// uniform draw of ligand site `site` at Lagrangian step `n`: 24 high bits of the
+// first output word of counter (n_lo, n_hi, site, 0) under key (seed_lo, seed_hi)
+__device__ __forceinline__ float bond_draw(uint64_t seed, int64_t n, uint32_t site)
+{
+    U4 c{(uint32_t)(uint64_t)n, (uint32_t)((uint64_t)n >> 32), site, 0u};
+    U4 o = philox10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return (float)(o.x >> 8) * (1.0f / 16777216.0f);
+}
+
+// ------------------------------------------------------------- reductions
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the block (deterministic tree); every thread gets the result.
+// scratch: >= 32 elements of T in shared memory.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* scratch)
+{
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    T t = (lane < nw) ? scratch[lane] : T(0);
+    t = warp_sum(t);
+    return t;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_min(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_min(T v, T* scratch)
+{
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_min(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    T t = (lane < nw) ? scratch[lane] : scratch[0];
+    return warp_min(t);
+}
+template <typename T>
+__device__ __forceinline__ T block_max(T v, T* scratch)
+{
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_max(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    T t = (lane < nw) ? scratch[lane] : scratch[0];
+    return warp_max(t);
+}
+
+__device__ __forceinline__ int tile_of(const Lattice& L, int i, int j)
+{
+    return (j / TY) * L.ntx + (i / TX);
+}
+
+}  // namespace lbib

@@ -1,0 +1,127 @@
+// lbib_internal.cuh -- device data layout and device helpers of the capillary
+// solver (internal to the library; the public boundary is include/lbib.h).
+//
+// Layout in HBM
+//   populations  Store f[2][9][ny][nxp], stored as deviations f_i - w_i from the
+//                rest weights (w_i rho_ref, rho_ref = 1), double-buffered; the
+//                lattice step m reads f[m & 1] and writes f[(m + 1) & 1].
+//   tiles        32 x 4 nodes; one thread block of the lattice kernels updates
+//                one tile.  Tiles within R_act of a membrane are "near": their
+//                update adds the spread immersed-boundary force and writes
+//                rho - 1 and u for the Lagrangian kernel; all others are "bulk".
+//   markers      element centroids with their direct force times ds,
+//                double-buffered by the parity of the lattice step that
+//                consumes them; per near tile a bit mask of the markers whose
+//                4 x 4 stencil touches it (ascending marker order = the order in
+//                which the forces are summed).
+//   bodies       vertex positions in FP64 (per-step displacements at
+//                Re = 1e-2 are ~1e-5 dx, below FP32 resolution at channel
+//                coordinates); forces in the compute precision.
+#pragma once
+
+#include <cstdint>
+
+#include "../../include/lbib.h"
+
+namespace lbib {
+
+constexpr int TX = 32;            // tile width (nodes along x) = one warp
+constexpr int TY = 4;             // tile height
+constexpr int MAX_BODIES = 16;
+constexpr int MAX_NV = 1024;      // vertices per body
+constexpr int LAG_THREADS = 256;  // threads of the Lagrangian kernel's blocks
+constexpr int NDIAG = LBIB_FIELD_COUNT;
+
+// device status bits (host maps them to lbib_status)
+enum : uint32_t {
+    ST_DIVERGED = 1u,       // non-finite or non-positive density/velocity/positions
+    ST_READ_MISS = 2u,      // an interpolation stencil reached a tile not updated as near
+    ST_SPREAD_MISS = 4u,    // a spreading stencil reached a tile not scheduled as near
+    ST_LIST_OVERFLOW = 8u,  // near-tile list capacity exceeded
+};
+
+enum { PREC_F64 = 0, PREC_F32 = 1 };
+
+struct Lattice {
+    int nx, ny, nxp;          // nodes; padded row length (multiple of TX)
+    int ntx, nty, ntiles;     // tiles
+    int bc;                   // lbib_bc_mode
+    int qstride;              // ny * nxp
+    double tau, omega, nu, umax, rho_out, gx, gy;
+};
+
+struct BodyConst {
+    int kind, motion, nv, off;        // off: global index of vertex 0 / element 0
+    int adhesive, nlig, lig_off, nl0;
+    int sigma_inf, pad0, pad1, pad2;
+    double A0, P0;
+    double ks, kb, ka, mv, mass, inertia;
+    double sigma, ycr, yeq, Pf, kr0_dt, xi;
+};
+
+// rigid-body state per body (FP64): centroid, angle, BDF2 history
+enum { RG_XC = 0, RG_YC, RG_ANG, RG_U1X, RG_U1Y, RG_U2X, RG_U2Y, RG_W1, RG_W2, RG_N };
+// per-body observables/extent written by the Lagrangian kernel (FP64)
+enum { BO_AREA = 0, BO_PERIM, BO_CX, BO_CY, BO_NBOUND, BO_XMIN, BO_XMAX, BO_YMIN, BO_YMAX, BO_N };
+
+// Every device pointer of a context.  Passed by value to the kernels.
+struct Dev {
+    Lattice L;
+    // lattice state
+    void* f[2];                // Store
+    void* drho;                // Real [ny][nxp]: rho - 1 on near tiles
+    void* ux;                  // Real [ny][nxp]
+    void* uy;                  // Real [ny][nxp]
+    int32_t* fresh;            // [ntiles]: lattice step whose near update wrote rho/u
+    uint32_t* nearflag[2];     // [ntiles]: tile is near for lattice steps of this parity
+    int32_t* list[3];          // [list_cap]: near tiles of lattice step m, m % 3
+    int32_t* count;            // [3]
+    uint32_t* mask[2];         // [ntiles][mw]
+    int mw, list_cap;
+    // markers consumed by lattice step m: mk[m & 1] = Real [4][nmark] (x, y, fx ds, fy ds)
+    void* mk[2];
+    // Lagrangian state
+    int nbodies, nmark, nlig, nv_max;
+    double* pos[2];            // [2][nmark] (x block then y block); X^n in pos[n & 1]
+    const BodyConst* body;     // [nbodies]
+    double* rigid;             // [nbodies][RG_N]
+    const void* l0;            // Real [nmark] stress-free element lengths
+    const void* th0;           // Real [nmark] stress-free turning angles
+    const double* rref;        // [2][nmark] rigid vertex offsets at angle 0
+    const int32_t* lig_el;     // [nlig] element (global index) of each ligand site
+    const void* lig_t;         // Real [nlig] fraction along the element
+    int32_t* bound;            // [nlig]
+    double* anchor;            // [2][nlig]
+    void* margin;              // Real [nlig]
+    const int32_t* site_off;   // [nmark + 1] sites of element e: [site_off[e], site_off[e+1])
+    void* diag;                // Real [NDIAG][nmark]
+    double* body_obs[2];       // [nbodies][BO_N] of X^k in body_obs[k & 1]
+    lbib_obs* ring;
+    int ring_cap;
+    int first_cell, first_particle;
+    int64_t* step;             // Lagrangian step counter n (advanced by the last Lagrangian block)
+    uint32_t* status;
+    uint32_t* ticket;
+    double r_act;              // activation radius around markers (lattice units)
+    double dcut;               // repulsion cut-off (Eq. 12)
+    double probe;              // probe length (Sec. 2.6)
+    double uscale;             // observables: u_max / H
+    uint64_t seed;             // Philox key of the bond kinetics
+};
+
+// ------------------------------------------------------------------ launchers
+// (defined in lbib_lbm.cu and lbib_lag.cu; `prec` selects FP64 or FP32)
+cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, cudaStream_t s);
+cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, cudaStream_t s);
+cudaError_t launch_init_populations(const Dev& d, int prec, int buf, cudaStream_t s);
+cudaError_t launch_macro(const Dev& d, int prec, int buf, int64_t m, double* rho, double* ux, double* uy,
+                         cudaStream_t s);
+cudaError_t launch_macro_typed(const Dev& d, int prec, int buf, int64_t m, void* ux, void* uy, int dtype,
+                               cudaStream_t s);
+cudaError_t launch_lagrangian(const Dev& d, int prec, int parity, cudaStream_t s);
+cudaError_t launch_activate(const Dev& d, int prec, int64_t m, int which, cudaStream_t s);
+cudaError_t launch_rebuild_mask(const Dev& d, int prec, int parity, cudaStream_t s);
+size_t lagrangian_smem_bytes(int prec, int nv_max);
+cudaError_t configure_kernels(int prec, int nv_max);
+
+}  // namespace lbib

@@ -1,0 +1,368 @@
+// lbib_lbm.cu -- lattice kernels: fused pull streaming + boundary conditions +
+// moments + Guo-forced BGK collision over SoA deviation populations.
+//
+// One thread updates one node; a 32 x 4 block updates one tile.  The bulk
+// kernel covers every tile that no membrane can reach this step and has no
+// immersed-boundary force to add; the near kernel walks the compact list of
+// the other tiles, gathers the spread direct-forcing force of the markers
+// whose stencil touches the tile (bit mask, ascending marker order), applies
+// the same node update with that force and writes rho - 1 and u for the
+// Lagrangian kernel.
+//
+// Per node and step: Eq. 1 (streaming as a pull from x - e_i, collision),
+// Eq. 2 (equilibrium), Eq. 4 (forcing), Eqs. 5-6 (moments with half force),
+// halfway bounce-back on the walls y = 0, ny and Zou-He on the inlet x = 0
+// (plane-Poiseuille velocity, Sec. 3.1) and outlet x = nx - 1 (density).
+#include <cuda_runtime.h>
+
+#include "lbib_device.cuh"
+
+namespace lbib {
+
+__device__ __forceinline__ constexpr int cx(int q) { return (q == 1 || q == 5 || q == 8) ? 1 : ((q == 3 || q == 6 || q == 7) ? -1 : 0); }
+__device__ __forceinline__ constexpr int cy(int q) { return (q == 2 || q == 5 || q == 6) ? 1 : ((q == 4 || q == 7 || q == 8) ? -1 : 0); }
+__device__ __forceinline__ constexpr int op(int q) { return q == 0 ? 0 : (q <= 4 ? ((q + 1) % 4) + 1 : ((q - 3) % 4) + 5); }
+
+template <typename R>
+__device__ __forceinline__ R inlet_profile(const Lattice& L, int y)
+{
+    R yy = R(y) + R(0.5), H = R(L.ny);
+    return R(4) * R(L.umax) * yy * (H - yy) / (H * H);
+}
+
+// Zou-He on deviations g_i = f_i - w_i (the rest weights cancel pairwise).
+template <typename R>
+__device__ __forceinline__ void zou_he_inlet(R g[9], R u)
+{
+    R s = g[0] + g[2] + g[4] + R(2) * (g[3] + g[6] + g[7]);
+    R rho = (R(1) + s) / (R(1) - u);
+    R ru = rho * u;
+    R h = R(0.5) * (g[2] - g[4]);
+    g[1] = g[3] + R(2) / R(3) * ru;
+    g[5] = g[7] - h + ru / R(6);
+    g[8] = g[6] + h + ru / R(6);
+}
+
+template <typename R>
+__device__ __forceinline__ void zou_he_outlet(R g[9], R rho_out)
+{
+    R s = g[0] + g[2] + g[4] + R(2) * (g[1] + g[5] + g[8]);
+    R u = (s + (R(1) - rho_out)) / rho_out;
+    R ru = rho_out * u;
+    R h = R(0.5) * (g[2] - g[4]);
+    g[3] = g[1] - R(2) / R(3) * ru;
+    g[7] = g[5] + h - ru / R(6);
+    g[6] = g[8] - h - ru / R(6);
+}
+
+// Pull the nine post-collision deviations that stream into node (x, y).
+template <typename S, typename R>
+__device__ __forceinline__ void pull(const Lattice& L, const S* __restrict__ fin, int x, int y, R g[9])
+{
+    const int qs = L.qstride, nxp = L.nxp;
+    if (x > 0 && x < L.nx - 1 && y > 0 && y < L.ny - 1) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) g[q] = ld<S, R>(fin + q * qs + (y - cy(q)) * nxp + (x - cx(q)));
+        return;
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        int xs = x - cx(q), ys = y - cy(q);
+        if (ys < 0 || ys >= L.ny) {
+            g[q] = ld<S, R>(fin + op(q) * qs + y * nxp + x);  // halfway bounce-back
+        } else if (xs < 0 || xs >= L.nx) {
+            if (L.bc == LBIB_BC_PERIODIC_FORCE) {
+                xs = xs < 0 ? xs + L.nx : xs - L.nx;
+                g[q] = ld<S, R>(fin + q * qs + ys * nxp + xs);
+            } else {
+                g[q] = R(0);  // unknown, set by Zou-He
+            }
+        } else {
+            g[q] = ld<S, R>(fin + q * qs + ys * nxp + xs);
+        }
+    }
+    if (L.bc == LBIB_BC_INLET_OUTLET) {
+        if (x == 0) zou_he_inlet<R>(g, inlet_profile<R>(L, y));
+        else if (x == L.nx - 1) zou_he_outlet<R>(g, R(L.rho_out));
+    }
+}
+
+// Moments with the half-force shift and the Guo-forced BGK collision, in place.
+template <typename R>
+__device__ __forceinline__ void collide(R g[9], R Fx, R Fy, R omega, R& drho, R& ux, R& uy)
+{
+    drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    R rho = R(1) + drho;
+    R jx = (g[1] + g[5] + g[8]) - (g[3] + g[6] + g[7]) + R(0.5) * Fx;
+    R jy = (g[2] + g[5] + g[6]) - (g[4] + g[7] + g[8]) + R(0.5) * Fy;
+    R inv = R(1) / rho;
+    ux = jx * inv;
+    uy = jy * inv;
+    R u2 = R(1.5) * (ux * ux + uy * uy);
+    R uF = ux * Fx + uy * Fy;
+    R cf = R(1) - R(0.5) * omega;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        R eu = R(cx(q)) * ux + R(cy(q)) * uy;
+        R eF = R(cx(q)) * Fx + R(cy(q)) * Fy;
+        R w = wq<R>(q);
+        R geq = w * (drho + rho * (R(3) * eu + R(4.5) * eu * eu - u2));
+        R src = cf * w * (R(3) * (eF - uF) + R(9) * eu * eF);
+        g[q] = g[q] - omega * (g[q] - geq) + src;
+    }
+}
+
+template <typename S, typename R>
+__global__ void __launch_bounds__(TX* TY) k_bulk(Dev d, int p)
+{
+    const Lattice& L = d.L;
+    int t = blockIdx.y * L.ntx + blockIdx.x;
+    if (d.nearflag[p][t]) return;
+    int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+    if (x >= L.nx || y >= L.ny) return;
+    const S* __restrict__ fin = static_cast<const S*>(d.f[p]);
+    S* __restrict__ fout = static_cast<S*>(d.f[p ^ 1]);
+    R g[9];
+    pull<S, R>(L, fin, x, y, g);
+    R drho, ux, uy;
+    collide<R>(g, R(L.gx), R(L.gy), R(L.omega), drho, ux, uy);
+    if (!(drho > R(-1)) || !isfinite(ux + uy)) atomicOr(d.status, ST_DIVERGED);
+    const int base = y * L.nxp + x;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) st<S, R>(fout + q * L.qstride + base, g[q]);
+}
+
+template <typename S, typename R>
+__global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
+{
+    const Lattice& L = d.L;
+    const int64_t m = *d.step;  // lattice step (the Lagrangian counter has reached it)
+    const int c = (int)(m % 3);
+    const int cnt = min(d.count[c], d.list_cap);
+    const S* __restrict__ fin = static_cast<const S*>(d.f[p]);
+    S* __restrict__ fout = static_cast<S*>(d.f[p ^ 1]);
+    const R* __restrict__ mk = static_cast<const R*>(d.mk[p]);
+    const int nm = d.nmark;
+    uint32_t* mask = d.mask[p];
+    R* drho_o = static_cast<R*>(d.drho);
+    R* ux_o = static_cast<R*>(d.ux);
+    R* uy_o = static_cast<R*>(d.uy);
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    for (int k = blockIdx.x; k < cnt; k += gridDim.x) {
+        const int t = d.list[c][k];
+        const int tx = t % L.ntx, ty = t / L.ntx;
+        const int x = tx * TX + threadIdx.x, y = ty * TY + threadIdx.y;
+        R Fx = R(L.gx), Fy = R(L.gy);
+        const R xr = R(x), yr = R(y) + R(0.5);
+        for (int w = 0; w < d.mw; ++w) {
+            uint32_t bits = mask[(size_t)t * d.mw + w];
+            while (bits) {
+                int b = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                int id = w * 32 + b;
+                R rx = mk[id] - xr, ry = mk[nm + id] - yr;
+                if (fabs(rx) < R(2) && fabs(ry) < R(2)) {
+                    R wt = peskin<R>(rx) * peskin<R>(ry);
+                    Fx += wt * mk[2 * nm + id];
+                    Fy += wt * mk[3 * nm + id];
+                }
+            }
+        }
+        if (x < L.nx && y < L.ny) {
+            R g[9];
+            pull<S, R>(L, fin, x, y, g);
+            R drho, ux, uy;
+            collide<R>(g, Fx, Fy, R(L.omega), drho, ux, uy);
+            if (!(drho > R(-1)) || !isfinite(ux + uy)) atomicOr(d.status, ST_DIVERGED);
+            const int base = y * L.nxp + x;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) st<S, R>(fout + q * L.qstride + base, g[q]);
+            drho_o[base] = drho;
+            ux_o[base] = ux;
+            uy_o[base] = uy;
+        }
+        __syncthreads();  // every thread has read the tile's mask words
+        for (int w = tid; w < d.mw; w += TX * TY) mask[(size_t)t * d.mw + w] = 0u;
+        if (tid == 0) {
+            d.nearflag[p][t] = 0u;
+            d.fresh[t] = (int32_t)m;
+        }
+    }
+}
+
+template <typename S, typename R>
+__global__ void k_init_populations(Dev d, int buf)
+{
+    const Lattice& L = d.L;
+    int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+    if (x >= L.nx || y >= L.ny) return;
+    S* f = static_cast<S*>(d.f[buf]);
+    R u = (L.bc == LBIB_BC_INLET_OUTLET) ? inlet_profile<R>(L, y) : R(0);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        R eu = R(cx(q)) * u;
+        st<S, R>(f + q * L.qstride + y * L.nxp + x, wq<R>(q) * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * u * u));
+    }
+}
+
+// Density and velocity of lattice step m: from the near kernel's output on
+// tiles it updated at step m, else from the post-collision populations
+// (sum f* e = rho u + F / 2 with F the uniform body force there).
+template <typename S, typename R, typename O>
+__global__ void k_macro(Dev d, int buf, int64_t m, O* rho_o, O* ux_o, O* uy_o, int add_one)
+{
+    const Lattice& L = d.L;
+    int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+    if (x >= L.nx || y >= L.ny) return;
+    int t = blockIdx.y * L.ntx + blockIdx.x;
+    int base = y * L.nxp + x, ob = y * L.nx + x;
+    R drho, ux, uy;
+    if (d.fresh[t] == (int32_t)m) {
+        drho = static_cast<const R*>(d.drho)[base];
+        ux = static_cast<const R*>(d.ux)[base];
+        uy = static_cast<const R*>(d.uy)[base];
+    } else {
+        const S* f = static_cast<const S*>(d.f[buf]);
+        R g[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) g[q] = static_cast<R>(f[q * L.qstride + base]);
+        drho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
+        R jx = (g[1] + g[5] + g[8]) - (g[3] + g[6] + g[7]) - R(0.5) * R(L.gx);
+        R jy = (g[2] + g[5] + g[6]) - (g[4] + g[7] + g[8]) - R(0.5) * R(L.gy);
+        ux = jx / (R(1) + drho);
+        uy = jy / (R(1) + drho);
+    }
+    if (rho_o) rho_o[ob] = add_one ? O(1) + O(drho) : O(drho);
+    if (ux_o) ux_o[ob] = O(ux);
+    if (uy_o) uy_o[ob] = O(uy);
+}
+
+// Marks as near, for lattice steps m (which & 1) and m + 1 (which & 2), every
+// tile within r_act of an element centroid of X^m (initial activation and
+// after a restore).
+template <typename R>
+__global__ void k_activate(Dev d, int64_t m, int which)
+{
+    const Lattice& L = d.L;
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.nmark) return;
+    int b = 0;
+    while (b + 1 < d.nbodies && d.body[b + 1].off <= k) ++b;
+    const BodyConst& B = d.body[b];
+    int l = k - B.off, w = B.off + (l + 1) % B.nv;
+    const double* P = d.pos[m & 1];
+    double X = 0.5 * (P[k] + P[w]), Y = 0.5 * (P[d.nmark + k] + P[d.nmark + w]);
+    int i0 = max(0, (int)floor(X - d.r_act)), i1 = min(L.nx - 1, (int)floor(X + d.r_act) + 1);
+    int j0 = max(0, (int)floor(Y - 0.5 - d.r_act)), j1 = min(L.ny - 1, (int)floor(Y - 0.5 + d.r_act) + 1);
+    if (i0 > i1 || j0 > j1) return;
+    for (int s = 0; s < 2; ++s) {
+        if (!(which & (1 << s))) continue;
+        int64_t step = m + s;
+        uint32_t* flag = d.nearflag[step & 1];
+        int c = (int)(step % 3);
+        for (int ty = j0 / TY; ty <= j1 / TY; ++ty)
+            for (int tx = i0 / TX; tx <= i1 / TX; ++tx) {
+                int t = ty * L.ntx + tx;
+                if (flag[t] == 0u && atomicExch(&flag[t], 1u) == 0u) {
+                    int pos = atomicAdd(&d.count[c], 1);
+                    if (pos < d.list_cap) d.list[c][pos] = t;
+                    else atomicOr(d.status, ST_LIST_OVERFLOW);
+                }
+            }
+    }
+}
+
+// Sets the spreading bit masks of the markers in mk[parity] (after a restore).
+template <typename R>
+__global__ void k_rebuild_mask(Dev d, int parity)
+{
+    const Lattice& L = d.L;
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.nmark) return;
+    const R* mk = static_cast<const R*>(d.mk[parity]);
+    int nm = d.nmark;
+    if (mk[2 * nm + k] == R(0) && mk[3 * nm + k] == R(0)) return;
+    double X = mk[k], Y = mk[nm + k];
+    int i0 = max(0, (int)floor(X) - 1), i1 = min(L.nx - 1, (int)floor(X) + 2);
+    int j0 = max(0, (int)floor(Y - 0.5) - 1), j1 = min(L.ny - 1, (int)floor(Y - 0.5) + 2);
+    if (i0 > i1 || j0 > j1) return;
+    for (int ty = j0 / TY; ty <= j1 / TY; ++ty)
+        for (int tx = i0 / TX; tx <= i1 / TX; ++tx) {
+            int t = ty * L.ntx + tx;
+            if (!d.nearflag[parity][t]) atomicOr(d.status, ST_SPREAD_MISS);
+            atomicOr(&d.mask[parity][(size_t)t * d.mw + (k >> 5)], 1u << (k & 31));
+        }
+}
+
+// ------------------------------------------------------------------ launchers
+
+cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, cudaStream_t s)
+{
+    dim3 grid(d.L.ntx, d.L.nty), block(TX, TY);
+    if (prec == PREC_F64) k_bulk<double, double><<<grid, block, 0, s>>>(d, parity);
+    else k_bulk<float, float><<<grid, block, 0, s>>>(d, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, cudaStream_t s)
+{
+    dim3 block(TX, TY);
+    if (prec == PREC_F64) k_near<double, double><<<grid, block, 0, s>>>(d, parity);
+    else k_near<float, float><<<grid, block, 0, s>>>(d, parity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_populations(const Dev& d, int prec, int buf, cudaStream_t s)
+{
+    dim3 grid(d.L.ntx, d.L.nty), block(TX, TY);
+    if (prec == PREC_F64) k_init_populations<double, double><<<grid, block, 0, s>>>(d, buf);
+    else k_init_populations<float, float><<<grid, block, 0, s>>>(d, buf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro(const Dev& d, int prec, int buf, int64_t m, double* rho, double* ux, double* uy,
+                         cudaStream_t s)
+{
+    dim3 grid(d.L.ntx, d.L.nty), block(TX, TY);
+    if (prec == PREC_F64) k_macro<double, double, double><<<grid, block, 0, s>>>(d, buf, m, rho, ux, uy, 1);
+    else k_macro<float, float, double><<<grid, block, 0, s>>>(d, buf, m, rho, ux, uy, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro_typed(const Dev& d, int prec, int buf, int64_t m, void* ux, void* uy, int dtype,
+                               cudaStream_t s)
+{
+    dim3 grid(d.L.ntx, d.L.nty), block(TX, TY);
+    if (dtype == 1) {
+        if (prec == PREC_F64)
+            k_macro<double, double, double><<<grid, block, 0, s>>>(d, buf, m, nullptr, (double*)ux, (double*)uy, 1);
+        else
+            k_macro<float, float, double><<<grid, block, 0, s>>>(d, buf, m, nullptr, (double*)ux, (double*)uy, 1);
+    } else {
+        if (prec == PREC_F64)
+            k_macro<double, double, float><<<grid, block, 0, s>>>(d, buf, m, nullptr, (float*)ux, (float*)uy, 1);
+        else
+            k_macro<float, float, float><<<grid, block, 0, s>>>(d, buf, m, nullptr, (float*)ux, (float*)uy, 1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_activate(const Dev& d, int prec, int64_t m, int which, cudaStream_t s)
+{
+    if (d.nmark == 0) return cudaSuccess;
+    int th = 128, bl = (d.nmark + th - 1) / th;
+    if (prec == PREC_F64) k_activate<double><<<bl, th, 0, s>>>(d, m, which);
+    else k_activate<float><<<bl, th, 0, s>>>(d, m, which);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rebuild_mask(const Dev& d, int prec, int parity, cudaStream_t s)
+{
+    if (d.nmark == 0) return cudaSuccess;
+    int th = 128, bl = (d.nmark + th - 1) / th;
+    if (prec == PREC_F64) k_rebuild_mask<double><<<bl, th, 0, s>>>(d, parity);
+    else k_rebuild_mask<float><<<bl, th, 0, s>>>(d, parity);
+    return cudaGetLastError();
+}
+
+}  // namespace lbib

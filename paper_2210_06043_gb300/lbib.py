@@ -1,0 +1,319 @@
+"""ctypes binding of the C ABI in ``include/lbib.h`` (same names, argument
+marshalling only: every step of the time step runs in the library's CUDA
+kernels).  Loading fails loudly if the library cannot be built or loaded; there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+# ------------------------------------------------------------------ enums
+LBIB_OK, LBIB_ERR_INVALID_ARG, LBIB_ERR_UNSUPPORTED, LBIB_ERR_CUDA = 0, 1, 2, 3
+LBIB_ERR_OOM, LBIB_ERR_DIVERGED, LBIB_ERR_TIMEOUT, LBIB_ERR_STATE = 4, 5, 6, 7
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "CUDA", 4: "OOM", 5: "DIVERGED",
+                6: "TIMEOUT", 7: "STATE"}
+LBIB_BC_INLET_OUTLET, LBIB_BC_PERIODIC_FORCE = 0, 1
+LBIB_STORE_FP64, LBIB_STORE_FP32, LBIB_STORE_BF16, LBIB_STORE_FP16 = 0, 1, 2, 3
+LBIB_CELL, LBIB_PARTICLE = 0, 1
+LBIB_DEFORMABLE, LBIB_RIGID, LBIB_FIXED = 0, 1, 2
+FIELDS = ("x", "y", "xp", "yp", "uvx", "uvy", "fsx", "fsy", "fbx", "fby", "fax", "fay",
+          "fpx", "fpy", "fwx", "fwy", "fhx", "fhy", "ftx", "fty", "vx", "vy",
+          "mx", "my", "mfx", "mfy", "mds")
+
+
+class lbib_fluid_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("tau", ctypes.c_double),
+                ("re", ctypes.c_double), ("rho_out", ctypes.c_double), ("gx", ctypes.c_double),
+                ("gy", ctypes.c_double), ("bc_mode", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("obs_capacity", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p), ("seed", ctypes.c_uint64)]
+
+
+class lbib_membrane_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("motion", ctypes.c_int32), ("nv", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("xy", ctypes.POINTER(ctypes.c_double)),
+                ("xy_ref", ctypes.POINTER(ctypes.c_double)), ("ca", ctypes.c_double),
+                ("beta", ctypes.c_double), ("ka", ctypes.c_double), ("density_ratio", ctypes.c_double)]
+
+
+class lbib_adhesion_params(ctypes.Structure):
+    _fields_ = [("n_ligands", ctypes.c_int32), ("reserved", ctypes.c_int32), ("sigma", ctypes.c_double),
+                ("y_cr", ctypes.c_double), ("y_eq", ctypes.c_double), ("kf_dt", ctypes.c_double),
+                ("kr0_dt", ctypes.c_double), ("xi", ctypes.c_double)]
+
+
+class lbib_obs(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("t_star", ctypes.c_double), ("delta_p", ctypes.c_double),
+                ("r", ctypes.c_double), ("n_l", ctypes.c_double), ("n_bound", ctypes.c_int32),
+                ("status", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "lbib_create": [ctypes.POINTER(lbib_fluid_params), ctypes.POINTER(_P)],
+    "lbib_add_membrane": [_P, ctypes.POINTER(lbib_membrane_desc), ctypes.POINTER(ctypes.c_int32)],
+    "lbib_set_adhesion": [_P, ctypes.c_int32, ctypes.POINTER(lbib_adhesion_params)],
+    "lbib_advance": [_P, ctypes.c_int64],
+    "lbib_sync": [_P],
+    "lbib_step_count": [_P, ctypes.POINTER(ctypes.c_int64)],
+    "lbib_read_velocity": [_P, _P, _P, ctypes.c_size_t],
+    "lbib_read_density": [_P, _P, ctypes.c_size_t],
+    "lbib_read_velocity_device": [_P, _P, _P, ctypes.c_size_t, ctypes.c_int32],
+    "lbib_read_populations": [_P, _P, ctypes.c_size_t],
+    "lbib_write_populations": [_P, _P, ctypes.c_size_t],
+    "lbib_read_observables": [_P, ctypes.POINTER(lbib_obs), ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
+    "lbib_read_markers": [_P, ctypes.c_int32, _P, ctypes.c_size_t],
+    "lbib_read_body_field": [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t],
+    "lbib_read_bonds": [_P, ctypes.c_int32, _P, _P, _P, _P, ctypes.c_size_t],
+    "lbib_state_size": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "lbib_save_state": [_P, _P, ctypes.c_size_t],
+    "lbib_load_state": [_P, _P, ctypes.c_size_t],
+    "lbib_set_profiling": [_P, ctypes.c_int32],
+    "lbib_read_kernel_times": [_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                               ctypes.POINTER(ctypes.c_float)],
+    "lbib_describe": [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                      ctypes.POINTER(ctypes.c_int32)],
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Build (if stale) and load liblbib.so; raises if either fails."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            lib = ctypes.CDLL(path)
+            for name, args in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            lib.lbib_last_error.argtypes = [_P]
+            lib.lbib_last_error.restype = ctypes.c_char_p
+            lib.lbib_destroy.argtypes = [_P]
+            lib.lbib_destroy.restype = None
+            _lib = lib
+        return _lib
+
+
+class LbibError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lbib {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status: int, ctx) -> None:
+    if status != LBIB_OK:
+        msg = load().lbib_last_error(ctx).decode(errors="replace")
+        raise LbibError(status, msg)
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _vp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ------------------------------------------------------ one-to-one wrappers
+
+def lbib_create(params: lbib_fluid_params) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().lbib_create(ctypes.byref(params), ctypes.byref(h)), None)
+    return h
+
+
+def lbib_add_membrane(ctx, desc: lbib_membrane_desc) -> int:
+    i = ctypes.c_int32()
+    _check(load().lbib_add_membrane(ctx, ctypes.byref(desc), ctypes.byref(i)), ctx)
+    return i.value
+
+
+def lbib_set_adhesion(ctx, body: int, params: lbib_adhesion_params) -> None:
+    _check(load().lbib_set_adhesion(ctx, body, ctypes.byref(params)), ctx)
+
+
+def lbib_advance(ctx, nsteps: int) -> None:
+    _check(load().lbib_advance(ctx, int(nsteps)), ctx)
+
+
+def lbib_sync(ctx) -> None:
+    _check(load().lbib_sync(ctx), ctx)
+
+
+def lbib_destroy(ctx) -> None:
+    load().lbib_destroy(ctx)
+
+
+class Solver:
+    """A context plus its geometry, driven through the C ABI."""
+
+    def __init__(self, nx, ny, tau=1.0, re=1e-2, rho_out=1.0, bc=LBIB_BC_INLET_OUTLET, g=(0.0, 0.0),
+                 storage=LBIB_STORE_FP64, device=0, seed=0, stream: Optional[int] = None, obs_capacity=0):
+        self.lib = load()
+        p = lbib_fluid_params(nx=int(nx), ny=int(ny), tau=float(tau), re=float(re), rho_out=float(rho_out),
+                              gx=float(g[0]), gy=float(g[1]), bc_mode=int(bc), storage=int(storage),
+                              device=int(device), obs_capacity=int(obs_capacity),
+                              cuda_stream=stream, seed=int(seed) & (2**64 - 1))
+        self.nx, self.ny = int(nx), int(ny)
+        self.ctx = lbib_create(p)
+        self.nv = []
+        self.nlig = {}
+
+    # lifetime
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbib_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self, status):
+        _check(status, self.ctx)
+
+    # set-up
+    def add_membrane(self, kind, motion, xy, xy_ref=None, ca=1e-3, beta=0.0, ka=1.0, density_ratio=1.0) -> int:
+        xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(-1))
+        ref = None if xy_ref is None else np.ascontiguousarray(np.asarray(xy_ref, dtype=np.float64).reshape(-1))
+        d = lbib_membrane_desc(kind=int(kind), motion=int(motion), nv=len(xy) // 2, xy=_dp(xy),
+                               xy_ref=_dp(ref) if ref is not None else None, ca=float(ca), beta=float(beta),
+                               ka=float(ka), density_ratio=float(density_ratio))
+        i = lbib_add_membrane(self.ctx, d)
+        self.nv.append(len(xy) // 2)
+        return i
+
+    def set_adhesion(self, body, n_lig, sigma, y_cr, y_eq, kf_dt, kr0_dt, xi=0.0):
+        a = lbib_adhesion_params(n_ligands=int(n_lig), sigma=float(sigma), y_cr=float(y_cr), y_eq=float(y_eq),
+                                 kf_dt=float(kf_dt), kr0_dt=float(kr0_dt), xi=float(xi))
+        lbib_set_adhesion(self.ctx, int(body), a)
+        self.nlig[int(body)] = int(n_lig)
+
+    # stepping
+    def advance(self, n=1):
+        lbib_advance(self.ctx, n)
+
+    def sync(self):
+        lbib_sync(self.ctx)
+
+    def step_count(self) -> int:
+        s = ctypes.c_int64()
+        self._c(self.lib.lbib_step_count(self.ctx, ctypes.byref(s)))
+        return s.value
+
+    # reads
+    def velocity(self):
+        ux = np.zeros((self.ny, self.nx)); uy = np.zeros_like(ux)
+        self._c(self.lib.lbib_read_velocity(self.ctx, _vp(ux), _vp(uy), ux.size))
+        return ux, uy
+
+    def density(self):
+        r = np.zeros((self.ny, self.nx))
+        self._c(self.lib.lbib_read_density(self.ctx, _vp(r), r.size))
+        return r
+
+    def velocity_device(self, ux_ptr: int, uy_ptr: int, n: int, dtype: int):
+        self._c(self.lib.lbib_read_velocity_device(self.ctx, ctypes.c_void_p(ux_ptr), ctypes.c_void_p(uy_ptr),
+                                                   n, dtype))
+
+    def populations(self):
+        f = np.zeros((9, self.ny, self.nx))
+        self._c(self.lib.lbib_read_populations(self.ctx, _vp(f), f.size))
+        return f
+
+    def write_populations(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == (9, self.ny, self.nx)
+        self._c(self.lib.lbib_write_populations(self.ctx, _vp(f), f.size))
+
+    def observables(self, cap=1 << 16):
+        buf = (lbib_obs * cap)()
+        n = ctypes.c_size_t()
+        self._c(self.lib.lbib_read_observables(self.ctx, buf, cap, ctypes.byref(n)))
+        return [dict(step=o.step, t_star=o.t_star, delta_p=o.delta_p, r=o.r, n_l=o.n_l, n_bound=o.n_bound,
+                     status=o.status) for o in buf[:n.value]]
+
+    def markers(self, body):
+        xy = np.zeros(2 * self.nv[body])
+        self._c(self.lib.lbib_read_markers(self.ctx, int(body), _vp(xy), xy.size))
+        return xy.reshape(-1, 2)
+
+    def body_field(self, body, field):
+        out = np.zeros(self.nv[body])
+        self._c(self.lib.lbib_read_body_field(self.ctx, int(body), FIELDS.index(field), _vp(out), out.size))
+        return out
+
+    def bonds(self, body):
+        n = self.nlig[int(body)]
+        bound = np.zeros(n, np.int32); ax = np.zeros(n); ay = np.zeros(n); mg = np.zeros(n)
+        self._c(self.lib.lbib_read_bonds(self.ctx, int(body), _vp(bound), _vp(ax), _vp(ay), _vp(mg), n))
+        return bound, ax, ay, mg
+
+    def state_size(self) -> int:
+        n = ctypes.c_size_t()
+        self._c(self.lib.lbib_state_size(self.ctx, ctypes.byref(n)))
+        return n.value
+
+    def save_state(self) -> bytearray:
+        buf = bytearray(self.state_size())
+        arr = (ctypes.c_char * len(buf)).from_buffer(buf)
+        self._c(self.lib.lbib_save_state(self.ctx, ctypes.cast(arr, ctypes.c_void_p), len(buf)))
+        return buf
+
+    def load_state(self, buf: bytearray):
+        arr = (ctypes.c_char * len(buf)).from_buffer(buf)
+        self._c(self.lib.lbib_load_state(self.ctx, ctypes.cast(arr, ctypes.c_void_p), len(buf)))
+
+    def set_profiling(self, on: bool):
+        self._c(self.lib.lbib_set_profiling(self.ctx, 1 if on else 0))
+
+    def kernel_times(self):
+        a, b, c = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+        self._c(self.lib.lbib_read_kernel_times(self.ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def describe(self):
+        k, n, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._c(self.lib.lbib_describe(self.ctx, ctypes.byref(k), ctypes.byref(n), ctypes.byref(t)))
+        return dict(kernels_per_step=k.value, near_tiles=n.value, tiles=t.value)
+
+
+def from_capillary(cap, storage=None, device=0, stream=None, obs_capacity=0) -> Solver:
+    """A Solver holding the lattice and bodies of a workloads.Capillary."""
+    st = storage
+    if st is None:
+        st = LBIB_STORE_FP64 if cap.storage == "fp64" else LBIB_STORE_FP32
+    s = Solver(cap.nx, cap.ny, tau=cap.tau, re=cap.re, rho_out=cap.rho_out, bc=cap.bc, g=cap.g, storage=st,
+               device=device, seed=cap.seed, stream=stream, obs_capacity=obs_capacity)
+    for b in cap.bodies:
+        i = s.add_membrane(b.kind, b.motion, b.xy, b.xy_ref, b.ca, b.beta, b.ka, b.density_ratio)
+        if b.adhesion is not None:
+            a = b.adhesion
+            s.set_adhesion(i, a.n_lig, a.sigma, a.y_cr, a.y_eq, a.kf_dt, a.kr0_dt, a.xi)
+    return s
+
+
+def roofline_bytes_per_node(storage: int) -> int:
+    """Algorithmic DRAM bytes of one lattice-node update: 9 populations read and
+    written once each."""
+    return 2 * 9 * {LBIB_STORE_FP64: 8, LBIB_STORE_FP32: 4, LBIB_STORE_BF16: 2, LBIB_STORE_FP16: 2}[storage]
+
+
+__all__ = [n for n in dir() if n.startswith("lbib_") or n.startswith("LBIB_")] + [
+    "Solver", "from_capillary", "load", "library_path", "LbibError", "roofline_bytes_per_node", "FIELDS"]

@@ -1,0 +1,102 @@
+"""GPU parity of the lattice kernels (bulk + near, no membranes): one and
+several steps from random post-collision populations, compared element by
+element with the oracle, on lattices that span several 32 x 4 tiles and end in
+ragged tiles, for both boundary modes and both storage precisions."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_06043_gb300 import lbib
+from paper_2210_06043_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(37, 9), (64, 8), (100, 23), (3, 2)]
+
+
+def _pair(nx, ny, bc, storage, f0, tau=0.8, re=5.0, g=(0.0, 0.0)):
+    o = oracle.OracleSim(nx, ny, tau=tau, re=re, bc=bc, g=g)
+    o.set_fpost(f0)
+    s = lbib.Solver(nx, ny, tau=tau, re=re, bc=bc, g=g, storage=storage)
+    s.write_populations(f0)
+    return o, s
+
+
+@pytest.mark.parametrize("nx,ny", SHAPES)
+@pytest.mark.parametrize("bc", [lbib.LBIB_BC_INLET_OUTLET, lbib.LBIB_BC_PERIODIC_FORCE])
+def test_lattice_step_fp64_matches_oracle(nx, ny, bc):
+    f0 = wl.random_populations(nx, ny, seed=nx * 7 + ny, eps=1e-2)
+    g = (2e-5, -1e-5) if bc == lbib.LBIB_BC_PERIODIC_FORCE else (0.0, 0.0)
+    o, s = _pair(nx, ny, bc, lbib.LBIB_STORE_FP64, f0, g=g)
+    for n in (1, 4):
+        o.step(n)
+        s.advance(n)
+        fo, fg = o.fpost(), s.populations()
+        assert np.abs(fg - fo).max() < 1e-14, np.abs(fg - fo).max()
+        r, ux, uy = o.macro()
+        gux, guy = s.velocity()
+        assert np.abs(gux - ux).max() < 1e-14 and np.abs(guy - uy).max() < 1e-14
+        assert np.abs(s.density() - r).max() < 1e-14
+    s.close()
+
+
+@pytest.mark.parametrize("nx,ny", SHAPES[:3])
+@pytest.mark.parametrize("bc", [lbib.LBIB_BC_INLET_OUTLET, lbib.LBIB_BC_PERIODIC_FORCE])
+def test_lattice_step_fp32_matches_oracle(nx, ny, bc):
+    """FP32 deviations from the rest weights: the absolute population error
+    stays near FP32 rounding of the deviations (1e-2 here), far below the
+    populations' own rounding (~3e-8)."""
+    f0 = wl.random_populations(nx, ny, seed=nx * 5 + ny, eps=1e-2)
+    f0 = np.asarray(np.asarray(f0 - np.array([4/9] + [1/9]*4 + [1/36]*4)[:, None, None], np.float32),
+                    np.float64) + np.array([4/9] + [1/9]*4 + [1/36]*4)[:, None, None]
+    g = (2e-5, -1e-5) if bc == lbib.LBIB_BC_PERIODIC_FORCE else (0.0, 0.0)
+    o, s = _pair(nx, ny, bc, lbib.LBIB_STORE_FP32, f0, g=g)
+    o.step(5)
+    s.advance(5)
+    fo, fg = o.fpost(), s.populations()
+    assert np.abs(fg - fo).max() < 5e-9
+    r, ux, uy = o.macro()
+    gux, guy = s.velocity()
+    assert np.abs(gux - ux).max() < 1e-8 and np.abs(guy - uy).max() < 1e-8
+    s.close()
+
+
+def test_forced_poiseuille_on_gpu_reaches_the_closed_form():
+    """Property at any size: the GPU's steady forced channel is the BGK
+    bounce-back closed form (parabola + slip) at FP64."""
+    tau, ny = 1.0, 12
+    nu = (tau - 0.5) / 3
+    gx = 8 * nu * 0.02 / ny**2
+    s = lbib.Solver(40, ny, tau=tau, re=0.0, bc=lbib.LBIB_BC_PERIODIC_FORCE, g=(gx, 0.0))
+    s.advance(int(6 * ny * ny / nu) + 2000)
+    ux, uy = s.velocity()
+    y = np.arange(ny) + 0.5
+    exact = gx / (2 * nu) * y * (ny - y) + gx * (16 * (tau - 0.5) ** 2 - 3) / (24 * nu)
+    assert np.abs(ux - exact[:, None]).max() < 1e-11 * exact.max()
+    s.close()
+
+
+def test_mass_is_conserved_in_a_periodic_channel_fp32():
+    nx, ny = 300, 50
+    f0 = wl.random_populations(nx, ny, seed=11, eps=1e-3)
+    s = lbib.Solver(nx, ny, tau=0.7, re=0.0, bc=lbib.LBIB_BC_PERIODIC_FORCE, storage=lbib.LBIB_STORE_FP32)
+    s.write_populations(f0)
+    m0 = s.populations().sum()
+    s.advance(500)
+    assert abs(s.populations().sum() - m0) < 1e-9 * m0
+    s.close()
+
+
+def test_injected_nan_is_reported_as_divergence():
+    """Host-side fault injection: a NaN population surfaces as
+    LBIB_ERR_DIVERGED at the next sync, and the context stays usable."""
+    nx, ny = 40, 8
+    f0 = wl.random_populations(nx, ny, seed=3)
+    f0[2, 4, 17] = np.nan
+    s = lbib.Solver(nx, ny, tau=1.0, re=1.0)
+    s.write_populations(f0)
+    s.advance(2)
+    with pytest.raises(lbib.LbibError) as e:
+        s.sync()
+    assert e.value.status == lbib.LBIB_ERR_DIVERGED
+    s.close()
