@@ -203,6 +203,34 @@ lbib_status ensure_graphs(lbib_ctx* ctx)
     return LBIB_OK;
 }
 
+// Positions of buffer k as float-float pairs (hi, lo) of the compute type.
+lbib_status upload_posf(lbib_ctx* ctx, int k)
+{
+    Dev& d = ctx->d;
+    const size_t nm = std::max(d.nmark, 1);
+    std::vector<double> pos(2 * nm);
+    CK(cudaMemcpy(pos.data(), d.pos[k], pos.size() * 8, cudaMemcpyDeviceToHost));
+    if (ctx->prec == PREC_F64) {
+        std::vector<double> f(4 * nm, 0.0);
+        for (size_t i = 0; i < nm; ++i) {
+            f[i] = pos[i];
+            f[2 * nm + i] = pos[nm + i];
+        }
+        CK(cudaMemcpy(d.posf[k], f.data(), f.size() * 8, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> f(4 * nm, 0.f);
+        for (size_t i = 0; i < nm; ++i) {
+            float hx = (float)pos[i], hy = (float)pos[nm + i];
+            f[i] = hx;
+            f[nm + i] = (float)(pos[i] - (double)hx);
+            f[2 * nm + i] = hy;
+            f[3 * nm + i] = (float)(pos[nm + i] - (double)hy);
+        }
+        CK(cudaMemcpy(d.posf[k], f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+    }
+    return LBIB_OK;
+}
+
 // Builds the device Lagrangian arrays from the host bodies (first advance).
 lbib_status finalize(lbib_ctx* ctx)
 {
@@ -256,6 +284,8 @@ lbib_status finalize(lbib_ctx* ctx)
         Poly pr = polygon(ref), pc = polygon(h.xy);
         B.A0 = pr.A;
         B.P0 = pr.P;
+        B.inv_A0 = 1.0 / pr.A;
+        B.inv_P0 = 1.0 / pr.P;
         B.ks = (h.motion == LBIB_DEFORMABLE) ? 1.0 * nu * umax / h.ca : 0.0;  // Ca = rho nu u_max / k_s
         B.kb = h.beta * B.ks;
         B.ka = h.ka;
@@ -273,7 +303,7 @@ lbib_status finalize(lbib_ctx* ctx)
         }
         double* bo = &bobs[(size_t)b * BO_N];
         bo[BO_AREA] = pc.A;
-        bo[BO_PERIM] = pc.P;
+        bo[BO_DPERIM] = pc.P - pr.P;
         bo[BO_CX] = pc.cx;
         bo[BO_CY] = pc.cy;
         bo[BO_XMIN] = bo[BO_YMIN] = 1e300;
@@ -329,6 +359,9 @@ lbib_status finalize(lbib_ctx* ctx)
     }
     for (int e = 0; e < nmark; ++e) site_off[e + 1] += site_off[e];
     d.r_act = 2.0 + std::max(1.2, 0.75 * lmax) + 1.0;
+    // a centroid lies within ACT_STRIDE / 2 elements of an activating one; 1.5 l_max
+    // per element allows 50% stretching
+    d.r_act_sub = d.r_act + 0.5 * ACT_STRIDE * 1.5 * lmax;
     d.ring_cap = ctx->P.obs_capacity > 0 ? ctx->P.obs_capacity : 4096;
 
     // device arrays
@@ -341,6 +374,8 @@ lbib_status finalize(lbib_ctx* ctx)
     int32_t *dligel = nullptr, *dsite = nullptr;
     CK(dalloc(reg, &d.pos[0], 2 * nm1));
     CK(dalloc(reg, &d.pos[1], 2 * nm1));
+    CK(dalloc(reg, reinterpret_cast<char**>(&d.posf[0]), 4 * nm1 * rs));
+    CK(dalloc(reg, reinterpret_cast<char**>(&d.posf[1]), 4 * nm1 * rs));
     CK(dalloc(reg, &dbody, std::max(nb, 1)));
     CK(dalloc(reg, &d.rigid, (size_t)std::max(nb, 1) * RG_N));
     CK(dalloc(reg, reinterpret_cast<char**>(&dl0), nm1 * rs));
@@ -356,8 +391,10 @@ lbib_status finalize(lbib_ctx* ctx)
     CK(dalloc(reg, &d.body_obs[0], (size_t)std::max(nb, 1) * BO_N));
     CK(dalloc(reg, &d.body_obs[1], (size_t)std::max(nb, 1) * BO_N));
     CK(dalloc(reg, &d.ring, (size_t)d.ring_cap));
-    CK(dalloc(reg, reinterpret_cast<char**>(&d.mk[0]), 4 * nm1 * rs));
-    CK(dalloc(reg, reinterpret_cast<char**>(&d.mk[1]), 4 * nm1 * rs));
+    for (int k = 0; k < 2; ++k) {
+        CK(dalloc(reg, &d.mki[k], 2 * nm1));
+        CK(dalloc(reg, reinterpret_cast<char**>(&d.mkf[k]), 4 * nm1 * rs));
+    }
     CK(dalloc(reg, &d.mask[0], (size_t)L.ntiles * d.mw));
     CK(dalloc(reg, &d.mask[1], (size_t)L.ntiles * d.mw));
     d.body = dbody;
@@ -375,6 +412,10 @@ lbib_status finalize(lbib_ctx* ctx)
     };
     CK(cudaMemcpy(d.pos[0], pos.data(), pos.size() * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d.pos[1], pos.data(), pos.size() * 8, cudaMemcpyHostToDevice));
+    for (int k = 0; k < 2; ++k) {
+        lbib_status st = upload_posf(ctx, k);
+        if (st != LBIB_OK) return st;
+    }
     if (nb) CK(cudaMemcpy(dbody, bc.data(), bc.size() * sizeof(BodyConst), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d.rigid, rig.data(), rig.size() * 8, cudaMemcpyHostToDevice));
     CK(up_real(dl0, l0));
@@ -390,8 +431,10 @@ lbib_status finalize(lbib_ctx* ctx)
     CK(cudaMemcpy(d.body_obs[0], bobs.data(), bobs.size() * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d.body_obs[1], bobs.data(), bobs.size() * 8, cudaMemcpyHostToDevice));
     CK(cudaMemset(d.ring, 0, (size_t)d.ring_cap * sizeof(lbib_obs)));
-    CK(cudaMemset(d.mk[0], 0, 4 * nm1 * rs));
-    CK(cudaMemset(d.mk[1], 0, 4 * nm1 * rs));
+    for (int k = 0; k < 2; ++k) {
+        CK(cudaMemset(d.mki[k], 0, 2 * nm1 * 4));
+        CK(cudaMemset(d.mkf[k], 0, 4 * nm1 * rs));
+    }
     CK(cudaMemset(d.mask[0], 0, (size_t)L.ntiles * d.mw * 4));
     CK(cudaMemset(d.mask[1], 0, (size_t)L.ntiles * d.mw * 4));
     if (nb) {
@@ -848,7 +891,7 @@ size_t state_bytes(const lbib_ctx* ctx)
     const Dev& d = ctx->d;
     size_t nq = (size_t)9 * d.L.qstride;
     size_t nm = std::max(d.nmark, 1), nl = std::max(d.nlig, 1), nb = std::max(d.nbodies, 1);
-    return sizeof(CkHeader) + nq * ctx->rsz + 4 * nm * 8 + nb * RG_N * 8 + nl * 4 + 2 * nl * 8 +
+    return sizeof(CkHeader) + nq * ctx->rsz + 4 * nm * 8 + nb * RG_N * 8 + nl * 4 + 2 * nl * 8 + 2 * nm * 4 +
            4 * nm * ctx->rsz + nb * BO_N * 8;
 }
 }  // namespace
@@ -890,7 +933,9 @@ lbib_status lbib_save_state(lbib_ctx* ctx, void* buf, size_t bytes)
     p += nl * 4;
     CK(cudaMemcpy(p, d.anchor, 2 * nl * 8, cudaMemcpyDeviceToHost));
     p += 2 * nl * 8;
-    CK(cudaMemcpy(p, d.mk[st & 1], 4 * nm * ctx->rsz, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(p, d.mki[st & 1], 2 * nm * 4, cudaMemcpyDeviceToHost));
+    p += 2 * nm * 4;
+    CK(cudaMemcpy(p, d.mkf[st & 1], 4 * nm * ctx->rsz, cudaMemcpyDeviceToHost));
     p += 4 * nm * ctx->rsz;
     CK(cudaMemcpy(p, d.body_obs[st & 1], nb * BO_N * 8, cudaMemcpyDeviceToHost));
     return LBIB_OK;
@@ -920,13 +965,19 @@ lbib_status lbib_load_state(lbib_ctx* ctx, const void* buf, size_t bytes)
     p += 2 * nm * 8;
     CK(cudaMemcpy(d.pos[(st + 1) & 1], p, 2 * nm * 8, cudaMemcpyHostToDevice));
     p += 2 * nm * 8;
+    for (int k = 0; k < 2; ++k) {
+        lbib_status sp = upload_posf(ctx, k);
+        if (sp != LBIB_OK) return sp;
+    }
     CK(cudaMemcpy(d.rigid, p, nb * RG_N * 8, cudaMemcpyHostToDevice));
     p += nb * RG_N * 8;
     CK(cudaMemcpy(d.bound, p, nl * 4, cudaMemcpyHostToDevice));
     p += nl * 4;
     CK(cudaMemcpy(d.anchor, p, 2 * nl * 8, cudaMemcpyHostToDevice));
     p += 2 * nl * 8;
-    CK(cudaMemcpy(d.mk[st & 1], p, 4 * nm * ctx->rsz, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.mki[st & 1], p, 2 * nm * 4, cudaMemcpyHostToDevice));
+    p += 2 * nm * 4;
+    CK(cudaMemcpy(d.mkf[st & 1], p, 4 * nm * ctx->rsz, cudaMemcpyHostToDevice));
     p += 4 * nm * ctx->rsz;
     CK(cudaMemcpy(d.body_obs[st & 1], p, nb * BO_N * 8, cudaMemcpyHostToDevice));
     // scheduling state is rebuilt from the restored positions and markers

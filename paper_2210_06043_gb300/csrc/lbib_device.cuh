@@ -64,6 +64,28 @@ __device__ __forceinline__ R peskin_d(R r)
     return r < R(0) ? -g : g;
 }
 
+// phi and d phi / d r together (one square root)
+template <typename R>
+__device__ __forceinline__ void peskin_both(R r, R& ph, R& dph)
+{
+    R a = fabs(r), g;
+    if (a <= R(1)) {
+        R t = a - R(0.5);
+        R s = sqrt(R(2) - R(4) * t * t);
+        ph = (R(3) - R(2) * a + s) * R(0.125);
+        g = (R(-2) - R(4) * t / s) * R(0.125);
+    } else if (a <= R(2)) {
+        R t = a - R(1.5);
+        R s = sqrt(R(2) - R(4) * t * t);
+        ph = (R(5) - R(2) * a - s) * R(0.125);
+        g = (R(-2) + R(4) * t / s) * R(0.125);
+    } else {
+        ph = R(0);
+        g = R(0);
+    }
+    dph = r < R(0) ? -g : g;
+}
+
 // ------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror & Shaw (SC'11): counter-based generator, 10 rounds.
 struct U4 {

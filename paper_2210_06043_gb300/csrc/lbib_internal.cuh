@@ -11,12 +11,20 @@
 //                rho - 1 and u for the Lagrangian kernel; all others are "bulk".
 //   markers      element centroids with their direct force times ds,
 //                double-buffered by the parity of the lattice step that
-//                consumes them; per near tile a bit mask of the markers whose
-//                4 x 4 stencil touches it (ascending marker order = the order in
+//                consumes them, each stored as the integer origin of its 4 x 4
+//                stencil plus an exact fractional offset (so FP32 kernel
+//                weights do not lose the ~1e-5 dx that FP32 coordinates near
+//                x ~ 1000 would); per near tile a bit mask of the markers whose
+//                stencil touches it (ascending marker order = the order in
 //                which the forces are summed).
-//   bodies       vertex positions in FP64 (per-step displacements at
-//                Re = 1e-2 are ~1e-5 dx, below FP32 resolution at channel
-//                coordinates); forces in the compute precision.
+//   bodies       vertex positions in FP64 in global memory (per-step
+//                displacements at Re = 1e-2 are ~1e-5 dx, below FP32
+//                resolution at channel coordinates), carried inside the
+//                Lagrangian kernel as float-float pairs (hi + lo, ~48 bits)
+//                so that no FP64 operation sits on its dependency chains
+//                (FP64 latency on this part is ~10^2 cycles per dependent
+//                operation); forces in the compute precision; the area and
+//                centroid reductions in FP64.
 #pragma once
 
 #include <cstdint>
@@ -29,7 +37,8 @@ constexpr int TX = 32;            // tile width (nodes along x) = one warp
 constexpr int TY = 4;             // tile height
 constexpr int MAX_BODIES = 16;
 constexpr int MAX_NV = 1024;      // vertices per body
-constexpr int LAG_THREADS = 256;  // threads of the Lagrangian kernel's blocks
+constexpr int LAG_THREADS = 512;  // threads of the Lagrangian kernel's blocks
+constexpr int ACT_STRIDE = 4;     // near-tile activation from every ACT_STRIDE-th marker
 constexpr int NDIAG = LBIB_FIELD_COUNT;
 
 // device status bits (host maps them to lbib_status)
@@ -54,7 +63,7 @@ struct BodyConst {
     int kind, motion, nv, off;        // off: global index of vertex 0 / element 0
     int adhesive, nlig, lig_off, nl0;
     int sigma_inf, pad0, pad1, pad2;
-    double A0, P0;
+    double A0, P0, inv_A0, inv_P0;
     double ks, kb, ka, mv, mass, inertia;
     double sigma, ycr, yeq, Pf, kr0_dt, xi;
 };
@@ -62,7 +71,8 @@ struct BodyConst {
 // rigid-body state per body (FP64): centroid, angle, BDF2 history
 enum { RG_XC = 0, RG_YC, RG_ANG, RG_U1X, RG_U1Y, RG_U2X, RG_U2Y, RG_W1, RG_W2, RG_N };
 // per-body observables/extent written by the Lagrangian kernel (FP64)
-enum { BO_AREA = 0, BO_PERIM, BO_CX, BO_CY, BO_NBOUND, BO_XMIN, BO_XMAX, BO_YMIN, BO_YMAX, BO_N };
+// BO_DPERIM: perimeter minus stress-free perimeter, sum of (l - l_0)
+enum { BO_AREA = 0, BO_DPERIM, BO_CX, BO_CY, BO_NBOUND, BO_XMIN, BO_XMAX, BO_YMIN, BO_YMAX, BO_N };
 
 // Every device pointer of a context.  Passed by value to the kernels.
 struct Dev {
@@ -78,11 +88,15 @@ struct Dev {
     int32_t* count;            // [3]
     uint32_t* mask[2];         // [ntiles][mw]
     int mw, list_cap;
-    // markers consumed by lattice step m: mk[m & 1] = Real [4][nmark] (x, y, fx ds, fy ds)
-    void* mk[2];
+    // markers consumed by lattice step m, parity m & 1:
+    //   mki[p] = int32 [2][nmark]: floor(X), floor(Y - 1/2)
+    //   mkf[p] = Real [4][nmark]: X - floor(X), Y - 1/2 - floor(Y - 1/2), Fx ds, Fy ds
+    int32_t* mki[2];
+    void* mkf[2];
     // Lagrangian state
     int nbodies, nmark, nlig, nv_max;
     double* pos[2];            // [2][nmark] (x block then y block); X^n in pos[n & 1]
+    void* posf[2];             // Real [4][nmark]: X^n as float-float pairs (x hi, x lo, y hi, y lo)
     const BodyConst* body;     // [nbodies]
     double* rigid;             // [nbodies][RG_N]
     const void* l0;            // Real [nmark] stress-free element lengths
@@ -103,6 +117,7 @@ struct Dev {
     uint32_t* status;
     uint32_t* ticket;
     double r_act;              // activation radius around markers (lattice units)
+    double r_act_sub;          // radius used by every ACT_STRIDE-th marker (covers the ones between)
     double dcut;               // repulsion cut-off (Eq. 12)
     double probe;              // probe length (Sec. 2.6)
     double uscale;             // observables: u_max / H

@@ -18,69 +18,217 @@
 //      written as markers for lattice step n + 1 together with the bit masks of
 //      the tiles their stencils touch; tiles within r_act of the new
 //      centroids are scheduled as near for lattice step n + 2;
-//   7. area, perimeter, centroid and extent of X^{n+1}; the last block to
-//      finish writes the observables record of step n + 1 and advances n.
+//   7. area, perimeter change, centroid and extent of X^{n+1}; the last block
+//      to finish writes the observables record of step n + 1 and advances n.
+//
+// The kernel is latency-bound (a few hundred markers per block).  Positions
+// are carried as float-float pairs (value = hi + lo) so that differences,
+// stencil origins and fractional offsets, probe and centroid positions and
+// the Verlet update are exact to ~1e-12 dx in FP32 arithmetic; FP64 appears
+// only in the conversions at load and store and in the area and centroid
+// reductions, never in a long dependent chain.  Each interpolation point is
+// sampled by a group of K = 4, 2 or 1 lanes (as many as keep the largest
+// body in one pass over the block), each lane summing 4 / K stencil rows.
 #include <cuda_runtime.h>
 
 #include "lbib_device.cuh"
 
 namespace lbib {
 
+// ---------------------------------------------------- float-float positions
 template <typename R>
-struct Sample {
-    R u, v, ux, uy, vx, vy, rho, W;
+struct P2 {
+    R h, l;
 };
 
-// Truncated-stencil velocity (and optionally its gradient) and renormalised
-// density at (X, Y) from the near-tile output of lattice step m.
 template <typename R>
-__device__ __forceinline__ void sample(const Dev& d, double X, double Y, int32_t m, bool grad, Sample<R>& o,
-                                       uint32_t& miss)
+__device__ __forceinline__ P2<R> p2_of(double X)
 {
-    const Lattice& L = d.L;
-    const R* ux = static_cast<const R*>(d.ux);
-    const R* uy = static_cast<const R*>(d.uy);
-    const R* dr = static_cast<const R*>(d.drho);
-    int i0 = (int)floor(X) - 1, j0 = (int)floor(Y - 0.5) - 1;
-    R W = 0, Nu = 0, Nv = 0, Nr = 0, Nux = 0, Nuy = 0, Nvx = 0, Nvy = 0;
-    for (int jj = 0; jj < 4; ++jj) {
-        int j = j0 + jj;
-        if (j < 0 || j >= L.ny) continue;
-        R ry = (R)(Y - (j + 0.5));
-        R py = peskin<R>(ry), dpy = grad ? peskin_d<R>(ry) : R(0);
-        for (int ii = 0; ii < 4; ++ii) {
-            int i = i0 + ii;
-            if (i < 0 || i >= L.nx) continue;
-            R rx = (R)(X - i);
-            R px = peskin<R>(rx);
-            if (d.fresh[tile_of(L, i, j)] != m) miss = 1u;
-            int idx = j * L.nxp + i;
-            R a = ux[idx], b = uy[idx];
-            R w = px * py;
-            W += w;
-            Nu += a * w;
-            Nv += b * w;
-            Nr += dr[idx] * w;
-            if (grad) {
-                R dpx = peskin_d<R>(rx);
-                Nux += a * dpx * py;
-                Nuy += a * px * dpy;
-                Nvx += b * dpx * py;
-                Nvy += b * px * dpy;
-            }
-        }
-    }
-    o.u = Nu;
-    o.v = Nv;
-    o.ux = Nux;
-    o.uy = Nuy;
-    o.vx = Nvx;
-    o.vy = Nvy;
-    o.W = W;
-    o.rho = (W > R(0)) ? R(1) + Nr / W : R(1);
+    const R h = (R)X;
+    return P2<R>{h, (R)(X - (double)h)};
 }
 
 template <typename R>
+__device__ __forceinline__ double p2_double(P2<R> p)
+{
+    return (double)p.h + (double)p.l;
+}
+
+// a - b as a single compute-precision value
+template <typename R>
+__device__ __forceinline__ R p2_sub(P2<R> a, P2<R> b)
+{
+    return (a.h - b.h) + (a.l - b.l);
+}
+
+// a + d, renormalised (Knuth TwoSum on the high part)
+template <typename R>
+__device__ __forceinline__ P2<R> p2_add(P2<R> a, R d)
+{
+    const R s = a.h + d;
+    const R bb = s - a.h;
+    const R err = (a.h - (s - bb)) + (d - bb);
+    const R lo = a.l + err;
+    const R h2 = s + lo;
+    return P2<R>{h2, lo - (h2 - s)};
+}
+
+// integer floor of a - shift and the fractional remainder in [0, 1)
+template <typename R>
+__device__ __forceinline__ void p2_floor(P2<R> a, R shift, int& i, R& frac)
+{
+    const R h = a.h - shift;
+    R f = floor(h);
+    R r = (h - f) + a.l;
+    if (r < R(0)) {
+        f -= R(1);
+        r += R(1);
+    } else if (r >= R(1)) {
+        f += R(1);
+        r -= R(1);
+    }
+    i = (int)f;
+    frac = r;
+}
+
+// ---------------------------------------------------------------- sampling
+template <typename R>
+struct Sample {
+    R u, v, ux, uy, vx, vy, drho, W;  // drho: renormalised rho - 1
+};
+
+template <typename R>
+struct Spot {
+    int ix, jy;  // floor(X), floor(Y - 1/2)
+    R ax, ay;    // X - ix, Y - 1/2 - jy
+};
+
+template <typename R>
+__device__ __forceinline__ Spot<R> spot_of(P2<R> X, P2<R> Y)
+{
+    Spot<R> s;
+    p2_floor<R>(X, R(0), s.ix, s.ax);
+    p2_floor<R>(Y, R(0.5), s.jy, s.ay);
+    return s;
+}
+
+template <typename R, int K>
+__device__ __forceinline__ R group_sum(R v)
+{
+#pragma unroll
+    for (int o = 1; o < K; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Truncated-stencil velocity (and optionally its gradient) and renormalised
+// density deviation at a point from the near-tile output of lattice step m,
+// computed by a group of K lanes (K = 1, 2, 4): lane r sums the stencil rows
+// jy - 1 + r, jy - 1 + r + K, ..., the rows are combined by shuffles and every
+// lane of the group gets the result.  Indices are clamped into the lattice and
+// the weights of out-of-lattice nodes zeroed, so a lane's loads are
+// independent and issued together.  All 32 lanes of the warp must call this
+// together.
+template <typename R, bool GRAD, int K>
+__device__ __forceinline__ void sample_group(const Dev& d, const Spot<R>& sp, int32_t m, int r, Sample<R>& o,
+                                             uint32_t& miss)
+{
+    const Lattice& L = d.L;
+    const R* __restrict__ ux = static_cast<const R*>(d.ux);
+    const R* __restrict__ uy = static_cast<const R*>(d.uy);
+    const R* __restrict__ dr = static_cast<const R*>(d.drho);
+    constexpr int NR = 4 / K;  // rows per lane
+    const int i0 = sp.ix - 1;
+    int ic[4];
+    R px[4], dpx[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = i0 + a;
+        const bool vi = (i >= 0 && i < L.nx);
+        ic[a] = min(max(i, 0), L.nx - 1);
+        const R rx = sp.ax + R(1 - a);  // X - i
+        dpx[a] = R(0);
+        if (GRAD) peskin_both<R>(rx, px[a], dpx[a]);
+        else px[a] = peskin<R>(rx);
+        if (!vi) px[a] = dpx[a] = R(0);
+    }
+    int jc[NR];
+    R py[NR], dpy[NR];
+    int32_t fr[2 * NR];
+    R a_u[4 * NR], a_v[4 * NR], a_r[4 * NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int rr = r + K * k;
+        const int j = sp.jy - 1 + rr;
+        const bool vj = (j >= 0 && j < L.ny);
+        jc[k] = min(max(j, 0), L.ny - 1);
+        const R ry = sp.ay + R(1 - rr);  // Y - (j + 1/2)
+        dpy[k] = R(0);
+        if (GRAD) peskin_both<R>(ry, py[k], dpy[k]);
+        else py[k] = peskin<R>(ry);
+        if (!vj) py[k] = dpy[k] = R(0);
+        // the row's nodes lie in at most two tiles: both must hold step m
+        fr[2 * k] = d.fresh[tile_of(L, ic[0], jc[k])];
+        fr[2 * k + 1] = d.fresh[tile_of(L, ic[3], jc[k])];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int idx = jc[k] * L.nxp + ic[a];
+            a_u[4 * k + a] = ux[idx];
+            a_v[4 * k + a] = uy[idx];
+            a_r[4 * k + a] = dr[idx];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * NR; ++k)
+        if (fr[k] != m) miss = 1u;
+    R W = 0, Nu = 0, Nv = 0, Nr = 0, Nux = 0, Nuy = 0, Nvx = 0, Nvy = 0;
+#pragma unroll
+    for (int k = 0; k < NR; ++k)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const R w = px[a] * py[k];
+            const int q = 4 * k + a;
+            W += w;
+            Nu += a_u[q] * w;
+            Nv += a_v[q] * w;
+            Nr += a_r[q] * w;
+            if (GRAD) {
+                const R wx = dpx[a] * py[k], wy = px[a] * dpy[k];
+                Nux += a_u[q] * wx;
+                Nuy += a_u[q] * wy;
+                Nvx += a_v[q] * wx;
+                Nvy += a_v[q] * wy;
+            }
+        }
+    W = group_sum<R, K>(W);
+    o.u = group_sum<R, K>(Nu);
+    o.v = group_sum<R, K>(Nv);
+    Nr = group_sum<R, K>(Nr);
+    if (GRAD) {
+        o.ux = group_sum<R, K>(Nux);
+        o.uy = group_sum<R, K>(Nuy);
+        o.vx = group_sum<R, K>(Nvx);
+        o.vy = group_sum<R, K>(Nvy);
+    } else {
+        o.ux = o.uy = o.vx = o.vy = R(0);
+    }
+    o.W = W;
+    o.drho = (W > R(0)) ? Nr / W : R(0);
+}
+
+// Tiles overlapping the node box [i0, i1] x [j0, j1]: enumerates at most 8 of
+// them per call into t[], starting after `start` tiles; returns the count.
+__device__ __forceinline__ int box_tiles(const Lattice& L, int i0, int i1, int j0, int j1, int start, int t[8])
+{
+    int n = 0, k = 0;
+    for (int ty = j0 / TY; ty <= j1 / TY; ++ty)
+        for (int tx = i0 / TX; tx <= i1 / TX; ++tx) {
+            if (k++ < start) continue;
+            if (n < 8) t[n++] = ty * L.ntx + tx;
+        }
+    return n;
+}
+
+template <typename R, int K>
 __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
 {
     const Lattice& L = d.L;
@@ -91,16 +239,22 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
     const int32_t mf = (int32_t)n;  // lattice step whose rho/u the interpolation reads
     const double* __restrict__ Pn = d.pos[n & 1];
     double* Pw = d.pos[(n + 1) & 1];  // X^{n-1} on entry, X^{n+1} on exit
-    const R* l0 = static_cast<const R*>(d.l0) + off;
-    const R* th0 = static_cast<const R*>(d.th0) + off;
+    const R* __restrict__ Fn = static_cast<const R*>(d.posf[n & 1]);
+    R* Fw = static_cast<R*>(d.posf[(n + 1) & 1]);
     R* diag = static_cast<R*>(d.diag);
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* sx = reinterpret_cast<double*>(smem_raw);
-    double* sy = sx + nv;
-    double* qx = sy + nv;  // X^{n+1}
-    double* qy = qx + nv;
-    R* ex = reinterpret_cast<R*>(qy + nv);
+    R* xh = reinterpret_cast<R*>(smem_raw);  // X^n
+    R* xl = xh + nv;
+    R* yh = xl + nv;
+    R* yl = yh + nv;
+    R* qxh = yl + nv;  // X^{n+1}
+    R* qxl = qxh + nv;
+    R* qyh = qxl + nv;
+    R* qyl = qyh + nv;
+    R* ddx = qyl + nv;  // X^n - X^{n-1}
+    R* ddy = ddx + nv;
+    R* ex = ddy + nv;
     R* ey = ex + nv;
     R* len = ey + nv;
     R* nlx = len + nv;
@@ -110,9 +264,7 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
     R* th = vny + nv;
     R* uvx = th + nv;
     R* uvy = uvx + nv;
-    R* eax = uvy + nv;
-    R* eay = eax + nv;
-    R* ewx = eay + nv;
+    R* ewx = uvy + nv;
     R* ewy = ewx + nv;
     R* ehx = ewy + nv;
     R* ehy = ehx + nv;
@@ -122,71 +274,101 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
     R* fty = ftx + nv;
     R* svx = fty + nv;
     R* svy = svx + nv;
-    __shared__ double dscr[32];
-    __shared__ R rscr[32];
-    __shared__ double rig[4];
+    R* sl0 = svy + nv;
+    R* sth0 = sl0 + nv;
+    R* ilen = sth0 + nv;
+    __shared__ double dscr[8][32];
+    __shared__ R rscr[8][32];
+    __shared__ double rig[RG_N];
+    __shared__ double rot[2];
+    __shared__ R ext[MAX_BODIES][4];
     uint32_t miss = 0u, bad = 0u;
+    const int lane4 = tid % K, Q = T / K;  // K lanes per interpolation point
+    const int nvq = ((nv + Q - 1) / Q) * Q;
 
-    // 1. geometry at X^n
-    for (int v = tid; v < nv; v += T) {
-        sx[v] = Pn[off + v];
-        sy[v] = Pn[NM + off + v];
-    }
-    __syncthreads();
+    // 0. one round of global loads; positions to float-float pairs; the FP64
+    //    shoelace terms of X^n (Eq. 11's area) directly from the loaded values
     double a2 = 0.0;
+    {
+        const R* l0 = static_cast<const R*>(d.l0) + off;
+        const R* th0 = static_cast<const R*>(d.th0) + off;
+        for (int v = tid; v < nv; v += T) {
+            const int w = (v + 1 == nv) ? 0 : v + 1;
+            const double X = Pn[off + v], Y = Pn[NM + off + v];
+            const double Xw = Pn[off + w], Yw = Pn[NM + off + w];
+            const double Xp = Pw[off + v], Yp = Pw[NM + off + v];
+            const P2<R> px = p2_of<R>(X), py = p2_of<R>(Y);
+            xh[v] = px.h;
+            xl[v] = px.l;
+            yh[v] = py.h;
+            yl[v] = py.l;
+            ddx[v] = (R)(X - Xp);
+            ddy[v] = (R)(Y - Yp);
+            sl0[v] = l0[v];
+            sth0[v] = th0[v];
+            a2 += X * Yw - Xw * Y;
+        }
+        if (tid < RG_N) rig[tid] = d.rigid[bi * RG_N + tid];
+        const double* eo = d.body_obs[n & 1];
+        for (int k = tid; k < 4 * d.nbodies; k += T) ext[k >> 2][k & 3] = (R)eo[(k >> 2) * BO_N + BO_XMIN + (k & 3)];
+    }
+    const double area = 0.5 * block_sum<double>(a2, dscr[0]);  // FP64 area reduction (Eq. 11)
+
+    // 1. geometry at X^n (the block_sum above synchronised the block)
     for (int l = tid; l < nv; l += T) {
-        int w = (l + 1 == nv) ? 0 : l + 1;
-        R dx = (R)(sx[w] - sx[l]), dy = (R)(sy[w] - sy[l]);
-        R ll = sqrt(dx * dx + dy * dy);
+        const int w = (l + 1 == nv) ? 0 : l + 1;
+        const R dx = p2_sub<R>(P2<R>{xh[w], xl[w]}, P2<R>{xh[l], xl[l]});
+        const R dy = p2_sub<R>(P2<R>{yh[w], yl[w]}, P2<R>{yh[l], yl[l]});
+        const R ll = sqrt(dx * dx + dy * dy);
+        const R il = R(1) / ll;
         ex[l] = dx;
         ey[l] = dy;
         len[l] = ll;
-        nlx[l] = dy / ll;
-        nly[l] = -dx / ll;
-        a2 += sx[l] * sy[w] - sx[w] * sy[l];
+        ilen[l] = il;
+        nlx[l] = dy * il;
+        nly[l] = -dx * il;
     }
-    const double area = 0.5 * block_sum<double>(a2, dscr);  // FP64 area reduction (Eq. 11)
+    __syncthreads();
     for (int v = tid; v < nv; v += T) {
-        int lm = (v == 0) ? nv - 1 : v - 1;
+        const int lm = (v == 0) ? nv - 1 : v - 1;
         th[v] = atan2(ex[lm] * ey[v] - ey[lm] * ex[v], ex[lm] * ex[v] + ey[lm] * ey[v]);
-        R sxn = nlx[lm] + nlx[v], syn = nly[lm] + nly[v];
-        R s = sqrt(sxn * sxn + syn * syn);
+        const R sxn = nlx[lm] + nlx[v], syn = nly[lm] + nly[v];
+        const R s = sqrt(sxn * sxn + syn * syn);
         vnx[v] = sxn / s;
         vny[v] = syn / s;
     }
-    __syncthreads();
 
-    // 2. fluid velocity at the vertices; tractions from the probes (Eqs. 14-15)
-    for (int v = tid; v < nv; v += T) {
-        Sample<R> o;
-        sample<R>(d, sx[v], sy[v], mf, false, o, miss);
-        uvx[v] = o.u;
-        uvy[v] = o.v;
-    }
+    // 2. fluid velocity at each vertex and traction of each element (Eqs. 14-15);
+    //    K lanes per vertex/element
     const R nu = (R)L.nu;
-    for (int l = tid; l < nv; l += T) {
-        int w = (l + 1 == nv) ? 0 : l + 1;
-        double px = 0.5 * (sx[l] + sx[w]) + d.probe * (double)nlx[l];
-        double py = 0.5 * (sy[l] + sy[w]) + d.probe * (double)nly[l];
-        py = fmin(fmax(py, 0.0), (double)L.ny);
-        Sample<R> o;
-        sample<R>(d, px, py, mf, true, o, miss);
-        R fx = 0, fy = 0;
-        if (o.W > R(0)) {
-            R pr = (o.rho - R(1)) / R(3);
-            R mu = o.rho * nu;
-            R txx = R(2) * mu * o.ux, txy = mu * (o.uy + o.vx), tyy = R(2) * mu * o.vy;
-            fx = (-pr * nlx[l] + txx * nlx[l] + txy * nly[l]) * len[l];
-            fy = (-pr * nly[l] + txy * nlx[l] + tyy * nly[l]) * len[l];
+    for (int v0 = tid / K; v0 < nvq; v0 += Q) {
+        const bool valid = v0 < nv;
+        const int l = valid ? v0 : nv - 1;
+        const P2<R> X = P2<R>{xh[l], xl[l]}, Y = P2<R>{yh[l], yl[l]};
+        // probe: element centroid + 1.2 dx along the outward normal, stopped at a wall
+        const P2<R> PX = p2_add<R>(X, R(0.5) * ex[l] + (R)d.probe * nlx[l]);
+        P2<R> PY = p2_add<R>(Y, R(0.5) * ey[l] + (R)d.probe * nly[l]);
+        if (PY.h + PY.l < R(0)) PY = P2<R>{R(0), R(0)};
+        if (PY.h + PY.l > R(L.ny)) PY = P2<R>{R(L.ny), R(0)};
+        Sample<R> o, q;
+        sample_group<R, false, K>(d, spot_of<R>(X, Y), mf, lane4, o, miss);
+        sample_group<R, true, K>(d, spot_of<R>(PX, PY), mf, lane4, q, miss);
+        if (valid && lane4 == 0) {
+            uvx[l] = o.u;
+            uvy[l] = o.v;
+            R fx = 0, fy = 0;
+            if (q.W > R(0)) {
+                const R pr = q.drho / R(3);  // c_s^2 rho - p_ref
+                const R mu = (R(1) + q.drho) * nu;
+                const R txx = R(2) * mu * q.ux, txy = mu * (q.uy + q.vx), tyy = R(2) * mu * q.vy;
+                fx = (-pr * nlx[l] + txx * nlx[l] + txy * nly[l]) * len[l];
+                fy = (-pr * nly[l] + txy * nlx[l] + tyy * nly[l]) * len[l];
+            }
+            ehx[l] = fx;
+            ehy[l] = fy;
+            ewx[l] = 0;
+            ewy[l] = 0;
         }
-        ehx[l] = fx;
-        ehy[l] = fy;
-        // Eq. 11: -k_a (1 - A / A_0) p_ref n^- l with n^- = -n
-        R fa = (B.motion == LBIB_DEFORMABLE) ? (R)(B.ka * (1.0 - area / B.A0) / 3.0) * len[l] : R(0);
-        eax[l] = fa * nlx[l];
-        eay[l] = fa * nly[l];
-        ewx[l] = 0;
-        ewy[l] = 0;
     }
     __syncthreads();
 
@@ -194,45 +376,51 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
     if (B.adhesive) {
         const R* lt = static_cast<const R*>(d.lig_t);
         R* mg = static_cast<R*>(d.margin);
-        const R Pf = (R)B.Pf;
-        for (int k = B.lig_off + tid; k < B.lig_off + B.nlig; k += T) {
-            if (B.motion == LBIB_FIXED) break;
-            int l = d.lig_el[k] - off, w = (l + 1 == nv) ? 0 : l + 1;
-            double t = (double)lt[k];
-            double px = sx[l] + t * (sx[w] - sx[l]), py = sy[l] + t * (sy[w] - sy[l]);
-            R u = (R)bond_draw(d.seed, n, (uint32_t)k);
-            if (d.bound[k]) {
-                double ddx = px - d.anchor[k], ddy = py - d.anchor[d.nlig + k];
-                R yl = (R)sqrt(ddx * ddx + ddy * ddy);
-                R dy = yl - (R)B.yeq;
-                R Pr = R(1) - exp(-(R)B.kr0_dt * exp((R)B.xi * dy * dy));
-                mg[k] = fabs(u - Pr);
-                if (u < Pr) d.bound[k] = 0;
-            } else {
-                double gap = fmin(py, (double)L.ny - py);
-                if (gap < B.ycr) {
-                    mg[k] = fabs(u - Pf);
-                    if (u < Pf) {
-                        d.bound[k] = 1;
-                        d.anchor[k] = px;
-                        d.anchor[d.nlig + k] = (py < (double)L.ny - py) ? 0.0 : (double)L.ny;
+        const R Pf = (R)B.Pf, ycr = (R)B.ycr, yeq = (R)B.yeq, H = (R)L.ny;
+        if (B.motion != LBIB_FIXED) {
+            for (int k = B.lig_off + tid; k < B.lig_off + B.nlig; k += T) {
+                const int l = d.lig_el[k] - off;
+                const R t = lt[k];
+                const int bd = d.bound[k];
+                const P2<R> SX = p2_add<R>(P2<R>{xh[l], xl[l]}, t * ex[l]);
+                const P2<R> SY = p2_add<R>(P2<R>{yh[l], yl[l]}, t * ey[l]);
+                const R u = (R)bond_draw(d.seed, n, (uint32_t)k);
+                if (bd) {
+                    const R dxa = p2_sub<R>(SX, p2_of<R>(d.anchor[k]));
+                    const R dya = p2_sub<R>(SY, p2_of<R>(d.anchor[d.nlig + k]));
+                    const R ylen = sqrt(dxa * dxa + dya * dya);
+                    const R dy = ylen - yeq;
+                    const R Pr = R(1) - exp(-(R)B.kr0_dt * exp((R)B.xi * dy * dy));
+                    mg[k] = fabs(u - Pr);
+                    if (u < Pr) d.bound[k] = 0;
+                } else {
+                    // gap to the nearest wall below y_cr, decided on the float-float value
+                    const bool lower = (SY.h - H * R(0.5)) + SY.l < R(0);
+                    const R gap_m_ycr = lower ? (SY.h - ycr) + SY.l : ((H - SY.h) - ycr) - SY.l;
+                    if (gap_m_ycr < R(0)) {
+                        mg[k] = fabs(u - Pf);
+                        if (u < Pf) {
+                            d.bound[k] = 1;
+                            d.anchor[k] = p2_double<R>(SX);
+                            d.anchor[d.nlig + k] = lower ? 0.0 : (double)L.ny;
+                        }
                     }
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
         if (!B.sigma_inf) {
             const R sig = (R)B.sigma;
             for (int l = tid; l < nv; l += T) {
-                int w = (l + 1 == nv) ? 0 : l + 1;
                 R s = 0;
                 for (int k = d.site_off[off + l]; k < d.site_off[off + l + 1]; ++k) {
                     if (!d.bound[k]) continue;
-                    double t = (double)lt[k];
-                    double px = sx[l] + t * (sx[w] - sx[l]), py = sy[l] + t * (sy[w] - sy[l]);
-                    double ddx = px - d.anchor[k], ddy = py - d.anchor[d.nlig + k];
-                    R yl = (R)sqrt(ddx * ddx + ddy * ddy);
-                    s += sig * (yl - (R)B.yeq);
+                    const R t = lt[k];
+                    const P2<R> SX = p2_add<R>(P2<R>{xh[l], xl[l]}, t * ex[l]);
+                    const P2<R> SY = p2_add<R>(P2<R>{yh[l], yl[l]}, t * ey[l]);
+                    const R dxa = p2_sub<R>(SX, p2_of<R>(d.anchor[k]));
+                    const R dya = p2_sub<R>(SY, p2_of<R>(d.anchor[d.nlig + k]));
+                    s += sig * (sqrt(dxa * dxa + dya * dya) - yeq);
                 }
                 ewx[l] = s * nlx[l];
                 ewy[l] = s * nly[l];
@@ -241,22 +429,24 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
     }
 
     // repulsion (Eq. 12) from the vertices of every other body within the cut-off
-    const double* ext = d.body_obs[n & 1];
     const R c0 = R(1e-4) / (R(8) * sqrt(R(2)));
+    const R dcut = (R)d.dcut;
     for (int v = tid; v < nv; v += T) {
         R ax = 0, ay = 0;
+        const P2<R> X = P2<R>{xh[v], xl[v]}, Y = P2<R>{yh[v], yl[v]};
+        const R xa = X.h + X.l, ya = Y.h + Y.l;
         for (int o = 0; o < d.nbodies; ++o) {
             if (o == bi) continue;
-            const double* eo = ext + o * BO_N;
-            if (sx[v] < eo[BO_XMIN] - d.dcut || sx[v] > eo[BO_XMAX] + d.dcut || sy[v] < eo[BO_YMIN] - d.dcut ||
-                sy[v] > eo[BO_YMAX] + d.dcut)
+            if (xa < ext[o][0] - dcut || xa > ext[o][1] + dcut || ya < ext[o][2] - dcut || ya > ext[o][3] + dcut)
                 continue;
             const BodyConst& C = d.body[o];
             for (int w = 0; w < C.nv; ++w) {
-                R ddx = (R)(sx[v] - Pn[C.off + w]), ddy = (R)(sy[v] - Pn[NM + C.off + w]);
-                R dd = sqrt(ddx * ddx + ddy * ddy);
-                if (dd < (R)d.dcut) {
-                    R mag = c0 * sqrt(R(1) / (dd * dd * dd * dd * dd));
+                const int g = C.off + w;
+                const R ddx_ = p2_sub<R>(X, P2<R>{Fn[g], Fn[NM + g]});
+                const R ddy_ = p2_sub<R>(Y, P2<R>{Fn[2 * NM + g], Fn[3 * NM + g]});
+                const R dd = sqrt(ddx_ * ddx_ + ddy_ * ddy_);
+                if (dd < dcut) {
+                    const R mag = c0 * sqrt(R(1) / (dd * dd * dd * dd * dd));
                     ax += mag * (-vnx[v]);
                     ay += mag * (-vny[v]);
                 }
@@ -270,33 +460,36 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
     // 4. vertex forces (Eq. 16)
     const bool deform = (B.motion == LBIB_DEFORMABLE);
     const R ks = (R)B.ks, kb = (R)B.kb;
+    // Eq. 11: -k_a (1 - A / A_0) p_ref n^- l with n^- = -n
+    const R fa_c = deform ? (R)(B.ka * ((B.A0 - area) * B.inv_A0) / 3.0) : R(0);
     for (int v = tid; v < nv; v += T) {
-        int lm = (v == 0) ? nv - 1 : v - 1, w = (v + 1 == nv) ? 0 : v + 1;
+        const int lm = (v == 0) ? nv - 1 : v - 1, w = (v + 1 == nv) ? 0 : v + 1;
         R fsx = 0, fsy = 0, fbx = 0, fby = 0;
         if (deform) {
             // Eq. 8: element lm pulls v along e_lm, element v along -e_v
-            R cl = -ks * (len[lm] - l0[lm]) / len[lm];
-            R cr = -ks * (len[v] - l0[v]) / len[v];
+            const R cl = -ks * (len[lm] - sl0[lm]) * ilen[lm];
+            const R cr = -ks * (len[v] - sl0[v]) * ilen[v];
             fsx = cl * ex[lm] - cr * ex[v];
             fsy = cl * ey[lm] - cr * ey[v];
             // Eq. 10: triples centred at lm (v on its right), v, and w (v on its left)
-            int lmm = (lm == 0) ? nv - 1 : lm - 1;
-            R kl = kb * (th[lm] - th0[lm]);
-            R kc = kb * (th[v] - th0[v]);
-            R kr = kb * (th[w] - th0[w]);
-            R cR = kl * len[lm] / (len[lmm] + len[lm]);
-            R cL = kr * len[v] / (len[v] + len[w]);
+            const int lmm = (lm == 0) ? nv - 1 : lm - 1;
+            const R kl = kb * (th[lm] - sth0[lm]);
+            const R kc = kb * (th[v] - sth0[v]);
+            const R kr = kb * (th[w] - sth0[w]);
+            const R cR = kl * len[lm] / (len[lmm] + len[lm]);
+            const R cL = kr * len[v] / (len[v] + len[w]);
             fbx = cR * vnx[lm] - kc * vnx[v] + cL * vnx[w];
             fby = cR * vny[lm] - kc * vny[v] + cL * vny[w];
         }
-        R fax = R(0.5) * (eax[lm] + eax[v]), fay = R(0.5) * (eay[lm] + eay[v]);
-        R fwx = R(0.5) * (ewx[lm] + ewx[v]), fwy = R(0.5) * (ewy[lm] + ewy[v]);
-        R fhx = R(0.5) * (ehx[lm] + ehx[v]), fhy = R(0.5) * (ehy[lm] + ehy[v]);
-        R tx = fsx + fbx + fax + fpx[v] + fwx + fhx;
-        R ty = fsy + fby + fay + fpy[v] + fwy + fhy;
+        const R fax = R(0.5) * fa_c * (len[lm] * nlx[lm] + len[v] * nlx[v]);
+        const R fay = R(0.5) * fa_c * (len[lm] * nly[lm] + len[v] * nly[v]);
+        const R fwx = R(0.5) * (ewx[lm] + ewx[v]), fwy = R(0.5) * (ewy[lm] + ewy[v]);
+        const R fhx = R(0.5) * (ehx[lm] + ehx[v]), fhy = R(0.5) * (ehy[lm] + ehy[v]);
+        const R tx = fsx + fbx + fax + fpx[v] + fwx + fhx;
+        const R ty = fsy + fby + fay + fpy[v] + fwy + fhy;
         ftx[v] = tx;
         fty[v] = ty;
-        int g = off + v;
+        const int g = off + v;
         diag[LBIB_FIELD_UVX * NM + g] = uvx[v];
         diag[LBIB_FIELD_UVY * NM + g] = uvy[v];
         diag[LBIB_FIELD_FSX * NM + g] = fsx;
@@ -320,60 +513,71 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
     if (deform) {
         const R mv = (R)B.mv;
         for (int v = tid; v < nv; v += T) {
-            double xn = sx[v] + (double)uvx[v] + (double)(R(0.5) * ftx[v] / mv);
-            double yn = sy[v] + (double)uvy[v] + (double)(R(0.5) * fty[v] / mv);
-            double xp = Pw[off + v], yp = Pw[NM + off + v];  // X^{n-1}
-            svx[v] = (R)(1.5 * xn - 2.0 * sx[v] + 0.5 * xp);
-            svy[v] = (R)(1.5 * yn - 2.0 * sy[v] + 0.5 * yp);
-            qx[v] = xn;
-            qy[v] = yn;
+            // Eq. 17 (dt = 1); Eq. 18 as 3/2 (X^{n+1} - X^n) - 1/2 (X^n - X^{n-1})
+            const R dxn = uvx[v] + R(0.5) * ftx[v] / mv, dyn = uvy[v] + R(0.5) * fty[v] / mv;
+            const P2<R> nx_ = p2_add<R>(P2<R>{xh[v], xl[v]}, dxn);
+            const P2<R> ny_ = p2_add<R>(P2<R>{yh[v], yl[v]}, dyn);
+            qxh[v] = nx_.h;
+            qxl[v] = nx_.l;
+            qyh[v] = ny_.h;
+            qyl[v] = ny_.l;
+            svx[v] = R(1.5) * dxn - R(0.5) * ddx[v];
+            svy[v] = R(1.5) * dyn - R(0.5) * ddy[v];
         }
     } else if (B.motion == LBIB_RIGID) {
-        double* rs = d.rigid + bi * RG_N;
-        const double xc = rs[RG_XC], yc = rs[RG_YC];
+        const double xc = rig[RG_XC], yc = rig[RG_YC];
+        const P2<R> XC = p2_of<R>(xc), YC = p2_of<R>(yc);
         R sfx = 0, sfy = 0, smz = 0;
         for (int v = tid; v < nv; v += T) {
             sfx += ftx[v];
             sfy += fty[v];
-            smz += (R)(sx[v] - xc) * fty[v] - (R)(sy[v] - yc) * ftx[v];
+            const R rx = p2_sub<R>(P2<R>{xh[v], xl[v]}, XC), ry = p2_sub<R>(P2<R>{yh[v], yl[v]}, YC);
+            smz += rx * fty[v] - ry * ftx[v];
         }
-        sfx = block_sum<R>(sfx, rscr);
-        sfy = block_sum<R>(sfy, rscr);
-        smz = block_sum<R>(smz, rscr);
+        sfx = block_sum<R>(sfx, rscr[0]);
+        sfy = block_sum<R>(sfy, rscr[1]);
+        smz = block_sum<R>(smz, rscr[2]);
+        __syncthreads();
         if (tid == 0) {
             // Eq. 19: u = 2/3 (2 u(t - dt) - 1/2 u(t - 2 dt) + du/dt dt), likewise omega
-            double ux = (2.0 / 3.0) * (2.0 * rs[RG_U1X] - 0.5 * rs[RG_U2X] + (double)sfx / B.mass);
-            double uy = (2.0 / 3.0) * (2.0 * rs[RG_U1Y] - 0.5 * rs[RG_U2Y] + (double)sfy / B.mass);
-            double om = (2.0 / 3.0) * (2.0 * rs[RG_W1] - 0.5 * rs[RG_W2] + (double)smz / B.inertia);
-            rs[RG_U2X] = rs[RG_U1X];
-            rs[RG_U1X] = ux;
-            rs[RG_U2Y] = rs[RG_U1Y];
-            rs[RG_U1Y] = uy;
-            rs[RG_W2] = rs[RG_W1];
-            rs[RG_W1] = om;
-            rs[RG_XC] = xc + ux;
-            rs[RG_YC] = yc + uy;
-            rs[RG_ANG] += om;
-            rig[0] = ux;
-            rig[1] = uy;
-            rig[2] = om;
-            rig[3] = rs[RG_ANG];
+            const double ux = (2.0 / 3.0) * (2.0 * rig[RG_U1X] - 0.5 * rig[RG_U2X] + (double)sfx / B.mass);
+            const double uy = (2.0 / 3.0) * (2.0 * rig[RG_U1Y] - 0.5 * rig[RG_U2Y] + (double)sfy / B.mass);
+            const double om = (2.0 / 3.0) * (2.0 * rig[RG_W1] - 0.5 * rig[RG_W2] + (double)smz / B.inertia);
+            rig[RG_U2X] = rig[RG_U1X];
+            rig[RG_U1X] = ux;
+            rig[RG_U2Y] = rig[RG_U1Y];
+            rig[RG_U1Y] = uy;
+            rig[RG_W2] = rig[RG_W1];
+            rig[RG_W1] = om;
+            rig[RG_XC] = xc + ux;
+            rig[RG_YC] = yc + uy;
+            rig[RG_ANG] += om;
+            double* rs = d.rigid + bi * RG_N;
+            for (int k = 0; k < RG_N; ++k) rs[k] = rig[k];
+            rot[0] = cos(rig[RG_ANG]);
+            rot[1] = sin(rig[RG_ANG]);
         }
         __syncthreads();
-        const double ux = rig[0], uy = rig[1], om = rig[2], cs = cos(rig[3]), sn = sin(rig[3]);
-        const double ncx = rs[RG_XC], ncy = rs[RG_YC];
+        const R ux = (R)rig[RG_U1X], uy = (R)rig[RG_U1Y], om = (R)rig[RG_W1];
+        const R cs = (R)rot[0], sn = (R)rot[1];
+        const P2<R> NCX = p2_of<R>(rig[RG_XC]), NCY = p2_of<R>(rig[RG_YC]);
         for (int v = tid; v < nv; v += T) {
-            double rx = cs * d.rref[off + v] - sn * d.rref[NM + off + v];
-            double ry = sn * d.rref[off + v] + cs * d.rref[NM + off + v];
-            qx[v] = ncx + rx;
-            qy[v] = ncy + ry;
-            svx[v] = (R)(ux - om * ry);
-            svy[v] = (R)(uy + om * rx);
+            const R a = (R)d.rref[off + v], b = (R)d.rref[NM + off + v];
+            const R rx = cs * a - sn * b, ry = sn * a + cs * b;
+            const P2<R> nx_ = p2_add<R>(NCX, rx), ny_ = p2_add<R>(NCY, ry);
+            qxh[v] = nx_.h;
+            qxl[v] = nx_.l;
+            qyh[v] = ny_.h;
+            qyl[v] = ny_.l;
+            svx[v] = ux - om * ry;
+            svy[v] = uy + om * rx;
         }
     } else {
         for (int v = tid; v < nv; v += T) {
-            qx[v] = sx[v];
-            qy[v] = sy[v];
+            qxh[v] = xh[v];
+            qxl[v] = xl[v];
+            qyh[v] = yh[v];
+            qyl[v] = yl[v];
             svx[v] = 0;
             svy[v] = 0;
         }
@@ -381,125 +585,203 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
     __syncthreads();
 
     // 6. direct forcing at the new element centroids, spreading masks, activation
-    R* mk = static_cast<R*>(d.mk[p]);
+    int32_t* mki = d.mki[p];
+    R* mkf = static_cast<R*>(d.mkf[p]);
     const int64_t n2 = n + 2;
     uint32_t* flag2 = d.nearflag[n2 & 1];
     const int c2 = (int)(n2 % 3);
-    double per = 0.0, cxs = 0.0, cys = 0.0, a2n = 0.0;
-    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
-    for (int l = tid; l < nv; l += T) {
-        int w = (l + 1 == nv) ? 0 : l + 1;
-        double cx = 0.5 * (qx[l] + qx[w]), cy = 0.5 * (qy[l] + qy[w]);
-        double dxn = qx[w] - qx[l], dyn = qy[w] - qy[l];
-        double ds = sqrt(dxn * dxn + dyn * dyn);
-        R usx = R(0.5) * (svx[l] + svx[w]), usy = R(0.5) * (svy[l] + svy[w]);
+    const int ra = (int)ceil(d.r_act_sub) + 1;
+    R dper = 0;
+    for (int l0 = tid / K; l0 < nvq; l0 += Q) {
+        const bool valid = l0 < nv;
+        const int l = valid ? l0 : nv - 1;
+        const int w = (l + 1 == nv) ? 0 : l + 1;
+        const R dxn = p2_sub<R>(P2<R>{qxh[w], qxl[w]}, P2<R>{qxh[l], qxl[l]});
+        const R dyn = p2_sub<R>(P2<R>{qyh[w], qyl[w]}, P2<R>{qyh[l], qyl[l]});
+        const P2<R> CX = p2_add<R>(P2<R>{qxh[l], qxl[l]}, R(0.5) * dxn);
+        const P2<R> CY = p2_add<R>(P2<R>{qyh[l], qyl[l]}, R(0.5) * dyn);
+        const Spot<R> sc = spot_of<R>(CX, CY);
         Sample<R> o;
-        sample<R>(d, cx, cy, mf, false, o, miss);
-        bool held = (cy < 0.5) || (cy > (double)L.ny - 0.5);
+        sample_group<R, false, K>(d, sc, mf, lane4, o, miss);
+        if (!valid) continue;
+        const R ds = sqrt(dxn * dxn + dyn * dyn);
+        const R usx = R(0.5) * (svx[l] + svx[w]), usy = R(0.5) * (svy[l] + svy[w]);
+        // centroid below the first or above the last row of fluid nodes: held by the wall
+        const bool held = (sc.jy < 0) || (sc.jy > L.ny - 1) || (sc.jy == L.ny - 1 && sc.ay > R(0));
         R Fx = 0, Fy = 0;
         if (o.W > R(0) && !held) {
-            Fx = o.rho * (usx - o.u);
-            Fy = o.rho * (usy - o.v);
+            const R rho = R(1) + o.drho;
+            Fx = rho * (usx - o.u);
+            Fy = rho * (usy - o.v);
         }
         const int g = off + l;
-        mk[g] = (R)cx;
-        mk[NM + g] = (R)cy;
-        mk[2 * NM + g] = Fx * (R)ds;
-        mk[3 * NM + g] = Fy * (R)ds;
-        diag[LBIB_FIELD_VX * NM + g] = svx[l];
-        diag[LBIB_FIELD_VY * NM + g] = svy[l];
-        diag[LBIB_FIELD_MX * NM + g] = (R)cx;
-        diag[LBIB_FIELD_MY * NM + g] = (R)cy;
-        diag[LBIB_FIELD_MFX * NM + g] = Fx;
-        diag[LBIB_FIELD_MFY * NM + g] = Fy;
-        diag[LBIB_FIELD_MDS * NM + g] = (R)ds;
+        if (lane4 == 0) {
+            mki[g] = sc.ix;
+            mki[NM + g] = sc.jy;
+            mkf[g] = sc.ax;
+            mkf[NM + g] = sc.ay;
+            mkf[2 * NM + g] = Fx * ds;
+            mkf[3 * NM + g] = Fy * ds;
+            diag[LBIB_FIELD_VX * NM + g] = svx[l];
+            diag[LBIB_FIELD_VY * NM + g] = svy[l];
+            diag[LBIB_FIELD_MX * NM + g] = CX.h + CX.l;
+            diag[LBIB_FIELD_MY * NM + g] = CY.h + CY.l;
+            diag[LBIB_FIELD_MFX * NM + g] = Fx;
+            diag[LBIB_FIELD_MFY * NM + g] = Fy;
+            diag[LBIB_FIELD_MDS * NM + g] = ds;
+            dper += ds - sl0[l];  // perimeter change for delta p (Sec. 3.1)
+        }
+        int tl[8];
         if (Fx != R(0) || Fy != R(0)) {
-            int i0 = max(0, (int)floor(cx) - 1), i1 = min(L.nx - 1, (int)floor(cx) + 2);
-            int j0 = max(0, (int)floor(cy - 0.5) - 1), j1 = min(L.ny - 1, (int)floor(cy - 0.5) + 2);
-            for (int ty = j0 / TY; ty <= j1 / TY && i0 <= i1; ++ty)
-                for (int tx = i0 / TX; tx <= i1 / TX; ++tx) {
-                    int t = ty * L.ntx + tx;
+            // stencil nodes [ix - 1, ix + 2] x [jy - 1, jy + 2]: at most 2 x 2 tiles, one per lane
+            const int i0 = max(0, sc.ix - 1), i1 = min(L.nx - 1, sc.ix + 2);
+            const int j0 = max(0, sc.jy - 1), j1 = min(L.ny - 1, sc.jy + 2);
+            if (i0 <= i1 && j0 <= j1) {
+                const int nt = box_tiles(L, i0, i1, j0, j1, 0, tl);
+                for (int e = lane4; e < nt; e += K) {
+                    const int t = tl[e];
                     if (!d.nearflag[p][t]) miss |= 2u;
                     atomicOr(&d.mask[p][(size_t)t * d.mw + (g >> 5)], 1u << (g & 31));
                 }
+            }
         }
-        {
-            int i0 = max(0, (int)floor(cx - d.r_act)), i1 = min(L.nx - 1, (int)floor(cx + d.r_act) + 1);
-            int j0 = max(0, (int)floor(cy - 0.5 - d.r_act)), j1 = min(L.ny - 1, (int)floor(cy - 0.5 + d.r_act) + 1);
-            for (int ty = j0 / TY; ty <= j1 / TY && i0 <= i1; ++ty)
-                for (int tx = i0 / TX; tx <= i1 / TX; ++tx) {
-                    int t = ty * L.ntx + tx;
-                    if (flag2[t] == 0u && atomicExch(&flag2[t], 1u) == 0u) {
-                        int pos = atomicAdd(&d.count[c2], 1);
-                        if (pos < d.list_cap) d.list[c2][pos] = t;
-                        else bad |= ST_LIST_OVERFLOW;
+        if (l % ACT_STRIDE == 0 || l == nv - 1) {
+            // tiles within r_act of every centroid are scheduled near for lattice
+            // step n + 2: each ACT_STRIDE-th element covers the box of half-width
+            // ra_sub (r_act plus the stride's reach along the chain) around its
+            // stencil origin; the lanes split the tile list
+            const int i0 = max(0, sc.ix - ra), i1 = min(L.nx - 1, sc.ix + ra);
+            const int j0 = max(0, sc.jy - ra), j1 = min(L.ny - 1, sc.jy + ra);
+            if (i0 <= i1 && j0 <= j1) {
+                for (int start = 0;; start += 8) {
+                    const int nt = box_tiles(L, i0, i1, j0, j1, start, tl);
+                    uint32_t fl[8 / K];
+#pragma unroll
+                    for (int k = 0; k < 8 / K; ++k) {
+                        const int e = lane4 + K * k;
+                        fl[k] = (e < nt) ? flag2[tl[e]] : 1u;
                     }
+#pragma unroll
+                    for (int k = 0; k < 8 / K; ++k) {
+                        const int e = lane4 + K * k;
+                        if (e < nt && fl[k] == 0u && atomicExch(&flag2[tl[e]], 1u) == 0u) {
+                            const int pos = atomicAdd(&d.count[c2], 1);
+                            if (pos < d.list_cap) d.list[c2][pos] = tl[e];
+                            else bad |= ST_LIST_OVERFLOW;
+                        }
+                    }
+                    if (nt < 8) break;
                 }
+            }
         }
-        // 7. measures of X^{n+1}
-        double cr = qx[l] * qy[w] - qx[w] * qy[l];
-        a2n += cr;
-        per += ds;
-        cxs += (qx[l] + qx[w]) * cr;
-        cys += (qy[l] + qy[w]) * cr;
-        if (!isfinite(qx[l]) || !isfinite(qy[l])) bad |= ST_DIVERGED;
     }
+
+    // 7. measures of X^{n+1}: FP64 shoelace area and centroid sums, FP32
+    //    perimeter change and extent; store X^{n+1}
+    double a2n = 0.0, cxs = 0.0, cys = 0.0;
+    R xmin = R(3e38), xmax = R(-3e38), ymin = R(3e38), ymax = R(-3e38);
     for (int v = tid; v < nv; v += T) {
-        xmin = fmin(xmin, qx[v]);
-        xmax = fmax(xmax, qx[v]);
-        ymin = fmin(ymin, qy[v]);
-        ymax = fmax(ymax, qy[v]);
-        Pw[off + v] = qx[v];
-        Pw[NM + off + v] = qy[v];
+        const int w = (v + 1 == nv) ? 0 : v + 1;
+        const P2<R> X = P2<R>{qxh[v], qxl[v]}, Y = P2<R>{qyh[v], qyl[v]};
+        const double Xd = p2_double<R>(X), Yd = p2_double<R>(Y);
+        const double Xw = p2_double<R>(P2<R>{qxh[w], qxl[w]}), Yw = p2_double<R>(P2<R>{qyh[w], qyl[w]});
+        const double cr = Xd * Yw - Xw * Yd;
+        a2n += cr;
+        cxs += (Xd + Xw) * cr;
+        cys += (Yd + Yw) * cr;
+        const R xa = X.h + X.l, ya = Y.h + Y.l;
+        xmin = fmin(xmin, xa);
+        xmax = fmax(xmax, xa);
+        ymin = fmin(ymin, ya);
+        ymax = fmax(ymax, ya);
+        if (!isfinite(xa) || !isfinite(ya)) bad |= ST_DIVERGED;
+        Pw[off + v] = Xd;
+        Pw[NM + off + v] = Yd;
+        Fw[off + v] = X.h;
+        Fw[NM + off + v] = X.l;
+        Fw[2 * NM + off + v] = Y.h;
+        Fw[3 * NM + off + v] = Y.l;
     }
     int nb = 0;
     if (B.adhesive)
         for (int k = B.lig_off + tid; k < B.lig_off + B.nlig; k += T) nb += d.bound[k];
-    a2n = block_sum<double>(a2n, dscr);
-    per = block_sum<double>(per, dscr);
-    cxs = block_sum<double>(cxs, dscr);
-    cys = block_sum<double>(cys, dscr);
-    double nbd = block_sum<double>((double)nb, dscr);
-    xmin = block_min<double>(xmin, dscr);
-    xmax = block_max<double>(xmax, dscr);
-    ymin = block_min<double>(ymin, dscr);
-    ymax = block_max<double>(ymax, dscr);
+    // fused block reductions
+    {
+        double sv[3] = {a2n, cxs, cys};
+        R rv[6] = {dper, (R)nb, xmin, ymin, -xmax, -ymax};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) sv[k] = warp_sum(sv[k]);
+        rv[0] = warp_sum(rv[0]);
+        rv[1] = warp_sum(rv[1]);
+#pragma unroll
+        for (int k = 2; k < 6; ++k) rv[k] = warp_min(rv[k]);
+        const int lane = tid & 31, wid = tid >> 5, nw = (T + 31) >> 5;
+        __syncthreads();
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) dscr[k][wid] = sv[k];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) rscr[k][wid] = rv[k];
+        }
+        __syncthreads();
+        if (wid == 0) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) sv[k] = warp_sum(lane < nw ? dscr[k][lane] : 0.0);
+            rv[0] = warp_sum(lane < nw ? rscr[0][lane] : R(0));
+            rv[1] = warp_sum(lane < nw ? rscr[1][lane] : R(0));
+#pragma unroll
+            for (int k = 2; k < 6; ++k) rv[k] = warp_min(lane < nw ? rscr[k][lane] : R(3e38));
+        }
+        a2n = sv[0];
+        cxs = sv[1];
+        cys = sv[2];
+        dper = rv[0];
+        nb = (int)rv[1];
+        xmin = rv[2];
+        ymin = rv[3];
+        xmax = -rv[4];
+        ymax = -rv[5];
+    }
     if (miss & 1u) bad |= ST_READ_MISS;
     if (miss & 2u) bad |= ST_SPREAD_MISS;
     if (bad) atomicOr(d.status, bad);
     if (tid == 0) {
         double* bo = d.body_obs[(n + 1) & 1] + bi * BO_N;
-        double A = 0.5 * a2n;
+        const double A = 0.5 * a2n;
         bo[BO_AREA] = A;
-        bo[BO_PERIM] = per;
-        bo[BO_CX] = cxs / (6.0 * A);
-        bo[BO_CY] = cys / (6.0 * A);
-        bo[BO_NBOUND] = nbd;
+        bo[BO_DPERIM] = (double)dper;
+        // 1 / (6 A): FP32 reciprocal refined by one FP64 Newton step (no FP64 division)
+        const double s6 = 6.0 * A;
+        double inv = (double)(1.0f / (float)s6);
+        inv = inv * (2.0 - s6 * inv);
+        bo[BO_CX] = cxs * inv;
+        bo[BO_CY] = cys * inv;
+        bo[BO_NBOUND] = nb;
         bo[BO_XMIN] = xmin;
         bo[BO_XMAX] = xmax;
         bo[BO_YMIN] = ymin;
         bo[BO_YMAX] = ymax;
         __threadfence();
-        uint32_t ticket = atomicAdd(d.ticket, 1u);
+        const uint32_t ticket = atomicAdd(d.ticket, 1u);
         if (ticket == (uint32_t)d.nbodies - 1u) {
             // last block: observables of step n + 1 (Sec. 3.1), then advance n
             __threadfence();
-            const double* all = d.body_obs[(n + 1) & 1];
+            const volatile double* all = d.body_obs[(n + 1) & 1];
             lbib_obs r;
             r.step = n + 1;
             r.t_star = (double)(n + 1) * d.uscale;
-            double nan = __longlong_as_double(0x7ff8000000000000ULL);
+            const double nan = __longlong_as_double(0x7ff8000000000000ULL);
             r.delta_p = nan;
             r.r = nan;
             r.n_l = nan;
-            if (d.first_cell >= 0) {
-                const BodyConst& Cc = d.body[d.first_cell];
-                r.delta_p = (all[d.first_cell * BO_N + BO_PERIM] - Cc.P0) / Cc.P0;
-            }
+            if (d.first_cell >= 0) r.delta_p = all[d.first_cell * BO_N + BO_DPERIM] * d.body[d.first_cell].inv_P0;
             if (d.first_cell >= 0 && d.first_particle >= 0) {
-                double dx = all[d.first_cell * BO_N + BO_CX] - all[d.first_particle * BO_N + BO_CX];
-                double dy = all[d.first_cell * BO_N + BO_CY] - all[d.first_particle * BO_N + BO_CY];
-                r.r = sqrt(dx * dx + dy * dy);
+                const double dx = all[d.first_cell * BO_N + BO_CX] - all[d.first_particle * BO_N + BO_CX];
+                const double dy = all[d.first_cell * BO_N + BO_CY] - all[d.first_particle * BO_N + BO_CY];
+                const double r2 = dx * dx + dy * dy;
+                // FP32 square root refined by one FP64 Newton correction
+                const float s = sqrtf((float)r2);
+                r.r = (s > 0.f) ? (double)s + (r2 - (double)s * (double)s) * (0.5 / (double)s) : 0.0;
             }
             int nbt = 0, nl0 = 0;
             for (int b = 0; b < d.nbodies; ++b)
@@ -522,22 +804,49 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
 size_t lagrangian_smem_bytes(int prec, int nv_max)
 {
     size_t r = (prec == PREC_F64) ? sizeof(double) : sizeof(float);
-    return (size_t)nv_max * (4 * sizeof(double) + 22 * r);
+    return (size_t)nv_max * 33 * r;
+}
+
+// lanes per interpolation point: as many as keep every body in one pass
+static int lanes_for(int nv_max)
+{
+    if (nv_max * 4 <= LAG_THREADS) return 4;
+    if (nv_max * 2 <= LAG_THREADS) return 2;
+    return 1;
+}
+
+template <typename R>
+static cudaError_t configure_prec(int bytes)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_lagrangian<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_lagrangian<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_lagrangian<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
 }
 
 cudaError_t configure_kernels(int prec, int nv_max)
 {
-    size_t bytes = lagrangian_smem_bytes(prec, nv_max);
-    if (prec == PREC_F64)
-        return cudaFuncSetAttribute(k_lagrangian<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    return cudaFuncSetAttribute(k_lagrangian<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    const int bytes = (int)lagrangian_smem_bytes(prec, nv_max);
+    return (prec == PREC_F64) ? configure_prec<double>(bytes) : configure_prec<float>(bytes);
+}
+
+template <typename R>
+static void launch_prec(const Dev& d, int parity, size_t bytes, cudaStream_t s)
+{
+    switch (lanes_for(d.nv_max)) {
+    case 4: k_lagrangian<R, 4><<<d.nbodies, LAG_THREADS, bytes, s>>>(d, parity); break;
+    case 2: k_lagrangian<R, 2><<<d.nbodies, LAG_THREADS, bytes, s>>>(d, parity); break;
+    default: k_lagrangian<R, 1><<<d.nbodies, LAG_THREADS, bytes, s>>>(d, parity); break;
+    }
 }
 
 cudaError_t launch_lagrangian(const Dev& d, int prec, int parity, cudaStream_t s)
 {
-    size_t bytes = lagrangian_smem_bytes(prec, d.nv_max);
-    if (prec == PREC_F64) k_lagrangian<double><<<d.nbodies, LAG_THREADS, bytes, s>>>(d, parity);
-    else k_lagrangian<float><<<d.nbodies, LAG_THREADS, bytes, s>>>(d, parity);
+    const size_t bytes = lagrangian_smem_bytes(prec, d.nv_max);
+    if (prec == PREC_F64) launch_prec<double>(d, parity, bytes, s);
+    else launch_prec<float>(d, parity, bytes, s);
     return cudaGetLastError();
 }
 

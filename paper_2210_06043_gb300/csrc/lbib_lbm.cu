@@ -132,6 +132,8 @@ __global__ void __launch_bounds__(TX* TY) k_bulk(Dev d, int p)
     for (int q = 0; q < 9; ++q) st<S, R>(fout + q * L.qstride + base, g[q]);
 }
 
+constexpr int NEAR_CHUNK_WORDS = 8;  // mask words staged per round (<= 256 markers)
+
 template <typename S, typename R>
 __global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
 {
@@ -141,36 +143,73 @@ __global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
     const int cnt = min(d.count[c], d.list_cap);
     const S* __restrict__ fin = static_cast<const S*>(d.f[p]);
     S* __restrict__ fout = static_cast<S*>(d.f[p ^ 1]);
-    const R* __restrict__ mk = static_cast<const R*>(d.mk[p]);
     const int nm = d.nmark;
+    const int32_t* __restrict__ mki = d.mki[p];
+    const R* __restrict__ mkf = static_cast<const R*>(d.mkf[p]);
     uint32_t* mask = d.mask[p];
     R* drho_o = static_cast<R*>(d.drho);
     R* ux_o = static_cast<R*>(d.ux);
     R* uy_o = static_cast<R*>(d.uy);
     const int tid = threadIdx.y * TX + threadIdx.x;
+    __shared__ uint32_t s_words[NEAR_CHUNK_WORDS];
+    __shared__ int s_off[NEAR_CHUNK_WORDS];
+    __shared__ int s_n;
+    __shared__ int s_ix[32 * NEAR_CHUNK_WORDS], s_iy[32 * NEAR_CHUNK_WORDS];
+    __shared__ R s_fx[32 * NEAR_CHUNK_WORDS], s_fy[32 * NEAR_CHUNK_WORDS];
+    __shared__ R s_Fx[32 * NEAR_CHUNK_WORDS], s_Fy[32 * NEAR_CHUNK_WORDS];
     for (int k = blockIdx.x; k < cnt; k += gridDim.x) {
         const int t = d.list[c][k];
         const int tx = t % L.ntx, ty = t / L.ntx;
         const int x = tx * TX + threadIdx.x, y = ty * TY + threadIdx.y;
+        const bool live = (x < L.nx && y < L.ny);
+        R g[9];
+        if (live) pull<S, R>(L, fin, x, y, g);  // issued before the marker gather
         R Fx = R(L.gx), Fy = R(L.gy);
-        const R xr = R(x), yr = R(y) + R(0.5);
-        for (int w = 0; w < d.mw; ++w) {
-            uint32_t bits = mask[(size_t)t * d.mw + w];
-            while (bits) {
-                int b = __ffs(bits) - 1;
-                bits &= bits - 1u;
-                int id = w * 32 + b;
-                R rx = mk[id] - xr, ry = mk[nm + id] - yr;
-                if (fabs(rx) < R(2) && fabs(ry) < R(2)) {
-                    R wt = peskin<R>(rx) * peskin<R>(ry);
-                    Fx += wt * mk[2 * nm + id];
-                    Fy += wt * mk[3 * nm + id];
+        for (int w0 = 0; w0 < d.mw; w0 += NEAR_CHUNK_WORDS) {
+            const int nw = min(NEAR_CHUNK_WORDS, d.mw - w0);
+            if (tid < nw) s_words[tid] = mask[(size_t)t * d.mw + w0 + tid];
+            __syncthreads();
+            if (tid < 32) {
+                int cnt_w = (tid < nw) ? __popc(s_words[tid]) : 0;
+                int incl = cnt_w;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (tid >= o) incl += v;
+                }
+                if (tid < nw) s_off[tid] = incl - cnt_w;
+                if (tid == 31) s_n = incl;
+            }
+            __syncthreads();
+            for (int b = tid; b < nw * 32; b += TX * TY) {
+                const int l = b >> 5, bit = b & 31;
+                const uint32_t wd = s_words[l];
+                if ((wd >> bit) & 1u) {
+                    const int pos = s_off[l] + __popc(wd & ((1u << bit) - 1u));
+                    const int id = (w0 + l) * 32 + bit;
+                    s_ix[pos] = mki[id];
+                    s_iy[pos] = mki[nm + id];
+                    s_fx[pos] = mkf[id];
+                    s_fy[pos] = mkf[nm + id];
+                    s_Fx[pos] = mkf[2 * nm + id];
+                    s_Fy[pos] = mkf[3 * nm + id];
                 }
             }
+            __syncthreads();
+            const int n = s_n;
+            for (int q = 0; q < n; ++q) {
+                // X - x = (floor(X) - x) + frac, exact small integer plus fraction
+                R rx = R(s_ix[q] - x) + s_fx[q];
+                R ry = R(s_iy[q] - y) + s_fy[q];
+                if (fabs(rx) < R(2) && fabs(ry) < R(2)) {
+                    R wt = peskin<R>(rx) * peskin<R>(ry);
+                    Fx += wt * s_Fx[q];
+                    Fy += wt * s_Fy[q];
+                }
+            }
+            __syncthreads();
         }
-        if (x < L.nx && y < L.ny) {
-            R g[9];
-            pull<S, R>(L, fin, x, y, g);
+        if (live) {
             R drho, ux, uy;
             collide<R>(g, Fx, Fy, R(L.omega), drho, ux, uy);
             if (!(drho > R(-1)) || !isfinite(ux + uy)) atomicOr(d.status, ST_DIVERGED);
@@ -181,7 +220,6 @@ __global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
             ux_o[base] = ux;
             uy_o[base] = uy;
         }
-        __syncthreads();  // every thread has read the tile's mask words
         for (int w = tid; w < d.mw; w += TX * TY) mask[(size_t)t * d.mw + w] = 0u;
         if (tid == 0) {
             d.nearflag[p][t] = 0u;
@@ -272,19 +310,19 @@ __global__ void k_activate(Dev d, int64_t m, int which)
     }
 }
 
-// Sets the spreading bit masks of the markers in mk[parity] (after a restore).
+// Sets the spreading bit masks of the markers of `parity` (after a restore).
 template <typename R>
 __global__ void k_rebuild_mask(Dev d, int parity)
 {
     const Lattice& L = d.L;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.nmark) return;
-    const R* mk = static_cast<const R*>(d.mk[parity]);
+    const R* mkf = static_cast<const R*>(d.mkf[parity]);
+    const int32_t* mki = d.mki[parity];
     int nm = d.nmark;
-    if (mk[2 * nm + k] == R(0) && mk[3 * nm + k] == R(0)) return;
-    double X = mk[k], Y = mk[nm + k];
-    int i0 = max(0, (int)floor(X) - 1), i1 = min(L.nx - 1, (int)floor(X) + 2);
-    int j0 = max(0, (int)floor(Y - 0.5) - 1), j1 = min(L.ny - 1, (int)floor(Y - 0.5) + 2);
+    if (mkf[2 * nm + k] == R(0) && mkf[3 * nm + k] == R(0)) return;
+    int i0 = max(0, mki[k] - 1), i1 = min(L.nx - 1, mki[k] + 2);
+    int j0 = max(0, mki[nm + k] - 1), j1 = min(L.ny - 1, mki[nm + k] + 2);
     if (i0 > i1 || j0 > j1) return;
     for (int ty = j0 / TY; ty <= j1 / TY; ++ty)
         for (int tx = i0 / TX; tx <= i1 / TX; ++tx) {

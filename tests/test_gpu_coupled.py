@@ -42,10 +42,22 @@ def test_small_capillary_first_step_every_force_fp64():
     o.step(1)
     s.advance(1)
     for bi in range(len(cap.bodies)):
-        for f in FIELDS_1STEP:
-            a, b = o.body(bi, f), s.body_field(bi, f)
-            scale = max(np.abs(a).max(), 1e-30)
-            assert np.abs(a - b).max() <= 1e-10 * scale + 1e-300, (bi, f, np.abs(a - b).max(), scale)
+        # x/y components are compared against their joint magnitude: a
+        # component that is zero in exact arithmetic carries rounding noise
+        for fx in FIELDS_1STEP:
+            if not fx.endswith("x"):
+                continue
+            fy = fx[:-1] + "y"
+            ax, ay = o.body(bi, fx), o.body(bi, fy)
+            bx, by = s.body_field(bi, fx), s.body_field(bi, fy)
+            scale = np.hypot(ax, ay).max()
+            err = max(np.abs(ax - bx).max(), np.abs(ay - by).max())
+            # floor 1e-13: rounding noise of components that vanish exactly at
+            # t = 0 (the area force is k_a p_ref l ~ 0.3 times A/A0 - 1 ~ 1e-16)
+            # and of BDF2 velocities formed from positions ~1e2 (ulp 1.4e-14)
+            assert err <= 1e-10 * scale + 1e-13, (bi, fx, err, scale)
+        a, b = o.body(bi, "mds"), s.body_field(bi, "mds")
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
         assert np.abs(o.body_xy(bi) - s.markers(bi)).max() < 1e-12
     fo = o.fpost()
     assert np.abs(s.populations() - fo).max() < 1e-14
@@ -213,6 +225,7 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(lbib.LbibError) as e:
         s.add_membrane(wl.CELL, wl.DEFORMABLE, wl.circle(20, 20, 10, 5))
     assert e.value.status == lbib.LBIB_ERR_STATE
-    with pytest.raises(lbib.LbibError):
-        s.markers(5)
+    buf = np.zeros(8)
+    assert s.lib.lbib_read_markers(s.ctx, 5, buf.ctypes.data, 8) == lbib.LBIB_ERR_INVALID_ARG
+    assert s.lib.lbib_read_markers(s.ctx, i, buf.ctypes.data, 2) == lbib.LBIB_ERR_INVALID_ARG
     s.close()
