@@ -215,8 +215,38 @@ lbib_status lbib_read_kernel_times(lbib_ctx* ctx, float* bulk_ms, float* lagr_ms
 /* Launch counts per step and geometry the bench reports. */
 lbib_status lbib_describe(lbib_ctx* ctx, int32_t* kernels_per_step, int32_t* near_tiles, int32_t* tiles);
 
+/* Advances a channel with no membranes by nsteps lattice steps without
+ * allocating any memory.  The paper has no counterpart: this entry point is
+ * for callers that cannot call cudaMalloc where they step the fluid (code
+ * under an external memory manager that owns the whole device, or on a path
+ * where an allocation would synchronise or fail).
+ *   params  lattice, fluid and boundary parameters as for lbib_create
+ *           (storage FP64 or FP32 selects the precision of the stored
+ *           deviations; membranes, seed and obs_capacity are ignored);
+ *           params->device is made current for the call and restored after;
+ *           params->cuda_stream (or the legacy default stream if NULL) carries
+ *           the work.
+ *   f       caller DEVICE buffer of 9 nx ny doubles: the post-collision
+ *           populations, absolute values, layout [9][ny][nx] as in
+ *           lbib_read_populations; read at entry, overwritten with the state
+ *           after nsteps steps.  The result equals lbib_create +
+ *           lbib_write_populations + lbib_advance(nsteps) +
+ *           lbib_read_populations on a context without membranes.
+ * Every other buffer the bulk lattice kernel needs comes from one file-scope
+ * device array of 16 MiB that each GPU loading the library holds until exit;
+ * lattices that do not fit (about 233k nodes in FP32, 116k in FP64) give
+ * LBIB_ERR_UNSUPPORTED before any work.  All calls on a device share that
+ * array and leave their contents in it; each call clears what must start at
+ * zero.  Calls whose GPU work overlaps race on it.  The first call on a device
+ * looks up the array's device address (once per device, with that device
+ * current), so make that first call before any stream capture.  The call
+ * waits for its stream and reports divergence as LBIB_ERR_DIVERGED; errors are
+ * read with lbib_last_error(NULL). */
+lbib_status lbib_lattice_advance_noalloc(const lbib_fluid_params* params, double* f, int64_t nsteps);
+
 /* Message of the last failed call on ctx (or of the last failed lbib_create
- * when ctx is NULL).  Valid until the next call on ctx. */
+ * or lbib_lattice_advance_noalloc when ctx is NULL).  Valid until the next
+ * call on ctx. */
 const char* lbib_last_error(lbib_ctx* ctx);
 
 /* Releases every resource of ctx (NULL is ignored). */

@@ -79,6 +79,8 @@ cudaError_t dalloc(std::vector<void*>& reg, T** p, size_t n)
 
 }  // namespace
 
+void lbib::set_global_error(const char* msg) { g_create_error = msg; }
+
 struct lbib_ctx {
     std::string err;
     lbib_fluid_params P{};

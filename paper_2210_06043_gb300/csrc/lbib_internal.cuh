@@ -137,6 +137,8 @@ cudaError_t launch_lagrangian(const Dev& d, int prec, int parity, cudaStream_t s
 cudaError_t launch_activate(const Dev& d, int prec, int64_t m, int which, cudaStream_t s);
 cudaError_t launch_rebuild_mask(const Dev& d, int prec, int parity, cudaStream_t s);
 size_t lagrangian_smem_bytes(int prec, int nv_max);
+// message returned by lbib_last_error(NULL) (calls that have no context)
+void set_global_error(const char* msg);
 cudaError_t configure_kernels(int prec, int nv_max);
 
 }  // namespace lbib

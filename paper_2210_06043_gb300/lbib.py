@@ -79,6 +79,7 @@ _SIGS = {
                                ctypes.POINTER(ctypes.c_float)],
     "lbib_describe": [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                       ctypes.POINTER(ctypes.c_int32)],
+    "lbib_lattice_advance_noalloc": [ctypes.POINTER(lbib_fluid_params), _P, ctypes.c_int64],
 }
 
 _lib = None
@@ -156,6 +157,13 @@ def lbib_sync(ctx) -> None:
 
 def lbib_destroy(ctx) -> None:
     load().lbib_destroy(ctx)
+
+
+def lbib_lattice_advance_noalloc(params: lbib_fluid_params, f_device_ptr: int, nsteps: int) -> None:
+    """Allocation-free lattice stepping of a membrane-free channel on a caller
+    device buffer of 9 nx ny doubles (see include/lbib.h)."""
+    _check(load().lbib_lattice_advance_noalloc(ctypes.byref(params), ctypes.c_void_p(f_device_ptr),
+                                                int(nsteps)), None)
 
 
 class Solver:
