@@ -6,11 +6,18 @@ step n (interpolation, bonds, membrane forces, integration, direct forcing)
 overlapped with the bulk lattice update of step n + 1, then the near-membrane
 lattice update of step n + 1 (one captured graph, three kernels).
 
-Workload (N = 1): the production capillary, 1200 x 150 nodes, globular cell
-(256 markers) + soft AR 0.5 particle (96 markers, 200 ligand sites), FP32
-populations, Re = 1e-2, seeded synthetic geometry.  Its 13 MB of populations
-fit in L2, so the 256 MiB flush buffer is rewritten between timed steps and
-every timed step starts cold.
+Workloads (seeded synthetic geometry, FP32 populations, Re = 1e-2, tau = 1):
+  sweep (default)  the 64-capillary parameter sweep of Sec. 3.1 (particle
+                   aspect ratio x Ca x cell shape x 2 bond seeds; channel
+                   lengths uniform in 600-1600 nodes, H = 150) stepped as one
+                   batch: 10.66 M nodes, 780 MB of populations, larger than
+                   L2, so every step streams from HBM.  Also times the plain
+                   solver (each capillary alone in its own context, warm L2)
+                   on the same 64 capillaries for simulations per hour.
+  production       one 1200 x 150 capillary, globular cell (256 markers) +
+                   soft AR 0.5 particle (96 markers, 200 ligand sites); its
+                   13 MB fit in L2, so a 256 MiB buffer is rewritten between
+                   timed steps and every timed step starts cold.
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle on the same
 workload instead (the only other place this script runs the oracle).
@@ -41,15 +48,28 @@ def _dist():
     return ws, rank, local
 
 
-def _workload():
+STEPS_PER_SIM = 200000  # one capillary simulation: 2e5 time steps (the production horizon)
+PRODUCTION = ("capillary 1200x150 nodes, globular cell 256 markers + soft AR0.5 ellipse 96 markers "
+              "(200 ligand sites), Re 1e-2, tau 1, fp32 populations")
+SWEEP = ("sweep of 64 capillaries in one batch: particle AR {0.25,0.5,0.75,1} x Ca {0 (rigid),1e-4,5e-4,1e-3} x "
+         "cell {globular,biconcave} x bond seeds {0,1}; channel lengths U[600,1600] (seed 0) x 150 nodes; "
+         "256-marker cells, 96-marker particles with 200 ligand sites; Re 1e-2, tau 1, fp32 populations")
+
+
+def _workload(name, instances=64):
+    """List of capillaries and the config block naming them."""
     from paper_2210_06043_gb300 import workloads as wl
-    cap = wl.production_capillary(seed=0)
-    cfg = {"workload": "capillary 1200x150 nodes, globular cell 256 markers + soft AR0.5 ellipse 96 markers "
-                       "(200 ligand sites), Re 1e-2, tau 1, fp32 populations",
-           "nx": cap.nx, "ny": cap.ny, "markers": cap.markers,
-           "ligand_sites": sum(b.adhesion.n_lig for b in cap.bodies if b.adhesion),
-           "parallelism": "replicas (one independent instance per GPU)"}
-    return cap, cfg
+    if name == "production":
+        caps = [wl.production_capillary(seed=0)]
+        cfg = {"workload": PRODUCTION, "nx": caps[0].nx, "ny": caps[0].ny}
+    else:
+        caps = wl.sweep_capillaries(seed=0)[:instances]
+        cfg = {"workload": SWEEP if instances == 64 else f"first {instances} capillaries of the {SWEEP}",
+               "instances": len(caps), "nx_total": sum(c.nx for c in caps), "ny": caps[0].ny}
+    cfg.update({"nodes": sum(c.nodes for c in caps), "markers": sum(c.markers for c in caps),
+                "ligand_sites": sum(b.adhesion.n_lig for c in caps for b in c.bodies if b.adhesion),
+                "parallelism": "replicas (one independent copy of the workload per GPU)"})
+    return caps, cfg
 
 
 def _peaks():
@@ -142,39 +162,82 @@ def _oracle_sim(cap):
     return s
 
 
-def cpu_baseline(cap, steps):
+def _oracle_sample(caps, nodes_budget):
+    """The capillaries the CPU oracle steps as a bounded sample of the
+    workload: every 8th capillary of a sweep (the production capillary
+    alone), and the number of steps that keeps the sample near nodes_budget
+    node updates."""
+    sample = caps[::8] if len(caps) > 1 else caps
+    nodes = sum(c.nodes for c in sample)
+    return sample, max(1, int(round(nodes_budget / nodes)))
+
+
+def cpu_baseline(caps, nodes_budget):
     """The oracle as it stands (single-threaded plain C, FP64) on a bounded
     sample of the workload."""
-    s = _oracle_sim(cap)
+    sample, steps = _oracle_sample(caps, nodes_budget)
+    sims = [_oracle_sim(c) for c in sample]
     t0 = time.perf_counter()
-    s.step(steps)
+    for s in sims:
+        s.step(steps)
     dt = time.perf_counter() - t0
-    return {"value": cap.nodes * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} steps of the same capillary from t = 0 (of {cap.steps}), FP64 plain C, one thread",
-            "seconds": dt}
+    nodes = sum(c.nodes for c in sample)
+    return {"value": nodes * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} steps from t = 0 of {len(sample)} of the {len(caps)} capillaries "
+                      f"({nodes} nodes), FP64 plain C, one thread", "seconds": dt}
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    cap, cfg = _workload()
-    s = _oracle_sim(cap)
-    s.step(args.warmup)
+    caps, cfg = _workload(args.workload, args.instances)
+    sample = caps[::32]  # every 32nd capillary of a sweep (the production capillary alone)
+    sims = [_oracle_sim(c) for c in sample]
+    nodes = sum(c.nodes for c in sample)
+    for s in sims:
+        s.step(args.warmup)
     t0 = time.perf_counter()
-    s.step(args.steps)
+    for s in sims:
+        s.step(args.steps)
     dt = time.perf_counter() - t0
-    v = cap.nodes * args.steps / dt / 1e6
+    v = nodes * args.steps / dt / 1e6
+    what = (f"{args.steps} timed steps after {args.warmup} warm-up steps of {len(sample)} of the {len(caps)} "
+            f"capillaries ({nodes} nodes), FP64 plain C oracle, one thread")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} timed steps after {args.warmup} warm-up steps, FP64 "
-                                       f"plain C oracle, one thread"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": what},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if len(caps) > 1:
+        line["sims_per_hour"] = 3600.0 / (STEPS_PER_SIM * dt / args.steps * sum(c.nodes for c in caps) / nodes) \
+            * len(caps)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def plain_solver(caps, local, steps, warmup):
+    """Each capillary alone in its own context (the one-instance solver), timed
+    with CUDA events on its stream over `steps` steps after `warmup`, warm L2;
+    returns the device seconds per step of every capillary."""
+    import torch
+
+    from paper_2210_06043_gb300 import lbib
+    out = []
+    for c in caps:
+        st = torch.cuda.Stream()
+        s = lbib.from_capillary(c, device=local, stream=st.cuda_stream)
+        s.advance(warmup)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st.synchronize()
+        a.record(st)
+        s.advance(steps)
+        b.record(st)
+        b.synchronize()
+        out.append(a.elapsed_time(b) / 1e3 / steps)
+        s.close()
+    return out
 
 
 def run_gpu(args):
@@ -188,15 +251,21 @@ def run_gpu(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    cap, cfg = _workload()
-    nodes = cap.nodes
+    caps, cfg = _workload(args.workload, args.instances)
+    batch = len(caps) > 1 or args.workload == "sweep"
+    nodes = cfg["nodes"]
     stream = torch.cuda.Stream()  # non-null handle: the library enqueues on it, the events bracket it
     torch.cuda.set_stream(stream)
-    s = lbib.from_capillary(cap, device=local, stream=stream.cuda_stream)
+    make = (lambda **kw: lbib.from_capillaries(caps, **kw)) if batch else \
+        (lambda **kw: lbib.from_capillary(caps[0], **kw))
+    s = make(device=local, stream=stream.cuda_stream)
     s.set_profiling(True)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    # populations beyond L2 (sweep): no flush; else a 256 MiB buffer rewritten between steps
+    pop_bytes = 2 * 9 * 4 * nodes
+    flush = None if pop_bytes > (256 << 20) else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(max(args.warmup, 3)):
-        flush.fill_(1)
+        if flush is not None:
+            flush.fill_(1)
         s.advance(1)
     torch.cuda.synchronize()
     desc = s.describe()
@@ -212,7 +281,8 @@ def run_gpu(args):
     time.sleep(0.25)
     t0 = time.perf_counter()
     for k in range(K):
-        flush.fill_(k & 0xFF)
+        if flush is not None:
+            flush.fill_(k & 0xFF)
         starts[k].record(stream)
         s.advance(1)
         ends[k].record(stream)
@@ -239,50 +309,64 @@ def run_gpu(args):
     traffic = _traffic("k_bulk<float,float>", cfg["workload"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "kernel": "k_bulk<float,float> (bulk lattice update)",
-                "algorithmic_bytes_per_launch": bulk_nodes * bpn, "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs)"}
+                "algorithmic_bytes_per_launch": bulk_nodes * bpn,
+                "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs, burst copy)"}
     s.close()
 
     # end to end through the C ABI with host buffers: create from host meshes,
-    # then per step advance + read that step's observables record to the host,
-    # finally the velocity field to the host
-    if True:
-        K2 = K
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        s2 = lbib.from_capillary(cap, device=local)
-        for _ in range(K2):
-            s2.advance(1)
-            obs = s2.observables(cap=4)
-        ux, uy = s2.velocity()
-        s2.close()
-        e2e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        h2d = sum(b.xy.nbytes for b in cap.bodies)
-        d2h_rec = 48
-        e2e = {"value": ws * nodes * K2 / e2e_s / 1e6, "unit": UNIT,
-               "h2d_bytes_per_step": h2d / K2, "d2h_bytes_per_step": d2h_rec + (ux.nbytes + uy.nbytes) / K2,
-               "what": "lbib_create + add_membrane (host meshes) + per step lbib_advance(1) and "
-                       "lbib_read_observables to host + final lbib_read_velocity to host + destroy",
-               "records_read_last_step": len(obs)}
+    # then per step advance + read that step's observables of every instance to
+    # the host, finally the velocity field of instance 0 to the host
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s2 = make(device=local)
+    for _ in range(K):
+        s2.advance(1)
+        obs = s2.latest_observables()
+    ux, uy = s2.velocity()
+    s2.close()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = sum(b.xy.nbytes for c in caps for b in c.bodies)
+    d2h_rec = 48 * len(caps)
+    e2e = {"value": ws * nodes * K / e2e_s / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h_rec + (ux.nbytes + uy.nbytes) / K,
+           "what": "create + add membranes from host meshes, then per step lbib_advance(1) and "
+                   "lbib_read_latest_observables (every instance) to host, final velocity of instance 0 "
+                   "to host, destroy", "records_last_step": len(obs)}
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
+    markers = cfg["markers"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
             "ms_per_step": dev_s * 1e3 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": dict(cfg, l2="256 MiB buffer rewritten between timed steps (cold L2 each step)"),
-            "marker_updates_per_s": ws * cap.markers * K / dev_s,
+            "config": dict(cfg, l2=("populations (780 MB) larger than L2: no flush" if flush is None else
+                                    "256 MiB buffer rewritten between timed steps (cold L2 each step)")),
+            "marker_updates_per_s": ws * markers * K / dev_s,
             "kernel_ms": {"bulk_lattice": bulk_ms, "lagrangian": lag_ms, "near_lattice": near_ms},
             "near_tiles": desc["near_tiles"], "tiles": desc["tiles"],
             "roofline": roofline, "e2e": e2e, "gpu_launches": 3 * K, "clocks": clk,
             "wall_s_timed_region": wall}
+    if batch:
+        t_plain = plain_solver(caps, local, args.plain_steps, 3)
+        t_batch = dev_s / K
+        line["sweep"] = {
+            "steps_per_sim": STEPS_PER_SIM,
+            "sims_per_hour": ws * len(caps) * 3600.0 / (STEPS_PER_SIM * t_batch),
+            "plain_solver_sims_per_hour": ws * len(caps) * 3600.0 / (STEPS_PER_SIM * sum(t_plain)),
+            "speedup_vs_plain_solver": sum(t_plain) / t_batch,
+            "plain_solver_ms_per_step": {"mean": 1e3 * statistics.mean(t_plain), "min": 1e3 * min(t_plain),
+                                         "max": 1e3 * max(t_plain)},
+            "plain_solver": f"each capillary alone in its own context (same kernels), {args.plain_steps} steps "
+                            f"after 3 warm-up steps, warm L2, CUDA events",
+            "accuracy": "every instance bit-identical to its lone run (tests/test_gpu_batch.py)"}
     if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cap, args.cpu_steps)
+        line["cpu_baseline"] = cpu_baseline(caps, args.cpu_nodes)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -292,10 +376,14 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="lbib", choices=["lbib", "reference"])
-    ap.add_argument("--cpu-steps", type=int, default=400)
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "production"])
+    ap.add_argument("--instances", type=int, default=64, help="first N capillaries of the sweep")
+    ap.add_argument("--plain-steps", type=int, default=50, help="steps per capillary of the plain-solver timing")
+    ap.add_argument("--cpu-nodes", type=float, default=1.0e8,
+                    help="node updates of the CPU oracle sample (about 15 s at 7 MLUPS)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

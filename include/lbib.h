@@ -145,8 +145,52 @@ typedef enum {
  * (INLET_OUTLET) or at rest (PERIODIC_FORCE).  *out receives the handle. */
 lbib_status lbib_create(const lbib_fluid_params* params, lbib_ctx** out);
 
-/* Adds a membrane before the first lbib_advance; *id_out its index (may be NULL). */
+/* Adds a membrane to instance 0 (the only instance of a context made by
+ * lbib_create) before the first lbib_advance; *id_out its index (may be NULL). */
 lbib_status lbib_add_membrane(lbib_ctx* ctx, const lbib_membrane_desc* desc, int32_t* id_out);
+
+/* ---- Batches of capillaries (parameter sweeps; the paper runs one capillary
+ * per simulation, Sec. 3.1 varies particle shape, Ca and cell shape across
+ * runs).  One context steps n_instances independent capillaries with the same
+ * ny and fluid parameters (params->nx and params->seed are ignored):
+ *   nx      host array of n_instances channel lengths (each >= 3), copied;
+ *   seeds   host array of n_instances Philox keys for the bond kinetics of
+ *           each instance, or NULL for params->seed + i.
+ * Instance i is laid out at its own node columns of one lattice; bodies added
+ * to it, its ligand sites (numbered from 0 within the instance for the random
+ * stream) and its observables are its own, and its positions are in its own
+ * coordinates (0 <= x < nx[i]).  Each instance gives bit-for-bit the results
+ * of a context holding that capillary alone.  Per-instance calls take the
+ * instance index; the calls without one act on instance 0.  Body ids are
+ * numbered over the whole context in order of addition.  At most 16 bodies
+ * per instance; nx summed over instances (each rounded up to 32) times ny
+ * times 9 must stay below 2^31. */
+lbib_status lbib_create_batch(const lbib_fluid_params* params, int32_t n_instances, const int32_t* nx,
+                              const uint64_t* seeds, lbib_ctx** out);
+
+/* Adds a membrane to `instance` (coordinates of that instance). */
+lbib_status lbib_add_membrane_to(lbib_ctx* ctx, int32_t instance, const lbib_membrane_desc* desc, int32_t* id_out);
+
+/* Velocity of one instance, host arrays of n >= nx[instance] ny doubles, [ny][nx]. */
+lbib_status lbib_read_instance_velocity(lbib_ctx* ctx, int32_t instance, double* ux, double* uy, size_t n);
+
+/* Post-collision populations of one instance (absolute), n >= 9 nx ny, [9][ny][nx]. */
+lbib_status lbib_read_instance_populations(lbib_ctx* ctx, int32_t instance, double* f, size_t n);
+
+/* Overwrites one instance's populations; only before the first lbib_advance. */
+lbib_status lbib_write_instance_populations(lbib_ctx* ctx, int32_t instance, const double* f, size_t n);
+
+/* Observables records of one instance, as lbib_read_observables (each
+ * instance keeps its own ring of obs_capacity records and its own cursor;
+ * an instance without membranes has none). */
+lbib_status lbib_read_instance_observables(lbib_ctx* ctx, int32_t instance, lbib_obs* out, size_t cap,
+                                           size_t* n_out);
+
+/* The record of the last completed step of every instance in one copy:
+ * out[i] for instance i, host array of n >= n_instances records; an instance
+ * without membranes gets step = -1.  The per-instance cursors of
+ * lbib_read_instance_observables do not move. */
+lbib_status lbib_read_latest_observables(lbib_ctx* ctx, lbib_obs* out, size_t n);
 
 /* Decorates body `body` with ligands (before the first lbib_advance).  Sites
  * within y_cr of a wall start bound. */

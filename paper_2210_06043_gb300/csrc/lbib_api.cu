@@ -10,6 +10,12 @@
 // is one captured graph per parity of m.  A context keeps the last Lagrangian
 // step pending after lbib_advance (so back-to-back calls overlap it with the
 // next lattice step); every call that reads Lagrangian state completes it.
+//
+// A context holds a batch of one or more capillary instances side by side in
+// one lattice (instance i at node columns [x0_i, x0_i + nx_i), x0_i a multiple
+// of the tile width), stepped by the same three launches.  Membranes, bonds and
+// observables are per instance and in the instance's own coordinates; the
+// bodies are stored grouped by instance.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,6 +33,7 @@ using namespace lbib;
 namespace {
 
 struct HostBody {
+    int inst = 0;  // capillary instance the body lives in
     int kind = 0, motion = 0, nv = 0;
     std::vector<double> xy, xy_ref;
     double ca = 0, beta = 0, ka = 0, dens = 1;
@@ -97,10 +104,19 @@ struct lbib_ctx {
     cudaEvent_t pe[6] = {};
     bool profiling = false, profiled_last = false;
     int near_grid = 1;
-    int64_t obs_consumed = 0;
     std::vector<void*> allocs;
     double* macro_buf = nullptr;
     int device = 0;
+    // batch of instances
+    int ninst = 1;
+    std::vector<int> inst_x0, inst_nx;
+    std::vector<uint64_t> inst_seed;
+    std::vector<int64_t> obs_consumed;     // [ninst] last observables step handed out
+    std::vector<int> inst_nbodies;         // [ninst]
+    std::vector<int> slot;                 // body id -> stored index (grouped by instance)
+    std::vector<int> mark_off, lig_off;    // body id -> first marker / first ligand site
+    int4* colinfo = nullptr;
+    InstConst* inst = nullptr;
 };
 
 namespace {
@@ -150,6 +166,8 @@ lbib_status check_status(lbib_ctx* ctx)
         return fail(ctx, LBIB_ERR_STATE, "a spreading stencil left the tiles scheduled as near-membrane");
     return LBIB_OK;
 }
+
+bool valid_instance(const lbib_ctx* ctx, int32_t i) { return i >= 0 && i < ctx->ninst; }
 
 lbib_status finish_pending(lbib_ctx* ctx)
 {
@@ -240,37 +258,77 @@ lbib_status finalize(lbib_ctx* ctx)
     Dev& d = ctx->d;
     const Lattice& L = d.L;
     const int nb = (int)ctx->bodies.size();
+    const int ni = ctx->ninst;
     d.nbodies = nb;
+    // stored order: grouped by instance, in order of addition within one
+    std::vector<int> order(nb);
+    for (int b = 0; b < nb; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return ctx->bodies[a].inst < ctx->bodies[b].inst; });
+    ctx->slot.assign(nb, 0);
+    ctx->mark_off.assign(nb, 0);
+    ctx->lig_off.assign(nb, 0);
+    for (int k = 0; k < nb; ++k) ctx->slot[order[k]] = k;
     std::vector<BodyConst> bc(nb);
-    int nmark = 0, nlig = 0, nv_max = 0;
-    for (int b = 0; b < nb; ++b) {
-        nmark += ctx->bodies[b].nv;
-        nv_max = std::max(nv_max, ctx->bodies[b].nv);
-        if (ctx->bodies[b].adhesive) nlig += ctx->bodies[b].adh.n_ligands;
+    std::vector<InstConst> ic(ni);
+    int nmark = 0, nlig = 0, nv_max = 0, mw = 1;
+    for (int i = 0; i < ni; ++i) {
+        InstConst& I = ic[i];
+        std::memset(&I, 0, sizeof(I));
+        I.x0 = ctx->inst_x0[i];
+        I.nx = ctx->inst_nx[i];
+        I.seed = ctx->inst_seed[i];
+        I.first_cell = I.first_particle = -1;
+        I.moff = nmark;
+        I.lig0 = nlig;
+        I.body0 = 0;
+        for (int k = 0; k < nb; ++k)
+            if (ctx->bodies[order[k]].inst < i) I.body0 = k + 1;
+        for (int k = I.body0; k < nb && ctx->bodies[order[k]].inst == i; ++k) {
+            const HostBody& h = ctx->bodies[order[k]];
+            I.nbodies += 1;
+            I.nmark += h.nv;
+            if (h.adhesive) I.nlig += h.adh.n_ligands;
+            if (h.kind == LBIB_CELL && I.first_cell < 0) I.first_cell = k;
+            if (h.kind == LBIB_PARTICLE && I.first_particle < 0) I.first_particle = k;
+            nv_max = std::max(nv_max, h.nv);
+        }
+        nmark += I.nmark;
+        nlig += I.nlig;
+        mw = std::max(mw, (I.nmark + 31) / 32);
     }
     d.nmark = nmark;
     d.nlig = nlig;
     d.nv_max = std::max(nv_max, 1);
-    d.mw = std::max(1, (nmark + 31) / 32);
+    d.mw = mw;
+    ctx->inst_nbodies.assign(ni, 0);
+    for (int i = 0; i < ni; ++i) ctx->inst_nbodies[i] = ic[i].nbodies;
     std::vector<double> pos(2 * (size_t)std::max(nmark, 1)), rref(2 * (size_t)std::max(nmark, 1));
     std::vector<double> l0(std::max(nmark, 1)), th0(std::max(nmark, 1));
     std::vector<double> rig((size_t)std::max(nb, 1) * RG_N, 0.0), bobs((size_t)std::max(nb, 1) * BO_N, 0.0);
     std::vector<int32_t> lig_el(std::max(nlig, 1)), bound(std::max(nlig, 1), 0), site_off(nmark + 1, 0);
     std::vector<double> lig_t(std::max(nlig, 1)), anchor(2 * (size_t)std::max(nlig, 1), 0.0);
     const double nu = L.nu, umax = L.umax;
-    double lmax = 0.0;
+    std::vector<double> inst_lmax(ni, 0.0);
     int off = 0, loff = 0;
-    d.first_cell = d.first_particle = -1;
     for (int b = 0; b < nb; ++b) {
-        const HostBody& h = ctx->bodies[b];
+        const HostBody& h = ctx->bodies[order[b]];
+        const InstConst& I = ic[h.inst];
         BodyConst& B = bc[b];
         std::memset(&B, 0, sizeof(B));
         B.kind = h.kind;
         B.motion = h.motion;
         B.nv = h.nv;
         B.off = off;
-        if (h.kind == LBIB_CELL && d.first_cell < 0) d.first_cell = b;
-        if (h.kind == LBIB_PARTICLE && d.first_particle < 0) d.first_particle = b;
+        B.inst = h.inst;
+        B.x0 = I.x0;
+        B.nxi = I.nx;
+        B.moff = I.moff;
+        B.lig0 = I.lig0;
+        B.b0 = I.body0;
+        B.nbi = I.nbodies;
+        ctx->mark_off[order[b]] = off;
+        ctx->lig_off[order[b]] = loff;
         const std::vector<double>& ref = h.xy_ref.empty() ? h.xy : h.xy_ref;
         const int nv = h.nv;
         // stress-free lengths and turning angles
@@ -281,7 +339,7 @@ lbib_status finalize(lbib_ctx* ctx)
             double ax = ref[2 * l] - ref[2 * lm], ay = ref[2 * l + 1] - ref[2 * lm + 1];
             th0[off + l] = std::atan2(ax * dy - ay * dx, ax * dx + ay * dy);
             double cx = h.xy[2 * w] - h.xy[2 * l], cy = h.xy[2 * w + 1] - h.xy[2 * l + 1];
-            lmax = std::max(lmax, std::sqrt(cx * cx + cy * cy));
+            inst_lmax[h.inst] = std::max(inst_lmax[h.inst], std::sqrt(cx * cx + cy * cy));
         }
         Poly pr = polygon(ref), pc = polygon(h.xy);
         B.A0 = pr.A;
@@ -360,10 +418,15 @@ lbib_status finalize(lbib_ctx* ctx)
         off += nv;
     }
     for (int e = 0; e < nmark; ++e) site_off[e + 1] += site_off[e];
-    d.r_act = 2.0 + std::max(1.2, 0.75 * lmax) + 1.0;
-    // a centroid lies within ACT_STRIDE / 2 elements of an activating one; 1.5 l_max
-    // per element allows 50% stretching
-    d.r_act_sub = d.r_act + 0.5 * ACT_STRIDE * 1.5 * lmax;
+    // activation radii from the longest element of the body's instance (a
+    // marker moves < 1 dx per step; stencil half-width 2; element growth)
+    for (int b = 0; b < nb; ++b) {
+        const double lmax = inst_lmax[bc[b].inst];
+        bc[b].r_act = 2.0 + std::max(1.2, 0.75 * lmax) + 1.0;
+        // a centroid lies within ACT_STRIDE / 2 elements of an activating one; 1.5 l_max
+        // per element allows 50% stretching
+        bc[b].r_act_sub = bc[b].r_act + 0.5 * ACT_STRIDE * 1.5 * lmax;
+    }
     d.ring_cap = ctx->P.obs_capacity > 0 ? ctx->P.obs_capacity : 4096;
 
     // device arrays
@@ -392,7 +455,7 @@ lbib_status finalize(lbib_ctx* ctx)
     CK(dalloc(reg, reinterpret_cast<char**>(&d.diag), (size_t)NDIAG * nm1 * rs));
     CK(dalloc(reg, &d.body_obs[0], (size_t)std::max(nb, 1) * BO_N));
     CK(dalloc(reg, &d.body_obs[1], (size_t)std::max(nb, 1) * BO_N));
-    CK(dalloc(reg, &d.ring, (size_t)d.ring_cap));
+    CK(dalloc(reg, &d.ring, (size_t)ni * d.ring_cap));
     for (int k = 0; k < 2; ++k) {
         CK(dalloc(reg, &d.mki[k], 2 * nm1));
         CK(dalloc(reg, reinterpret_cast<char**>(&d.mkf[k]), 4 * nm1 * rs));
@@ -419,6 +482,7 @@ lbib_status finalize(lbib_ctx* ctx)
         if (st != LBIB_OK) return st;
     }
     if (nb) CK(cudaMemcpy(dbody, bc.data(), bc.size() * sizeof(BodyConst), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->inst, ic.data(), ic.size() * sizeof(InstConst), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d.rigid, rig.data(), rig.size() * 8, cudaMemcpyHostToDevice));
     CK(up_real(dl0, l0));
     CK(up_real(dth0, th0));
@@ -432,7 +496,7 @@ lbib_status finalize(lbib_ctx* ctx)
     CK(cudaMemset(d.diag, 0, (size_t)NDIAG * nm1 * rs));
     CK(cudaMemcpy(d.body_obs[0], bobs.data(), bobs.size() * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d.body_obs[1], bobs.data(), bobs.size() * 8, cudaMemcpyHostToDevice));
-    CK(cudaMemset(d.ring, 0, (size_t)d.ring_cap * sizeof(lbib_obs)));
+    CK(cudaMemset(d.ring, 0, (size_t)ni * d.ring_cap * sizeof(lbib_obs)));
     for (int k = 0; k < 2; ++k) {
         CK(cudaMemset(d.mki[k], 0, 2 * nm1 * 4));
         CK(cudaMemset(d.mkf[k], 0, 4 * nm1 * rs));
@@ -473,12 +537,20 @@ extern "C" {
 
 const char* lbib_last_error(lbib_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
-lbib_status lbib_create(const lbib_fluid_params* P, lbib_ctx** out)
+}  // extern "C"
+
+namespace {
+
+lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t* nxs, const uint64_t* seeds,
+                        lbib_ctx** out)
 {
     lbib_ctx* ctx = nullptr;
-    if (!P || !out) return fail(nullptr, LBIB_ERR_INVALID_ARG, "null argument");
+    if (!P || !out || !nxs) return fail(nullptr, LBIB_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
-    if (P->nx < 3 || P->ny < 2) return fail(nullptr, LBIB_ERR_INVALID_ARG, "need nx >= 3 and ny >= 2");
+    if (ninst < 1) return fail(nullptr, LBIB_ERR_INVALID_ARG, "need at least one instance");
+    for (int i = 0; i < ninst; ++i)
+        if (nxs[i] < 3) return fail(nullptr, LBIB_ERR_INVALID_ARG, "need nx >= 3 for every instance");
+    if (P->ny < 2) return fail(nullptr, LBIB_ERR_INVALID_ARG, "need nx >= 3 and ny >= 2");
     if (!(P->tau > 0.5)) return fail(nullptr, LBIB_ERR_INVALID_ARG, "tau must exceed 1/2");
     if (!(P->re >= 0.0) || !(P->rho_out > 0.0)) return fail(nullptr, LBIB_ERR_INVALID_ARG, "re >= 0 and rho_out > 0");
     if (P->bc_mode != LBIB_BC_INLET_OUTLET && P->bc_mode != LBIB_BC_PERIODIC_FORCE)
@@ -488,6 +560,11 @@ lbib_status lbib_create(const lbib_fluid_params* P, lbib_ctx** out)
     if (P->storage != LBIB_STORE_FP64 && P->storage != LBIB_STORE_FP32)
         return fail(nullptr, LBIB_ERR_INVALID_ARG, "unknown storage");
     if (P->obs_capacity < 0) return fail(nullptr, LBIB_ERR_INVALID_ARG, "obs_capacity < 0");
+    // instances side by side, each starting on a tile column
+    long long ntx = 0;
+    for (int i = 0; i < ninst; ++i) ntx += (nxs[i] + TX - 1) / TX;
+    long long qs = ntx * TX * (long long)P->ny;
+    if (qs * 9 >= (1LL << 31)) return fail(nullptr, LBIB_ERR_UNSUPPORTED, "lattice too large for 32-bit indexing");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || P->device < 0 || P->device >= ndev) {
         cudaGetLastError();
@@ -500,19 +577,26 @@ lbib_status lbib_create(const lbib_fluid_params* P, lbib_ctx** out)
     DeviceGuard guard(ctx->device);
     ctx->prec = (P->storage == LBIB_STORE_FP64) ? PREC_F64 : PREC_F32;
     ctx->rsz = (ctx->prec == PREC_F64) ? 8 : 4;
+    ctx->ninst = ninst;
+    std::vector<int4> cols;
+    for (int i = 0, x0 = 0; i < ninst; ++i) {
+        ctx->inst_x0.push_back(x0);
+        ctx->inst_nx.push_back(nxs[i]);
+        ctx->inst_seed.push_back(seeds ? seeds[i] : P->seed + (uint64_t)i);
+        const int w = (nxs[i] + TX - 1) / TX;
+        for (int c = 0; c < w; ++c) cols.push_back(make_int4(x0, nxs[i], 0, i));
+        x0 += w * TX;
+    }
+    ctx->obs_consumed.assign(ninst, 0);
+    ctx->inst_nbodies.assign(ninst, 0);
     Lattice& L = ctx->d.L;
-    L.nx = P->nx;
+    L.nx = ctx->inst_x0.back() + nxs[ninst - 1];
     L.ny = P->ny;
-    L.ntx = (P->nx + TX - 1) / TX;
+    L.ntx = (int)ntx;
     L.nty = (P->ny + TY - 1) / TY;
     L.nxp = L.ntx * TX;
     L.ntiles = L.ntx * L.nty;
     L.bc = P->bc_mode;
-    long long qs = (long long)L.nxp * L.ny;
-    if (qs * 9 >= (1LL << 31)) {
-        delete ctx;
-        return fail(nullptr, LBIB_ERR_UNSUPPORTED, "lattice too large for 32-bit indexing");
-    }
     L.qstride = (int)qs;
     L.tau = P->tau;
     L.omega = 1.0 / P->tau;
@@ -526,8 +610,8 @@ lbib_status lbib_create(const lbib_fluid_params* P, lbib_ctx** out)
     d.dcut = 2.0;
     d.probe = 1.2;
     d.uscale = L.umax / P->ny;
-    d.seed = P->seed;
     d.ring_cap = 1;
+    d.ninst = ninst;
     auto bail = [&](lbib_status s) {
         std::string m = ctx->err;
         lbib_destroy(ctx);
@@ -554,6 +638,13 @@ lbib_status lbib_create(const lbib_fluid_params* P, lbib_ctx** out)
     CKC(dalloc(reg, &d.step, 1));
     CKC(dalloc(reg, &d.status, 1));
     CKC(dalloc(reg, &d.ticket, 1));
+    CKC(dalloc(reg, &d.inst_ticket, (size_t)ninst));
+    CKC(dalloc(reg, &ctx->colinfo, cols.size()));
+    CKC(dalloc(reg, &ctx->inst, (size_t)ninst));
+    d.colinfo = ctx->colinfo;
+    d.inst = ctx->inst;
+    CKC(cudaMemcpy(ctx->colinfo, cols.data(), cols.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CKC(cudaMemset(d.f[0], 0, nq * ctx->rsz));
     CKC(cudaMemset(d.f[1], 0, nq * ctx->rsz));
     CKC(cudaMemset(d.drho, 0, nn * ctx->rsz));
     CKC(cudaMemset(d.ux, 0, nn * ctx->rsz));
@@ -565,6 +656,7 @@ lbib_status lbib_create(const lbib_fluid_params* P, lbib_ctx** out)
     CKC(cudaMemset(d.step, 0, 8));
     CKC(cudaMemset(d.status, 0, 4));
     CKC(cudaMemset(d.ticket, 0, 4));
+    CKC(cudaMemset(d.inst_ticket, 0, (size_t)ninst * 4));
     if (P->cuda_stream) {
         ctx->stream = static_cast<cudaStream_t>(P->cuda_stream);
     } else {
@@ -583,11 +675,30 @@ lbib_status lbib_create(const lbib_fluid_params* P, lbib_ctx** out)
     return LBIB_OK;
 }
 
-lbib_status lbib_add_membrane(lbib_ctx* ctx, const lbib_membrane_desc* m, int32_t* id_out)
+}  // namespace
+
+extern "C" {
+
+lbib_status lbib_create(const lbib_fluid_params* P, lbib_ctx** out)
+{
+    if (!P || !out) return fail(nullptr, LBIB_ERR_INVALID_ARG, "null argument");
+    const uint64_t seed = P->seed;
+    return create_impl(P, 1, &P->nx, &seed, out);
+}
+
+lbib_status lbib_create_batch(const lbib_fluid_params* P, int32_t n_instances, const int32_t* nx,
+                              const uint64_t* seeds, lbib_ctx** out)
+{
+    return create_impl(P, n_instances, nx, seeds, out);
+}
+
+lbib_status lbib_add_membrane_to(lbib_ctx* ctx, int32_t instance, const lbib_membrane_desc* m, int32_t* id_out)
 {
     if (!ctx || !m) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    if (!valid_instance(ctx, instance)) return fail(ctx, LBIB_ERR_INVALID_ARG, "no such instance");
     if (ctx->finalized) return fail(ctx, LBIB_ERR_STATE, "membranes must be added before the first advance");
-    if ((int)ctx->bodies.size() >= MAX_BODIES) return fail(ctx, LBIB_ERR_UNSUPPORTED, "too many bodies");
+    if (ctx->inst_nbodies[instance] >= MAX_BODIES)
+        return fail(ctx, LBIB_ERR_UNSUPPORTED, "too many bodies in one instance");
     if (m->nv < 3 || m->nv > MAX_NV || !m->xy) return fail(ctx, LBIB_ERR_INVALID_ARG, "need 3 <= nv <= 1024 and xy");
     if (m->kind != LBIB_CELL && m->kind != LBIB_PARTICLE) return fail(ctx, LBIB_ERR_INVALID_ARG, "unknown kind");
     if (m->motion < LBIB_DEFORMABLE || m->motion > LBIB_FIXED) return fail(ctx, LBIB_ERR_INVALID_ARG, "unknown motion");
@@ -595,6 +706,7 @@ lbib_status lbib_add_membrane(lbib_ctx* ctx, const lbib_membrane_desc* m, int32_
         return fail(ctx, LBIB_ERR_INVALID_ARG, "a deformable membrane needs Ca > 0");
     if (!(m->density_ratio > 0.0)) return fail(ctx, LBIB_ERR_INVALID_ARG, "density_ratio must be > 0");
     HostBody h;
+    h.inst = instance;
     h.kind = m->kind;
     h.motion = m->motion;
     h.nv = m->nv;
@@ -609,8 +721,14 @@ lbib_status lbib_add_membrane(lbib_ctx* ctx, const lbib_membrane_desc* m, int32_
     h.ka = m->ka;
     h.dens = m->density_ratio;
     ctx->bodies.push_back(h);
+    ctx->inst_nbodies[instance] += 1;
     if (id_out) *id_out = (int32_t)ctx->bodies.size() - 1;
     return LBIB_OK;
+}
+
+lbib_status lbib_add_membrane(lbib_ctx* ctx, const lbib_membrane_desc* m, int32_t* id_out)
+{
+    return lbib_add_membrane_to(ctx, 0, m, id_out);
 }
 
 lbib_status lbib_set_adhesion(lbib_ctx* ctx, int32_t body, const lbib_adhesion_params* a)
@@ -680,35 +798,45 @@ lbib_status lbib_step_count(lbib_ctx* ctx, int64_t* steps)
     return s;
 }
 
-static lbib_status read_macro(lbib_ctx* ctx, double* rho, double* ux, double* uy, size_t n)
+static lbib_status read_macro(lbib_ctx* ctx, int32_t inst, double* rho, double* ux, double* uy, size_t n)
 {
+    if (!valid_instance(ctx, inst)) return fail(ctx, LBIB_ERR_INVALID_ARG, "no such instance");
     const Lattice& L = ctx->d.L;
-    size_t nn = (size_t)L.nx * L.ny;
+    const int inx = ctx->inst_nx[inst];
+    size_t nn = (size_t)inx * L.ny;
     if (n < nn) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than nx * ny");
     DeviceGuard guard(ctx->device);
     lbib_status s = pre_read(ctx);
     if (s != LBIB_OK) return s;
-    if (!ctx->macro_buf) CK(dalloc(ctx->allocs, &ctx->macro_buf, 3 * nn));
+    int max_nx = 0;
+    for (int v : ctx->inst_nx) max_nx = std::max(max_nx, v);
+    const size_t cap = (size_t)max_nx * L.ny;
+    if (!ctx->macro_buf) CK(dalloc(ctx->allocs, &ctx->macro_buf, 3 * cap));
     int64_t m = ctx->s_f - 1;
-    CK(launch_macro(ctx->d, ctx->prec, (int)(ctx->s_f & 1), m, ctx->macro_buf, ctx->macro_buf + nn,
-                    ctx->macro_buf + 2 * nn, ctx->stream));
+    CK(launch_macro(ctx->d, ctx->prec, (int)(ctx->s_f & 1), m, ctx->inst_x0[inst], inx, ctx->macro_buf,
+                    ctx->macro_buf + cap, ctx->macro_buf + 2 * cap, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     if (rho) CK(cudaMemcpy(rho, ctx->macro_buf, nn * 8, cudaMemcpyDeviceToHost));
-    if (ux) CK(cudaMemcpy(ux, ctx->macro_buf + nn, nn * 8, cudaMemcpyDeviceToHost));
-    if (uy) CK(cudaMemcpy(uy, ctx->macro_buf + 2 * nn, nn * 8, cudaMemcpyDeviceToHost));
+    if (ux) CK(cudaMemcpy(ux, ctx->macro_buf + cap, nn * 8, cudaMemcpyDeviceToHost));
+    if (uy) CK(cudaMemcpy(uy, ctx->macro_buf + 2 * cap, nn * 8, cudaMemcpyDeviceToHost));
     return LBIB_OK;
+}
+
+lbib_status lbib_read_instance_velocity(lbib_ctx* ctx, int32_t instance, double* ux, double* uy, size_t n)
+{
+    if (!ctx || !ux || !uy) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    return read_macro(ctx, instance, nullptr, ux, uy, n);
 }
 
 lbib_status lbib_read_velocity(lbib_ctx* ctx, double* ux, double* uy, size_t n)
 {
-    if (!ctx || !ux || !uy) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
-    return read_macro(ctx, nullptr, ux, uy, n);
+    return lbib_read_instance_velocity(ctx, 0, ux, uy, n);
 }
 
 lbib_status lbib_read_density(lbib_ctx* ctx, double* rho, size_t n)
 {
     if (!ctx || !rho) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
-    return read_macro(ctx, rho, nullptr, nullptr, n);
+    return read_macro(ctx, 0, rho, nullptr, nullptr, n);
 }
 
 lbib_status lbib_read_velocity_device(lbib_ctx* ctx, void* dux, void* duy, size_t n, int32_t dtype)
@@ -716,79 +844,135 @@ lbib_status lbib_read_velocity_device(lbib_ctx* ctx, void* dux, void* duy, size_
     if (!ctx || !dux || !duy) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
     if (dtype != 0 && dtype != 1) return fail(ctx, LBIB_ERR_INVALID_ARG, "dtype must be 0 (float) or 1 (double)");
     const Lattice& L = ctx->d.L;
-    if (n < (size_t)L.nx * L.ny) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than nx * ny");
+    if (n < (size_t)ctx->inst_nx[0] * L.ny) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than nx * ny");
     DeviceGuard guard(ctx->device);
     lbib_status s = finalize(ctx);
     if (s != LBIB_OK) return s;
     s = finish_pending(ctx);
     if (s != LBIB_OK) return s;
-    CK(launch_macro_typed(ctx->d, ctx->prec, (int)(ctx->s_f & 1), ctx->s_f - 1, dux, duy, dtype, ctx->stream));
+    CK(launch_macro_typed(ctx->d, ctx->prec, (int)(ctx->s_f & 1), ctx->s_f - 1, ctx->inst_x0[0], ctx->inst_nx[0], dux,
+                          duy, dtype, ctx->stream));
     return LBIB_OK;
 }
 
 static double wrest(int q) { return q == 0 ? 4.0 / 9.0 : (q < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
 
-lbib_status lbib_read_populations(lbib_ctx* ctx, double* f, size_t n)
+lbib_status lbib_read_instance_populations(lbib_ctx* ctx, int32_t instance, double* f, size_t n)
 {
     if (!ctx || !f) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    if (!valid_instance(ctx, instance)) return fail(ctx, LBIB_ERR_INVALID_ARG, "no such instance");
     const Lattice& L = ctx->d.L;
-    size_t nn = (size_t)L.nx * L.ny;
+    const int inx = ctx->inst_nx[instance], x0 = ctx->inst_x0[instance];
+    size_t nn = (size_t)inx * L.ny;
     if (n < 9 * nn) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than 9 nx ny");
     DeviceGuard guard(ctx->device);
     lbib_status s = pre_read(ctx);
     if (s != LBIB_OK) return s;
-    size_t nq = (size_t)9 * L.qstride;
-    std::vector<char> raw(nq * ctx->rsz);
-    CK(cudaMemcpy(raw.data(), ctx->d.f[ctx->s_f & 1], raw.size(), cudaMemcpyDeviceToHost));
+    // one strided copy per direction: rows of the instance's columns
+    std::vector<char> raw((size_t)9 * nn * ctx->rsz);
+    const char* src = static_cast<const char*>(ctx->d.f[ctx->s_f & 1]);
     for (int q = 0; q < 9; ++q)
-        for (int y = 0; y < L.ny; ++y)
-            for (int x = 0; x < L.nx; ++x) {
-                size_t i = (size_t)q * L.qstride + (size_t)y * L.nxp + x;
-                double v = ctx->prec == PREC_F64 ? reinterpret_cast<double*>(raw.data())[i]
-                                                 : (double)reinterpret_cast<float*>(raw.data())[i];
-                f[((size_t)q * L.ny + y) * L.nx + x] = v + wrest(q);
-            }
+        CK(cudaMemcpy2D(raw.data() + (size_t)q * nn * ctx->rsz, (size_t)inx * ctx->rsz,
+                        src + ((size_t)q * L.qstride + x0) * ctx->rsz, (size_t)L.nxp * ctx->rsz,
+                        (size_t)inx * ctx->rsz, L.ny, cudaMemcpyDeviceToHost));
+    for (int q = 0; q < 9; ++q)
+        for (size_t i = 0; i < nn; ++i) {
+            const size_t k = (size_t)q * nn + i;
+            double v = ctx->prec == PREC_F64 ? reinterpret_cast<double*>(raw.data())[k]
+                                             : (double)reinterpret_cast<float*>(raw.data())[k];
+            f[k] = v + wrest(q);
+        }
+    return LBIB_OK;
+}
+
+lbib_status lbib_read_populations(lbib_ctx* ctx, double* f, size_t n)
+{
+    return lbib_read_instance_populations(ctx, 0, f, n);
+}
+
+lbib_status lbib_write_instance_populations(lbib_ctx* ctx, int32_t instance, const double* f, size_t n)
+{
+    if (!ctx || !f) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    if (!valid_instance(ctx, instance)) return fail(ctx, LBIB_ERR_INVALID_ARG, "no such instance");
+    const Lattice& L = ctx->d.L;
+    const int inx = ctx->inst_nx[instance], x0 = ctx->inst_x0[instance];
+    size_t nn = (size_t)inx * L.ny;
+    if (n < 9 * nn) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than 9 nx ny");
+    if (ctx->s_f != 0) return fail(ctx, LBIB_ERR_STATE, "populations can only be written before the first step");
+    DeviceGuard guard(ctx->device);
+    std::vector<char> raw((size_t)9 * nn * ctx->rsz);
+    for (int q = 0; q < 9; ++q)
+        for (size_t i = 0; i < nn; ++i) {
+            const size_t k = (size_t)q * nn + i;
+            double v = f[k] - wrest(q);
+            if (ctx->prec == PREC_F64) reinterpret_cast<double*>(raw.data())[k] = v;
+            else reinterpret_cast<float*>(raw.data())[k] = (float)v;
+        }
+    CK(cudaStreamSynchronize(ctx->stream));
+    char* dst = static_cast<char*>(ctx->d.f[0]);
+    for (int q = 0; q < 9; ++q)
+        CK(cudaMemcpy2D(dst + ((size_t)q * L.qstride + x0) * ctx->rsz, (size_t)L.nxp * ctx->rsz,
+                        raw.data() + (size_t)q * nn * ctx->rsz, (size_t)inx * ctx->rsz, (size_t)inx * ctx->rsz,
+                        L.ny, cudaMemcpyHostToDevice));
     return LBIB_OK;
 }
 
 lbib_status lbib_write_populations(lbib_ctx* ctx, const double* f, size_t n)
 {
-    if (!ctx || !f) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
-    const Lattice& L = ctx->d.L;
-    size_t nn = (size_t)L.nx * L.ny;
-    if (n < 9 * nn) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than 9 nx ny");
-    if (ctx->s_f != 0) return fail(ctx, LBIB_ERR_STATE, "populations can only be written before the first step");
+    return lbib_write_instance_populations(ctx, 0, f, n);
+}
+
+lbib_status lbib_read_instance_observables(lbib_ctx* ctx, int32_t instance, lbib_obs* out, size_t cap,
+                                           size_t* n_out)
+{
+    if (!ctx || !n_out || (cap && !out)) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    if (!valid_instance(ctx, instance)) return fail(ctx, LBIB_ERR_INVALID_ARG, "no such instance");
+    *n_out = 0;
     DeviceGuard guard(ctx->device);
-    size_t nq = (size_t)9 * L.qstride;
-    std::vector<char> raw(nq * ctx->rsz, 0);
-    for (int q = 0; q < 9; ++q)
-        for (int y = 0; y < L.ny; ++y)
-            for (int x = 0; x < L.nx; ++x) {
-                size_t i = (size_t)q * L.qstride + (size_t)y * L.nxp + x;
-                double v = f[((size_t)q * L.ny + y) * L.nx + x] - wrest(q);
-                if (ctx->prec == PREC_F64) reinterpret_cast<double*>(raw.data())[i] = v;
-                else reinterpret_cast<float*>(raw.data())[i] = (float)v;
-            }
-    CK(cudaStreamSynchronize(ctx->stream));
-    CK(cudaMemcpy(ctx->d.f[0], raw.data(), raw.size(), cudaMemcpyHostToDevice));
-    return LBIB_OK;
+    lbib_status s = pre_read(ctx);
+    if (ctx->inst_nbodies[instance] == 0) return s;
+    const int64_t last = ctx->s_l, rc = ctx->d.ring_cap;
+    int64_t& consumed = ctx->obs_consumed[instance];
+    int64_t first = std::max<int64_t>(consumed + 1, last - rc + 1);
+    int64_t cnt = std::min<int64_t>((int64_t)cap, last - first + 1);
+    const lbib_obs* ring = ctx->d.ring + (size_t)instance * rc;
+    // the requested steps occupy at most two contiguous runs of the ring
+    int64_t k = 0;
+    while (k < cnt) {
+        const int64_t slot = (first + k) % rc;
+        const int64_t run = std::min<int64_t>(cnt - k, rc - slot);
+        CK(cudaMemcpy(out + k, ring + slot, (size_t)run * sizeof(lbib_obs), cudaMemcpyDeviceToHost));
+        k += run;
+    }
+    if (cnt > 0) consumed = first + cnt - 1;
+    *n_out = (size_t)std::max<int64_t>(cnt, 0);
+    return s;
+}
+
+lbib_status lbib_read_latest_observables(lbib_ctx* ctx, lbib_obs* out, size_t n)
+{
+    if (!ctx || !out) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    if (n < (size_t)ctx->ninst) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than n_instances");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = pre_read(ctx);
+    if (s != LBIB_OK && s != LBIB_ERR_DIVERGED) return s;
+    const int64_t rc = ctx->d.ring_cap, last = ctx->s_l;
+    if (ctx->d.nbodies > 0 && last > 0) {
+        // one strided copy: slot last % rc of every instance's ring
+        CK(cudaMemcpy2D(out, sizeof(lbib_obs), ctx->d.ring + last % rc, (size_t)rc * sizeof(lbib_obs),
+                        sizeof(lbib_obs), (size_t)ctx->ninst, cudaMemcpyDeviceToHost));
+    }
+    for (int i = 0; i < ctx->ninst; ++i)
+        if (ctx->inst_nbodies[i] == 0 || last == 0) {
+            std::memset(&out[i], 0, sizeof(lbib_obs));
+            out[i].step = -1;
+        }
+    return s;
 }
 
 lbib_status lbib_read_observables(lbib_ctx* ctx, lbib_obs* out, size_t cap, size_t* n_out)
 {
-    if (!ctx || !n_out || (cap && !out)) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
-    *n_out = 0;
-    DeviceGuard guard(ctx->device);
-    lbib_status s = pre_read(ctx);
-    if (ctx->d.nbodies == 0) return s;
-    const int64_t last = ctx->s_l, rc = ctx->d.ring_cap;
-    int64_t first = std::max<int64_t>(ctx->obs_consumed + 1, last - rc + 1);
-    int64_t cnt = std::min<int64_t>((int64_t)cap, last - first + 1);
-    for (int64_t k = 0; k < cnt; ++k)
-        CK(cudaMemcpy(out + k, ctx->d.ring + ((first + k) % rc), sizeof(lbib_obs), cudaMemcpyDeviceToHost));
-    if (cnt > 0) ctx->obs_consumed = first + cnt - 1;
-    *n_out = (size_t)std::max<int64_t>(cnt, 0);
-    return s;
+    return lbib_read_instance_observables(ctx, 0, out, cap, n_out);
 }
 
 lbib_status lbib_read_markers(lbib_ctx* ctx, int32_t id, double* xy, size_t n)
@@ -801,8 +985,7 @@ lbib_status lbib_read_markers(lbib_ctx* ctx, int32_t id, double* xy, size_t n)
     lbib_status s = pre_read(ctx);
     if (s != LBIB_OK && s != LBIB_ERR_DIVERGED) return s;
     const Dev& d = ctx->d;
-    int off = 0;
-    for (int b = 0; b < id; ++b) off += ctx->bodies[b].nv;
+    const int off = ctx->mark_off[id];
     std::vector<double> x(nv), y(nv);
     const double* P = d.pos[ctx->s_l & 1];
     CK(cudaMemcpy(x.data(), P + off, nv * 8, cudaMemcpyDeviceToHost));
@@ -825,8 +1008,7 @@ lbib_status lbib_read_body_field(lbib_ctx* ctx, int32_t id, int32_t field, doubl
     lbib_status s = pre_read(ctx);
     if (s != LBIB_OK && s != LBIB_ERR_DIVERGED) return s;
     const Dev& d = ctx->d;
-    int off = 0;
-    for (int b = 0; b < id; ++b) off += ctx->bodies[b].nv;
+    const int off = ctx->mark_off[id];
     if (field <= LBIB_FIELD_YPREV) {
         int64_t k = (field <= LBIB_FIELD_Y) ? ctx->s_l : ctx->s_l - 1;
         const double* P = d.pos[k & 1];
@@ -858,9 +1040,7 @@ lbib_status lbib_read_bonds(lbib_ctx* ctx, int32_t id, int32_t* bound, double* a
     lbib_status s = pre_read(ctx);
     if (s != LBIB_OK && s != LBIB_ERR_DIVERGED) return s;
     const Dev& d = ctx->d;
-    int loff = 0;
-    for (int b = 0; b < id; ++b)
-        if (ctx->bodies[b].adhesive) loff += ctx->bodies[b].adh.n_ligands;
+    const int loff = ctx->lig_off[id];
     if (bound) CK(cudaMemcpy(bound, d.bound + loff, nl * 4, cudaMemcpyDeviceToHost));
     if (ax) CK(cudaMemcpy(ax, d.anchor + loff, nl * 8, cudaMemcpyDeviceToHost));
     if (ay) CK(cudaMemcpy(ay, d.anchor + d.nlig + loff, nl * 8, cudaMemcpyDeviceToHost));
@@ -884,9 +1064,9 @@ struct CkHeader {
     uint64_t magic;
     int32_t nx, ny, nbodies, nmark, nlig, prec;
     int64_t steps;
-    uint64_t seed;
+    int32_t ninst, pad;
 };
-constexpr uint64_t kMagic = 0x314b4350424942ULL;  // "LBIBPCK1"
+constexpr uint64_t kMagic = 0x324b4350424942ULL;  // "BIBPCK2"
 
 size_t state_bytes(const lbib_ctx* ctx)
 {
@@ -918,7 +1098,7 @@ lbib_status lbib_save_state(lbib_ctx* ctx, void* buf, size_t bytes)
     const Dev& d = ctx->d;
     const int64_t st = ctx->s_f;
     char* p = static_cast<char*>(buf);
-    CkHeader h{kMagic, d.L.nx, d.L.ny, d.nbodies, d.nmark, d.nlig, ctx->prec, st, d.seed};
+    CkHeader h{kMagic, d.L.nx, d.L.ny, d.nbodies, d.nmark, d.nlig, ctx->prec, st, ctx->ninst, 0};
     std::memcpy(p, &h, sizeof(h));
     p += sizeof(h);
     size_t nq = (size_t)9 * d.L.qstride;
@@ -956,7 +1136,7 @@ lbib_status lbib_load_state(lbib_ctx* ctx, const void* buf, size_t bytes)
     std::memcpy(&h, p, sizeof(h));
     p += sizeof(h);
     if (h.magic != kMagic || h.nx != d.L.nx || h.ny != d.L.ny || h.nbodies != d.nbodies || h.nmark != d.nmark ||
-        h.nlig != d.nlig || h.prec != ctx->prec || h.steps < 0)
+        h.nlig != d.nlig || h.prec != ctx->prec || h.steps < 0 || h.ninst != ctx->ninst)
         return fail(ctx, LBIB_ERR_INVALID_ARG, "checkpoint does not match this context");
     const int64_t st = h.steps;
     size_t nq = (size_t)9 * d.L.qstride;
@@ -992,9 +1172,10 @@ lbib_status lbib_load_state(lbib_ctx* ctx, const void* buf, size_t bytes)
     CK(cudaMemset(d.count, 0, 12));
     CK(cudaMemset(d.status, 0, 4));
     CK(cudaMemset(d.ticket, 0, 4));
+    CK(cudaMemset(d.inst_ticket, 0, (size_t)ctx->ninst * 4));
     CK(cudaMemcpy(d.step, &st, 8, cudaMemcpyHostToDevice));
     ctx->s_f = ctx->s_l = st;
-    ctx->obs_consumed = st;
+    ctx->obs_consumed.assign(ctx->ninst, st);
     if (d.nbodies) {
         CK(launch_activate(d, ctx->prec, st, 3, ctx->stream));
         CK(launch_rebuild_mask(d, ctx->prec, (int)(st & 1), ctx->stream));

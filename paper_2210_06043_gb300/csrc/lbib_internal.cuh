@@ -51,19 +51,43 @@ enum : uint32_t {
 
 enum { PREC_F64 = 0, PREC_F32 = 1 };
 
+// A context holds one or more capillary instances (a sweep) side by side
+// along x in one lattice: instance i occupies the node columns
+// [x0_i, x0_i + nx_i) with x0_i a multiple of TX, so that every tile column
+// belongs to exactly one instance; all instances share ny and the fluid
+// parameters.  A single capillary is the batch of one.
 struct Lattice {
-    int nx, ny, nxp;          // nodes; padded row length (multiple of TX)
-    int ntx, nty, ntiles;     // tiles
+    int nx, ny, nxp;          // nx: node columns of the whole batch; nxp: row pitch (multiple of TX)
+    int ntx, nty, ntiles;     // tiles of the whole batch
     int bc;                   // lbib_bc_mode
     int qstride;              // ny * nxp
     double tau, omega, nu, umax, rho_out, gx, gy;
 };
 
+// Per tile column: origin and width of its instance, the instance's first
+// marker (marker ids in the tile bit masks are local to the instance) and the
+// instance index.  Layout of an int4.
+struct ColInfo {
+    int x0, nx, moff, inst;
+};
+
+struct InstConst {
+    int x0, nx;               // node columns [x0, x0 + nx)
+    int moff, nmark;          // markers (= vertices) of the instance's bodies
+    int body0, nbodies;       // bodies [body0, body0 + nbodies)
+    int lig0, nlig;           // ligand sites
+    int first_cell, first_particle;  // global body ids or -1
+    int pad0, pad1;
+    uint64_t seed;            // Philox key of the instance's bond kinetics
+};
+
 struct BodyConst {
     int kind, motion, nv, off;        // off: global index of vertex 0 / element 0
     int adhesive, nlig, lig_off, nl0;
-    int sigma_inf, pad0, pad1, pad2;
+    int sigma_inf, inst, x0, nxi;     // instance and its node columns [x0, x0 + nxi)
+    int moff, lig0, b0, nbi;          // instance's first marker, first site, first body, body count
     double A0, P0, inv_A0, inv_P0;
+    double r_act, r_act_sub;          // the instance's activation radii (see Dev)
     double ks, kb, ka, mv, mass, inertia;
     double sigma, ycr, yeq, Pf, kr0_dt, xi;
 };
@@ -86,13 +110,17 @@ struct Dev {
     uint32_t* nearflag[2];     // [ntiles]: tile is near for lattice steps of this parity
     int32_t* list[3];          // [list_cap]: near tiles of lattice step m, m % 3
     int32_t* count;            // [3]
-    uint32_t* mask[2];         // [ntiles][mw]
+    uint32_t* mask[2];         // [ntiles][mw], bit k: the instance's marker k
     int mw, list_cap;
     // markers consumed by lattice step m, parity m & 1:
     //   mki[p] = int32 [2][nmark]: floor(X), floor(Y - 1/2)
     //   mkf[p] = Real [4][nmark]: X - floor(X), Y - 1/2 - floor(Y - 1/2), Fx ds, Fy ds
     int32_t* mki[2];
     void* mkf[2];
+    const int4* colinfo;       // [ntx] ColInfo of each tile column
+    int ninst;
+    const InstConst* inst;     // [ninst]
+    uint32_t* inst_ticket;     // [ninst] Lagrangian blocks of the instance done this step
     // Lagrangian state
     int nbodies, nmark, nlig, nv_max;
     double* pos[2];            // [2][nmark] (x block then y block); X^n in pos[n & 1]
@@ -110,18 +138,17 @@ struct Dev {
     const int32_t* site_off;   // [nmark + 1] sites of element e: [site_off[e], site_off[e+1])
     void* diag;                // Real [NDIAG][nmark]
     double* body_obs[2];       // [nbodies][BO_N] of X^k in body_obs[k & 1]
-    lbib_obs* ring;
+    lbib_obs* ring;            // [ninst][ring_cap]
     int ring_cap;
-    int first_cell, first_particle;
     int64_t* step;             // Lagrangian step counter n (advanced by the last Lagrangian block)
     uint32_t* status;
     uint32_t* ticket;
-    double r_act;              // activation radius around markers (lattice units)
-    double r_act_sub;          // radius used by every ACT_STRIDE-th marker (covers the ones between)
+    // activation radius around markers (lattice units) and the radius used by
+    // every ACT_STRIDE-th marker (covers the ones between) are per instance:
+    // BodyConst::r_act, BodyConst::r_act_sub
     double dcut;               // repulsion cut-off (Eq. 12)
     double probe;              // probe length (Sec. 2.6)
     double uscale;             // observables: u_max / H
-    uint64_t seed;             // Philox key of the bond kinetics
 };
 
 // ------------------------------------------------------------------ launchers
@@ -129,10 +156,11 @@ struct Dev {
 cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, cudaStream_t s);
 cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, cudaStream_t s);
 cudaError_t launch_init_populations(const Dev& d, int prec, int buf, cudaStream_t s);
-cudaError_t launch_macro(const Dev& d, int prec, int buf, int64_t m, double* rho, double* ux, double* uy,
-                         cudaStream_t s);
-cudaError_t launch_macro_typed(const Dev& d, int prec, int buf, int64_t m, void* ux, void* uy, int dtype,
-                               cudaStream_t s);
+// moments of one instance (node columns [x0, x0 + inx)) into [ny][inx] arrays
+cudaError_t launch_macro(const Dev& d, int prec, int buf, int64_t m, int x0, int inx, double* rho, double* ux,
+                         double* uy, cudaStream_t s);
+cudaError_t launch_macro_typed(const Dev& d, int prec, int buf, int64_t m, int x0, int inx, void* ux, void* uy,
+                               int dtype, cudaStream_t s);
 cudaError_t launch_lagrangian(const Dev& d, int prec, int parity, cudaStream_t s);
 cudaError_t launch_activate(const Dev& d, int prec, int64_t m, int which, cudaStream_t s);
 cudaError_t launch_rebuild_mask(const Dev& d, int prec, int parity, cudaStream_t s);

@@ -112,25 +112,62 @@ __device__ __forceinline__ Spot<R> spot_of(P2<R> X, P2<R> Y)
     return s;
 }
 
-template <typename R, int K>
-__device__ __forceinline__ R group_sum(R v)
-{
-#pragma unroll
-    for (int o = 1; o < K; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
+// Products and fused multiply-adds with rounding stated explicitly, so that a
+// sum is evaluated the same way whatever the surrounding code.
+template <typename R>
+__device__ __forceinline__ R mul_rn(R a, R b);
+template <>
+__device__ __forceinline__ float mul_rn<float>(float a, float b) { return __fmul_rn(a, b); }
+template <>
+__device__ __forceinline__ double mul_rn<double>(double a, double b) { return __dmul_rn(a, b); }
+
+template <typename R, bool GRAD>
+struct RowSums {
+    R W, u, v, r, ux, uy, vx, vy;
+    __device__ __forceinline__ void add(const RowSums& o)
+    {
+        W += o.W;
+        u += o.u;
+        v += o.v;
+        r += o.r;
+        if (GRAD) {
+            ux += o.ux;
+            uy += o.uy;
+            vx += o.vx;
+            vy += o.vy;
+        }
+    }
+    __device__ __forceinline__ RowSums xor_partner(int o) const
+    {
+        RowSums t;
+        t.W = __shfl_xor_sync(0xffffffffu, W, o);
+        t.u = __shfl_xor_sync(0xffffffffu, u, o);
+        t.v = __shfl_xor_sync(0xffffffffu, v, o);
+        t.r = __shfl_xor_sync(0xffffffffu, r, o);
+        if (GRAD) {
+            t.ux = __shfl_xor_sync(0xffffffffu, ux, o);
+            t.uy = __shfl_xor_sync(0xffffffffu, uy, o);
+            t.vx = __shfl_xor_sync(0xffffffffu, vx, o);
+            t.vy = __shfl_xor_sync(0xffffffffu, vy, o);
+        }
+        return t;
+    }
+};
 
 // Truncated-stencil velocity (and optionally its gradient) and renormalised
 // density deviation at a point from the near-tile output of lattice step m,
-// computed by a group of K lanes (K = 1, 2, 4): lane r sums the stencil rows
-// jy - 1 + r, jy - 1 + r + K, ..., the rows are combined by shuffles and every
-// lane of the group gets the result.  Indices are clamped into the lattice and
-// the weights of out-of-lattice nodes zeroed, so a lane's loads are
-// independent and issued together.  All 32 lanes of the warp must call this
-// together.
+// computed by a group of K lanes (K = 1, 2, 4): lane r takes the stencil rows
+// jy - 1 + r, jy - 1 + r + K, ...  Each row is summed over its four nodes in
+// order and the four row sums are combined as (row0 + row1) + (row2 + row3)
+// for every K (by shuffles across the group), so the result does not depend
+// on K; every lane of the group gets it.  The point is in the coordinates of
+// its instance (node columns [x0, x0 + nxi) of the lattice).  Indices are
+// clamped into the instance and the weights of nodes outside it zeroed, so a
+// lane's loads are independent and issued together.  All 32 lanes of the warp
+// must call this together.
 template <typename R, bool GRAD, int K>
-__device__ __forceinline__ void sample_group(const Dev& d, const Spot<R>& sp, int32_t m, int r, Sample<R>& o,
-                                             uint32_t& miss)
+__device__ __forceinline__ void sample_group(const Dev& d, const Spot<R>& sp, int32_t m, int r, int x0, int nxi,
+                                             Sample<R>& o, uint32_t& miss)
 {
     const Lattice& L = d.L;
     const R* __restrict__ ux = static_cast<const R*>(d.ux);
@@ -143,8 +180,8 @@ __device__ __forceinline__ void sample_group(const Dev& d, const Spot<R>& sp, in
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         const int i = i0 + a;
-        const bool vi = (i >= 0 && i < L.nx);
-        ic[a] = min(max(i, 0), L.nx - 1);
+        const bool vi = (i >= 0 && i < nxi);
+        ic[a] = x0 + min(max(i, 0), nxi - 1);
         const R rx = sp.ax + R(1 - a);  // X - i
         dpx[a] = R(0);
         if (GRAD) peskin_both<R>(rx, px[a], dpx[a]);
@@ -180,39 +217,60 @@ __device__ __forceinline__ void sample_group(const Dev& d, const Spot<R>& sp, in
 #pragma unroll
     for (int k = 0; k < 2 * NR; ++k)
         if (fr[k] != m) miss = 1u;
-    R W = 0, Nu = 0, Nv = 0, Nr = 0, Nux = 0, Nuy = 0, Nvx = 0, Nvy = 0;
+    RowSums<R, GRAD> rs[NR];
 #pragma unroll
-    for (int k = 0; k < NR; ++k)
+    for (int k = 0; k < NR; ++k) {
+        RowSums<R, GRAD>& s = rs[k];
+        s.W = s.u = s.v = s.r = s.ux = s.uy = s.vx = s.vy = R(0);
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            const R w = px[a] * py[k];
+            const R w = mul_rn<R>(px[a], py[k]);
             const int q = 4 * k + a;
-            W += w;
-            Nu += a_u[q] * w;
-            Nv += a_v[q] * w;
-            Nr += a_r[q] * w;
+            s.W += w;
+            s.u = fma(a_u[q], w, s.u);
+            s.v = fma(a_v[q], w, s.v);
+            s.r = fma(a_r[q], w, s.r);
             if (GRAD) {
-                const R wx = dpx[a] * py[k], wy = px[a] * dpy[k];
-                Nux += a_u[q] * wx;
-                Nuy += a_u[q] * wy;
-                Nvx += a_v[q] * wx;
-                Nvy += a_v[q] * wy;
+                const R wx = mul_rn<R>(dpx[a], py[k]), wy = mul_rn<R>(px[a], dpy[k]);
+                s.ux = fma(a_u[q], wx, s.ux);
+                s.uy = fma(a_u[q], wy, s.uy);
+                s.vx = fma(a_v[q], wx, s.vx);
+                s.vy = fma(a_v[q], wy, s.vy);
             }
         }
-    W = group_sum<R, K>(W);
-    o.u = group_sum<R, K>(Nu);
-    o.v = group_sum<R, K>(Nv);
-    Nr = group_sum<R, K>(Nr);
+    }
+    // (row0 + row1) + (row2 + row3); IEEE addition is commutative, so both
+    // lanes of a pair form the same partial sum
+    RowSums<R, GRAD> t;
+    if (K == 1) {
+        t = rs[0];
+        t.add(rs[1]);
+        RowSums<R, GRAD> t2 = rs[NR > 2 ? 2 : 0];
+        t2.add(rs[NR > 3 ? 3 : 0]);
+        t.add(t2);
+    } else if (K == 2) {  // lane r holds rows r and r + 2
+        t = rs[0];
+        t.add(rs[0].xor_partner(1));
+        RowSums<R, GRAD> t2 = rs[NR > 1 ? 1 : 0];
+        t2.add(rs[NR > 1 ? 1 : 0].xor_partner(1));
+        t.add(t2);
+    } else {  // K == 4: lane r holds row r
+        t = rs[0];
+        t.add(t.xor_partner(1));
+        t.add(t.xor_partner(2));
+    }
+    o.W = t.W;
+    o.u = t.u;
+    o.v = t.v;
     if (GRAD) {
-        o.ux = group_sum<R, K>(Nux);
-        o.uy = group_sum<R, K>(Nuy);
-        o.vx = group_sum<R, K>(Nvx);
-        o.vy = group_sum<R, K>(Nvy);
+        o.ux = t.ux;
+        o.uy = t.uy;
+        o.vx = t.vx;
+        o.vy = t.vy;
     } else {
         o.ux = o.uy = o.vx = o.vy = R(0);
     }
-    o.W = W;
-    o.drho = (W > R(0)) ? Nr / W : R(0);
+    o.drho = (t.W > R(0)) ? t.r / t.W : R(0);
 }
 
 // Tiles overlapping the node box [i0, i1] x [j0, j1]: enumerates at most 8 of
@@ -309,8 +367,8 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
             a2 += X * Yw - Xw * Y;
         }
         if (tid < RG_N) rig[tid] = d.rigid[bi * RG_N + tid];
-        const double* eo = d.body_obs[n & 1];
-        for (int k = tid; k < 4 * d.nbodies; k += T) ext[k >> 2][k & 3] = (R)eo[(k >> 2) * BO_N + BO_XMIN + (k & 3)];
+        const double* eo = d.body_obs[n & 1] + (size_t)B.b0 * BO_N;  // the instance's bodies
+        for (int k = tid; k < 4 * B.nbi; k += T) ext[k >> 2][k & 3] = (R)eo[(k >> 2) * BO_N + BO_XMIN + (k & 3)];
     }
     const double area = 0.5 * block_sum<double>(a2, dscr[0]);  // FP64 area reduction (Eq. 11)
 
@@ -351,8 +409,8 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
         if (PY.h + PY.l < R(0)) PY = P2<R>{R(0), R(0)};
         if (PY.h + PY.l > R(L.ny)) PY = P2<R>{R(L.ny), R(0)};
         Sample<R> o, q;
-        sample_group<R, false, K>(d, spot_of<R>(X, Y), mf, lane4, o, miss);
-        sample_group<R, true, K>(d, spot_of<R>(PX, PY), mf, lane4, q, miss);
+        sample_group<R, false, K>(d, spot_of<R>(X, Y), mf, lane4, B.x0, B.nxi, o, miss);
+        sample_group<R, true, K>(d, spot_of<R>(PX, PY), mf, lane4, B.x0, B.nxi, q, miss);
         if (valid && lane4 == 0) {
             uvx[l] = o.u;
             uvy[l] = o.v;
@@ -377,6 +435,7 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
         const R* lt = static_cast<const R*>(d.lig_t);
         R* mg = static_cast<R*>(d.margin);
         const R Pf = (R)B.Pf, ycr = (R)B.ycr, yeq = (R)B.yeq, H = (R)L.ny;
+        const uint64_t seed = d.inst[B.inst].seed;  // sites are numbered within the instance
         if (B.motion != LBIB_FIXED) {
             for (int k = B.lig_off + tid; k < B.lig_off + B.nlig; k += T) {
                 const int l = d.lig_el[k] - off;
@@ -384,7 +443,7 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
                 const int bd = d.bound[k];
                 const P2<R> SX = p2_add<R>(P2<R>{xh[l], xl[l]}, t * ex[l]);
                 const P2<R> SY = p2_add<R>(P2<R>{yh[l], yl[l]}, t * ey[l]);
-                const R u = (R)bond_draw(d.seed, n, (uint32_t)k);
+                const R u = (R)bond_draw(seed, n, (uint32_t)(k - B.lig0));
                 if (bd) {
                     const R dxa = p2_sub<R>(SX, p2_of<R>(d.anchor[k]));
                     const R dya = p2_sub<R>(SY, p2_of<R>(d.anchor[d.nlig + k]));
@@ -428,16 +487,17 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
         }
     }
 
-    // repulsion (Eq. 12) from the vertices of every other body within the cut-off
+    // repulsion (Eq. 12) from the vertices of every other body of the instance within the cut-off
     const R c0 = R(1e-4) / (R(8) * sqrt(R(2)));
     const R dcut = (R)d.dcut;
     for (int v = tid; v < nv; v += T) {
         R ax = 0, ay = 0;
         const P2<R> X = P2<R>{xh[v], xl[v]}, Y = P2<R>{yh[v], yl[v]};
         const R xa = X.h + X.l, ya = Y.h + Y.l;
-        for (int o = 0; o < d.nbodies; ++o) {
+        for (int ol = 0; ol < B.nbi; ++ol) {
+            const int o = B.b0 + ol;
             if (o == bi) continue;
-            if (xa < ext[o][0] - dcut || xa > ext[o][1] + dcut || ya < ext[o][2] - dcut || ya > ext[o][3] + dcut)
+            if (xa < ext[ol][0] - dcut || xa > ext[ol][1] + dcut || ya < ext[ol][2] - dcut || ya > ext[ol][3] + dcut)
                 continue;
             const BodyConst& C = d.body[o];
             for (int w = 0; w < C.nv; ++w) {
@@ -590,8 +650,7 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
     const int64_t n2 = n + 2;
     uint32_t* flag2 = d.nearflag[n2 & 1];
     const int c2 = (int)(n2 % 3);
-    const int ra = (int)ceil(d.r_act_sub) + 1;
-    R dper = 0;
+    const int ra = (int)ceil(B.r_act_sub) + 1;
     for (int l0 = tid / K; l0 < nvq; l0 += Q) {
         const bool valid = l0 < nv;
         const int l = valid ? l0 : nv - 1;
@@ -602,7 +661,7 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
         const P2<R> CY = p2_add<R>(P2<R>{qyh[l], qyl[l]}, R(0.5) * dyn);
         const Spot<R> sc = spot_of<R>(CX, CY);
         Sample<R> o;
-        sample_group<R, false, K>(d, sc, mf, lane4, o, miss);
+        sample_group<R, false, K>(d, sc, mf, lane4, B.x0, B.nxi, o, miss);
         if (!valid) continue;
         const R ds = sqrt(dxn * dxn + dyn * dyn);
         const R usx = R(0.5) * (svx[l] + svx[w]), usy = R(0.5) * (svy[l] + svy[w]);
@@ -616,7 +675,7 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
         }
         const int g = off + l;
         if (lane4 == 0) {
-            mki[g] = sc.ix;
+            mki[g] = B.x0 + sc.ix;  // lattice column of the stencil origin
             mki[NM + g] = sc.jy;
             mkf[g] = sc.ax;
             mkf[NM + g] = sc.ay;
@@ -629,19 +688,20 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
             diag[LBIB_FIELD_MFX * NM + g] = Fx;
             diag[LBIB_FIELD_MFY * NM + g] = Fy;
             diag[LBIB_FIELD_MDS * NM + g] = ds;
-            dper += ds - sl0[l];  // perimeter change for delta p (Sec. 3.1)
+            len[l] = ds;  // X^n lengths are no longer needed
         }
         int tl[8];
         if (Fx != R(0) || Fy != R(0)) {
             // stencil nodes [ix - 1, ix + 2] x [jy - 1, jy + 2]: at most 2 x 2 tiles, one per lane
-            const int i0 = max(0, sc.ix - 1), i1 = min(L.nx - 1, sc.ix + 2);
+            const int i0 = max(0, sc.ix - 1), i1 = min(B.nxi - 1, sc.ix + 2);
             const int j0 = max(0, sc.jy - 1), j1 = min(L.ny - 1, sc.jy + 2);
+            const int gl = g - B.moff;  // bit of the marker within its instance
             if (i0 <= i1 && j0 <= j1) {
-                const int nt = box_tiles(L, i0, i1, j0, j1, 0, tl);
+                const int nt = box_tiles(L, B.x0 + i0, B.x0 + i1, j0, j1, 0, tl);
                 for (int e = lane4; e < nt; e += K) {
                     const int t = tl[e];
                     if (!d.nearflag[p][t]) miss |= 2u;
-                    atomicOr(&d.mask[p][(size_t)t * d.mw + (g >> 5)], 1u << (g & 31));
+                    atomicOr(&d.mask[p][(size_t)t * d.mw + (gl >> 5)], 1u << (gl & 31));
                 }
             }
         }
@@ -650,11 +710,11 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
             // step n + 2: each ACT_STRIDE-th element covers the box of half-width
             // ra_sub (r_act plus the stride's reach along the chain) around its
             // stencil origin; the lanes split the tile list
-            const int i0 = max(0, sc.ix - ra), i1 = min(L.nx - 1, sc.ix + ra);
+            const int i0 = max(0, sc.ix - ra), i1 = min(B.nxi - 1, sc.ix + ra);
             const int j0 = max(0, sc.jy - ra), j1 = min(L.ny - 1, sc.jy + ra);
             if (i0 <= i1 && j0 <= j1) {
                 for (int start = 0;; start += 8) {
-                    const int nt = box_tiles(L, i0, i1, j0, j1, start, tl);
+                    const int nt = box_tiles(L, B.x0 + i0, B.x0 + i1, j0, j1, start, tl);
                     uint32_t fl[8 / K];
 #pragma unroll
                     for (int k = 0; k < 8 / K; ++k) {
@@ -677,10 +737,14 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
     }
 
     // 7. measures of X^{n+1}: FP64 shoelace area and centroid sums, FP32
-    //    perimeter change and extent; store X^{n+1}
+    //    perimeter change (from the element lengths of step 6) and extent;
+    //    store X^{n+1}
+    __syncthreads();
     double a2n = 0.0, cxs = 0.0, cys = 0.0;
+    R dper = 0;
     R xmin = R(3e38), xmax = R(-3e38), ymin = R(3e38), ymax = R(-3e38);
     for (int v = tid; v < nv; v += T) {
+        dper += len[v] - sl0[v];  // perimeter change for delta p (Sec. 3.1)
         const int w = (v + 1 == nv) ? 0 : v + 1;
         const P2<R> X = P2<R>{qxh[v], qxl[v]}, Y = P2<R>{qyh[v], qyl[v]};
         const double Xd = p2_double<R>(X), Yd = p2_double<R>(Y);
@@ -762,9 +826,10 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
         bo[BO_YMIN] = ymin;
         bo[BO_YMAX] = ymax;
         __threadfence();
-        const uint32_t ticket = atomicAdd(d.ticket, 1u);
-        if (ticket == (uint32_t)d.nbodies - 1u) {
-            // last block: observables of step n + 1 (Sec. 3.1), then advance n
+        const InstConst& I = d.inst[B.inst];
+        const uint32_t iticket = atomicAdd(&d.inst_ticket[B.inst], 1u);
+        if (iticket == (uint32_t)I.nbodies - 1u) {
+            // last block of the instance: its observables of step n + 1 (Sec. 3.1)
             __threadfence();
             const volatile double* all = d.body_obs[(n + 1) & 1];
             lbib_obs r;
@@ -774,17 +839,18 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
             r.delta_p = nan;
             r.r = nan;
             r.n_l = nan;
-            if (d.first_cell >= 0) r.delta_p = all[d.first_cell * BO_N + BO_DPERIM] * d.body[d.first_cell].inv_P0;
-            if (d.first_cell >= 0 && d.first_particle >= 0) {
-                const double dx = all[d.first_cell * BO_N + BO_CX] - all[d.first_particle * BO_N + BO_CX];
-                const double dy = all[d.first_cell * BO_N + BO_CY] - all[d.first_particle * BO_N + BO_CY];
+            const int fc = I.first_cell, fp = I.first_particle;
+            if (fc >= 0) r.delta_p = all[fc * BO_N + BO_DPERIM] * d.body[fc].inv_P0;
+            if (fc >= 0 && fp >= 0) {
+                const double dx = all[fc * BO_N + BO_CX] - all[fp * BO_N + BO_CX];
+                const double dy = all[fc * BO_N + BO_CY] - all[fp * BO_N + BO_CY];
                 const double r2 = dx * dx + dy * dy;
                 // FP32 square root refined by one FP64 Newton correction
                 const float s = sqrtf((float)r2);
                 r.r = (s > 0.f) ? (double)s + (r2 - (double)s * (double)s) * (0.5 / (double)s) : 0.0;
             }
             int nbt = 0, nl0 = 0;
-            for (int b = 0; b < d.nbodies; ++b)
+            for (int b = I.body0; b < I.body0 + I.nbodies; ++b)
                 if (d.body[b].adhesive) {
                     nbt += (int)all[b * BO_N + BO_NBOUND];
                     nl0 += d.body[b].nl0;
@@ -792,7 +858,15 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
             if (nl0 > 0) r.n_l = (double)nbt / (double)nl0;
             r.n_bound = nbt;
             r.status = (int32_t)atomicOr(d.status, 0u);
-            d.ring[(n + 1) % d.ring_cap] = r;
+            d.ring[(size_t)B.inst * d.ring_cap + (n + 1) % d.ring_cap] = r;
+            d.inst_ticket[B.inst] = 0u;
+            __threadfence();
+        }
+        // every block takes the batch ticket after its instance's work, so the
+        // last one sees all records written
+        const uint32_t ticket = atomicAdd(d.ticket, 1u);
+        if (ticket == (uint32_t)d.nbodies - 1u) {
+            __threadfence();
             d.count[n % 3] = 0;  // list of lattice step n is consumed
             *d.ticket = 0u;
             *d.step = n + 1;

@@ -12,7 +12,10 @@
 // Per node and step: Eq. 1 (streaming as a pull from x - e_i, collision),
 // Eq. 2 (equilibrium), Eq. 4 (forcing), Eqs. 5-6 (moments with half force),
 // halfway bounce-back on the walls y = 0, ny and Zou-He on the inlet x = 0
-// (plane-Poiseuille velocity, Sec. 3.1) and outlet x = nx - 1 (density).
+// (plane-Poiseuille velocity, Sec. 3.1) and outlet x = nx - 1 (density),
+// x counted within the node's instance (a context may hold a batch of
+// capillaries side by side; each tile column carries its instance's origin
+// and width).
 #include <cuda_runtime.h>
 
 #include "lbib_device.cuh"
@@ -55,35 +58,37 @@ __device__ __forceinline__ void zou_he_outlet(R g[9], R rho_out)
     g[6] = g[8] - h - ru / R(6);
 }
 
-// Pull the nine post-collision deviations that stream into node (x, y).
+// Pull the nine post-collision deviations that stream into node (x, y); xl is
+// x within its instance of width nxi (global column x - xl is the origin).
 template <typename S, typename R>
-__device__ __forceinline__ void pull(const Lattice& L, const S* __restrict__ fin, int x, int y, R g[9])
+__device__ __forceinline__ void pull(const Lattice& L, const S* __restrict__ fin, int x, int y, int xl, int nxi,
+                                     R g[9])
 {
     const int qs = L.qstride, nxp = L.nxp;
-    if (x > 0 && x < L.nx - 1 && y > 0 && y < L.ny - 1) {
+    if (xl > 0 && xl < nxi - 1 && y > 0 && y < L.ny - 1) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) g[q] = ld<S, R>(fin + q * qs + (y - cy(q)) * nxp + (x - cx(q)));
         return;
     }
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-        int xs = x - cx(q), ys = y - cy(q);
+        int xs = xl - cx(q), ys = y - cy(q);
         if (ys < 0 || ys >= L.ny) {
             g[q] = ld<S, R>(fin + op(q) * qs + y * nxp + x);  // halfway bounce-back
-        } else if (xs < 0 || xs >= L.nx) {
+        } else if (xs < 0 || xs >= nxi) {
             if (L.bc == LBIB_BC_PERIODIC_FORCE) {
-                xs = xs < 0 ? xs + L.nx : xs - L.nx;
-                g[q] = ld<S, R>(fin + q * qs + ys * nxp + xs);
+                xs = xs < 0 ? xs + nxi : xs - nxi;
+                g[q] = ld<S, R>(fin + q * qs + ys * nxp + (x - xl) + xs);
             } else {
                 g[q] = R(0);  // unknown, set by Zou-He
             }
         } else {
-            g[q] = ld<S, R>(fin + q * qs + ys * nxp + xs);
+            g[q] = ld<S, R>(fin + q * qs + ys * nxp + (x - cx(q)));
         }
     }
     if (L.bc == LBIB_BC_INLET_OUTLET) {
-        if (x == 0) zou_he_inlet<R>(g, inlet_profile<R>(L, y));
-        else if (x == L.nx - 1) zou_he_outlet<R>(g, R(L.rho_out));
+        if (xl == 0) zou_he_inlet<R>(g, inlet_profile<R>(L, y));
+        else if (xl == nxi - 1) zou_he_outlet<R>(g, R(L.rho_out));
     }
 }
 
@@ -118,12 +123,14 @@ __global__ void __launch_bounds__(TX* TY) k_bulk(Dev d, int p)
     const Lattice& L = d.L;
     int t = blockIdx.y * L.ntx + blockIdx.x;
     if (d.nearflag[p][t]) return;
+    const int4 ci = d.colinfo[blockIdx.x];
     int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
-    if (x >= L.nx || y >= L.ny) return;
+    const int xl = x - ci.x;
+    if (xl >= ci.y || y >= L.ny) return;
     const S* __restrict__ fin = static_cast<const S*>(d.f[p]);
     S* __restrict__ fout = static_cast<S*>(d.f[p ^ 1]);
     R g[9];
-    pull<S, R>(L, fin, x, y, g);
+    pull<S, R>(L, fin, x, y, xl, ci.y, g);
     R drho, ux, uy;
     collide<R>(g, R(L.gx), R(L.gy), R(L.omega), drho, ux, uy);
     if (!(drho > R(-1)) || !isfinite(ux + uy)) atomicOr(d.status, ST_DIVERGED);
@@ -143,7 +150,7 @@ __global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
     const int cnt = min(d.count[c], d.list_cap);
     const S* __restrict__ fin = static_cast<const S*>(d.f[p]);
     S* __restrict__ fout = static_cast<S*>(d.f[p ^ 1]);
-    const int nm = d.nmark;
+    const int nm = d.nmark;  // marker arrays span the whole batch
     const int32_t* __restrict__ mki = d.mki[p];
     const R* __restrict__ mkf = static_cast<const R*>(d.mkf[p]);
     uint32_t* mask = d.mask[p];
@@ -160,10 +167,12 @@ __global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
     for (int k = blockIdx.x; k < cnt; k += gridDim.x) {
         const int t = d.list[c][k];
         const int tx = t % L.ntx, ty = t / L.ntx;
+        const int4 ci = d.colinfo[tx];
         const int x = tx * TX + threadIdx.x, y = ty * TY + threadIdx.y;
-        const bool live = (x < L.nx && y < L.ny);
+        const int xl = x - ci.x;
+        const bool live = (xl < ci.y && y < L.ny);
         R g[9];
-        if (live) pull<S, R>(L, fin, x, y, g);  // issued before the marker gather
+        if (live) pull<S, R>(L, fin, x, y, xl, ci.y, g);  // issued before the marker gather
         R Fx = R(L.gx), Fy = R(L.gy);
         for (int w0 = 0; w0 < d.mw; w0 += NEAR_CHUNK_WORDS) {
             const int nw = min(NEAR_CHUNK_WORDS, d.mw - w0);
@@ -186,7 +195,7 @@ __global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
                 const uint32_t wd = s_words[l];
                 if ((wd >> bit) & 1u) {
                     const int pos = s_off[l] + __popc(wd & ((1u << bit) - 1u));
-                    const int id = (w0 + l) * 32 + bit;
+                    const int id = ci.z + (w0 + l) * 32 + bit;  // instance-local bit -> batch marker
                     s_ix[pos] = mki[id];
                     s_iy[pos] = mki[nm + id];
                     s_fx[pos] = mkf[id];
@@ -233,7 +242,7 @@ __global__ void k_init_populations(Dev d, int buf)
 {
     const Lattice& L = d.L;
     int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
-    if (x >= L.nx || y >= L.ny) return;
+    if (x - d.colinfo[blockIdx.x].x >= d.colinfo[blockIdx.x].y || y >= L.ny) return;
     S* f = static_cast<S*>(d.f[buf]);
     R u = (L.bc == LBIB_BC_INLET_OUTLET) ? inlet_profile<R>(L, y) : R(0);
 #pragma unroll
@@ -247,13 +256,14 @@ __global__ void k_init_populations(Dev d, int buf)
 // tiles it updated at step m, else from the post-collision populations
 // (sum f* e = rho u + F / 2 with F the uniform body force there).
 template <typename S, typename R, typename O>
-__global__ void k_macro(Dev d, int buf, int64_t m, O* rho_o, O* ux_o, O* uy_o, int add_one)
+__global__ void k_macro(Dev d, int buf, int64_t m, int x0, int inx, O* rho_o, O* ux_o, O* uy_o, int add_one)
 {
     const Lattice& L = d.L;
-    int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
-    if (x >= L.nx || y >= L.ny) return;
-    int t = blockIdx.y * L.ntx + blockIdx.x;
-    int base = y * L.nxp + x, ob = y * L.nx + x;
+    const int xl = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+    if (xl >= inx || y >= L.ny) return;
+    const int x = x0 + xl;
+    int t = blockIdx.y * L.ntx + x / TX;
+    int base = y * L.nxp + x, ob = y * inx + xl;
     R drho, ux, uy;
     if (d.fresh[t] == (int32_t)m) {
         drho = static_cast<const R*>(d.drho)[base];
@@ -276,8 +286,8 @@ __global__ void k_macro(Dev d, int buf, int64_t m, O* rho_o, O* ux_o, O* uy_o, i
 }
 
 // Marks as near, for lattice steps m (which & 1) and m + 1 (which & 2), every
-// tile within r_act of an element centroid of X^m (initial activation and
-// after a restore).
+// tile within its instance's r_act of an element centroid of X^m (initial
+// activation and after a restore).
 template <typename R>
 __global__ void k_activate(Dev d, int64_t m, int which)
 {
@@ -290,8 +300,10 @@ __global__ void k_activate(Dev d, int64_t m, int which)
     int l = k - B.off, w = B.off + (l + 1) % B.nv;
     const double* P = d.pos[m & 1];
     double X = 0.5 * (P[k] + P[w]), Y = 0.5 * (P[d.nmark + k] + P[d.nmark + w]);
-    int i0 = max(0, (int)floor(X - d.r_act)), i1 = min(L.nx - 1, (int)floor(X + d.r_act) + 1);
-    int j0 = max(0, (int)floor(Y - 0.5 - d.r_act)), j1 = min(L.ny - 1, (int)floor(Y - 0.5 + d.r_act) + 1);
+    // positions are in instance coordinates; the box is clipped to the instance
+    const double ra = B.r_act;
+    int i0 = B.x0 + max(0, (int)floor(X - ra)), i1 = B.x0 + min(B.nxi - 1, (int)floor(X + ra) + 1);
+    int j0 = max(0, (int)floor(Y - 0.5 - ra)), j1 = min(L.ny - 1, (int)floor(Y - 0.5 + ra) + 1);
     if (i0 > i1 || j0 > j1) return;
     for (int s = 0; s < 2; ++s) {
         if (!(which & (1 << s))) continue;
@@ -321,14 +333,18 @@ __global__ void k_rebuild_mask(Dev d, int parity)
     const int32_t* mki = d.mki[parity];
     int nm = d.nmark;
     if (mkf[2 * nm + k] == R(0) && mkf[3 * nm + k] == R(0)) return;
-    int i0 = max(0, mki[k] - 1), i1 = min(L.nx - 1, mki[k] + 2);
+    int b = 0;
+    while (b + 1 < d.nbodies && d.body[b + 1].off <= k) ++b;
+    const BodyConst& B = d.body[b];
+    const int kl = k - B.moff;  // instance-local marker id
+    int i0 = max(B.x0, mki[k] - 1), i1 = min(B.x0 + B.nxi - 1, mki[k] + 2);
     int j0 = max(0, mki[nm + k] - 1), j1 = min(L.ny - 1, mki[nm + k] + 2);
     if (i0 > i1 || j0 > j1) return;
     for (int ty = j0 / TY; ty <= j1 / TY; ++ty)
         for (int tx = i0 / TX; tx <= i1 / TX; ++tx) {
             int t = ty * L.ntx + tx;
             if (!d.nearflag[parity][t]) atomicOr(d.status, ST_SPREAD_MISS);
-            atomicOr(&d.mask[parity][(size_t)t * d.mw + (k >> 5)], 1u << (k & 31));
+            atomicOr(&d.mask[parity][(size_t)t * d.mw + (kl >> 5)], 1u << (kl & 31));
         }
 }
 
@@ -358,29 +374,35 @@ cudaError_t launch_init_populations(const Dev& d, int prec, int buf, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_macro(const Dev& d, int prec, int buf, int64_t m, double* rho, double* ux, double* uy,
-                         cudaStream_t s)
+cudaError_t launch_macro(const Dev& d, int prec, int buf, int64_t m, int x0, int inx, double* rho, double* ux,
+                         double* uy, cudaStream_t s)
 {
-    dim3 grid(d.L.ntx, d.L.nty), block(TX, TY);
-    if (prec == PREC_F64) k_macro<double, double, double><<<grid, block, 0, s>>>(d, buf, m, rho, ux, uy, 1);
-    else k_macro<float, float, double><<<grid, block, 0, s>>>(d, buf, m, rho, ux, uy, 1);
+    dim3 grid((inx + TX - 1) / TX, d.L.nty), block(TX, TY);
+    if (prec == PREC_F64)
+        k_macro<double, double, double><<<grid, block, 0, s>>>(d, buf, m, x0, inx, rho, ux, uy, 1);
+    else
+        k_macro<float, float, double><<<grid, block, 0, s>>>(d, buf, m, x0, inx, rho, ux, uy, 1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_macro_typed(const Dev& d, int prec, int buf, int64_t m, void* ux, void* uy, int dtype,
-                               cudaStream_t s)
+cudaError_t launch_macro_typed(const Dev& d, int prec, int buf, int64_t m, int x0, int inx, void* ux, void* uy,
+                               int dtype, cudaStream_t s)
 {
-    dim3 grid(d.L.ntx, d.L.nty), block(TX, TY);
+    dim3 grid((inx + TX - 1) / TX, d.L.nty), block(TX, TY);
     if (dtype == 1) {
         if (prec == PREC_F64)
-            k_macro<double, double, double><<<grid, block, 0, s>>>(d, buf, m, nullptr, (double*)ux, (double*)uy, 1);
+            k_macro<double, double, double><<<grid, block, 0, s>>>(d, buf, m, x0, inx, nullptr, (double*)ux,
+                                                                   (double*)uy, 1);
         else
-            k_macro<float, float, double><<<grid, block, 0, s>>>(d, buf, m, nullptr, (double*)ux, (double*)uy, 1);
+            k_macro<float, float, double><<<grid, block, 0, s>>>(d, buf, m, x0, inx, nullptr, (double*)ux,
+                                                                 (double*)uy, 1);
     } else {
         if (prec == PREC_F64)
-            k_macro<double, double, float><<<grid, block, 0, s>>>(d, buf, m, nullptr, (float*)ux, (float*)uy, 1);
+            k_macro<double, double, float><<<grid, block, 0, s>>>(d, buf, m, x0, inx, nullptr, (float*)ux,
+                                                                  (float*)uy, 1);
         else
-            k_macro<float, float, float><<<grid, block, 0, s>>>(d, buf, m, nullptr, (float*)ux, (float*)uy, 1);
+            k_macro<float, float, float><<<grid, block, 0, s>>>(d, buf, m, x0, inx, nullptr, (float*)ux,
+                                                                (float*)uy, 1);
     }
     return cudaGetLastError();
 }

@@ -7,8 +7,9 @@
 // or fail.  lbib_lattice_advance_noalloc serves them: it advances a channel
 // without membranes by running the library's bulk lattice kernel, with every
 // buffer beyond the caller's populations (the two padded deviation buffers
-// the kernel ping-pongs between, the per-tile flags it reads and the status
-// word it sets) carved out of one file-scope device array of fixed size.
+// the kernel ping-pongs between, the per-tile flags and per-tile-column
+// instance table it reads and the status word it sets) carved out of one
+// file-scope device array of fixed size.
 //
 // The array exists once per device for the life of the process (every GPU
 // that loads the library holds it until exit).  All calls on a device share
@@ -75,6 +76,13 @@ __global__ void k_deviation_to_absolute(const S* __restrict__ g, double* __restr
     }
 }
 
+// one instance over every tile column: origin 0, width nx
+__global__ void k_single_instance_columns(int4* ci, int ntx, int nx)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntx) ci[t] = make_int4(0, nx, 0, 0);
+}
+
 lbib_status fail_noalloc(lbib_status s, const std::string& msg)
 {
     set_global_error(msg.c_str());
@@ -115,8 +123,9 @@ extern "C" lbib_status lbib_lattice_advance_noalloc(const lbib_fluid_params* P, 
     const int prec = (P->storage == LBIB_STORE_FP64) ? PREC_F64 : PREC_F32;
     const size_t s = (prec == PREC_F64) ? 8 : 4;
     const size_t need_flags = up256((size_t)L.ntiles * 4);
+    const size_t need_cols = up256((size_t)L.ntx * sizeof(int4));
     const size_t need_f = up256((size_t)9 * L.qstride * s);
-    const size_t need = 256 + need_flags + 2 * need_f;
+    const size_t need = 256 + need_flags + need_cols + 2 * need_f;
     if ((double)L.nxp * L.ny * 9 >= 2147483648.0 || need > kScratchBytes)
         return fail_noalloc(LBIB_ERR_UNSUPPORTED,
                             "lattice needs " + std::to_string(need) + " bytes of scratch; the fixed array holds " +
@@ -136,11 +145,18 @@ extern "C" lbib_status lbib_lattice_advance_noalloc(const lbib_fluid_params* P, 
         d.L = L;
         d.status = reinterpret_cast<uint32_t*>(base);
         d.nearflag[0] = d.nearflag[1] = reinterpret_cast<uint32_t*>(base + 256);
-        d.f[0] = base + 256 + need_flags;
-        d.f[1] = base + 256 + need_flags + need_f;
+        int4* cols = reinterpret_cast<int4*>(base + 256 + need_flags);
+        d.colinfo = cols;
+        d.ninst = 1;
+        d.f[0] = base + 256 + need_flags + need_cols;
+        d.f[1] = base + 256 + need_flags + need_cols + need_f;
         const dim3 grid(L.ntx, L.nty), block(TX, TY);
         // status and tile flags must start at zero (the array keeps the last call's contents)
         e = cudaMemsetAsync(base, 0, 256 + need_flags, stream);
+        if (e == cudaSuccess) {
+            k_single_instance_columns<<<(L.ntx + 127) / 128, 128, 0, stream>>>(cols, L.ntx, L.nx);
+            e = cudaGetLastError();
+        }
         if (e == cudaSuccess) {
             if (prec == PREC_F64)
                 k_absolute_to_deviation<double><<<grid, block, 0, stream>>>(f, static_cast<double*>(d.f[0]), L);

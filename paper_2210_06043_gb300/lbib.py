@@ -80,6 +80,14 @@ _SIGS = {
     "lbib_describe": [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                       ctypes.POINTER(ctypes.c_int32)],
     "lbib_lattice_advance_noalloc": [ctypes.POINTER(lbib_fluid_params), _P, ctypes.c_int64],
+    "lbib_create_batch": [ctypes.POINTER(lbib_fluid_params), ctypes.c_int32, _P, _P, ctypes.POINTER(_P)],
+    "lbib_add_membrane_to": [_P, ctypes.c_int32, ctypes.POINTER(lbib_membrane_desc), ctypes.POINTER(ctypes.c_int32)],
+    "lbib_read_instance_velocity": [_P, ctypes.c_int32, _P, _P, ctypes.c_size_t],
+    "lbib_read_instance_populations": [_P, ctypes.c_int32, _P, ctypes.c_size_t],
+    "lbib_write_instance_populations": [_P, ctypes.c_int32, _P, ctypes.c_size_t],
+    "lbib_read_instance_observables": [_P, ctypes.c_int32, ctypes.POINTER(lbib_obs), ctypes.c_size_t,
+                                       ctypes.POINTER(ctypes.c_size_t)],
+    "lbib_read_latest_observables": [_P, ctypes.POINTER(lbib_obs), ctypes.c_size_t],
 }
 
 _lib = None
@@ -137,9 +145,24 @@ def lbib_create(params: lbib_fluid_params) -> ctypes.c_void_p:
     return h
 
 
+def lbib_create_batch(params: lbib_fluid_params, nx, seeds=None) -> ctypes.c_void_p:
+    nxa = np.ascontiguousarray(np.asarray(nx, dtype=np.int32))
+    sa = None if seeds is None else np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+    h = ctypes.c_void_p()
+    _check(load().lbib_create_batch(ctypes.byref(params), len(nxa), _vp(nxa), None if sa is None else _vp(sa),
+                                    ctypes.byref(h)), None)
+    return h
+
+
 def lbib_add_membrane(ctx, desc: lbib_membrane_desc) -> int:
     i = ctypes.c_int32()
     _check(load().lbib_add_membrane(ctx, ctypes.byref(desc), ctypes.byref(i)), ctx)
+    return i.value
+
+
+def lbib_add_membrane_to(ctx, instance: int, desc: lbib_membrane_desc) -> int:
+    i = ctypes.c_int32()
+    _check(load().lbib_add_membrane_to(ctx, int(instance), ctypes.byref(desc), ctypes.byref(i)), ctx)
     return i.value
 
 
@@ -167,17 +190,24 @@ def lbib_lattice_advance_noalloc(params: lbib_fluid_params, f_device_ptr: int, n
 
 
 class Solver:
-    """A context plus its geometry, driven through the C ABI."""
+    """A context plus its geometry, driven through the C ABI.  ``nx`` is one
+    channel length (a single capillary) or a sequence of them (a batch of
+    capillaries sharing ny and the fluid parameters, one Philox seed each:
+    ``seeds`` or seed + i)."""
 
     def __init__(self, nx, ny, tau=1.0, re=1e-2, rho_out=1.0, bc=LBIB_BC_INLET_OUTLET, g=(0.0, 0.0),
-                 storage=LBIB_STORE_FP64, device=0, seed=0, stream: Optional[int] = None, obs_capacity=0):
+                 storage=LBIB_STORE_FP64, device=0, seed=0, stream: Optional[int] = None, obs_capacity=0,
+                 seeds=None):
         self.lib = load()
-        p = lbib_fluid_params(nx=int(nx), ny=int(ny), tau=float(tau), re=float(re), rho_out=float(rho_out),
+        batch = np.ndim(nx) > 0
+        nxs = [int(v) for v in (nx if batch else [nx])]
+        p = lbib_fluid_params(nx=nxs[0], ny=int(ny), tau=float(tau), re=float(re), rho_out=float(rho_out),
                               gx=float(g[0]), gy=float(g[1]), bc_mode=int(bc), storage=int(storage),
                               device=int(device), obs_capacity=int(obs_capacity),
                               cuda_stream=stream, seed=int(seed) & (2**64 - 1))
-        self.nx, self.ny = int(nx), int(ny)
-        self.ctx = lbib_create(p)
+        self.nxs, self.ny = nxs, int(ny)
+        self.nx = nxs[0]
+        self.ctx = lbib_create_batch(p, nxs, seeds) if batch else lbib_create(p)
         self.nv = []
         self.nlig = {}
 
@@ -197,13 +227,14 @@ class Solver:
         _check(status, self.ctx)
 
     # set-up
-    def add_membrane(self, kind, motion, xy, xy_ref=None, ca=1e-3, beta=0.0, ka=1.0, density_ratio=1.0) -> int:
+    def add_membrane(self, kind, motion, xy, xy_ref=None, ca=1e-3, beta=0.0, ka=1.0, density_ratio=1.0,
+                     instance=0) -> int:
         xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(-1))
         ref = None if xy_ref is None else np.ascontiguousarray(np.asarray(xy_ref, dtype=np.float64).reshape(-1))
         d = lbib_membrane_desc(kind=int(kind), motion=int(motion), nv=len(xy) // 2, xy=_dp(xy),
                                xy_ref=_dp(ref) if ref is not None else None, ca=float(ca), beta=float(beta),
                                ka=float(ka), density_ratio=float(density_ratio))
-        i = lbib_add_membrane(self.ctx, d)
+        i = lbib_add_membrane_to(self.ctx, instance, d)
         self.nv.append(len(xy) // 2)
         return i
 
@@ -226,9 +257,9 @@ class Solver:
         return s.value
 
     # reads
-    def velocity(self):
-        ux = np.zeros((self.ny, self.nx)); uy = np.zeros_like(ux)
-        self._c(self.lib.lbib_read_velocity(self.ctx, _vp(ux), _vp(uy), ux.size))
+    def velocity(self, instance=0):
+        ux = np.zeros((self.ny, self.nxs[instance])); uy = np.zeros_like(ux)
+        self._c(self.lib.lbib_read_instance_velocity(self.ctx, int(instance), _vp(ux), _vp(uy), ux.size))
         return ux, uy
 
     def density(self):
@@ -240,22 +271,29 @@ class Solver:
         self._c(self.lib.lbib_read_velocity_device(self.ctx, ctypes.c_void_p(ux_ptr), ctypes.c_void_p(uy_ptr),
                                                    n, dtype))
 
-    def populations(self):
-        f = np.zeros((9, self.ny, self.nx))
-        self._c(self.lib.lbib_read_populations(self.ctx, _vp(f), f.size))
+    def populations(self, instance=0):
+        f = np.zeros((9, self.ny, self.nxs[instance]))
+        self._c(self.lib.lbib_read_instance_populations(self.ctx, int(instance), _vp(f), f.size))
         return f
 
-    def write_populations(self, f):
+    def write_populations(self, f, instance=0):
         f = np.ascontiguousarray(f, dtype=np.float64)
-        assert f.shape == (9, self.ny, self.nx)
-        self._c(self.lib.lbib_write_populations(self.ctx, _vp(f), f.size))
+        assert f.shape == (9, self.ny, self.nxs[instance])
+        self._c(self.lib.lbib_write_instance_populations(self.ctx, int(instance), _vp(f), f.size))
 
-    def observables(self, cap=1 << 16):
+    def observables(self, cap=1 << 16, instance=0):
         buf = (lbib_obs * cap)()
         n = ctypes.c_size_t()
-        self._c(self.lib.lbib_read_observables(self.ctx, buf, cap, ctypes.byref(n)))
+        self._c(self.lib.lbib_read_instance_observables(self.ctx, int(instance), buf, cap, ctypes.byref(n)))
         return [dict(step=o.step, t_star=o.t_star, delta_p=o.delta_p, r=o.r, n_l=o.n_l, n_bound=o.n_bound,
                      status=o.status) for o in buf[:n.value]]
+
+    def latest_observables(self):
+        """Record of the last completed step of every instance (one copy)."""
+        buf = (lbib_obs * len(self.nxs))()
+        self._c(self.lib.lbib_read_latest_observables(self.ctx, buf, len(self.nxs)))
+        return [dict(step=o.step, t_star=o.t_star, delta_p=o.delta_p, r=o.r, n_l=o.n_l, n_bound=o.n_bound,
+                     status=o.status) for o in buf]
 
     def markers(self, body):
         xy = np.zeros(2 * self.nv[body])
@@ -309,11 +347,35 @@ def from_capillary(cap, storage=None, device=0, stream=None, obs_capacity=0) -> 
         st = LBIB_STORE_FP64 if cap.storage == "fp64" else LBIB_STORE_FP32
     s = Solver(cap.nx, cap.ny, tau=cap.tau, re=cap.re, rho_out=cap.rho_out, bc=cap.bc, g=cap.g, storage=st,
                device=device, seed=cap.seed, stream=stream, obs_capacity=obs_capacity)
+    _add_bodies(s, cap, 0)
+    return s
+
+
+def _add_bodies(s: Solver, cap, instance: int) -> None:
     for b in cap.bodies:
-        i = s.add_membrane(b.kind, b.motion, b.xy, b.xy_ref, b.ca, b.beta, b.ka, b.density_ratio)
+        i = s.add_membrane(b.kind, b.motion, b.xy, b.xy_ref, b.ca, b.beta, b.ka, b.density_ratio,
+                           instance=instance)
         if b.adhesion is not None:
             a = b.adhesion
             s.set_adhesion(i, a.n_lig, a.sigma, a.y_cr, a.y_eq, a.kf_dt, a.kr0_dt, a.xi)
+
+
+def from_capillaries(caps, storage=None, device=0, stream=None, obs_capacity=0) -> Solver:
+    """One batched Solver holding every workloads.Capillary of ``caps`` as its
+    instances (same ny, tau, Re, boundary mode, body force and storage; each
+    keeps its own length, bodies and seed)."""
+    c0 = caps[0]
+    for c in caps:
+        if (c.ny, c.tau, c.re, c.rho_out, c.bc, tuple(c.g), c.storage) != \
+                (c0.ny, c0.tau, c0.re, c0.rho_out, c0.bc, tuple(c0.g), c0.storage):
+            raise ValueError("instances of a batch share ny and the fluid parameters")
+    st = storage
+    if st is None:
+        st = LBIB_STORE_FP64 if c0.storage == "fp64" else LBIB_STORE_FP32
+    s = Solver([c.nx for c in caps], c0.ny, tau=c0.tau, re=c0.re, rho_out=c0.rho_out, bc=c0.bc, g=c0.g,
+               storage=st, device=device, stream=stream, obs_capacity=obs_capacity, seeds=[c.seed for c in caps])
+    for k, c in enumerate(caps):
+        _add_bodies(s, c, k)
     return s
 
 
@@ -324,4 +386,4 @@ def roofline_bytes_per_node(storage: int) -> int:
 
 
 __all__ = [n for n in dir() if n.startswith("lbib_") or n.startswith("LBIB_")] + [
-    "Solver", "from_capillary", "load", "library_path", "LbibError", "roofline_bytes_per_node", "FIELDS"]
+    "Solver", "from_capillary", "from_capillaries", "load", "library_path", "LbibError", "roofline_bytes_per_node", "FIELDS"]

@@ -18,6 +18,7 @@ channel").
 from __future__ import annotations
 
 import dataclasses
+import itertools
 import math
 from typing import List, Optional
 
@@ -188,6 +189,50 @@ def production_capillary(seed: int = 0) -> Capillary:
     ]
     return Capillary("capillary 1200x150, globular cell + soft ellipse (AR 0.5), fp32", nx, ny, 1.0,
                      1e-2, 200000, "fp32", seed, bodies)
+
+
+# parameter sweep of Sec. 3.1: particle aspect ratio h / b, particle capillary
+# number (0: rigid), cell shape, and two bond-kinetics seeds
+SWEEP_AR = (0.25, 0.5, 0.75, 1.0)
+SWEEP_CA = (0.0, 1e-4, 5e-4, 1e-3)
+SWEEP_CELLS = ("globular", "biconcave")
+SWEEP_SEEDS = (0, 1)
+
+
+def sweep_capillary(nx: int, ny: int, ar: float, ca: float, cell: str, seed: int,
+                    storage: str = "fp32", cell_markers: int = 256, particle_markers: int = 96,
+                    n_lig: int = 200) -> Capillary:
+    """One capillary of the sweep: a 7 um cell (globular or biconcave) at the
+    release point and a 2 um particle of thickness ar * 2 um on the lower wall
+    (rigid when ca == 0, else deformable with that Ca), 200 ligand sites."""
+    dx = H_UM / ny
+    if cell == "globular":
+        c = circle(cell_markers, CELL_X_UM / dx, CELL_Y_UM / dx, CELL_RADIUS_UM / dx)
+        body_c = Body(CELL, DEFORMABLE, c, ca=1e-3, beta=0.0)
+    else:
+        c = biconcave(cell_markers, CELL_X_UM / dx, CELL_Y_UM / dx, CELL_RADIUS_UM / dx)
+        body_c = Body(CELL, DEFORMABLE, c, ca=1e-3, beta=1e-2)
+    a, b = 0.5 * PARTICLE_LENGTH_UM / dx, 0.5 * ar * PARTICLE_LENGTH_UM / dx
+    part = ellipse(particle_markers, PARTICLE_X_UM / dx, PARTICLE_GAP_UM / dx + b, a, b)
+    if ca == 0.0:
+        body_p = Body(PARTICLE, RIGID, part, ca=0.0, beta=0.0, density_ratio=1.1,
+                      adhesion=_bond_defaults(ny, n_lig, 1.0))
+    else:
+        body_p = Body(PARTICLE, DEFORMABLE, part, ca=ca, beta=1e-2, density_ratio=1.1,
+                      adhesion=_bond_defaults(ny, n_lig, 1.0))
+    name = f"{nx}x{ny} {cell} cell, particle AR {ar} Ca {ca}, seed {seed}"
+    return Capillary(name, nx, ny, 1.0, 1e-2, 200000, storage, seed, [body_c, body_p])
+
+
+def sweep_capillaries(seed: int = 0, ny: int = 150, nx_range=(600, 1600), storage: str = "fp32") -> List[Capillary]:
+    """The 64-capillary sweep: every combination of SWEEP_AR x SWEEP_CA x
+    SWEEP_CELLS x SWEEP_SEEDS, channel lengths drawn uniformly from nx_range
+    (inclusive) with numpy's default generator seeded by ``seed``."""
+    rng = np.random.default_rng(seed)
+    combos = list(itertools.product(SWEEP_AR, SWEEP_CA, SWEEP_CELLS, SWEEP_SEEDS))
+    lengths = rng.integers(nx_range[0], nx_range[1] + 1, size=len(combos))
+    return [sweep_capillary(int(n), ny, ar, ca, cell, s, storage)
+            for n, (ar, ca, cell, s) in zip(lengths, combos)]
 
 
 def scaled(cap: Capillary, nx: int, ny: int) -> Capillary:

@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_2210_06043_gb300 import build, lbib
@@ -94,3 +95,19 @@ def test_create_reports_errors_through_the_boundary():
         lib.lbib_destroy(h)
     else:
         assert st == lbib.LBIB_ERR_CUDA and lib.lbib_last_error(None)
+
+
+def test_create_batch_reports_errors_through_the_boundary():
+    lib = lbib.load()
+    p = lbib.lbib_fluid_params(nx=0, ny=10, tau=1.0, re=0.01, rho_out=1.0)
+    h = ctypes.c_void_p()
+    nx = np.array([40, 2, 50], dtype=np.int32)
+    assert lib.lbib_create_batch(ctypes.byref(p), 3, nx.ctypes.data, None, ctypes.byref(h)) == \
+        lbib.LBIB_ERR_INVALID_ARG
+    assert lib.lbib_create_batch(ctypes.byref(p), 0, nx.ctypes.data, None, ctypes.byref(h)) == \
+        lbib.LBIB_ERR_INVALID_ARG
+    assert lib.lbib_create_batch(ctypes.byref(p), 2, None, None, ctypes.byref(h)) == lbib.LBIB_ERR_INVALID_ARG
+    # 9 * (sum of padded widths) * ny must stay below 2^31
+    big = np.full(4, 1 << 23, dtype=np.int32)
+    assert lib.lbib_create_batch(ctypes.byref(p), 4, big.ctypes.data, None, ctypes.byref(h)) == \
+        lbib.LBIB_ERR_UNSUPPORTED

@@ -83,3 +83,24 @@ def test_small_capillary_is_stable_and_conserves_cell_area():
     assert 0 <= o["n_bound"] <= cap.bodies[1].adhesion.n_lig
     rho, ux, uy = s.macro()
     assert np.all(np.isfinite(ux)) and np.abs(rho - 1).max() < 1e-2
+
+
+def test_sweep_workload_covers_the_parameter_matrix():
+    """64 capillaries: each (AR, Ca, cell, seed) combination of Sec. 3.1's
+    sweep once, lengths within [600, 1600], H = 150; rigid exactly when Ca = 0;
+    particle thickness = AR x length."""
+    caps = wl.sweep_capillaries()
+    assert len(caps) == 64
+    seen = set()
+    for c in caps:
+        assert 600 <= c.nx <= 1600 and c.ny == 150 and c.storage == "fp32"
+        cell, part = c.bodies
+        ext = part.xy.max(0) - part.xy.min(0)
+        ar = round(float(ext[1] / ext[0]), 2)
+        shape = "globular" if np.ptp(np.hypot(*(cell.xy - cell.xy.mean(0)).T)) < 1e-6 else "biconcave"
+        seen.add((ar, part.ca, shape, c.seed))
+        assert (part.motion == wl.RIGID) == (part.ca == 0.0)
+        assert part.adhesion.n_lig == 200
+    assert seen == {(ar, ca, cell, s) for ar in wl.SWEEP_AR for ca in wl.SWEEP_CA for cell in wl.SWEEP_CELLS
+                    for s in wl.SWEEP_SEEDS}
+    assert wl.sweep_capillaries()[5].nx == caps[5].nx  # seeded
