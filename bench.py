@@ -228,6 +228,7 @@ def plain_solver(caps, local, steps, warmup):
     for c in caps:
         st = torch.cuda.Stream()
         s = lbib.from_capillary(c, device=local, stream=st.cuda_stream)
+        s.autotune(steps_per_trial=10)
         s.advance(warmup)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         st.synchronize()
@@ -259,6 +260,7 @@ def run_gpu(args):
     make = (lambda **kw: lbib.from_capillaries(caps, **kw)) if batch else \
         (lambda **kw: lbib.from_capillary(caps[0], **kw))
     s = make(device=local, stream=stream.cuda_stream)
+    tuned = s.autotune(steps_per_trial=args.tune_steps)  # leaves the state unchanged
     s.set_profiling(True)
     # populations beyond L2 (sweep): no flush; else a 256 MiB buffer rewritten between steps
     pop_bytes = 2 * 9 * 4 * nodes
@@ -351,6 +353,7 @@ def run_gpu(args):
             "kernel_ms": {"bulk_lattice": bulk_ms, "lagrangian": lag_ms, "near_lattice": near_ms},
             "near_tiles": desc["near_tiles"], "tiles": desc["tiles"],
             "roofline": roofline, "e2e": e2e, "gpu_launches": 3 * K, "clocks": clk,
+            "launch_config": dict(tuned, chosen_by=f"lbib_autotune, {args.tune_steps} steps per trial"),
             "wall_s_timed_region": wall}
     if batch:
         t_plain = plain_solver(caps, local, args.plain_steps, 3)
@@ -362,8 +365,8 @@ def run_gpu(args):
             "speedup_vs_plain_solver": sum(t_plain) / t_batch,
             "plain_solver_ms_per_step": {"mean": 1e3 * statistics.mean(t_plain), "min": 1e3 * min(t_plain),
                                          "max": 1e3 * max(t_plain)},
-            "plain_solver": f"each capillary alone in its own context (same kernels), {args.plain_steps} steps "
-                            f"after 3 warm-up steps, warm L2, CUDA events",
+            "plain_solver": f"each capillary alone in its own context (same kernels, autotuned), "
+                            f"{args.plain_steps} steps after 3 warm-up steps, warm L2, CUDA events",
             "accuracy": "every instance bit-identical to its lone run (tests/test_gpu_batch.py)"}
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(caps, args.cpu_nodes)
@@ -384,6 +387,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=50, help="steps per capillary of the plain-solver timing")
     ap.add_argument("--cpu-nodes", type=float, default=1.0e8,
                     help="node updates of the CPU oracle sample (about 15 s at 7 MLUPS)")
+    ap.add_argument("--tune-steps", type=int, default=20, help="steps per autotuner trial")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -256,6 +256,39 @@ lbib_status lbib_load_state(lbib_ctx* ctx, const void* buf, size_t bytes);
 lbib_status lbib_set_profiling(lbib_ctx* ctx, int32_t enable);
 lbib_status lbib_read_kernel_times(lbib_ctx* ctx, float* bulk_ms, float* lagr_ms, float* near_ms);
 
+/* Launch configuration of the time step.  No choice changes a result: every
+ * configuration gives bit-for-bit the same state (the lattice kernels update
+ * each node independently; the membrane kernel's sums follow one fixed order
+ * whatever its block size). */
+typedef struct {
+    int32_t lagrangian_threads; /* threads per membrane block: 256 or 512 */
+    int32_t near_blocks;        /* blocks of the near-membrane lattice kernel, >= 1 */
+    int32_t bulk_tiles_y;       /* 32 x 4 node tiles per bulk lattice block, stacked in y: 1, 2 or 4 */
+    int32_t activation_stride;  /* every k-th element centroid schedules the near tiles around it
+                                 * (over a radius grown to cover the k - 1 between): 1, 2 or 4 */
+} lbib_launch_config;
+
+/* Current configuration.  Like lbib_advance, the call completes the set-up
+ * (no membranes can be added afterwards) and fills in the defaults: membrane
+ * blocks of 256 threads when the bodies outnumber half the SMs (else 512),
+ * near kernel 4 blocks per SM, one tile per bulk block, activation stride 4. */
+lbib_status lbib_get_launch_config(lbib_ctx* ctx, lbib_launch_config* out);
+
+/* Sets the configuration used by the following steps (re-captures the step
+ * graphs); LBIB_ERR_INVALID_ARG for values outside the ranges above. */
+lbib_status lbib_set_launch_config(lbib_ctx* ctx, const lbib_launch_config* cfg);
+
+/* Autotuner (no counterpart in the paper; the launch shapes are this
+ * implementation's).  Times candidate configurations on the context's own
+ * state: a device snapshot of the state is taken, each candidate advances it
+ * by steps_per_trial >= 1 steps (after two warm-up steps) timed with CUDA
+ * events, the snapshot is restored, and the fastest candidate is kept.  The
+ * search is coordinate-wise: bulk tiles per block, then membrane block size,
+ * then activation stride, then near-kernel blocks.  On return the state, the step count and the
+ * observables cursors are as on entry; *chosen (may be NULL) receives the
+ * configuration.  Needs device memory for one more copy of the state. */
+lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_config* chosen);
+
 /* Launch counts per step and geometry the bench reports. */
 lbib_status lbib_describe(lbib_ctx* ctx, int32_t* kernels_per_step, int32_t* near_tiles, int32_t* tiles);
 

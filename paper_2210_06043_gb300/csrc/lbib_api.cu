@@ -103,7 +103,7 @@ struct lbib_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t pe[6] = {};
     bool profiling = false, profiled_last = false;
-    int near_grid = 1;
+    int near_grid = 0;  // 0: default, set at finalize
     std::vector<void*> allocs;
     double* macro_buf = nullptr;
     int device = 0;
@@ -187,15 +187,17 @@ lbib_status capture_unit(lbib_ctx* ctx, int prof, int p)
     auto rec = [&](int i, cudaStream_t s) {
         if (prof && e == cudaSuccess) e = cudaEventRecordWithFlags(ctx->pe[i], s, cudaEventRecordExternal);
     };
+    // the membrane kernel is enqueued first so that its blocks are resident
+    // before the bulk lattice blocks fill the SMs
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_fork, ctx->cap);
+    rec(2, ctx->cap);
+    if (e == cudaSuccess) e = launch_lagrangian(d, ctx->prec, p, ctx->cap);
+    rec(3, ctx->cap);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
     rec(0, ctx->side);
     if (e == cudaSuccess) e = launch_lbm_bulk(d, ctx->prec, p, ctx->side);
     rec(1, ctx->side);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
-    rec(2, ctx->cap);
-    if (e == cudaSuccess) e = launch_lagrangian(d, ctx->prec, p, ctx->cap);
-    rec(3, ctx->cap);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap, ctx->ev_join, 0);
     rec(4, ctx->cap);
     if (e == cudaSuccess) e = launch_lbm_near(d, ctx->prec, p, ctx->near_grid, ctx->cap);
@@ -423,9 +425,9 @@ lbib_status finalize(lbib_ctx* ctx)
     for (int b = 0; b < nb; ++b) {
         const double lmax = inst_lmax[bc[b].inst];
         bc[b].r_act = 2.0 + std::max(1.2, 0.75 * lmax) + 1.0;
-        // a centroid lies within ACT_STRIDE / 2 elements of an activating one; 1.5 l_max
+        // a centroid lies within stride / 2 elements of an activating one; 1.5 l_max
         // per element allows 50% stretching
-        bc[b].r_act_sub = bc[b].r_act + 0.5 * ACT_STRIDE * 1.5 * lmax;
+        bc[b].act_reach = 0.5 * 1.5 * lmax;
     }
     d.ring_cap = ctx->P.obs_capacity > 0 ? ctx->P.obs_capacity : 4096;
 
@@ -483,6 +485,14 @@ lbib_status finalize(lbib_ctx* ctx)
     }
     if (nb) CK(cudaMemcpy(dbody, bc.data(), bc.size() * sizeof(BodyConst), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->inst, ic.data(), ic.size() * sizeof(InstConst), cudaMemcpyHostToDevice));
+    {
+        // tile-column table with the instances' first markers, now known
+        std::vector<int4> cols;
+        for (int i = 0; i < ni; ++i)
+            for (int c = 0; c < (ic[i].nx + TX - 1) / TX; ++c)
+                cols.push_back(make_int4(ic[i].x0, ic[i].nx, ic[i].moff, i));
+        CK(cudaMemcpy(ctx->colinfo, cols.data(), cols.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    }
     CK(cudaMemcpy(d.rigid, rig.data(), rig.size() * 8, cudaMemcpyHostToDevice));
     CK(up_real(dl0, l0));
     CK(up_real(dth0, th0));
@@ -509,7 +519,13 @@ lbib_status finalize(lbib_ctx* ctx)
         CK(configure_kernels(ctx->prec, d.nv_max));
         CK(launch_activate(d, ctx->prec, ctx->s_f, 3, ctx->stream));
     }
-    ctx->near_grid = std::max(1, std::min(L.ntiles, 4 * 152));
+    int nsm = 152;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    // default launch shapes (lbib_set_launch_config / lbib_autotune may change them):
+    // membrane blocks of 256 threads once the bodies outnumber half the SMs, so that
+    // they share SMs with the bulk lattice update; near kernel 4 blocks per SM
+    if (!d.lag_threads) d.lag_threads = (nb > nsm / 2) ? 256 : 512;
+    if (!ctx->near_grid) ctx->near_grid = std::max(1, std::min(L.ntiles, 4 * nsm));
     ctx->finalized = true;
     if (nb) {
         lbib_status s = ensure_graphs(ctx);
@@ -584,7 +600,7 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
         ctx->inst_nx.push_back(nxs[i]);
         ctx->inst_seed.push_back(seeds ? seeds[i] : P->seed + (uint64_t)i);
         const int w = (nxs[i] + TX - 1) / TX;
-        for (int c = 0; c < w; ++c) cols.push_back(make_int4(x0, nxs[i], 0, i));
+        for (int c = 0; c < w; ++c) cols.push_back(make_int4(x0, nxs[i], 0, i));  // moff set once bodies are known
         x0 += w * TX;
     }
     ctx->obs_consumed.assign(ninst, 0);
@@ -612,6 +628,9 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     d.uscale = L.umax / P->ny;
     d.ring_cap = 1;
     d.ninst = ninst;
+    d.lag_threads = 0;  // 0: default, set at finalize
+    d.bulk_tiles_y = 1;
+    d.act_stride = ACT_STRIDE;
     auto bail = [&](lbib_status s) {
         std::string m = ctx->err;
         lbib_destroy(ctx);
@@ -630,6 +649,8 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     CKC(dalloc(reg, reinterpret_cast<char**>(&d.drho), nn * ctx->rsz));
     CKC(dalloc(reg, reinterpret_cast<char**>(&d.ux), nn * ctx->rsz));
     CKC(dalloc(reg, reinterpret_cast<char**>(&d.uy), nn * ctx->rsz));
+    CKC(dalloc(reg, reinterpret_cast<char**>(&d.fx), nn * ctx->rsz));
+    CKC(dalloc(reg, reinterpret_cast<char**>(&d.fy), nn * ctx->rsz));
     CKC(dalloc(reg, &d.fresh, L.ntiles));
     CKC(dalloc(reg, &d.nearflag[0], L.ntiles));
     CKC(dalloc(reg, &d.nearflag[1], L.ntiles));
@@ -649,6 +670,8 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     CKC(cudaMemset(d.drho, 0, nn * ctx->rsz));
     CKC(cudaMemset(d.ux, 0, nn * ctx->rsz));
     CKC(cudaMemset(d.uy, 0, nn * ctx->rsz));
+    CKC(cudaMemset(d.fx, 0, nn * ctx->rsz));
+    CKC(cudaMemset(d.fy, 0, nn * ctx->rsz));
     CKC(cudaMemset(d.fresh, 0x80, L.ntiles * 4));  // matches no step
     CKC(cudaMemset(d.nearflag[0], 0, L.ntiles * 4));
     CKC(cudaMemset(d.nearflag[1], 0, L.ntiles * 4));
@@ -1057,8 +1080,10 @@ lbib_status lbib_read_bonds(lbib_ctx* ctx, int32_t id, int32_t* bound, double* a
 }
 
 // ------------------------------------------------------------- checkpoints
-// layout: header | populations f*^{s-1} | X^s | X^{s-1} | rigid | bonds |
-//         anchors | markers for lattice step s | extents of X^s
+// layout: header | populations f*^{s-1} | force density of the near tiles and
+//         their step stamps | X^s | X^{s-1} | X^s as compute-type pairs |
+//         rigid | bonds | anchors | markers for lattice step s | extents of
+//         X^s | per-vertex diagnostics and bond margins of the last step
 namespace {
 struct CkHeader {
     uint64_t magic;
@@ -1066,15 +1091,17 @@ struct CkHeader {
     int64_t steps;
     int32_t ninst, pad;
 };
-constexpr uint64_t kMagic = 0x324b4350424942ULL;  // "BIBPCK2"
+constexpr uint64_t kMagic = 0x334b4350424942ULL;  // "BIBPCK3"
 
 size_t state_bytes(const lbib_ctx* ctx)
 {
     const Dev& d = ctx->d;
     size_t nq = (size_t)9 * d.L.qstride;
     size_t nm = std::max(d.nmark, 1), nl = std::max(d.nlig, 1), nb = std::max(d.nbodies, 1);
-    return sizeof(CkHeader) + nq * ctx->rsz + 4 * nm * 8 + nb * RG_N * 8 + nl * 4 + 2 * nl * 8 + 2 * nm * 4 +
-           4 * nm * ctx->rsz + nb * BO_N * 8;
+    size_t nn = (size_t)d.L.qstride;
+    return sizeof(CkHeader) + nq * ctx->rsz + 2 * nn * ctx->rsz + (size_t)d.L.ntiles * 4 + 4 * nm * 8 +
+           4 * nm * ctx->rsz + nb * RG_N * 8 + nl * 4 + 2 * nl * 8 + 2 * nm * 4 + 4 * nm * ctx->rsz + nb * BO_N * 8 +
+           (size_t)NDIAG * nm * ctx->rsz + nl * ctx->rsz;
 }
 }  // namespace
 
@@ -1088,52 +1115,54 @@ lbib_status lbib_state_size(lbib_ctx* ctx, size_t* bytes)
     return LBIB_OK;
 }
 
-lbib_status lbib_save_state(lbib_ctx* ctx, void* buf, size_t bytes)
+}  // extern "C"
+
+namespace {
+
+// Copies the context state into buf (host or device memory, `kind` the
+// direction of every copy) in the layout above.  Everything a later step or
+// read uses is saved exactly, so a restored context continues bit for bit.
+lbib_status save_into(lbib_ctx* ctx, char* p, cudaMemcpyKind kind)
 {
-    if (!ctx || !buf) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
-    DeviceGuard guard(ctx->device);
-    lbib_status s = pre_read(ctx);
-    if (s != LBIB_OK) return s;
-    if (bytes < state_bytes(ctx)) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than lbib_state_size");
     const Dev& d = ctx->d;
     const int64_t st = ctx->s_f;
-    char* p = static_cast<char*>(buf);
     CkHeader h{kMagic, d.L.nx, d.L.ny, d.nbodies, d.nmark, d.nlig, ctx->prec, st, ctx->ninst, 0};
-    std::memcpy(p, &h, sizeof(h));
+    if (kind == cudaMemcpyDeviceToHost) std::memcpy(p, &h, sizeof(h));
+    else CK(cudaMemcpy(p, &h, sizeof(h), cudaMemcpyHostToDevice));
     p += sizeof(h);
     size_t nq = (size_t)9 * d.L.qstride;
     size_t nm = std::max(d.nmark, 1), nl = std::max(d.nlig, 1), nb = std::max(d.nbodies, 1);
-    CK(cudaMemcpy(p, d.f[st & 1], nq * ctx->rsz, cudaMemcpyDeviceToHost));
-    p += nq * ctx->rsz;
-    CK(cudaMemcpy(p, d.pos[st & 1], 2 * nm * 8, cudaMemcpyDeviceToHost));
-    p += 2 * nm * 8;
-    CK(cudaMemcpy(p, d.pos[(st + 1) & 1], 2 * nm * 8, cudaMemcpyDeviceToHost));
-    p += 2 * nm * 8;
-    CK(cudaMemcpy(p, d.rigid, nb * RG_N * 8, cudaMemcpyDeviceToHost));
-    p += nb * RG_N * 8;
-    CK(cudaMemcpy(p, d.bound, nl * 4, cudaMemcpyDeviceToHost));
-    p += nl * 4;
-    CK(cudaMemcpy(p, d.anchor, 2 * nl * 8, cudaMemcpyDeviceToHost));
-    p += 2 * nl * 8;
-    CK(cudaMemcpy(p, d.mki[st & 1], 2 * nm * 4, cudaMemcpyDeviceToHost));
-    p += 2 * nm * 4;
-    CK(cudaMemcpy(p, d.mkf[st & 1], 4 * nm * ctx->rsz, cudaMemcpyDeviceToHost));
-    p += 4 * nm * ctx->rsz;
-    CK(cudaMemcpy(p, d.body_obs[st & 1], nb * BO_N * 8, cudaMemcpyDeviceToHost));
+    auto put = [&](const void* src, size_t n) -> cudaError_t {
+        cudaError_t e = cudaMemcpy(p, src, n, kind);
+        p += n;
+        return e;
+    };
+    const size_t nn = (size_t)d.L.qstride;
+    CK(put(d.f[st & 1], nq * ctx->rsz));
+    CK(put(d.fx, nn * ctx->rsz));
+    CK(put(d.fy, nn * ctx->rsz));
+    CK(put(d.fresh, (size_t)d.L.ntiles * 4));
+    CK(put(d.pos[st & 1], 2 * nm * 8));
+    CK(put(d.pos[(st + 1) & 1], 2 * nm * 8));
+    CK(put(d.posf[st & 1], 4 * nm * ctx->rsz));
+    CK(put(d.rigid, nb * RG_N * 8));
+    CK(put(d.bound, nl * 4));
+    CK(put(d.anchor, 2 * nl * 8));
+    CK(put(d.mki[st & 1], 2 * nm * 4));
+    CK(put(d.mkf[st & 1], 4 * nm * ctx->rsz));
+    CK(put(d.body_obs[st & 1], nb * BO_N * 8));
+    CK(put(d.diag, (size_t)NDIAG * nm * ctx->rsz));
+    CK(put(d.margin, nl * ctx->rsz));
     return LBIB_OK;
 }
 
-lbib_status lbib_load_state(lbib_ctx* ctx, const void* buf, size_t bytes)
+// Restores a state written by save_into (kind: direction of the copies).
+lbib_status load_from(lbib_ctx* ctx, const char* p, cudaMemcpyKind kind)
 {
-    if (!ctx || !buf) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
-    DeviceGuard guard(ctx->device);
-    lbib_status s = pre_read(ctx);
-    if (s != LBIB_OK && s != LBIB_ERR_DIVERGED && s != LBIB_ERR_STATE) return s;
-    if (bytes < state_bytes(ctx)) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than lbib_state_size");
     Dev& d = ctx->d;
-    const char* p = static_cast<const char*>(buf);
     CkHeader h;
-    std::memcpy(&h, p, sizeof(h));
+    if (kind == cudaMemcpyHostToDevice) std::memcpy(&h, p, sizeof(h));
+    else CK(cudaMemcpy(&h, p, sizeof(h), cudaMemcpyDeviceToHost));
     p += sizeof(h);
     if (h.magic != kMagic || h.nx != d.L.nx || h.ny != d.L.ny || h.nbodies != d.nbodies || h.nmark != d.nmark ||
         h.nlig != d.nlig || h.prec != ctx->prec || h.steps < 0 || h.ninst != ctx->ninst)
@@ -1141,34 +1170,33 @@ lbib_status lbib_load_state(lbib_ctx* ctx, const void* buf, size_t bytes)
     const int64_t st = h.steps;
     size_t nq = (size_t)9 * d.L.qstride;
     size_t nm = std::max(d.nmark, 1), nl = std::max(d.nlig, 1), nb = std::max(d.nbodies, 1);
-    CK(cudaMemcpy(d.f[st & 1], p, nq * ctx->rsz, cudaMemcpyHostToDevice));
-    p += nq * ctx->rsz;
-    CK(cudaMemcpy(d.pos[st & 1], p, 2 * nm * 8, cudaMemcpyHostToDevice));
-    p += 2 * nm * 8;
-    CK(cudaMemcpy(d.pos[(st + 1) & 1], p, 2 * nm * 8, cudaMemcpyHostToDevice));
-    p += 2 * nm * 8;
-    for (int k = 0; k < 2; ++k) {
-        lbib_status sp = upload_posf(ctx, k);
-        if (sp != LBIB_OK) return sp;
-    }
-    CK(cudaMemcpy(d.rigid, p, nb * RG_N * 8, cudaMemcpyHostToDevice));
-    p += nb * RG_N * 8;
-    CK(cudaMemcpy(d.bound, p, nl * 4, cudaMemcpyHostToDevice));
-    p += nl * 4;
-    CK(cudaMemcpy(d.anchor, p, 2 * nl * 8, cudaMemcpyHostToDevice));
-    p += 2 * nl * 8;
-    CK(cudaMemcpy(d.mki[st & 1], p, 2 * nm * 4, cudaMemcpyHostToDevice));
-    p += 2 * nm * 4;
-    CK(cudaMemcpy(d.mkf[st & 1], p, 4 * nm * ctx->rsz, cudaMemcpyHostToDevice));
-    p += 4 * nm * ctx->rsz;
-    CK(cudaMemcpy(d.body_obs[st & 1], p, nb * BO_N * 8, cudaMemcpyHostToDevice));
+    auto get = [&](void* dst, size_t n) -> cudaError_t {
+        cudaError_t e = cudaMemcpy(dst, p, n, kind);
+        p += n;
+        return e;
+    };
+    const size_t nn = (size_t)d.L.qstride;
+    CK(get(d.f[st & 1], nq * ctx->rsz));
+    CK(get(d.fx, nn * ctx->rsz));
+    CK(get(d.fy, nn * ctx->rsz));
+    CK(get(d.fresh, (size_t)d.L.ntiles * 4));
+    CK(get(d.pos[st & 1], 2 * nm * 8));
+    CK(get(d.pos[(st + 1) & 1], 2 * nm * 8));
+    CK(get(d.posf[st & 1], 4 * nm * ctx->rsz));  // the next membrane update reads these pairs
+    CK(get(d.rigid, nb * RG_N * 8));
+    CK(get(d.bound, nl * 4));
+    CK(get(d.anchor, 2 * nl * 8));
+    CK(get(d.mki[st & 1], 2 * nm * 4));
+    CK(get(d.mkf[st & 1], 4 * nm * ctx->rsz));
+    CK(get(d.body_obs[st & 1], nb * BO_N * 8));
+    CK(get(d.diag, (size_t)NDIAG * nm * ctx->rsz));
+    CK(get(d.margin, nl * ctx->rsz));
     // scheduling state is rebuilt from the restored positions and markers
     const Lattice& L = d.L;
     CK(cudaMemset(d.nearflag[0], 0, L.ntiles * 4));
     CK(cudaMemset(d.nearflag[1], 0, L.ntiles * 4));
     CK(cudaMemset(d.mask[0], 0, (size_t)L.ntiles * d.mw * 4));
     CK(cudaMemset(d.mask[1], 0, (size_t)L.ntiles * d.mw * 4));
-    CK(cudaMemset(d.fresh, 0x80, L.ntiles * 4));
     CK(cudaMemset(d.count, 0, 12));
     CK(cudaMemset(d.status, 0, 4));
     CK(cudaMemset(d.ticket, 0, 4));
@@ -1182,6 +1210,200 @@ lbib_status lbib_load_state(lbib_ctx* ctx, const void* buf, size_t bytes)
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return check_status(ctx);
+}
+
+bool valid_config(const lbib_launch_config& c)
+{
+    return (c.lagrangian_threads == 256 || c.lagrangian_threads == 512) && c.near_blocks >= 1 &&
+           (c.bulk_tiles_y == 1 || c.bulk_tiles_y == 2 || c.bulk_tiles_y == 4) &&
+           (c.activation_stride == 1 || c.activation_stride == 2 || c.activation_stride == 4);
+}
+
+lbib_launch_config current_config(const lbib_ctx* ctx)
+{
+    lbib_launch_config c{};
+    c.lagrangian_threads = ctx->d.lag_threads;
+    c.near_blocks = ctx->near_grid;
+    c.bulk_tiles_y = ctx->d.bulk_tiles_y;
+    c.activation_stride = ctx->d.act_stride;
+    return c;
+}
+
+void destroy_graphs(lbib_ctx* ctx)
+{
+    for (auto& row : ctx->unit)
+        for (auto& g : row)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+}
+
+void apply_config(lbib_ctx* ctx, const lbib_launch_config& c)
+{
+    destroy_graphs(ctx);
+    ctx->d.lag_threads = c.lagrangian_threads;
+    ctx->near_grid = c.near_blocks;
+    ctx->d.bulk_tiles_y = c.bulk_tiles_y;
+    ctx->d.act_stride = c.activation_stride;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbib_status lbib_save_state(lbib_ctx* ctx, void* buf, size_t bytes)
+{
+    if (!ctx || !buf) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = pre_read(ctx);
+    if (s != LBIB_OK) return s;
+    if (bytes < state_bytes(ctx)) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than lbib_state_size");
+    return save_into(ctx, static_cast<char*>(buf), cudaMemcpyDeviceToHost);
+}
+
+lbib_status lbib_load_state(lbib_ctx* ctx, const void* buf, size_t bytes)
+{
+    if (!ctx || !buf) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = pre_read(ctx);
+    if (s != LBIB_OK && s != LBIB_ERR_DIVERGED && s != LBIB_ERR_STATE) return s;
+    if (bytes < state_bytes(ctx)) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than lbib_state_size");
+    return load_from(ctx, static_cast<const char*>(buf), cudaMemcpyHostToDevice);
+}
+
+lbib_status lbib_get_launch_config(lbib_ctx* ctx, lbib_launch_config* out)
+{
+    if (!ctx || !out) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = finalize(ctx);
+    if (s != LBIB_OK) return s;
+    *out = current_config(ctx);
+    return LBIB_OK;
+}
+
+lbib_status lbib_set_launch_config(lbib_ctx* ctx, const lbib_launch_config* cfg)
+{
+    if (!ctx || !cfg) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    if (!valid_config(*cfg)) return fail(ctx, LBIB_ERR_INVALID_ARG, "launch configuration out of range");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = finalize(ctx);
+    if (s != LBIB_OK) return s;
+    s = finish_pending(ctx);
+    if (s != LBIB_OK) return s;
+    CK(cudaStreamSynchronize(ctx->stream));
+    apply_config(ctx, *cfg);
+    return LBIB_OK;
+}
+
+lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_config* chosen)
+{
+    if (!ctx) return fail(ctx, LBIB_ERR_INVALID_ARG, "null context");
+    if (steps_per_trial < 1) return fail(ctx, LBIB_ERR_INVALID_ARG, "steps_per_trial < 1");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = pre_read(ctx);
+    if (s != LBIB_OK) return s;
+    Dev& d = ctx->d;
+    // device snapshot of the state, the observables rings and the cursors
+    const size_t sb = state_bytes(ctx);
+    const size_t rb = (size_t)ctx->ninst * d.ring_cap * sizeof(lbib_obs);
+    char* snap = nullptr;
+    lbib_obs* ring = nullptr;
+    CK(cudaMalloc(&snap, sb));
+    cudaError_t e = cudaMalloc(&ring, std::max<size_t>(rb, 1));
+    if (e != cudaSuccess) {
+        cudaFree(snap);
+        return cuda_fail(ctx, e, "cudaMalloc");
+    }
+    const std::vector<int64_t> cursors = ctx->obs_consumed;
+    const lbib_launch_config entry = current_config(ctx);
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+    cudaEvent_t a = nullptr, b = nullptr;
+    auto cleanup = [&]() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        cudaFree(snap);
+        cudaFree(ring);
+    };
+    s = save_into(ctx, snap, cudaMemcpyDeviceToDevice);
+    if (s == LBIB_OK && rb) {
+        e = cudaMemcpy(ring, d.ring, rb, cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) s = cuda_fail(ctx, e, "ring snapshot");
+    }
+    if (s == LBIB_OK && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess))
+        s = cuda_fail(ctx, cudaErrorUnknown, "cudaEventCreate");
+    // one trial: restore, two warm-up steps, time steps_per_trial steps
+    auto trial = [&](const lbib_launch_config& c, float* ms) -> lbib_status {
+        apply_config(ctx, c);
+        lbib_status t = load_from(ctx, snap, cudaMemcpyDeviceToDevice);
+        if (t != LBIB_OK) return t;
+        t = lbib_advance(ctx, 2);
+        if (t != LBIB_OK) return t;
+        CK(cudaEventRecord(a, ctx->stream));
+        t = lbib_advance(ctx, steps_per_trial);
+        if (t != LBIB_OK) return t;
+        t = finish_pending(ctx);
+        if (t != LBIB_OK) return t;
+        CK(cudaEventRecord(b, ctx->stream));
+        CK(cudaEventSynchronize(b));
+        CK(cudaEventElapsedTime(ms, a, b));
+        return check_status(ctx);
+    };
+    lbib_launch_config best = entry;
+    float best_ms = 0.f;
+    if (s == LBIB_OK) s = trial(best, &best_ms);
+    auto consider = [&](lbib_launch_config c) {
+        if (s != LBIB_OK || !valid_config(c)) return;
+        if (c.lagrangian_threads == best.lagrangian_threads && c.near_blocks == best.near_blocks &&
+            c.bulk_tiles_y == best.bulk_tiles_y && c.activation_stride == best.activation_stride)
+            return;
+        float ms = 0.f;
+        s = trial(c, &ms);
+        if (s == LBIB_OK && ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    };
+    const lbib_launch_config start = best;
+    for (int rt : {1, 2, 4}) {
+        lbib_launch_config c = start;
+        c.bulk_tiles_y = rt;
+        consider(c);
+    }
+    if (d.nbodies) {
+        const lbib_launch_config after_bulk = best;
+        for (int lt : {256, 512}) {
+            lbib_launch_config c = after_bulk;
+            c.lagrangian_threads = lt;
+            consider(c);
+        }
+        const lbib_launch_config after_lag = best;
+        for (int stride : {1, 2, 4}) {
+            lbib_launch_config c = after_lag;
+            c.activation_stride = stride;
+            consider(c);
+        }
+        const lbib_launch_config after_stride = best;
+        for (int per_sm : {2, 4, 8, 12}) {
+            lbib_launch_config c = after_stride;
+            c.near_blocks = per_sm * nsm;
+            consider(c);
+        }
+    }
+    // back to the entry state with the chosen configuration
+    if (s == LBIB_OK) {
+        apply_config(ctx, best);
+        s = load_from(ctx, snap, cudaMemcpyDeviceToDevice);
+    }
+    if (s == LBIB_OK && rb) {
+        e = cudaMemcpy(d.ring, ring, rb, cudaMemcpyDeviceToDevice);
+        if (e != cudaSuccess) s = cuda_fail(ctx, e, "ring restore");
+    }
+    ctx->obs_consumed = cursors;
+    cleanup();
+    if (s == LBIB_OK && chosen) *chosen = best;
+    return s;
 }
 
 lbib_status lbib_set_profiling(lbib_ctx* ctx, int32_t enable)
@@ -1230,9 +1452,7 @@ void lbib_destroy(lbib_ctx* ctx)
     if (!ctx) return;
     DeviceGuard guard(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    for (auto& row : ctx->unit)
-        for (auto& g : row)
-            if (g) cudaGraphExecDestroy(g);
+    destroy_graphs(ctx);
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);

@@ -37,8 +37,8 @@ constexpr int TX = 32;            // tile width (nodes along x) = one warp
 constexpr int TY = 4;             // tile height
 constexpr int MAX_BODIES = 16;
 constexpr int MAX_NV = 1024;      // vertices per body
-constexpr int LAG_THREADS = 512;  // threads of the Lagrangian kernel's blocks
-constexpr int ACT_STRIDE = 4;     // near-tile activation from every ACT_STRIDE-th marker
+constexpr int LAG_THREADS = 512;  // default threads of the Lagrangian kernel's blocks (256 or 512)
+constexpr int ACT_STRIDE = 4;     // default: near-tile activation from every 4th element centroid
 constexpr int NDIAG = LBIB_FIELD_COUNT;
 
 // device status bits (host maps them to lbib_status)
@@ -87,7 +87,8 @@ struct BodyConst {
     int sigma_inf, inst, x0, nxi;     // instance and its node columns [x0, x0 + nxi)
     int moff, lig0, b0, nbi;          // instance's first marker, first site, first body, body count
     double A0, P0, inv_A0, inv_P0;
-    double r_act, r_act_sub;          // the instance's activation radii (see Dev)
+    double r_act;                     // the instance's activation radius (lattice units)
+    double act_reach;                 // added to r_act per element of activation stride
     double ks, kb, ka, mv, mass, inertia;
     double sigma, ycr, yeq, Pf, kr0_dt, xi;
 };
@@ -106,6 +107,8 @@ struct Dev {
     void* drho;                // Real [ny][nxp]: rho - 1 on near tiles
     void* ux;                  // Real [ny][nxp]
     void* uy;                  // Real [ny][nxp]
+    void* fx;                  // Real [ny][nxp]: total force density (g + F_E) the near update used
+    void* fy;                  // Real [ny][nxp]
     int32_t* fresh;            // [ntiles]: lattice step whose near update wrote rho/u
     uint32_t* nearflag[2];     // [ntiles]: tile is near for lattice steps of this parity
     int32_t* list[3];          // [list_cap]: near tiles of lattice step m, m % 3
@@ -123,6 +126,8 @@ struct Dev {
     uint32_t* inst_ticket;     // [ninst] Lagrangian blocks of the instance done this step
     // Lagrangian state
     int nbodies, nmark, nlig, nv_max;
+    int lag_threads;           // Lagrangian block size: 256 or 512 (results do not depend on it)
+    int bulk_tiles_y;          // tiles per bulk-kernel block, stacked in y: 1, 2 or 4 (likewise)
     double* pos[2];            // [2][nmark] (x block then y block); X^n in pos[n & 1]
     void* posf[2];             // Real [4][nmark]: X^n as float-float pairs (x hi, x lo, y hi, y lo)
     const BodyConst* body;     // [nbodies]
@@ -143,9 +148,9 @@ struct Dev {
     int64_t* step;             // Lagrangian step counter n (advanced by the last Lagrangian block)
     uint32_t* status;
     uint32_t* ticket;
-    // activation radius around markers (lattice units) and the radius used by
-    // every ACT_STRIDE-th marker (covers the ones between) are per instance:
-    // BodyConst::r_act, BodyConst::r_act_sub
+    // activation radius around markers (lattice units) per instance: BodyConst::r_act;
+    // every act_stride-th element centroid activates r_act + act_stride * act_reach
+    int act_stride;            // 1, 2 or 4 (results do not depend on it)
     double dcut;               // repulsion cut-off (Eq. 12)
     double probe;              // probe length (Sec. 2.6)
     double uscale;             // observables: u_max / H

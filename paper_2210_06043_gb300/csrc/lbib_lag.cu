@@ -286,13 +286,37 @@ __device__ __forceinline__ int box_tiles(const Lattice& L, int i0, int i1, int j
     return n;
 }
 
-template <typename R, int K>
-__global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
+// Sums of per-vertex terms are laid out over VLANES virtual lanes (vertex v
+// in lane v % VLANES, each lane summing its vertices in ascending order) and
+// combined by one fixed shuffle tree, whatever the block size T: a thread of
+// a T-thread block holds VL = VLANES / T lanes.  So T changes no result.
+constexpr int VLANES = 512;
+
+template <typename V, int VL>
+__device__ __forceinline__ V vlane_sum(V (&acc)[VL], V* scratch)  // scratch: >= VLANES / 32 elements
 {
+    constexpr int W = VLANES / VL / 32;  // warps of the block
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < VL; ++j) acc[j] = warp_sum(acc[j]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < VL; ++j) scratch[j * W + wid] = acc[j];
+    __syncthreads();
+    const V t = (lane < VLANES / 32) ? scratch[lane] : V(0);
+    return warp_sum(t);
+}
+
+template <typename R, int K, int T>
+__global__ void __launch_bounds__(T) k_lagrangian(Dev d, int p)
+{
+    static_assert(VLANES % T == 0 && T % 32 == 0, "block size divides the virtual lanes");
+    constexpr int VL = VLANES / T;
     const Lattice& L = d.L;
     const int bi = blockIdx.x;
     const BodyConst& B = d.body[bi];
-    const int nv = B.nv, off = B.off, NM = d.nmark, tid = threadIdx.x, T = blockDim.x;
+    const int nv = B.nv, off = B.off, NM = d.nmark, tid = threadIdx.x;
     const int64_t n = *d.step;
     const int32_t mf = (int32_t)n;  // lattice step whose rho/u the interpolation reads
     const double* __restrict__ Pn = d.pos[n & 1];
@@ -346,11 +370,17 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
 
     // 0. one round of global loads; positions to float-float pairs; the FP64
     //    shoelace terms of X^n (Eq. 11's area) directly from the loaded values
-    double a2 = 0.0;
+    double a2[VL];
+#pragma unroll
+    for (int j = 0; j < VL; ++j) a2[j] = 0.0;
     {
         const R* l0 = static_cast<const R*>(d.l0) + off;
         const R* th0 = static_cast<const R*>(d.th0) + off;
-        for (int v = tid; v < nv; v += T) {
+        for (int v0 = tid; v0 < nv; v0 += VLANES)
+#pragma unroll
+        for (int j = 0; j < VL; ++j) {
+            const int v = v0 + j * T;  // virtual lane tid + j T
+            if (v >= nv) break;
             const int w = (v + 1 == nv) ? 0 : v + 1;
             const double X = Pn[off + v], Y = Pn[NM + off + v];
             const double Xw = Pn[off + w], Yw = Pn[NM + off + w];
@@ -364,15 +394,15 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
             ddy[v] = (R)(Y - Yp);
             sl0[v] = l0[v];
             sth0[v] = th0[v];
-            a2 += X * Yw - Xw * Y;
+            a2[j] += X * Yw - Xw * Y;
         }
         if (tid < RG_N) rig[tid] = d.rigid[bi * RG_N + tid];
         const double* eo = d.body_obs[n & 1] + (size_t)B.b0 * BO_N;  // the instance's bodies
         for (int k = tid; k < 4 * B.nbi; k += T) ext[k >> 2][k & 3] = (R)eo[(k >> 2) * BO_N + BO_XMIN + (k & 3)];
     }
-    const double area = 0.5 * block_sum<double>(a2, dscr[0]);  // FP64 area reduction (Eq. 11)
+    const double area = 0.5 * vlane_sum<double, VL>(a2, dscr[0]);  // FP64 area reduction (Eq. 11)
 
-    // 1. geometry at X^n (the block_sum above synchronised the block)
+    // 1. geometry at X^n (the reduction above synchronised the block)
     for (int l = tid; l < nv; l += T) {
         const int w = (l + 1 == nv) ? 0 : l + 1;
         const R dx = p2_sub<R>(P2<R>{xh[w], xl[w]}, P2<R>{xh[l], xl[l]});
@@ -587,16 +617,22 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
     } else if (B.motion == LBIB_RIGID) {
         const double xc = rig[RG_XC], yc = rig[RG_YC];
         const P2<R> XC = p2_of<R>(xc), YC = p2_of<R>(yc);
-        R sfx = 0, sfy = 0, smz = 0;
-        for (int v = tid; v < nv; v += T) {
-            sfx += ftx[v];
-            sfy += fty[v];
+        R sfx_[VL], sfy_[VL], smz_[VL];
+#pragma unroll
+        for (int j = 0; j < VL; ++j) sfx_[j] = sfy_[j] = smz_[j] = R(0);
+        for (int v0 = tid; v0 < nv; v0 += VLANES)
+#pragma unroll
+        for (int j = 0; j < VL; ++j) {
+            const int v = v0 + j * T;
+            if (v >= nv) break;
+            sfx_[j] += ftx[v];
+            sfy_[j] += fty[v];
             const R rx = p2_sub<R>(P2<R>{xh[v], xl[v]}, XC), ry = p2_sub<R>(P2<R>{yh[v], yl[v]}, YC);
-            smz += rx * fty[v] - ry * ftx[v];
+            smz_[j] += rx * fty[v] - ry * ftx[v];
         }
-        sfx = block_sum<R>(sfx, rscr[0]);
-        sfy = block_sum<R>(sfy, rscr[1]);
-        smz = block_sum<R>(smz, rscr[2]);
+        const R sfx = vlane_sum<R, VL>(sfx_, rscr[0]);
+        const R sfy = vlane_sum<R, VL>(sfy_, rscr[1]);
+        const R smz = vlane_sum<R, VL>(smz_, rscr[2]);
         __syncthreads();
         if (tid == 0) {
             // Eq. 19: u = 2/3 (2 u(t - dt) - 1/2 u(t - 2 dt) + du/dt dt), likewise omega
@@ -650,7 +686,8 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
     const int64_t n2 = n + 2;
     uint32_t* flag2 = d.nearflag[n2 & 1];
     const int c2 = (int)(n2 % 3);
-    const int ra = (int)ceil(B.r_act_sub) + 1;
+    const int stride = d.act_stride;
+    const int ra = (int)ceil(B.r_act + stride * B.act_reach) + 1;
     for (int l0 = tid / K; l0 < nvq; l0 += Q) {
         const bool valid = l0 < nv;
         const int l = valid ? l0 : nv - 1;
@@ -705,10 +742,10 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
                 }
             }
         }
-        if (l % ACT_STRIDE == 0 || l == nv - 1) {
+        if (l % stride == 0 || l == nv - 1) {
             // tiles within r_act of every centroid are scheduled near for lattice
-            // step n + 2: each ACT_STRIDE-th element covers the box of half-width
-            // ra_sub (r_act plus the stride's reach along the chain) around its
+            // step n + 2: each stride-th element covers the box of half-width
+            // ra (r_act plus the stride's reach along the chain) around its
             // stencil origin; the lanes split the tile list
             const int i0 = max(0, sc.ix - ra), i1 = min(B.nxi - 1, sc.ix + ra);
             const int j0 = max(0, sc.jy - ra), j1 = min(L.ny - 1, sc.jy + ra);
@@ -740,19 +777,28 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
     //    perimeter change (from the element lengths of step 6) and extent;
     //    store X^{n+1}
     __syncthreads();
-    double a2n = 0.0, cxs = 0.0, cys = 0.0;
-    R dper = 0;
+    double a2n_[VL], cxs_[VL], cys_[VL];
+    R dper_[VL];
+#pragma unroll
+    for (int j = 0; j < VL; ++j) {
+        a2n_[j] = cxs_[j] = cys_[j] = 0.0;
+        dper_[j] = R(0);
+    }
     R xmin = R(3e38), xmax = R(-3e38), ymin = R(3e38), ymax = R(-3e38);
-    for (int v = tid; v < nv; v += T) {
-        dper += len[v] - sl0[v];  // perimeter change for delta p (Sec. 3.1)
+    for (int v0 = tid; v0 < nv; v0 += VLANES)
+#pragma unroll
+    for (int j = 0; j < VL; ++j) {
+        const int v = v0 + j * T;
+        if (v >= nv) break;
+        dper_[j] += len[v] - sl0[v];  // perimeter change for delta p (Sec. 3.1)
         const int w = (v + 1 == nv) ? 0 : v + 1;
         const P2<R> X = P2<R>{qxh[v], qxl[v]}, Y = P2<R>{qyh[v], qyl[v]};
         const double Xd = p2_double<R>(X), Yd = p2_double<R>(Y);
         const double Xw = p2_double<R>(P2<R>{qxh[w], qxl[w]}), Yw = p2_double<R>(P2<R>{qyh[w], qyl[w]});
         const double cr = Xd * Yw - Xw * Yd;
-        a2n += cr;
-        cxs += (Xd + Xw) * cr;
-        cys += (Yd + Yw) * cr;
+        a2n_[j] += cr;
+        cxs_[j] += (Xd + Xw) * cr;
+        cys_[j] += (Yd + Yw) * cr;
         const R xa = X.h + X.l, ya = Y.h + Y.l;
         xmin = fmin(xmin, xa);
         xmax = fmax(xmax, xa);
@@ -769,42 +815,58 @@ __global__ void __launch_bounds__(LAG_THREADS) k_lagrangian(Dev d, int p)
     int nb = 0;
     if (B.adhesive)
         for (int k = B.lig_off + tid; k < B.lig_off + B.nlig; k += T) nb += d.bound[k];
-    // fused block reductions
+    // fused block reductions: sums over the virtual lanes, extent and bond
+    // count (exact in any order) over the real warps
+    double a2n, cxs, cys;
+    R dper;
     {
-        double sv[3] = {a2n, cxs, cys};
-        R rv[6] = {dper, (R)nb, xmin, ymin, -xmax, -ymax};
-#pragma unroll
-        for (int k = 0; k < 3; ++k) sv[k] = warp_sum(sv[k]);
+        constexpr int W = T / 32;
+        const int lane = tid & 31, wid = tid >> 5;
+        R rv[5] = {(R)nb, xmin, ymin, -xmax, -ymax};
         rv[0] = warp_sum(rv[0]);
-        rv[1] = warp_sum(rv[1]);
 #pragma unroll
-        for (int k = 2; k < 6; ++k) rv[k] = warp_min(rv[k]);
-        const int lane = tid & 31, wid = tid >> 5, nw = (T + 31) >> 5;
+        for (int k = 1; k < 5; ++k) rv[k] = warp_min(rv[k]);
+        double sv[VL][3];
+        R pv[VL];
+#pragma unroll
+        for (int j = 0; j < VL; ++j) {
+            sv[j][0] = warp_sum(a2n_[j]);
+            sv[j][1] = warp_sum(cxs_[j]);
+            sv[j][2] = warp_sum(cys_[j]);
+            pv[j] = warp_sum(dper_[j]);
+        }
         __syncthreads();
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) dscr[k][wid] = sv[k];
+            for (int j = 0; j < VL; ++j) {
 #pragma unroll
-            for (int k = 0; k < 6; ++k) rscr[k][wid] = rv[k];
+                for (int k = 0; k < 3; ++k) dscr[k][j * W + wid] = sv[j][k];
+                rscr[0][j * W + wid] = pv[j];
+            }
+#pragma unroll
+            for (int k = 0; k < 5; ++k) rscr[1 + k][wid] = rv[k];
         }
         __syncthreads();
+        double tv[3] = {0.0, 0.0, 0.0};
+        R tp = R(0);
         if (wid == 0) {
+            constexpr int VW = VLANES / 32;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) sv[k] = warp_sum(lane < nw ? dscr[k][lane] : 0.0);
-            rv[0] = warp_sum(lane < nw ? rscr[0][lane] : R(0));
-            rv[1] = warp_sum(lane < nw ? rscr[1][lane] : R(0));
+            for (int k = 0; k < 3; ++k) tv[k] = warp_sum(lane < VW ? dscr[k][lane] : 0.0);
+            tp = warp_sum(lane < VW ? rscr[0][lane] : R(0));
+            rv[0] = warp_sum(lane < W ? rscr[1][lane] : R(0));
 #pragma unroll
-            for (int k = 2; k < 6; ++k) rv[k] = warp_min(lane < nw ? rscr[k][lane] : R(3e38));
+            for (int k = 1; k < 5; ++k) rv[k] = warp_min(lane < W ? rscr[1 + k][lane] : R(3e38));
         }
-        a2n = sv[0];
-        cxs = sv[1];
-        cys = sv[2];
-        dper = rv[0];
-        nb = (int)rv[1];
-        xmin = rv[2];
-        ymin = rv[3];
-        xmax = -rv[4];
-        ymax = -rv[5];
+        a2n = tv[0];
+        cxs = tv[1];
+        cys = tv[2];
+        dper = tp;
+        nb = (int)rv[0];
+        xmin = rv[1];
+        ymin = rv[2];
+        xmax = -rv[3];
+        ymax = -rv[4];
     }
     if (miss & 1u) bad |= ST_READ_MISS;
     if (miss & 2u) bad |= ST_SPREAD_MISS;
@@ -881,22 +943,31 @@ size_t lagrangian_smem_bytes(int prec, int nv_max)
     return (size_t)nv_max * 33 * r;
 }
 
-// lanes per interpolation point: as many as keep every body in one pass
-static int lanes_for(int nv_max)
+// lanes per interpolation point: as many as keep every body in one pass of
+// a T-thread block
+static int lanes_for(int nv_max, int T)
 {
-    if (nv_max * 4 <= LAG_THREADS) return 4;
-    if (nv_max * 2 <= LAG_THREADS) return 2;
+    if (nv_max * 4 <= T) return 4;
+    if (nv_max * 2 <= T) return 2;
     return 1;
+}
+
+template <typename R, int T>
+static cudaError_t configure_threads(int bytes)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_lagrangian<R, 1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_lagrangian<R, 2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_lagrangian<R, 4, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
 }
 
 template <typename R>
 static cudaError_t configure_prec(int bytes)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_lagrangian<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_lagrangian<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_lagrangian<R, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = configure_threads<R, 256>(bytes);
+    if (e == cudaSuccess) e = configure_threads<R, 512>(bytes);
     return e;
 }
 
@@ -906,21 +977,26 @@ cudaError_t configure_kernels(int prec, int nv_max)
     return (prec == PREC_F64) ? configure_prec<double>(bytes) : configure_prec<float>(bytes);
 }
 
-template <typename R>
-static void launch_prec(const Dev& d, int parity, size_t bytes, cudaStream_t s)
+template <typename R, int T>
+static void launch_threads(const Dev& d, int parity, size_t bytes, cudaStream_t s)
 {
-    switch (lanes_for(d.nv_max)) {
-    case 4: k_lagrangian<R, 4><<<d.nbodies, LAG_THREADS, bytes, s>>>(d, parity); break;
-    case 2: k_lagrangian<R, 2><<<d.nbodies, LAG_THREADS, bytes, s>>>(d, parity); break;
-    default: k_lagrangian<R, 1><<<d.nbodies, LAG_THREADS, bytes, s>>>(d, parity); break;
+    switch (lanes_for(d.nv_max, T)) {
+    case 4: k_lagrangian<R, 4, T><<<d.nbodies, T, bytes, s>>>(d, parity); break;
+    case 2: k_lagrangian<R, 2, T><<<d.nbodies, T, bytes, s>>>(d, parity); break;
+    default: k_lagrangian<R, 1, T><<<d.nbodies, T, bytes, s>>>(d, parity); break;
     }
 }
 
 cudaError_t launch_lagrangian(const Dev& d, int prec, int parity, cudaStream_t s)
 {
     const size_t bytes = lagrangian_smem_bytes(prec, d.nv_max);
-    if (prec == PREC_F64) launch_prec<double>(d, parity, bytes, s);
-    else launch_prec<float>(d, parity, bytes, s);
+    if (d.lag_threads == 256) {
+        if (prec == PREC_F64) launch_threads<double, 256>(d, parity, bytes, s);
+        else launch_threads<float, 256>(d, parity, bytes, s);
+    } else {
+        if (prec == PREC_F64) launch_threads<double, 512>(d, parity, bytes, s);
+        else launch_threads<float, 512>(d, parity, bytes, s);
+    }
     return cudaGetLastError();
 }
 

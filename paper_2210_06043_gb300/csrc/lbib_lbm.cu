@@ -117,14 +117,18 @@ __device__ __forceinline__ void collide(R g[9], R Fx, R Fy, R omega, R& drho, R&
     }
 }
 
-template <typename S, typename R>
-__global__ void __launch_bounds__(TX* TY) k_bulk(Dev d, int p)
+// One block covers RT tiles stacked in y (a TX x RT TY node box); each warp
+// lies in one tile row and skips its tile when the near kernel owns it.
+template <typename S, typename R, int RT>
+__global__ void __launch_bounds__(TX* TY* RT) k_bulk(Dev d, int p)
 {
     const Lattice& L = d.L;
-    int t = blockIdx.y * L.ntx + blockIdx.x;
+    const int tyl = blockIdx.y * RT + threadIdx.y / TY;  // tile row
+    if (tyl >= L.nty) return;
+    const int t = tyl * L.ntx + blockIdx.x;
     if (d.nearflag[p][t]) return;
     const int4 ci = d.colinfo[blockIdx.x];
-    int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+    int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY * RT + threadIdx.y;
     const int xl = x - ci.x;
     if (xl >= ci.y || y >= L.ny) return;
     const S* __restrict__ fin = static_cast<const S*>(d.f[p]);
@@ -157,6 +161,8 @@ __global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
     R* drho_o = static_cast<R*>(d.drho);
     R* ux_o = static_cast<R*>(d.ux);
     R* uy_o = static_cast<R*>(d.uy);
+    R* fx_o = static_cast<R*>(d.fx);
+    R* fy_o = static_cast<R*>(d.fy);
     const int tid = threadIdx.y * TX + threadIdx.x;
     __shared__ uint32_t s_words[NEAR_CHUNK_WORDS];
     __shared__ int s_off[NEAR_CHUNK_WORDS];
@@ -228,6 +234,8 @@ __global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
             drho_o[base] = drho;
             ux_o[base] = ux;
             uy_o[base] = uy;
+            fx_o[base] = Fx;
+            fy_o[base] = Fy;
         }
         for (int w = tid; w < d.mw; w += TX * TY) mask[(size_t)t * d.mw + w] = 0u;
         if (tid == 0) {
@@ -252,9 +260,11 @@ __global__ void k_init_populations(Dev d, int buf)
     }
 }
 
-// Density and velocity of lattice step m: from the near kernel's output on
-// tiles it updated at step m, else from the post-collision populations
-// (sum f* e = rho u + F / 2 with F the uniform body force there).
+// Density and velocity of lattice step m from the post-collision populations:
+// sum f* = rho, sum f* e = rho u + F / 2 with F the force density of the step
+// (the near kernel's on tiles it updated at step m, else the uniform body
+// force).  One formula for every tile, so a read does not depend on which
+// tiles were scheduled near.
 template <typename S, typename R, typename O>
 __global__ void k_macro(Dev d, int buf, int64_t m, int x0, int inx, O* rho_o, O* ux_o, O* uy_o, int add_one)
 {
@@ -264,22 +274,20 @@ __global__ void k_macro(Dev d, int buf, int64_t m, int x0, int inx, O* rho_o, O*
     const int x = x0 + xl;
     int t = blockIdx.y * L.ntx + x / TX;
     int base = y * L.nxp + x, ob = y * inx + xl;
-    R drho, ux, uy;
+    R Fx = R(L.gx), Fy = R(L.gy);
     if (d.fresh[t] == (int32_t)m) {
-        drho = static_cast<const R*>(d.drho)[base];
-        ux = static_cast<const R*>(d.ux)[base];
-        uy = static_cast<const R*>(d.uy)[base];
-    } else {
-        const S* f = static_cast<const S*>(d.f[buf]);
-        R g[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) g[q] = static_cast<R>(f[q * L.qstride + base]);
-        drho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
-        R jx = (g[1] + g[5] + g[8]) - (g[3] + g[6] + g[7]) - R(0.5) * R(L.gx);
-        R jy = (g[2] + g[5] + g[6]) - (g[4] + g[7] + g[8]) - R(0.5) * R(L.gy);
-        ux = jx / (R(1) + drho);
-        uy = jy / (R(1) + drho);
+        Fx = static_cast<const R*>(d.fx)[base];
+        Fy = static_cast<const R*>(d.fy)[base];
     }
+    const S* f = static_cast<const S*>(d.f[buf]);
+    R g[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) g[q] = static_cast<R>(f[q * L.qstride + base]);
+    const R drho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
+    const R jx = (g[1] + g[5] + g[8]) - (g[3] + g[6] + g[7]) - R(0.5) * Fx;
+    const R jy = (g[2] + g[5] + g[6]) - (g[4] + g[7] + g[8]) - R(0.5) * Fy;
+    const R ux = jx / (R(1) + drho);
+    const R uy = jy / (R(1) + drho);
     if (rho_o) rho_o[ob] = add_one ? O(1) + O(drho) : O(drho);
     if (ux_o) ux_o[ob] = O(ux);
     if (uy_o) uy_o[ob] = O(uy);
@@ -350,11 +358,21 @@ __global__ void k_rebuild_mask(Dev d, int parity)
 
 // ------------------------------------------------------------------ launchers
 
+template <int RT>
+static void launch_bulk_rt(const Dev& d, int prec, int parity, cudaStream_t s)
+{
+    dim3 grid(d.L.ntx, (d.L.nty + RT - 1) / RT), block(TX, TY * RT);
+    if (prec == PREC_F64) k_bulk<double, double, RT><<<grid, block, 0, s>>>(d, parity);
+    else k_bulk<float, float, RT><<<grid, block, 0, s>>>(d, parity);
+}
+
 cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, cudaStream_t s)
 {
-    dim3 grid(d.L.ntx, d.L.nty), block(TX, TY);
-    if (prec == PREC_F64) k_bulk<double, double><<<grid, block, 0, s>>>(d, parity);
-    else k_bulk<float, float><<<grid, block, 0, s>>>(d, parity);
+    switch (d.bulk_tiles_y) {
+    case 2: launch_bulk_rt<2>(d, prec, parity, s); break;
+    case 4: launch_bulk_rt<4>(d, prec, parity, s); break;
+    default: launch_bulk_rt<1>(d, prec, parity, s); break;
+    }
     return cudaGetLastError();
 }
 

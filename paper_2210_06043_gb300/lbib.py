@@ -54,6 +54,11 @@ class lbib_obs(ctypes.Structure):
                 ("status", ctypes.c_int32)]
 
 
+class lbib_launch_config(ctypes.Structure):
+    _fields_ = [("lagrangian_threads", ctypes.c_int32), ("near_blocks", ctypes.c_int32),
+                ("bulk_tiles_y", ctypes.c_int32), ("activation_stride", ctypes.c_int32)]
+
+
 _P = ctypes.c_void_p
 _SIGS = {
     "lbib_create": [ctypes.POINTER(lbib_fluid_params), ctypes.POINTER(_P)],
@@ -88,6 +93,9 @@ _SIGS = {
     "lbib_read_instance_observables": [_P, ctypes.c_int32, ctypes.POINTER(lbib_obs), ctypes.c_size_t,
                                        ctypes.POINTER(ctypes.c_size_t)],
     "lbib_read_latest_observables": [_P, ctypes.POINTER(lbib_obs), ctypes.c_size_t],
+    "lbib_get_launch_config": [_P, ctypes.POINTER(lbib_launch_config)],
+    "lbib_set_launch_config": [_P, ctypes.POINTER(lbib_launch_config)],
+    "lbib_autotune": [_P, ctypes.c_int32, ctypes.POINTER(lbib_launch_config)],
 }
 
 _lib = None
@@ -187,6 +195,11 @@ def lbib_lattice_advance_noalloc(params: lbib_fluid_params, f_device_ptr: int, n
     device buffer of 9 nx ny doubles (see include/lbib.h)."""
     _check(load().lbib_lattice_advance_noalloc(ctypes.byref(params), ctypes.c_void_p(f_device_ptr),
                                                 int(nsteps)), None)
+
+
+def _config_dict(c: lbib_launch_config) -> dict:
+    return dict(lagrangian_threads=c.lagrangian_threads, near_blocks=c.near_blocks, bulk_tiles_y=c.bulk_tiles_y,
+                activation_stride=c.activation_stride)
 
 
 class Solver:
@@ -333,6 +346,23 @@ class Solver:
         a, b, c = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
         self._c(self.lib.lbib_read_kernel_times(self.ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return a.value, b.value, c.value
+
+    def launch_config(self) -> dict:
+        c = lbib_launch_config()
+        self._c(self.lib.lbib_get_launch_config(self.ctx, ctypes.byref(c)))
+        return _config_dict(c)
+
+    def set_launch_config(self, lagrangian_threads, near_blocks, bulk_tiles_y, activation_stride=4):
+        c = lbib_launch_config(lagrangian_threads=int(lagrangian_threads), near_blocks=int(near_blocks),
+                               bulk_tiles_y=int(bulk_tiles_y), activation_stride=int(activation_stride))
+        self._c(self.lib.lbib_set_launch_config(self.ctx, ctypes.byref(c)))
+
+    def autotune(self, steps_per_trial=20) -> dict:
+        """Times candidate launch configurations on this context's state and
+        keeps the fastest; the state is unchanged (see include/lbib.h)."""
+        c = lbib_launch_config()
+        self._c(self.lib.lbib_autotune(self.ctx, int(steps_per_trial), ctypes.byref(c)))
+        return _config_dict(c)
 
     def describe(self):
         k, n, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

@@ -53,6 +53,8 @@ int main(void) {
   S(lbib_membrane_desc); O(lbib_membrane_desc, xy); O(lbib_membrane_desc, xy_ref); O(lbib_membrane_desc, density_ratio);
   S(lbib_adhesion_params); O(lbib_adhesion_params, sigma); O(lbib_adhesion_params, xi);
   S(lbib_obs); O(lbib_obs, n_l); O(lbib_obs, n_bound); O(lbib_obs, status);
+  S(lbib_launch_config); O(lbib_launch_config, near_blocks); O(lbib_launch_config, bulk_tiles_y);
+  O(lbib_launch_config, activation_stride);
   return 0;
 }
 '''
@@ -68,7 +70,8 @@ int main(void) {
 
 def test_ctypes_structs_match_the_header():
     lay = _c_layout()
-    for cls in (lbib.lbib_fluid_params, lbib.lbib_membrane_desc, lbib.lbib_adhesion_params, lbib.lbib_obs):
+    for cls in (lbib.lbib_fluid_params, lbib.lbib_membrane_desc, lbib.lbib_adhesion_params, lbib.lbib_obs,
+                lbib.lbib_launch_config):
         name = cls.__name__
         assert int(lay[f"{name}.sizeof"]) == ctypes.sizeof(cls), name
         for key, val in lay.items():

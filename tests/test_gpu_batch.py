@@ -40,8 +40,9 @@ def _mixed_fp64():
     return [a, b, c, d]
 
 
-def _same_state(batch, k, lone, cap, body0):
-    """Instance k of `batch` (its bodies numbered from body0) equals `lone`."""
+def _same_state(batch, k, lone, cap, body0, observables=True):
+    """Instance k of `batch` (its bodies numbered from body0) equals `lone`
+    (observables records too, which moves both cursors)."""
     for bi, b in enumerate(cap.bodies):
         assert np.array_equal(batch.markers(body0 + bi), lone.markers(bi)), (k, bi)
         for f in ("uvx", "uvy", "ftx", "fty", "mfx", "mfy", "vx", "vy"):
@@ -53,6 +54,8 @@ def _same_state(batch, k, lone, cap, body0):
     lu, lv = lone.velocity()
     assert np.array_equal(gu, lu) and np.array_equal(gv, lv), k
     assert np.array_equal(batch.populations(k), lone.populations()), k
+    if not observables:
+        return
     ob, ol = batch.observables(instance=k), lone.observables()
     assert len(ob) == len(ol), k
     for x, y in zip(ob, ol):
@@ -113,13 +116,20 @@ def test_sweep_full_size_fp32_sampled():
     batch.advance(n)
     d = batch.describe()
     assert d["kernels_per_step"] == 3
+    latest = batch.latest_observables()
+    records = [batch.observables(instance=inst) for inst in range(len(caps))]
+    for inst, obs in enumerate(records):
+        assert latest[inst] == obs[-1]
+        assert len(obs) == n and obs[-1]["step"] == n and obs[-1]["status"] == 0
+        assert np.isfinite(obs[-1]["delta_p"]) and np.isfinite(obs[-1]["r"])
     body0 = np.cumsum([0] + [len(c.bodies) for c in caps])
     lengths = [c.nx for c in caps]
     sample = sorted({int(np.argmin(lengths)), int(np.argmax(lengths)), 37})
     for k in sample:
         lone = lbib.from_capillary(caps[k])
         lone.advance(n)
-        _same_state(batch, k, lone, caps[k], int(body0[k]))
+        _same_state(batch, k, lone, caps[k], int(body0[k]), observables=False)
+        assert lone.observables() == records[k]
         lone.close()
     k = sample[0]
     o = oracle_from(caps[k])
@@ -129,12 +139,6 @@ def test_sweep_full_size_fp32_sampled():
     assert rel_l2(np.stack([gu, gv]), np.stack([ux, uy])) < 1e-5
     for bi in range(2):
         assert np.abs(o.body_xy(bi) - batch.markers(int(body0[k]) + bi)).max() < 1e-6
-    latest = batch.latest_observables()
-    for inst in range(len(caps)):
-        obs = batch.observables(instance=inst)
-        assert latest[inst] == obs[-1]
-        assert len(obs) == n and obs[-1]["step"] == n and obs[-1]["status"] == 0
-        assert np.isfinite(obs[-1]["delta_p"]) and np.isfinite(obs[-1]["r"])
     batch.close()
 
 
@@ -146,6 +150,11 @@ def test_batch_checkpoint_restart_is_bit_identical():
     a.advance(60)
     b = lbib.from_capillaries(caps)
     b.load_state(blob)
+    c = lbib.from_capillaries(caps)
+    c.advance(60)
+    for k in range(len(caps)):  # reads right after the restore equal the saved run's
+        assert np.array_equal(b.velocity(k)[0], c.velocity(k)[0])
+    c.close()
     b.advance(60)
     for k in range(len(caps)):
         assert np.array_equal(a.velocity(k)[0], b.velocity(k)[0])
