@@ -2,14 +2,16 @@
 // streams, CUDA graphs of the time step and the C ABI.
 //
 // Time-step pipeline.  Lattice step m (bulk + near kernels) must follow the
-// Lagrangian step m - 1 only on near tiles, so the bulk lattice update of step
-// m runs on a forked stream concurrently with the Lagrangian step m - 1:
+// Lagrangian step m - 1 only on near tiles, and the bulk and near updates of
+// one step write disjoint tiles from the same input, so the bulk lattice
+// update of step m runs on a forked stream alongside the chain
 //
-//     [Lagrangian(m-1) || bulk lattice(m)] -> near lattice(m)
+//     Lagrangian(m-1) -> near lattice(m)      ||      bulk lattice(m)
 //
-// is one captured graph per parity of m.  A context keeps the last Lagrangian
-// step pending after lbib_advance (so back-to-back calls overlap it with the
-// next lattice step); every call that reads Lagrangian state completes it.
+// one captured graph per m % 6 (buffer parity and near-flag slot).  A context
+// keeps the last Lagrangian step pending after lbib_advance (so back-to-back
+// calls overlap it with the next lattice step); every call that reads
+// Lagrangian state completes it.
 //
 // A context holds a batch of one or more capillary instances side by side in
 // one lattice (instance i at node columns [x0_i, x0_i + nx_i), x0_i a multiple
@@ -99,7 +101,7 @@ struct lbib_ctx {
     int64_t s_f = 0, s_l = 0;  // lattice and Lagrangian steps done
     cudaStream_t stream = nullptr, side = nullptr, cap = nullptr;
     bool own_stream = false;
-    cudaGraphExec_t unit[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [profiling][parity]
+    cudaGraphExec_t unit[2][6] = {};  // [profiling][lattice step % 6]: buffer parity and flag slot
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t pe[6] = {};
     bool profiling = false, profiled_last = false;
@@ -178,9 +180,14 @@ lbib_status finish_pending(lbib_ctx* ctx)
     return LBIB_OK;
 }
 
-lbib_status capture_unit(lbib_ctx* ctx, int prof, int p)
+// Graph of lattice step m (v = m % 6): the membrane update of step m - 1 then
+// the near lattice update of step m on one branch, the bulk lattice update of
+// step m on the other (they write disjoint tiles and read only step m's
+// populations).
+lbib_status capture_unit(lbib_ctx* ctx, int prof, int v)
 {
     Dev& d = ctx->d;
+    const int p = v & 1, slot = v % 3;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
@@ -195,20 +202,21 @@ lbib_status capture_unit(lbib_ctx* ctx, int prof, int p)
     rec(3, ctx->cap);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
     rec(0, ctx->side);
-    if (e == cudaSuccess) e = launch_lbm_bulk(d, ctx->prec, p, ctx->side);
+    if (e == cudaSuccess) e = launch_lbm_bulk(d, ctx->prec, p, slot, ctx->side);
     rec(1, ctx->side);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap, ctx->ev_join, 0);
     rec(4, ctx->cap);
     if (e == cudaSuccess) e = launch_lbm_near(d, ctx->prec, p, ctx->near_grid, ctx->cap);
     rec(5, ctx->cap);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap, ctx->ev_join, 0);
     cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &g);
     if (e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return cuda_fail(ctx, e, "capturing the step graph");
     }
     if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&ctx->unit[prof][p], g, 0);
+    // per-node priorities: the membrane -> near chain ahead of the bulk blocks
+    e = cudaGraphInstantiate(&ctx->unit[prof][v], g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
     return LBIB_OK;
@@ -217,9 +225,9 @@ lbib_status capture_unit(lbib_ctx* ctx, int prof, int p)
 lbib_status ensure_graphs(lbib_ctx* ctx)
 {
     int prof = ctx->profiling ? 1 : 0;
-    for (int p = 0; p < 2; ++p)
-        if (!ctx->unit[prof][p]) {
-            lbib_status s = capture_unit(ctx, prof, p);
+    for (int v = 0; v < 6; ++v)
+        if (!ctx->unit[prof][v]) {
+            lbib_status s = capture_unit(ctx, prof, v);
             if (s != LBIB_OK) return s;
         }
     return LBIB_OK;
@@ -525,6 +533,11 @@ lbib_status finalize(lbib_ctx* ctx)
     // membrane blocks of 256 threads once the bodies outnumber half the SMs, so that
     // they share SMs with the bulk lattice update; near kernel 4 blocks per SM
     if (!d.lag_threads) d.lag_threads = (nb > nsm / 2) ? 256 : 512;
+    {
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        d.chain_priority = greatest;  // numerically lowest = most urgent
+    }
     if (!ctx->near_grid) ctx->near_grid = std::max(1, std::min(L.ntiles, 4 * nsm));
     ctx->finalized = true;
     if (nb) {
@@ -652,8 +665,7 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     CKC(dalloc(reg, reinterpret_cast<char**>(&d.fx), nn * ctx->rsz));
     CKC(dalloc(reg, reinterpret_cast<char**>(&d.fy), nn * ctx->rsz));
     CKC(dalloc(reg, &d.fresh, L.ntiles));
-    CKC(dalloc(reg, &d.nearflag[0], L.ntiles));
-    CKC(dalloc(reg, &d.nearflag[1], L.ntiles));
+    for (int i = 0; i < 3; ++i) CKC(dalloc(reg, &d.nearflag[i], L.ntiles));
     for (int i = 0; i < 3; ++i) CKC(dalloc(reg, &d.list[i], d.list_cap));
     CKC(dalloc(reg, &d.count, 3));
     CKC(dalloc(reg, &d.step, 1));
@@ -673,8 +685,7 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     CKC(cudaMemset(d.fx, 0, nn * ctx->rsz));
     CKC(cudaMemset(d.fy, 0, nn * ctx->rsz));
     CKC(cudaMemset(d.fresh, 0x80, L.ntiles * 4));  // matches no step
-    CKC(cudaMemset(d.nearflag[0], 0, L.ntiles * 4));
-    CKC(cudaMemset(d.nearflag[1], 0, L.ntiles * 4));
+    for (int i = 0; i < 3; ++i) CKC(cudaMemset(d.nearflag[i], 0, L.ntiles * 4));
     CKC(cudaMemset(d.count, 0, 12));
     CKC(cudaMemset(d.step, 0, 8));
     CKC(cudaMemset(d.status, 0, 4));
@@ -778,7 +789,7 @@ lbib_status lbib_advance(lbib_ctx* ctx, int64_t nsteps)
     Dev& d = ctx->d;
     if (d.nbodies == 0) {
         for (int64_t k = 0; k < nsteps; ++k) {
-            CK(launch_lbm_bulk(d, ctx->prec, (int)(ctx->s_f & 1), ctx->stream));
+            CK(launch_lbm_bulk(d, ctx->prec, (int)(ctx->s_f & 1), (int)(ctx->s_f % 3), ctx->stream));
             ctx->s_f += 1;
         }
         ctx->s_l = ctx->s_f;
@@ -789,7 +800,7 @@ lbib_status lbib_advance(lbib_ctx* ctx, int64_t nsteps)
     if (s != LBIB_OK) return s;
     if (ctx->s_l == ctx->s_f) {  // open the pipeline: lattice step s_f alone
         int p = (int)(ctx->s_f & 1);
-        CK(launch_lbm_bulk(d, ctx->prec, p, ctx->stream));
+        CK(launch_lbm_bulk(d, ctx->prec, p, (int)(ctx->s_f % 3), ctx->stream));
         CK(launch_lbm_near(d, ctx->prec, p, ctx->near_grid, ctx->stream));
         ctx->s_f += 1;
         nsteps -= 1;
@@ -797,7 +808,7 @@ lbib_status lbib_advance(lbib_ctx* ctx, int64_t nsteps)
     }
     const int prof = ctx->profiling ? 1 : 0;
     for (int64_t k = 0; k < nsteps; ++k) {
-        CK(cudaGraphLaunch(ctx->unit[prof][ctx->s_f & 1], ctx->stream));
+        CK(cudaGraphLaunch(ctx->unit[prof][ctx->s_f % 6], ctx->stream));
         ctx->s_f += 1;
         ctx->s_l += 1;
         ctx->profiled_last = (prof != 0);
@@ -1193,8 +1204,7 @@ lbib_status load_from(lbib_ctx* ctx, const char* p, cudaMemcpyKind kind)
     CK(get(d.margin, nl * ctx->rsz));
     // scheduling state is rebuilt from the restored positions and markers
     const Lattice& L = d.L;
-    CK(cudaMemset(d.nearflag[0], 0, L.ntiles * 4));
-    CK(cudaMemset(d.nearflag[1], 0, L.ntiles * 4));
+    for (int i = 0; i < 3; ++i) CK(cudaMemset(d.nearflag[i], 0, L.ntiles * 4));
     CK(cudaMemset(d.mask[0], 0, (size_t)L.ntiles * d.mw * 4));
     CK(cudaMemset(d.mask[1], 0, (size_t)L.ntiles * d.mw * 4));
     CK(cudaMemset(d.count, 0, 12));
@@ -1206,7 +1216,7 @@ lbib_status load_from(lbib_ctx* ctx, const char* p, cudaMemcpyKind kind)
     ctx->obs_consumed.assign(ctx->ninst, st);
     if (d.nbodies) {
         CK(launch_activate(d, ctx->prec, st, 3, ctx->stream));
-        CK(launch_rebuild_mask(d, ctx->prec, (int)(st & 1), ctx->stream));
+        CK(launch_rebuild_mask(d, ctx->prec, st, ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return check_status(ctx);

@@ -110,7 +110,12 @@ struct Dev {
     void* fx;                  // Real [ny][nxp]: total force density (g + F_E) the near update used
     void* fy;                  // Real [ny][nxp]
     int32_t* fresh;            // [ntiles]: lattice step whose near update wrote rho/u
-    uint32_t* nearflag[2];     // [ntiles]: tile is near for lattice steps of this parity
+    // nearflag[m % 3][t]: tile t is updated by the near kernel at lattice step m.
+    // Set by the membrane update of step m - 2 (or an activation), read by the
+    // bulk and near updates of step m, cleared by the membrane update of step m;
+    // three slots so that the bulk update of step m + 1, which runs alongside
+    // the membrane update of step m, reads a slot nobody writes.
+    uint32_t* nearflag[3];
     int32_t* list[3];          // [list_cap]: near tiles of lattice step m, m % 3
     int32_t* count;            // [3]
     uint32_t* mask[2];         // [ntiles][mw], bit k: the instance's marker k
@@ -151,6 +156,7 @@ struct Dev {
     // activation radius around markers (lattice units) per instance: BodyConst::r_act;
     // every act_stride-th element centroid activates r_act + act_stride * act_reach
     int act_stride;            // 1, 2 or 4 (results do not depend on it)
+    int chain_priority;        // stream priority of the membrane and near launches (0: default)
     double dcut;               // repulsion cut-off (Eq. 12)
     double probe;              // probe length (Sec. 2.6)
     double uscale;             // observables: u_max / H
@@ -158,7 +164,8 @@ struct Dev {
 
 // ------------------------------------------------------------------ launchers
 // (defined in lbib_lbm.cu and lbib_lag.cu; `prec` selects FP64 or FP32)
-cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, cudaStream_t s);
+// bulk update of lattice step m: parity = m & 1, slot = m % 3
+cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, int slot, cudaStream_t s);
 cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, cudaStream_t s);
 cudaError_t launch_init_populations(const Dev& d, int prec, int buf, cudaStream_t s);
 // moments of one instance (node columns [x0, x0 + inx)) into [ny][inx] arrays
@@ -168,7 +175,7 @@ cudaError_t launch_macro_typed(const Dev& d, int prec, int buf, int64_t m, int x
                                int dtype, cudaStream_t s);
 cudaError_t launch_lagrangian(const Dev& d, int prec, int parity, cudaStream_t s);
 cudaError_t launch_activate(const Dev& d, int prec, int64_t m, int which, cudaStream_t s);
-cudaError_t launch_rebuild_mask(const Dev& d, int prec, int parity, cudaStream_t s);
+cudaError_t launch_rebuild_mask(const Dev& d, int prec, int64_t m, cudaStream_t s);
 size_t lagrangian_smem_bytes(int prec, int nv_max);
 // message returned by lbib_last_error(NULL) (calls that have no context)
 void set_global_error(const char* msg);

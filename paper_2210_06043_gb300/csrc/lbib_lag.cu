@@ -368,6 +368,17 @@ __global__ void __launch_bounds__(T) k_lagrangian(Dev d, int p)
     const int lane4 = tid % K, Q = T / K;  // K lanes per interpolation point
     const int nvq = ((nv + Q - 1) / Q) * Q;
 
+    // the near update of lattice step n is done: its tiles' flags (slot n % 3)
+    // are cleared here, spread over the blocks; the last block then empties
+    // the list (the slot is set again for step n + 3 by the next update)
+    {
+        const int c0 = (int)(n % 3);
+        const int cnt = min(d.count[c0], d.list_cap);
+        uint32_t* f0 = d.nearflag[c0];
+        const int32_t* l0 = d.list[c0];
+        for (int k = blockIdx.x * T + tid; k < cnt; k += gridDim.x * T) f0[l0[k]] = 0u;
+    }
+
     // 0. one round of global loads; positions to float-float pairs; the FP64
     //    shoelace terms of X^n (Eq. 11's area) directly from the loaded values
     double a2[VL];
@@ -684,7 +695,8 @@ __global__ void __launch_bounds__(T) k_lagrangian(Dev d, int p)
     int32_t* mki = d.mki[p];
     R* mkf = static_cast<R*>(d.mkf[p]);
     const int64_t n2 = n + 2;
-    uint32_t* flag2 = d.nearflag[n2 & 1];
+    uint32_t* flag2 = d.nearflag[n2 % 3];
+    const uint32_t* flag1 = d.nearflag[(n + 1) % 3];  // near tiles of lattice step n + 1
     const int c2 = (int)(n2 % 3);
     const int stride = d.act_stride;
     const int ra = (int)ceil(B.r_act + stride * B.act_reach) + 1;
@@ -737,7 +749,7 @@ __global__ void __launch_bounds__(T) k_lagrangian(Dev d, int p)
                 const int nt = box_tiles(L, B.x0 + i0, B.x0 + i1, j0, j1, 0, tl);
                 for (int e = lane4; e < nt; e += K) {
                     const int t = tl[e];
-                    if (!d.nearflag[p][t]) miss |= 2u;
+                    if (!flag1[t]) miss |= 2u;
                     atomicOr(&d.mask[p][(size_t)t * d.mw + (gl >> 5)], 1u << (gl & 31));
                 }
             }
@@ -978,26 +990,33 @@ cudaError_t configure_kernels(int prec, int nv_max)
 }
 
 template <typename R, int T>
-static void launch_threads(const Dev& d, int parity, size_t bytes, cudaStream_t s)
+static cudaError_t launch_threads(const Dev& d, int parity, size_t bytes, cudaStream_t s)
 {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(d.nbodies);
+    cfg.blockDim = dim3(T);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = d.chain_priority;
+    cfg.attrs = attr;
+    cfg.numAttrs = d.chain_priority ? 1 : 0;
     switch (lanes_for(d.nv_max, T)) {
-    case 4: k_lagrangian<R, 4, T><<<d.nbodies, T, bytes, s>>>(d, parity); break;
-    case 2: k_lagrangian<R, 2, T><<<d.nbodies, T, bytes, s>>>(d, parity); break;
-    default: k_lagrangian<R, 1, T><<<d.nbodies, T, bytes, s>>>(d, parity); break;
+    case 4: return cudaLaunchKernelEx(&cfg, k_lagrangian<R, 4, T>, d, parity);
+    case 2: return cudaLaunchKernelEx(&cfg, k_lagrangian<R, 2, T>, d, parity);
+    default: return cudaLaunchKernelEx(&cfg, k_lagrangian<R, 1, T>, d, parity);
     }
 }
 
 cudaError_t launch_lagrangian(const Dev& d, int prec, int parity, cudaStream_t s)
 {
     const size_t bytes = lagrangian_smem_bytes(prec, d.nv_max);
-    if (d.lag_threads == 256) {
-        if (prec == PREC_F64) launch_threads<double, 256>(d, parity, bytes, s);
-        else launch_threads<float, 256>(d, parity, bytes, s);
-    } else {
-        if (prec == PREC_F64) launch_threads<double, 512>(d, parity, bytes, s);
-        else launch_threads<float, 512>(d, parity, bytes, s);
-    }
-    return cudaGetLastError();
+    if (d.lag_threads == 256)
+        return (prec == PREC_F64) ? launch_threads<double, 256>(d, parity, bytes, s)
+                                  : launch_threads<float, 256>(d, parity, bytes, s);
+    return (prec == PREC_F64) ? launch_threads<double, 512>(d, parity, bytes, s)
+                              : launch_threads<float, 512>(d, parity, bytes, s);
 }
 
 }  // namespace lbib

@@ -120,13 +120,13 @@ __device__ __forceinline__ void collide(R g[9], R Fx, R Fy, R omega, R& drho, R&
 // One block covers RT tiles stacked in y (a TX x RT TY node box); each warp
 // lies in one tile row and skips its tile when the near kernel owns it.
 template <typename S, typename R, int RT>
-__global__ void __launch_bounds__(TX* TY* RT) k_bulk(Dev d, int p)
+__global__ void __launch_bounds__(TX* TY* RT) k_bulk(Dev d, int p, int slot)
 {
     const Lattice& L = d.L;
     const int tyl = blockIdx.y * RT + threadIdx.y / TY;  // tile row
     if (tyl >= L.nty) return;
     const int t = tyl * L.ntx + blockIdx.x;
-    if (d.nearflag[p][t]) return;
+    if (d.nearflag[slot][t]) return;
     const int4 ci = d.colinfo[blockIdx.x];
     int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY * RT + threadIdx.y;
     const int xl = x - ci.x;
@@ -238,10 +238,7 @@ __global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
             fy_o[base] = Fy;
         }
         for (int w = tid; w < d.mw; w += TX * TY) mask[(size_t)t * d.mw + w] = 0u;
-        if (tid == 0) {
-            d.nearflag[p][t] = 0u;
-            d.fresh[t] = (int32_t)m;
-        }
+        if (tid == 0) d.fresh[t] = (int32_t)m;  // the flag is cleared by the next membrane update
     }
 }
 
@@ -316,7 +313,7 @@ __global__ void k_activate(Dev d, int64_t m, int which)
     for (int s = 0; s < 2; ++s) {
         if (!(which & (1 << s))) continue;
         int64_t step = m + s;
-        uint32_t* flag = d.nearflag[step & 1];
+        uint32_t* flag = d.nearflag[step % 3];
         int c = (int)(step % 3);
         for (int ty = j0 / TY; ty <= j1 / TY; ++ty)
             for (int tx = i0 / TX; tx <= i1 / TX; ++tx) {
@@ -330,9 +327,9 @@ __global__ void k_activate(Dev d, int64_t m, int which)
     }
 }
 
-// Sets the spreading bit masks of the markers of `parity` (after a restore).
+// Sets the spreading bit masks of the markers of lattice step m (after a restore).
 template <typename R>
-__global__ void k_rebuild_mask(Dev d, int parity)
+__global__ void k_rebuild_mask(Dev d, int parity, int slot)
 {
     const Lattice& L = d.L;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -351,7 +348,7 @@ __global__ void k_rebuild_mask(Dev d, int parity)
     for (int ty = j0 / TY; ty <= j1 / TY; ++ty)
         for (int tx = i0 / TX; tx <= i1 / TX; ++tx) {
             int t = ty * L.ntx + tx;
-            if (!d.nearflag[parity][t]) atomicOr(d.status, ST_SPREAD_MISS);
+            if (!d.nearflag[slot][t]) atomicOr(d.status, ST_SPREAD_MISS);
             atomicOr(&d.mask[parity][(size_t)t * d.mw + (kl >> 5)], 1u << (kl & 31));
         }
 }
@@ -359,29 +356,36 @@ __global__ void k_rebuild_mask(Dev d, int parity)
 // ------------------------------------------------------------------ launchers
 
 template <int RT>
-static void launch_bulk_rt(const Dev& d, int prec, int parity, cudaStream_t s)
+static void launch_bulk_rt(const Dev& d, int prec, int parity, int slot, cudaStream_t s)
 {
     dim3 grid(d.L.ntx, (d.L.nty + RT - 1) / RT), block(TX, TY * RT);
-    if (prec == PREC_F64) k_bulk<double, double, RT><<<grid, block, 0, s>>>(d, parity);
-    else k_bulk<float, float, RT><<<grid, block, 0, s>>>(d, parity);
+    if (prec == PREC_F64) k_bulk<double, double, RT><<<grid, block, 0, s>>>(d, parity, slot);
+    else k_bulk<float, float, RT><<<grid, block, 0, s>>>(d, parity, slot);
 }
 
-cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, cudaStream_t s)
+cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, int slot, cudaStream_t s)
 {
     switch (d.bulk_tiles_y) {
-    case 2: launch_bulk_rt<2>(d, prec, parity, s); break;
-    case 4: launch_bulk_rt<4>(d, prec, parity, s); break;
-    default: launch_bulk_rt<1>(d, prec, parity, s); break;
+    case 2: launch_bulk_rt<2>(d, prec, parity, slot, s); break;
+    case 4: launch_bulk_rt<4>(d, prec, parity, slot, s); break;
+    default: launch_bulk_rt<1>(d, prec, parity, slot, s); break;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, cudaStream_t s)
 {
-    dim3 block(TX, TY);
-    if (prec == PREC_F64) k_near<double, double><<<grid, block, 0, s>>>(d, parity);
-    else k_near<float, float><<<grid, block, 0, s>>>(d, parity);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(TX, TY);
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = d.chain_priority;
+    cfg.attrs = attr;
+    cfg.numAttrs = d.chain_priority ? 1 : 0;
+    if (prec == PREC_F64) return cudaLaunchKernelEx(&cfg, k_near<double, double>, d, parity);
+    return cudaLaunchKernelEx(&cfg, k_near<float, float>, d, parity);
 }
 
 cudaError_t launch_init_populations(const Dev& d, int prec, int buf, cudaStream_t s)
@@ -434,12 +438,13 @@ cudaError_t launch_activate(const Dev& d, int prec, int64_t m, int which, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t launch_rebuild_mask(const Dev& d, int prec, int parity, cudaStream_t s)
+cudaError_t launch_rebuild_mask(const Dev& d, int prec, int64_t m, cudaStream_t s)
 {
     if (d.nmark == 0) return cudaSuccess;
     int th = 128, bl = (d.nmark + th - 1) / th;
-    if (prec == PREC_F64) k_rebuild_mask<double><<<bl, th, 0, s>>>(d, parity);
-    else k_rebuild_mask<float><<<bl, th, 0, s>>>(d, parity);
+    const int parity = (int)(m & 1), slot = (int)(m % 3);
+    if (prec == PREC_F64) k_rebuild_mask<double><<<bl, th, 0, s>>>(d, parity, slot);
+    else k_rebuild_mask<float><<<bl, th, 0, s>>>(d, parity, slot);
     return cudaGetLastError();
 }
 

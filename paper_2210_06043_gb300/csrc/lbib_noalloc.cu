@@ -144,7 +144,7 @@ extern "C" lbib_status lbib_lattice_advance_noalloc(const lbib_fluid_params* P, 
         Dev d{};
         d.L = L;
         d.status = reinterpret_cast<uint32_t*>(base);
-        d.nearflag[0] = d.nearflag[1] = reinterpret_cast<uint32_t*>(base + 256);
+        d.nearflag[0] = d.nearflag[1] = d.nearflag[2] = reinterpret_cast<uint32_t*>(base + 256);
         int4* cols = reinterpret_cast<int4*>(base + 256 + need_flags);
         d.colinfo = cols;
         d.ninst = 1;
@@ -164,7 +164,8 @@ extern "C" lbib_status lbib_lattice_advance_noalloc(const lbib_fluid_params* P, 
                 k_absolute_to_deviation<float><<<grid, block, 0, stream>>>(f, static_cast<float*>(d.f[0]), L);
             e = cudaGetLastError();
         }
-        for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k) e = launch_lbm_bulk(d, prec, (int)(k & 1), stream);
+        for (int64_t k = 0; k < nsteps && e == cudaSuccess; ++k)
+            e = launch_lbm_bulk(d, prec, (int)(k & 1), (int)(k % 3), stream);
         if (e == cudaSuccess) {
             const int last = (int)(nsteps & 1);
             if (prec == PREC_F64)
