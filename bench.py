@@ -260,7 +260,13 @@ def run_gpu(args):
     make = (lambda **kw: lbib.from_capillaries(caps, **kw)) if batch else \
         (lambda **kw: lbib.from_capillary(caps[0], **kw))
     s = make(device=local, stream=stream.cuda_stream)
-    tuned = s.autotune(steps_per_trial=args.tune_steps)  # leaves the state unchanged
+    if args.config:  # a fixed launch configuration (profiling runs) instead of the autotuner
+        s.set_launch_config(*(int(v) for v in args.config.split(",")))
+        tuned = dict(s.launch_config())
+        tuned_by = "--config"
+    else:
+        tuned = s.autotune(steps_per_trial=args.tune_steps)  # leaves the state unchanged
+        tuned_by = f"lbib_autotune, {args.tune_steps} steps per trial"
     s.set_profiling(True)
     # populations beyond L2 (sweep): no flush; else a 256 MiB buffer rewritten between steps
     pop_bytes = 2 * 9 * 4 * nodes
@@ -353,7 +359,7 @@ def run_gpu(args):
             "kernel_ms": {"bulk_lattice": bulk_ms, "lagrangian": lag_ms, "near_lattice": near_ms},
             "near_tiles": desc["near_tiles"], "tiles": desc["tiles"],
             "roofline": roofline, "e2e": e2e, "gpu_launches": 3 * K, "clocks": clk,
-            "launch_config": dict(tuned, chosen_by=f"lbib_autotune, {args.tune_steps} steps per trial"),
+            "launch_config": dict(tuned, chosen_by=tuned_by),
             "wall_s_timed_region": wall}
     if batch:
         t_plain = plain_solver(caps, local, args.plain_steps, 3)
@@ -388,6 +394,9 @@ def main():
     ap.add_argument("--cpu-nodes", type=float, default=1.0e8,
                     help="node updates of the CPU oracle sample (about 15 s at 7 MLUPS)")
     ap.add_argument("--tune-steps", type=int, default=20, help="steps per autotuner trial")
+    ap.add_argument("--config", default="", help="fixed launch configuration "
+                    "lagrangian_threads,near_blocks,bulk_tiles_y,activation_stride[,bulk_nodes_per_thread] "
+                    "instead of the autotuner")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -266,12 +266,15 @@ typedef struct {
     int32_t bulk_tiles_y;       /* 32 x 4 node tiles per bulk lattice block, stacked in y: 1, 2 or 4 */
     int32_t activation_stride;  /* every k-th element centroid schedules the near tiles around it
                                  * (over a radius grown to cover the k - 1 between): 1, 2 or 4 */
+    int32_t bulk_nodes_per_thread; /* nodes each bulk lattice thread updates: 1 or 2 */
+    int32_t reserved;           /* 0 */
 } lbib_launch_config;
 
 /* Current configuration.  Like lbib_advance, the call completes the set-up
  * (no membranes can be added afterwards) and fills in the defaults: membrane
  * blocks of 256 threads when the bodies outnumber half the SMs (else 512),
- * near kernel 4 blocks per SM, one tile per bulk block, activation stride 4. */
+ * near kernel 4 blocks per SM, one tile per bulk block and one node per bulk
+ * thread, activation stride 4. */
 lbib_status lbib_get_launch_config(lbib_ctx* ctx, lbib_launch_config* out);
 
 /* Sets the configuration used by the following steps (re-captures the step
@@ -283,7 +286,7 @@ lbib_status lbib_set_launch_config(lbib_ctx* ctx, const lbib_launch_config* cfg)
  * state: a device snapshot of the state is taken, each candidate advances it
  * by steps_per_trial >= 1 steps (after two warm-up steps) timed with CUDA
  * events, the snapshot is restored, and the fastest candidate is kept.  The
- * search is coordinate-wise: bulk tiles per block, then membrane block size,
+ * search is coordinate-wise: bulk tiles per block and nodes per thread, then membrane block size,
  * then activation stride, then near-kernel blocks.  On return the state, the step count and the
  * observables cursors are as on entry; *chosen (may be NULL) receives the
  * configuration.  Needs device memory for one more copy of the state. */

@@ -643,6 +643,7 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     d.ninst = ninst;
     d.lag_threads = 0;  // 0: default, set at finalize
     d.bulk_tiles_y = 1;
+    d.bulk_nodes_per_thread = 1;
     d.act_stride = ACT_STRIDE;
     auto bail = [&](lbib_status s) {
         std::string m = ctx->err;
@@ -1226,7 +1227,8 @@ bool valid_config(const lbib_launch_config& c)
 {
     return (c.lagrangian_threads == 256 || c.lagrangian_threads == 512) && c.near_blocks >= 1 &&
            (c.bulk_tiles_y == 1 || c.bulk_tiles_y == 2 || c.bulk_tiles_y == 4) &&
-           (c.activation_stride == 1 || c.activation_stride == 2 || c.activation_stride == 4);
+           (c.activation_stride == 1 || c.activation_stride == 2 || c.activation_stride == 4) &&
+           (c.bulk_nodes_per_thread == 1 || c.bulk_nodes_per_thread == 2) && c.reserved == 0;
 }
 
 lbib_launch_config current_config(const lbib_ctx* ctx)
@@ -1236,6 +1238,7 @@ lbib_launch_config current_config(const lbib_ctx* ctx)
     c.near_blocks = ctx->near_grid;
     c.bulk_tiles_y = ctx->d.bulk_tiles_y;
     c.activation_stride = ctx->d.act_stride;
+    c.bulk_nodes_per_thread = ctx->d.bulk_nodes_per_thread;
     return c;
 }
 
@@ -1256,6 +1259,7 @@ void apply_config(lbib_ctx* ctx, const lbib_launch_config& c)
     ctx->near_grid = c.near_blocks;
     ctx->d.bulk_tiles_y = c.bulk_tiles_y;
     ctx->d.act_stride = c.activation_stride;
+    ctx->d.bulk_nodes_per_thread = c.bulk_nodes_per_thread;
 }
 
 }  // namespace
@@ -1366,7 +1370,8 @@ lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_co
     auto consider = [&](lbib_launch_config c) {
         if (s != LBIB_OK || !valid_config(c)) return;
         if (c.lagrangian_threads == best.lagrangian_threads && c.near_blocks == best.near_blocks &&
-            c.bulk_tiles_y == best.bulk_tiles_y && c.activation_stride == best.activation_stride)
+            c.bulk_tiles_y == best.bulk_tiles_y && c.activation_stride == best.activation_stride &&
+            c.bulk_nodes_per_thread == best.bulk_nodes_per_thread)
             return;
         float ms = 0.f;
         s = trial(c, &ms);
@@ -1376,11 +1381,13 @@ lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_co
         }
     };
     const lbib_launch_config start = best;
-    for (int rt : {1, 2, 4}) {
-        lbib_launch_config c = start;
-        c.bulk_tiles_y = rt;
-        consider(c);
-    }
+    for (int npt : {1, 2})
+        for (int rt : {1, 2, 4}) {
+            lbib_launch_config c = start;
+            c.bulk_tiles_y = rt;
+            c.bulk_nodes_per_thread = npt;
+            consider(c);
+        }
     if (d.nbodies) {
         const lbib_launch_config after_bulk = best;
         for (int lt : {256, 512}) {

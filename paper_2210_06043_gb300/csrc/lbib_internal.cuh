@@ -133,6 +133,7 @@ struct Dev {
     int nbodies, nmark, nlig, nv_max;
     int lag_threads;           // Lagrangian block size: 256 or 512 (results do not depend on it)
     int bulk_tiles_y;          // tiles per bulk-kernel block, stacked in y: 1, 2 or 4 (likewise)
+    int bulk_nodes_per_thread; // nodes per bulk-kernel thread: 1 or 2 (likewise)
     double* pos[2];            // [2][nmark] (x block then y block); X^n in pos[n & 1]
     void* posf[2];             // Real [4][nmark]: X^n as float-float pairs (x hi, x lo, y hi, y lo)
     const BodyConst* body;     // [nbodies]

@@ -117,33 +117,44 @@ __device__ __forceinline__ void collide(R g[9], R Fx, R Fy, R omega, R& drho, R&
     }
 }
 
-// One block covers RT tiles stacked in y (a TX x RT TY node box); each warp
-// lies in one tile row and skips its tile when the near kernel owns it.
-template <typename S, typename R, int RT>
-__global__ void __launch_bounds__(TX* TY* RT) k_bulk(Dev d, int p, int slot)
+// One block covers RT tiles stacked in y (a TX x RT TY node box) with
+// TX x (RT TY / NPT) threads; a thread updates NPT nodes of one column, NPT
+// rows apart, issuing all their loads before the first collision (more bytes
+// in flight per thread when fewer threads are resident).  A node is skipped
+// when the near kernel owns its tile.
+template <typename S, typename R, int RT, int NPT>
+__global__ void __launch_bounds__(TX* TY* RT / NPT) k_bulk(Dev d, int p, int slot)
 {
     const Lattice& L = d.L;
-    const int tyl = blockIdx.y * RT + threadIdx.y / TY;  // tile row
-    if (tyl >= L.nty) return;
-    const int t = tyl * L.ntx + blockIdx.x;
-    if (d.nearflag[slot][t]) return;
+    constexpr int ROWS = TY * RT, STEP = ROWS / NPT;
     const int4 ci = d.colinfo[blockIdx.x];
-    int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY * RT + threadIdx.y;
+    const int x = blockIdx.x * TX + threadIdx.x;
     const int xl = x - ci.x;
-    if (xl >= ci.y || y >= L.ny) return;
     const S* __restrict__ fin = static_cast<const S*>(d.f[p]);
     S* __restrict__ fout = static_cast<S*>(d.f[p ^ 1]);
-    R g[9];
-    pull<S, R>(L, fin, x, y, xl, ci.y, g);
-    R drho, ux, uy;
-    collide<R>(g, R(L.gx), R(L.gy), R(L.omega), drho, ux, uy);
-    if (!(drho > R(-1)) || !isfinite(ux + uy)) atomicOr(d.status, ST_DIVERGED);
-    const int base = y * L.nxp + x;
+    R g[NPT][9];
+    bool act[NPT];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) st<S, R>(fout + q * L.qstride + base, g[q]);
+    for (int j = 0; j < NPT; ++j) {
+        const int y = blockIdx.y * ROWS + threadIdx.y + j * STEP;
+        const int tyl = y / TY;
+        act[j] = (y < L.ny) && (xl < ci.y) && !d.nearflag[slot][tyl * L.ntx + blockIdx.x];
+        if (act[j]) pull<S, R>(L, fin, x, y, xl, ci.y, g[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        if (!act[j]) continue;
+        const int y = blockIdx.y * ROWS + threadIdx.y + j * STEP;
+        R drho, ux, uy;
+        collide<R>(g[j], R(L.gx), R(L.gy), R(L.omega), drho, ux, uy);
+        if (!(drho > R(-1)) || !isfinite(ux + uy)) atomicOr(d.status, ST_DIVERGED);
+        const int base = y * L.nxp + x;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) st<S, R>(fout + q * L.qstride + base, g[j][q]);
+    }
 }
 
-constexpr int NEAR_CHUNK_WORDS = 8;  // mask words staged per round (<= 256 markers)
+constexpr int NEAR_CHUNK_WORDS = 16;  // mask words staged per round (<= 512 markers)
 
 template <typename S, typename R>
 __global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
@@ -164,25 +175,39 @@ __global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
     R* fx_o = static_cast<R*>(d.fx);
     R* fy_o = static_cast<R*>(d.fy);
     const int tid = threadIdx.y * TX + threadIdx.x;
+    constexpr int CAP = 32 * NEAR_CHUNK_WORDS;
     __shared__ uint32_t s_words[NEAR_CHUNK_WORDS];
     __shared__ int s_off[NEAR_CHUNK_WORDS];
     __shared__ int s_n;
-    __shared__ int s_ix[32 * NEAR_CHUNK_WORDS], s_iy[32 * NEAR_CHUNK_WORDS];
-    __shared__ R s_fx[32 * NEAR_CHUNK_WORDS], s_fy[32 * NEAR_CHUNK_WORDS];
-    __shared__ R s_Fx[32 * NEAR_CHUNK_WORDS], s_Fy[32 * NEAR_CHUNK_WORDS];
+    // per staged marker: stencil origin, the four x and four y kernel weights
+    // phi(1 - a + frac), a = 0..3, over its columns / rows, and F ds
+    __shared__ int s_ix[CAP], s_iy[CAP];
+    __shared__ R s_wx[CAP][4], s_wy[CAP][4];
+    __shared__ R s_Fx[CAP], s_Fy[CAP];
+    // the next tile's list entry, column record and first mask word are
+    // loaded while the current tile is updated (a block walks its tiles in turn)
+    int t_next = (blockIdx.x < cnt) ? d.list[c][blockIdx.x] : 0;
+    int4 ci_next = d.colinfo[t_next % L.ntx];
+    uint32_t w_next = (tid < min(NEAR_CHUNK_WORDS, d.mw)) ? mask[(size_t)t_next * d.mw + tid] : 0u;
     for (int k = blockIdx.x; k < cnt; k += gridDim.x) {
-        const int t = d.list[c][k];
+        const int t = t_next;
+        const int4 ci = ci_next;
+        const uint32_t w_first = w_next;
         const int tx = t % L.ntx, ty = t / L.ntx;
-        const int4 ci = d.colinfo[tx];
         const int x = tx * TX + threadIdx.x, y = ty * TY + threadIdx.y;
         const int xl = x - ci.x;
         const bool live = (xl < ci.y && y < L.ny);
         R g[9];
         if (live) pull<S, R>(L, fin, x, y, xl, ci.y, g);  // issued before the marker gather
+        if (k + (int)gridDim.x < cnt) {
+            t_next = d.list[c][k + gridDim.x];
+            ci_next = d.colinfo[t_next % L.ntx];
+            if (tid < min(NEAR_CHUNK_WORDS, d.mw)) w_next = mask[(size_t)t_next * d.mw + tid];
+        }
         R Fx = R(L.gx), Fy = R(L.gy);
         for (int w0 = 0; w0 < d.mw; w0 += NEAR_CHUNK_WORDS) {
             const int nw = min(NEAR_CHUNK_WORDS, d.mw - w0);
-            if (tid < nw) s_words[tid] = mask[(size_t)t * d.mw + w0 + tid];
+            if (tid < nw) s_words[tid] = (w0 == 0) ? w_first : mask[(size_t)t * d.mw + w0 + tid];
             __syncthreads();
             if (tid < 32) {
                 int cnt_w = (tid < nw) ? __popc(s_words[tid]) : 0;
@@ -196,6 +221,8 @@ __global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
                 if (tid == 31) s_n = incl;
             }
             __syncthreads();
+            const int n = s_n;
+            if (n == 0) continue;  // uniform: no marker of this chunk spreads here
             for (int b = tid; b < nw * 32; b += TX * TY) {
                 const int l = b >> 5, bit = b & 31;
                 const uint32_t wd = s_words[l];
@@ -204,20 +231,23 @@ __global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
                     const int id = ci.z + (w0 + l) * 32 + bit;  // instance-local bit -> batch marker
                     s_ix[pos] = mki[id];
                     s_iy[pos] = mki[nm + id];
-                    s_fx[pos] = mkf[id];
-                    s_fy[pos] = mkf[nm + id];
+                    const R fx = mkf[id], fy = mkf[nm + id];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        // X - (ix - 1 + a) = 1 - a + frac, as the node-side difference below
+                        s_wx[pos][a] = peskin<R>(R(1 - a) + fx);
+                        s_wy[pos][a] = peskin<R>(R(1 - a) + fy);
+                    }
                     s_Fx[pos] = mkf[2 * nm + id];
                     s_Fy[pos] = mkf[3 * nm + id];
                 }
             }
             __syncthreads();
-            const int n = s_n;
             for (int q = 0; q < n; ++q) {
-                // X - x = (floor(X) - x) + frac, exact small integer plus fraction
-                R rx = R(s_ix[q] - x) + s_fx[q];
-                R ry = R(s_iy[q] - y) + s_fy[q];
-                if (fabs(rx) < R(2) && fabs(ry) < R(2)) {
-                    R wt = peskin<R>(rx) * peskin<R>(ry);
+                // node (x, y) in the marker's 4 x 4 stencil [ix - 1, ix + 2] x [iy - 1, iy + 2]
+                const int a = x - s_ix[q] + 1, b = y - s_iy[q] + 1;
+                if ((unsigned)a < 4u && (unsigned)b < 4u) {
+                    const R wt = s_wx[q][a] * s_wy[q][b];
                     Fx += wt * s_Fx[q];
                     Fy += wt * s_Fy[q];
                 }
@@ -355,20 +385,25 @@ __global__ void k_rebuild_mask(Dev d, int parity, int slot)
 
 // ------------------------------------------------------------------ launchers
 
-template <int RT>
+template <int RT, int NPT>
 static void launch_bulk_rt(const Dev& d, int prec, int parity, int slot, cudaStream_t s)
 {
-    dim3 grid(d.L.ntx, (d.L.nty + RT - 1) / RT), block(TX, TY * RT);
-    if (prec == PREC_F64) k_bulk<double, double, RT><<<grid, block, 0, s>>>(d, parity, slot);
-    else k_bulk<float, float, RT><<<grid, block, 0, s>>>(d, parity, slot);
+    dim3 grid(d.L.ntx, (d.L.nty + RT - 1) / RT), block(TX, TY * RT / NPT);
+    if (prec == PREC_F64) k_bulk<double, double, RT, NPT><<<grid, block, 0, s>>>(d, parity, slot);
+    else k_bulk<float, float, RT, NPT><<<grid, block, 0, s>>>(d, parity, slot);
 }
 
 cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, int slot, cudaStream_t s)
 {
-    switch (d.bulk_tiles_y) {
-    case 2: launch_bulk_rt<2>(d, prec, parity, slot, s); break;
-    case 4: launch_bulk_rt<4>(d, prec, parity, slot, s); break;
-    default: launch_bulk_rt<1>(d, prec, parity, slot, s); break;
+    const int v = 10 * (d.bulk_tiles_y == 2 || d.bulk_tiles_y == 4 ? d.bulk_tiles_y : 1) +
+                  (d.bulk_nodes_per_thread == 2 ? 2 : 1);
+    switch (v) {
+    case 12: launch_bulk_rt<1, 2>(d, prec, parity, slot, s); break;
+    case 21: launch_bulk_rt<2, 1>(d, prec, parity, slot, s); break;
+    case 22: launch_bulk_rt<2, 2>(d, prec, parity, slot, s); break;
+    case 41: launch_bulk_rt<4, 1>(d, prec, parity, slot, s); break;
+    case 42: launch_bulk_rt<4, 2>(d, prec, parity, slot, s); break;
+    default: launch_bulk_rt<1, 1>(d, prec, parity, slot, s); break;
     }
     return cudaGetLastError();
 }

@@ -56,7 +56,8 @@ class lbib_obs(ctypes.Structure):
 
 class lbib_launch_config(ctypes.Structure):
     _fields_ = [("lagrangian_threads", ctypes.c_int32), ("near_blocks", ctypes.c_int32),
-                ("bulk_tiles_y", ctypes.c_int32), ("activation_stride", ctypes.c_int32)]
+                ("bulk_tiles_y", ctypes.c_int32), ("activation_stride", ctypes.c_int32),
+                ("bulk_nodes_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -199,7 +200,7 @@ def lbib_lattice_advance_noalloc(params: lbib_fluid_params, f_device_ptr: int, n
 
 def _config_dict(c: lbib_launch_config) -> dict:
     return dict(lagrangian_threads=c.lagrangian_threads, near_blocks=c.near_blocks, bulk_tiles_y=c.bulk_tiles_y,
-                activation_stride=c.activation_stride)
+                activation_stride=c.activation_stride, bulk_nodes_per_thread=c.bulk_nodes_per_thread)
 
 
 class Solver:
@@ -352,9 +353,11 @@ class Solver:
         self._c(self.lib.lbib_get_launch_config(self.ctx, ctypes.byref(c)))
         return _config_dict(c)
 
-    def set_launch_config(self, lagrangian_threads, near_blocks, bulk_tiles_y, activation_stride=4):
+    def set_launch_config(self, lagrangian_threads, near_blocks, bulk_tiles_y, activation_stride=4,
+                          bulk_nodes_per_thread=1):
         c = lbib_launch_config(lagrangian_threads=int(lagrangian_threads), near_blocks=int(near_blocks),
-                               bulk_tiles_y=int(bulk_tiles_y), activation_stride=int(activation_stride))
+                               bulk_tiles_y=int(bulk_tiles_y), activation_stride=int(activation_stride),
+                               bulk_nodes_per_thread=int(bulk_nodes_per_thread))
         self._c(self.lib.lbib_set_launch_config(self.ctx, ctypes.byref(c)))
 
     def autotune(self, steps_per_trial=20) -> dict:

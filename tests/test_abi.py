@@ -54,7 +54,7 @@ int main(void) {
   S(lbib_adhesion_params); O(lbib_adhesion_params, sigma); O(lbib_adhesion_params, xi);
   S(lbib_obs); O(lbib_obs, n_l); O(lbib_obs, n_bound); O(lbib_obs, status);
   S(lbib_launch_config); O(lbib_launch_config, near_blocks); O(lbib_launch_config, bulk_tiles_y);
-  O(lbib_launch_config, activation_stride);
+  O(lbib_launch_config, activation_stride); O(lbib_launch_config, bulk_nodes_per_thread);
   return 0;
 }
 '''
