@@ -634,6 +634,7 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     L.rho_out = P->rho_out;
     L.gx = P->gx;
     L.gy = P->gy;
+    set_float_params(L);
     Dev& d = ctx->d;
     d.list_cap = L.ntiles;
     d.dcut = 2.0;

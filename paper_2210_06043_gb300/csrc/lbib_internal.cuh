@@ -62,7 +62,28 @@ struct Lattice {
     int bc;                   // lbib_bc_mode
     int qstride;              // ny * nxp
     double tau, omega, nu, umax, rho_out, gx, gy;
+    // the same parameters rounded to FP32 once on the host: FP32 kernels read
+    // these instead of converting the doubles per node (FP64 is a narrow pipe)
+    float omega_f, umax_f, rho_out_f, gx_f, gy_f;
 };
+
+// Lattice parameter in the compute type R: the double for R = double, the
+// host-rounded float for R = float.
+template <typename R>
+__host__ __device__ __forceinline__ R lat_param(double d, float f);
+template <>
+__host__ __device__ __forceinline__ double lat_param<double>(double d, float) { return d; }
+template <>
+__host__ __device__ __forceinline__ float lat_param<float>(double, float f) { return f; }
+
+inline void set_float_params(Lattice& L)
+{
+    L.omega_f = (float)L.omega;
+    L.umax_f = (float)L.umax;
+    L.rho_out_f = (float)L.rho_out;
+    L.gx_f = (float)L.gx;
+    L.gy_f = (float)L.gy;
+}
 
 // Per tile column: origin and width of its instance, the instance's first
 // marker (marker ids in the tile bit masks are local to the instance) and the

@@ -30,7 +30,7 @@ template <typename R>
 __device__ __forceinline__ R inlet_profile(const Lattice& L, int y)
 {
     R yy = R(y) + R(0.5), H = R(L.ny);
-    return R(4) * R(L.umax) * yy * (H - yy) / (H * H);
+    return R(4) * lat_param<R>(L.umax, L.umax_f) * yy * (H - yy) / (H * H);
 }
 
 // Zou-He on deviations g_i = f_i - w_i (the rest weights cancel pairwise).
@@ -88,33 +88,63 @@ __device__ __forceinline__ void pull(const Lattice& L, const S* __restrict__ fin
     }
     if (L.bc == LBIB_BC_INLET_OUTLET) {
         if (xl == 0) zou_he_inlet<R>(g, inlet_profile<R>(L, y));
-        else if (xl == nxi - 1) zou_he_outlet<R>(g, R(L.rho_out));
+        else if (xl == nxi - 1) zou_he_outlet<R>(g, lat_param<R>(L.rho_out, L.rho_out_f));
     }
 }
 
 // Moments with the half-force shift and the Guo-forced BGK collision, in place.
+// Opposite directions q, o (e_o = -e_q) share the even part of the
+// equilibrium, A = w (drho + rho (9/2 (e.u)^2 - 3/2 u.u)), and differ in the
+// sign of the odd part, B = 3 w rho e_q.u (Eq. 2); likewise the forcing term
+// of Eq. 4.  FORCED = false is the same update for F = 0 (it gives the same
+// values as FORCED = true with F = 0, without the source arithmetic).
+template <typename R, bool FORCED>
+__device__ __forceinline__ void collide_t(R g[9], R Fx, R Fy, R omega, R& drho, R& ux, R& uy)
+{
+    drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+    const R rho = R(1) + drho;
+    R jx = (g[1] + g[5] + g[8]) - (g[3] + g[6] + g[7]);
+    R jy = (g[2] + g[5] + g[6]) - (g[4] + g[7] + g[8]);
+    if (FORCED) {
+        jx += R(0.5) * Fx;
+        jy += R(0.5) * Fy;
+    }
+    const R inv = R(1) / rho;
+    ux = jx * inv;
+    uy = jy * inv;
+    const R u2 = R(1.5) * (ux * ux + uy * uy);
+    const R uF = FORCED ? ux * Fx + uy * Fy : R(0);
+    const R cf = R(1) - R(0.5) * omega;
+    // rest population
+    {
+        const R geq = wq<R>(0) * (drho - rho * u2);
+        g[0] = g[0] - omega * (g[0] - geq);
+        if (FORCED) g[0] += cf * wq<R>(0) * (R(-3) * uF);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int q = (k < 2) ? 1 + k : 3 + k;  // 1, 2, 5, 6
+        const int o = op(q);                    // 3, 4, 7, 8
+        const R w = wq<R>(q);
+        const R eu = R(cx(q)) * ux + R(cy(q)) * uy;
+        const R A = w * (drho + rho * (R(4.5) * eu * eu - u2));
+        const R B = w * rho * (R(3) * eu);
+        g[q] = g[q] - omega * (g[q] - (A + B));
+        g[o] = g[o] - omega * (g[o] - (A - B));
+        if (FORCED) {
+            const R eF = R(cx(q)) * Fx + R(cy(q)) * Fy;
+            const R even = cf * w * (R(9) * eu * eF - R(3) * uF);
+            const R odd = cf * w * (R(3) * eF);
+            g[q] += even + odd;
+            g[o] += even - odd;
+        }
+    }
+}
+
 template <typename R>
 __device__ __forceinline__ void collide(R g[9], R Fx, R Fy, R omega, R& drho, R& ux, R& uy)
 {
-    drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-    R rho = R(1) + drho;
-    R jx = (g[1] + g[5] + g[8]) - (g[3] + g[6] + g[7]) + R(0.5) * Fx;
-    R jy = (g[2] + g[5] + g[6]) - (g[4] + g[7] + g[8]) + R(0.5) * Fy;
-    R inv = R(1) / rho;
-    ux = jx * inv;
-    uy = jy * inv;
-    R u2 = R(1.5) * (ux * ux + uy * uy);
-    R uF = ux * Fx + uy * Fy;
-    R cf = R(1) - R(0.5) * omega;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        R eu = R(cx(q)) * ux + R(cy(q)) * uy;
-        R eF = R(cx(q)) * Fx + R(cy(q)) * Fy;
-        R w = wq<R>(q);
-        R geq = w * (drho + rho * (R(3) * eu + R(4.5) * eu * eu - u2));
-        R src = cf * w * (R(3) * (eF - uF) + R(9) * eu * eF);
-        g[q] = g[q] - omega * (g[q] - geq) + src;
-    }
+    collide_t<R, true>(g, Fx, Fy, omega, drho, ux, uy);
 }
 
 // One block covers RT tiles stacked in y (a TX x RT TY node box) with
@@ -122,7 +152,7 @@ __device__ __forceinline__ void collide(R g[9], R Fx, R Fy, R omega, R& drho, R&
 // rows apart, issuing all their loads before the first collision (more bytes
 // in flight per thread when fewer threads are resident).  A node is skipped
 // when the near kernel owns its tile.
-template <typename S, typename R, int RT, int NPT>
+template <typename S, typename R, int RT, int NPT, bool FORCED>
 __global__ void __launch_bounds__(TX* TY* RT / NPT) k_bulk(Dev d, int p, int slot)
 {
     const Lattice& L = d.L;
@@ -146,7 +176,8 @@ __global__ void __launch_bounds__(TX* TY* RT / NPT) k_bulk(Dev d, int p, int slo
         if (!act[j]) continue;
         const int y = blockIdx.y * ROWS + threadIdx.y + j * STEP;
         R drho, ux, uy;
-        collide<R>(g[j], R(L.gx), R(L.gy), R(L.omega), drho, ux, uy);
+        collide_t<R, FORCED>(g[j], lat_param<R>(L.gx, L.gx_f), lat_param<R>(L.gy, L.gy_f),
+                             lat_param<R>(L.omega, L.omega_f), drho, ux, uy);
         if (!(drho > R(-1)) || !isfinite(ux + uy)) atomicOr(d.status, ST_DIVERGED);
         const int base = y * L.nxp + x;
 #pragma unroll
@@ -204,7 +235,7 @@ __global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
             ci_next = d.colinfo[t_next % L.ntx];
             if (tid < min(NEAR_CHUNK_WORDS, d.mw)) w_next = mask[(size_t)t_next * d.mw + tid];
         }
-        R Fx = R(L.gx), Fy = R(L.gy);
+        R Fx = lat_param<R>(L.gx, L.gx_f), Fy = lat_param<R>(L.gy, L.gy_f);
         for (int w0 = 0; w0 < d.mw; w0 += NEAR_CHUNK_WORDS) {
             const int nw = min(NEAR_CHUNK_WORDS, d.mw - w0);
             if (tid < nw) s_words[tid] = (w0 == 0) ? w_first : mask[(size_t)t * d.mw + w0 + tid];
@@ -256,7 +287,7 @@ __global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
         }
         if (live) {
             R drho, ux, uy;
-            collide<R>(g, Fx, Fy, R(L.omega), drho, ux, uy);
+            collide<R>(g, Fx, Fy, lat_param<R>(L.omega, L.omega_f), drho, ux, uy);
             if (!(drho > R(-1)) || !isfinite(ux + uy)) atomicOr(d.status, ST_DIVERGED);
             const int base = y * L.nxp + x;
 #pragma unroll
@@ -301,7 +332,7 @@ __global__ void k_macro(Dev d, int buf, int64_t m, int x0, int inx, O* rho_o, O*
     const int x = x0 + xl;
     int t = blockIdx.y * L.ntx + x / TX;
     int base = y * L.nxp + x, ob = y * inx + xl;
-    R Fx = R(L.gx), Fy = R(L.gy);
+    R Fx = lat_param<R>(L.gx, L.gx_f), Fy = lat_param<R>(L.gy, L.gy_f);
     if (d.fresh[t] == (int32_t)m) {
         Fx = static_cast<const R*>(d.fx)[base];
         Fy = static_cast<const R*>(d.fy)[base];
@@ -389,8 +420,14 @@ template <int RT, int NPT>
 static void launch_bulk_rt(const Dev& d, int prec, int parity, int slot, cudaStream_t s)
 {
     dim3 grid(d.L.ntx, (d.L.nty + RT - 1) / RT), block(TX, TY * RT / NPT);
-    if (prec == PREC_F64) k_bulk<double, double, RT, NPT><<<grid, block, 0, s>>>(d, parity, slot);
-    else k_bulk<float, float, RT, NPT><<<grid, block, 0, s>>>(d, parity, slot);
+    const bool forced = d.L.gx != 0.0 || d.L.gy != 0.0;  // uniform body force (PERIODIC_FORCE mode)
+    if (prec == PREC_F64) {
+        if (forced) k_bulk<double, double, RT, NPT, true><<<grid, block, 0, s>>>(d, parity, slot);
+        else k_bulk<double, double, RT, NPT, false><<<grid, block, 0, s>>>(d, parity, slot);
+    } else {
+        if (forced) k_bulk<float, float, RT, NPT, true><<<grid, block, 0, s>>>(d, parity, slot);
+        else k_bulk<float, float, RT, NPT, false><<<grid, block, 0, s>>>(d, parity, slot);
+    }
 }
 
 cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, int slot, cudaStream_t s)

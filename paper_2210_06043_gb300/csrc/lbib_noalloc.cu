@@ -120,6 +120,7 @@ extern "C" lbib_status lbib_lattice_advance_noalloc(const lbib_fluid_params* P, 
     L.rho_out = P->rho_out;
     L.gx = P->gx;
     L.gy = P->gy;
+    set_float_params(L);
     const int prec = (P->storage == LBIB_STORE_FP64) ? PREC_F64 : PREC_F32;
     const size_t s = (prec == PREC_F64) ? 8 : 4;
     const size_t need_flags = up256((size_t)L.ntiles * 4);
