@@ -185,10 +185,18 @@ __global__ void __launch_bounds__(TX* TY* RT / NPT) k_bulk(Dev d, int p, int slo
     }
 }
 
-constexpr int NEAR_CHUNK_WORDS = 16;  // mask words staged per round (<= 512 markers)
+constexpr int NEAR_WARPS = 4;     // warps per near-kernel block; each warp updates one tile at a time
+constexpr int NEAR_STAGE = 64;    // markers a warp stages per pass
 
+// Near-membrane update: each warp walks its share of the near-tile list and
+// updates a whole 32 x 4 tile, lane l owning column l (its four nodes' loads
+// are issued together).  The tile's bit mask is read 32 words per round (one
+// word per lane); the set bits are ranked across the warp (ascending marker
+// order) and staged in passes of NEAR_STAGE markers with their stencil
+// weights; each node then adds the forces of the staged markers whose 4 x 4
+// stencil holds it, in that order.  Warp-local throughout: no block barrier.
 template <typename S, typename R>
-__global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
+__global__ void __launch_bounds__(32 * NEAR_WARPS) k_near(Dev d, int p)
 {
     const Lattice& L = d.L;
     const int64_t m = *d.step;  // lattice step (the Lagrangian counter has reached it)
@@ -205,101 +213,116 @@ __global__ void __launch_bounds__(TX* TY) k_near(Dev d, int p)
     R* uy_o = static_cast<R*>(d.uy);
     R* fx_o = static_cast<R*>(d.fx);
     R* fy_o = static_cast<R*>(d.fy);
-    const int tid = threadIdx.y * TX + threadIdx.x;
-    constexpr int CAP = 32 * NEAR_CHUNK_WORDS;
-    __shared__ uint32_t s_words[NEAR_CHUNK_WORDS];
-    __shared__ int s_off[NEAR_CHUNK_WORDS];
-    __shared__ int s_n;
-    // per staged marker: stencil origin, the four x and four y kernel weights
-    // phi(1 - a + frac), a = 0..3, over its columns / rows, and F ds
-    __shared__ int s_ix[CAP], s_iy[CAP];
-    __shared__ R s_wx[CAP][4], s_wy[CAP][4];
-    __shared__ R s_Fx[CAP], s_Fy[CAP];
-    // the next tile's list entry, column record and first mask word are
-    // loaded while the current tile is updated (a block walks its tiles in turn)
-    int t_next = (blockIdx.x < cnt) ? d.list[c][blockIdx.x] : 0;
-    int4 ci_next = d.colinfo[t_next % L.ntx];
-    uint32_t w_next = (tid < min(NEAR_CHUNK_WORDS, d.mw)) ? mask[(size_t)t_next * d.mw + tid] : 0u;
-    for (int k = blockIdx.x; k < cnt; k += gridDim.x) {
-        const int t = t_next;
-        const int4 ci = ci_next;
-        const uint32_t w_first = w_next;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // per warp: stencil origin, the four x and y weights phi(1 - a + frac),
+    // a = 0..3, over the marker's columns / rows, and F ds
+    __shared__ int s_ix[NEAR_WARPS][NEAR_STAGE], s_iy[NEAR_WARPS][NEAR_STAGE];
+    __shared__ R s_wx[NEAR_WARPS][NEAR_STAGE][4], s_wy[NEAR_WARPS][NEAR_STAGE][4];
+    __shared__ R s_Fx[NEAR_WARPS][NEAR_STAGE], s_Fy[NEAR_WARPS][NEAR_STAGE];
+    const R gx = lat_param<R>(L.gx, L.gx_f), gy = lat_param<R>(L.gy, L.gy_f);
+    const R omega = lat_param<R>(L.omega, L.omega_f);
+    const int k0 = blockIdx.x * NEAR_WARPS + wid, kstep = gridDim.x * NEAR_WARPS;
+    for (int k = k0; k < cnt; k += kstep) {
+        const int t = d.list[c][k];
         const int tx = t % L.ntx, ty = t / L.ntx;
-        const int x = tx * TX + threadIdx.x, y = ty * TY + threadIdx.y;
+        const int4 ci = d.colinfo[tx];
+        const int x = tx * TX + lane, y0 = ty * TY;
         const int xl = x - ci.x;
-        const bool live = (xl < ci.y && y < L.ny);
-        R g[9];
-        if (live) pull<S, R>(L, fin, x, y, xl, ci.y, g);  // issued before the marker gather
-        if (k + (int)gridDim.x < cnt) {
-            t_next = d.list[c][k + gridDim.x];
-            ci_next = d.colinfo[t_next % L.ntx];
-            if (tid < min(NEAR_CHUNK_WORDS, d.mw)) w_next = mask[(size_t)t_next * d.mw + tid];
+        bool live[TY];
+        R g[TY][9];
+#pragma unroll
+        for (int r = 0; r < TY; ++r) {
+            live[r] = (xl < ci.y && y0 + r < L.ny);
+            if (live[r]) pull<S, R>(L, fin, x, y0 + r, xl, ci.y, g[r]);  // issued before the marker gather
         }
-        R Fx = lat_param<R>(L.gx, L.gx_f), Fy = lat_param<R>(L.gy, L.gy_f);
-        for (int w0 = 0; w0 < d.mw; w0 += NEAR_CHUNK_WORDS) {
-            const int nw = min(NEAR_CHUNK_WORDS, d.mw - w0);
-            if (tid < nw) s_words[tid] = (w0 == 0) ? w_first : mask[(size_t)t * d.mw + w0 + tid];
-            __syncthreads();
-            if (tid < 32) {
-                int cnt_w = (tid < nw) ? __popc(s_words[tid]) : 0;
-                int incl = cnt_w;
+        R Fx[TY], Fy[TY];
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int v = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (tid >= o) incl += v;
-                }
-                if (tid < nw) s_off[tid] = incl - cnt_w;
-                if (tid == 31) s_n = incl;
+        for (int r = 0; r < TY; ++r) {
+            Fx[r] = gx;
+            Fy[r] = gy;
+        }
+        for (int w0 = 0; w0 < d.mw; w0 += 32) {
+            const bool has = w0 + lane < d.mw;
+            const uint32_t wd = has ? mask[(size_t)t * d.mw + w0 + lane] : 0u;
+            // exclusive prefix of the set-bit counts across the lanes
+            const int cw = __popc(wd);
+            int incl = cw;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
             }
-            __syncthreads();
-            const int n = s_n;
-            if (n == 0) continue;  // uniform: no marker of this chunk spreads here
-            for (int b = tid; b < nw * 32; b += TX * TY) {
-                const int l = b >> 5, bit = b & 31;
-                const uint32_t wd = s_words[l];
-                if ((wd >> bit) & 1u) {
-                    const int pos = s_off[l] + __popc(wd & ((1u << bit) - 1u));
-                    const int id = ci.z + (w0 + l) * 32 + bit;  // instance-local bit -> batch marker
-                    s_ix[pos] = mki[id];
-                    s_iy[pos] = mki[nm + id];
-                    const R fx = mkf[id], fy = mkf[nm + id];
+            const int off = incl - cw;
+            const int n = __shfl_sync(0xffffffffu, incl, 31);
+            if (has && wd) mask[(size_t)t * d.mw + w0 + lane] = 0u;  // consumed
+            for (int base = 0; base < n; base += NEAR_STAGE) {
+                // stage the markers of rank [base, base + NEAR_STAGE): lane l takes
+                // ranks base + l, base + l + 32, ...; the word holding rank r is the
+                // last lane whose exclusive prefix is <= r (binary search by shuffles)
+                const int ns = min(NEAR_STAGE, n - base);
+                for (int pos = lane; pos < 32 * ((ns + 31) / 32); pos += 32) {
+                    const int r = base + pos;
+                    int src = 0;
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        // X - (ix - 1 + a) = 1 - a + frac, as the node-side difference below
-                        s_wx[pos][a] = peskin<R>(R(1 - a) + fx);
-                        s_wy[pos][a] = peskin<R>(R(1 - a) + fy);
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const int cand = src + step;
+                        const int co = __shfl_sync(0xffffffffu, off, cand & 31);
+                        if (cand < 32 && co <= r) src = cand;
                     }
-                    s_Fx[pos] = mkf[2 * nm + id];
-                    s_Fy[pos] = mkf[3 * nm + id];
-                }
-            }
-            __syncthreads();
-            for (int q = 0; q < n; ++q) {
-                // node (x, y) in the marker's 4 x 4 stencil [ix - 1, ix + 2] x [iy - 1, iy + 2]
-                const int a = x - s_ix[q] + 1, b = y - s_iy[q] + 1;
-                if ((unsigned)a < 4u && (unsigned)b < 4u) {
-                    const R wt = s_wx[q][a] * s_wy[q][b];
-                    Fx += wt * s_Fx[q];
-                    Fy += wt * s_Fy[q];
-                }
-            }
-            __syncthreads();
-        }
-        if (live) {
-            R drho, ux, uy;
-            collide<R>(g, Fx, Fy, lat_param<R>(L.omega, L.omega_f), drho, ux, uy);
-            if (!(drho > R(-1)) || !isfinite(ux + uy)) atomicOr(d.status, ST_DIVERGED);
-            const int base = y * L.nxp + x;
+                    const uint32_t sw = __shfl_sync(0xffffffffu, wd, src);
+                    const int so = __shfl_sync(0xffffffffu, off, src);
+                    if (pos < ns) {
+                        const int bit = (int)__fns(sw, 0u, r - so + 1);  // (r - so + 1)-th set bit
+                        const int id = ci.z + (w0 + src) * 32 + bit;     // instance-local bit -> batch marker
+                        s_ix[wid][pos] = mki[id];
+                        s_iy[wid][pos] = mki[nm + id];
+                        const R fx = mkf[id], fy = mkf[nm + id];
 #pragma unroll
-            for (int q = 0; q < 9; ++q) st<S, R>(fout + q * L.qstride + base, g[q]);
+                        for (int a = 0; a < 4; ++a) {
+                            // X - (ix - 1 + a) = 1 - a + frac, as the node-side difference below
+                            s_wx[wid][pos][a] = peskin<R>(R(1 - a) + fx);
+                            s_wy[wid][pos][a] = peskin<R>(R(1 - a) + fy);
+                        }
+                        s_Fx[wid][pos] = mkf[2 * nm + id];
+                        s_Fy[wid][pos] = mkf[3 * nm + id];
+                    }
+                }
+                __syncwarp();
+                for (int q = 0; q < ns; ++q) {
+                    // node (x, y) in the marker's 4 x 4 stencil [ix - 1, ix + 2] x [iy - 1, iy + 2]
+                    const int a = x - s_ix[wid][q] + 1;
+                    if ((unsigned)a >= 4u) continue;
+                    const R wxa = s_wx[wid][q][a], Fq = s_Fx[wid][q], Gq = s_Fy[wid][q];
+                    const int b0 = y0 - s_iy[wid][q] + 1;
+#pragma unroll
+                    for (int r = 0; r < TY; ++r) {
+                        const int b = b0 + r;
+                        if ((unsigned)b < 4u) {
+                            const R wt = wxa * s_wy[wid][q][b];
+                            Fx[r] += wt * Fq;
+                            Fy[r] += wt * Gq;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < TY; ++r) {
+            if (!live[r]) continue;
+            R drho, ux, uy;
+            collide<R>(g[r], Fx[r], Fy[r], omega, drho, ux, uy);
+            if (!(drho > R(-1)) || !isfinite(ux + uy)) atomicOr(d.status, ST_DIVERGED);
+            const int base = (y0 + r) * L.nxp + x;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) st<S, R>(fout + q * L.qstride + base, g[r][q]);
             drho_o[base] = drho;
             ux_o[base] = ux;
             uy_o[base] = uy;
-            fx_o[base] = Fx;
-            fy_o[base] = Fy;
+            fx_o[base] = Fx[r];
+            fy_o[base] = Fy[r];
         }
-        for (int w = tid; w < d.mw; w += TX * TY) mask[(size_t)t * d.mw + w] = 0u;
-        if (tid == 0) d.fresh[t] = (int32_t)m;  // the flag is cleared by the next membrane update
+        if (lane == 0) d.fresh[t] = (int32_t)m;  // the flag is cleared by the next membrane update
     }
 }
 
@@ -450,7 +473,7 @@ cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, cudaSt
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(TX, TY);
+    cfg.blockDim = dim3(32 * NEAR_WARPS);
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributePriority;
     attr[0].val.priority = d.chain_priority;
