@@ -284,8 +284,9 @@ lbib_status lbib_set_launch_config(lbib_ctx* ctx, const lbib_launch_config* cfg)
 /* Autotuner (no counterpart in the paper; the launch shapes are this
  * implementation's).  Times candidate configurations on the context's own
  * state: a device snapshot of the state is taken, each candidate advances it
- * by steps_per_trial >= 1 steps (after two warm-up steps) timed with CUDA
- * events, the snapshot is restored, and the fastest candidate is kept.  The
+ * by two warm-up steps and twice steps_per_trial >= 1 steps, timed with CUDA
+ * events (the faster run counts), the snapshot is restored, and the fastest
+ * candidate is kept.  The
  * search is coordinate-wise: bulk tiles per block and nodes per thread, then membrane block size,
  * then activation stride, then near-kernel blocks.  On return the state, the step count and the
  * observables cursors are as on entry; *chosen (may be NULL) receives the
