@@ -253,6 +253,12 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     caps, cfg = _workload(args.workload, args.instances)
+    if args.storage:  # population storage other than the workload's FP32
+        import dataclasses
+        caps = [dataclasses.replace(c, storage=args.storage) for c in caps]
+        cfg["workload"] = cfg["workload"].replace("fp32 populations", f"{args.storage} populations")
+        cfg["storage"] = args.storage
+    store = lbib.STORAGE_CODES[caps[0].storage]
     batch = len(caps) > 1 or args.workload == "sweep"
     nodes = cfg["nodes"]
     stream = torch.cuda.Stream()  # non-null handle: the library enqueues on it, the events bracket it
@@ -267,9 +273,8 @@ def run_gpu(args):
     else:
         tuned = s.autotune(steps_per_trial=args.tune_steps)  # leaves the state unchanged
         tuned_by = f"lbib_autotune, {args.tune_steps} steps per trial"
-    s.set_profiling(True)
     # populations beyond L2 (sweep): no flush; else a 256 MiB buffer rewritten between steps
-    pop_bytes = 2 * 9 * 4 * nodes
+    pop_bytes = lbib.roofline_bytes_per_node(store) * nodes
     flush = None if pop_bytes > (256 << 20) else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(max(args.warmup, 3)):
         if flush is not None:
@@ -280,7 +285,6 @@ def run_gpu(args):
     K = args.steps
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    kern = []
     clocks = Clocks(local)
     if dist:
         dist.barrier()
@@ -288,16 +292,25 @@ def run_gpu(args):
     clocks.start()
     time.sleep(0.25)
     t0 = time.perf_counter()
+    # steps enqueued back to back (no host synchronisation inside the timed region)
     for k in range(K):
         if flush is not None:
             flush.fill_(k & 0xFF)
         starts[k].record(stream)
         s.advance(1)
         ends[k].record(stream)
-        kern.append(s.kernel_times())  # synchronises the stream
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     clk = clocks.stop()
+    # per-kernel device times from a separate profiled pass (events inside the step graph)
+    s.set_profiling(True)
+    kern = []
+    for k in range(args.profile_steps):
+        if flush is not None:
+            flush.fill_(k & 0xFF)
+        s.advance(1)
+        kern.append(s.kernel_times())  # synchronises the stream
+    s.set_profiling(False)
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     dev_s = sum(step_ms) / 1e3
     if dist:
@@ -311,10 +324,10 @@ def run_gpu(args):
     near_ms = statistics.mean(k[2] for k in kern)
     near_nodes = desc["near_tiles"] * 32 * 4
     bulk_nodes = nodes - near_nodes
-    bpn = lbib.roofline_bytes_per_node(lbib.LBIB_STORE_FP32)
+    bpn = lbib.roofline_bytes_per_node(store)
     hbm, src = _peaks()
     achieved = bulk_nodes * bpn / (bulk_ms * 1e-3) / 1e9
-    traffic = _traffic("k_bulk<float,float>", cfg["workload"])
+    traffic = _traffic("k_bulk<float,float>", cfg["workload"]) if caps[0].storage == "fp32" else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "kernel": "k_bulk<float,float> (bulk lattice update)",
                 "algorithmic_bytes_per_launch": bulk_nodes * bpn,
@@ -352,8 +365,9 @@ def run_gpu(args):
     markers = cfg["markers"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
             "ms_per_step": dev_s * 1e3 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": dict(cfg, l2=("populations (780 MB) larger than L2: no flush" if flush is None else
+            "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16 storage, f32 arithmetic",
+                      "fp16": "f16 storage (x 2^14), f32 arithmetic"}[caps[0].storage], "data": "synthetic",
+            "config": dict(cfg, l2=(f"populations ({pop_bytes / 1e6:.0f} MB) larger than L2: no flush" if flush is None else
                                     "256 MiB buffer rewritten between timed steps (cold L2 each step)")),
             "marker_updates_per_s": ws * markers * K / dev_s,
             "kernel_ms": {"bulk_lattice": bulk_ms, "lagrangian": lag_ms, "near_lattice": near_ms},
@@ -385,7 +399,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="lbib", choices=["lbib", "reference"])
     ap.add_argument("--workload", default="sweep", choices=["sweep", "production"])
@@ -393,7 +407,11 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=50, help="steps per capillary of the plain-solver timing")
     ap.add_argument("--cpu-nodes", type=float, default=1.0e8,
                     help="node updates of the CPU oracle sample (about 15 s at 7 MLUPS)")
-    ap.add_argument("--tune-steps", type=int, default=20, help="steps per autotuner trial")
+    ap.add_argument("--tune-steps", type=int, default=50, help="steps per autotuner trial")
+    ap.add_argument("--storage", default="", choices=["", "fp32", "bf16", "fp16", "fp64"],
+                    help="population storage (default: the workload's, FP32)")
+    ap.add_argument("--profile-steps", type=int, default=50,
+                    help="steps of the separate profiled pass that gives the per-kernel times")
     ap.add_argument("--config", default="", help="fixed launch configuration "
                     "lagrangian_threads,near_blocks,bulk_tiles_y,activation_stride[,bulk_nodes_per_thread] "
                     "instead of the autotuner")

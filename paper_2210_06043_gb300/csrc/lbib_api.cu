@@ -18,6 +18,8 @@
 // of the tile width), stepped by the same three launches.  Membranes, bonds and
 // observables are per instance and in the instance's own coordinates; the
 // bodies are stored grouped by instance.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -94,7 +96,8 @@ struct lbib_ctx {
     std::string err;
     lbib_fluid_params P{};
     int prec = PREC_F64;
-    size_t rsz = 8;  // bytes of one stored population / compute value
+    size_t rsz = 8;  // bytes of one compute value
+    size_t ssz = 8;  // bytes of one stored population
     Dev d{};
     std::vector<HostBody> bodies;
     bool finalized = false;
@@ -584,9 +587,8 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     if (!(P->re >= 0.0) || !(P->rho_out > 0.0)) return fail(nullptr, LBIB_ERR_INVALID_ARG, "re >= 0 and rho_out > 0");
     if (P->bc_mode != LBIB_BC_INLET_OUTLET && P->bc_mode != LBIB_BC_PERIODIC_FORCE)
         return fail(nullptr, LBIB_ERR_INVALID_ARG, "unknown bc_mode");
-    if (P->storage == LBIB_STORE_BF16 || P->storage == LBIB_STORE_FP16)
-        return fail(nullptr, LBIB_ERR_UNSUPPORTED, "16-bit population storage is not built");
-    if (P->storage != LBIB_STORE_FP64 && P->storage != LBIB_STORE_FP32)
+    if (P->storage != LBIB_STORE_FP64 && P->storage != LBIB_STORE_FP32 && P->storage != LBIB_STORE_BF16 &&
+        P->storage != LBIB_STORE_FP16)
         return fail(nullptr, LBIB_ERR_INVALID_ARG, "unknown storage");
     if (P->obs_capacity < 0) return fail(nullptr, LBIB_ERR_INVALID_ARG, "obs_capacity < 0");
     // instances side by side, each starting on a tile column
@@ -606,6 +608,11 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     DeviceGuard guard(ctx->device);
     ctx->prec = (P->storage == LBIB_STORE_FP64) ? PREC_F64 : PREC_F32;
     ctx->rsz = (ctx->prec == PREC_F64) ? 8 : 4;
+    ctx->ssz = (P->storage == LBIB_STORE_FP64) ? 8 : (P->storage == LBIB_STORE_FP32 ? 4 : 2);
+    ctx->d.store = (P->storage == LBIB_STORE_FP64)   ? STORE_F64
+                   : (P->storage == LBIB_STORE_FP32) ? STORE_F32
+                   : (P->storage == LBIB_STORE_BF16) ? STORE_BF16
+                                                     : STORE_F16;
     ctx->ninst = ninst;
     std::vector<int4> cols;
     for (int i = 0, x0 = 0; i < ninst; ++i) {
@@ -659,8 +666,8 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     } while (0)
     auto& reg = ctx->allocs;
     size_t nq = (size_t)9 * qs, nn = (size_t)qs;
-    CKC(dalloc(reg, reinterpret_cast<char**>(&d.f[0]), nq * ctx->rsz));
-    CKC(dalloc(reg, reinterpret_cast<char**>(&d.f[1]), nq * ctx->rsz));
+    CKC(dalloc(reg, reinterpret_cast<char**>(&d.f[0]), nq * ctx->ssz));
+    CKC(dalloc(reg, reinterpret_cast<char**>(&d.f[1]), nq * ctx->ssz));
     CKC(dalloc(reg, reinterpret_cast<char**>(&d.drho), nn * ctx->rsz));
     CKC(dalloc(reg, reinterpret_cast<char**>(&d.ux), nn * ctx->rsz));
     CKC(dalloc(reg, reinterpret_cast<char**>(&d.uy), nn * ctx->rsz));
@@ -679,8 +686,8 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     d.colinfo = ctx->colinfo;
     d.inst = ctx->inst;
     CKC(cudaMemcpy(ctx->colinfo, cols.data(), cols.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    CKC(cudaMemset(d.f[0], 0, nq * ctx->rsz));
-    CKC(cudaMemset(d.f[1], 0, nq * ctx->rsz));
+    CKC(cudaMemset(d.f[0], 0, nq * ctx->ssz));
+    CKC(cudaMemset(d.f[1], 0, nq * ctx->ssz));
     CKC(cudaMemset(d.drho, 0, nn * ctx->rsz));
     CKC(cudaMemset(d.ux, 0, nn * ctx->rsz));
     CKC(cudaMemset(d.uy, 0, nn * ctx->rsz));
@@ -893,6 +900,28 @@ lbib_status lbib_read_velocity_device(lbib_ctx* ctx, void* dux, void* duy, size_
 
 static double wrest(int q) { return q == 0 ? 4.0 / 9.0 : (q < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
 
+// stored deviation element k of a host copy <-> double (the storage rules of
+// the device's ld / st: FP16 carries the HALF_SCALE factor)
+static double stored_to_double(const lbib_ctx* ctx, const char* raw, size_t k)
+{
+    switch (ctx->d.store) {
+    case STORE_F64: return reinterpret_cast<const double*>(raw)[k];
+    case STORE_F32: return (double)reinterpret_cast<const float*>(raw)[k];
+    case STORE_BF16: return (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(raw)[k]);
+    default: return (double)(__half2float(reinterpret_cast<const __half*>(raw)[k]) * (1.0f / HALF_SCALE));
+    }
+}
+
+static void double_to_stored(const lbib_ctx* ctx, char* raw, size_t k, double v)
+{
+    switch (ctx->d.store) {
+    case STORE_F64: reinterpret_cast<double*>(raw)[k] = v; break;
+    case STORE_F32: reinterpret_cast<float*>(raw)[k] = (float)v; break;
+    case STORE_BF16: reinterpret_cast<__nv_bfloat16*>(raw)[k] = __float2bfloat16_rn((float)v); break;
+    default: reinterpret_cast<__half*>(raw)[k] = __float2half_rn((float)v * HALF_SCALE); break;
+    }
+}
+
 lbib_status lbib_read_instance_populations(lbib_ctx* ctx, int32_t instance, double* f, size_t n)
 {
     if (!ctx || !f) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
@@ -905,18 +934,16 @@ lbib_status lbib_read_instance_populations(lbib_ctx* ctx, int32_t instance, doub
     lbib_status s = pre_read(ctx);
     if (s != LBIB_OK) return s;
     // one strided copy per direction: rows of the instance's columns
-    std::vector<char> raw((size_t)9 * nn * ctx->rsz);
+    const size_t es = ctx->ssz;
+    std::vector<char> raw((size_t)9 * nn * es);
     const char* src = static_cast<const char*>(ctx->d.f[ctx->s_f & 1]);
     for (int q = 0; q < 9; ++q)
-        CK(cudaMemcpy2D(raw.data() + (size_t)q * nn * ctx->rsz, (size_t)inx * ctx->rsz,
-                        src + ((size_t)q * L.qstride + x0) * ctx->rsz, (size_t)L.nxp * ctx->rsz,
-                        (size_t)inx * ctx->rsz, L.ny, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy2D(raw.data() + (size_t)q * nn * es, (size_t)inx * es, src + ((size_t)q * L.qstride + x0) * es,
+                        (size_t)L.nxp * es, (size_t)inx * es, L.ny, cudaMemcpyDeviceToHost));
     for (int q = 0; q < 9; ++q)
         for (size_t i = 0; i < nn; ++i) {
             const size_t k = (size_t)q * nn + i;
-            double v = ctx->prec == PREC_F64 ? reinterpret_cast<double*>(raw.data())[k]
-                                             : (double)reinterpret_cast<float*>(raw.data())[k];
-            f[k] = v + wrest(q);
+            f[k] = stored_to_double(ctx, raw.data(), k) + wrest(q);
         }
     return LBIB_OK;
 }
@@ -936,20 +963,18 @@ lbib_status lbib_write_instance_populations(lbib_ctx* ctx, int32_t instance, con
     if (n < 9 * nn) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than 9 nx ny");
     if (ctx->s_f != 0) return fail(ctx, LBIB_ERR_STATE, "populations can only be written before the first step");
     DeviceGuard guard(ctx->device);
-    std::vector<char> raw((size_t)9 * nn * ctx->rsz);
+    const size_t es = ctx->ssz;
+    std::vector<char> raw((size_t)9 * nn * es);
     for (int q = 0; q < 9; ++q)
         for (size_t i = 0; i < nn; ++i) {
             const size_t k = (size_t)q * nn + i;
-            double v = f[k] - wrest(q);
-            if (ctx->prec == PREC_F64) reinterpret_cast<double*>(raw.data())[k] = v;
-            else reinterpret_cast<float*>(raw.data())[k] = (float)v;
+            double_to_stored(ctx, raw.data(), k, f[k] - wrest(q));
         }
     CK(cudaStreamSynchronize(ctx->stream));
     char* dst = static_cast<char*>(ctx->d.f[0]);
     for (int q = 0; q < 9; ++q)
-        CK(cudaMemcpy2D(dst + ((size_t)q * L.qstride + x0) * ctx->rsz, (size_t)L.nxp * ctx->rsz,
-                        raw.data() + (size_t)q * nn * ctx->rsz, (size_t)inx * ctx->rsz, (size_t)inx * ctx->rsz,
-                        L.ny, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy2D(dst + ((size_t)q * L.qstride + x0) * es, (size_t)L.nxp * es, raw.data() + (size_t)q * nn * es,
+                        (size_t)inx * es, (size_t)inx * es, L.ny, cudaMemcpyHostToDevice));
     return LBIB_OK;
 }
 
@@ -1112,7 +1137,7 @@ size_t state_bytes(const lbib_ctx* ctx)
     size_t nq = (size_t)9 * d.L.qstride;
     size_t nm = std::max(d.nmark, 1), nl = std::max(d.nlig, 1), nb = std::max(d.nbodies, 1);
     size_t nn = (size_t)d.L.qstride;
-    return sizeof(CkHeader) + nq * ctx->rsz + 2 * nn * ctx->rsz + (size_t)d.L.ntiles * 4 + 4 * nm * 8 +
+    return sizeof(CkHeader) + nq * ctx->ssz + 2 * nn * ctx->rsz + (size_t)d.L.ntiles * 4 + 4 * nm * 8 +
            4 * nm * ctx->rsz + nb * RG_N * 8 + nl * 4 + 2 * nl * 8 + 2 * nm * 4 + 4 * nm * ctx->rsz + nb * BO_N * 8 +
            (size_t)NDIAG * nm * ctx->rsz + nl * ctx->rsz;
 }
@@ -1151,7 +1176,7 @@ lbib_status save_into(lbib_ctx* ctx, char* p, cudaMemcpyKind kind)
         return e;
     };
     const size_t nn = (size_t)d.L.qstride;
-    CK(put(d.f[st & 1], nq * ctx->rsz));
+    CK(put(d.f[st & 1], nq * ctx->ssz));
     CK(put(d.fx, nn * ctx->rsz));
     CK(put(d.fy, nn * ctx->rsz));
     CK(put(d.fresh, (size_t)d.L.ntiles * 4));
@@ -1189,7 +1214,7 @@ lbib_status load_from(lbib_ctx* ctx, const char* p, cudaMemcpyKind kind)
         return e;
     };
     const size_t nn = (size_t)d.L.qstride;
-    CK(get(d.f[st & 1], nq * ctx->rsz));
+    CK(get(d.f[st & 1], nq * ctx->ssz));
     CK(get(d.fx, nn * ctx->rsz));
     CK(get(d.fy, nn * ctx->rsz));
     CK(get(d.fresh, (size_t)d.L.ntiles * 4));

@@ -1,6 +1,8 @@
 // lbib_device.cuh -- device helpers shared by the library's kernels.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -26,6 +28,28 @@ template <typename S, typename R>
 __device__ __forceinline__ void st(S* p, R v)
 {
     *p = static_cast<S>(v);
+}
+// 16-bit storage of FP32 deviations: bfloat16 as is (round to nearest even);
+// binary16 scaled by HALF_SCALE (exact power of two) on the way in and out
+template <>
+__device__ __forceinline__ float ld<__nv_bfloat16, float>(const __nv_bfloat16* p)
+{
+    return __bfloat162float(__ldg(p));
+}
+template <>
+__device__ __forceinline__ void st<__nv_bfloat16, float>(__nv_bfloat16* p, float v)
+{
+    *p = __float2bfloat16_rn(v);
+}
+template <>
+__device__ __forceinline__ float ld<__half, float>(const __half* p)
+{
+    return __half2float(__ldg(p)) * (1.0f / HALF_SCALE);
+}
+template <>
+__device__ __forceinline__ void st<__half, float>(__half* p, float v)
+{
+    *p = __float2half_rn(v * HALF_SCALE);
 }
 
 // ------------------------------------------------------- Peskin 4-point kernel

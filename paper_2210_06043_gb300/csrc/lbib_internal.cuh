@@ -49,7 +49,14 @@ enum : uint32_t {
     ST_LIST_OVERFLOW = 8u,  // near-tile list capacity exceeded
 };
 
-enum { PREC_F64 = 0, PREC_F32 = 1 };
+enum { PREC_F64 = 0, PREC_F32 = 1 };  // compute type of the kernels
+
+// Population storage type (values of lbib_storage): FP64 and FP32 store the
+// deviations f_i - w_i as is; BF16 stores them rounded to bfloat16; FP16
+// stores them times HALF_SCALE (an exact power of two that keeps deviations of
+// 1e-9 .. 3 in the normal range of binary16).  The 16-bit kinds compute in FP32.
+enum { STORE_F64 = 0, STORE_F32 = 1, STORE_BF16 = 2, STORE_F16 = 3 };
+constexpr float HALF_SCALE = 16384.0f;
 
 // A context holds one or more capillary instances (a sweep) side by side
 // along x in one lattice: instance i occupies the node columns
@@ -123,6 +130,7 @@ enum { BO_AREA = 0, BO_DPERIM, BO_CX, BO_CY, BO_NBOUND, BO_XMIN, BO_XMAX, BO_YMI
 // Every device pointer of a context.  Passed by value to the kernels.
 struct Dev {
     Lattice L;
+    int store;                 // STORE_*: element type of f
     // lattice state
     void* f[2];                // Store
     void* drho;                // Real [ny][nxp]: rho - 1 on near tiles

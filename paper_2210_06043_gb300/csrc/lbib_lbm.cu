@@ -18,6 +18,8 @@
 // and width).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "lbib_device.cuh"
 
 namespace lbib {
@@ -363,7 +365,7 @@ __global__ void k_macro(Dev d, int buf, int64_t m, int x0, int inx, O* rho_o, O*
     const S* f = static_cast<const S*>(d.f[buf]);
     R g[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) g[q] = static_cast<R>(f[q * L.qstride + base]);
+    for (int q = 0; q < 9; ++q) g[q] = ld<S, R>(f + q * L.qstride + base);
     const R drho = g[0] + g[1] + g[2] + g[3] + g[4] + g[5] + g[6] + g[7] + g[8];
     const R jx = (g[1] + g[5] + g[8]) - (g[3] + g[6] + g[7]) - R(0.5) * Fx;
     const R jy = (g[2] + g[5] + g[6]) - (g[4] + g[7] + g[8]) - R(0.5) * Fy;
@@ -439,37 +441,54 @@ __global__ void k_rebuild_mask(Dev d, int parity, int slot)
 
 // ------------------------------------------------------------------ launchers
 
+// Calls fn(S*, R*) with null pointers of the storage and compute types of the
+// context's populations (the lattice kernels are templates on both).
+template <typename F>
+static void by_store(int store, F&& fn)
+{
+    switch (store) {
+    case STORE_F64: fn((double*)nullptr, (double*)nullptr); break;
+    case STORE_BF16: fn((__nv_bfloat16*)nullptr, (float*)nullptr); break;
+    case STORE_F16: fn((__half*)nullptr, (float*)nullptr); break;
+    default: fn((float*)nullptr, (float*)nullptr); break;
+    }
+}
+
+#define LBIB_TYPES(sp, rp)                                  \
+    using S = typename std::remove_pointer<decltype(sp)>::type; \
+    using R = typename std::remove_pointer<decltype(rp)>::type
+
 template <int RT, int NPT>
-static void launch_bulk_rt(const Dev& d, int prec, int parity, int slot, cudaStream_t s)
+static void launch_bulk_rt(const Dev& d, int parity, int slot, cudaStream_t s)
 {
     dim3 grid(d.L.ntx, (d.L.nty + RT - 1) / RT), block(TX, TY * RT / NPT);
     const bool forced = d.L.gx != 0.0 || d.L.gy != 0.0;  // uniform body force (PERIODIC_FORCE mode)
-    if (prec == PREC_F64) {
-        if (forced) k_bulk<double, double, RT, NPT, true><<<grid, block, 0, s>>>(d, parity, slot);
-        else k_bulk<double, double, RT, NPT, false><<<grid, block, 0, s>>>(d, parity, slot);
-    } else {
-        if (forced) k_bulk<float, float, RT, NPT, true><<<grid, block, 0, s>>>(d, parity, slot);
-        else k_bulk<float, float, RT, NPT, false><<<grid, block, 0, s>>>(d, parity, slot);
-    }
+    by_store(d.store, [&](auto sp, auto rp) {
+        LBIB_TYPES(sp, rp);
+        if (forced) k_bulk<S, R, RT, NPT, true><<<grid, block, 0, s>>>(d, parity, slot);
+        else k_bulk<S, R, RT, NPT, false><<<grid, block, 0, s>>>(d, parity, slot);
+    });
 }
 
 cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, int slot, cudaStream_t s)
 {
+    (void)prec;  // the storage type fixes the compute type
     const int v = 10 * (d.bulk_tiles_y == 2 || d.bulk_tiles_y == 4 ? d.bulk_tiles_y : 1) +
                   (d.bulk_nodes_per_thread == 2 ? 2 : 1);
     switch (v) {
-    case 12: launch_bulk_rt<1, 2>(d, prec, parity, slot, s); break;
-    case 21: launch_bulk_rt<2, 1>(d, prec, parity, slot, s); break;
-    case 22: launch_bulk_rt<2, 2>(d, prec, parity, slot, s); break;
-    case 41: launch_bulk_rt<4, 1>(d, prec, parity, slot, s); break;
-    case 42: launch_bulk_rt<4, 2>(d, prec, parity, slot, s); break;
-    default: launch_bulk_rt<1, 1>(d, prec, parity, slot, s); break;
+    case 12: launch_bulk_rt<1, 2>(d, parity, slot, s); break;
+    case 21: launch_bulk_rt<2, 1>(d, parity, slot, s); break;
+    case 22: launch_bulk_rt<2, 2>(d, parity, slot, s); break;
+    case 41: launch_bulk_rt<4, 1>(d, parity, slot, s); break;
+    case 42: launch_bulk_rt<4, 2>(d, parity, slot, s); break;
+    default: launch_bulk_rt<1, 1>(d, parity, slot, s); break;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, cudaStream_t s)
 {
+    (void)prec;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3(grid);
@@ -479,50 +498,53 @@ cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, cudaSt
     attr[0].val.priority = d.chain_priority;
     cfg.attrs = attr;
     cfg.numAttrs = d.chain_priority ? 1 : 0;
-    if (prec == PREC_F64) return cudaLaunchKernelEx(&cfg, k_near<double, double>, d, parity);
-    return cudaLaunchKernelEx(&cfg, k_near<float, float>, d, parity);
+    cudaError_t e = cudaSuccess;
+    by_store(d.store, [&](auto sp, auto rp) {
+        LBIB_TYPES(sp, rp);
+        e = cudaLaunchKernelEx(&cfg, k_near<S, R>, d, parity);
+    });
+    return e;
 }
 
 cudaError_t launch_init_populations(const Dev& d, int prec, int buf, cudaStream_t s)
 {
+    (void)prec;
     dim3 grid(d.L.ntx, d.L.nty), block(TX, TY);
-    if (prec == PREC_F64) k_init_populations<double, double><<<grid, block, 0, s>>>(d, buf);
-    else k_init_populations<float, float><<<grid, block, 0, s>>>(d, buf);
+    by_store(d.store, [&](auto sp, auto rp) {
+        LBIB_TYPES(sp, rp);
+        k_init_populations<S, R><<<grid, block, 0, s>>>(d, buf);
+    });
     return cudaGetLastError();
 }
 
 cudaError_t launch_macro(const Dev& d, int prec, int buf, int64_t m, int x0, int inx, double* rho, double* ux,
                          double* uy, cudaStream_t s)
 {
+    (void)prec;
     dim3 grid((inx + TX - 1) / TX, d.L.nty), block(TX, TY);
-    if (prec == PREC_F64)
-        k_macro<double, double, double><<<grid, block, 0, s>>>(d, buf, m, x0, inx, rho, ux, uy, 1);
-    else
-        k_macro<float, float, double><<<grid, block, 0, s>>>(d, buf, m, x0, inx, rho, ux, uy, 1);
+    by_store(d.store, [&](auto sp, auto rp) {
+        LBIB_TYPES(sp, rp);
+        k_macro<S, R, double><<<grid, block, 0, s>>>(d, buf, m, x0, inx, rho, ux, uy, 1);
+    });
     return cudaGetLastError();
 }
 
 cudaError_t launch_macro_typed(const Dev& d, int prec, int buf, int64_t m, int x0, int inx, void* ux, void* uy,
                                int dtype, cudaStream_t s)
 {
+    (void)prec;
     dim3 grid((inx + TX - 1) / TX, d.L.nty), block(TX, TY);
-    if (dtype == 1) {
-        if (prec == PREC_F64)
-            k_macro<double, double, double><<<grid, block, 0, s>>>(d, buf, m, x0, inx, nullptr, (double*)ux,
-                                                                   (double*)uy, 1);
+    by_store(d.store, [&](auto sp, auto rp) {
+        LBIB_TYPES(sp, rp);
+        if (dtype == 1)
+            k_macro<S, R, double><<<grid, block, 0, s>>>(d, buf, m, x0, inx, nullptr, (double*)ux, (double*)uy, 1);
         else
-            k_macro<float, float, double><<<grid, block, 0, s>>>(d, buf, m, x0, inx, nullptr, (double*)ux,
-                                                                 (double*)uy, 1);
-    } else {
-        if (prec == PREC_F64)
-            k_macro<double, double, float><<<grid, block, 0, s>>>(d, buf, m, x0, inx, nullptr, (float*)ux,
-                                                                  (float*)uy, 1);
-        else
-            k_macro<float, float, float><<<grid, block, 0, s>>>(d, buf, m, x0, inx, nullptr, (float*)ux,
-                                                                (float*)uy, 1);
-    }
+            k_macro<S, R, float><<<grid, block, 0, s>>>(d, buf, m, x0, inx, nullptr, (float*)ux, (float*)uy, 1);
+    });
     return cudaGetLastError();
 }
+
+#undef LBIB_TYPES
 
 cudaError_t launch_activate(const Dev& d, int prec, int64_t m, int which, cudaStream_t s)
 {

@@ -144,6 +144,7 @@ extern "C" lbib_status lbib_lattice_advance_noalloc(const lbib_fluid_params* P, 
     if (e == cudaSuccess) {
         Dev d{};
         d.L = L;
+        d.store = (prec == PREC_F64) ? STORE_F64 : STORE_F32;
         d.status = reinterpret_cast<uint32_t*>(base);
         d.nearflag[0] = d.nearflag[1] = d.nearflag[2] = reinterpret_cast<uint32_t*>(base + 256);
         int4* cols = reinterpret_cast<int4*>(base + 256 + need_flags);

@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "CUDA", 4: "OOM"
                 6: "TIMEOUT", 7: "STATE"}
 LBIB_BC_INLET_OUTLET, LBIB_BC_PERIODIC_FORCE = 0, 1
 LBIB_STORE_FP64, LBIB_STORE_FP32, LBIB_STORE_BF16, LBIB_STORE_FP16 = 0, 1, 2, 3
+STORAGE_CODES = {"fp64": LBIB_STORE_FP64, "fp32": LBIB_STORE_FP32, "bf16": LBIB_STORE_BF16, "fp16": LBIB_STORE_FP16}
 LBIB_CELL, LBIB_PARTICLE = 0, 1
 LBIB_DEFORMABLE, LBIB_RIGID, LBIB_FIXED = 0, 1, 2
 FIELDS = ("x", "y", "xp", "yp", "uvx", "uvy", "fsx", "fsy", "fbx", "fby", "fax", "fay",
@@ -377,7 +378,7 @@ def from_capillary(cap, storage=None, device=0, stream=None, obs_capacity=0) -> 
     """A Solver holding the lattice and bodies of a workloads.Capillary."""
     st = storage
     if st is None:
-        st = LBIB_STORE_FP64 if cap.storage == "fp64" else LBIB_STORE_FP32
+        st = STORAGE_CODES[cap.storage]
     s = Solver(cap.nx, cap.ny, tau=cap.tau, re=cap.re, rho_out=cap.rho_out, bc=cap.bc, g=cap.g, storage=st,
                device=device, seed=cap.seed, stream=stream, obs_capacity=obs_capacity)
     _add_bodies(s, cap, 0)
@@ -404,7 +405,7 @@ def from_capillaries(caps, storage=None, device=0, stream=None, obs_capacity=0) 
             raise ValueError("instances of a batch share ny and the fluid parameters")
     st = storage
     if st is None:
-        st = LBIB_STORE_FP64 if c0.storage == "fp64" else LBIB_STORE_FP32
+        st = STORAGE_CODES[c0.storage]
     s = Solver([c.nx for c in caps], c0.ny, tau=c0.tau, re=c0.re, rho_out=c0.rho_out, bc=c0.bc, g=c0.g,
                storage=st, device=device, stream=stream, obs_capacity=obs_capacity, seeds=[c.seed for c in caps])
     for k, c in enumerate(caps):

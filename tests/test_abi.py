@@ -90,8 +90,8 @@ def test_create_reports_errors_through_the_boundary():
     assert b"nx" in lib.lbib_last_error(None)
     p = lbib.lbib_fluid_params(nx=16, ny=8, tau=0.5, re=0.01, rho_out=1.0)
     assert lib.lbib_create(ctypes.byref(p), ctypes.byref(h)) == lbib.LBIB_ERR_INVALID_ARG
-    p = lbib.lbib_fluid_params(nx=16, ny=8, tau=1.0, re=0.01, rho_out=1.0, storage=lbib.LBIB_STORE_BF16)
-    assert lib.lbib_create(ctypes.byref(p), ctypes.byref(h)) == lbib.LBIB_ERR_UNSUPPORTED
+    p = lbib.lbib_fluid_params(nx=16, ny=8, tau=1.0, re=0.01, rho_out=1.0, storage=7)
+    assert lib.lbib_create(ctypes.byref(p), ctypes.byref(h)) == lbib.LBIB_ERR_INVALID_ARG
     p = lbib.lbib_fluid_params(nx=16, ny=8, tau=1.0, re=0.01, rho_out=1.0, device=0)
     st = lib.lbib_create(ctypes.byref(p), ctypes.byref(h))
     if st == lbib.LBIB_OK:  # a GPU is present
