@@ -1,0 +1,86 @@
+/* lbib_mlp.h -- C ABI of the learned surrogate: a multilayer perceptron
+ * trained and evaluated on the GPU by the library's own kernels.
+ *
+ * The paper reports trajectories of the adhesion observables N_L, delta p and
+ * r for a parameter sweep (particle aspect ratio, Ca, cell shape, ligand
+ * density; Sec. 3.1, Figs. 5-9).  The surrogate maps such parameters and the
+ * time t u_max / H to those observables; it has no counterpart in the paper.
+ *
+ * Network: n_hidden hidden layers of `width` units with GELU,
+ *   a_0 = bf16(s_in * (x - c_in)),
+ *   z_l = W_l a_{l-1} + b_l,  a_l = bf16(GELU(z_l))   (l = 1 .. n_hidden),
+ *   y   = s_out * (W_out a_{n_hidden} + b_out) + c_out,
+ * weights used in BF16 (FP32 master copies), products accumulated in FP32.
+ * GELU(z) = z Phi(z), Phi the standard normal distribution function.
+ * Training minimises the mean over the batch and the outputs of
+ * ((y - t) / s_out)^2 (targets standardised by the same affine map) with Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).
+ *
+ * All calls return lbib_status (include/lbib.h); messages through
+ * lbib_last_error(NULL).  A context is used by one thread at a time.
+ */
+#ifndef LBIB_MLP_H
+#define LBIB_MLP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "lbib.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbib_mlp lbib_mlp;
+
+typedef struct lbib_mlp_desc {
+    int32_t n_in;        /* input features, 1 .. 32 */
+    int32_t width;       /* hidden units, a multiple of 64, <= 1024 */
+    int32_t n_hidden;    /* hidden layers, 1 .. 8 */
+    int32_t n_out;       /* outputs, 1 .. 64 */
+    int32_t max_batch;   /* largest batch a call may pass, >= 1 */
+    int32_t device;      /* CUDA device ordinal */
+    void* cuda_stream;   /* cudaStream_t to enqueue on (borrowed), or NULL for a private one */
+    uint64_t seed;       /* weight initialisation (uniform +-sqrt(6 / (fan_in + fan_out)), biases 0) */
+    const float* in_shift;   /* host, n_in values c_in (copied); NULL: zeros */
+    const float* in_scale;   /* host, n_in values s_in (copied); NULL: ones */
+    const float* out_shift;  /* host, n_out values c_out (copied); NULL: zeros */
+    const float* out_scale;  /* host, n_out values s_out (copied); NULL: ones */
+} lbib_mlp_desc;
+
+/* Creates a network on desc->device; *out receives the handle. */
+lbib_status lbib_mlp_create(const lbib_mlp_desc* desc, lbib_mlp** out);
+
+/* Inference: x DEVICE [batch][n_in] floats, y DEVICE [batch][n_out] floats,
+ * 1 <= batch <= max_batch; enqueued on the context stream (no wait). */
+lbib_status lbib_mlp_forward(lbib_mlp* net, const float* x, int32_t batch, float* y);
+
+/* One Adam step on the batch: x DEVICE [batch][n_in], t DEVICE [batch][n_out]
+ * targets; lr the step size; loss DEVICE float (may be NULL) receives the
+ * batch loss before the update.  Enqueued on the context stream. */
+lbib_status lbib_mlp_train_step(lbib_mlp* net, const float* x, const float* t, int32_t batch, float lr,
+                                float* loss);
+
+/* Gradient of the batch loss with respect to every parameter, without an
+ * update, copied to the HOST array grad of n >= lbib_mlp_param_count values
+ * (layout as lbib_mlp_get_params); *loss (host, may be NULL) the loss.  Waits. */
+lbib_status lbib_mlp_gradients(lbib_mlp* net, const float* x, const float* t, int32_t batch, float* grad, size_t n,
+                               float* loss);
+
+/* Number of parameters: for each layer (hidden ones first, then the output
+ * layer) its weights W [out][in] row-major, then its biases b [out]. */
+lbib_status lbib_mlp_param_count(lbib_mlp* net, size_t* n);
+
+/* FP32 master parameters to / from a HOST array of n >= param_count values
+ * (set also resets the Adam moments and step count).  Wait for the stream. */
+lbib_status lbib_mlp_get_params(lbib_mlp* net, float* params, size_t n);
+lbib_status lbib_mlp_set_params(lbib_mlp* net, const float* params, size_t n);
+
+/* Releases every resource of net (NULL is ignored). */
+void lbib_mlp_destroy(lbib_mlp* net);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBIB_MLP_H */

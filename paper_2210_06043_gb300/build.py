@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbib.so")
-SOURCES = ("lbib_api.cu", "lbib_lbm.cu", "lbib_lag.cu", "lbib_noalloc.cu")
+SOURCES = ("lbib_api.cu", "lbib_lbm.cu", "lbib_lag.cu", "lbib_noalloc.cu", "lbib_mlp.cu")
 HEADERS = ("lbib_internal.cuh", "lbib_device.cuh")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -33,6 +33,7 @@ def _stale() -> bool:
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
     deps.append(os.path.join(HERE, "..", "include", "lbib.h"))
+    deps.append(os.path.join(HERE, "..", "include", "lbib_mlp.h"))
     deps.append(os.path.abspath(__file__))
     return any(os.path.getmtime(p) > t for p in deps)
 

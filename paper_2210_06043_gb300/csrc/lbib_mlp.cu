@@ -1,0 +1,787 @@
+// lbib_mlp.cu -- the learned surrogate (include/lbib_mlp.h): a multilayer
+// perceptron with BF16 weights and activations, FP32 accumulation, trained
+// with Adam, every step on the GPU in the kernels below.
+//
+// The dense products run on the tensor cores: one GEMM kernel computes
+// C[M][N] = A[M][K] B[N][K]^T with A and B read either K-major or M/N-major
+// from global memory (cp.async into padded shared tiles, ldmatrix / ldmatrix
+// .trans into mma.sync m16n8k16 BF16 fragments, FP32 accumulators), with the
+// layer's epilogue fused: bias + GELU (forward), bias (output layer), GELU'
+// (backward), or an FP32 partial of a deterministic split-K (weight
+// gradients).  Reductions (bias gradients, split-K sums, the loss) run in a
+// fixed order, so a step is reproducible bit for bit.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbib_internal.cuh"
+#include "../../include/lbib_mlp.h"
+
+using namespace lbib;
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 32;  // block tile; 4 warps, each 32 x 32
+constexpr int GEMM_THREADS = 128;
+constexpr int PAD = 8;  // bf16 elements of row padding (ldmatrix rows stay 16-byte aligned, banks spread)
+constexpr int MAX_SPLITS = 64;
+
+enum Epi { EPI_FWD_GELU = 0, EPI_FWD_LIN = 1, EPI_BWD_GELU = 2, EPI_PARTIAL = 3 };
+
+struct GemmArgs {
+    const __nv_bfloat16* A;  // K-major: [M][lda]; M-major (TA): [K][lda]
+    const __nv_bfloat16* B;  // K-major: [N][ldb]; N-major (TB): [K][ldb]
+    int lda, ldb;
+    int M, N, K;              // M rows valid (ragged), N multiple of BN, K valid (ragged allowed on trans operands)
+    int k_tiles_per_split;
+    const float* bias;        // [N] (forward epilogues)
+    const float* Zin;         // [M][ldc] pre-activations (backward epilogue)
+    float* Zout;              // [M][ldc] pre-activations (forward GELU) or output (forward linear)
+    __nv_bfloat16* Aout;      // [M][ldc] bf16 activations (forward GELU) or gradients (backward)
+    float* part;              // [splits][M][ldc] (split-K partials)
+    int ldc;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid)
+{
+    const int n = valid ? 16 : 0;  // 0 source bytes: the 16 destination bytes are zero-filled
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t r[4], const void* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t r[4], const void* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d(float z)
+{
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+// Shared tiles: A as [BM][BK+PAD] (K-major) or [BK][BM+PAD] (M-major), B likewise.
+template <bool TA, bool TB>
+struct Tiles {
+    __nv_bfloat16 a[2][TA ? BK : BM][(TA ? BM : BK) + PAD];
+    __nv_bfloat16 b[2][TB ? BK : BN][(TB ? BN : BK) + PAD];
+};
+
+template <bool TA, bool TB>
+__device__ __forceinline__ void load_tiles(Tiles<TA, TB>& s, int buf, const GemmArgs& g, int m0, int n0, int k0)
+{
+    const int tid = threadIdx.x;
+    // 256 chunks of 8 bf16 per operand tile, two per thread
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int ch = tid + c * GEMM_THREADS;
+        if (!TA) {  // rows m, 4 chunks of k
+            const int r = ch >> 2, kc = (ch & 3) * 8;
+            const int m = m0 + r;
+            const bool v = m < g.M;
+            cp_async16(&s.a[buf][r][kc], g.A + (size_t)(v ? m : 0) * g.lda + k0 + kc, v);
+        } else {    // rows k, 8 chunks of m
+            const int r = ch >> 3, mc = (ch & 7) * 8;
+            const int k = k0 + r;
+            const bool v = k < g.K;
+            cp_async16(&s.a[buf][r][mc], g.A + (size_t)(v ? k : 0) * g.lda + m0 + mc, v);
+        }
+        if (!TB) {
+            const int r = ch >> 2, kc = (ch & 3) * 8;
+            cp_async16(&s.b[buf][r][kc], g.B + (size_t)(n0 + r) * g.ldb + k0 + kc, true);
+        } else {
+            const int r = ch >> 3, nc = (ch & 7) * 8;
+            const int k = k0 + r;
+            const bool v = k < g.K;
+            cp_async16(&s.b[buf][r][nc], g.B + (size_t)(v ? k : 0) * g.ldb + n0 + nc, v);
+        }
+    }
+}
+
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(GEMM_THREADS) k_gemm(GemmArgs g)
+{
+    __shared__ __align__(16) Tiles<TA, TB> s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int kt_total = (g.K + BK - 1) / BK;
+    const int kt0 = blockIdx.z * g.k_tiles_per_split;
+    const int kt1 = min(kt_total, kt0 + g.k_tiles_per_split);
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+    if (kt0 < kt1) {
+        load_tiles<TA, TB>(s, 0, g, m0, n0, kt0 * BK);
+        cp_async_commit();
+    }
+    for (int kt = kt0; kt < kt1; ++kt) {
+        const int buf = (kt - kt0) & 1;
+        cp_async_wait_all();
+        __syncthreads();
+        if (kt + 1 < kt1) {  // prefetch the next tile into the other buffer
+            load_tiles<TA, TB>(s, buf ^ 1, g, m0, n0, (kt + 1) * BK);
+            cp_async_commit();
+        }
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t af[2][4], bf[2][4];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int mb = wm + i * 16;
+                if (!TA) ldsm_x4(af[i], &s.a[buf][mb + (lane & 7) + 8 * ((lane >> 3) & 1)][kk + 8 * (lane >> 4)]);
+                else ldsm_x4_t(af[i], &s.a[buf][kk + (lane & 7) + 8 * (lane >> 4)][mb + 8 * ((lane >> 3) & 1)]);
+            }
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const int nb = wn + p * 16;
+                if (!TB) ldsm_x4(bf[p], &s.b[buf][nb + (lane & 7) + 8 * (lane >> 4)][kk + 8 * ((lane >> 3) & 1)]);
+                else ldsm_x4_t(bf[p], &s.b[buf][kk + (lane & 7) + 8 * ((lane >> 3) & 1)][nb + 8 * (lane >> 4)]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bf[j >> 1][2 * (j & 1)], bf[j >> 1][2 * (j & 1) + 1]);
+        }
+        __syncthreads();
+    }
+    // epilogue: c0, c1 at (row g, cols 2t, 2t + 1), c2, c3 at row g + 8
+    const int gr = lane >> 2, tc = (lane & 3) * 2;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int m = m0 + wm + i * 16 + gr + 8 * h;
+                const int n = n0 + wn + j * 8 + tc;
+                if (m >= g.M) continue;
+                const float v0 = acc[i][j][2 * h], v1 = acc[i][j][2 * h + 1];
+                const size_t o = (size_t)m * g.ldc + n;
+                if (EPI == EPI_FWD_GELU) {
+                    const float z0 = v0 + g.bias[n], z1 = v1 + g.bias[n + 1];
+                    g.Zout[o] = z0;
+                    g.Zout[o + 1] = z1;
+                    g.Aout[o] = __float2bfloat16_rn(gelu(z0));
+                    g.Aout[o + 1] = __float2bfloat16_rn(gelu(z1));
+                } else if (EPI == EPI_FWD_LIN) {
+                    g.Zout[o] = v0 + g.bias[n];
+                    g.Zout[o + 1] = v1 + g.bias[n + 1];
+                } else if (EPI == EPI_BWD_GELU) {
+                    g.Aout[o] = __float2bfloat16_rn(v0 * gelu_d(g.Zin[o]));
+                    g.Aout[o + 1] = __float2bfloat16_rn(v1 * gelu_d(g.Zin[o + 1]));
+                } else {
+                    float* pp = g.part + (size_t)blockIdx.z * g.M * g.ldc;
+                    pp[o] = v0;
+                    pp[o + 1] = v1;
+                }
+            }
+}
+
+// a0 = bf16(s_in (x - c_in)), zero beyond n_in (blockDim.x = the padded width ldo)
+__global__ void k_prep_input(const float* __restrict__ x, int batch, int n_in, int ldo, const float* __restrict__ c,
+                             const float* __restrict__ sc, __nv_bfloat16* __restrict__ a0)
+{
+    const int b = blockIdx.x * blockDim.y + threadIdx.y, j = threadIdx.x;
+    if (b >= batch || j >= ldo) return;
+    const float v = (j < n_in) ? sc[j] * (x[(size_t)b * n_in + j] - c[j]) : 0.f;
+    a0[(size_t)b * ldo + j] = __float2bfloat16_rn(v);
+}
+
+// loss terms and output gradient: d = y_raw - (t - c_out) / s_out over the first
+// n_out columns; dY = bf16(2 d / (batch n_out)); per-block partial sums of d^2
+__global__ void k_loss_grad(const float* __restrict__ yraw, int ldy, const float* __restrict__ t, int batch, int n_out,
+                            const float* __restrict__ c, const float* __restrict__ sc, __nv_bfloat16* __restrict__ dY,
+                            float* __restrict__ partial)
+{
+    __shared__ float red[256];
+    const int b = blockIdx.x * blockDim.y + threadIdx.y, j = threadIdx.x;  // blockDim (64, 4)
+    float d2 = 0.f;
+    if (b < batch) {
+        float gval = 0.f;
+        if (j < n_out) {
+            const float ts = (t[(size_t)b * n_out + j] - c[j]) / sc[j];
+            const float d = yraw[(size_t)b * ldy + j] - ts;
+            d2 = d * d;
+            gval = 2.0f * d / ((float)batch * (float)n_out);
+        }
+        dY[(size_t)b * ldy + j] = __float2bfloat16_rn(gval);
+    }
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    red[tid] = d2;
+    __syncthreads();
+    for (int s2 = 128; s2 > 0; s2 >>= 1) {
+        if (tid < s2) red[tid] += red[tid + s2];
+        __syncthreads();
+    }
+    if (tid == 0) partial[blockIdx.x] = red[0];
+}
+
+// sum of n partials in a fixed order, divided by `div`, into *out
+__global__ void k_sum_partials(const float* __restrict__ partial, int n, float div, float* __restrict__ out)
+{
+    __shared__ float red[256];
+    float s = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int s2 = 128; s2 > 0; s2 >>= 1) {
+        if (threadIdx.x < s2) red[threadIdx.x] += red[threadIdx.x + s2];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0] / div;
+}
+
+// bias gradient: per (column, batch chunk) partial sums of the bf16 gradients
+__global__ void k_bias_partial(const __nv_bfloat16* __restrict__ dZ, int ld, int batch, int rows_per_chunk,
+                               float* __restrict__ part)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x, ch = blockIdx.y;
+    if (n >= ld) return;
+    const int b0 = ch * rows_per_chunk, b1 = min(batch, b0 + rows_per_chunk);
+    float s = 0.f;
+    for (int b = b0; b < b1; ++b) s += __bfloat162float(dZ[(size_t)b * ld + n]);
+    part[(size_t)ch * ld + n] = s;
+}
+
+// out[i] = sum over s < splits of part[s][i], in order
+__global__ void k_reduce_splits(const float* __restrict__ part, int splits, size_t count, float* __restrict__ out)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float s = 0.f;
+    for (int k = 0; k < splits; ++k) s += part[(size_t)k * count + i];
+    out[i] = s;
+}
+
+// Adam (bias-corrected) on the FP32 masters; refreshes the BF16 copies
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ gr, float* __restrict__ m, float* __restrict__ v,
+                       __nv_bfloat16* __restrict__ pb, size_t n, float lr, float c1, float c2)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = gr[i];
+    const float mi = 0.9f * m[i] + 0.1f * g, vi = 0.999f * v[i] + 0.001f * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    const float upd = lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+    const float pn = p[i] - upd;
+    p[i] = pn;
+    pb[i] = __float2bfloat16_rn(pn);
+}
+
+// y = s_out y_raw + c_out over the first n_out columns
+__global__ void k_output(const float* __restrict__ yraw, int ldy, int batch, int n_out, const float* __restrict__ c,
+                         const float* __restrict__ sc, float* __restrict__ y)
+{
+    const int b = blockIdx.x * blockDim.y + threadIdx.y, j = threadIdx.x;
+    if (b >= batch || j >= n_out) return;
+    y[(size_t)b * n_out + j] = sc[j] * yraw[(size_t)b * ldy + j] + c[j];
+}
+
+__global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict__ pb, size_t n)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) pb[i] = __float2bfloat16_rn(p[i]);
+}
+
+thread_local std::string g_mlp_error;
+
+lbib_status mlp_fail(lbib_status s, const std::string& m)
+{
+    g_mlp_error = m;
+    set_global_error(m.c_str());
+    return s;
+}
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+struct lbib_mlp {
+    lbib_mlp_desc desc{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int L = 0;                      // weight layers
+    std::vector<int> in, out;       // padded dims per layer
+    std::vector<int> in_true, out_true;
+    std::vector<size_t> woff, boff; // offsets into the flat parameter arrays
+    size_t nparam = 0;              // padded flat size
+    size_t ntrue = 0;               // host (unpadded) size
+    float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+    __nv_bfloat16* pb = nullptr;
+    float *cin = nullptr, *sin = nullptr, *cout = nullptr, *sout = nullptr;
+    int max_batch = 0;
+    __nv_bfloat16* a0 = nullptr;            // [B][in0]
+    std::vector<__nv_bfloat16*> act;        // per hidden layer [B][width]
+    std::vector<float*> z;                  // per hidden layer [B][width]
+    float* yraw = nullptr;                  // [B][outL]
+    __nv_bfloat16 *dY = nullptr, *dZa = nullptr, *dZb = nullptr;
+    float* part = nullptr;                  // split-K / bias partials
+    size_t part_floats = 0;
+    float* loss_part = nullptr;
+    float* loss_dev = nullptr;
+    int64_t t = 0;                          // Adam steps
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t mlp_alloc(lbib_mlp* net, T** p, size_t n)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+    if (e == cudaSuccess) {
+        net->allocs.push_back(q);
+        *p = static_cast<T*>(q);
+    }
+    return e;
+}
+
+template <bool TA, bool TB, int EPI>
+cudaError_t gemm(const GemmArgs& a0, int splits, cudaStream_t s)
+{
+    GemmArgs a = a0;
+    const int kt = (a.K + BK - 1) / BK;
+    splits = std::max(1, std::min(splits, kt));
+    a.k_tiles_per_split = (kt + splits - 1) / splits;
+    splits = (kt + a.k_tiles_per_split - 1) / a.k_tiles_per_split;
+    dim3 grid((a.M + BM - 1) / BM, a.N / BN, splits);
+    k_gemm<TA, TB, EPI><<<grid, GEMM_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// forward pass of `batch` rows already in net->a0; leaves y_raw
+cudaError_t forward_core(lbib_mlp* net, int batch)
+{
+    cudaError_t e = cudaSuccess;
+    const __nv_bfloat16* a = net->a0;
+    int lda = net->in[0];
+    for (int l = 0; l < net->L && e == cudaSuccess; ++l) {
+        GemmArgs g{};
+        g.A = a;
+        g.lda = lda;
+        g.B = net->pb + net->woff[l];
+        g.ldb = net->in[l];
+        g.M = batch;
+        g.N = net->out[l];
+        g.K = net->in[l];
+        g.bias = net->p + net->boff[l];
+        g.ldc = net->out[l];
+        if (l + 1 < net->L) {
+            g.Zout = net->z[l];
+            g.Aout = net->act[l];
+            e = gemm<false, false, EPI_FWD_GELU>(g, 1, net->stream);
+            a = net->act[l];
+            lda = net->out[l];
+        } else {
+            g.Zout = net->yraw;
+            e = gemm<false, false, EPI_FWD_LIN>(g, 1, net->stream);
+        }
+    }
+    return e;
+}
+
+int splits_for(int batch)
+{
+    // enough blocks for the weight-gradient GEMMs (K = batch) to fill the GPU
+    return std::max(1, std::min(MAX_SPLITS, (batch + 255) / 256));
+}
+
+// backward pass after forward_core and the loss gradient in dY; gradients into net->g
+cudaError_t backward_core(lbib_mlp* net, int batch)
+{
+    cudaError_t e = cudaSuccess;
+    const __nv_bfloat16* dcur = net->dY;  // gradient w.r.t. the current layer's output (pre-activation)
+    int ldd = net->out[net->L - 1];
+    const int splits = splits_for(batch);
+    for (int l = net->L - 1; l >= 0 && e == cudaSuccess; --l) {
+        const __nv_bfloat16* ain = (l == 0) ? net->a0 : net->act[l - 1];
+        const int ldin = net->in[l];
+        // dW_l = dcur^T ain: M = out, N = in, K = batch; both operands batch-major
+        GemmArgs gw{};
+        gw.A = dcur;
+        gw.lda = ldd;
+        gw.B = ain;
+        gw.ldb = ldin;
+        gw.M = net->out[l];
+        gw.N = net->in[l];
+        gw.K = batch;
+        gw.part = net->part;
+        gw.ldc = net->in[l];
+        e = gemm<true, true, EPI_PARTIAL>(gw, splits, net->stream);
+        if (e != cudaSuccess) break;
+        {
+            const int kt = (batch + BK - 1) / BK;
+            const int tps = (kt + std::min(splits, kt) - 1) / std::min(splits, kt);
+            const int used = (kt + tps - 1) / tps;
+            const size_t cnt = (size_t)net->out[l] * net->in[l];
+            k_reduce_splits<<<(unsigned)((cnt + 255) / 256), 256, 0, net->stream>>>(net->part, used, cnt,
+                                                                                     net->g + net->woff[l]);
+        }
+        // db_l = column sums of dcur
+        {
+            const int rows = 256, chunks = (batch + rows - 1) / rows;
+            dim3 grid((ldd + 63) / 64, chunks);
+            k_bias_partial<<<grid, 64, 0, net->stream>>>(dcur, ldd, batch, rows, net->part);
+            k_reduce_splits<<<(ldd + 255) / 256, 256, 0, net->stream>>>(net->part, chunks, (size_t)ldd,
+                                                                       net->g + net->boff[l]);
+        }
+        e = cudaGetLastError();
+        if (l == 0 || e != cudaSuccess) break;
+        // d pre-activation of layer l-1 = (dcur W_l) * GELU'(z_{l-1}): M = batch, N = in_l, K = out_l
+        __nv_bfloat16* dnext = (dcur == net->dZa) ? net->dZb : net->dZa;
+        GemmArgs gx{};
+        gx.A = dcur;
+        gx.lda = ldd;
+        gx.B = net->pb + net->woff[l];  // W_l stored [out][in] = [K][N]
+        gx.ldb = net->in[l];
+        gx.M = batch;
+        gx.N = net->in[l];
+        gx.K = net->out[l];
+        gx.Zin = net->z[l - 1];
+        gx.Aout = dnext;
+        gx.ldc = net->in[l];
+        e = gemm<false, true, EPI_BWD_GELU>(gx, 1, net->stream);
+        dcur = dnext;
+        ldd = net->in[l];
+    }
+    return e;
+}
+
+cudaError_t prep_and_loss(lbib_mlp* net, const float* x, const float* t, int batch)
+{
+    dim3 blk(64, 4);
+    k_prep_input<<<(batch + blk.y - 1) / blk.y, blk, 0, net->stream>>>(x, batch, net->desc.n_in, net->in[0], net->cin,
+                                                                       net->sin, net->a0);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = forward_core(net, batch);
+    if (e != cudaSuccess) return e;
+    const int ldy = net->out[net->L - 1];
+    dim3 lb(64, 4);
+    const int nblk = (batch + 3) / 4;
+    // the output layer is padded to 64 columns: blockDim.x covers it
+    k_loss_grad<<<nblk, lb, 0, net->stream>>>(net->yraw, ldy, t, batch, net->desc.n_out, net->cout, net->sout,
+                                              net->dY, net->loss_part);
+    k_sum_partials<<<1, 256, 0, net->stream>>>(net->loss_part, nblk, (float)batch * (float)net->desc.n_out,
+                                               net->loss_dev);
+    return cudaGetLastError();
+}
+
+struct Guard {
+    int prev = -1;
+    explicit Guard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        cudaSetDevice(dev);
+    }
+    ~Guard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
+{
+    if (!d || !out) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (d->n_in < 1 || d->n_in > 32 || d->width < 64 || d->width % 64 || d->width > 1024 || d->n_hidden < 1 ||
+        d->n_hidden > 8 || d->n_out < 1 || d->n_out > 64 || d->max_batch < 1)
+        return mlp_fail(LBIB_ERR_INVALID_ARG, "need 1 <= n_in <= 32, width a multiple of 64 up to 1024, "
+                                              "1 <= n_hidden <= 8, 1 <= n_out <= 64, max_batch >= 1");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || d->device < 0 || d->device >= ndev) {
+        cudaGetLastError();
+        return mlp_fail(LBIB_ERR_CUDA, "no CUDA device with that ordinal");
+    }
+    lbib_mlp* net = new (std::nothrow) lbib_mlp();
+    if (!net) return mlp_fail(LBIB_ERR_OOM, "host allocation failed");
+    net->desc = *d;
+    net->desc.in_shift = net->desc.in_scale = net->desc.out_shift = net->desc.out_scale = nullptr;
+    net->device = d->device;
+    Guard guard(net->device);
+    auto bail = [&](cudaError_t e, const char* what) {
+        lbib_mlp_destroy(net);
+        cudaGetLastError();
+        return mlp_fail(e == cudaErrorMemoryAllocation ? LBIB_ERR_OOM : LBIB_ERR_CUDA,
+                        std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    net->L = d->n_hidden + 1;
+    for (int l = 0; l < net->L; ++l) {
+        const int it = (l == 0) ? d->n_in : d->width, ot = (l + 1 < net->L) ? d->width : d->n_out;
+        net->in_true.push_back(it);
+        net->out_true.push_back(ot);
+        net->in.push_back(l == 0 ? 64 : d->width);  // every GEMM dimension a multiple of the 64 tile
+        net->out.push_back(l + 1 < net->L ? d->width : 64);
+    }
+    size_t off = 0;
+    for (int l = 0; l < net->L; ++l) {
+        net->woff.push_back(off);
+        off += (size_t)net->out[l] * net->in[l];
+        net->boff.push_back(off);
+        off += (size_t)net->out[l];
+        net->ntrue += (size_t)net->out_true[l] * net->in_true[l] + net->out_true[l];
+    }
+    net->nparam = off;
+    net->max_batch = d->max_batch;
+    const size_t B = (size_t)d->max_batch;
+    cudaError_t e = cudaSuccess;
+#define MA(p, n)                                     \
+    do {                                             \
+        e = mlp_alloc(net, &(p), (n));               \
+        if (e != cudaSuccess) return bail(e, #p);    \
+    } while (0)
+    MA(net->p, net->nparam);
+    MA(net->g, net->nparam);
+    MA(net->m, net->nparam);
+    MA(net->v, net->nparam);
+    MA(net->pb, net->nparam);
+    MA(net->cin, 32);
+    MA(net->sin, 32);
+    MA(net->cout, 64);
+    MA(net->sout, 64);
+    MA(net->a0, B * 64);
+    for (int l = 0; l + 1 < net->L; ++l) {
+        __nv_bfloat16* a = nullptr;
+        float* z = nullptr;
+        MA(a, B * d->width);
+        MA(z, B * d->width);
+        net->act.push_back(a);
+        net->z.push_back(z);
+    }
+    MA(net->yraw, B * 64);
+    MA(net->dY, B * 64);
+    MA(net->dZa, B * d->width);
+    MA(net->dZb, B * d->width);
+    const size_t wmax = (size_t)d->width * d->width;
+    const int chunks = (int)((B + 255) / 256);
+    net->part_floats = std::max((size_t)MAX_SPLITS * wmax, (size_t)chunks * d->width);
+    MA(net->part, net->part_floats);
+    MA(net->loss_part, (B + 3) / 4);
+    MA(net->loss_dev, 1);
+#undef MA
+    if (d->cuda_stream) {
+        net->stream = static_cast<cudaStream_t>(d->cuda_stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&net->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(e, "cudaStreamCreate");
+        net->own_stream = true;
+    }
+    // normalisation constants
+    std::vector<float> cin(32, 0.f), sin(32, 1.f), cout(64, 0.f), sout(64, 1.f);
+    for (int j = 0; j < d->n_in; ++j) {
+        if (d->in_shift) cin[j] = d->in_shift[j];
+        if (d->in_scale) sin[j] = d->in_scale[j];
+    }
+    for (int j = 0; j < d->n_out; ++j) {
+        if (d->out_shift) cout[j] = d->out_shift[j];
+        if (d->out_scale) sout[j] = d->out_scale[j];
+    }
+    for (int j = 0; j < d->n_out; ++j)
+        if (!(sout[j] != 0.f) || !std::isfinite(sout[j])) {
+            lbib_mlp_destroy(net);
+            return mlp_fail(LBIB_ERR_INVALID_ARG, "out_scale must be finite and non-zero");
+        }
+    if ((e = cudaMemcpy(net->cin, cin.data(), 32 * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(net->sin, sin.data(), 32 * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(net->cout, cout.data(), 64 * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(net->sout, sout.data(), 64 * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(e, "cudaMemcpy");
+    // Glorot-uniform weights from a host generator (splitmix64), zero biases and padding
+    std::vector<float> h(net->nparam, 0.f);
+    uint64_t st = d->seed ^ 0x9e3779b97f4a7c15ULL;
+    auto next = [&]() {
+        st += 0x9e3779b97f4a7c15ULL;
+        uint64_t zz = st;
+        zz = (zz ^ (zz >> 30)) * 0xbf58476d1ce4e5b9ULL;
+        zz = (zz ^ (zz >> 27)) * 0x94d049bb133111ebULL;
+        zz ^= zz >> 31;
+        return (double)(zz >> 11) * (1.0 / 9007199254740992.0);
+    };
+    for (int l = 0; l < net->L; ++l) {
+        const double lim = std::sqrt(6.0 / (net->in_true[l] + net->out_true[l]));
+        for (int o = 0; o < net->out_true[l]; ++o)
+            for (int i = 0; i < net->in_true[l]; ++i)
+                h[net->woff[l] + (size_t)o * net->in[l] + i] = (float)((2.0 * next() - 1.0) * lim);
+    }
+    if ((e = cudaMemcpy(net->p, h.data(), net->nparam * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemset(net->m, 0, net->nparam * 4)) != cudaSuccess ||
+        (e = cudaMemset(net->v, 0, net->nparam * 4)) != cudaSuccess ||
+        (e = cudaMemset(net->g, 0, net->nparam * 4)) != cudaSuccess)
+        return bail(e, "initialisation");
+    k_to_bf16<<<(unsigned)((net->nparam + 255) / 256), 256, 0, net->stream>>>(net->p, net->pb, net->nparam);
+    if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(net->stream)) != cudaSuccess)
+        return bail(e, "initialisation");
+    *out = net;
+    return LBIB_OK;
+}
+
+lbib_status lbib_mlp_forward(lbib_mlp* net, const float* x, int32_t batch, float* y)
+{
+    if (!net || !x || !y) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
+    if (batch < 1 || batch > net->max_batch) return mlp_fail(LBIB_ERR_INVALID_ARG, "batch outside 1 .. max_batch");
+    Guard guard(net->device);
+    dim3 blk(64, 4);
+    k_prep_input<<<(batch + 3) / 4, blk, 0, net->stream>>>(x, batch, net->desc.n_in, net->in[0], net->cin, net->sin,
+                                                           net->a0);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = forward_core(net, batch);
+    if (e == cudaSuccess) {
+        dim3 ob(64, 4);
+        k_output<<<(batch + 3) / 4, ob, 0, net->stream>>>(net->yraw, net->out[net->L - 1], batch, net->desc.n_out,
+                                                          net->cout, net->sout, y);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_forward: ") + cudaGetErrorString(e));
+    return LBIB_OK;
+}
+
+lbib_status lbib_mlp_train_step(lbib_mlp* net, const float* x, const float* t, int32_t batch, float lr, float* loss)
+{
+    if (!net || !x || !t) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
+    if (batch < 1 || batch > net->max_batch) return mlp_fail(LBIB_ERR_INVALID_ARG, "batch outside 1 .. max_batch");
+    if (!(lr > 0.f) || !std::isfinite(lr)) return mlp_fail(LBIB_ERR_INVALID_ARG, "lr must be positive");
+    Guard guard(net->device);
+    cudaError_t e = prep_and_loss(net, x, t, batch);
+    if (e == cudaSuccess) e = backward_core(net, batch);
+    if (e == cudaSuccess) {
+        net->t += 1;
+        const float c1 = 1.0f - (float)std::pow(0.9, (double)net->t);
+        const float c2 = 1.0f - (float)std::pow(0.999, (double)net->t);
+        k_adam<<<(unsigned)((net->nparam + 255) / 256), 256, 0, net->stream>>>(net->p, net->g, net->m, net->v, net->pb,
+                                                                               net->nparam, lr, c1, c2);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, net->loss_dev, 4, cudaMemcpyDeviceToDevice, net->stream);
+    if (e != cudaSuccess) return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_train_step: ") + cudaGetErrorString(e));
+    return LBIB_OK;
+}
+
+lbib_status lbib_mlp_param_count(lbib_mlp* net, size_t* n)
+{
+    if (!net || !n) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
+    *n = net->ntrue;
+    return LBIB_OK;
+}
+
+static void padded_to_host(const lbib_mlp* net, const std::vector<float>& pad, float* out)
+{
+    size_t k = 0;
+    for (int l = 0; l < net->L; ++l) {
+        for (int o = 0; o < net->out_true[l]; ++o)
+            for (int i = 0; i < net->in_true[l]; ++i) out[k++] = pad[net->woff[l] + (size_t)o * net->in[l] + i];
+        for (int o = 0; o < net->out_true[l]; ++o) out[k++] = pad[net->boff[l] + o];
+    }
+}
+
+lbib_status lbib_mlp_gradients(lbib_mlp* net, const float* x, const float* t, int32_t batch, float* grad, size_t n,
+                               float* loss)
+{
+    if (!net || !x || !t || !grad) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
+    if (n < net->ntrue) return mlp_fail(LBIB_ERR_INVALID_ARG, "buffer smaller than the parameter count");
+    if (batch < 1 || batch > net->max_batch) return mlp_fail(LBIB_ERR_INVALID_ARG, "batch outside 1 .. max_batch");
+    Guard guard(net->device);
+    cudaError_t e = prep_and_loss(net, x, t, batch);
+    if (e == cudaSuccess) e = backward_core(net, batch);
+    std::vector<float> h(net->nparam);
+    float lh = 0.f;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), net->g, net->nparam * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&lh, net->loss_dev, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_gradients: ") + cudaGetErrorString(e));
+    padded_to_host(net, h, grad);
+    if (loss) *loss = lh;
+    return LBIB_OK;
+}
+
+lbib_status lbib_mlp_get_params(lbib_mlp* net, float* params, size_t n)
+{
+    if (!net || !params) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
+    if (n < net->ntrue) return mlp_fail(LBIB_ERR_INVALID_ARG, "buffer smaller than the parameter count");
+    Guard guard(net->device);
+    std::vector<float> h(net->nparam);
+    cudaError_t e = cudaStreamSynchronize(net->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), net->p, net->nparam * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_get_params: ") + cudaGetErrorString(e));
+    padded_to_host(net, h, params);
+    return LBIB_OK;
+}
+
+lbib_status lbib_mlp_set_params(lbib_mlp* net, const float* params, size_t n)
+{
+    if (!net || !params) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
+    if (n < net->ntrue) return mlp_fail(LBIB_ERR_INVALID_ARG, "buffer smaller than the parameter count");
+    for (size_t i = 0; i < net->ntrue; ++i)
+        if (!std::isfinite(params[i])) return mlp_fail(LBIB_ERR_INVALID_ARG, "non-finite parameter");
+    Guard guard(net->device);
+    std::vector<float> h(net->nparam, 0.f);
+    size_t k = 0;
+    for (int l = 0; l < net->L; ++l) {
+        for (int o = 0; o < net->out_true[l]; ++o)
+            for (int i = 0; i < net->in_true[l]; ++i) h[net->woff[l] + (size_t)o * net->in[l] + i] = params[k++];
+        for (int o = 0; o < net->out_true[l]; ++o) h[net->boff[l] + o] = params[k++];
+    }
+    cudaError_t e = cudaStreamSynchronize(net->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(net->p, h.data(), net->nparam * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(net->m, 0, net->nparam * 4);
+    if (e == cudaSuccess) e = cudaMemset(net->v, 0, net->nparam * 4);
+    if (e == cudaSuccess) {
+        k_to_bf16<<<(unsigned)((net->nparam + 255) / 256), 256, 0, net->stream>>>(net->p, net->pb, net->nparam);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
+    if (e != cudaSuccess) return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_set_params: ") + cudaGetErrorString(e));
+    net->t = 0;
+    return LBIB_OK;
+}
+
+void lbib_mlp_destroy(lbib_mlp* net)
+{
+    if (!net) return;
+    Guard guard(net->device);
+    if (net->stream) cudaStreamSynchronize(net->stream);
+    for (void* p : net->allocs) cudaFree(p);
+    if (net->own_stream && net->stream) cudaStreamDestroy(net->stream);
+    cudaGetLastError();
+    delete net;
+}
+
+}  // extern "C"

@@ -61,6 +61,14 @@ class lbib_launch_config(ctypes.Structure):
                 ("bulk_nodes_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class lbib_mlp_desc(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int32), ("width", ctypes.c_int32), ("n_hidden", ctypes.c_int32),
+                ("n_out", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p), ("seed", ctypes.c_uint64),
+                ("in_shift", ctypes.POINTER(ctypes.c_float)), ("in_scale", ctypes.POINTER(ctypes.c_float)),
+                ("out_shift", ctypes.POINTER(ctypes.c_float)), ("out_scale", ctypes.POINTER(ctypes.c_float))]
+
+
 _P = ctypes.c_void_p
 _SIGS = {
     "lbib_create": [ctypes.POINTER(lbib_fluid_params), ctypes.POINTER(_P)],
@@ -98,6 +106,13 @@ _SIGS = {
     "lbib_get_launch_config": [_P, ctypes.POINTER(lbib_launch_config)],
     "lbib_set_launch_config": [_P, ctypes.POINTER(lbib_launch_config)],
     "lbib_autotune": [_P, ctypes.c_int32, ctypes.POINTER(lbib_launch_config)],
+    "lbib_mlp_create": [ctypes.POINTER(lbib_mlp_desc), ctypes.POINTER(_P)],
+    "lbib_mlp_forward": [_P, _P, ctypes.c_int32, _P],
+    "lbib_mlp_train_step": [_P, _P, _P, ctypes.c_int32, ctypes.c_float, _P],
+    "lbib_mlp_gradients": [_P, _P, _P, ctypes.c_int32, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_float)],
+    "lbib_mlp_param_count": [_P, ctypes.POINTER(ctypes.c_size_t)],
+    "lbib_mlp_get_params": [_P, _P, ctypes.c_size_t],
+    "lbib_mlp_set_params": [_P, _P, ctypes.c_size_t],
 }
 
 _lib = None
@@ -123,6 +138,8 @@ def load() -> ctypes.CDLL:
             lib.lbib_last_error.restype = ctypes.c_char_p
             lib.lbib_destroy.argtypes = [_P]
             lib.lbib_destroy.restype = None
+            lib.lbib_mlp_destroy.argtypes = [_P]
+            lib.lbib_mlp_destroy.restype = None
             _lib = lib
         return _lib
 
@@ -385,6 +402,88 @@ def from_capillary(cap, storage=None, device=0, stream=None, obs_capacity=0) -> 
     return s
 
 
+class Mlp:
+    """The surrogate network of include/lbib_mlp.h.  Device arrays are passed
+    as raw pointers (e.g. ``tensor.data_ptr()`` of contiguous float32 CUDA
+    tensors); this class only marshals arguments."""
+
+    def __init__(self, n_in, n_out, width=256, n_hidden=3, max_batch=65536, device=0, stream=None, seed=0,
+                 in_shift=None, in_scale=None, out_shift=None, out_scale=None):
+        self.lib = load()
+        keep = []
+
+        def fp(v):
+            if v is None:
+                return None
+            a = np.ascontiguousarray(np.asarray(v, dtype=np.float32))
+            keep.append(a)
+            return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+        d = lbib_mlp_desc(n_in=int(n_in), width=int(width), n_hidden=int(n_hidden), n_out=int(n_out),
+                          max_batch=int(max_batch), device=int(device), cuda_stream=stream,
+                          seed=int(seed) & (2**64 - 1), in_shift=fp(in_shift), in_scale=fp(in_scale),
+                          out_shift=fp(out_shift), out_scale=fp(out_scale))
+        h = ctypes.c_void_p()
+        _check(self.lib.lbib_mlp_create(ctypes.byref(d), ctypes.byref(h)), None)
+        self.net = h
+        self.n_in, self.n_out, self.width, self.n_hidden = int(n_in), int(n_out), int(width), int(n_hidden)
+
+    def close(self):
+        if getattr(self, "net", None):
+            self.lib.lbib_mlp_destroy(self.net)
+            self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self, st):
+        _check(st, None)
+
+    def forward(self, x_ptr: int, batch: int, y_ptr: int):
+        self._c(self.lib.lbib_mlp_forward(self.net, ctypes.c_void_p(x_ptr), int(batch), ctypes.c_void_p(y_ptr)))
+
+    def train_step(self, x_ptr: int, t_ptr: int, batch: int, lr: float, loss_ptr: Optional[int] = None):
+        self._c(self.lib.lbib_mlp_train_step(self.net, ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr), int(batch),
+                                             float(lr), ctypes.c_void_p(loss_ptr) if loss_ptr else None))
+
+    def param_count(self) -> int:
+        n = ctypes.c_size_t()
+        self._c(self.lib.lbib_mlp_param_count(self.net, ctypes.byref(n)))
+        return n.value
+
+    def gradients(self, x_ptr: int, t_ptr: int, batch: int):
+        g = np.zeros(self.param_count(), np.float32)
+        loss = ctypes.c_float()
+        self._c(self.lib.lbib_mlp_gradients(self.net, ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr), int(batch),
+                                            _vp(g), g.size, ctypes.byref(loss)))
+        return g, loss.value
+
+    def get_params(self):
+        p = np.zeros(self.param_count(), np.float32)
+        self._c(self.lib.lbib_mlp_get_params(self.net, _vp(p), p.size))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(np.asarray(p, dtype=np.float32))
+        self._c(self.lib.lbib_mlp_set_params(self.net, _vp(p), p.size))
+
+    def layers(self, p=None):
+        """Split a flat parameter vector into [(W, b), ...] (hidden layers, then output)."""
+        p = self.get_params() if p is None else p
+        dims = [self.n_in] + [self.width] * self.n_hidden + [self.n_out]
+        out, k = [], 0
+        for i, o in zip(dims[:-1], dims[1:]):
+            W = p[k:k + o * i].reshape(o, i)
+            k += o * i
+            b = p[k:k + o]
+            k += o
+            out.append((W, b))
+        return out
+
+
 def _add_bodies(s: Solver, cap, instance: int) -> None:
     for b in cap.bodies:
         i = s.add_membrane(b.kind, b.motion, b.xy, b.xy_ref, b.ca, b.beta, b.ka, b.density_ratio,
@@ -420,4 +519,4 @@ def roofline_bytes_per_node(storage: int) -> int:
 
 
 __all__ = [n for n in dir() if n.startswith("lbib_") or n.startswith("LBIB_")] + [
-    "Solver", "from_capillary", "from_capillaries", "load", "library_path", "LbibError", "roofline_bytes_per_node", "FIELDS"]
+    "Solver", "Mlp", "from_capillary", "from_capillaries", "load", "library_path", "LbibError", "roofline_bytes_per_node", "FIELDS"]

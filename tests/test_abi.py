@@ -12,11 +12,11 @@ import pytest
 from paper_2210_06043_gb300 import build, lbib
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "lbib.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("lbib.h", "lbib_mlp.h")]
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(lbib_[a-z0-9_]+)\s*\(", text)))
 
@@ -45,6 +45,7 @@ def _c_layout():
 #include <stdio.h>
 #include <stddef.h>
 #include "lbib.h"
+#include "lbib_mlp.h"
 #define O(t, f) printf("%s.%s %zu\n", #t, #f, offsetof(t, f))
 #define S(t) printf("%s.sizeof %zu\n", #t, sizeof(t))
 int main(void) {
@@ -55,6 +56,7 @@ int main(void) {
   S(lbib_obs); O(lbib_obs, n_l); O(lbib_obs, n_bound); O(lbib_obs, status);
   S(lbib_launch_config); O(lbib_launch_config, near_blocks); O(lbib_launch_config, bulk_tiles_y);
   O(lbib_launch_config, activation_stride); O(lbib_launch_config, bulk_nodes_per_thread);
+  S(lbib_mlp_desc); O(lbib_mlp_desc, cuda_stream); O(lbib_mlp_desc, seed); O(lbib_mlp_desc, out_scale);
   return 0;
 }
 '''
@@ -71,7 +73,7 @@ int main(void) {
 def test_ctypes_structs_match_the_header():
     lay = _c_layout()
     for cls in (lbib.lbib_fluid_params, lbib.lbib_membrane_desc, lbib.lbib_adhesion_params, lbib.lbib_obs,
-                lbib.lbib_launch_config):
+                lbib.lbib_launch_config, lbib.lbib_mlp_desc):
         name = cls.__name__
         assert int(lay[f"{name}.sizeof"]) == ctypes.sizeof(cls), name
         for key, val in lay.items():

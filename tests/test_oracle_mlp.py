@@ -1,0 +1,77 @@
+"""Pins of the surrogate network's CPU oracle (oracle/mlp.py) against facts
+other than itself: finite differences of the FP64 loss, closed forms of the
+Gaussian error linear unit, and the bfloat16 rounding rule."""
+import math
+
+import numpy as np
+
+from oracle import mlp
+
+
+def _tiny(seed=0, n_in=3, width=5, n_hidden=2, n_out=2):
+    rng = np.random.default_rng(seed)
+    dims = [n_in] + [width] * n_hidden + [n_out]
+    layers = [(rng.normal(0, 0.7, (o, i)), rng.normal(0, 0.2, o)) for i, o in zip(dims[:-1], dims[1:])]
+    x = rng.uniform(-1, 1, (7, n_in))
+    t = rng.normal(0, 1, (7, n_out))
+    norm = dict(c_in=rng.uniform(-0.2, 0.2, n_in), s_in=rng.uniform(0.5, 2, n_in),
+                c_out=rng.uniform(-1, 1, n_out), s_out=rng.uniform(0.5, 2, n_out))
+    return layers, x, t, norm
+
+
+def test_gradients_match_central_differences():
+    layers, x, t, norm = _tiny()
+    loss, grads = mlp.gradients(layers, x, t, **norm)
+    h = 1e-6
+    for l, (W, b) in enumerate(layers):
+        for arr, g in ((W, grads[l][0]), (b, grads[l][1])):
+            it = np.nditer(arr, flags=["multi_index"])
+            for _ in it:
+                idx = it.multi_index
+                old = arr[idx]
+                arr[idx] = old + h
+                lp, _ = mlp.gradients(layers, x, t, **norm)
+                arr[idx] = old - h
+                lm, _ = mlp.gradients(layers, x, t, **norm)
+                arr[idx] = old
+                fd = (lp - lm) / (2 * h)
+                assert abs(fd - g[idx]) <= 1e-7 * max(1.0, abs(fd)), (l, idx, fd, g[idx])
+    # the loss is the mean squared standardised error
+    _, yraw, _ = mlp.forward(layers, x, **norm)
+    ts = (t - norm["c_out"]) / norm["s_out"]
+    assert abs(loss - np.mean((yraw - ts) ** 2)) < 1e-15
+
+
+def test_gelu_closed_forms():
+    z = np.linspace(-6, 6, 241)
+    assert mlp.gelu(0.0) == 0.0 and abs(mlp.gelu_d(0.0) - 0.5) < 1e-16
+    # GELU(z) - GELU(-z) = z (Phi(z) + Phi(-z) = 1)
+    assert np.abs(mlp.gelu(z) - mlp.gelu(-z) - z).max() < 1e-14
+    # derivative by central differences
+    h = 1e-6
+    fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
+    assert np.abs(fd - mlp.gelu_d(z)).max() < 1e-8
+    # Phi(1) = 0.841344746068543 (standard normal table)
+    assert abs(float(mlp.phi_cdf(1.0)) - 0.8413447460685429) < 1e-15
+
+
+def test_bf16_rounding_rule():
+    # 8 significant bits: 1 + 2^-7 is representable, 1 + 2^-8 is a tie -> even (1), 1 + 3 * 2^-8 -> 1 + 2^-6
+    v = np.array([1.0, 1 + 2.0**-7, 1 + 2.0**-8, 1 + 3 * 2.0**-8, -2.5, 3.0e-30], np.float64)
+    r = mlp.bf16(v)
+    assert r[0] == 1.0 and r[1] == 1 + 2.0**-7 and r[2] == 1.0 and r[3] == 1 + 2.0**-6 and r[4] == -2.5
+    assert abs(r[5] - 3.0e-30) <= 2.0**-8 * 3.0e-30
+    rng = np.random.default_rng(1)
+    x = rng.normal(0, 10, 10000)
+    q = mlp.bf16(x)
+    assert (np.abs(q - x) <= 2.0**-8 * np.abs(x) + 1e-45).all()
+    assert np.array_equal(mlp.bf16(q), q)  # idempotent
+
+
+def test_quantized_oracle_stays_near_the_exact_one():
+    layers, x, t, norm = _tiny(seed=3, width=16)
+    l64, g64 = mlp.gradients(layers, x, t, **norm)
+    lq, gq = mlp.gradients(layers, x, t, quantize=True, **norm)
+    assert abs(lq - l64) <= 0.05 * l64
+    f64, fq = mlp.flat(g64), mlp.flat(gq)
+    assert np.linalg.norm(fq - f64) <= 0.05 * np.linalg.norm(f64)
