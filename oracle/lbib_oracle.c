@@ -832,10 +832,16 @@ static void body_bonds(orc_sim* s, int bi, const double* nlx, const double* nly,
             }
         }
         if (b->bound[k] && !isinf(b->sigma)) {
-            double yl = hypot(px - b->ax[k], py - b->ay[k]);
+            /* Eq. 13: a linear spring, F = sigma (y_l - y_eq) along n_l, the unit
+             * vector from the ligand site to its receptor (the element's outward
+             * normal for a bond perpendicular to the wall under a base element);
+             * the element normal if the site sits on its anchor */
+            double dx = b->ax[k] - px, dy = b->ay[k] - py;
+            double yl = hypot(dx, dy);
             double F = b->sigma * (yl - b->yeq);
-            fex[a] += F * nlx[a];
-            fey[a] += F * nly[a];
+            double ex = (yl > 0.0) ? dx / yl : nlx[a], ey = (yl > 0.0) ? dy / yl : nly[a];
+            fex[a] += F * ex;
+            fey[a] += F * ey;
         }
     }
 }

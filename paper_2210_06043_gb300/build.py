@@ -61,11 +61,18 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        for obj, log in ex.map(compile_one, SOURCES):
-            objs.append(obj)
-            if verbose and log:
-                print(log)
+    try:
+        with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+            for obj, log in ex.map(compile_one, SOURCES):
+                objs.append(obj)
+                if verbose and log:
+                    print(log)
+    finally:  # a failed compile leaves no objects behind
+        if len(objs) < len(SOURCES):
+            for src in SOURCES:
+                o = os.path.join(OUT_DIR, src.replace(".cu", f".{tag}.o"))
+                if os.path.exists(o):
+                    os.remove(o)
     tmp = LIB + f".{tag}.tmp"
     r = subprocess.run([cc, "-shared", ARCH, "-o", tmp, *objs], capture_output=True, text=True)
     for o in objs:

@@ -322,7 +322,6 @@ lbib_status finalize(lbib_ctx* ctx)
     std::vector<int32_t> lig_el(std::max(nlig, 1)), bound(std::max(nlig, 1), 0), site_off(nmark + 1, 0);
     std::vector<double> lig_t(std::max(nlig, 1)), anchor(2 * (size_t)std::max(nlig, 1), 0.0);
     const double nu = L.nu, umax = L.umax;
-    std::vector<double> inst_lmax(ni, 0.0);
     int off = 0, loff = 0;
     for (int b = 0; b < nb; ++b) {
         const HostBody& h = ctx->bodies[order[b]];
@@ -351,8 +350,6 @@ lbib_status finalize(lbib_ctx* ctx)
             l0[off + l] = std::sqrt(dx * dx + dy * dy);
             double ax = ref[2 * l] - ref[2 * lm], ay = ref[2 * l + 1] - ref[2 * lm + 1];
             th0[off + l] = std::atan2(ax * dy - ay * dx, ax * dx + ay * dy);
-            double cx = h.xy[2 * w] - h.xy[2 * l], cy = h.xy[2 * w + 1] - h.xy[2 * l + 1];
-            inst_lmax[h.inst] = std::max(inst_lmax[h.inst], std::sqrt(cx * cx + cy * cy));
         }
         Poly pr = polygon(ref), pc = polygon(h.xy);
         B.A0 = pr.A;
@@ -431,15 +428,6 @@ lbib_status finalize(lbib_ctx* ctx)
         off += nv;
     }
     for (int e = 0; e < nmark; ++e) site_off[e + 1] += site_off[e];
-    // activation radii from the longest element of the body's instance (a
-    // marker moves < 1 dx per step; stencil half-width 2; element growth)
-    for (int b = 0; b < nb; ++b) {
-        const double lmax = inst_lmax[bc[b].inst];
-        bc[b].r_act = 2.0 + std::max(1.2, 0.75 * lmax) + 1.0;
-        // a centroid lies within stride / 2 elements of an activating one; 1.5 l_max
-        // per element allows 50% stretching
-        bc[b].act_reach = 0.5 * 1.5 * lmax;
-    }
     d.ring_cap = ctx->P.obs_capacity > 0 ? ctx->P.obs_capacity : 4096;
 
     // device arrays

@@ -115,8 +115,6 @@ struct BodyConst {
     int sigma_inf, inst, x0, nxi;     // instance and its node columns [x0, x0 + nxi)
     int moff, lig0, b0, nbi;          // instance's first marker, first site, first body, body count
     double A0, P0, inv_A0, inv_P0;
-    double r_act;                     // the instance's activation radius (lattice units)
-    double act_reach;                 // added to r_act per element of activation stride
     double ks, kb, ka, mv, mass, inertia;
     double sigma, ycr, yeq, Pf, kr0_dt, xi;
 };
@@ -183,8 +181,9 @@ struct Dev {
     int64_t* step;             // Lagrangian step counter n (advanced by the last Lagrangian block)
     uint32_t* status;
     uint32_t* ticket;
-    // activation radius around markers (lattice units) per instance: BodyConst::r_act;
-    // every act_stride-th element centroid activates r_act + act_stride * act_reach
+    // every act_stride-th element centroid activates the tiles within reach of
+    // itself and the elements up to the next activating one (from the current
+    // positions)
     int act_stride;            // 1, 2 or 4 (results do not depend on it)
     int chain_priority;        // stream priority of the membrane and near launches (0: default)
     double dcut;               // repulsion cut-off (Eq. 12)

@@ -510,20 +510,26 @@ __global__ void __launch_bounds__(T) k_lagrangian(Dev d, int p)
             __syncthreads();
         }
         if (!B.sigma_inf) {
+            // Eq. 13 as a linear spring: sigma (y_l - y_eq) along the unit vector
+            // from the site to its receptor (the element normal for a site on its anchor)
             const R sig = (R)B.sigma;
             for (int l = tid; l < nv; l += T) {
-                R s = 0;
+                R fx = 0, fy = 0;
                 for (int k = d.site_off[off + l]; k < d.site_off[off + l + 1]; ++k) {
                     if (!d.bound[k]) continue;
                     const R t = lt[k];
                     const P2<R> SX = p2_add<R>(P2<R>{xh[l], xl[l]}, t * ex[l]);
                     const P2<R> SY = p2_add<R>(P2<R>{yh[l], yl[l]}, t * ey[l]);
-                    const R dxa = p2_sub<R>(SX, p2_of<R>(d.anchor[k]));
-                    const R dya = p2_sub<R>(SY, p2_of<R>(d.anchor[d.nlig + k]));
-                    s += sig * (sqrt(dxa * dxa + dya * dya) - yeq);
+                    const R dxa = p2_sub<R>(p2_of<R>(d.anchor[k]), SX);
+                    const R dya = p2_sub<R>(p2_of<R>(d.anchor[d.nlig + k]), SY);
+                    const R ylen = sqrt(dxa * dxa + dya * dya);
+                    const R F = sig * (ylen - yeq);
+                    const bool on = ylen > R(0);
+                    fx += F * (on ? dxa / ylen : nlx[l]);
+                    fy += F * (on ? dya / ylen : nly[l]);
                 }
-                ewx[l] = s * nlx[l];
-                ewy[l] = s * nly[l];
+                ewx[l] = fx;
+                ewy[l] = fy;
             }
         }
     }
@@ -699,7 +705,6 @@ __global__ void __launch_bounds__(T) k_lagrangian(Dev d, int p)
     const uint32_t* flag1 = d.nearflag[(n + 1) % 3];  // near tiles of lattice step n + 1
     const int c2 = (int)(n2 % 3);
     const int stride = d.act_stride;
-    const int ra = (int)ceil(B.r_act + stride * B.act_reach) + 1;
     for (int l0 = tid / K; l0 < nvq; l0 += Q) {
         const bool valid = l0 < nv;
         const int l = valid ? l0 : nv - 1;
@@ -755,10 +760,28 @@ __global__ void __launch_bounds__(T) k_lagrangian(Dev d, int p)
             }
         }
         if (l % stride == 0 || l == nv - 1) {
-            // tiles within r_act of every centroid are scheduled near for lattice
-            // step n + 2: each stride-th element covers the box of half-width
-            // ra (r_act plus the stride's reach along the chain) around its
-            // stencil origin; the lanes split the tile list
+            // Tiles the lattice step n + 2 must update as near: every stencil the
+            // membrane update of step n + 2 reads (vertices, probes, new element
+            // centroids) and the spreading of step n + 2 writes lies, per element
+            // e, within the box of half-width reach_e = max(l_e / 2, 1.2) + 2
+            // around its centroid (vertex / probe offset plus the stencil),
+            // widened by one node for two steps of motion.  Each stride-th element
+            // covers itself and the following ones up to the next activating
+            // element, at their current distances; the box is taken around the
+            // stencil origin floor(c), one more node.  The lanes split the tiles.
+            const int cover = (l % stride == 0) ? min(stride, nv - l) : 1;
+            R reach = R(0);
+            for (int j = 0; j < cover; ++j) {
+                const int e = l + j, e1 = (e + 1 == nv) ? 0 : e + 1;
+                const R ex_ = p2_sub<R>(P2<R>{qxh[e1], qxl[e1]}, P2<R>{qxh[e], qxl[e]});
+                const R ey_ = p2_sub<R>(P2<R>{qyh[e1], qyl[e1]}, P2<R>{qyh[e], qyl[e]});
+                const P2<R> cxe = p2_add<R>(P2<R>{qxh[e], qxl[e]}, R(0.5) * ex_);
+                const P2<R> cye = p2_add<R>(P2<R>{qyh[e], qyl[e]}, R(0.5) * ey_);
+                const R dxe = fabs(p2_sub<R>(cxe, CX)), dye = fabs(p2_sub<R>(cye, CY));
+                const R own = fmax(R(0.5) * sqrt(ex_ * ex_ + ey_ * ey_), R(1.2)) + R(2);
+                reach = fmax(reach, fmax(dxe, dye) + own);
+            }
+            const int ra = (int)ceil(reach + R(1)) + 1;
             const int i0 = max(0, sc.ix - ra), i1 = min(B.nxi - 1, sc.ix + ra);
             const int j0 = max(0, sc.jy - ra), j1 = min(L.ny - 1, sc.jy + ra);
             if (i0 <= i1 && j0 <= j1) {

@@ -377,8 +377,8 @@ __global__ void k_macro(Dev d, int buf, int64_t m, int x0, int inx, O* rho_o, O*
 }
 
 // Marks as near, for lattice steps m (which & 1) and m + 1 (which & 2), every
-// tile within its instance's r_act of an element centroid of X^m (initial
-// activation and after a restore).
+// tile within an element's reach of its centroid of X^m (initial activation
+// and after a restore).
 template <typename R>
 __global__ void k_activate(Dev d, int64_t m, int which)
 {
@@ -392,7 +392,10 @@ __global__ void k_activate(Dev d, int64_t m, int which)
     const double* P = d.pos[m & 1];
     double X = 0.5 * (P[k] + P[w]), Y = 0.5 * (P[d.nmark + k] + P[d.nmark + w]);
     // positions are in instance coordinates; the box is clipped to the instance
-    const double ra = B.r_act;
+    // half-width: vertex / probe offset plus the stencil (max(l / 2, 1.2) + 2)
+    // and one node of motion, as the membrane update's activation
+    const double ex_ = P[w] - P[k], ey_ = P[d.nmark + w] - P[d.nmark + k];
+    const double ra = fmax(0.5 * sqrt(ex_ * ex_ + ey_ * ey_), 1.2) + 3.0;
     int i0 = B.x0 + max(0, (int)floor(X - ra)), i1 = B.x0 + min(B.nxi - 1, (int)floor(X + ra) + 1);
     int j0 = max(0, (int)floor(Y - 0.5 - ra)), j1 = min(L.ny - 1, (int)floor(Y - 0.5 + ra) + 1);
     if (i0 > i1 || j0 > j1) return;

@@ -1,0 +1,266 @@
+"""Learned surrogate of the adhesion observables (N_L, delta p, r) over the
+particle / cell parameter space of Sec. 3.1, trained on trajectories the
+solver itself generates, with the solver as fallback outside the training hull.
+
+Pieces (all numerical work in the library's kernels; this module only lays
+out inputs and drives the C ABI):
+  * the parameter space and its sampling (``Point``, ``sample_points``);
+  * the capillary each point runs in (``capillary_for``);
+  * trajectory generation with batched solver contexts (``generate``);
+  * training of ``lbib.Mlp`` on the trajectories (``train``);
+  * ``Surrogate.predict``: the network inside the hull, the solver outside.
+
+Training geometry (a reading; the paper's Table 1 is missing): H = 40 nodes,
+160 nodes long, tau = 1, Re = 0.05 (Stokes regime, u_max = 2.08e-4), cell
+(7 um, 96 markers) released 40 nodes from the inlet, particle (2 um long,
+32 markers) at 75 nodes on the lower wall, 3e5 steps (t u_max / H = 1.56),
+observables sampled 512 times; bond stiffness and rates scaled by Re / 0.01
+(Stokes scaling of the paper's Re = 1e-2).  The particle's capillary number spans
+log10 Ca in [-4, -3] (stiffer membranes exceed the explicit membrane update's
+stability limit at this step; they are outside the hull) or rigid.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import lbib
+from . import workloads as wl
+
+NY, NX = 40, 160
+RE = 0.05
+RE_PAPER = 0.01  # Sec. 3.1; bond stiffness and rates scale with RE / RE_PAPER (Stokes scaling)
+CELL_X, PARTICLE_X = 40.0, 75.0
+CELL_MARKERS, PARTICLE_MARKERS = 96, 32
+STEPS, SAMPLES = 300000, 512
+AR_RANGE = (0.25, 1.0)
+LOGCA_RANGE = (-4.0, -3.0)
+DENSITY_RANGE = (10.0, 50.0)  # ligand sites per um of particle perimeter
+FEATURES = ("aspect_ratio", "log10_ca", "rigid", "globular", "biconcave", "ligand_density", "t_star")
+OUTPUTS = ("n_l", "delta_p", "r")
+
+
+@dataclasses.dataclass(frozen=True)
+class Point:
+    """One point of the parameter space."""
+    aspect_ratio: float      # particle thickness / length
+    log10_ca: float          # particle capillary number (ignored when rigid)
+    rigid: bool
+    cell: str                # "globular" | "biconcave"
+    ligand_density: float    # sites per um of perimeter
+    seed: int = 0            # Philox key of the bond kinetics
+
+
+def sample_points(n: int, seed: int = 0, rigid_fraction: float = 0.2) -> List[Point]:
+    """Stratified (Latin hypercube) samples of the continuous axes, rigid
+    particles with probability rigid_fraction, both cell shapes alternating."""
+    rng = np.random.default_rng(seed)
+
+    def lhs(lo, hi):
+        u = (rng.permutation(n) + rng.uniform(0, 1, n)) / n
+        return lo + (hi - lo) * u
+
+    ar, lc, dens = lhs(*AR_RANGE), lhs(*LOGCA_RANGE), lhs(*DENSITY_RANGE)
+    rig = rng.uniform(0, 1, n) < rigid_fraction
+    return [Point(float(ar[i]), float(lc[i]), bool(rig[i]), ("globular", "biconcave")[i % 2], float(dens[i]),
+                  seed=int(seed * 100003 + i)) for i in range(n)]
+
+
+def features(p: Point, t_star) -> np.ndarray:
+    """Feature rows [len(t_star), 7] for point p at the given times."""
+    t = np.atleast_1d(np.asarray(t_star, np.float64))
+    row = [p.aspect_ratio, LOGCA_RANGE[0] if p.rigid else p.log10_ca, float(p.rigid),
+           float(p.cell == "globular"), float(p.cell == "biconcave"), p.ligand_density]
+    return np.concatenate([np.tile(np.asarray(row, np.float64), (t.size, 1)), t[:, None]], 1).astype(np.float32)
+
+
+def in_hull(p: Point, t_star_max: float) -> bool:
+    """Inside the box the training set covers (per axis; categories always)."""
+    ok = AR_RANGE[0] <= p.aspect_ratio <= AR_RANGE[1] and DENSITY_RANGE[0] <= p.ligand_density <= DENSITY_RANGE[1]
+    if not p.rigid:
+        ok = ok and LOGCA_RANGE[0] <= p.log10_ca <= LOGCA_RANGE[1]
+    return ok and t_star_max <= STEPS * u_max() / NY + 1e-12
+
+
+def u_max(re: float = RE) -> float:
+    nu = (1.0 - 0.5) / 3.0
+    return re * nu / NY
+
+
+def capillary_for(p: Point, re: float = RE) -> wl.Capillary:
+    """The training capillary of point p (geometry in the module docstring)."""
+    dx = wl.H_UM / NY
+    if p.cell == "globular":
+        c = wl.circle(CELL_MARKERS, CELL_X, 0.5 * NY, wl.CELL_RADIUS_UM / dx)
+        body_c = wl.Body(wl.CELL, wl.DEFORMABLE, c, ca=1e-3, beta=0.0)
+    else:
+        c = wl.biconcave(CELL_MARKERS, CELL_X, 0.5 * NY, wl.CELL_RADIUS_UM / dx)
+        body_c = wl.Body(wl.CELL, wl.DEFORMABLE, c, ca=1e-3, beta=1e-2)
+    a, b = 0.5 * wl.PARTICLE_LENGTH_UM / dx, 0.5 * p.aspect_ratio * wl.PARTICLE_LENGTH_UM / dx
+    part = wl.ellipse(PARTICLE_MARKERS, PARTICLE_X, wl.PARTICLE_GAP_UM / dx + b, a, b)
+    perim = float(np.sum(np.hypot(*(np.roll(part, -1, 0) - part).T))) * dx  # um
+    y_cr = wl.Y_CR_UM / dx
+    # sigma (units rho nu^2 / H) and the per-step rates scaled by Re / Re_paper: the
+    # ratios sigma / (rho nu u_max) and k H / u_max stay those of the paper's flow
+    f = re / RE_PAPER
+    adh = wl.Adhesion(n_lig=max(4, int(round(p.ligand_density * perim))), sigma=1.0 * f, y_cr=y_cr, y_eq=0.5 * y_cr,
+                      kf_dt=0.085 * f, kr0_dt=1e-5 * f, xi=1.0 / (0.5 * y_cr) ** 2)
+    if p.rigid:
+        body_p = wl.Body(wl.PARTICLE, wl.RIGID, part, ca=0.0, beta=0.0, density_ratio=1.1, adhesion=adh)
+    else:
+        body_p = wl.Body(wl.PARTICLE, wl.DEFORMABLE, part, ca=10.0 ** p.log10_ca, beta=1e-2, density_ratio=1.1,
+                         adhesion=adh)
+    return wl.Capillary(f"surrogate capillary {p}", NX, NY, 1.0, re, STEPS, "fp32", p.seed, [body_c, body_p])
+
+
+def generate(points: Sequence[Point], steps: int = STEPS, samples: int = SAMPLES, batch: int = 256, device: int = 0,
+             stream: Optional[int] = None, log=None):
+    """Runs every point's capillary for `steps` steps in batches of `batch`
+    instances and samples the observables `samples` times (every
+    steps / samples steps).  Returns t_star [samples], Y [len(points),
+    samples, 3] (N_L, delta p, r) and the GPU seconds spent."""
+    stride = max(1, steps // samples)
+    out = np.zeros((len(points), samples, 3))
+    t_star = np.zeros(samples)
+    secs = 0.0
+    for b0 in range(0, len(points), batch):
+        chunk = points[b0:b0 + batch]
+        caps = [capillary_for(p) for p in chunk]
+        s = lbib.from_capillaries(caps, device=device, stream=stream, obs_capacity=max(64, 2 * stride))
+        s.autotune(steps_per_trial=20)
+        t0 = time.perf_counter()
+        for k in range(samples):
+            s.advance(stride)
+            rec = s.latest_observables()
+            for i, r in enumerate(rec):
+                out[b0 + i, k] = (r["n_l"], r["delta_p"], r["r"])
+            t_star[k] = rec[0]["t_star"]
+        secs += time.perf_counter() - t0
+        s.close()
+        if log:
+            log(f"generated {b0 + len(chunk)}/{len(points)} trajectories, {secs:.1f} s")
+    return t_star, out, secs
+
+
+@dataclasses.dataclass
+class Trained:
+    net: "lbib.Mlp"
+    in_shift: np.ndarray
+    in_scale: np.ndarray
+    out_shift: np.ndarray
+    out_scale: np.ndarray
+    t_star_max: float
+    losses: List[float]
+
+
+def normalisation(X: np.ndarray, Y: np.ndarray):
+    """Affine maps to roughly unit scale: inputs to [-1, 1] by their range,
+    outputs standardised."""
+    lo, hi = X.min(0), X.max(0)
+    span = np.where(hi > lo, hi - lo, 1.0)
+    in_shift, in_scale = 0.5 * (lo + hi), 2.0 / span
+    out_shift, out_scale = Y.mean(0), np.where(Y.std(0) > 0, Y.std(0), 1.0)
+    return (in_shift.astype(np.float32), in_scale.astype(np.float32), out_shift.astype(np.float32),
+            out_scale.astype(np.float32))
+
+
+def train(X: np.ndarray, Y: np.ndarray, steps: int = 3000, batch: int = 8192, lr: float = 2e-3, seed: int = 0,
+          device: int = 0, width: int = 256, n_hidden: int = 3, log=None) -> Trained:
+    """Adam on minibatches drawn from (X, Y) by the library's kernels;
+    cosine decay of the step size."""
+    import torch
+
+    torch.cuda.set_device(device)
+    st = torch.cuda.current_stream()
+    norm = normalisation(X, Y)
+    net = lbib.Mlp(X.shape[1], Y.shape[1], width=width, n_hidden=n_hidden, max_batch=max(batch, 65536),
+                   device=device, stream=st.cuda_stream if st.cuda_stream else None, seed=seed,
+                   in_shift=norm[0], in_scale=norm[1], out_shift=norm[2], out_scale=norm[3])
+    Xd = torch.as_tensor(X, dtype=torch.float32).cuda()
+    Yd = torch.as_tensor(Y, dtype=torch.float32).cuda()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    loss = torch.zeros(1, device="cuda")
+    losses = []
+    for k in range(steps):
+        idx = torch.randint(0, X.shape[0], (batch,), device="cuda", generator=g)
+        xb, yb = Xd[idx].contiguous(), Yd[idx].contiguous()
+        eta = lr * 0.5 * (1.0 + math.cos(math.pi * k / steps))
+        net.train_step(xb.data_ptr(), yb.data_ptr(), batch, max(eta, lr * 1e-3), loss.data_ptr())
+        if k % 100 == 0 or k == steps - 1:
+            torch.cuda.synchronize()
+            losses.append(float(loss.item()))
+            if log:
+                log(f"step {k}: loss {losses[-1]:.4e}")
+    torch.cuda.synchronize()
+    return Trained(net, *norm, t_star_max=float(X[:, -1].max()), losses=losses)
+
+
+def predict_network(tr: Trained, X: np.ndarray) -> np.ndarray:
+    """Network outputs for feature rows X (any count; batches of 65536)."""
+    import torch
+
+    out = np.zeros((X.shape[0], tr.net.n_out), np.float32)
+    Xd = torch.as_tensor(X, dtype=torch.float32).cuda()
+    Yd = torch.zeros(X.shape[0], tr.net.n_out, device="cuda")
+    for b0 in range(0, X.shape[0], 65536):
+        n = min(65536, X.shape[0] - b0)
+        tr.net.forward(Xd[b0:].data_ptr(), n, Yd[b0:].data_ptr())
+    torch.cuda.synchronize()
+    out[:] = Yd.cpu().numpy()
+    return out
+
+
+class Surrogate:
+    """Predicts (N_L, delta p, r) at times t_star for parameter points: the
+    trained network inside the hull of its training set, the solver outside
+    (flagged)."""
+
+    def __init__(self, trained: Trained, steps: int = STEPS):
+        self.tr = trained
+        self.steps = steps
+
+    def predict(self, points: Sequence[Point], t_star: np.ndarray):
+        t_star = np.asarray(t_star, np.float64)
+        inside = [in_hull(p, float(t_star.max())) and float(t_star.max()) <= self.tr.t_star_max + 1e-9
+                  for p in points]
+        Y = np.zeros((len(points), t_star.size, 3))
+        idx_in = [i for i, ok in enumerate(inside) if ok]
+        if idx_in:
+            X = np.concatenate([features(points[i], t_star) for i in idx_in])
+            Yn = predict_network(self.tr, X).reshape(len(idx_in), t_star.size, 3)
+            for j, i in enumerate(idx_in):
+                Y[i] = Yn[j]
+        idx_out = [i for i, ok in enumerate(inside) if not ok]
+        if idx_out:
+            Y[idx_out] = solve(points=[points[i] for i in idx_out], t_star=t_star)
+        return Y, np.asarray(inside)
+
+
+def solve(points: Sequence[Point], t_star: np.ndarray, device: int = 0) -> np.ndarray:
+    """The solver at the requested times (the fallback).  Points with
+    log10 Ca below the range run with u_max lowered to keep the explicit
+    membrane update stable (t_star is kept; more steps)."""
+    t_star = np.asarray(t_star, np.float64)
+    Y = np.zeros((len(points), t_star.size, 3))
+    for i, p in enumerate(points):
+        re = RE
+        if not p.rigid and p.log10_ca < LOGCA_RANGE[0]:
+            re = RE * 10.0 ** (p.log10_ca - LOGCA_RANGE[0])
+        cap = capillary_for(p, re=re)
+        s = lbib.from_capillary(cap, device=device)
+        um = u_max(re)
+        done = 0
+        for k, ts in enumerate(t_star):
+            target = int(round(ts * NY / um))
+            if target > done:
+                s.advance(target - done)
+                done = target
+            r = s.latest_observables()[0] if done > 0 else None
+            Y[i, k] = (r["n_l"], r["delta_p"], r["r"]) if r else (1.0, 0.0, np.nan)
+        s.close()
+    return Y

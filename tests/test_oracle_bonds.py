@@ -87,10 +87,11 @@ def test_bound_fraction_relaxes_to_the_two_state_equilibrium():
     assert np.mean(acc) == pytest.approx(pf / (pf + pr), abs=0.03)
 
 
-def test_bond_force_is_a_linear_spring_along_the_element_normal():
-    """Eq. 13 with sigma in units rho nu^2 / H (Sec. 2.5): every base bond
-    pulls along the base's outward normal (towards the wall) with
-    sigma (y - y_eq); only the twenty base sites are within y_cr."""
+def test_bond_force_is_a_linear_spring_normal_to_the_wall_at_formation():
+    """Eq. 13 with sigma in units rho nu^2 / H (Sec. 2.5): every base bond,
+    perpendicular to the wall when it forms, pulls along the base's outward
+    normal (towards the wall) with sigma (y - y_eq); only the twenty base sites
+    are within y_cr."""
     gap, y_cr, y_eq, sigma = 0.3, 0.35, 0.1, 2.0
     s, b = _flat_particle_sim(gap, y_cr, y_eq, 0.0, 0.0, 0.0, sigma=sigma, n_lig=48)
     assert s.body_scalars(b)["nl0"] == 20
@@ -99,6 +100,31 @@ def test_bond_force_is_a_linear_spring_along_the_element_normal():
     nu, ny = 1.0 / 6.0, 24
     assert fwy.sum() == pytest.approx(-20 * sigma * nu * nu / ny * (gap - y_eq), rel=1e-6)
     assert abs(fwx.sum()) < 1e-12 * abs(fwy.sum())
+
+
+def test_bond_force_resists_the_drift_of_its_site():
+    """A linear spring pulls a site back towards its receptor: a rigid particle
+    dragged downstream by a forced channel flow stretches its bonds along x,
+    and their total force then opposes the drift (x component of opposite sign
+    to the sites' mean displacement from their anchors) while still pulling
+    towards the wall."""
+    nx, ny = 48, 24
+    s = oracle.OracleSim(nx, ny, tau=1.0, re=0.0, bc=oracle.BC_PERIODIC_FORCE, g=(2e-6, 0.0), seed=0)
+    xy = np.stack([np.linspace(14, 30, 40, endpoint=False), np.full(40, 0.2)], 1)
+    top = np.stack([np.linspace(30, 14, 40, endpoint=False), np.full(40, 2.2)], 1)
+    rect = np.concatenate([xy, [[30, 0.2], [30, 1.2]], top, [[14, 2.2], [14, 1.2]]])
+    b = s.add_body(oracle.PARTICLE, oracle.RIGID, rect, None, 0.0, 0.0, 1.0, 1.1)
+    s.set_adhesion(b, 60, 1.0, 0.35, 0.1, 0.0, 0.0, 0.0)  # bonds neither form nor break
+    nl0 = s.body_scalars(b)["nl0"]
+    assert nl0 > 10
+    s.step(400)
+    bound, ax, ay, _ = s.bonds(b, 60)
+    xp = s.body_xy(b)[:, 0].mean()
+    drift = xp - 22.0
+    assert drift > 1e-4  # dragged downstream
+    fwx, fwy = s.body(b, "fwx"), s.body(b, "fwy")
+    assert fwx.sum() < 0 and fwy.sum() < 0
+    assert abs(fwx.sum()) > 1e-3 * abs(fwy.sum())
 
 
 def test_fixed_particle_keeps_its_bonds():
