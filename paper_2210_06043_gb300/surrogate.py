@@ -264,3 +264,118 @@ def solve(points: Sequence[Point], t_star: np.ndarray, device: int = 0) -> np.nd
             Y[i, k] = (r["n_l"], r["delta_p"], r["r"]) if r else (1.0, 0.0, np.nan)
         s.close()
     return Y
+
+
+def plain_solver_seconds_per_step(points: Sequence[Point], steps: int = 2000, device: int = 0) -> float:
+    """Device seconds per step of the one-instance solver (each point alone in
+    its own autotuned context), mean over the points."""
+    import torch
+
+    out = []
+    for p in points:
+        st = torch.cuda.Stream()
+        s = lbib.from_capillary(capillary_for(p), device=device, stream=st.cuda_stream)
+        s.autotune(steps_per_trial=20)
+        s.advance(10)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st.synchronize()
+        a.record(st)
+        s.advance(steps)
+        b.record(st)
+        b.synchronize()
+        out.append(a.elapsed_time(b) / 1e3 / steps)
+        s.close()
+    return float(np.mean(out))
+
+
+def evaluate(tr: Trained, points: Sequence[Point], t_star: np.ndarray, Y: np.ndarray):
+    """Held-out errors of the network: per output, RMSE, mean absolute error,
+    RMSE relative to the output's spread over the held-out set, and the
+    inference time of all (points x times) queries."""
+    import torch
+
+    X = np.concatenate([features(p, t_star) for p in points])
+    predict_network(tr, X[:65536])  # warm-up
+    t0 = time.perf_counter()
+    P = predict_network(tr, X).reshape(len(points), t_star.size, 3)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    err = {}
+    for j, name in enumerate(OUTPUTS):
+        e = P[:, :, j] - Y[:, :, j]
+        spread = float(Y[:, :, j].std())
+        err[name] = {"rmse": float(np.sqrt(np.mean(e * e))), "mae": float(np.mean(np.abs(e))),
+                     "rmse_over_std": float(np.sqrt(np.mean(e * e)) / spread) if spread > 0 else None,
+                     "std": spread}
+    return err, secs, P
+
+
+def main(argv=None):
+    import argparse
+    import json
+    import os
+
+    import torch
+
+    ap = argparse.ArgumentParser(description="generate solver trajectories, train the surrogate, evaluate it")
+    ap.add_argument("--points", type=int, default=2048)
+    ap.add_argument("--holdout", type=float, default=0.1)
+    ap.add_argument("--steps", type=int, default=STEPS)
+    ap.add_argument("--samples", type=int, default=SAMPLES)
+    ap.add_argument("--batch", type=int, default=256, help="capillaries per solver context")
+    ap.add_argument("--train-steps", type=int, default=4000)
+    ap.add_argument("--train-batch", type=int, default=8192)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--out", default="surrogate_run")
+    args = ap.parse_args(argv)
+    os.makedirs(args.out, exist_ok=True)
+    st = torch.cuda.Stream()
+    torch.cuda.set_stream(st)
+    pts = sample_points(args.points, seed=args.seed)
+    t_star, Y, gen_secs = generate(pts, steps=args.steps, samples=args.samples, batch=args.batch,
+                                   stream=st.cuda_stream, log=print)
+    np.savez_compressed(os.path.join(args.out, "trajectories.npz"), t_star=t_star, Y=Y,
+                        P=np.array([[p.aspect_ratio, p.log10_ca, p.rigid, p.cell == "globular", p.ligand_density,
+                                     p.seed] for p in pts]))
+    n_hold = max(1, int(round(args.holdout * len(pts))))
+    rng = np.random.default_rng(args.seed + 1)
+    order = rng.permutation(len(pts))
+    hold, fit = order[:n_hold], order[n_hold:]
+    X = np.concatenate([features(pts[i], t_star) for i in fit])
+    T = Y[fit].reshape(-1, 3).astype(np.float32)
+    t0 = time.perf_counter()
+    tr = train(X, T, steps=args.train_steps, batch=args.train_batch, lr=args.lr, seed=args.seed, log=print)
+    train_secs = time.perf_counter() - t0
+    err, inf_secs, P = evaluate(tr, [pts[i] for i in hold], t_star, Y[hold])
+    # solver costs: the batched sweep that generated the data and the plain one-instance solver
+    per_step_plain = plain_solver_seconds_per_step([pts[i] for i in hold[:8]])
+    plain_per_traj = per_step_plain * args.steps
+    batched_per_traj = gen_secs / len(pts)
+    surrogate_per_traj = inf_secs / len(hold)
+    # fallback: a particle stiffer than the training range goes to the solver
+    stiff = dataclasses.replace(pts[hold[0]], rigid=False, log10_ca=-4.5)
+    sur = Surrogate(tr, steps=args.steps)
+    short = t_star[: max(2, args.samples // 64)]
+    Yf, inside = sur.predict([pts[hold[0]], stiff], short)
+    report = {
+        "points": len(pts), "holdout_points": int(n_hold), "samples_per_trajectory": int(args.samples),
+        "steps_per_trajectory": int(args.steps), "t_star_max": float(t_star[-1]),
+        "generation_gpu_seconds": gen_secs, "training_seconds": train_secs, "train_steps": args.train_steps,
+        "final_training_loss": tr.losses[-1], "holdout_errors": err,
+        "seconds_per_trajectory": {"plain_solver": plain_per_traj, "batched_solver": batched_per_traj,
+                                   "surrogate": surrogate_per_traj},
+        "sims_per_hour": {"plain_solver": 3600.0 / plain_per_traj, "batched_solver": 3600.0 / batched_per_traj,
+                          "surrogate": 3600.0 / surrogate_per_traj},
+        "speedup_vs_plain_solver": plain_per_traj / surrogate_per_traj,
+        "fallback": {"inside_hull": [bool(v) for v in inside], "stiff_point_solved": bool(np.isfinite(Yf[1]).all())},
+    }
+    tr.net.get_params().tofile(os.path.join(args.out, "weights.f32"))
+    with open(os.path.join(args.out, "report.json"), "w") as fh:
+        json.dump(report, fh, indent=1)
+    print(json.dumps(report))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
