@@ -45,6 +45,7 @@ struct GemmArgs {
     __nv_bfloat16* Aout;      // [M][ldc] bf16 activations (forward GELU) or gradients (backward)
     float* part;              // [splits][M][ldc] (split-K partials)
     int ldc;
+    uint32_t* status;         // error word: bit 0 set when a bounded wait gave up
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -210,6 +211,159 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_gemm(GemmArgs g)
             }
 }
 
+// ---------------------------------------------------------------- tcgen05 path
+// C[M][N] = A[M][K] B[N][K]^T with both operands K-major: one CTA of 128
+// threads per 128 x N tile (N <= 256, a multiple of 16), K in blocks of 64.
+// Operand tiles are staged (cp.async) in the canonical no-swizzle K-major
+// layout of 8 x 8 core matrices (element (r, k) at (r / 8) * 1024 + (k / 8) *
+// 128 + (r % 8) * 16 + (k % 8) * 2 bytes: 128 B between core matrices along K,
+// 1024 B between 8-row groups); one elected thread issues tcgen05.mma (M 128,
+// N, K 16 per instruction, BF16 x BF16 -> FP32) into a tensor-memory
+// accumulator of N columns and commits to an mbarrier; the epilogue reads the
+// accumulator with tcgen05.ld (warp w owns rows 32 w .. 32 w + 31).
+constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 128;
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 26;  // mbarrier polls before giving up
+
+__host__ __device__ constexpr size_t tc_smem_bytes(int n) { return (size_t)(TC_BM + n) * TC_BK * 2 + 64; }
+// shared memory requested per CTA: at most two CTAs per SM, so their tensor-memory
+// allocations (<= 256 columns each) never exceed the SM's 512 columns
+constexpr size_t TC_SMEM_REQUEST = 96 * 1024;
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+    d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;     // leading byte offset: next core matrix along K
+    d |= (uint64_t)((1024u >> 4) & 0x3FFF) << 32;    // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                          // descriptor version (sm_100 family)
+    // base offset 0, absolute LBO mode 0, layout type 0 (no swizzle)
+    return d;
+}
+
+__device__ __forceinline__ uint32_t tc_idesc(int n)
+{
+    uint32_t d = 0;
+    d |= 1u << 4;                     // D format FP32
+    d |= 1u << 7;                     // A format BF16
+    d |= 1u << 10;                    // B format BF16
+    // A, B K-major (bits 15, 16 zero), no negation
+    d |= (uint32_t)(n >> 3) << 17;    // N / 8
+    d |= (uint32_t)(TC_BM >> 4) << 24; // M / 16
+    return d;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase)
+{
+    for (uint32_t it = 0; it < TC_WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(phase)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(GemmArgs g)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char* sa = tc_smem;                                   // 128 x 64 bf16, 16 KB
+    unsigned char* sb = tc_smem + TC_BM * TC_BK * 2;               // N x 64 bf16
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tc_smem + (size_t)(TC_BM + g.N) * TC_BK * 2);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TC_BM, N = g.N;
+    uint32_t ncols = 32;
+    while ((int)ncols < N) ncols <<= 1;  // power of two >= 32
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = tc_idesc(N);
+    uint32_t phase = 0;
+    bool ok = true;
+    const int kblocks = g.K / TC_BK;
+    for (int kb = 0; kb < kblocks && ok; ++kb) {
+        const int k0 = kb * TC_BK;
+        // stage A (128 rows) and B (N rows), 16-byte chunks, rows beyond M zero
+        for (int c = tid; c < TC_BM * 8; c += TC_THREADS) {
+            const int r = c >> 3, kc = c & 7;
+            const int m = m0 + r;
+            const bool v = m < g.M;
+            cp_async16(sa + (r >> 3) * 1024 + kc * 128 + (r & 7) * 16, g.A + (size_t)(v ? m : 0) * g.lda + k0 + kc * 8,
+                       v);
+        }
+        for (int c = tid; c < N * 8; c += TC_THREADS) {
+            const int r = c >> 3, kc = c & 7;
+            cp_async16(sb + (r >> 3) * 1024 + kc * 128 + (r & 7) * 16, g.B + (size_t)r * g.ldb + k0 + kc * 8, true);
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {  // K 16 per instruction: two core matrices along K
+                const uint64_t da = tc_desc(smem_u32(sa) + kk * 256);
+                const uint64_t db = tc_desc(smem_u32(sb) + kk * 256);
+                const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(bar)));
+        }
+        ok = mbar_wait(bar, phase);  // the tiles are free again once the MMAs completed
+        phase ^= 1u;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!ok) {
+        if (tid == 0) atomicOr(g.status, 1u);
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31 (tile rows), 16 columns at a time
+        const int m = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                "%13, %14, %15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (m < g.M) {
+                const size_t o = (size_t)m * g.ldc + c0;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float z = __uint_as_float(r[j]) + g.bias[c0 + j];
+                    g.Zout[o + j] = z;
+                    if (EPI == EPI_FWD_GELU) g.Aout[o + j] = __float2bfloat16_rn(gelu(z));
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
 // a0 = bf16(s_in (x - c_in)), zero beyond n_in (blockDim.x = the padded width ldo)
 __global__ void k_prep_input(const float* __restrict__ x, int batch, int n_in, int ldo, const float* __restrict__ c,
                              const float* __restrict__ sc, __nv_bfloat16* __restrict__ a0)
@@ -355,6 +509,8 @@ struct lbib_mlp {
     float* loss_part = nullptr;
     float* loss_dev = nullptr;
     int64_t t = 0;                          // Adam steps
+    uint32_t* status = nullptr;             // bounded-wait error word of the tensor-core kernels
+    bool tc = true;                         // forward products on tcgen05
     std::vector<void*> allocs;
 };
 
@@ -385,6 +541,23 @@ cudaError_t gemm(const GemmArgs& a0, int splits, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <int EPI>
+cudaError_t gemm_tc(const GemmArgs& a, cudaStream_t s)
+{
+    static_assert(tc_smem_bytes(256) <= TC_SMEM_REQUEST, "tiles fit the request");
+    const size_t smem = TC_SMEM_REQUEST;
+    static bool configured[4] = {false, false, false, false};
+    if (!configured[EPI]) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)TC_SMEM_REQUEST);
+        if (e != cudaSuccess) return e;
+        configured[EPI] = true;
+    }
+    dim3 grid((a.M + TC_BM - 1) / TC_BM);
+    k_gemm_tc<EPI><<<grid, TC_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 // forward pass of `batch` rows already in net->a0; leaves y_raw
 cudaError_t forward_core(lbib_mlp* net, int batch)
 {
@@ -402,15 +575,17 @@ cudaError_t forward_core(lbib_mlp* net, int batch)
         g.K = net->in[l];
         g.bias = net->p + net->boff[l];
         g.ldc = net->out[l];
+        g.status = net->status;
+        const bool tc = net->tc && g.K % TC_BK == 0 && g.N % 16 == 0 && g.N <= 256;
         if (l + 1 < net->L) {
             g.Zout = net->z[l];
             g.Aout = net->act[l];
-            e = gemm<false, false, EPI_FWD_GELU>(g, 1, net->stream);
+            e = tc ? gemm_tc<EPI_FWD_GELU>(g, net->stream) : gemm<false, false, EPI_FWD_GELU>(g, 1, net->stream);
             a = net->act[l];
             lda = net->out[l];
         } else {
             g.Zout = net->yraw;
-            e = gemm<false, false, EPI_FWD_LIN>(g, 1, net->stream);
+            e = tc ? gemm_tc<EPI_FWD_LIN>(g, net->stream) : gemm<false, false, EPI_FWD_LIN>(g, 1, net->stream);
         }
     }
     return e;
@@ -597,6 +772,7 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
     MA(net->part, net->part_floats);
     MA(net->loss_part, (B + 3) / 4);
     MA(net->loss_dev, 1);
+    MA(net->status, 1);
 #undef MA
     if (d->cuda_stream) {
         net->stream = static_cast<cudaStream_t>(d->cuda_stream);
@@ -645,7 +821,8 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
     if ((e = cudaMemcpy(net->p, h.data(), net->nparam * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(net->m, 0, net->nparam * 4)) != cudaSuccess ||
         (e = cudaMemset(net->v, 0, net->nparam * 4)) != cudaSuccess ||
-        (e = cudaMemset(net->g, 0, net->nparam * 4)) != cudaSuccess)
+        (e = cudaMemset(net->g, 0, net->nparam * 4)) != cudaSuccess ||
+        (e = cudaMemset(net->status, 0, 4)) != cudaSuccess)
         return bail(e, "initialisation");
     k_to_bf16<<<(unsigned)((net->nparam + 255) / 256), 256, 0, net->stream>>>(net->p, net->pb, net->nparam);
     if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(net->stream)) != cudaSuccess)
