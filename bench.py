@@ -241,6 +241,62 @@ def plain_solver(caps, local, steps, warmup):
     return out
 
 
+def surrogate_inference(local, stream, iters=50, batch=65536):
+    """Throughput of the surrogate network's inference (include/lbib_mlp.h:
+    7 inputs, 3 x 256 GELU, 3 outputs; forward products on tcgen05) on batches
+    of 65 536 queries, CUDA events on the launching stream; and one training
+    step (batch 8192, mma.sync backward).  Weights random: timing only."""
+    import torch
+
+    from paper_2210_06043_gb300 import lbib
+    from paper_2210_06043_gb300 import surrogate as sg
+
+    net = lbib.Mlp(7, 3, width=256, n_hidden=3, max_batch=batch, device=local, stream=stream.cuda_stream, seed=0)
+    x = torch.rand(batch, 7, device="cuda")
+    y = torch.empty(batch, 3, device="cuda")
+    t = torch.rand(batch, 3, device="cuda")
+    for _ in range(5):
+        net.forward(x.data_ptr(), batch, y.data_ptr())
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(iters):
+        net.forward(x.data_ptr(), batch, y.data_ptr())
+    b.record(stream)
+    b.synchronize()
+    t_inf = a.elapsed_time(b) / 1e3 / iters
+    tb = 8192
+    for _ in range(3):
+        net.train_step(x.data_ptr(), t.data_ptr(), tb, 1e-4)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(iters):
+        net.train_step(x.data_ptr(), t.data_ptr(), tb, 1e-4)
+    b.record(stream)
+    b.synchronize()
+    t_train = a.elapsed_time(b) / 1e3 / iters
+    net.close()
+    flops = 2.0 * batch * (64 * 256 + 2 * 256 * 256 + 256 * 64)  # products as padded and run
+    alg = 2.0 * batch * (7 * 256 + 2 * 256 * 256 + 256 * 3)
+    peak = None
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            peak = float(json.load(fh)["bf16_tflops"])
+    per_step = sg.plain_solver_seconds_per_step(sg.sample_points(2, seed=9), steps=500)
+    plain_traj = per_step * sg.STEPS
+    traj_per_call = batch / sg.SAMPLES
+    return {"inference_batch": batch, "inference_ms": t_inf * 1e3, "queries_per_s": batch / t_inf,
+            "tflops_run": flops / t_inf / 1e12, "tflops_algorithmic": alg / t_inf / 1e12,
+            "bf16_peak_tflops": peak, "frac_of_bf16_peak": (flops / t_inf / 1e12 / peak) if peak else None,
+            "train_step_ms_batch_8192": t_train * 1e3,
+            "sims_per_hour": traj_per_call * 3600.0 / t_inf,
+            "plain_solver_sims_per_hour": 3600.0 / plain_traj,
+            "speedup_vs_plain_solver": plain_traj * traj_per_call / t_inf,
+            "note": f"a simulation = one {sg.SAMPLES}-sample trajectory of the surrogate's {sg.NX}x{sg.NY} capillary "
+                    f"({sg.STEPS} solver steps); held-out accuracy of the trained network in the design notes"}
+
+
 def run_gpu(args):
     import torch
 
@@ -388,6 +444,8 @@ def run_gpu(args):
             "plain_solver": f"each capillary alone in its own context (same kernels, autotuned), "
                             f"{args.plain_steps} steps after 3 warm-up steps, warm L2, CUDA events",
             "accuracy": "every instance bit-identical to its lone run (tests/test_gpu_batch.py)"}
+    if batch and not args.no_surrogate:
+        line["surrogate"] = surrogate_inference(local, stream)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(caps, args.cpu_nodes)
     print(json.dumps(line), flush=True)
@@ -416,6 +474,7 @@ def main():
                     "lagrangian_threads,near_blocks,bulk_tiles_y,activation_stride[,bulk_nodes_per_thread] "
                     "instead of the autotuner")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate inference timing")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -272,7 +272,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(GemmArgs g)
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     unsigned char* sa = tc_smem;                                   // 128 x 64 bf16, 16 KB
     unsigned char* sb = tc_smem + TC_BM * TC_BK * 2;               // N x 64 bf16
-    uint64_t* bar = reinterpret_cast<uint64_t*>(tc_smem + (size_t)(TC_BM + g.N) * TC_BK * 2);
+    // barrier and tensor-memory address at the end of the region (the epilogue
+    // reuses the front for staging)
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tc_smem + TC_SMEM_REQUEST - 64);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * TC_BM, N = g.N;
@@ -335,28 +337,50 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(GemmArgs g)
     if (!ok) {
         if (tid == 0) atomicOr(g.status, 1u);
     } else {
-        // epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31 (tile rows), 16 columns at a time
-        const int m = m0 + warp * 32 + lane;
-        for (int c0 = 0; c0 < N; c0 += 16) {
-            uint32_t r[16];
-            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                "%13, %14, %15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
-                : "r"(ta));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (m < g.M) {
-                const size_t o = (size_t)m * g.ldc + c0;
+        // epilogue: warp w reads TMEM lanes 32 w .. 32 w + 31 (its tile rows) in
+        // blocks of 64 columns and stages them in shared memory (the operand
+        // tiles are free once the last MMA completed), then writes whole row
+        // segments: consecutive lanes, consecutive columns (coalesced)
+        constexpr int SC = 64, ZP = SC + 1, AP = SC + 2;  // 12.5 KB per warp, 50 KB in all
+        static_assert(4 * (32 * ZP + 16 * AP) * 4 <= TC_SMEM_REQUEST - 64, "staging below the barrier");
+        float* zst = reinterpret_cast<float*>(tc_smem) + warp * (32 * ZP + 16 * AP);
+        __nv_bfloat16* ast = reinterpret_cast<__nv_bfloat16*>(zst + 32 * ZP);
+        for (int c0 = 0; c0 < N; c0 += SC) {
+#pragma unroll
+            for (int sub = 0; sub < SC / 16; ++sub) {
+                uint32_t r[16];
+                const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c0 + 16 * sub);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15}, [%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const float z = __uint_as_float(r[j]) + g.bias[c0 + j];
-                    g.Zout[o + j] = z;
-                    if (EPI == EPI_FWD_GELU) g.Aout[o + j] = __float2bfloat16_rn(gelu(z));
+                    const int col = 16 * sub + j;
+                    const float z = __uint_as_float(r[j]) + g.bias[c0 + col];
+                    zst[lane * ZP + col] = z;
+                    if (EPI == EPI_FWD_GELU) ast[lane * AP + col] = __float2bfloat16_rn(gelu(z));
                 }
             }
+            __syncwarp();
+            for (int rr = 0; rr < 32; ++rr) {
+                const int m = m0 + warp * 32 + rr;
+                if (m >= g.M) break;
+                const size_t o = (size_t)m * g.ldc + c0;
+                if (g.Zout) {
+                    g.Zout[o + lane] = zst[rr * ZP + lane];
+                    g.Zout[o + 32 + lane] = zst[rr * ZP + 32 + lane];
+                }
+                if (EPI == EPI_FWD_GELU) {
+                    const __nv_bfloat162 v = __halves2bfloat162(ast[rr * AP + 2 * lane], ast[rr * AP + 2 * lane + 1]);
+                    reinterpret_cast<__nv_bfloat162*>(g.Aout + o)[lane] = v;
+                }
+            }
+            __syncwarp();
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -559,7 +583,7 @@ cudaError_t gemm_tc(const GemmArgs& a, cudaStream_t s)
 }
 
 // forward pass of `batch` rows already in net->a0; leaves y_raw
-cudaError_t forward_core(lbib_mlp* net, int batch)
+cudaError_t forward_core(lbib_mlp* net, int batch, bool store_z = true)
 {
     cudaError_t e = cudaSuccess;
     const __nv_bfloat16* a = net->a0;
@@ -578,7 +602,8 @@ cudaError_t forward_core(lbib_mlp* net, int batch)
         g.status = net->status;
         const bool tc = net->tc && g.K % TC_BK == 0 && g.N % 16 == 0 && g.N <= 256;
         if (l + 1 < net->L) {
-            g.Zout = net->z[l];
+            // pre-activations are kept for the backward pass only (the tensor-core path may skip them)
+            g.Zout = (store_z || !tc) ? net->z[l] : nullptr;
             g.Aout = net->act[l];
             e = tc ? gemm_tc<EPI_FWD_GELU>(g, net->stream) : gemm<false, false, EPI_FWD_GELU>(g, 1, net->stream);
             a = net->act[l];
@@ -840,7 +865,7 @@ lbib_status lbib_mlp_forward(lbib_mlp* net, const float* x, int32_t batch, float
     k_prep_input<<<(batch + 3) / 4, blk, 0, net->stream>>>(x, batch, net->desc.n_in, net->in[0], net->cin, net->sin,
                                                            net->a0);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = forward_core(net, batch);
+    if (e == cudaSuccess) e = forward_core(net, batch, false);
     if (e == cudaSuccess) {
         dim3 ob(64, 4);
         k_output<<<(batch + 3) / 4, ob, 0, net->stream>>>(net->yraw, net->out[net->L - 1], batch, net->desc.n_out,
