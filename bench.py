@@ -56,19 +56,23 @@ SWEEP = ("sweep of 64 capillaries in one batch: particle AR {0.25,0.5,0.75,1} x 
          "256-marker cells, 96-marker particles with 200 ligand sites; Re 1e-2, tau 1, fp32 populations")
 
 
-def _workload(name, instances=64):
-    """List of capillaries and the config block naming them."""
+def _workload(name, instances=64, seed=0):
+    """List of capillaries and the config block naming them.  Under torchrun
+    each rank draws its own sweep (seed = rank): the ranks together run a
+    sweep of 64 N capillaries split across the GPUs, no exchange between them."""
     from paper_2210_06043_gb300 import workloads as wl
     if name == "production":
         caps = [wl.production_capillary(seed=0)]
         cfg = {"workload": PRODUCTION, "nx": caps[0].nx, "ny": caps[0].ny}
     else:
-        caps = wl.sweep_capillaries(seed=0)[:instances]
+        caps = wl.sweep_capillaries(seed=seed)[:instances]
         cfg = {"workload": SWEEP if instances == 64 else f"first {instances} capillaries of the {SWEEP}",
                "instances": len(caps), "nx_total": sum(c.nx for c in caps), "ny": caps[0].ny}
     cfg.update({"nodes": sum(c.nodes for c in caps), "markers": sum(c.markers for c in caps),
                 "ligand_sites": sum(b.adhesion.n_lig for c in caps for b in c.bodies if b.adhesion),
-                "parallelism": "replicas (one independent copy of the workload per GPU)"})
+                "parallelism": ("data-parallel over capillaries: each rank steps its own 64-capillary draw "
+                                "(seed = rank), no collective on the data path" if name == "sweep" else
+                                "replicas (one independent copy of the capillary per GPU)")})
     return caps, cfg
 
 
@@ -308,7 +312,7 @@ def run_gpu(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    caps, cfg = _workload(args.workload, args.instances)
+    caps, cfg = _workload(args.workload, args.instances, seed=rank)
     if args.storage:  # population storage other than the workload's FP32
         import dataclasses
         caps = [dataclasses.replace(c, storage=args.storage) for c in caps]
