@@ -67,6 +67,28 @@ lbib_status lbib_mlp_train_step(lbib_mlp* net, const float* x, const float* t, i
 lbib_status lbib_mlp_gradients(lbib_mlp* net, const float* x, const float* t, int32_t batch, float* grad, size_t n,
                                float* loss);
 
+/* Data-parallel training (each rank holds a copy of the network; the ranks'
+ * shards of one global batch have equal size).  The loss is a mean over the
+ * batch, so the global batch's gradient is the mean of the shards' gradients:
+ * every rank calls lbib_mlp_backward on its shard, the caller sums the arrays
+ * across ranks (an all-reduce) and every rank calls lbib_mlp_apply_gradient
+ * with scale = 1 / ranks, which leaves the copies identical.
+ *
+ * lbib_mlp_backward: gradient of the batch loss with respect to every
+ * parameter, without an update, into the DEVICE array grad of
+ * n >= lbib_mlp_param_count floats (layout as lbib_mlp_get_params); loss
+ * DEVICE float (may be NULL) receives the batch loss.  Enqueued on the context
+ * stream (no wait); the values equal lbib_mlp_gradients' bit for bit. */
+lbib_status lbib_mlp_backward(lbib_mlp* net, const float* x, const float* t, int32_t batch, float* grad, size_t n,
+                              float* loss);
+
+/* One Adam step (as lbib_mlp_train_step's) with the gradient scale * grad in
+ * place of a batch's own: grad DEVICE, n >= param_count floats, layout as
+ * lbib_mlp_get_params; scale finite, lr > 0.  Enqueued on the context stream;
+ * grad may be overwritten by the next call on the context only after this one
+ * has run (stream order). */
+lbib_status lbib_mlp_apply_gradient(lbib_mlp* net, const float* grad, size_t n, float scale, float lr);
+
 /* Number of parameters: for each layer (hidden ones first, then the output
  * layer) its weights W [out][in] row-major, then its biases b [out]. */
 lbib_status lbib_mlp_param_count(lbib_mlp* net, size_t* n);

@@ -14,7 +14,9 @@ tests/test_oracle_mlp.py.  quantize=True inserts the library's roundings at
 the same points: weights and activations to bfloat16 (round to nearest even),
 the input scaling and the targets' standardisation in float32, the output
 gradient and the back-propagated pre-activation gradients to bfloat16; the
-products stay exact (FP64) where the GPU accumulates in FP32.
+products stay exact (FP64) where the GPU accumulates in FP32.  ``adam_step`` is
+the optimiser's update rule; it is pinned by its closed forms (first step and
+constant gradient move every parameter by lr against the gradient's sign).
 """
 from __future__ import annotations
 
@@ -105,6 +107,18 @@ def gradients(layers, x, t, c_in, s_in, c_out, s_out, quantize=False):
         _, z_prev = cache[l - 1]
         g = _q((g @ _q(W, quantize)) * gelu_d(z_prev), quantize)
     return loss, grads
+
+
+def adam_step(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1) in FP64: moment
+    estimates m, v updated with gradient g at step t (1-based), bias-corrected,
+    p moved by lr * m_hat / (sqrt(v_hat) + eps).  Returns (p, m, v)."""
+    p, g = np.asarray(p, np.float64), np.asarray(g, np.float64)
+    m = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    mh = m / (1.0 - beta1 ** t)
+    vh = v / (1.0 - beta2 ** t)
+    return p - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
 def flat(grads) -> np.ndarray:

@@ -489,6 +489,21 @@ __global__ void k_output(const float* __restrict__ yraw, int ldy, int batch, int
     y[(size_t)b * n_out + j] = sc[j] * yraw[(size_t)b * ldy + j] + c[j];
 }
 
+// public (unpadded) gradient layout <-> the padded device layout, through the
+// index map pidx[k] = padded position of public parameter k
+__global__ void k_pack(const float* __restrict__ g, const int* __restrict__ pidx, size_t n, float* __restrict__ out)
+{
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = g[pidx[k]];
+}
+
+__global__ void k_unpack_scaled(const float* __restrict__ in, const int* __restrict__ pidx, size_t n, float scale,
+                                float* __restrict__ g)
+{
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) g[pidx[k]] = scale * in[k];
+}
+
 __global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict__ pb, size_t n)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -532,6 +547,7 @@ struct lbib_mlp {
     size_t part_floats = 0;
     float* loss_part = nullptr;
     float* loss_dev = nullptr;
+    int* pidx = nullptr;                    // padded position of each public parameter
     int64_t t = 0;                          // Adam steps
     uint32_t* status = nullptr;             // bounded-wait error word of the tensor-core kernels
     bool tc = true;                         // forward products on tcgen05
@@ -798,6 +814,7 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
     MA(net->loss_part, (B + 3) / 4);
     MA(net->loss_dev, 1);
     MA(net->status, 1);
+    MA(net->pidx, net->ntrue);
 #undef MA
     if (d->cuda_stream) {
         net->stream = static_cast<cudaStream_t>(d->cuda_stream);
@@ -821,6 +838,17 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
             lbib_mlp_destroy(net);
             return mlp_fail(LBIB_ERR_INVALID_ARG, "out_scale must be finite and non-zero");
         }
+    {
+        std::vector<int> idx;
+        idx.reserve(net->ntrue);
+        for (int l = 0; l < net->L; ++l) {
+            for (int o = 0; o < net->out_true[l]; ++o)
+                for (int i = 0; i < net->in_true[l]; ++i) idx.push_back((int)(net->woff[l] + (size_t)o * net->in[l] + i));
+            for (int o = 0; o < net->out_true[l]; ++o) idx.push_back((int)(net->boff[l] + o));
+        }
+        if ((e = cudaMemcpy(net->pidx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "cudaMemcpy");
+    }
     if ((e = cudaMemcpy(net->cin, cin.data(), 32 * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(net->sin, sin.data(), 32 * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(net->cout, cout.data(), 64 * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -894,6 +922,51 @@ lbib_status lbib_mlp_train_step(lbib_mlp* net, const float* x, const float* t, i
     }
     if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, net->loss_dev, 4, cudaMemcpyDeviceToDevice, net->stream);
     if (e != cudaSuccess) return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_train_step: ") + cudaGetErrorString(e));
+    return LBIB_OK;
+}
+
+lbib_status lbib_mlp_backward(lbib_mlp* net, const float* x, const float* t, int32_t batch, float* grad, size_t n,
+                              float* loss)
+{
+    if (!net || !x || !t || !grad) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
+    if (n < net->ntrue) return mlp_fail(LBIB_ERR_INVALID_ARG, "buffer smaller than the parameter count");
+    if (batch < 1 || batch > net->max_batch) return mlp_fail(LBIB_ERR_INVALID_ARG, "batch outside 1 .. max_batch");
+    Guard guard(net->device);
+    cudaError_t e = prep_and_loss(net, x, t, batch);
+    if (e == cudaSuccess) e = backward_core(net, batch);
+    if (e == cudaSuccess) {
+        k_pack<<<(unsigned)((net->ntrue + 255) / 256), 256, 0, net->stream>>>(net->g, net->pidx, net->ntrue, grad);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, net->loss_dev, 4, cudaMemcpyDeviceToDevice, net->stream);
+    if (e != cudaSuccess) return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_backward: ") + cudaGetErrorString(e));
+    return LBIB_OK;
+}
+
+lbib_status lbib_mlp_apply_gradient(lbib_mlp* net, const float* grad, size_t n, float scale, float lr)
+{
+    if (!net || !grad) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
+    if (n < net->ntrue) return mlp_fail(LBIB_ERR_INVALID_ARG, "buffer smaller than the parameter count");
+    if (!std::isfinite(scale)) return mlp_fail(LBIB_ERR_INVALID_ARG, "scale must be finite");
+    if (!(lr > 0.f) || !std::isfinite(lr)) return mlp_fail(LBIB_ERR_INVALID_ARG, "lr must be positive");
+    Guard guard(net->device);
+    // padding entries of the gradient stay zero, so Adam leaves the padded weights at zero
+    cudaError_t e = cudaMemsetAsync(net->g, 0, net->nparam * 4, net->stream);
+    if (e == cudaSuccess) {
+        k_unpack_scaled<<<(unsigned)((net->ntrue + 255) / 256), 256, 0, net->stream>>>(grad, net->pidx, net->ntrue,
+                                                                                       scale, net->g);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        net->t += 1;
+        const float c1 = 1.0f - (float)std::pow(0.9, (double)net->t);
+        const float c2 = 1.0f - (float)std::pow(0.999, (double)net->t);
+        k_adam<<<(unsigned)((net->nparam + 255) / 256), 256, 0, net->stream>>>(net->p, net->g, net->m, net->v, net->pb,
+                                                                               net->nparam, lr, c1, c2);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess)
+        return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_apply_gradient: ") + cudaGetErrorString(e));
     return LBIB_OK;
 }
 

@@ -110,6 +110,8 @@ _SIGS = {
     "lbib_mlp_forward": [_P, _P, ctypes.c_int32, _P],
     "lbib_mlp_train_step": [_P, _P, _P, ctypes.c_int32, ctypes.c_float, _P],
     "lbib_mlp_gradients": [_P, _P, _P, ctypes.c_int32, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_float)],
+    "lbib_mlp_backward": [_P, _P, _P, ctypes.c_int32, _P, ctypes.c_size_t, _P],
+    "lbib_mlp_apply_gradient": [_P, _P, ctypes.c_size_t, ctypes.c_float, ctypes.c_float],
     "lbib_mlp_param_count": [_P, ctypes.POINTER(ctypes.c_size_t)],
     "lbib_mlp_get_params": [_P, _P, ctypes.c_size_t],
     "lbib_mlp_set_params": [_P, _P, ctypes.c_size_t],
@@ -460,6 +462,17 @@ class Mlp:
         self._c(self.lib.lbib_mlp_gradients(self.net, ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr), int(batch),
                                             _vp(g), g.size, ctypes.byref(loss)))
         return g, loss.value
+
+    def backward(self, x_ptr: int, t_ptr: int, batch: int, grad_ptr: int, n: int, loss_ptr: Optional[int] = None):
+        """Gradient of the batch loss into the device array at grad_ptr (n floats), no update."""
+        self._c(self.lib.lbib_mlp_backward(self.net, ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr), int(batch),
+                                           ctypes.c_void_p(grad_ptr), int(n),
+                                           ctypes.c_void_p(loss_ptr) if loss_ptr else None))
+
+    def apply_gradient(self, grad_ptr: int, n: int, scale: float, lr: float):
+        """One Adam step with scale * the device gradient at grad_ptr."""
+        self._c(self.lib.lbib_mlp_apply_gradient(self.net, ctypes.c_void_p(grad_ptr), int(n), float(scale),
+                                                 float(lr)))
 
     def get_params(self):
         p = np.zeros(self.param_count(), np.float32)

@@ -7,7 +7,9 @@ out inputs and drives the C ABI):
   * the parameter space and its sampling (``Point``, ``sample_points``);
   * the capillary each point runs in (``capillary_for``);
   * trajectory generation with batched solver contexts (``generate``);
-  * training of ``lbib.Mlp`` on the trajectories (``train``);
+  * training of ``lbib.Mlp`` on the trajectories (``train``), on one GPU or
+    data-parallel over several (``data_parallel_step``: shard gradients summed
+    by an all-reduce);
   * ``Surrogate.predict``: the network inside the hull, the solver outside.
 
 Training geometry (a reading; the paper's Table 1 is missing): H = 40 nodes,
@@ -155,6 +157,7 @@ class Trained:
     out_scale: np.ndarray
     t_star_max: float
     losses: List[float]
+    stream: object = None  # torch stream the network enqueues on
 
 
 def normalisation(X: np.ndarray, Y: np.ndarray):
@@ -168,36 +171,77 @@ def normalisation(X: np.ndarray, Y: np.ndarray):
             out_scale.astype(np.float32))
 
 
+def _net_stream():
+    """The torch stream the library's calls are enqueued on: the current one,
+    or a new side stream when the current one is the legacy default stream
+    (handle 0, which the library would replace by a private, unordered one)."""
+    import torch
+
+    st = torch.cuda.current_stream()
+    return st if st.cuda_stream else torch.cuda.Stream()
+
+
+def data_parallel_step(net, xb, yb, grad, loss, lr: float, rank: int = 0, world: int = 1, group=None) -> None:
+    """One Adam step of ``net`` on the global batch (xb, yb), data-parallel over
+    `world` ranks (include/lbib_mlp.h): rank r takes rows [r b, (r + 1) b) with
+    b = len(xb) / world, computes its shard's gradient into ``grad`` (float32
+    tensor of param_count values on the network's device) and its loss into
+    ``loss``, the gradients are summed across ranks (all-reduce over `group`),
+    and every rank applies 1 / world times the sum, so the copies stay equal.
+    All tensors live on the stream the network enqueues on."""
+    B = int(xb.shape[0])
+    if B % world:
+        raise ValueError("the global batch must split into equal shards")
+    b = B // world
+    xs = xb[rank * b:(rank + 1) * b].contiguous()
+    ys = yb[rank * b:(rank + 1) * b].contiguous()
+    net.backward(xs.data_ptr(), ys.data_ptr(), b, grad.data_ptr(), grad.numel(), loss.data_ptr())
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.all_reduce(grad, group=group)
+    net.apply_gradient(grad.data_ptr(), grad.numel(), 1.0 / world, lr)
+
+
 def train(X: np.ndarray, Y: np.ndarray, steps: int = 3000, batch: int = 8192, lr: float = 2e-3, seed: int = 0,
-          device: int = 0, width: int = 256, n_hidden: int = 3, log=None) -> Trained:
+          device: int = 0, width: int = 256, n_hidden: int = 3, log=None, rank: int = 0, world: int = 1,
+          group=None) -> Trained:
     """Adam on minibatches drawn from (X, Y) by the library's kernels;
-    cosine decay of the step size."""
+    cosine decay of the step size.  With world > 1 (one process per GPU,
+    torch.distributed initialised) every rank draws the same global batches
+    (same seed) and trains on its shard of each (``data_parallel_step``); the
+    networks start from the same seed and stay identical."""
     import torch
 
     torch.cuda.set_device(device)
-    st = torch.cuda.current_stream()
+    st = _net_stream()
     norm = normalisation(X, Y)
-    net = lbib.Mlp(X.shape[1], Y.shape[1], width=width, n_hidden=n_hidden, max_batch=max(batch, 65536),
-                   device=device, stream=st.cuda_stream if st.cuda_stream else None, seed=seed,
-                   in_shift=norm[0], in_scale=norm[1], out_shift=norm[2], out_scale=norm[3])
-    Xd = torch.as_tensor(X, dtype=torch.float32).cuda()
-    Yd = torch.as_tensor(Y, dtype=torch.float32).cuda()
-    g = torch.Generator(device="cuda")
-    g.manual_seed(seed)
-    loss = torch.zeros(1, device="cuda")
-    losses = []
-    for k in range(steps):
-        idx = torch.randint(0, X.shape[0], (batch,), device="cuda", generator=g)
-        xb, yb = Xd[idx].contiguous(), Yd[idx].contiguous()
-        eta = lr * 0.5 * (1.0 + math.cos(math.pi * k / steps))
-        net.train_step(xb.data_ptr(), yb.data_ptr(), batch, max(eta, lr * 1e-3), loss.data_ptr())
-        if k % 100 == 0 or k == steps - 1:
-            torch.cuda.synchronize()
-            losses.append(float(loss.item()))
-            if log:
-                log(f"step {k}: loss {losses[-1]:.4e}")
-    torch.cuda.synchronize()
-    return Trained(net, *norm, t_star_max=float(X[:, -1].max()), losses=losses)
+    with torch.cuda.stream(st):
+        net = lbib.Mlp(X.shape[1], Y.shape[1], width=width, n_hidden=n_hidden, max_batch=max(batch, 65536),
+                       device=device, stream=st.cuda_stream, seed=seed,
+                       in_shift=norm[0], in_scale=norm[1], out_shift=norm[2], out_scale=norm[3])
+        Xd = torch.as_tensor(X, dtype=torch.float32).cuda()
+        Yd = torch.as_tensor(Y, dtype=torch.float32).cuda()
+        g = torch.Generator(device="cuda")
+        g.manual_seed(seed)
+        loss = torch.zeros(1, device="cuda")
+        grad = torch.zeros(net.param_count(), device="cuda") if world > 1 else None
+        losses = []
+        for k in range(steps):
+            idx = torch.randint(0, X.shape[0], (batch,), device="cuda", generator=g)
+            xb, yb = Xd[idx].contiguous(), Yd[idx].contiguous()
+            eta = max(lr * 0.5 * (1.0 + math.cos(math.pi * k / steps)), lr * 1e-3)
+            if world > 1:
+                data_parallel_step(net, xb, yb, grad, loss, eta, rank, world, group)
+            else:
+                net.train_step(xb.data_ptr(), yb.data_ptr(), batch, eta, loss.data_ptr())
+            if k % 100 == 0 or k == steps - 1:
+                st.synchronize()
+                losses.append(float(loss.item()))
+                if log:
+                    log(f"step {k}: loss {losses[-1]:.4e}")
+        st.synchronize()
+    return Trained(net, *norm, t_star_max=float(X[:, -1].max()), losses=losses, stream=st)
 
 
 def predict_network(tr: Trained, X: np.ndarray) -> np.ndarray:
@@ -205,13 +249,15 @@ def predict_network(tr: Trained, X: np.ndarray) -> np.ndarray:
     import torch
 
     out = np.zeros((X.shape[0], tr.net.n_out), np.float32)
-    Xd = torch.as_tensor(X, dtype=torch.float32).cuda()
-    Yd = torch.zeros(X.shape[0], tr.net.n_out, device="cuda")
-    for b0 in range(0, X.shape[0], 65536):
-        n = min(65536, X.shape[0] - b0)
-        tr.net.forward(Xd[b0:].data_ptr(), n, Yd[b0:].data_ptr())
-    torch.cuda.synchronize()
-    out[:] = Yd.cpu().numpy()
+    st = tr.stream if tr.stream is not None else torch.cuda.current_stream()
+    with torch.cuda.stream(st):
+        Xd = torch.as_tensor(X, dtype=torch.float32).cuda()
+        Yd = torch.zeros(X.shape[0], tr.net.n_out, device="cuda")
+        for b0 in range(0, X.shape[0], 65536):
+            n = min(65536, X.shape[0] - b0)
+            tr.net.forward(Xd[b0:].data_ptr(), n, Yd[b0:].data_ptr())
+        st.synchronize()
+        out[:] = Yd.cpu().numpy()
     return out
 
 

@@ -133,3 +133,52 @@ def test_params_roundtrip_and_invalid_arguments():
     with pytest.raises(lbib.LbibError):
         lbib.Mlp(7, 3, width=100)
     net.close()
+
+
+def test_data_parallel_calls():
+    """lbib_mlp_backward equals lbib_mlp_gradients bit for bit; backward + apply
+    (scale 1) equals train_step bit for bit; apply_gradient is the oracle's
+    Adam update on the FP32 masters; the mean of two shards' gradients is the
+    whole batch's (what the ranks of a data-parallel step exchange)."""
+    rng = np.random.default_rng(5)
+    norm = _norm(rng)
+    B = 2048
+    x = rng.uniform(-1, 1, (B, N_IN)).astype(np.float32)
+    t = rng.normal(0, 1, (B, N_OUT)).astype(np.float32)
+    xd, td = _dev(x), _dev(t)
+    a, b = _net(norm, seed=3), _net(norm, seed=3)
+    n = a.param_count()
+    grad = torch.zeros(n, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    a.backward(xd.data_ptr(), td.data_ptr(), B, grad.data_ptr(), n, loss.data_ptr())
+    g_host, l_host = a.gradients(xd.data_ptr(), td.data_ptr(), B)
+    torch.cuda.synchronize()
+    assert np.array_equal(grad.cpu().numpy(), g_host) and float(loss.item()) == l_host
+    # backward + apply(1) == train_step, two steps
+    for lr in (1e-3, 5e-4):
+        a.backward(xd.data_ptr(), td.data_ptr(), B, grad.data_ptr(), n, None)
+        a.apply_gradient(grad.data_ptr(), n, 1.0, lr)
+        b.train_step(xd.data_ptr(), td.data_ptr(), B, lr)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.get_params(), b.get_params())
+    # apply_gradient against the oracle's Adam on a fresh network (first step)
+    c = _net(norm, seed=4)
+    p0 = c.get_params().astype(np.float64)
+    gg = rng.normal(0, 1e-2, n).astype(np.float32)
+    gd = _dev(gg)
+    c.apply_gradient(gd.data_ptr(), n, 0.5, 1e-3)
+    p1, m1, v1 = omlp.adam_step(p0, 0.5 * gg.astype(np.float64), np.zeros(n), np.zeros(n), 1, 1e-3)
+    assert np.abs(c.get_params() - p1).max() < 1e-6
+    # shard gradients: mean of two halves == whole batch (bf16 roundings differ slightly)
+    d = _net(norm, seed=6)
+    g1, g2 = torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+    d.backward(xd[: B // 2].data_ptr(), td[: B // 2].data_ptr(), B // 2, g1.data_ptr(), n, None)
+    d.backward(xd[B // 2:].data_ptr(), td[B // 2:].data_ptr(), B // 2, g2.data_ptr(), n, None)
+    d.backward(xd.data_ptr(), td.data_ptr(), B, grad.data_ptr(), n, None)
+    torch.cuda.synchronize()
+    assert _rel(0.5 * (g1 + g2).cpu().numpy(), grad.cpu().numpy().astype(np.float64)) < 1e-2
+    for bad in (lambda: a.backward(xd.data_ptr(), td.data_ptr(), B, grad.data_ptr(), n - 1, None),
+                lambda: a.apply_gradient(grad.data_ptr(), n, float("nan"), 1e-3),
+                lambda: a.apply_gradient(grad.data_ptr(), n, 1.0, 0.0)):
+        with pytest.raises(lbib.LbibError):
+            bad()

@@ -75,3 +75,29 @@ def test_quantized_oracle_stays_near_the_exact_one():
     assert abs(lq - l64) <= 0.05 * l64
     f64, fq = mlp.flat(g64), mlp.flat(gq)
     assert np.linalg.norm(fq - f64) <= 0.05 * np.linalg.norm(f64)
+
+
+def test_adam_closed_forms():
+    """Adam's bias correction makes the first step, and every step under a
+    constant gradient, move each parameter by lr g / (|g| + eps): lr against
+    the gradient's sign (Kingma & Ba 2015, Sec. 2.1: the effective step is
+    bounded by the step size and equals it in these cases)."""
+    rng = np.random.default_rng(3)
+    p0 = rng.normal(0, 1, 50)
+    g = rng.normal(0, 1, 50)
+    g[0] = 0.0
+    lr = 1e-3
+    m = v = np.zeros(50)
+    p1, m, v = mlp.adam_step(p0, g, m, v, 1, lr)
+    want = lr * g / (np.abs(g) + 1e-8)
+    assert np.abs((p0 - p1) - want).max() < 1e-15
+    assert p1[0] == p0[0]  # zero gradient, zero moments: no move
+    # a constant gradient keeps m_hat = g and v_hat = g^2 at every step
+    p = p1
+    for t in range(2, 40):
+        pn, m, v = mlp.adam_step(p, g, m, v, t, lr)
+        assert np.abs((p - pn) - want).max() < 1e-12, t
+        p = pn
+    # steps scale with lr and not with the gradient's magnitude
+    q1, _, _ = mlp.adam_step(p0, 1e3 * g, np.zeros(50), np.zeros(50), 1, 2 * lr)
+    assert np.abs((p0 - q1) - 2 * lr * g / (np.abs(g) + 1e-11)).max() < 1e-14
