@@ -28,6 +28,7 @@ _lib = None
 BC_INLET_OUTLET, BC_PERIODIC_FORCE = 0, 1
 CELL, PARTICLE = 0, 1
 DEFORMABLE, RIGID, FIXED = 0, 1, 2
+TRANSFER_PESKIN, TRANSFER_MLS = 0, 1
 
 # order of the per-vertex arrays exposed by orc_get_body
 BODY_FIELDS = (
@@ -71,8 +72,9 @@ def _load():
             "orc_stream_bc": (None, [I, I, I, D, D, P, P]),
             "orc_phi": (D, [D]),
             "orc_dphi": (D, [D]),
-            "orc_interp": (D, [I, I, P, D, D, P, P, P, I]),
-            "orc_spread": (None, [I, I, I, P, P, P, P, P, P, P]),
+            "orc_mls_weight": (D, [D]),
+            "orc_interp": (D, [I, I, P, D, D, P, P, P, I, I]),
+            "orc_spread": (None, [I, I, I, P, P, P, P, P, P, P, I]),
             "orc_philox4x32_10": (None, [P, P, P]),
             "orc_bond_uniform": (D, [U64, I64, ctypes.c_uint32]),
             "orc_polygon": (None, [I, P, P, P]),
@@ -83,6 +85,7 @@ def _load():
             "orc_create": (P, [I, I, D, D, D, I, D, D, U64]),
             "orc_destroy": (None, [P]),
             "orc_set_repulsion_cutoff": (None, [P, D]),
+            "orc_set_transfer": (I, [P, I]),
             "orc_add_body": (I, [P, I, I, I, P, P, D, D, D, D]),
             "orc_set_adhesion": (I, [P, I, I, D, D, D, D, D, D]),
             "orc_set_fpost": (None, [P, P]),
@@ -157,21 +160,27 @@ def dphi(r):
     return _load().orc_dphi(float(r))
 
 
-def interp(field, X, Y, renorm=False):
-    """(W, value, d/dX, d/dY) of the Peskin interpolant: velocity-type
-    (stencil truncated at the walls) or, with renorm, density-type."""
+def mls_weight(r):
+    return _load().orc_mls_weight(float(r))
+
+
+def interp(field, X, Y, renorm=False, kind=TRANSFER_PESKIN):
+    """(W, value, d/dX, d/dY) of the interpolant: Peskin velocity-type
+    (stencil truncated at the walls) or, with renorm, density-type; or, with
+    kind=TRANSFER_MLS, the moving-least-squares fit (W = the sum of its shape
+    functions, gradients its linear coefficients)."""
     field = _f64(field)
     ny, nx = field.shape
     v = ctypes.c_double(); gx = ctypes.c_double(); gy = ctypes.c_double()
     W = _load().orc_interp(nx, ny, _p(field), float(X), float(Y), ctypes.byref(v),
-                           ctypes.byref(gx), ctypes.byref(gy), int(bool(renorm)))
+                           ctypes.byref(gx), ctypes.byref(gy), int(bool(renorm)), int(kind))
     return W, v.value, gx.value, gy.value
 
 
-def spread(nx, ny, X, Y, Fx, Fy, ds):
+def spread(nx, ny, X, Y, Fx, Fy, ds, kind=TRANSFER_PESKIN):
     X, Y, Fx, Fy, ds = map(_f64, (X, Y, Fx, Fy, ds))
     ox = np.zeros((ny, nx)); oy = np.zeros((ny, nx))
-    _load().orc_spread(nx, ny, len(X), _p(X), _p(Y), _p(Fx), _p(Fy), _p(ds), _p(ox), _p(oy))
+    _load().orc_spread(nx, ny, len(X), _p(X), _p(Y), _p(Fx), _p(Fy), _p(ds), _p(ox), _p(oy), int(kind))
     return ox, oy
 
 
@@ -256,6 +265,10 @@ class OracleSim:
 
     def set_repulsion_cutoff(self, d):
         self._lib.orc_set_repulsion_cutoff(self._h, float(d))
+
+    def set_transfer(self, kind):
+        if self._lib.orc_set_transfer(self._h, int(kind)) != 0:
+            raise ValueError("unknown transfer kernel")
 
     def add_body(self, kind, motion, xy, xy_ref=None, ca=1e-3, beta=0.0, ka=1.0, density_ratio=1.0):
         xy = _f64(np.asarray(xy).reshape(-1))

@@ -40,6 +40,12 @@
  *     sum) and absorb the share of a spread force that falls on them.  Density
  *     has no wall value: its weights are renormalised over the fluid nodes.
  *     Gradients are the exact derivatives of these interpolants.
+ *   - The alternative transfer (orc_set_transfer): the moving-least-squares
+ *     reconstruction of Vanella and Balaras (2009) that Sec. 2.2 cites, with
+ *     a linear basis and the cubic-spline weight of support half-width 2 (the
+ *     same 4 x 4 stencil); stencil nodes outside the lattice are left out of
+ *     the fit, gradients are the fit's linear coefficients, and spreading uses
+ *     the same shape functions (the adjoint).
  *   - Direct forcing: F_L = rho (U_struct - U*) / dt at the new element
  *     centroids, U* and rho interpolated from the moments of step 2, spread
  *     with weight ds = element length.  A marker closer than half a spacing
@@ -70,6 +76,9 @@
 #define ORC_MAX_BODIES 16
 
 enum { ORC_BC_INLET_OUTLET = 0, ORC_BC_PERIODIC_FORCE = 1 };
+/* Eulerian-Lagrangian transfer kernel: Peskin's 4-point delta (the default
+ * reading) or the moving-least-squares reconstruction the paper cites. */
+enum { ORC_TRANSFER_PESKIN = 0, ORC_TRANSFER_MLS = 1 };
 enum { ORC_CELL = 0, ORC_PARTICLE = 1 };
 enum { ORC_DEFORMABLE = 0, ORC_RIGID = 1, ORC_FIXED = 2 };
 
@@ -227,6 +236,101 @@ double orc_dphi(double r)
     return s * d;
 }
 
+/* ------------------------------------------ moving least squares (MLS) */
+
+/* MLS weight along one direction: the cubic spline of |r| / 2, so its
+ * support covers the same 4 x 4 nodes around a point as the Peskin stencil.
+ * Values 2/3 at r = 0, 1/6 at |r| = 1, 0 from |r| = 2 on. */
+double orc_mls_weight(double r)
+{
+    double q = fabs(r) / 2.0;
+    if (q <= 0.5) return 2.0 / 3.0 - 4.0 * q * q + 4.0 * q * q * q;
+    if (q <= 1.0) return (4.0 / 3.0) * (1.0 - q) * (1.0 - q) * (1.0 - q);
+    return 0.0;
+}
+
+/* The moving-least-squares reconstruction cited in Sec. 2.2 (Vanella and
+ * Balaras 2009), with the linear basis p(x, y) = (1, x - X, y - Y) about the
+ * point (X, Y) and weights W_j = w(x_j - X) w(y_j - Y) over the 4 x 4 stencil
+ * nodes that lie inside the lattice: the weighted least-squares fit of a
+ * nodal field f has coefficients a = A^{-1} sum_j W_j p_j f_j with
+ * A = sum_j W_j p_j p_j^T; a_0 is the reconstructed value at (X, Y) and
+ * (a_1, a_2) its gradient.  Writes A^{-1} (row-major 3 x 3) to inv; returns 0
+ * when A is singular (the stencil holds fewer than two weighted columns or
+ * rows), else 1. */
+static int mls_inverse(int nx, int ny, double X, double Y, double inv[9])
+{
+    double A[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int i0 = (int)floor(X) - 1, j0 = (int)floor(Y - 0.5) - 1;
+    for (int j = j0; j <= j0 + 3; ++j) {
+        if (j < 0 || j >= ny) continue;
+        for (int i = i0; i <= i0 + 3; ++i) {
+            if (i < 0 || i >= nx) continue;
+            double W = orc_mls_weight(i - X) * orc_mls_weight(j + 0.5 - Y);
+            double pv[3] = {1.0, i - X, j + 0.5 - Y};
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) A[3 * r + c] += W * pv[r] * pv[c];
+        }
+    }
+    /* inverse by cofactors (A is symmetric) */
+    double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+    double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    if (!(fabs(det) > 1e-12 * A[0] * A[0] * A[0])) return 0;
+    inv[0] = c00 / det;
+    inv[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+    inv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+    inv[3] = c01 / det;
+    inv[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+    inv[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+    inv[6] = c02 / det;
+    inv[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+    inv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+    return 1;
+}
+
+/* MLS shape functions at (X, Y) of the stencil node (i, j): phi[0] weights the
+ * nodal values into the reconstruction, phi[1] and phi[2] into its x- and
+ * y-derivatives: phi[k] = W_j (A^{-1} p_j)_k. */
+static void mls_shape(const double inv[9], double X, double Y, int i, int j, double phi[3])
+{
+    double W = orc_mls_weight(i - X) * orc_mls_weight(j + 0.5 - Y);
+    double pv[3] = {1.0, i - X, j + 0.5 - Y};
+    for (int k = 0; k < 3; ++k) phi[k] = W * (inv[3 * k] * pv[0] + inv[3 * k + 1] * pv[1] + inv[3 * k + 2] * pv[2]);
+}
+
+/* MLS interpolation of a nodal field at (X, Y): *val the reconstruction, *gx,
+ * *gy its gradient coefficients; returns the sum of the value's shape
+ * functions (one up to rounding, the linear basis holds the constant), 0 if
+ * the stencil is degenerate.  Walls and instance ends truncate the stencil;
+ * the fit uses the nodes that remain, so no renormalisation is needed. */
+static double interp_mls(int nx, int ny, const double* fld, double X, double Y, double* val, double* gx, double* gy)
+{
+    double inv[9];
+    if (val) *val = 0.0;
+    if (gx) *gx = 0.0;
+    if (gy) *gy = 0.0;
+    if (!mls_inverse(nx, ny, X, Y, inv)) return 0.0;
+    double S = 0.0, a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    int i0 = (int)floor(X) - 1, j0 = (int)floor(Y - 0.5) - 1;
+    for (int j = j0; j <= j0 + 3; ++j) {
+        if (j < 0 || j >= ny) continue;
+        for (int i = i0; i <= i0 + 3; ++i) {
+            if (i < 0 || i >= nx) continue;
+            double phi[3];
+            mls_shape(inv, X, Y, i, j, phi);
+            double u = fld[(size_t)j * nx + i];
+            S += phi[0];
+            a0 += phi[0] * u;
+            a1 += phi[1] * u;
+            a2 += phi[2] * u;
+        }
+    }
+    if (val) *val = a0;
+    if (gx) *gx = a1;
+    if (gy) *gy = a2;
+    return S;
+}
+
 /* Interpolation of a nodal field at (X, Y) with the 4 x 4 Peskin stencil.
  * Nodes beyond the walls are wall nodes: for a velocity (renorm = 0) they hold
  * the wall's zero velocity, so the stencil is simply truncated; a density
@@ -268,26 +372,45 @@ static double interp_field(int nx, int ny, const double* fld, double X, double Y
     return W;
 }
 
-/* Stand-alone interpolation on a caller field (for the pins). */
-double orc_interp(int nx, int ny, const double* fld, double X, double Y, double* val, double* gx, double* gy,
-                  int renorm)
+/* Interpolation with the transfer kernel `kind` (ORC_TRANSFER_*). */
+static double interp_kind(int kind, int nx, int ny, const double* fld, double X, double Y, double* val, double* gx,
+                          double* gy, int renorm)
 {
+    if (kind == ORC_TRANSFER_MLS) return interp_mls(nx, ny, fld, X, Y, val, gx, gy);
     return interp_field(nx, ny, fld, X, Y, val, gx, gy, renorm);
 }
 
+/* Stand-alone interpolation on a caller field (for the pins). */
+double orc_interp(int nx, int ny, const double* fld, double X, double Y, double* val, double* gx, double* gy,
+                  int renorm, int kind)
+{
+    return interp_kind(kind, nx, ny, fld, X, Y, val, gx, gy, renorm);
+}
+
 /* Spreading of point forces (Fx, Fy) with weights ds onto a field with the
- * same truncated stencil (the adjoint of the velocity interpolation): the share
- * that would land on wall nodes is taken up by the wall. */
+ * same truncated stencil (the adjoint of the velocity interpolation).  Peskin:
+ * the share that would land on wall nodes is taken up by the wall.  MLS: the
+ * shape functions of the nodes inside the lattice sum to one, so the whole
+ * force reaches the fluid. */
 void orc_spread(int nx, int ny, int n, const double* X, const double* Y, const double* Fx, const double* Fy,
-                const double* ds, double* outx, double* outy)
+                const double* ds, double* outx, double* outy, int kind)
 {
     for (int m = 0; m < n; ++m) {
         int i0 = (int)floor(X[m]) - 1, j0 = (int)floor(Y[m] - 0.5) - 1;
+        double inv[9];
+        if (kind == ORC_TRANSFER_MLS && !mls_inverse(nx, ny, X[m], Y[m], inv)) continue;
         for (int j = j0; j <= j0 + 3; ++j) {
             if (j < 0 || j >= ny) continue;
             for (int i = i0; i <= i0 + 3; ++i) {
                 if (i < 0 || i >= nx) continue;
-                double w = orc_phi(X[m] - i) * orc_phi(Y[m] - (j + 0.5));
+                double w;
+                if (kind == ORC_TRANSFER_MLS) {
+                    double phi[3];
+                    mls_shape(inv, X[m], Y[m], i, j, phi);
+                    w = phi[0];
+                } else {
+                    w = orc_phi(X[m] - i) * orc_phi(Y[m] - (j + 0.5));
+                }
                 outx[(size_t)j * nx + i] += Fx[m] * ds[m] * w;
                 outy[(size_t)j * nx + i] += Fy[m] * ds[m] * w;
             }
@@ -491,7 +614,7 @@ typedef struct {
 } orc_body;
 
 typedef struct orc_sim {
-    int nx, ny, bc, nb, diverged;
+    int nx, ny, bc, nb, diverged, transfer;
     double tau, nu, umax, rho_out, gx, gy, dcut, probe;
     uint64_t seed;
     int64_t step;
@@ -570,6 +693,15 @@ void orc_destroy(orc_sim* s)
 }
 
 void orc_set_repulsion_cutoff(orc_sim* s, double d) { s->dcut = d; }
+
+/* Selects the transfer kernel (ORC_TRANSFER_*) of the interpolation and the
+ * spreading; returns -1 for an unknown kind. */
+int orc_set_transfer(orc_sim* s, int kind)
+{
+    if (kind != ORC_TRANSFER_PESKIN && kind != ORC_TRANSFER_MLS) return -1;
+    s->transfer = kind;
+    return 0;
+}
 
 /* Adds a closed counter-clockwise chain.  xy: interleaved (x0, y0, x1, ...);
  * xy_ref: stress-free shape or NULL.  k_s = rho nu u_max / Ca (Sec. 3.1),
@@ -767,10 +899,10 @@ static void body_traction(const orc_sim* s, const orc_body* b, const double* len
         if (py < 0.0) py = 0.0; /* a probe that would cross a wall stops at it */
         if (py > s->ny) py = (double)s->ny;
         double rho, u, v, ux, uy, vx, vy;
-        double W = interp_field(s->nx, s->ny, s->rho, px, py, &rho, NULL, NULL, 1);
+        double W = interp_kind(s->transfer, s->nx, s->ny, s->rho, px, py, &rho, NULL, NULL, 1);
         if (!(W > 0.0)) continue;
-        interp_field(s->nx, s->ny, s->ux, px, py, &u, &ux, &uy, 0);
-        interp_field(s->nx, s->ny, s->uy, px, py, &v, &vx, &vy, 0);
+        interp_kind(s->transfer, s->nx, s->ny, s->ux, px, py, &u, &ux, &uy, 0);
+        interp_kind(s->transfer, s->nx, s->ny, s->uy, px, py, &v, &vx, &vy, 0);
         double p = CS2 * rho - CS2 * 1.0;
         double mu = rho * s->nu;
         double txx = 2.0 * mu * ux, txy = mu * (uy + vx), tyy = 2.0 * mu * vy;
@@ -911,8 +1043,8 @@ void orc_step(orc_sim* s)
         chain_geometry(nv, b->x, b->y, len[bi], nlx[bi], nly[bi], nvx[bi], nvy[bi], th[bi]);
         /* tentative vertex velocity: fluid velocity at the vertex (Eq. 17) */
         for (int v = 0; v < nv; ++v) {
-            interp_field(nx, ny, s->ux, b->x[v], b->y[v], &b->uvx[v], NULL, NULL, 0);
-            interp_field(nx, ny, s->uy, b->x[v], b->y[v], &b->uvy[v], NULL, NULL, 0);
+            interp_kind(s->transfer, nx, ny, s->ux, b->x[v], b->y[v], &b->uvx[v], NULL, NULL, 0);
+            interp_kind(s->transfer, nx, ny, s->uy, b->x[v], b->y[v], &b->uvy[v], NULL, NULL, 0);
         }
     }
     for (int bi = 0; bi < nb; ++bi) {
@@ -1006,9 +1138,9 @@ void orc_step(orc_sim* s)
             double cx = 0.5 * (b->x[l] + b->x[w]), cy = 0.5 * (b->y[l] + b->y[w]);
             double usx = 0.5 * (b->vx[l] + b->vx[w]), usy = 0.5 * (b->vy[l] + b->vy[w]);
             double rho, ux, uy;
-            double W = interp_field(nx, ny, s->rho, cx, cy, &rho, NULL, NULL, 1);
-            interp_field(nx, ny, s->ux, cx, cy, &ux, NULL, NULL, 0);
-            interp_field(nx, ny, s->uy, cx, cy, &uy, NULL, NULL, 0);
+            double W = interp_kind(s->transfer, nx, ny, s->rho, cx, cy, &rho, NULL, NULL, 1);
+            interp_kind(s->transfer, nx, ny, s->ux, cx, cy, &ux, NULL, NULL, 0);
+            interp_kind(s->transfer, nx, ny, s->uy, cx, cy, &uy, NULL, NULL, 0);
             b->mx[l] = cx;
             b->my[l] = cy;
             b->mds[l] = hypot(b->x[w] - b->x[l], b->y[w] - b->y[l]);
@@ -1018,7 +1150,7 @@ void orc_step(orc_sim* s)
             b->mfx[l] = (W > 0.0 && !held) ? rho * (usx - ux) : 0.0;
             b->mfy[l] = (W > 0.0 && !held) ? rho * (usy - uy) : 0.0;
         }
-        orc_spread(nx, ny, nv, b->mx, b->my, b->mfx, b->mfy, b->mds, s->Fx, s->Fy);
+        orc_spread(nx, ny, nv, b->mx, b->my, b->mfx, b->mfy, b->mds, s->Fx, s->Fy, s->transfer);
         double poly[5];
         orc_polygon(nv, b->x, b->y, poly);
         b->area = poly[0];

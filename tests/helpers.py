@@ -8,6 +8,7 @@ import oracle
 def oracle_from(cap):
     s = oracle.OracleSim(cap.nx, cap.ny, tau=cap.tau, re=cap.re, rho_out=cap.rho_out, bc=cap.bc, g=cap.g,
                          seed=cap.seed)
+    s.set_transfer(getattr(cap, "transfer", 0))
     for b in cap.bodies:
         i = s.add_body(b.kind, b.motion, b.xy, b.xy_ref, b.ca, b.beta, b.ka, b.density_ratio)
         if b.adhesion is not None:
