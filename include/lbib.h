@@ -10,8 +10,9 @@
  *      halfway bounce-back walls and Zou-He inlet/outlet (Sec. 2.2, Sec. 3.1);
  *   2. moments with the half-force shift (Eqs. 5-6) and BGK collision with the
  *      Hermite equilibrium and Guo's forcing term (Eqs. 1, 2, 4);
- *   3. the Lagrangian update of every membrane from that velocity: Peskin
- *      interpolation (Sec. 2.2, Sec. 2.9), ligand-receptor kinetics and force
+ *   3. the Lagrangian update of every membrane from that velocity: Peskin or
+ *      moving-least-squares interpolation (Sec. 2.2, Sec. 2.9; lbib_transfer),
+ *      ligand-receptor kinetics and force
  *      (Sec. 2.5, Eq. 13), membrane forces (Eqs. 8, 10, 11), repulsion
  *      (Eq. 12), probe tractions (Eqs. 14-15), Verlet + BDF2 (Eqs. 17-18) or
  *      rigid BDF2 (Eq. 19);
@@ -68,6 +69,21 @@ typedef enum { LBIB_BC_INLET_OUTLET = 0, LBIB_BC_PERIODIC_FORCE = 1 } lbib_bc_mo
  * 1e-9 to 3 stay in binary16's normal range.  16-bit storage halves the
  * lattice's memory traffic (36 bytes per node update instead of 72). */
 typedef enum { LBIB_STORE_FP64 = 0, LBIB_STORE_FP32 = 1, LBIB_STORE_BF16 = 2, LBIB_STORE_FP16 = 3 } lbib_storage;
+/* Eulerian-Lagrangian transfer (interpolation of the fluid at the membrane
+ * and spreading of the direct force, Sec. 2.2), over the same 4 x 4 nodes
+ * around a point either way:
+ *   PESKIN: Peskin's 4-point discrete delta, phi(dx) phi(dy); stencil nodes
+ *     beyond a wall carry its zero velocity and absorb the force that falls
+ *     on them; density weights are renormalised over the fluid nodes;
+ *     gradients are the delta's exact derivatives.
+ *   MLS: the moving-least-squares reconstruction of Vanella and Balaras
+ *     (2009) that Sec. 2.2 cites: linear basis (1, x - X, y - Y), weights
+ *     w(dx) w(dy) with w the cubic spline of |r| / 2, fitted over the stencil
+ *     nodes inside the lattice (walls and instance ends truncate it, the fit
+ *     stays consistent: the shape functions sum to one and reproduce linear
+ *     fields); gradients are the fit's linear coefficients; spreading uses the
+ *     same shape functions, so the spread force is conserved at walls too. */
+typedef enum { LBIB_TRANSFER_PESKIN = 0, LBIB_TRANSFER_MLS = 1 } lbib_transfer;
 typedef enum { LBIB_CELL = 0, LBIB_PARTICLE = 1 } lbib_body_kind;
 typedef enum { LBIB_DEFORMABLE = 0, LBIB_RIGID = 1, LBIB_FIXED = 2 } lbib_motion;
 
@@ -87,6 +103,8 @@ typedef struct lbib_fluid_params {
     int32_t obs_capacity;/* observables ring-buffer records (0: 4096) */
     void* cuda_stream;   /* borrowed cudaStream_t to enqueue on, or NULL */
     uint64_t seed;       /* Philox key of the bond kinetics */
+    int32_t transfer;    /* lbib_transfer (0: Peskin) */
+    int32_t reserved;    /* 0 */
 } lbib_fluid_params;
 
 /* A closed membrane chain (Sec. 2.2-2.3); nv vertices joined by nv elements. */

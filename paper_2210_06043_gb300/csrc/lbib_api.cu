@@ -575,6 +575,8 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     if (!(P->re >= 0.0) || !(P->rho_out > 0.0)) return fail(nullptr, LBIB_ERR_INVALID_ARG, "re >= 0 and rho_out > 0");
     if (P->bc_mode != LBIB_BC_INLET_OUTLET && P->bc_mode != LBIB_BC_PERIODIC_FORCE)
         return fail(nullptr, LBIB_ERR_INVALID_ARG, "unknown bc_mode");
+    if (P->transfer != LBIB_TRANSFER_PESKIN && P->transfer != LBIB_TRANSFER_MLS)
+        return fail(nullptr, LBIB_ERR_INVALID_ARG, "unknown transfer kernel");
     if (P->storage != LBIB_STORE_FP64 && P->storage != LBIB_STORE_FP32 && P->storage != LBIB_STORE_BF16 &&
         P->storage != LBIB_STORE_FP16)
         return fail(nullptr, LBIB_ERR_INVALID_ARG, "unknown storage");
@@ -621,6 +623,7 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     L.nxp = L.ntx * TX;
     L.ntiles = L.ntx * L.nty;
     L.bc = P->bc_mode;
+    L.transfer = P->transfer;
     L.qstride = (int)qs;
     L.tau = P->tau;
     L.omega = 1.0 / P->tau;

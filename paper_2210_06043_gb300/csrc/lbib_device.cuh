@@ -70,6 +70,46 @@ __device__ __forceinline__ R peskin(R r)
     return R(0);
 }
 
+// ------------------------------------------ moving-least-squares transfer
+// Weight along one direction: the cubic spline of q = |r| / 2,
+// 2/3 - 4 q^2 + 4 q^3 on [0, 1/2], (4/3) (1 - q)^3 on (1/2, 1], zero beyond,
+// so its support is the 4 x 4 stencil of the Peskin kernel.
+template <typename R>
+__device__ __forceinline__ R mls_w(R r)
+{
+    const R q = fabs(r) * R(0.5);
+    if (q <= R(0.5)) return R(2.0 / 3.0) - R(4) * q * q + R(4) * q * q * q;
+    if (q < R(1)) {
+        const R t = R(1) - q;
+        return R(4.0 / 3.0) * t * t * t;
+    }
+    return R(0);
+}
+
+// Inverse of the MLS moment matrix A = sum_j W_j p_j p_j^T for the linear
+// basis p = (1, dx, dy) and separable weights W = wx(dx) wy(dy) over a
+// product stencil, from the 1-D moments a_k = sum wx dx^k, b_k = sum wy dy^k:
+// A = [[a0 b0, a1 b0, a0 b1], [a1 b0, a2 b0, a1 b1], [a0 b1, a1 b1, a0 b2]].
+// Row r of the inverse gives the shape functions W_j (inv_r . p_j) of the
+// value (r = 0) and of the x- and y-derivatives (r = 1, 2).  False when A is
+// singular (fewer than two weighted columns or rows).
+template <typename R>
+__device__ __forceinline__ bool mls_inverse(R a0, R a1, R a2, R b0, R b1, R b2, R inv[9])
+{
+    const R A0 = a0 * b0, A1 = a1 * b0, A2 = a0 * b1, A4 = a2 * b0, A5 = a1 * b1, A8 = a0 * b2;
+    const R c00 = A4 * A8 - A5 * A5, c01 = A5 * A2 - A1 * A8, c02 = A1 * A5 - A4 * A2;
+    const R det = A0 * c00 + A1 * c01 + A2 * c02;
+    if (!(fabs(det) > R(1e-6) * A0 * A0 * A0)) return false;
+    const R id = R(1) / det;
+    inv[0] = c00 * id;
+    inv[1] = inv[3] = c01 * id;
+    inv[2] = inv[6] = c02 * id;
+    inv[4] = (A0 * A8 - A2 * A2) * id;
+    inv[5] = inv[7] = (A2 * A1 - A0 * A5) * id;
+    inv[8] = (A0 * A4 - A1 * A1) * id;
+    return true;
+}
+
 // d phi / d r
 template <typename R>
 __device__ __forceinline__ R peskin_d(R r)

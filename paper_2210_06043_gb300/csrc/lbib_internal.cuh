@@ -67,6 +67,7 @@ struct Lattice {
     int nx, ny, nxp;          // nx: node columns of the whole batch; nxp: row pitch (multiple of TX)
     int ntx, nty, ntiles;     // tiles of the whole batch
     int bc;                   // lbib_bc_mode
+    int transfer;             // lbib_transfer
     int qstride;              // ny * nxp
     double tau, omega, nu, umax, rho_out, gx, gy;
     // the same parameters rounded to FP32 once on the host: FP32 kernels read

@@ -164,7 +164,9 @@ struct RowSums {
 // its instance (node columns [x0, x0 + nxi) of the lattice).  Indices are
 // clamped into the instance and the weights of nodes outside it zeroed, so a
 // lane's loads are independent and issued together.  All 32 lanes of the warp
-// must call this together.
+// must call this together.  With the MLS transfer the node weights are the
+// fit's shape functions (value and gradient) over the nodes inside the
+// instance and the lattice, and the density needs no renormalisation.
 template <typename R, bool GRAD, int K>
 __device__ __forceinline__ void sample_group(const Dev& d, const Spot<R>& sp, int32_t m, int r, int x0, int nxi,
                                              Sample<R>& o, uint32_t& miss)
@@ -174,6 +176,7 @@ __device__ __forceinline__ void sample_group(const Dev& d, const Spot<R>& sp, in
     const R* __restrict__ uy = static_cast<const R*>(d.uy);
     const R* __restrict__ dr = static_cast<const R*>(d.drho);
     constexpr int NR = 4 / K;  // rows per lane
+    const bool mls = (L.transfer == LBIB_TRANSFER_MLS);
     const int i0 = sp.ix - 1;
     int ic[4];
     R px[4], dpx[4];
@@ -184,9 +187,38 @@ __device__ __forceinline__ void sample_group(const Dev& d, const Spot<R>& sp, in
         ic[a] = x0 + min(max(i, 0), nxi - 1);
         const R rx = sp.ax + R(1 - a);  // X - i
         dpx[a] = R(0);
-        if (GRAD) peskin_both<R>(rx, px[a], dpx[a]);
+        if (mls) px[a] = mls_w<R>(rx);
+        else if (GRAD) peskin_both<R>(rx, px[a], dpx[a]);
         else px[a] = peskin<R>(rx);
         if (!vi) px[a] = dpx[a] = R(0);
+    }
+    // MLS: the fit's inverse moment matrix from the whole 4 x 4 stencil (every
+    // lane forms it from the same terms in the same order, whatever K)
+    R inv[9];
+    if (mls) {
+        R a0 = R(0), a1 = R(0), a2 = R(0), b0 = R(0), b1 = R(0), b2 = R(0);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const R dx = R(a - 1) - sp.ax;  // x_i - X
+            a0 += px[a];
+            a1 += px[a] * dx;
+            a2 += px[a] * dx * dx;
+        }
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+            const int j = sp.jy - 1 + rr;
+            const R dy = R(rr - 1) - sp.ay;  // y_j - Y
+            const R w = (j >= 0 && j < L.ny) ? mls_w<R>(dy) : R(0);
+            b0 += w;
+            b1 += w * dy;
+            b2 += w * dy * dy;
+        }
+        if (!mls_inverse<R>(a0, a1, a2, b0, b1, b2, inv)) {
+#pragma unroll
+            for (int a = 0; a < 4; ++a) px[a] = R(0);  // degenerate stencil: no sample (W = 0)
+#pragma unroll
+            for (int q = 0; q < 9; ++q) inv[q] = R(0);
+        }
     }
     int jc[NR];
     R py[NR], dpy[NR];
@@ -200,7 +232,8 @@ __device__ __forceinline__ void sample_group(const Dev& d, const Spot<R>& sp, in
         jc[k] = min(max(j, 0), L.ny - 1);
         const R ry = sp.ay + R(1 - rr);  // Y - (j + 1/2)
         dpy[k] = R(0);
-        if (GRAD) peskin_both<R>(ry, py[k], dpy[k]);
+        if (mls) py[k] = mls_w<R>(ry);
+        else if (GRAD) peskin_both<R>(ry, py[k], dpy[k]);
         else py[k] = peskin<R>(ry);
         if (!vj) py[k] = dpy[k] = R(0);
         // the row's nodes lie in at most two tiles: both must hold step m
@@ -222,16 +255,31 @@ __device__ __forceinline__ void sample_group(const Dev& d, const Spot<R>& sp, in
     for (int k = 0; k < NR; ++k) {
         RowSums<R, GRAD>& s = rs[k];
         s.W = s.u = s.v = s.r = s.ux = s.uy = s.vx = s.vy = R(0);
+        const R dy = R(r + K * k - 1) - sp.ay;  // y_j - Y (MLS)
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            const R w = mul_rn<R>(px[a], py[k]);
+            R w, wx = R(0), wy = R(0);
+            if (mls) {
+                // shape functions W_j (inv_r . (1, dx, dy)) of the value and the gradient
+                const R base = mul_rn<R>(px[a], py[k]), dx = R(a - 1) - sp.ax;
+                w = base * (inv[0] + inv[1] * dx + inv[2] * dy);
+                if (GRAD) {
+                    wx = base * (inv[3] + inv[4] * dx + inv[5] * dy);
+                    wy = base * (inv[6] + inv[7] * dx + inv[8] * dy);
+                }
+            } else {
+                w = mul_rn<R>(px[a], py[k]);
+                if (GRAD) {
+                    wx = mul_rn<R>(dpx[a], py[k]);
+                    wy = mul_rn<R>(px[a], dpy[k]);
+                }
+            }
             const int q = 4 * k + a;
             s.W += w;
             s.u = fma(a_u[q], w, s.u);
             s.v = fma(a_v[q], w, s.v);
             s.r = fma(a_r[q], w, s.r);
             if (GRAD) {
-                const R wx = mul_rn<R>(dpx[a], py[k]), wy = mul_rn<R>(px[a], dpy[k]);
                 s.ux = fma(a_u[q], wx, s.ux);
                 s.uy = fma(a_u[q], wy, s.uy);
                 s.vx = fma(a_v[q], wx, s.vx);
@@ -270,7 +318,9 @@ __device__ __forceinline__ void sample_group(const Dev& d, const Spot<R>& sp, in
     } else {
         o.ux = o.uy = o.vx = o.vy = R(0);
     }
-    o.drho = (t.W > R(0)) ? t.r / t.W : R(0);
+    // Peskin: density weights renormalised over the fluid nodes; MLS: the fit
+    // over the fluid nodes is already consistent
+    o.drho = mls ? t.r : ((t.W > R(0)) ? t.r / t.W : R(0));
 }
 
 // Tiles overlapping the node box [i0, i1] x [j0, j1]: enumerates at most 8 of

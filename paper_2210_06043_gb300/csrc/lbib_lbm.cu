@@ -197,7 +197,7 @@ constexpr int NEAR_STAGE = 64;    // markers a warp stages per pass
 // order) and staged in passes of NEAR_STAGE markers with their stencil
 // weights; each node then adds the forces of the staged markers whose 4 x 4
 // stencil holds it, in that order.  Warp-local throughout: no block barrier.
-template <typename S, typename R>
+template <typename S, typename R, bool MLS>
 __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near(Dev d, int p)
 {
     const Lattice& L = d.L;
@@ -220,6 +220,8 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near(Dev d, int p)
     // a = 0..3, over the marker's columns / rows, and F ds
     __shared__ int s_ix[NEAR_WARPS][NEAR_STAGE], s_iy[NEAR_WARPS][NEAR_STAGE];
     __shared__ R s_wx[NEAR_WARPS][NEAR_STAGE][4], s_wy[NEAR_WARPS][NEAR_STAGE][4];
+    // MLS only: node weight = s_wx[a] s_wy[b] + s_ax[a] s_cy[b]
+    __shared__ R s_ax[NEAR_WARPS][MLS ? NEAR_STAGE : 1][4], s_cy[NEAR_WARPS][MLS ? NEAR_STAGE : 1][4];
     __shared__ R s_Fx[NEAR_WARPS][NEAR_STAGE], s_Fy[NEAR_WARPS][NEAR_STAGE];
     const R gx = lat_param<R>(L.gx, L.gx_f), gy = lat_param<R>(L.gy, L.gy_f);
     const R omega = lat_param<R>(L.omega, L.omega_f);
@@ -279,30 +281,78 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near(Dev d, int p)
                         s_ix[wid][pos] = mki[id];
                         s_iy[wid][pos] = mki[nm + id];
                         const R fx = mkf[id], fy = mkf[nm + id];
+                        if constexpr (MLS) {
+                            // MLS shape function of node (a, b) at the marker:
+                            // wx_a wy_b (c0 + c1 dx_a + c2 dy_b), the fit over the
+                            // stencil nodes inside the instance and the lattice
+                            const int il = s_ix[wid][pos] - ci.x - 1, jl = s_iy[wid][pos] - 1;
+                            R wxv[4], wyv[4], a0 = R(0), a1 = R(0), a2 = R(0), b0 = R(0), b1 = R(0), b2 = R(0);
 #pragma unroll
-                        for (int a = 0; a < 4; ++a) {
-                            // X - (ix - 1 + a) = 1 - a + frac, as the node-side difference below
-                            s_wx[wid][pos][a] = peskin<R>(R(1 - a) + fx);
-                            s_wy[wid][pos][a] = peskin<R>(R(1 - a) + fy);
+                            for (int a = 0; a < 4; ++a) {
+                                const R dx = R(a - 1) - fx, dy = R(a - 1) - fy;
+                                wxv[a] = (il + a >= 0 && il + a < ci.y) ? mls_w<R>(dx) : R(0);
+                                wyv[a] = (jl + a >= 0 && jl + a < L.ny) ? mls_w<R>(dy) : R(0);
+                                a0 += wxv[a];
+                                a1 += wxv[a] * dx;
+                                a2 += wxv[a] * dx * dx;
+                                b0 += wyv[a];
+                                b1 += wyv[a] * dy;
+                                b2 += wyv[a] * dy * dy;
+                            }
+                            R inv[9];
+                            const bool ok = mls_inverse<R>(a0, a1, a2, b0, b1, b2, inv);
+                            const R c0 = ok ? inv[0] : R(0), c1 = ok ? inv[1] : R(0), c2 = ok ? inv[2] : R(0);
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) {
+                                s_wx[wid][pos][a] = wxv[a] * (c0 + c1 * (R(a - 1) - fx));
+                                s_ax[wid][pos][a] = wxv[a];
+                                s_wy[wid][pos][a] = wyv[a];
+                                s_cy[wid][pos][a] = wyv[a] * c2 * (R(a - 1) - fy);
+                            }
+                        } else {
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) {
+                                // X - (ix - 1 + a) = 1 - a + frac, as the node-side difference below
+                                s_wx[wid][pos][a] = peskin<R>(R(1 - a) + fx);
+                                s_wy[wid][pos][a] = peskin<R>(R(1 - a) + fy);
+                            }
                         }
                         s_Fx[wid][pos] = mkf[2 * nm + id];
                         s_Fy[wid][pos] = mkf[3 * nm + id];
                     }
                 }
                 __syncwarp();
-                for (int q = 0; q < ns; ++q) {
-                    // node (x, y) in the marker's 4 x 4 stencil [ix - 1, ix + 2] x [iy - 1, iy + 2]
-                    const int a = x - s_ix[wid][q] + 1;
-                    if ((unsigned)a >= 4u) continue;
-                    const R wxa = s_wx[wid][q][a], Fq = s_Fx[wid][q], Gq = s_Fy[wid][q];
-                    const int b0 = y0 - s_iy[wid][q] + 1;
+                if constexpr (MLS) {
+                    for (int q = 0; q < ns; ++q) {
+                        const int a = x - s_ix[wid][q] + 1;
+                        if ((unsigned)a >= 4u) continue;
+                        const R wxa = s_wx[wid][q][a], axa = s_ax[wid][q][a], Fq = s_Fx[wid][q], Gq = s_Fy[wid][q];
+                        const int b0 = y0 - s_iy[wid][q] + 1;
 #pragma unroll
-                    for (int r = 0; r < TY; ++r) {
-                        const int b = b0 + r;
-                        if ((unsigned)b < 4u) {
-                            const R wt = wxa * s_wy[wid][q][b];
-                            Fx[r] += wt * Fq;
-                            Fy[r] += wt * Gq;
+                        for (int r = 0; r < TY; ++r) {
+                            const int b = b0 + r;
+                            if ((unsigned)b < 4u) {
+                                const R wt = wxa * s_wy[wid][q][b] + axa * s_cy[wid][q][b];
+                                Fx[r] += wt * Fq;
+                                Fy[r] += wt * Gq;
+                            }
+                        }
+                    }
+                } else {
+                    for (int q = 0; q < ns; ++q) {
+                        // node (x, y) in the marker's 4 x 4 stencil [ix - 1, ix + 2] x [iy - 1, iy + 2]
+                        const int a = x - s_ix[wid][q] + 1;
+                        if ((unsigned)a >= 4u) continue;
+                        const R wxa = s_wx[wid][q][a], Fq = s_Fx[wid][q], Gq = s_Fy[wid][q];
+                        const int b0 = y0 - s_iy[wid][q] + 1;
+#pragma unroll
+                        for (int r = 0; r < TY; ++r) {
+                            const int b = b0 + r;
+                            if ((unsigned)b < 4u) {
+                                const R wt = wxa * s_wy[wid][q][b];
+                                Fx[r] += wt * Fq;
+                                Fy[r] += wt * Gq;
+                            }
                         }
                     }
                 }
@@ -504,7 +554,8 @@ cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, cudaSt
     cudaError_t e = cudaSuccess;
     by_store(d.store, [&](auto sp, auto rp) {
         LBIB_TYPES(sp, rp);
-        e = cudaLaunchKernelEx(&cfg, k_near<S, R>, d, parity);
+        if (d.L.transfer == LBIB_TRANSFER_MLS) e = cudaLaunchKernelEx(&cfg, k_near<S, R, true>, d, parity);
+        else e = cudaLaunchKernelEx(&cfg, k_near<S, R, false>, d, parity);
     });
     return e;
 }

@@ -19,6 +19,7 @@ LBIB_ERR_OOM, LBIB_ERR_DIVERGED, LBIB_ERR_TIMEOUT, LBIB_ERR_STATE = 4, 5, 6, 7
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "CUDA", 4: "OOM", 5: "DIVERGED",
                 6: "TIMEOUT", 7: "STATE"}
 LBIB_BC_INLET_OUTLET, LBIB_BC_PERIODIC_FORCE = 0, 1
+LBIB_TRANSFER_PESKIN, LBIB_TRANSFER_MLS = 0, 1
 LBIB_STORE_FP64, LBIB_STORE_FP32, LBIB_STORE_BF16, LBIB_STORE_FP16 = 0, 1, 2, 3
 STORAGE_CODES = {"fp64": LBIB_STORE_FP64, "fp32": LBIB_STORE_FP32, "bf16": LBIB_STORE_BF16, "fp16": LBIB_STORE_FP16}
 LBIB_CELL, LBIB_PARTICLE = 0, 1
@@ -33,7 +34,8 @@ class lbib_fluid_params(ctypes.Structure):
                 ("re", ctypes.c_double), ("rho_out", ctypes.c_double), ("gx", ctypes.c_double),
                 ("gy", ctypes.c_double), ("bc_mode", ctypes.c_int32), ("storage", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("obs_capacity", ctypes.c_int32),
-                ("cuda_stream", ctypes.c_void_p), ("seed", ctypes.c_uint64)]
+                ("cuda_stream", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("transfer", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class lbib_membrane_desc(ctypes.Structure):
@@ -231,14 +233,14 @@ class Solver:
 
     def __init__(self, nx, ny, tau=1.0, re=1e-2, rho_out=1.0, bc=LBIB_BC_INLET_OUTLET, g=(0.0, 0.0),
                  storage=LBIB_STORE_FP64, device=0, seed=0, stream: Optional[int] = None, obs_capacity=0,
-                 seeds=None):
+                 seeds=None, transfer=0):
         self.lib = load()
         batch = np.ndim(nx) > 0
         nxs = [int(v) for v in (nx if batch else [nx])]
         p = lbib_fluid_params(nx=nxs[0], ny=int(ny), tau=float(tau), re=float(re), rho_out=float(rho_out),
                               gx=float(g[0]), gy=float(g[1]), bc_mode=int(bc), storage=int(storage),
                               device=int(device), obs_capacity=int(obs_capacity),
-                              cuda_stream=stream, seed=int(seed) & (2**64 - 1))
+                              cuda_stream=stream, seed=int(seed) & (2**64 - 1), transfer=int(transfer))
         self.nxs, self.ny = nxs, int(ny)
         self.nx = nxs[0]
         self.ctx = lbib_create_batch(p, nxs, seeds) if batch else lbib_create(p)
@@ -399,7 +401,7 @@ def from_capillary(cap, storage=None, device=0, stream=None, obs_capacity=0) -> 
     if st is None:
         st = STORAGE_CODES[cap.storage]
     s = Solver(cap.nx, cap.ny, tau=cap.tau, re=cap.re, rho_out=cap.rho_out, bc=cap.bc, g=cap.g, storage=st,
-               device=device, seed=cap.seed, stream=stream, obs_capacity=obs_capacity)
+               device=device, seed=cap.seed, stream=stream, obs_capacity=obs_capacity, transfer=cap.transfer)
     _add_bodies(s, cap, 0)
     return s
 
@@ -512,14 +514,15 @@ def from_capillaries(caps, storage=None, device=0, stream=None, obs_capacity=0) 
     keeps its own length, bodies and seed)."""
     c0 = caps[0]
     for c in caps:
-        if (c.ny, c.tau, c.re, c.rho_out, c.bc, tuple(c.g), c.storage) != \
-                (c0.ny, c0.tau, c0.re, c0.rho_out, c0.bc, tuple(c0.g), c0.storage):
+        if (c.ny, c.tau, c.re, c.rho_out, c.bc, tuple(c.g), c.storage, c.transfer) != \
+                (c0.ny, c0.tau, c0.re, c0.rho_out, c0.bc, tuple(c0.g), c0.storage, c0.transfer):
             raise ValueError("instances of a batch share ny and the fluid parameters")
     st = storage
     if st is None:
         st = STORAGE_CODES[c0.storage]
     s = Solver([c.nx for c in caps], c0.ny, tau=c0.tau, re=c0.re, rho_out=c0.rho_out, bc=c0.bc, g=c0.g,
-               storage=st, device=device, stream=stream, obs_capacity=obs_capacity, seeds=[c.seed for c in caps])
+               storage=st, device=device, stream=stream, obs_capacity=obs_capacity, seeds=[c.seed for c in caps],
+               transfer=c0.transfer)
     for k, c in enumerate(caps):
         _add_bodies(s, c, k)
     return s

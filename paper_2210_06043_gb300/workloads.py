@@ -136,6 +136,7 @@ class Capillary:
     bc: int = 0  # 0 inlet/outlet, 1 periodic + body force
     g: tuple = (0.0, 0.0)
     rho_out: float = 1.0
+    transfer: int = 0  # 0 Peskin delta, 1 moving least squares
 
     @property
     def nodes(self) -> int:

@@ -51,6 +51,7 @@ def _c_layout():
 int main(void) {
   S(lbib_fluid_params); O(lbib_fluid_params, tau); O(lbib_fluid_params, bc_mode);
   O(lbib_fluid_params, obs_capacity); O(lbib_fluid_params, cuda_stream); O(lbib_fluid_params, seed);
+  O(lbib_fluid_params, transfer);
   S(lbib_membrane_desc); O(lbib_membrane_desc, xy); O(lbib_membrane_desc, xy_ref); O(lbib_membrane_desc, density_ratio);
   S(lbib_adhesion_params); O(lbib_adhesion_params, sigma); O(lbib_adhesion_params, xi);
   S(lbib_obs); O(lbib_obs, n_l); O(lbib_obs, n_bound); O(lbib_obs, status);
@@ -94,6 +95,9 @@ def test_create_reports_errors_through_the_boundary():
     assert lib.lbib_create(ctypes.byref(p), ctypes.byref(h)) == lbib.LBIB_ERR_INVALID_ARG
     p = lbib.lbib_fluid_params(nx=16, ny=8, tau=1.0, re=0.01, rho_out=1.0, storage=7)
     assert lib.lbib_create(ctypes.byref(p), ctypes.byref(h)) == lbib.LBIB_ERR_INVALID_ARG
+    p = lbib.lbib_fluid_params(nx=16, ny=8, tau=1.0, re=0.01, rho_out=1.0, transfer=2)
+    assert lib.lbib_create(ctypes.byref(p), ctypes.byref(h)) == lbib.LBIB_ERR_INVALID_ARG
+    assert b"transfer" in lib.lbib_last_error(None)
     p = lbib.lbib_fluid_params(nx=16, ny=8, tau=1.0, re=0.01, rho_out=1.0, device=0)
     st = lib.lbib_create(ctypes.byref(p), ctypes.byref(h))
     if st == lbib.LBIB_OK:  # a GPU is present

@@ -1,0 +1,127 @@
+"""GPU parity of the moving-least-squares transfer (LBIB_TRANSFER_MLS,
+Sec. 2.2) against the oracle with the same transfer, through the C ABI.
+
+Tolerances as the Peskin runs (test_gpu_coupled.py): FP64 storage agrees to
+rounding (forces of the first step to 1e-10 of their scale, positions to
+1e-9 dx after the full small run); FP32 storage to 1e-5 relative L2 on the
+velocity and 1e-6 dx on positions.  The MLS fit's inverse moment matrix is
+formed in the compute precision; in FP32 its relative error is ~1e-6, inside
+the FP32 bar."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from helpers import oracle_from, rel_l2
+from paper_2210_06043_gb300 import lbib
+from paper_2210_06043_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+MLS = lbib.LBIB_TRANSFER_MLS
+FORCES = ("uvx", "fpx", "ftx", "vx", "mfx")
+
+
+def _mls(cap):
+    return dataclasses.replace(cap, transfer=MLS)
+
+
+def test_first_step_every_force_fp64():
+    cap = _mls(wl.small_capillary())
+    o = oracle_from(cap)
+    s = lbib.from_capillary(cap)
+    o.step(1)
+    s.advance(1)
+    for bi in range(len(cap.bodies)):
+        for fx in FORCES:
+            fy = fx[:-1] + "y"
+            ax, ay = o.body(bi, fx), o.body(bi, fy)
+            bx, by = s.body_field(bi, fx), s.body_field(bi, fy)
+            scale = np.hypot(ax, ay).max()
+            err = max(np.abs(ax - bx).max(), np.abs(ay - by).max())
+            assert err <= 1e-10 * scale + 1e-13, (bi, fx, err, scale)
+    fo = o.fpost()
+    assert np.abs(s.populations() - fo).max() < 1e-14
+    s.close()
+
+
+def test_full_run_fp64_differs_from_peskin():
+    """240 x 60 capillary, 2000 steps with MLS: parity with the oracle, and
+    the trajectory is not the Peskin one (the transfer is really switched)."""
+    cap = _mls(wl.small_capillary())
+    o = oracle_from(cap)
+    s = lbib.from_capillary(cap)
+    for chunk in (1, 499, 1500):
+        o.step(chunk)
+        s.advance(chunk)
+        for bi in range(len(cap.bodies)):
+            assert np.abs(o.body_xy(bi) - s.markers(bi)).max() < 1e-9
+    _, ux, uy = o.macro()
+    gux, guy = s.velocity()
+    assert rel_l2(np.stack([gux, guy]), np.stack([ux, uy])) < 1e-9
+    peskin = lbib.from_capillary(wl.small_capillary())
+    peskin.advance(2000)
+    assert np.abs(peskin.markers(0) - s.markers(0)).max() > 1e-8
+    oo, go = o.obs(), s.observables()[-1]
+    assert go["delta_p"] == pytest.approx(oo["delta_p"], abs=1e-10)
+    assert go["r"] == pytest.approx(oo["r"], abs=1e-9)
+    s.close()
+    peskin.close()
+
+
+def test_bodies_at_inlet_and_wall_fp64():
+    """Stencils cut by the lower wall and the inlet column (the fit over the
+    remaining nodes), a rigid adhering rectangle on the wall under a cell."""
+    nx, ny = 70, 20
+    part = wl.rectangle(24, 9.0, 0.1 + 1.5, 8.0, 3.0)
+    cell = wl.circle(40, 9.0, 3.1 + 1.5 + 5.0, 5.0)
+    cap = wl.Capillary("edge", nx, ny, 0.9, 2.0, 300, "fp64", 3, [
+        wl.Body(wl.CELL, wl.DEFORMABLE, cell, ca=1e-2, beta=5e-2),
+        wl.Body(wl.PARTICLE, wl.RIGID, part, ca=0.0, beta=0.0, density_ratio=1.1,
+                adhesion=wl.Adhesion(30, 1.0, 0.2, 0.1, 0.2, 0.05, 25.0)),
+    ], transfer=MLS)
+    o = oracle_from(cap)
+    s = lbib.from_capillary(cap)
+    o.step(300)
+    s.advance(300)
+    for bi in range(2):
+        assert np.abs(o.body_xy(bi) - s.markers(bi)).max() < 1e-9
+    _, ux, uy = o.macro()
+    gux, guy = s.velocity()
+    assert rel_l2(np.stack([gux, guy]), np.stack([ux, uy])) < 1e-9
+    s.close()
+
+
+def test_production_capillary_fp32():
+    cap = _mls(wl.production_capillary())
+    o = oracle_from(cap)
+    s = lbib.from_capillary(cap)
+    o.step(300)
+    s.advance(300)
+    _, ux, uy = o.macro()
+    gux, guy = s.velocity()
+    assert rel_l2(np.stack([gux, guy]), np.stack([ux, uy])) < 1e-5
+    for bi in range(len(cap.bodies)):
+        assert np.abs(o.body_xy(bi) - s.markers(bi)).max() < 1e-6
+    s.close()
+
+
+def test_launch_shapes_do_not_change_mls_results():
+    cap = _mls(wl.production_capillary())
+    ref = None
+    for cfg in ((256, 304, 1, 1, 1), (512, 1216, 2, 2, 2)):
+        s = lbib.from_capillary(cap)
+        s.set_launch_config(*cfg)
+        s.advance(60)
+        m = np.concatenate([s.markers(b) for b in range(len(cap.bodies))])
+        u = np.stack(s.velocity())
+        if ref is None:
+            ref = (m, u)
+        else:
+            assert np.array_equal(m, ref[0]) and np.array_equal(u, ref[1])
+        s.close()
+
+
+def test_unknown_transfer_is_rejected():
+    with pytest.raises(lbib.LbibError):
+        lbib.Solver(64, 16, transfer=7)
