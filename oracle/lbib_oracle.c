@@ -43,9 +43,10 @@
  *   - The alternative transfer (orc_set_transfer): the moving-least-squares
  *     reconstruction of Vanella and Balaras (2009) that Sec. 2.2 cites, with
  *     a linear basis and the cubic-spline weight of support half-width 2 (the
- *     same 4 x 4 stencil); stencil nodes outside the lattice are left out of
- *     the fit, gradients are the fit's linear coefficients, and spreading uses
- *     the same shape functions (the adjoint).
+ *     same 4 x 4 stencil); walls as for the Peskin stencil (wall nodes in the
+ *     fit, zero velocity, force absorbed, density renormalised), gradients
+ *     the fit's linear coefficients, spreading with the same shape functions
+ *     (the adjoint).
  *   - Direct forcing: F_L = rho (U_struct - U*) / dt at the new element
  *     centroids, U* and rho interpolated from the moments of step 2, spread
  *     with weight ds = element length.  A marker closer than half a spacing
@@ -252,30 +253,27 @@ double orc_mls_weight(double r)
 /* The moving-least-squares reconstruction cited in Sec. 2.2 (Vanella and
  * Balaras 2009), with the linear basis p(x, y) = (1, x - X, y - Y) about the
  * point (X, Y) and weights W_j = w(x_j - X) w(y_j - Y) over the 4 x 4 stencil
- * nodes that lie inside the lattice: the weighted least-squares fit of a
- * nodal field f has coefficients a = A^{-1} sum_j W_j p_j f_j with
- * A = sum_j W_j p_j p_j^T; a_0 is the reconstructed value at (X, Y) and
- * (a_1, a_2) its gradient.  Writes A^{-1} (row-major 3 x 3) to inv; returns 0
- * when A is singular (the stencil holds fewer than two weighted columns or
- * rows), else 1. */
-static int mls_inverse(int nx, int ny, double X, double Y, double inv[9])
+ * around it: the weighted least-squares fit of a nodal field f has
+ * coefficients a = A^{-1} sum_j W_j p_j f_j with A = sum_j W_j p_j p_j^T;
+ * a_0 is the reconstructed value at (X, Y) and (a_1, a_2) its gradient.  The
+ * walls follow the same reading as the Peskin stencil: nodes beyond a wall
+ * (or beyond the lattice ends) are wall nodes, so the fit always spans the
+ * whole stencil and A depends on (X, Y) alone.  Writes A^{-1} (row-major
+ * 3 x 3) to inv. */
+static void mls_inverse(double X, double Y, double inv[9])
 {
     double A[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     int i0 = (int)floor(X) - 1, j0 = (int)floor(Y - 0.5) - 1;
-    for (int j = j0; j <= j0 + 3; ++j) {
-        if (j < 0 || j >= ny) continue;
+    for (int j = j0; j <= j0 + 3; ++j)
         for (int i = i0; i <= i0 + 3; ++i) {
-            if (i < 0 || i >= nx) continue;
             double W = orc_mls_weight(i - X) * orc_mls_weight(j + 0.5 - Y);
             double pv[3] = {1.0, i - X, j + 0.5 - Y};
             for (int r = 0; r < 3; ++r)
                 for (int c = 0; c < 3; ++c) A[3 * r + c] += W * pv[r] * pv[c];
         }
-    }
-    /* inverse by cofactors (A is symmetric) */
+    /* inverse by cofactors (A is symmetric; the full stencil keeps it regular) */
     double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
     double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
-    if (!(fabs(det) > 1e-12 * A[0] * A[0] * A[0])) return 0;
     inv[0] = c00 / det;
     inv[1] = (A[2] * A[7] - A[1] * A[8]) / det;
     inv[2] = (A[1] * A[5] - A[2] * A[4]) / det;
@@ -285,7 +283,6 @@ static int mls_inverse(int nx, int ny, double X, double Y, double inv[9])
     inv[6] = c02 / det;
     inv[7] = (A[1] * A[6] - A[0] * A[7]) / det;
     inv[8] = (A[0] * A[4] - A[1] * A[3]) / det;
-    return 1;
 }
 
 /* MLS shape functions at (X, Y) of the stencil node (i, j): phi[0] weights the
@@ -298,19 +295,19 @@ static void mls_shape(const double inv[9], double X, double Y, int i, int j, dou
     for (int k = 0; k < 3; ++k) phi[k] = W * (inv[3 * k] * pv[0] + inv[3 * k + 1] * pv[1] + inv[3 * k + 2] * pv[2]);
 }
 
-/* MLS interpolation of a nodal field at (X, Y): *val the reconstruction, *gx,
- * *gy its gradient coefficients; returns the sum of the value's shape
- * functions (one up to rounding, the linear basis holds the constant), 0 if
- * the stencil is degenerate.  Walls and instance ends truncate the stencil;
- * the fit uses the nodes that remain, so no renormalisation is needed. */
-static double interp_mls(int nx, int ny, const double* fld, double X, double Y, double* val, double* gx, double* gy)
+/* MLS interpolation of a nodal field at (X, Y).  Velocity-type (renorm = 0):
+ * wall nodes carry the wall's zero velocity, so the sums simply skip them;
+ * *val the reconstruction, *gx, *gy its gradient coefficients.  Density-type
+ * (renorm = 1): no wall value, so the value's shape functions are
+ * renormalised over the fluid nodes (as the Peskin weights are).  Returns the
+ * sum S of the value's shape functions over the nodes inside the lattice (one
+ * away from walls). */
+static double interp_mls(int nx, int ny, const double* fld, double X, double Y, double* val, double* gx, double* gy,
+                         int renorm)
 {
     double inv[9];
-    if (val) *val = 0.0;
-    if (gx) *gx = 0.0;
-    if (gy) *gy = 0.0;
-    if (!mls_inverse(nx, ny, X, Y, inv)) return 0.0;
-    double S = 0.0, a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    mls_inverse(X, Y, inv);
+    double S = 0.0, Sx = 0.0, Sy = 0.0, a0 = 0.0, a1 = 0.0, a2 = 0.0;
     int i0 = (int)floor(X) - 1, j0 = (int)floor(Y - 0.5) - 1;
     for (int j = j0; j <= j0 + 3; ++j) {
         if (j < 0 || j >= ny) continue;
@@ -320,14 +317,23 @@ static double interp_mls(int nx, int ny, const double* fld, double X, double Y, 
             mls_shape(inv, X, Y, i, j, phi);
             double u = fld[(size_t)j * nx + i];
             S += phi[0];
+            Sx += phi[1];
+            Sy += phi[2];
             a0 += phi[0] * u;
             a1 += phi[1] * u;
             a2 += phi[2] * u;
         }
     }
-    if (val) *val = a0;
-    if (gx) *gx = a1;
-    if (gy) *gy = a2;
+    if (!renorm) {
+        if (val) *val = a0;
+        if (gx) *gx = a1;
+        if (gy) *gy = a2;
+        return S;
+    }
+    double I = (S > 0.0) ? a0 / S : 0.0;
+    if (val) *val = I;
+    if (gx) *gx = (S > 0.0) ? (a1 - I * Sx) / S : 0.0;
+    if (gy) *gy = (S > 0.0) ? (a2 - I * Sy) / S : 0.0;
     return S;
 }
 
@@ -376,7 +382,7 @@ static double interp_field(int nx, int ny, const double* fld, double X, double Y
 static double interp_kind(int kind, int nx, int ny, const double* fld, double X, double Y, double* val, double* gx,
                           double* gy, int renorm)
 {
-    if (kind == ORC_TRANSFER_MLS) return interp_mls(nx, ny, fld, X, Y, val, gx, gy);
+    if (kind == ORC_TRANSFER_MLS) return interp_mls(nx, ny, fld, X, Y, val, gx, gy, renorm);
     return interp_field(nx, ny, fld, X, Y, val, gx, gy, renorm);
 }
 
@@ -388,17 +394,16 @@ double orc_interp(int nx, int ny, const double* fld, double X, double Y, double*
 }
 
 /* Spreading of point forces (Fx, Fy) with weights ds onto a field with the
- * same truncated stencil (the adjoint of the velocity interpolation).  Peskin:
- * the share that would land on wall nodes is taken up by the wall.  MLS: the
- * shape functions of the nodes inside the lattice sum to one, so the whole
- * force reaches the fluid. */
+ * same truncated stencil (the adjoint of the velocity interpolation), Peskin
+ * weights or MLS shape functions: the share that would land on wall nodes is
+ * taken up by the wall. */
 void orc_spread(int nx, int ny, int n, const double* X, const double* Y, const double* Fx, const double* Fy,
                 const double* ds, double* outx, double* outy, int kind)
 {
     for (int m = 0; m < n; ++m) {
         int i0 = (int)floor(X[m]) - 1, j0 = (int)floor(Y[m] - 0.5) - 1;
         double inv[9];
-        if (kind == ORC_TRANSFER_MLS && !mls_inverse(nx, ny, X[m], Y[m], inv)) continue;
+        if (kind == ORC_TRANSFER_MLS) mls_inverse(X[m], Y[m], inv);
         for (int j = j0; j <= j0 + 3; ++j) {
             if (j < 0 || j >= ny) continue;
             for (int i = i0; i <= i0 + 3; ++i) {

@@ -1,9 +1,11 @@
 """Pins of the oracle's moving-least-squares transfer (Sec. 2.2 cites Vanella
 and Balaras 2009 for it) against facts other than its own code: the cubic
 spline's closed-form values and smoothness, the weighted least-squares fit
-solved by numpy's lstsq, exact reproduction of linear fields (value and
-gradient) including stencils cut by walls and lattice ends, conservation of
-spread force, and the adjoint identity between spreading and interpolation."""
+solved by numpy's lstsq (wall nodes holding the wall's zero velocity, the
+reading the Peskin stencil follows), exact reproduction of linear fields away
+from walls, exact constant density at walls (renormalised over the fluid),
+second-order interior error, conservation of spread force away from walls
+and the adjoint identity between spreading and interpolation."""
 import math
 
 import numpy as np
@@ -46,41 +48,52 @@ POINTS = [(5.3, 4.1), (7.0, 5.5), (0.2, 0.1), (11.0, 9.9), (3.7, 0.0), (0.0, 10.
 
 
 def test_fit_equals_weighted_least_squares():
-    """The reconstruction and its gradient are the weighted least-squares fit
-    of a + b (x - X) + c (y - Y) over the stencil nodes inside the lattice
-    (solved here by numpy's lstsq on the sqrt(W)-scaled system)."""
+    """The velocity-type reconstruction and its gradient are the weighted
+    least-squares fit of a + b (x - X) + c (y - Y) over the whole 4 x 4
+    stencil, nodes beyond a wall or a lattice end holding zero (solved here by
+    numpy's lstsq on the sqrt(W)-scaled system)."""
     rng = np.random.default_rng(0)
     nx, ny = 12, 10
     f = rng.normal(0, 1, (ny, nx))
     for X, Y in POINTS:
-        nodes = _stencil(nx, ny, X, Y)
+        i0, j0 = math.floor(X) - 1, math.floor(Y - 0.5) - 1
+        nodes = [(i, j) for j in range(j0, j0 + 4) for i in range(i0, i0 + 4)]
+        vals = np.array([f[j, i] if 0 <= i < nx and 0 <= j < ny else 0.0 for i, j in nodes])
         P = np.array([[1.0, i - X, j + 0.5 - Y] for i, j in nodes])
         W = np.array([oracle.mls_weight(i - X) * oracle.mls_weight(j + 0.5 - Y) for i, j in nodes])
         keep = W > 0
         sw = np.sqrt(W[keep])
-        coef, *_ = np.linalg.lstsq(P[keep] * sw[:, None], np.array([f[j, i] for i, j in nodes])[keep] * sw,
-                                   rcond=None)
+        coef, *_ = np.linalg.lstsq(P[keep] * sw[:, None], vals[keep] * sw, rcond=None)
         S, v, gx, gy = oracle.interp(f, X, Y, kind=MLS)
-        assert S == pytest.approx(1.0, abs=1e-13)
+        inside = all(0 <= i < nx and 0 <= j < ny for i, j in nodes)
+        if inside:
+            assert S == pytest.approx(1.0, abs=1e-13)
         assert v == pytest.approx(coef[0], abs=1e-12)
         assert gx == pytest.approx(coef[1], abs=1e-12)
         assert gy == pytest.approx(coef[2], abs=1e-12)
 
 
-def test_linear_fields_reproduced_at_walls_and_ends():
+def test_linear_fields_and_wall_density():
     nx, ny = 12, 10
     jj, ii = np.mgrid[0:ny, 0:nx]
+    interior = [(5.3, 4.1), (7.0, 5.5), (2.6, 1.6), (8.99, 8.4)]
     for a, b, c in ((0.3, 0.7, -1.1), (2.0, 0.0, 0.0), (-1.0, 0.25, 3.0)):
         f = a + b * ii + c * (jj + 0.5)
-        for X, Y in POINTS:
+        for X, Y in interior:
             S, v, gx, gy = oracle.interp(f, X, Y, kind=MLS)
+            assert S == pytest.approx(1.0, abs=1e-13)
             assert v == pytest.approx(a + b * X + c * Y, abs=1e-12)
             assert gx == pytest.approx(b, abs=1e-12) and gy == pytest.approx(c, abs=1e-12)
-            # the Peskin interpolant, for contrast, loses consistency at a wall
-    W, v, _, _ = oracle.interp(np.ones((ny, nx)), 5.0, 0.2)
-    assert W < 0.9  # truncated Peskin stencil
+    # a uniform density is reproduced exactly everywhere, walls included
+    rho = np.full((ny, nx), 1.0137)
+    for X, Y in POINTS:
+        S, v, gx, gy = oracle.interp(rho, X, Y, renorm=True, kind=MLS)
+        assert S > 0 and v == pytest.approx(1.0137, abs=1e-13)
+        assert abs(gx) < 1e-12 and abs(gy) < 1e-12
+    # at a wall the velocity-type fit sees the wall nodes' zero: a uniform
+    # field is reconstructed as the fluid share of the shape functions
     S, v, _, _ = oracle.interp(np.ones((ny, nx)), 5.0, 0.2, kind=MLS)
-    assert v == pytest.approx(1.0, abs=1e-14)
+    assert 0.3 < S < 0.9 and v == pytest.approx(S, abs=1e-14)
 
 
 def test_interior_error_is_second_order():
@@ -102,18 +115,20 @@ def test_spreading_conserves_force_and_is_the_adjoint():
     rng = np.random.default_rng(1)
     nx, ny = 14, 9
     n = 12
-    X = rng.uniform(0, nx - 1, n)
-    Y = rng.uniform(0, ny, n)
-    X[:3] = (0.0, 13.0, 6.5)
-    Y[:3] = (0.1, 8.95, 0.0)  # at the walls and the lattice ends
+    X = rng.uniform(2, nx - 3, n)
+    Y = rng.uniform(2, ny - 2, n)
     Fx, Fy, ds = rng.normal(0, 1, n), rng.normal(0, 1, n), rng.uniform(0.5, 1.5, n)
     ox, oy = oracle.spread(nx, ny, X, Y, Fx, Fy, ds, kind=MLS)
+    # away from walls every shape function lands in the fluid
     assert ox.sum() == pytest.approx((Fx * ds).sum(), abs=1e-12)
     assert oy.sum() == pytest.approx((Fy * ds).sum(), abs=1e-12)
+    # markers at the walls and lattice ends: the wall takes the share that
+    # falls on wall nodes; spreading stays the adjoint of the interpolation
+    X[:3] = (0.0, 13.0, 6.5)
+    Y[:3] = (0.1, 8.95, 0.0)
+    ox, oy = oracle.spread(nx, ny, X, Y, Fx, Fy, ds, kind=MLS)
     u = rng.normal(0, 1, (ny, nx))
     lhs = (u * ox).sum()
     rhs = sum(Fx[m] * ds[m] * oracle.interp(u, X[m], Y[m], kind=MLS)[1] for m in range(n))
     assert lhs == pytest.approx(rhs, abs=1e-12)
-    # the Peskin spreading loses the share that falls beyond the walls
-    px, _ = oracle.spread(nx, ny, X, Y, Fx, np.zeros(n), ds)
-    assert abs(px.sum() - (Fx * ds).sum()) > 1e-3
+    assert abs(ox.sum() - (Fx * ds).sum()) > 1e-3
