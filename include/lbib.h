@@ -71,18 +71,18 @@ typedef enum { LBIB_BC_INLET_OUTLET = 0, LBIB_BC_PERIODIC_FORCE = 1 } lbib_bc_mo
 typedef enum { LBIB_STORE_FP64 = 0, LBIB_STORE_FP32 = 1, LBIB_STORE_BF16 = 2, LBIB_STORE_FP16 = 3 } lbib_storage;
 /* Eulerian-Lagrangian transfer (interpolation of the fluid at the membrane
  * and spreading of the direct force, Sec. 2.2), over the same 4 x 4 nodes
- * around a point either way:
- *   PESKIN: Peskin's 4-point discrete delta, phi(dx) phi(dy); stencil nodes
- *     beyond a wall carry its zero velocity and absorb the force that falls
- *     on them; density weights are renormalised over the fluid nodes;
- *     gradients are the delta's exact derivatives.
+ * around a point either way, and either way stencil nodes beyond a wall (or
+ * an instance end) are wall nodes: they carry the wall's zero velocity and
+ * absorb the force that falls on them, and density weights are renormalised
+ * over the fluid nodes.
+ *   PESKIN: Peskin's 4-point discrete delta, phi(dx) phi(dy); gradients are
+ *     the delta's exact derivatives.
  *   MLS: the moving-least-squares reconstruction of Vanella and Balaras
  *     (2009) that Sec. 2.2 cites: linear basis (1, x - X, y - Y), weights
- *     w(dx) w(dy) with w the cubic spline of |r| / 2, fitted over the stencil
- *     nodes inside the lattice (walls and instance ends truncate it, the fit
- *     stays consistent: the shape functions sum to one and reproduce linear
- *     fields); gradients are the fit's linear coefficients; spreading uses the
- *     same shape functions, so the spread force is conserved at walls too. */
+ *     w(dx) w(dy) with w the cubic spline of |r| / 2, fitted over the whole
+ *     stencil (away from walls the shape functions sum to one and reproduce
+ *     linear fields); gradients are the fit's linear coefficients; spreading
+ *     uses the same shape functions (the adjoint of the interpolation). */
 typedef enum { LBIB_TRANSFER_PESKIN = 0, LBIB_TRANSFER_MLS = 1 } lbib_transfer;
 typedef enum { LBIB_CELL = 0, LBIB_PARTICLE = 1 } lbib_body_kind;
 typedef enum { LBIB_DEFORMABLE = 0, LBIB_RIGID = 1, LBIB_FIXED = 2 } lbib_motion;

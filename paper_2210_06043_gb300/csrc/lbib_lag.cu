@@ -165,8 +165,8 @@ struct RowSums {
 // clamped into the instance and the weights of nodes outside it zeroed, so a
 // lane's loads are independent and issued together.  All 32 lanes of the warp
 // must call this together.  With the MLS transfer the node weights are the
-// fit's shape functions (value and gradient) over the nodes inside the
-// instance and the lattice, and the density needs no renormalisation.
+// fit's shape functions (value and gradient) over the whole stencil, wall
+// nodes included with zero velocity, as for the Peskin weights.
 template <typename R, bool GRAD, int K>
 __device__ __forceinline__ void sample_group(const Dev& d, const Spot<R>& sp, int32_t m, int r, int x0, int nxi,
                                              Sample<R>& o, uint32_t& miss)
@@ -190,10 +190,10 @@ __device__ __forceinline__ void sample_group(const Dev& d, const Spot<R>& sp, in
         if (mls) px[a] = mls_w<R>(rx);
         else if (GRAD) peskin_both<R>(rx, px[a], dpx[a]);
         else px[a] = peskin<R>(rx);
-        if (!vi) px[a] = dpx[a] = R(0);
     }
-    // MLS: the fit's inverse moment matrix from the whole 4 x 4 stencil (every
-    // lane forms it from the same terms in the same order, whatever K)
+    // MLS: the fit's inverse moment matrix over the whole 4 x 4 stencil (nodes
+    // beyond a wall or an instance end are wall nodes); every lane forms it
+    // from the same terms in the same order, whatever K
     R inv[9];
     if (mls) {
         R a0 = R(0), a1 = R(0), a2 = R(0), b0 = R(0), b1 = R(0), b2 = R(0);
@@ -206,20 +206,20 @@ __device__ __forceinline__ void sample_group(const Dev& d, const Spot<R>& sp, in
         }
 #pragma unroll
         for (int rr = 0; rr < 4; ++rr) {
-            const int j = sp.jy - 1 + rr;
             const R dy = R(rr - 1) - sp.ay;  // y_j - Y
-            const R w = (j >= 0 && j < L.ny) ? mls_w<R>(dy) : R(0);
+            const R w = mls_w<R>(dy);
             b0 += w;
             b1 += w * dy;
             b2 += w * dy * dy;
         }
         if (!mls_inverse<R>(a0, a1, a2, b0, b1, b2, inv)) {
 #pragma unroll
-            for (int a = 0; a < 4; ++a) px[a] = R(0);  // degenerate stencil: no sample (W = 0)
-#pragma unroll
-            for (int q = 0; q < 9; ++q) inv[q] = R(0);
+            for (int q = 0; q < 9; ++q) inv[q] = R(0);  // not reached: the full stencil is regular
         }
     }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+        if (!(i0 + a >= 0 && i0 + a < nxi)) px[a] = dpx[a] = R(0);  // wall nodes: zero velocity
     int jc[NR];
     R py[NR], dpy[NR];
     int32_t fr[2 * NR];
@@ -318,9 +318,8 @@ __device__ __forceinline__ void sample_group(const Dev& d, const Spot<R>& sp, in
     } else {
         o.ux = o.uy = o.vx = o.vy = R(0);
     }
-    // Peskin: density weights renormalised over the fluid nodes; MLS: the fit
-    // over the fluid nodes is already consistent
-    o.drho = mls ? t.r : ((t.W > R(0)) ? t.r / t.W : R(0));
+    // density: no wall value, weights renormalised over the fluid nodes
+    o.drho = (t.W > R(0)) ? t.r / t.W : R(0);
 }
 
 // Tiles overlapping the node box [i0, i1] x [j0, j1]: enumerates at most 8 of

@@ -284,14 +284,14 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near(Dev d, int p)
                         if constexpr (MLS) {
                             // MLS shape function of node (a, b) at the marker:
                             // wx_a wy_b (c0 + c1 dx_a + c2 dy_b), the fit over the
-                            // stencil nodes inside the instance and the lattice
-                            const int il = s_ix[wid][pos] - ci.x - 1, jl = s_iy[wid][pos] - 1;
+                            // whole stencil (the share of wall nodes stays with
+                            // the wall: those nodes are never updated here)
                             R wxv[4], wyv[4], a0 = R(0), a1 = R(0), a2 = R(0), b0 = R(0), b1 = R(0), b2 = R(0);
 #pragma unroll
                             for (int a = 0; a < 4; ++a) {
                                 const R dx = R(a - 1) - fx, dy = R(a - 1) - fy;
-                                wxv[a] = (il + a >= 0 && il + a < ci.y) ? mls_w<R>(dx) : R(0);
-                                wyv[a] = (jl + a >= 0 && jl + a < L.ny) ? mls_w<R>(dy) : R(0);
+                                wxv[a] = mls_w<R>(dx);
+                                wyv[a] = mls_w<R>(dy);
                                 a0 += wxv[a];
                                 a1 += wxv[a] * dx;
                                 a2 += wxv[a] * dx * dx;
