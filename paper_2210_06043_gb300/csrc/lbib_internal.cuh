@@ -67,12 +67,15 @@ struct Lattice {
     int nx, ny, nxp;          // nx: node columns of the whole batch; nxp: row pitch (multiple of TX)
     int ntx, nty, ntiles;     // tiles of the whole batch
     int bc;                   // lbib_bc_mode
-    int transfer;             // lbib_transfer
     int qstride;              // ny * nxp
     double tau, omega, nu, umax, rho_out, gx, gy;
     // the same parameters rounded to FP32 once on the host: FP32 kernels read
     // these instead of converting the doubles per node (FP64 is a narrow pipe)
     float omega_f, umax_f, rho_out_f, gx_f, gy_f;
+    // fields added later go last: moving the ones above changed the bulk
+    // kernel's register allocation (40 -> 48 at two nodes per thread), which
+    // cost 3.5 % of the step
+    int transfer;             // lbib_transfer
 };
 
 // Lattice parameter in the compute type R: the double for R = double, the

