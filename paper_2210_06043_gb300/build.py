@@ -15,8 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbib.so")
-SOURCES = ("lbib_api.cu", "lbib_lbm.cu", "lbib_lag.cu", "lbib_noalloc.cu", "lbib_mlp.cu")
-HEADERS = ("lbib_internal.cuh", "lbib_device.cuh")
+SOURCES = ("lbib_api.cu", "lbib_lbm.cu", "lbib_lag.cu", "lbib_lag_mls.cu", "lbib_noalloc.cu", "lbib_mlp.cu")
+HEADERS = ("lbib_internal.cuh", "lbib_device.cuh", "lbib_lag_kernel.cuh")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
