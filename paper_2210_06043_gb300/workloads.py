@@ -247,3 +247,51 @@ def reduced_area(xy: np.ndarray) -> float:
     A = 0.5 * np.sum(x * np.roll(y, -1) - np.roll(x, -1) * y)
     P = np.sum(np.hypot(np.roll(x, -1) - x, np.roll(y, -1) - y))
     return 4.0 * math.pi * A / P**2
+
+
+# Sec. 3.1 compares square particles with circular ones whose diameter equals
+# the squares' thickness: d = 0.5, 1.0, 1.5 and 2.0 um
+COMPARISON_D_UM = (0.5, 1.0, 1.5, 2.0)
+LIGAND_DENSITY_PER_UM = 40.0  # ~ the 200 sites of the 2 x 1 um particle's 4.8 um perimeter
+
+
+def particle_shape(shape: str, n: int, d_um: float, ny: int) -> np.ndarray:
+    """A particle of thickness d_um resting on the lower wall at the release
+    point of the particles of Sec. 3.1: a d x d square or a circle of diameter
+    d, in lattice units of a channel ny nodes high."""
+    dx = H_UM / ny
+    d = d_um / dx
+    cx, cy = PARTICLE_X_UM / dx, PARTICLE_GAP_UM / dx + 0.5 * d
+    if shape == "square":
+        return rectangle(n, cx, cy, d, d)
+    if shape == "circle":
+        return circle(n, cx, cy, 0.5 * d, phase=-0.5 * np.pi)
+    raise ValueError("shape is 'square' or 'circle'")
+
+
+def particle_comparison_capillary(shape: str, d_um: float, nx: int = 1200, ny: int = 150, ca: float = 0.0,
+                                  seed: int = 0, storage: str = "fp32", markers: Optional[int] = None) -> Capillary:
+    """The globular 7 um cell over a square or circular particle of thickness
+    d_um adhering to the lower wall (sigma = 1), rigid when ca == 0, with
+    ligand sites at LIGAND_DENSITY_PER_UM along the perimeter and (by default)
+    one marker per lattice spacing of perimeter."""
+    dx = H_UM / ny
+    perim_um = (4.0 if shape == "square" else math.pi) * d_um
+    if markers is None:
+        markers = max(32, int(math.ceil(perim_um / dx)))
+    part = particle_shape(shape, markers, d_um, ny)
+    n_lig = max(4, int(round(LIGAND_DENSITY_PER_UM * perim_um)))
+    cell = circle(256, CELL_X_UM / dx, CELL_Y_UM / dx, CELL_RADIUS_UM / dx)
+    motion = RIGID if ca == 0.0 else DEFORMABLE
+    bodies = [Body(CELL, DEFORMABLE, cell, ca=1e-3, beta=0.0),
+              Body(PARTICLE, motion, part, ca=ca, beta=0.0 if ca == 0.0 else 1e-2, density_ratio=1.1,
+                   adhesion=_bond_defaults(ny, n_lig, 1.0))]
+    return Capillary(f"{nx}x{ny} globular cell, {shape} particle d = {d_um} um, Ca {ca}", nx, ny, 1.0, 1e-2,
+                     200000, storage, seed, bodies)
+
+
+def particle_comparison_capillaries(ca: float = 0.0, nx: int = 1200, ny: int = 150, seed: int = 0,
+                                    storage: str = "fp32") -> List[Capillary]:
+    """Square and circular particles of every COMPARISON_D_UM (8 capillaries)."""
+    return [particle_comparison_capillary(s, d, nx, ny, ca, seed, storage)
+            for s in ("square", "circle") for d in COMPARISON_D_UM]
