@@ -309,9 +309,12 @@ lbib_status lbib_set_launch_config(lbib_ctx* ctx, const lbib_launch_config* cfg)
  * state: a device snapshot of the state is taken, each candidate advances it
  * by two warm-up steps and twice steps_per_trial >= 1 steps, timed with CUDA
  * events (the faster run counts), the snapshot is restored, and the fastest
- * candidate is kept.  The
- * search is coordinate-wise: bulk tiles per block and nodes per thread, then membrane block size,
- * then activation stride, then near-kernel blocks.  On return the state, the step count and the
+ * candidate is kept.  The search is coordinate-wise, in two rounds: bulk
+ * tiles per block and nodes per thread, then membrane block size, then
+ * activation stride, then near-kernel blocks (2, 4, 6, 8 or 12 per SM), and
+ * the same again from the first round's optimum (the bulk and near kernels
+ * share the SMs, so their best shapes depend on each other).  On return the
+ * state, the step count and the
  * observables cursors are as on entry; *chosen (may be NULL) receives the
  * configuration.  Needs device memory for one more copy of the state. */
 lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_config* chosen);

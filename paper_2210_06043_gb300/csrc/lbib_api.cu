@@ -1404,32 +1404,37 @@ lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_co
             best = c;
         }
     };
-    const lbib_launch_config start = best;
-    for (int npt : {1, 2})
-        for (int rt : {1, 2, 4}) {
-            lbib_launch_config c = start;
-            c.bulk_tiles_y = rt;
-            c.bulk_nodes_per_thread = npt;
-            consider(c);
-        }
-    if (d.nbodies) {
-        const lbib_launch_config after_bulk = best;
-        for (int lt : {256, 512}) {
-            lbib_launch_config c = after_bulk;
-            c.lagrangian_threads = lt;
-            consider(c);
-        }
-        const lbib_launch_config after_lag = best;
-        for (int stride : {1, 2, 4}) {
-            lbib_launch_config c = after_lag;
-            c.activation_stride = stride;
-            consider(c);
-        }
-        const lbib_launch_config after_stride = best;
-        for (int per_sm : {2, 4, 8, 12}) {
-            lbib_launch_config c = after_stride;
-            c.near_blocks = per_sm * nsm;
-            consider(c);
+    // coordinate descent, two rounds: the bulk shape and the near grid interact
+    // (the near blocks take SMs from the bulk blocks), so the second round
+    // revisits each coordinate from the first round's optimum
+    for (int round = 0; round < 2; ++round) {
+        const lbib_launch_config start = best;
+        for (int npt : {1, 2})
+            for (int rt : {1, 2, 4}) {
+                lbib_launch_config c = start;
+                c.bulk_tiles_y = rt;
+                c.bulk_nodes_per_thread = npt;
+                consider(c);
+            }
+        if (d.nbodies) {
+            const lbib_launch_config after_bulk = best;
+            for (int lt : {256, 512}) {
+                lbib_launch_config c = after_bulk;
+                c.lagrangian_threads = lt;
+                consider(c);
+            }
+            const lbib_launch_config after_lag = best;
+            for (int stride : {1, 2, 4}) {
+                lbib_launch_config c = after_lag;
+                c.activation_stride = stride;
+                consider(c);
+            }
+            const lbib_launch_config after_stride = best;
+            for (int per_sm : {2, 4, 6, 8, 12}) {
+                lbib_launch_config c = after_stride;
+                c.near_blocks = per_sm * nsm;
+                consider(c);
+            }
         }
     }
     // back to the entry state with the chosen configuration
