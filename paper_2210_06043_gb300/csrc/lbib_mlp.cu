@@ -388,6 +388,311 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(GemmArgs g)
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
 }
 
+// ------------------------------------------- fused inference (all layers)
+// One persistent CTA per SM evaluates the whole network on 128-row tiles,
+// two tiles in flight (slots 0 and 1).  A tile's activations stay in shared
+// memory between layers, as the next layer's A operand (K-major core-matrix
+// layout in 64-wide K chunks: element (r, k) at (k / 64) * 16384 + (r / 8) *
+// 1024 + (k % 64 / 8) * 128 + (r % 8) * 16 + (k % 8) * 2 bytes); its
+// accumulator lives in tensor-memory columns [256 s, 256 s + 256).  Roles:
+//   warp 0, lane 0: issues the MMAs of each layer, slot by slot, and commits
+//     them to the stage's "empty" barrier and then to the slot's "accumulator
+//     full" barrier;
+//   warp 1, lane 0: streams the pre-packed weight chunks (a layer's N x 64
+//     K slice in the same core-matrix layout, contiguous in global memory)
+//     through FZ_STAGES shared-memory stages with cp.async.bulk, each chunk
+//     completing a "full" barrier by its byte count;
+//   warps 4 .. 11: the epilogue.  Warp w reads tensor-memory lanes
+//     32 (w % 4) .. + 31 (its tile rows) over half of the columns, adds the
+//     bias, applies GELU and writes the BF16 operand of the next layer in
+//     place, or writes the output rows; they also load the inputs of the
+//     next tile of the slot.  Each step ends with an arrival on the slot's
+//     "epilogue done" barrier, which the MMA issuer waits for.
+// While the MMAs of one slot's layer run, the epilogue of the other slot's
+// previous layer runs.  Every wait is bounded: on timeout the CTA sets the
+// status word, the other roles leave their loops, the copies and MMAs still
+// in flight are waited for (bounded) and the tensor memory is freed.
+constexpr int FZ_THREADS = 384, FZ_STAGES = 3, FZ_MAXW = 256, FZ_MAXL = 9;
+constexpr size_t FZ_ACT = (size_t)TC_BM * FZ_MAXW * 2;        // 64 KB per slot
+constexpr size_t FZ_STAGE = (size_t)FZ_MAXW * TC_BK * 2;      // 32 KB per weight chunk
+constexpr size_t FZ_BAR = 2 * FZ_ACT + FZ_STAGES * FZ_STAGE;  // barriers after the buffers
+constexpr size_t FZ_SMEM = FZ_BAR + 256;
+static_assert(FZ_SMEM <= 227 * 1024, "fused kernel shared memory");
+
+struct FusedArgs {
+    const float* x;
+    float* y;
+    int M, n_in, n_out, L;
+    const unsigned char* w;    // packed weight chunks
+    const float* bias;         // FP32 parameters (biases at boff)
+    int K[FZ_MAXL], N[FZ_MAXL], boff[FZ_MAXL];
+    long long woff[FZ_MAXL];   // byte offset of layer l's first chunk in w
+    const float *cin, *sin, *cout, *sout;
+    uint32_t* status;
+};
+
+__device__ __forceinline__ bool fz_wait(uint64_t* bar, uint32_t parity, volatile uint32_t* abort_flag,
+                                        uint32_t* status, bool honour_abort = true)
+{
+    for (uint32_t it = 0; it < TC_WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (honour_abort && (it & 255u) == 255u && *abort_flag) return false;
+    }
+    *abort_flag = 1u;
+    atomicOr(status, 1u);
+    return false;
+}
+
+__device__ __forceinline__ void fz_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// inputs of a tile into the slot's first K chunk: a0 = bf16(s_in (x - c_in)),
+// zero beyond n_in and beyond the last row; 256 epilogue threads, two per row
+__device__ __forceinline__ void fz_prep(const FusedArgs& a, int tile, unsigned char* act, int e)
+{
+    const int r = e >> 1, part = e & 1, row = tile * TC_BM + r;
+#pragma unroll
+    for (int g8 = 0; g8 < 4; ++g8) {
+        const int c0 = part * 32 + g8 * 8;
+        uint32_t pk[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float v[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = c0 + 2 * i + h;
+                v[h] = (row < a.M && j < a.n_in) ? a.sin[j] * (a.x[(size_t)row * a.n_in + j] - a.cin[j]) : 0.f;
+            }
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[0], v[1]);
+            pk[i] = *reinterpret_cast<const uint32_t*>(&b2);
+        }
+        *reinterpret_cast<uint4*>(act + (r >> 3) * 1024 + (c0 >> 3) * 128 + (r & 7) * 16) =
+            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+}
+
+__global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char fz[];
+    unsigned char* act[2] = {fz, fz + FZ_ACT};
+    unsigned char* stages = fz + 2 * FZ_ACT;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(fz + FZ_BAR);
+    uint64_t* full = bar;                    // [FZ_STAGES]
+    uint64_t* empty = bar + FZ_STAGES;       // [FZ_STAGES]
+    uint64_t* accf = bar + 2 * FZ_STAGES;    // [2]
+    uint64_t* epid = accf + 2;               // [2]
+    uint64_t* fin = epid + 2;                // MMAs drained on an abort
+    volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(fin + 1);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1) + 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntiles = (a.M + TC_BM - 1) / TC_BM;
+    // this CTA's tiles: blockIdx.x + k gridDim.x, k < nk; tile k uses slot k & 1
+    const int nk = ((int)blockIdx.x < ntiles) ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (tid == 0) {
+        for (int i = 0; i < FZ_STAGES; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(1));
+        }
+        for (int sl = 0; sl < 2; ++sl) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&accf[sl])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&epid[sl])), "r"(256));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(fin)), "r"(1));
+        *abort_flag = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    if (tid == 0) {
+        // ---------------------------------------------------- MMA issuer
+        uint32_t q = 0, epar[2] = {0u, 0u};
+        bool ok = true;
+        for (int k0 = 0; k0 < nk && ok; k0 += 2)
+            for (int l = 0; l < a.L && ok; ++l)
+                for (int sl = 0; sl < 2 && ok; ++sl) {
+                    if (k0 + sl >= nk) break;
+                    ok = fz_wait(&epid[sl], epar[sl], abort_flag, a.status);
+                    epar[sl] ^= 1u;
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t idesc = tc_idesc(a.N[l]);
+                    const uint32_t dcol = tmem + (uint32_t)(sl * 256);
+                    const int nch = a.K[l] / TC_BK;
+                    for (int c = 0; c < nch && ok; ++c, ++q) {
+                        const int st = (int)(q % FZ_STAGES);
+                        ok = fz_wait(&full[st], (q / FZ_STAGES) & 1u, abort_flag, a.status);
+                        if (!ok) break;
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                            const uint64_t da = tc_desc(smem_u32(act[sl]) + c * 16384 + kk * 256);
+                            const uint64_t db = tc_desc(smem_u32(stages + st * FZ_STAGE) + kk * 256);
+                            const uint32_t acc = (c > 0 || kk > 0) ? 1u : 0u;
+                            asm volatile(
+                                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
+                                "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                        }
+                        asm volatile(
+                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                smem_u32(&empty[st])));
+                    }
+                    if (ok)
+                        asm volatile(
+                            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                smem_u32(&accf[sl])));
+                }
+        if (!ok) {
+            // let every MMA already issued finish before the memory is freed
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(fin)));
+            fz_wait(fin, 0u, abort_flag, a.status, false);
+        }
+    } else if (tid == 32) {
+        // ---------------------------------------------------- weight producer
+        uint32_t qi = 0;
+        bool ok = true;
+        for (int k0 = 0; k0 < nk && ok; k0 += 2)
+            for (int l = 0; l < a.L && ok; ++l)
+                for (int sl = 0; sl < 2 && ok; ++sl) {
+                    if (k0 + sl >= nk) break;
+                    const uint32_t bytes = (uint32_t)a.N[l] * TC_BK * 2;
+                    const int nch = a.K[l] / TC_BK;
+                    for (int c = 0; c < nch && ok; ++c, ++qi) {
+                        const int st = (int)(qi % FZ_STAGES);
+                        ok = fz_wait(&empty[st], ((qi / FZ_STAGES) & 1u) ^ 1u, abort_flag, a.status);
+                        if (!ok) break;
+                        const unsigned char* src = a.w + a.woff[l] + (long long)c * bytes;
+                        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                                         smem_u32(&full[st])),
+                                     "r"(bytes)
+                                     : "memory");
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                                smem_u32(stages + st * FZ_STAGE)),
+                            "l"(src), "r"(bytes), "r"(smem_u32(&full[st]))
+                            : "memory");
+                    }
+                }
+        if (!ok) {
+            // copies still in flight land before the CTA leaves
+            for (uint32_t qq = (qi > FZ_STAGES ? qi - FZ_STAGES : 0u); qq < qi; ++qq)
+                fz_wait(&full[qq % FZ_STAGES], (qq / FZ_STAGES) & 1u, abort_flag, a.status, false);
+        }
+    } else if (warp >= 4) {
+        // ---------------------------------------------------- epilogue
+        const int e = tid - 128, q4 = warp & 3, half = (warp - 4) >> 2, r = q4 * 32 + lane;
+        for (int sl = 0; sl < 2 && sl < nk; ++sl) {
+            fz_prep(a, (int)blockIdx.x + sl * (int)gridDim.x, act[sl], e);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            fz_arrive(&epid[sl]);
+        }
+        uint32_t apar[2] = {0u, 0u};
+        bool ok = true;
+        for (int k0 = 0; k0 < nk && ok; k0 += 2)
+            for (int l = 0; l < a.L && ok; ++l)
+                for (int sl = 0; sl < 2 && ok; ++sl) {
+                    const int k = k0 + sl;
+                    if (k >= nk) break;
+                    ok = fz_wait(&accf[sl], apar[sl], abort_flag, a.status);
+                    apar[sl] ^= 1u;
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const int tile = (int)blockIdx.x + k * (int)gridDim.x;
+                    const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(sl * 256);
+                    if (l + 1 < a.L) {
+                        const int N = a.N[l], cbeg = half * (N >> 1), cend = cbeg + (N >> 1);
+                        const float* bias = a.bias + a.boff[l];
+                        for (int cb = cbeg; cb < cend; cb += 16) {
+                            uint32_t v[16];
+                            asm volatile(
+                                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+                                "%10, %11, %12, %13, %14, %15}, [%16];"
+                                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                                  "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                                : "r"(trow + (uint32_t)cb));
+                            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                            uint32_t pk[8];
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                const float z0 = __uint_as_float(v[2 * i]) + bias[cb + 2 * i];
+                                const float z1 = __uint_as_float(v[2 * i + 1]) + bias[cb + 2 * i + 1];
+                                const __nv_bfloat162 b2 = __floats2bfloat162_rn(gelu(z0), gelu(z1));
+                                pk[i] = *reinterpret_cast<const uint32_t*>(&b2);
+                            }
+                            unsigned char* dst = act[sl] + (cb >> 6) * 16384 + (r >> 3) * 1024 +
+                                                 ((cb & 63) >> 3) * 128 + (r & 7) * 16;
+                            *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                            *reinterpret_cast<uint4*>(dst + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                        }
+                    } else {
+                        const float* bias = a.bias + a.boff[l];
+                        const int row = tile * TC_BM + r;
+                        for (int cb = half * 32; cb < half * 32 + 32; cb += 16) {
+                            if (cb >= a.n_out) break;  // uniform across the warp
+                            uint32_t v[16];
+                            asm volatile(
+                                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+                                "%10, %11, %12, %13, %14, %15}, [%16];"
+                                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                                  "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                                : "r"(trow + (uint32_t)cb));
+                            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                            if (row < a.M)
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) {
+                                    const int col = cb + j;
+                                    if (col < a.n_out)
+                                        a.y[(size_t)row * a.n_out + col] =
+                                            a.sout[col] * (__uint_as_float(v[j]) + bias[col]) + a.cout[col];
+                                }
+                        }
+                        // the slot's next tile: the MMAs of this one have all completed
+                        if (k + 2 < nk) fz_prep(a, tile + 2 * (int)gridDim.x, act[sl], e);
+                    }
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    fz_arrive(&epid[sl]);
+                }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// weights of every layer into the fused kernel's chunks: layer l, K chunk c
+// (columns 64 c .. 64 c + 63) as an N_l x 64 core-matrix image of N_l * 128
+// bytes, element (n, k) at (n / 8) * 1024 + (k % 64 / 8) * 128 + (n % 8) * 16 +
+// (k % 8) * 2 within it; one thread per element
+__global__ void k_pack_fused(const __nv_bfloat16* __restrict__ pb, size_t wsrc, int N, int K,
+                             unsigned char* __restrict__ dst)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)N * K) return;
+    const int n = (int)(i / K), k = (int)(i % K);
+    const size_t o = (size_t)(k >> 6) * N * 128 + (n >> 3) * 1024 + ((k & 63) >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+    *reinterpret_cast<__nv_bfloat16*>(dst + o) = pb[wsrc + i];
+}
+
 // a0 = bf16(s_in (x - c_in)), zero beyond n_in (blockDim.x = the padded width ldo)
 __global__ void k_prep_input(const float* __restrict__ x, int batch, int n_in, int ldo, const float* __restrict__ c,
                              const float* __restrict__ sc, __nv_bfloat16* __restrict__ a0)
@@ -551,6 +856,12 @@ struct lbib_mlp {
     int64_t t = 0;                          // Adam steps
     uint32_t* status = nullptr;             // bounded-wait error word of the tensor-core kernels
     bool tc = true;                         // forward products on tcgen05
+    // fused inference (k_mlp_fused): packed weight chunks, refreshed after every update
+    unsigned char* pw = nullptr;
+    long long pwoff[FZ_MAXL] = {};
+    bool pw_dirty = true;
+    bool fused = false;                     // network shape fits the fused kernel
+    int nsm = 148;
     std::vector<void*> allocs;
 };
 
@@ -630,6 +941,51 @@ cudaError_t forward_core(lbib_mlp* net, int batch, bool store_z = true)
         }
     }
     return e;
+}
+
+// inference through k_mlp_fused: weight chunks re-packed after an update,
+// one persistent CTA per SM (at most one per 128-row tile)
+cudaError_t forward_fused(lbib_mlp* net, const float* x, int batch, float* y)
+{
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FZ_SMEM);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    if (net->pw_dirty) {
+        for (int l = 0; l < net->L; ++l) {
+            const size_t n = (size_t)net->out[l] * net->in[l];
+            k_pack_fused<<<(unsigned)((n + 255) / 256), 256, 0, net->stream>>>(net->pb, net->woff[l], net->out[l],
+                                                                               net->in[l], net->pw + net->pwoff[l]);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        net->pw_dirty = false;
+    }
+    FusedArgs a{};
+    a.x = x;
+    a.y = y;
+    a.M = batch;
+    a.n_in = net->desc.n_in;
+    a.n_out = net->desc.n_out;
+    a.L = net->L;
+    a.w = net->pw;
+    a.bias = net->p;
+    for (int l = 0; l < net->L; ++l) {
+        a.K[l] = net->in[l];
+        a.N[l] = net->out[l];
+        a.boff[l] = (int)net->boff[l];
+        a.woff[l] = net->pwoff[l];
+    }
+    a.cin = net->cin;
+    a.sin = net->sin;
+    a.cout = net->cout;
+    a.sout = net->sout;
+    a.status = net->status;
+    const int ntiles = (batch + TC_BM - 1) / TC_BM;
+    k_mlp_fused<<<std::min(ntiles, net->nsm), FZ_THREADS, FZ_SMEM, net->stream>>>(a);
+    return cudaGetLastError();
 }
 
 int splits_for(int batch)
@@ -815,7 +1171,17 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
     MA(net->loss_dev, 1);
     MA(net->status, 1);
     MA(net->pidx, net->ntrue);
+    net->fused = d->width <= FZ_MAXW && net->L <= FZ_MAXL;
+    if (net->fused) {
+        size_t bytes = 0;
+        for (int l = 0; l < net->L; ++l) {
+            net->pwoff[l] = (long long)bytes;
+            bytes += (size_t)net->out[l] * net->in[l] * 2;
+        }
+        MA(net->pw, bytes);
+    }
 #undef MA
+    cudaDeviceGetAttribute(&net->nsm, cudaDevAttrMultiProcessorCount, net->device);
     if (d->cuda_stream) {
         net->stream = static_cast<cudaStream_t>(d->cuda_stream);
     } else {
@@ -889,6 +1255,12 @@ lbib_status lbib_mlp_forward(lbib_mlp* net, const float* x, int32_t batch, float
     if (!net || !x || !y) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
     if (batch < 1 || batch > net->max_batch) return mlp_fail(LBIB_ERR_INVALID_ARG, "batch outside 1 .. max_batch");
     Guard guard(net->device);
+    if (net->tc && net->fused) {
+        cudaError_t e = forward_fused(net, x, batch, y);
+        if (e != cudaSuccess)
+            return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_forward: ") + cudaGetErrorString(e));
+        return LBIB_OK;
+    }
     dim3 blk(64, 4);
     k_prep_input<<<(batch + 3) / 4, blk, 0, net->stream>>>(x, batch, net->desc.n_in, net->in[0], net->cin, net->sin,
                                                            net->a0);
@@ -919,6 +1291,7 @@ lbib_status lbib_mlp_train_step(lbib_mlp* net, const float* x, const float* t, i
         k_adam<<<(unsigned)((net->nparam + 255) / 256), 256, 0, net->stream>>>(net->p, net->g, net->m, net->v, net->pb,
                                                                                net->nparam, lr, c1, c2);
         e = cudaGetLastError();
+        net->pw_dirty = true;
     }
     if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, net->loss_dev, 4, cudaMemcpyDeviceToDevice, net->stream);
     if (e != cudaSuccess) return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_train_step: ") + cudaGetErrorString(e));
@@ -964,6 +1337,7 @@ lbib_status lbib_mlp_apply_gradient(lbib_mlp* net, const float* grad, size_t n, 
         k_adam<<<(unsigned)((net->nparam + 255) / 256), 256, 0, net->stream>>>(net->p, net->g, net->m, net->v, net->pb,
                                                                                net->nparam, lr, c1, c2);
         e = cudaGetLastError();
+        net->pw_dirty = true;
     }
     if (e != cudaSuccess)
         return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_apply_gradient: ") + cudaGetErrorString(e));
@@ -1045,6 +1419,7 @@ lbib_status lbib_mlp_set_params(lbib_mlp* net, const float* params, size_t n)
     if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
     if (e != cudaSuccess) return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_set_params: ") + cudaGetErrorString(e));
     net->t = 0;
+    net->pw_dirty = true;
     return LBIB_OK;
 }
 
