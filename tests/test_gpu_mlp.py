@@ -182,3 +182,27 @@ def test_data_parallel_calls():
                 lambda: a.apply_gradient(grad.data_ptr(), n, 1.0, 0.0)):
         with pytest.raises(lbib.LbibError):
             bad()
+
+
+def test_fused_forward_many_tiles_ragged_and_after_new_weights():
+    """The fused inference kernel on 305 tiles of 128 rows (the last one
+    ragged; each persistent CTA runs 2 or 3 tiles, so both tensor-memory
+    slots and an odd tile count per CTA occur), against the oracle on sampled
+    rows; then again after new weights (the packed copy is refreshed)."""
+    rng = np.random.default_rng(11)
+    norm = _norm(rng)
+    B = 304 * 128 + 77
+    net = _net(norm, max_batch=B, seed=2)
+    x = rng.uniform(-1, 1, (B, N_IN)).astype(np.float32)
+    xd, yd = _dev(x), torch.zeros(B, N_OUT, device="cuda")
+    rows = np.concatenate([np.arange(0, 300), rng.choice(B, 1200, replace=False), np.arange(B - 200, B)])
+    for attempt in range(2):
+        if attempt == 1:
+            p = net.get_params()
+            net.set_params(p + rng.normal(0, 0.02, p.size).astype(np.float32))
+        net.forward(xd.data_ptr(), B, yd.data_ptr())
+        torch.cuda.synchronize()
+        layers = omlp.split_params(net.get_params(), N_IN, WIDTH, HIDDEN, N_OUT)
+        y, _, _ = omlp.forward(layers, x[rows], quantize=True, **norm)
+        assert _rel(yd.cpu().numpy()[rows], y) < 5e-3, attempt
+        assert np.isfinite(yd.cpu().numpy()).all()
