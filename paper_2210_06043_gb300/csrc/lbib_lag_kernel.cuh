@@ -820,7 +820,9 @@ __global__ void __launch_bounds__(T) k_lagrangian(Dev d, int p)
             // centroids) and the spreading of step n + 2 writes lies, per element
             // e, within the box of half-width reach_e = max(l_e / 2, 1.2) + 2
             // around its centroid (vertex / probe offset plus the stencil),
-            // widened by one node for two steps of motion.  Each stride-th element
+            // widened by a quarter node for two steps of motion (a stable lattice
+            // flow moves a marker by less than 0.1 dx per step; a larger move
+            // shows up as a read or spread miss).  Each stride-th element
             // covers itself and the following ones up to the next activating
             // element, at their current distances; the box is taken around the
             // stencil origin floor(c), one more node.  The lanes split the tiles.
@@ -836,7 +838,7 @@ __global__ void __launch_bounds__(T) k_lagrangian(Dev d, int p)
                 const R own = fmax(R(0.5) * sqrt(ex_ * ex_ + ey_ * ey_), R(1.2)) + R(2);
                 reach = fmax(reach, fmax(dxe, dye) + own);
             }
-            const int ra = (int)ceil(reach + R(1)) + 1;
+            const int ra = (int)ceil(reach + R(0.25)) + 1;
             const int i0 = max(0, sc.ix - ra), i1 = min(B.nxi - 1, sc.ix + ra);
             const int j0 = max(0, sc.jy - ra), j1 = min(L.ny - 1, sc.jy + ra);
             if (i0 <= i1 && j0 <= j1) {

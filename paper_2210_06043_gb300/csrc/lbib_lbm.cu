@@ -443,9 +443,9 @@ __global__ void k_activate(Dev d, int64_t m, int which)
     double X = 0.5 * (P[k] + P[w]), Y = 0.5 * (P[d.nmark + k] + P[d.nmark + w]);
     // positions are in instance coordinates; the box is clipped to the instance
     // half-width: vertex / probe offset plus the stencil (max(l / 2, 1.2) + 2)
-    // and one node of motion, as the membrane update's activation
+    // and a quarter node of motion, as the membrane update's activation
     const double ex_ = P[w] - P[k], ey_ = P[d.nmark + w] - P[d.nmark + k];
-    const double ra = fmax(0.5 * sqrt(ex_ * ex_ + ey_ * ey_), 1.2) + 3.0;
+    const double ra = fmax(0.5 * sqrt(ex_ * ex_ + ey_ * ey_), 1.2) + 2.25;
     int i0 = B.x0 + max(0, (int)floor(X - ra)), i1 = B.x0 + min(B.nxi - 1, (int)floor(X + ra) + 1);
     int j0 = max(0, (int)floor(Y - 0.5 - ra)), j1 = min(L.ny - 1, (int)floor(Y - 0.5 + ra) + 1);
     if (i0 > i1 || j0 > j1) return;
