@@ -215,6 +215,22 @@ lbib_status lbib_read_instance_observables(lbib_ctx* ctx, int32_t instance, lbib
  * lbib_read_instance_observables do not move. */
 lbib_status lbib_read_latest_observables(lbib_ctx* ctx, lbib_obs* out, size_t n);
 
+/* The same records without waiting: enqueues on the context stream a copy of
+ * the record of the newest step whose membrane update is already enqueued
+ * (while steps are in flight this is one step behind the lattice: the
+ * membrane update of a lattice step runs with the next step) into out, host
+ * memory of n >= n_instances records, and returns at once; the records are
+ * valid after lbib_sync (or once the stream has passed the copy).  With
+ * page-locked memory (cudaHostAlloc, a pinned torch tensor) the copy
+ * overlaps the following steps; pageable memory works but makes the call
+ * wait for the copy.  Before the first membrane update (and for instances
+ * without membranes) the records get step = -1 at once.  Unlike the waiting
+ * reads, this call does not drain the step pipeline, so a monitoring loop of
+ * lbib_advance(ctx, 1) + this call keeps the membrane update of each step
+ * overlapped with the next lattice update.  Device-side errors surface at the
+ * next waiting call. */
+lbib_status lbib_read_latest_observables_async(lbib_ctx* ctx, lbib_obs* out, size_t n);
+
 /* Decorates body `body` with ligands (before the first lbib_advance).  Sites
  * within y_cr of a wall start bound. */
 lbib_status lbib_set_adhesion(lbib_ctx* ctx, int32_t body, const lbib_adhesion_params* params);

@@ -1022,6 +1022,38 @@ lbib_status lbib_read_latest_observables(lbib_ctx* ctx, lbib_obs* out, size_t n)
     return s;
 }
 
+lbib_status lbib_read_latest_observables_async(lbib_ctx* ctx, lbib_obs* out, size_t n)
+{
+    if (!ctx || !out) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    if (n < (size_t)ctx->ninst) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than n_instances");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = finalize(ctx);
+    if (s != LBIB_OK) return s;
+    const int64_t rc = ctx->d.ring_cap, last = ctx->s_l;
+    for (int i = 0; i < ctx->ninst; ++i)
+        if (ctx->inst_nbodies[i] == 0 || last == 0) {
+            std::memset(&out[i], 0, sizeof(lbib_obs));
+            out[i].step = -1;
+        }
+    if (ctx->d.nbodies > 0 && last > 0) {
+        // every instance's ring slot last % rc; instances without membranes
+        // have no ring entries and keep the record set above
+        for (int i = 0; i < ctx->ninst;) {
+            if (ctx->inst_nbodies[i] == 0) {
+                ++i;
+                continue;
+            }
+            int j = i;
+            while (j < ctx->ninst && ctx->inst_nbodies[j] != 0) ++j;  // a run of instances with membranes
+            CK(cudaMemcpy2DAsync(out + i, sizeof(lbib_obs), ctx->d.ring + (size_t)i * rc + last % rc,
+                                 (size_t)rc * sizeof(lbib_obs), sizeof(lbib_obs), (size_t)(j - i),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+            i = j;
+        }
+    }
+    return LBIB_OK;
+}
+
 lbib_status lbib_read_observables(lbib_ctx* ctx, lbib_obs* out, size_t cap, size_t* n_out)
 {
     return lbib_read_instance_observables(ctx, 0, out, cap, n_out);

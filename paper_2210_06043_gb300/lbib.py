@@ -105,6 +105,7 @@ _SIGS = {
     "lbib_read_instance_observables": [_P, ctypes.c_int32, ctypes.POINTER(lbib_obs), ctypes.c_size_t,
                                        ctypes.POINTER(ctypes.c_size_t)],
     "lbib_read_latest_observables": [_P, ctypes.POINTER(lbib_obs), ctypes.c_size_t],
+    "lbib_read_latest_observables_async": [_P, _P, ctypes.c_size_t],
     "lbib_get_launch_config": [_P, ctypes.POINTER(lbib_launch_config)],
     "lbib_set_launch_config": [_P, ctypes.POINTER(lbib_launch_config)],
     "lbib_autotune": [_P, ctypes.c_int32, ctypes.POINTER(lbib_launch_config)],
@@ -330,6 +331,16 @@ class Solver:
         self._c(self.lib.lbib_read_latest_observables(self.ctx, buf, len(self.nxs)))
         return [dict(step=o.step, t_star=o.t_star, delta_p=o.delta_p, r=o.r, n_l=o.n_l, n_bound=o.n_bound,
                      status=o.status) for o in buf]
+
+    # numpy layout of lbib_obs (48 bytes)
+    OBS_DTYPE = np.dtype([("step", "<i8"), ("t_star", "<f8"), ("delta_p", "<f8"), ("r", "<f8"), ("n_l", "<f8"),
+                          ("n_bound", "<i4"), ("status", "<i4")])
+
+    def latest_observables_async(self, out_ptr: int):
+        """Enqueues the copy of every instance's newest record into host memory
+        at out_ptr (n_instances records of OBS_DTYPE, ideally page-locked) and
+        returns at once; valid after sync()."""
+        self._c(self.lib.lbib_read_latest_observables_async(self.ctx, ctypes.c_void_p(out_ptr), len(self.nxs)))
 
     def markers(self, body):
         xy = np.zeros(2 * self.nv[body])
