@@ -897,13 +897,6 @@ cudaError_t gemm_tc(const GemmArgs& a, cudaStream_t s)
 {
     static_assert(tc_smem_bytes(256) <= TC_SMEM_REQUEST, "tiles fit the request");
     const size_t smem = TC_SMEM_REQUEST;
-    static bool configured[4] = {false, false, false, false};
-    if (!configured[EPI]) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)TC_SMEM_REQUEST);
-        if (e != cudaSuccess) return e;
-        configured[EPI] = true;
-    }
     dim3 grid((a.M + TC_BM - 1) / TC_BM);
     k_gemm_tc<EPI><<<grid, TC_THREADS, smem, s>>>(a);
     return cudaGetLastError();
@@ -947,12 +940,6 @@ cudaError_t forward_core(lbib_mlp* net, int batch, bool store_z = true)
 // one persistent CTA per SM (at most one per 128-row tile)
 cudaError_t forward_fused(lbib_mlp* net, const float* x, int batch, float* y)
 {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FZ_SMEM);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
     if (net->pw_dirty) {
         for (int l = 0; l < net->L; ++l) {
             const size_t n = (size_t)net->out[l] * net->in[l];
@@ -1182,6 +1169,14 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
     }
 #undef MA
     cudaDeviceGetAttribute(&net->nsm, cudaDevAttrMultiProcessorCount, net->device);
+    // shared-memory opt-ins are per device: set them here, with the net's device current
+    if ((e = cudaFuncSetAttribute(k_gemm_tc<EPI_FWD_GELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)TC_SMEM_REQUEST)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_gemm_tc<EPI_FWD_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)TC_SMEM_REQUEST)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FZ_SMEM)) !=
+            cudaSuccess)
+        return bail(e, "cudaFuncSetAttribute");
     if (d->cuda_stream) {
         net->stream = static_cast<cudaStream_t>(d->cuda_stream);
     } else {
