@@ -229,3 +229,33 @@ def test_invalid_arguments_are_rejected():
     assert s.lib.lbib_read_markers(s.ctx, 5, buf.ctypes.data, 8) == lbib.LBIB_ERR_INVALID_ARG
     assert s.lib.lbib_read_markers(s.ctx, i, buf.ctypes.data, 2) == lbib.LBIB_ERR_INVALID_ARG
     s.close()
+
+
+def test_largest_membrane():
+    """A cell of 1024 vertices (the largest the ABI accepts) in FP32 against
+    the oracle; 1025 vertices are refused; in FP64 a 1024-vertex membrane
+    needs more shared memory than a block has and is reported as unsupported."""
+    nx, ny = 300, 150
+    cell = wl.circle(1024, 90.0, 75.0, 60.0)
+    cap = wl.Capillary("1024-vertex cell", nx, ny, 1.0, 1.0, 0, "fp32", 0,
+                       [wl.Body(wl.CELL, wl.DEFORMABLE, cell, ca=1e-2, beta=1e-2)])
+    o = oracle_from(cap)
+    s = lbib.from_capillary(cap)
+    o.step(60)
+    s.advance(60)
+    assert np.abs(o.body_xy(0) - s.markers(0)).max() < 1e-6
+    _, ux, uy = o.macro()
+    gux, guy = s.velocity()
+    assert rel_l2(np.stack([gux, guy]), np.stack([ux, uy])) < 1e-5
+    s.close()
+    t = lbib.Solver(nx, ny, storage=lbib.LBIB_STORE_FP32)
+    with pytest.raises(lbib.LbibError) as e:
+        t.add_membrane(wl.CELL, wl.DEFORMABLE, wl.circle(1025, 90.0, 75.0, 60.0), ca=1e-2)
+    assert e.value.status == lbib.LBIB_ERR_INVALID_ARG
+    t.close()
+    u = lbib.Solver(nx, ny, storage=lbib.LBIB_STORE_FP64)
+    u.add_membrane(wl.CELL, wl.DEFORMABLE, cell, ca=1e-2)
+    with pytest.raises(lbib.LbibError) as e:
+        u.advance(1)
+    assert e.value.status == lbib.LBIB_ERR_UNSUPPORTED
+    u.close()
