@@ -62,11 +62,11 @@ def test_forward_matches_quantized_oracle():
     net.close()
 
 
-def test_gradients_match_quantized_oracle_and_repeat_exactly():
+@pytest.mark.parametrize("B", [500, 1024])  # a ragged batch and one of whole 64-row tiles
+def test_gradients_match_quantized_oracle_and_repeat_exactly(B):
     rng = np.random.default_rng(1)
     norm = _norm(rng)
     net = _net(norm, seed=7)
-    B = 500
     x = rng.uniform(-1, 1, (B, N_IN)).astype(np.float32)
     t = (rng.normal(0, 1, (B, N_OUT)) * norm["s_out"] + norm["c_out"]).astype(np.float32)
     xd, td = _dev(x), _dev(t)
