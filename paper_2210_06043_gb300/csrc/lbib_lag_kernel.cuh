@@ -850,14 +850,23 @@ __global__ void __launch_bounds__(T) k_lagrangian(Dev d, int p)
                         const int e = lane4 + K * k;
                         fl[k] = (e < nt) ? flag2[tl[e]] : 1u;
                     }
+                    // claim the unflagged tiles, then append the claimed ones to the
+                    // list: each round's atomics are independent of one another, so
+                    // they are issued back to back instead of one round trip each
+                    uint32_t prev[8 / K];
 #pragma unroll
                     for (int k = 0; k < 8 / K; ++k) {
                         const int e = lane4 + K * k;
-                        if (e < nt && fl[k] == 0u && atomicExch(&flag2[tl[e]], 1u) == 0u) {
-                            const int pos = atomicAdd(&d.count[c2], 1);
-                            if (pos < d.list_cap) d.list[c2][pos] = tl[e];
-                            else bad |= ST_LIST_OVERFLOW;
-                        }
+                        prev[k] = (e < nt && fl[k] == 0u) ? atomicExch(&flag2[tl[e]], 1u) : 1u;
+                    }
+                    int pos[8 / K];
+#pragma unroll
+                    for (int k = 0; k < 8 / K; ++k) pos[k] = (prev[k] == 0u) ? atomicAdd(&d.count[c2], 1) : -1;
+#pragma unroll
+                    for (int k = 0; k < 8 / K; ++k) {
+                        if (pos[k] < 0) continue;
+                        if (pos[k] < d.list_cap) d.list[c2][pos[k]] = tl[lane4 + K * k];
+                        else bad |= ST_LIST_OVERFLOW;
                     }
                     if (nt < 8) break;
                 }
