@@ -440,7 +440,7 @@ def run_gpu(args):
             "marker_updates_per_s": ws * markers * K / dev_s,
             "kernel_ms": {"bulk_lattice": bulk_ms, "lagrangian": lag_ms, "near_lattice": near_ms},
             "near_tiles": desc["near_tiles"], "tiles": desc["tiles"],
-            "roofline": roofline, "e2e": e2e, "gpu_launches": 3 * K, "clocks": clk,
+            "roofline": roofline, "e2e": e2e, "gpu_launches": desc["kernels_per_step"] * K, "clocks": clk,
             "launch_config": dict(tuned, chosen_by=tuned_by),
             "wall_s_timed_region": wall}
     if batch:
@@ -483,7 +483,8 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=50,
                     help="steps of the separate profiled pass that gives the per-kernel times")
     ap.add_argument("--config", default="", help="fixed launch configuration "
-                    "lagrangian_threads,near_blocks,bulk_tiles_y,activation_stride[,bulk_nodes_per_thread] "
+                    "lagrangian_threads,near_blocks,bulk_tiles_y,activation_stride[,bulk_nodes_per_thread"
+                    "[,observables_branch]] "
                     "instead of the autotuner")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate inference timing")

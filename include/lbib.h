@@ -306,14 +306,16 @@ typedef struct {
     int32_t activation_stride;  /* every k-th element centroid schedules the near tiles around it
                                  * (over a radius grown to cover the k - 1 between): 1, 2 or 4 */
     int32_t bulk_nodes_per_thread; /* nodes each bulk lattice thread updates: 1 or 2 */
-    int32_t reserved;           /* 0 */
+    int32_t observables_branch; /* where the observables record of a step is written: 0 after the
+                                 * near update (on the membrane -> near chain), 1 on a branch of its
+                                 * own (off the chain, at normal priority) */
 } lbib_launch_config;
 
 /* Current configuration.  Like lbib_advance, the call completes the set-up
  * (no membranes can be added afterwards) and fills in the defaults: membrane
  * blocks of 256 threads when the bodies outnumber half the SMs (else 512),
  * near kernel 4 blocks per SM, one tile per bulk block and one node per bulk
- * thread, activation stride 4. */
+ * thread, activation stride 4, observables after the near update. */
 lbib_status lbib_get_launch_config(lbib_ctx* ctx, lbib_launch_config* out);
 
 /* Sets the configuration used by the following steps (re-captures the step
@@ -327,8 +329,8 @@ lbib_status lbib_set_launch_config(lbib_ctx* ctx, const lbib_launch_config* cfg)
  * events (the faster run counts), the snapshot is restored, and the fastest
  * candidate is kept.  The search is coordinate-wise, in two rounds: bulk
  * tiles per block and nodes per thread, then membrane block size, then
- * activation stride, then near-kernel blocks (2, 4, 6, 8 or 12 per SM), and
- * the same again from the first round's optimum (the bulk and near kernels
+ * activation stride, then near-kernel blocks (2, 4, 6, 8 or 12 per SM), then
+ * the observables branch, and the same again from the first round's optimum (the bulk and near kernels
  * share the SMs, so their best shapes depend on each other).  On return the
  * state, the step count and the
  * observables cursors are as on entry; *chosen (may be NULL) receives the

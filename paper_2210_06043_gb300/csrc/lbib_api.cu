@@ -102,10 +102,11 @@ struct lbib_ctx {
     std::vector<HostBody> bodies;
     bool finalized = false;
     int64_t s_f = 0, s_l = 0;  // lattice and Lagrangian steps done
-    cudaStream_t stream = nullptr, side = nullptr, cap = nullptr;
+    cudaStream_t stream = nullptr, side = nullptr, cap = nullptr, obs = nullptr;
     bool own_stream = false;
     cudaGraphExec_t unit[2][6] = {};  // [profiling][lattice step % 6]: buffer parity and flag slot
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_lag = nullptr, ev_obs = nullptr;
+    int obs_branch = 0;  // observables record: 0 after the near update, 1 on its own branch
     cudaEvent_t pe[6] = {};
     bool profiling = false, profiled_last = false;
     int near_grid = 0;  // 0: default, set at finalize
@@ -178,6 +179,7 @@ lbib_status finish_pending(lbib_ctx* ctx)
 {
     if (ctx->d.nbodies > 0 && ctx->s_l < ctx->s_f) {
         CK(launch_lagrangian(ctx->d, ctx->prec, (int)((ctx->s_l + 1) & 1), ctx->stream));
+        CK(launch_observables(ctx->d, ctx->stream, true));
         ctx->s_l += 1;
     }
     return LBIB_OK;
@@ -203,6 +205,16 @@ lbib_status capture_unit(lbib_ctx* ctx, int prof, int v)
     rec(2, ctx->cap);
     if (e == cudaSuccess) e = launch_lagrangian(d, ctx->prec, p, ctx->cap);
     rec(3, ctx->cap);
+    // observables record on a branch of its own (the near update does not wait
+    // for it; best when the chain sets the step) or after the near update
+    // (best when the bulk update does: a lone block queued at normal priority
+    // would wait behind the bulk blocks and end the step late)
+    if (ctx->obs_branch) {
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_lag, ctx->cap);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->obs, ctx->ev_lag, 0);
+        if (e == cudaSuccess) e = launch_observables(d, ctx->obs, false);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_obs, ctx->obs);
+    }
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
     rec(0, ctx->side);
     if (e == cudaSuccess) e = launch_lbm_bulk(d, ctx->prec, p, slot, ctx->side);
@@ -211,7 +223,9 @@ lbib_status capture_unit(lbib_ctx* ctx, int prof, int v)
     rec(4, ctx->cap);
     if (e == cudaSuccess) e = launch_lbm_near(d, ctx->prec, p, ctx->near_grid, ctx->cap);
     rec(5, ctx->cap);
+    if (!ctx->obs_branch && e == cudaSuccess) e = launch_observables(d, ctx->cap, true);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap, ctx->ev_join, 0);
+    if (ctx->obs_branch && e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap, ctx->ev_obs, 0);
     cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &g);
     if (e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -671,7 +685,6 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     CKC(dalloc(reg, &d.step, 1));
     CKC(dalloc(reg, &d.status, 1));
     CKC(dalloc(reg, &d.ticket, 1));
-    CKC(dalloc(reg, &d.inst_ticket, (size_t)ninst));
     CKC(dalloc(reg, &ctx->colinfo, cols.size()));
     CKC(dalloc(reg, &ctx->inst, (size_t)ninst));
     d.colinfo = ctx->colinfo;
@@ -690,7 +703,6 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     CKC(cudaMemset(d.step, 0, 8));
     CKC(cudaMemset(d.status, 0, 4));
     CKC(cudaMemset(d.ticket, 0, 4));
-    CKC(cudaMemset(d.inst_ticket, 0, (size_t)ninst * 4));
     if (P->cuda_stream) {
         ctx->stream = static_cast<cudaStream_t>(P->cuda_stream);
     } else {
@@ -699,8 +711,11 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     }
     CKC(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
     CKC(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
+    CKC(cudaStreamCreateWithFlags(&ctx->obs, cudaStreamNonBlocking));
     CKC(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    CKC(cudaEventCreateWithFlags(&ctx->ev_lag, cudaEventDisableTiming));
+    CKC(cudaEventCreateWithFlags(&ctx->ev_obs, cudaEventDisableTiming));
     for (int i = 0; i < 6; ++i) CKC(cudaEventCreate(&ctx->pe[i]));
     CKC(launch_init_populations(d, ctx->prec, 0, ctx->stream));
     CKC(cudaStreamSynchronize(ctx->stream));
@@ -1260,7 +1275,6 @@ lbib_status load_from(lbib_ctx* ctx, const char* p, cudaMemcpyKind kind)
     CK(cudaMemset(d.count, 0, 12));
     CK(cudaMemset(d.status, 0, 4));
     CK(cudaMemset(d.ticket, 0, 4));
-    CK(cudaMemset(d.inst_ticket, 0, (size_t)ctx->ninst * 4));
     CK(cudaMemcpy(d.step, &st, 8, cudaMemcpyHostToDevice));
     ctx->s_f = ctx->s_l = st;
     ctx->obs_consumed.assign(ctx->ninst, st);
@@ -1277,7 +1291,8 @@ bool valid_config(const lbib_launch_config& c)
     return (c.lagrangian_threads == 256 || c.lagrangian_threads == 512) && c.near_blocks >= 1 &&
            (c.bulk_tiles_y == 1 || c.bulk_tiles_y == 2 || c.bulk_tiles_y == 4) &&
            (c.activation_stride == 1 || c.activation_stride == 2 || c.activation_stride == 4) &&
-           (c.bulk_nodes_per_thread == 1 || c.bulk_nodes_per_thread == 2) && c.reserved == 0;
+           (c.bulk_nodes_per_thread == 1 || c.bulk_nodes_per_thread == 2) &&
+           (c.observables_branch == 0 || c.observables_branch == 1);
 }
 
 lbib_launch_config current_config(const lbib_ctx* ctx)
@@ -1288,6 +1303,7 @@ lbib_launch_config current_config(const lbib_ctx* ctx)
     c.bulk_tiles_y = ctx->d.bulk_tiles_y;
     c.activation_stride = ctx->d.act_stride;
     c.bulk_nodes_per_thread = ctx->d.bulk_nodes_per_thread;
+    c.observables_branch = ctx->obs_branch;
     return c;
 }
 
@@ -1309,6 +1325,7 @@ void apply_config(lbib_ctx* ctx, const lbib_launch_config& c)
     ctx->d.bulk_tiles_y = c.bulk_tiles_y;
     ctx->d.act_stride = c.activation_stride;
     ctx->d.bulk_nodes_per_thread = c.bulk_nodes_per_thread;
+    ctx->obs_branch = c.observables_branch;
 }
 
 }  // namespace
@@ -1427,7 +1444,7 @@ lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_co
         if (s != LBIB_OK || !valid_config(c)) return;
         if (c.lagrangian_threads == best.lagrangian_threads && c.near_blocks == best.near_blocks &&
             c.bulk_tiles_y == best.bulk_tiles_y && c.activation_stride == best.activation_stride &&
-            c.bulk_nodes_per_thread == best.bulk_nodes_per_thread)
+            c.bulk_nodes_per_thread == best.bulk_nodes_per_thread && c.observables_branch == best.observables_branch)
             return;
         float ms = 0.f;
         s = trial(c, &ms);
@@ -1465,6 +1482,12 @@ lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_co
             for (int per_sm : {2, 4, 6, 8, 12}) {
                 lbib_launch_config c = after_stride;
                 c.near_blocks = per_sm * nsm;
+                consider(c);
+            }
+            const lbib_launch_config after_near = best;
+            for (int ob : {0, 1}) {
+                lbib_launch_config c = after_near;
+                c.observables_branch = ob;
                 consider(c);
             }
         }
@@ -1514,7 +1537,7 @@ lbib_status lbib_describe(lbib_ctx* ctx, int32_t* kernels_per_step, int32_t* nea
     DeviceGuard guard(ctx->device);
     lbib_status s = finalize(ctx);
     if (s != LBIB_OK) return s;
-    if (kernels_per_step) *kernels_per_step = ctx->d.nbodies ? 3 : 1;
+    if (kernels_per_step) *kernels_per_step = ctx->d.nbodies ? 4 : 1;
     if (tiles) *tiles = ctx->d.L.ntiles;
     if (near_tiles) {
         int32_t c[3] = {0, 0, 0};
@@ -1534,6 +1557,9 @@ void lbib_destroy(lbib_ctx* ctx)
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_lag) cudaEventDestroy(ctx->ev_lag);
+    if (ctx->ev_obs) cudaEventDestroy(ctx->ev_obs);
+    if (ctx->obs) cudaStreamDestroy(ctx->obs);
     for (auto& e : ctx->pe)
         if (e) cudaEventDestroy(e);
     if (ctx->side) cudaStreamDestroy(ctx->side);

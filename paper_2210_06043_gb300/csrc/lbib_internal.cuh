@@ -159,7 +159,6 @@ struct Dev {
     const int4* colinfo;       // [ntx] ColInfo of each tile column
     int ninst;
     const InstConst* inst;     // [ninst]
-    uint32_t* inst_ticket;     // [ninst] Lagrangian blocks of the instance done this step
     // Lagrangian state
     int nbodies, nmark, nlig, nv_max;
     int lag_threads;           // Lagrangian block size: 256 or 512 (results do not depend on it)
@@ -207,6 +206,8 @@ cudaError_t launch_macro(const Dev& d, int prec, int buf, int64_t m, int x0, int
 cudaError_t launch_macro_typed(const Dev& d, int prec, int buf, int64_t m, int x0, int inx, void* ux, void* uy,
                                int dtype, cudaStream_t s);
 cudaError_t launch_lagrangian(const Dev& d, int prec, int parity, cudaStream_t s);
+// the observables record of the step the last membrane update completed
+cudaError_t launch_observables(const Dev& d, cudaStream_t s, bool urgent);
 cudaError_t launch_activate(const Dev& d, int prec, int64_t m, int which, cudaStream_t s);
 cudaError_t launch_rebuild_mask(const Dev& d, int prec, int64_t m, cudaStream_t s);
 size_t lagrangian_smem_bytes(int prec, int nv_max);

@@ -4,6 +4,67 @@
 
 namespace lbib {
 
+// Observables record of the step the membrane update has just completed
+// (Sec. 3.1): for every instance with membranes, delta p of its first cell,
+// the distance r between the area centroids of its first cell and first
+// particle, and N_L = bonds engaged / bonds engaged at t = 0, from the per-body
+// measures the membrane kernel left in body_obs.  One block; launched after
+// the membrane kernel on a branch of its own, so the lattice update of the
+// next step does not wait for it.  The record's status is the status word
+// when the record is written.
+__global__ void k_observables(Dev d)
+{
+    const int64_t n1 = *d.step;  // advanced by the membrane kernel
+    const double* all = d.body_obs[n1 & 1];
+    const double nan = __longlong_as_double(0x7ff8000000000000ULL);
+    for (int i = threadIdx.x; i < d.ninst; i += blockDim.x) {
+        const InstConst& I = d.inst[i];
+        if (I.nbodies == 0) continue;
+        lbib_obs r;
+        r.step = n1;
+        r.t_star = (double)n1 * d.uscale;
+        r.delta_p = nan;
+        r.r = nan;
+        r.n_l = nan;
+        const int fc = I.first_cell, fp = I.first_particle;
+        if (fc >= 0) r.delta_p = all[fc * BO_N + BO_DPERIM] * d.body[fc].inv_P0;
+        if (fc >= 0 && fp >= 0) {
+            const double dx = all[fc * BO_N + BO_CX] - all[fp * BO_N + BO_CX];
+            const double dy = all[fc * BO_N + BO_CY] - all[fp * BO_N + BO_CY];
+            const double r2 = dx * dx + dy * dy;
+            // FP32 square root refined by one FP64 Newton correction
+            const float sq = sqrtf((float)r2);
+            r.r = (sq > 0.f) ? (double)sq + (r2 - (double)sq * (double)sq) * (0.5 / (double)sq) : 0.0;
+        }
+        int nbt = 0, nl0 = 0;
+        for (int b = I.body0; b < I.body0 + I.nbodies; ++b)
+            if (d.body[b].adhesive) {
+                nbt += (int)all[b * BO_N + BO_NBOUND];
+                nl0 += d.body[b].nl0;
+            }
+        if (nl0 > 0) r.n_l = (double)nbt / (double)nl0;
+        r.n_bound = nbt;
+        r.status = (int32_t)atomicOr(d.status, 0u);
+        d.ring[(size_t)i * d.ring_cap + n1 % d.ring_cap] = r;
+    }
+}
+
+cudaError_t launch_observables(const Dev& d, cudaStream_t s, bool urgent)
+{
+    // urgent: at the chain's priority (on the chain, queued behind the bulk
+    // lattice blocks it would finish after them and hold up the end of the step)
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(128);
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = d.chain_priority;
+    cfg.attrs = attr;
+    cfg.numAttrs = (urgent && d.chain_priority) ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_observables, d);
+}
+
 size_t lagrangian_smem_bytes(int prec, int nv_max)
 {
     size_t r = (prec == PREC_F64) ? sizeof(double) : sizeof(float);

@@ -20,8 +20,9 @@
 //      written as markers for lattice step n + 1 together with the bit masks of
 //      the tiles their stencils touch; tiles within r_act of the new
 //      centroids are scheduled as near for lattice step n + 2;
-//   7. area, perimeter change, centroid and extent of X^{n+1}; the last block
-//      to finish writes the observables record of step n + 1 and advances n.
+//   7. area, perimeter change, centroid and extent of X^{n+1} (per body, for
+//      k_observables, which writes the record of step n + 1 right after); the
+//      last block to finish advances n.
 //
 // The kernel is latency-bound (a few hundred markers per block).  Positions
 // are carried as float-float pairs (value = hi + lo) so that differences,
@@ -988,45 +989,10 @@ __global__ void __launch_bounds__(T) k_lagrangian(Dev d, int p)
         bo[BO_XMAX] = xmax;
         bo[BO_YMIN] = ymin;
         bo[BO_YMAX] = ymax;
-        __threadfence();
-        const InstConst& I = d.inst[B.inst];
-        const uint32_t iticket = atomicAdd(&d.inst_ticket[B.inst], 1u);
-        if (iticket == (uint32_t)I.nbodies - 1u) {
-            // last block of the instance: its observables of step n + 1 (Sec. 3.1)
-            __threadfence();
-            const volatile double* all = d.body_obs[(n + 1) & 1];
-            lbib_obs r;
-            r.step = n + 1;
-            r.t_star = (double)(n + 1) * d.uscale;
-            const double nan = __longlong_as_double(0x7ff8000000000000ULL);
-            r.delta_p = nan;
-            r.r = nan;
-            r.n_l = nan;
-            const int fc = I.first_cell, fp = I.first_particle;
-            if (fc >= 0) r.delta_p = all[fc * BO_N + BO_DPERIM] * d.body[fc].inv_P0;
-            if (fc >= 0 && fp >= 0) {
-                const double dx = all[fc * BO_N + BO_CX] - all[fp * BO_N + BO_CX];
-                const double dy = all[fc * BO_N + BO_CY] - all[fp * BO_N + BO_CY];
-                const double r2 = dx * dx + dy * dy;
-                // FP32 square root refined by one FP64 Newton correction
-                const float s = sqrtf((float)r2);
-                r.r = (s > 0.f) ? (double)s + (r2 - (double)s * (double)s) * (0.5 / (double)s) : 0.0;
-            }
-            int nbt = 0, nl0 = 0;
-            for (int b = I.body0; b < I.body0 + I.nbodies; ++b)
-                if (d.body[b].adhesive) {
-                    nbt += (int)all[b * BO_N + BO_NBOUND];
-                    nl0 += d.body[b].nl0;
-                }
-            if (nl0 > 0) r.n_l = (double)nbt / (double)nl0;
-            r.n_bound = nbt;
-            r.status = (int32_t)atomicOr(d.status, 0u);
-            d.ring[(size_t)B.inst * d.ring_cap + (n + 1) % d.ring_cap] = r;
-            d.inst_ticket[B.inst] = 0u;
-            __threadfence();
-        }
-        // every block takes the batch ticket after its instance's work, so the
-        // last one sees all records written
+        // the last block to finish empties the consumed list and advances the
+        // step counter (every block has read both by now); the observables
+        // record of the step is written by k_observables, off the membrane ->
+        // near chain
         const uint32_t ticket = atomicAdd(d.ticket, 1u);
         if (ticket == (uint32_t)d.nbodies - 1u) {
             __threadfence();
