@@ -101,3 +101,17 @@ def parachute_cell(n: int, ny: int, **kw) -> SteadyShape:
     dx = wl.H_UM / ny
     kw.setdefault("beta", 1e-2)
     return steady_shape(wl.biconcave(n, 0.0, 0.0, wl.CELL_RADIUS_UM / dx), ny, **kw)
+
+
+def rescale(xy: np.ndarray, from_ny: int, to_ny: int, n: Optional[int] = None) -> np.ndarray:
+    """A shape generated in a channel from_ny nodes high, in lattice units of a
+    channel to_ny nodes high (same physical size: coordinates scale by
+    to_ny / from_ny), resampled to n vertices equally spaced in arc length
+    (n = the input's count by default), counter-clockwise, about its area
+    centroid.  Lets a shape generated on a coarse lattice serve a fine one."""
+    xy = np.asarray(xy, np.float64) * (float(to_ny) / float(from_ny))
+    n = int(n or len(xy))
+    dense = wl._resample_closed(xy, max(20000, 8 * n))
+    out = wl._ccw(wl._resample_closed(dense, n))
+    c, _ = _centroid(out)
+    return out - c
