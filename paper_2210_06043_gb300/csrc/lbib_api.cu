@@ -1537,7 +1537,7 @@ lbib_status lbib_describe(lbib_ctx* ctx, int32_t* kernels_per_step, int32_t* nea
     DeviceGuard guard(ctx->device);
     lbib_status s = finalize(ctx);
     if (s != LBIB_OK) return s;
-    if (kernels_per_step) *kernels_per_step = ctx->d.nbodies ? 4 : 1;
+    if (kernels_per_step) *kernels_per_step = ctx->d.nbodies ? 5 : 1;
     if (tiles) *tiles = ctx->d.L.ntiles;
     if (near_tiles) {
         int32_t c[3] = {0, 0, 0};

@@ -190,29 +190,28 @@ __global__ void __launch_bounds__(TX* TY* RT / NPT) k_bulk(Dev d, int p, int slo
 constexpr int NEAR_WARPS = 4;     // warps per near-kernel block; each warp updates one tile at a time
 constexpr int NEAR_STAGE = 64;    // markers a warp stages per pass
 
-// Near-membrane update: each warp walks its share of the near-tile list and
-// updates a whole 32 x 4 tile, lane l owning column l (its four nodes' loads
-// are issued together).  The tile's bit mask is read 32 words per round (one
+// Near-membrane update, in two launches.  k_spread: each warp walks its share
+// of the near-tile list and forms the force density of a whole 32 x 4 tile,
+// lane l owning column l.  The tile's bit mask is read 32 words per round (one
 // word per lane); the set bits are ranked across the warp (ascending marker
 // order) and staged in passes of NEAR_STAGE markers with their stencil
 // weights; each node then adds the forces of the staged markers whose 4 x 4
-// stencil holds it, in that order.  Warp-local throughout: no block barrier.
-template <typename S, typename R, bool MLS>
-__global__ void __launch_bounds__(32 * NEAR_WARPS) k_near(Dev d, int p)
+// stencil holds it, in that order, to the uniform body force, and the sums go
+// to fx / fy.  Warp-local throughout: no block barrier.  k_near_lbm then
+// updates the tiles' nodes with that force, a thread per node: the latency-
+// bound gather and the bandwidth-bound lattice update no longer share one
+// warp's registers, and the update runs at the bulk kernel's efficiency.
+template <typename R, bool MLS>
+__global__ void __launch_bounds__(32 * NEAR_WARPS) k_spread(Dev d, int p)
 {
     const Lattice& L = d.L;
     const int64_t m = *d.step;  // lattice step (the Lagrangian counter has reached it)
     const int c = (int)(m % 3);
     const int cnt = min(d.count[c], d.list_cap);
-    const S* __restrict__ fin = static_cast<const S*>(d.f[p]);
-    S* __restrict__ fout = static_cast<S*>(d.f[p ^ 1]);
     const int nm = d.nmark;  // marker arrays span the whole batch
     const int32_t* __restrict__ mki = d.mki[p];
     const R* __restrict__ mkf = static_cast<const R*>(d.mkf[p]);
     uint32_t* mask = d.mask[p];
-    R* drho_o = static_cast<R*>(d.drho);
-    R* ux_o = static_cast<R*>(d.ux);
-    R* uy_o = static_cast<R*>(d.uy);
     R* fx_o = static_cast<R*>(d.fx);
     R* fy_o = static_cast<R*>(d.fy);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -224,7 +223,6 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near(Dev d, int p)
     __shared__ R s_ax[NEAR_WARPS][MLS ? NEAR_STAGE : 1][4], s_cy[NEAR_WARPS][MLS ? NEAR_STAGE : 1][4];
     __shared__ R s_Fx[NEAR_WARPS][NEAR_STAGE], s_Fy[NEAR_WARPS][NEAR_STAGE];
     const R gx = lat_param<R>(L.gx, L.gx_f), gy = lat_param<R>(L.gy, L.gy_f);
-    const R omega = lat_param<R>(L.omega, L.omega_f);
     const int k0 = blockIdx.x * NEAR_WARPS + wid, kstep = gridDim.x * NEAR_WARPS;
     for (int k = k0; k < cnt; k += kstep) {
         const int t = d.list[c][k];
@@ -233,12 +231,8 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near(Dev d, int p)
         const int x = tx * TX + lane, y0 = ty * TY;
         const int xl = x - ci.x;
         bool live[TY];
-        R g[TY][9];
 #pragma unroll
-        for (int r = 0; r < TY; ++r) {
-            live[r] = (xl < ci.y && y0 + r < L.ny);
-            if (live[r]) pull<S, R>(L, fin, x, y0 + r, xl, ci.y, g[r]);  // issued before the marker gather
-        }
+        for (int r = 0; r < TY; ++r) live[r] = (xl < ci.y && y0 + r < L.ny);
         R Fx[TY], Fy[TY];
 #pragma unroll
         for (int r = 0; r < TY; ++r) {
@@ -362,19 +356,52 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near(Dev d, int p)
 #pragma unroll
         for (int r = 0; r < TY; ++r) {
             if (!live[r]) continue;
-            R drho, ux, uy;
-            collide<R>(g[r], Fx[r], Fy[r], omega, drho, ux, uy);
-            if (!(drho > R(-1)) || !isfinite(ux + uy)) atomicOr(d.status, ST_DIVERGED);
             const int base = (y0 + r) * L.nxp + x;
-#pragma unroll
-            for (int q = 0; q < 9; ++q) st<S, R>(fout + q * L.qstride + base, g[r][q]);
-            drho_o[base] = drho;
-            ux_o[base] = ux;
-            uy_o[base] = uy;
             fx_o[base] = Fx[r];
             fy_o[base] = Fy[r];
         }
-        if (lane == 0) d.fresh[t] = (int32_t)m;  // the flag is cleared by the next membrane update
+    }
+}
+
+// Forced lattice update of the near tiles of step m: one block of TX x TY
+// threads per tile (a thread per node; blocks stride over the list), with the
+// force density k_spread left in fx / fy; writes the populations, rho - 1 and
+// u for the membrane update, and marks the tile as holding step m.
+template <typename S, typename R>
+__global__ void __launch_bounds__(TX* TY) k_near_lbm(Dev d, int p)
+{
+    const Lattice& L = d.L;
+    const int64_t m = *d.step;
+    const int c = (int)(m % 3);
+    const int cnt = min(d.count[c], d.list_cap);
+    const S* __restrict__ fin = static_cast<const S*>(d.f[p]);
+    S* __restrict__ fout = static_cast<S*>(d.f[p ^ 1]);
+    const R* __restrict__ fx_i = static_cast<const R*>(d.fx);
+    const R* __restrict__ fy_i = static_cast<const R*>(d.fy);
+    R* drho_o = static_cast<R*>(d.drho);
+    R* ux_o = static_cast<R*>(d.ux);
+    R* uy_o = static_cast<R*>(d.uy);
+    const R omega = lat_param<R>(L.omega, L.omega_f);
+    for (int k = blockIdx.x; k < cnt; k += gridDim.x) {
+        const int t = d.list[c][k];
+        const int tx = t % L.ntx, ty = t / L.ntx;
+        const int4 ci = d.colinfo[tx];
+        const int x = tx * TX + threadIdx.x, y = ty * TY + threadIdx.y;
+        const int xl = x - ci.x;
+        if (xl < ci.y && y < L.ny) {
+            R g[9];
+            pull<S, R>(L, fin, x, y, xl, ci.y, g);
+            const int base = y * L.nxp + x;
+            R drho, ux, uy;
+            collide<R>(g, fx_i[base], fy_i[base], omega, drho, ux, uy);
+            if (!(drho > R(-1)) || !isfinite(ux + uy)) atomicOr(d.status, ST_DIVERGED);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) st<S, R>(fout + q * L.qstride + base, g[q]);
+            drho_o[base] = drho;
+            ux_o[base] = ux;
+            uy_o[base] = uy;
+        }
+        if (threadIdx.x == 0 && threadIdx.y == 0) d.fresh[t] = (int32_t)m;  // cleared by the next membrane update
     }
 }
 
@@ -552,10 +579,19 @@ cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, cudaSt
     cfg.attrs = attr;
     cfg.numAttrs = d.chain_priority ? 1 : 0;
     cudaError_t e = cudaSuccess;
+    int nsm = 148;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     by_store(d.store, [&](auto sp, auto rp) {
         LBIB_TYPES(sp, rp);
-        if (d.L.transfer == LBIB_TRANSFER_MLS) e = cudaLaunchKernelEx(&cfg, k_near<S, R, true>, d, parity);
-        else e = cudaLaunchKernelEx(&cfg, k_near<S, R, false>, d, parity);
+        if (d.L.transfer == LBIB_TRANSFER_MLS) e = cudaLaunchKernelEx(&cfg, k_spread<R, true>, d, parity);
+        else e = cudaLaunchKernelEx(&cfg, k_spread<R, false>, d, parity);
+        if (e != cudaSuccess) return;
+        // one tile per block at a time, up to 16 resident blocks of 128 threads per SM
+        cfg.gridDim = dim3((unsigned)std::max(1, std::min(d.list_cap, 16 * nsm)));
+        cfg.blockDim = dim3(TX, TY);
+        e = cudaLaunchKernelEx(&cfg, k_near_lbm<S, R>, d, parity);
     });
     return e;
 }

@@ -115,7 +115,7 @@ def test_sweep_full_size_fp32_sampled():
     n = 40
     batch.advance(n)
     d = batch.describe()
-    assert d["kernels_per_step"] == 4
+    assert d["kernels_per_step"] == 5
     latest = batch.latest_observables()
     records = [batch.observables(instance=inst) for inst in range(len(caps))]
     for inst, obs in enumerate(records):
