@@ -215,12 +215,16 @@ lbib_status lbib_read_instance_observables(lbib_ctx* ctx, int32_t instance, lbib
  * lbib_read_instance_observables do not move. */
 lbib_status lbib_read_latest_observables(lbib_ctx* ctx, lbib_obs* out, size_t n);
 
-/* The same records without waiting: enqueues on the context stream a copy of
- * the record of the newest step whose membrane update is already enqueued
- * (while steps are in flight this is one step behind the lattice: the
- * membrane update of a lattice step runs with the next step) into out, host
- * memory of n >= n_instances records, and returns at once; the records are
- * valid after lbib_sync (or once the stream has passed the copy).  With
+/* The same records without waiting: enqueues a copy of the record of the
+ * newest step whose membrane update is already enqueued (while steps are in
+ * flight this is one step behind the lattice: the membrane update of a
+ * lattice step runs with the next step) into out, host memory of
+ * n >= n_instances records, and returns at once.  The copy runs on a stream
+ * of the library's own, after the work enqueued so far on the context
+ * stream; steps enqueued later do not wait for it, except the step that
+ * would overwrite a record still being copied (the ring of obs_capacity
+ * records per instance has wrapped).  The records are valid after lbib_sync
+ * or any waiting read (not merely after a wait on the context stream).  With
  * page-locked memory (cudaHostAlloc, a pinned torch tensor) the copy
  * overlaps the following steps; pageable memory works but makes the call
  * wait for the copy.  Before the first membrane update (and for instances
@@ -309,13 +313,19 @@ typedef struct {
     int32_t observables_branch; /* where the observables record of a step is written: 0 after the
                                  * near update (on the membrane -> near chain), 1 on a branch of its
                                  * own (off the chain, at normal priority) */
+    int32_t chain_programmatic; /* 1: the force gather, the near update and the observables kernel
+                                 * on the chain are launched as programmatic dependents of the
+                                 * kernel before them (scheduled while it finishes, so the launch
+                                 * latency leaves the chain; their blocks then hold SM slots the
+                                 * bulk update could use); 0: plain stream order */
 } lbib_launch_config;
 
 /* Current configuration.  Like lbib_advance, the call completes the set-up
  * (no membranes can be added afterwards) and fills in the defaults: membrane
  * blocks of 256 threads when the bodies outnumber half the SMs (else 512),
  * near kernel 4 blocks per SM, one tile per bulk block and one node per bulk
- * thread, activation stride 4, observables after the near update. */
+ * thread, activation stride 4, observables after the near update, plain
+ * stream order on the chain. */
 lbib_status lbib_get_launch_config(lbib_ctx* ctx, lbib_launch_config* out);
 
 /* Sets the configuration used by the following steps (re-captures the step
@@ -330,7 +340,7 @@ lbib_status lbib_set_launch_config(lbib_ctx* ctx, const lbib_launch_config* cfg)
  * candidate is kept.  The search is coordinate-wise, in two rounds: bulk
  * tiles per block and nodes per thread, then membrane block size, then
  * activation stride, then near-kernel blocks (2, 4, 6, 8 or 12 per SM), then
- * the observables branch, and the same again from the first round's optimum (the bulk and near kernels
+ * the observables branch, then programmatic launch on the chain, and the same again from the first round's optimum (the bulk and near kernels
  * share the SMs, so their best shapes depend on each other).  On return the
  * state, the step count and the
  * observables cursors are as on entry; *chosen (may be NULL) receives the

@@ -107,6 +107,14 @@ struct lbib_ctx {
     cudaGraphExec_t unit[2][6] = {};  // [profiling][lattice step % 6]: buffer parity and flag slot
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_lag = nullptr, ev_obs = nullptr;
     int obs_branch = 0;  // observables record: 0 after the near update, 1 on its own branch
+    int chain_pdl = 0;   // chain kernels as programmatic dependents of the kernel before them
+    // copies of lbib_read_latest_observables_async run on `copy` after ev_step;
+    // ev_copy marks the newest; copy_first is the oldest step whose copy may
+    // still be in flight (its ring slot is written again ring_cap steps later)
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ev_step = nullptr, ev_copy = nullptr;
+    bool copy_pending = false;
+    int64_t copy_first = 0;
     cudaEvent_t pe[6] = {};
     bool profiling = false, profiled_last = false;
     int near_grid = 0;  // 0: default, set at finalize
@@ -175,11 +183,25 @@ lbib_status check_status(lbib_ctx* ctx)
 
 bool valid_instance(const lbib_ctx* ctx, int32_t i) { return i >= 0 && i < ctx->ninst; }
 
+// Before the stream gets the membrane update of step `step` (which writes the
+// ring slot step % ring_cap): wait for the observables copies in flight if one
+// of them may read that slot.
+lbib_status guard_ring(lbib_ctx* ctx, int64_t step)
+{
+    if (ctx->copy_pending && step >= ctx->copy_first + ctx->d.ring_cap) {
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copy, 0));
+        ctx->copy_pending = false;
+    }
+    return LBIB_OK;
+}
+
 lbib_status finish_pending(lbib_ctx* ctx)
 {
     if (ctx->d.nbodies > 0 && ctx->s_l < ctx->s_f) {
+        lbib_status s = guard_ring(ctx, ctx->s_l + 1);
+        if (s != LBIB_OK) return s;
         CK(launch_lagrangian(ctx->d, ctx->prec, (int)((ctx->s_l + 1) & 1), ctx->stream));
-        CK(launch_observables(ctx->d, ctx->stream, true));
+        CK(launch_observables(ctx->d, ctx->stream, true, ctx->chain_pdl != 0));  // after the membrane kernel
         ctx->s_l += 1;
     }
     return LBIB_OK;
@@ -212,7 +234,7 @@ lbib_status capture_unit(lbib_ctx* ctx, int prof, int v)
     if (ctx->obs_branch) {
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_lag, ctx->cap);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->obs, ctx->ev_lag, 0);
-        if (e == cudaSuccess) e = launch_observables(d, ctx->obs, false);
+        if (e == cudaSuccess) e = launch_observables(d, ctx->obs, false, false);
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_obs, ctx->obs);
     }
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
@@ -221,9 +243,13 @@ lbib_status capture_unit(lbib_ctx* ctx, int prof, int v)
     rec(1, ctx->side);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
     rec(4, ctx->cap);
-    if (e == cudaSuccess) e = launch_lbm_near(d, ctx->prec, p, ctx->near_grid, ctx->cap);
+    // optionally programmatic dependents of the kernel before them on the
+    // chain (launch latency hidden behind its tail), never in the profiling
+    // graphs, whose timing events sit between the kernels
+    const bool pdl = ctx->chain_pdl && !prof;
+    if (e == cudaSuccess) e = launch_lbm_near(d, ctx->prec, p, ctx->near_grid, ctx->cap, pdl);
     rec(5, ctx->cap);
-    if (!ctx->obs_branch && e == cudaSuccess) e = launch_observables(d, ctx->cap, true);
+    if (!ctx->obs_branch && e == cudaSuccess) e = launch_observables(d, ctx->cap, true, pdl);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap, ctx->ev_join, 0);
     if (ctx->obs_branch && e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap, ctx->ev_obs, 0);
     cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &g);
@@ -560,6 +586,8 @@ lbib_status pre_read(lbib_ctx* ctx)
     s = finish_pending(ctx);
     if (s != LBIB_OK) return s;
     CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaStreamSynchronize(ctx->copy));
+    ctx->copy_pending = false;
     return check_status(ctx);
 }
 
@@ -712,6 +740,9 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     CKC(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
     CKC(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
     CKC(cudaStreamCreateWithFlags(&ctx->obs, cudaStreamNonBlocking));
+    CKC(cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
+    CKC(cudaEventCreateWithFlags(&ctx->ev_step, cudaEventDisableTiming));
+    CKC(cudaEventCreateWithFlags(&ctx->ev_copy, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&ctx->ev_lag, cudaEventDisableTiming));
@@ -816,13 +847,15 @@ lbib_status lbib_advance(lbib_ctx* ctx, int64_t nsteps)
     if (ctx->s_l == ctx->s_f) {  // open the pipeline: lattice step s_f alone
         int p = (int)(ctx->s_f & 1);
         CK(launch_lbm_bulk(d, ctx->prec, p, (int)(ctx->s_f % 3), ctx->stream));
-        CK(launch_lbm_near(d, ctx->prec, p, ctx->near_grid, ctx->stream));
+        CK(launch_lbm_near(d, ctx->prec, p, ctx->near_grid, ctx->stream, false));
         ctx->s_f += 1;
         nsteps -= 1;
         ctx->profiled_last = false;
     }
     const int prof = ctx->profiling ? 1 : 0;
     for (int64_t k = 0; k < nsteps; ++k) {
+        s = guard_ring(ctx, ctx->s_l + 1);
+        if (s != LBIB_OK) return s;
         CK(cudaGraphLaunch(ctx->unit[prof][ctx->s_f % 6], ctx->stream));
         ctx->s_f += 1;
         ctx->s_l += 1;
@@ -1051,8 +1084,12 @@ lbib_status lbib_read_latest_observables_async(lbib_ctx* ctx, lbib_obs* out, siz
             out[i].step = -1;
         }
     if (ctx->d.nbodies > 0 && last > 0) {
-        // every instance's ring slot last % rc; instances without membranes
-        // have no ring entries and keep the record set above
+        // every instance's ring slot last % rc, copied on the copy stream after
+        // the steps enqueued so far, so the next step need not wait for it;
+        // instances without membranes have no ring entries and keep the record
+        // set above
+        CK(cudaEventRecord(ctx->ev_step, ctx->stream));
+        CK(cudaStreamWaitEvent(ctx->copy, ctx->ev_step, 0));
         for (int i = 0; i < ctx->ninst;) {
             if (ctx->inst_nbodies[i] == 0) {
                 ++i;
@@ -1062,8 +1099,13 @@ lbib_status lbib_read_latest_observables_async(lbib_ctx* ctx, lbib_obs* out, siz
             while (j < ctx->ninst && ctx->inst_nbodies[j] != 0) ++j;  // a run of instances with membranes
             CK(cudaMemcpy2DAsync(out + i, sizeof(lbib_obs), ctx->d.ring + (size_t)i * rc + last % rc,
                                  (size_t)rc * sizeof(lbib_obs), sizeof(lbib_obs), (size_t)(j - i),
-                                 cudaMemcpyDeviceToHost, ctx->stream));
+                                 cudaMemcpyDeviceToHost, ctx->copy));
             i = j;
+        }
+        CK(cudaEventRecord(ctx->ev_copy, ctx->copy));
+        if (!ctx->copy_pending) {
+            ctx->copy_pending = true;
+            ctx->copy_first = last;
         }
     }
     return LBIB_OK;
@@ -1292,7 +1334,8 @@ bool valid_config(const lbib_launch_config& c)
            (c.bulk_tiles_y == 1 || c.bulk_tiles_y == 2 || c.bulk_tiles_y == 4) &&
            (c.activation_stride == 1 || c.activation_stride == 2 || c.activation_stride == 4) &&
            (c.bulk_nodes_per_thread == 1 || c.bulk_nodes_per_thread == 2) &&
-           (c.observables_branch == 0 || c.observables_branch == 1);
+           (c.observables_branch == 0 || c.observables_branch == 1) &&
+           (c.chain_programmatic == 0 || c.chain_programmatic == 1);
 }
 
 lbib_launch_config current_config(const lbib_ctx* ctx)
@@ -1304,6 +1347,7 @@ lbib_launch_config current_config(const lbib_ctx* ctx)
     c.activation_stride = ctx->d.act_stride;
     c.bulk_nodes_per_thread = ctx->d.bulk_nodes_per_thread;
     c.observables_branch = ctx->obs_branch;
+    c.chain_programmatic = ctx->chain_pdl;
     return c;
 }
 
@@ -1326,6 +1370,7 @@ void apply_config(lbib_ctx* ctx, const lbib_launch_config& c)
     ctx->d.act_stride = c.activation_stride;
     ctx->d.bulk_nodes_per_thread = c.bulk_nodes_per_thread;
     ctx->obs_branch = c.observables_branch;
+    ctx->chain_pdl = c.chain_programmatic;
 }
 
 }  // namespace
@@ -1444,7 +1489,8 @@ lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_co
         if (s != LBIB_OK || !valid_config(c)) return;
         if (c.lagrangian_threads == best.lagrangian_threads && c.near_blocks == best.near_blocks &&
             c.bulk_tiles_y == best.bulk_tiles_y && c.activation_stride == best.activation_stride &&
-            c.bulk_nodes_per_thread == best.bulk_nodes_per_thread && c.observables_branch == best.observables_branch)
+            c.bulk_nodes_per_thread == best.bulk_nodes_per_thread && c.observables_branch == best.observables_branch &&
+            c.chain_programmatic == best.chain_programmatic)
             return;
         float ms = 0.f;
         s = trial(c, &ms);
@@ -1488,6 +1534,12 @@ lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_co
             for (int ob : {0, 1}) {
                 lbib_launch_config c = after_near;
                 c.observables_branch = ob;
+                consider(c);
+            }
+            const lbib_launch_config after_obs = best;
+            for (int pdl : {0, 1}) {
+                lbib_launch_config c = after_obs;
+                c.chain_programmatic = pdl;
                 consider(c);
             }
         }
@@ -1553,6 +1605,7 @@ void lbib_destroy(lbib_ctx* ctx)
     if (!ctx) return;
     DeviceGuard guard(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->copy) cudaStreamSynchronize(ctx->copy);
     destroy_graphs(ctx);
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
@@ -1560,6 +1613,9 @@ void lbib_destroy(lbib_ctx* ctx)
     if (ctx->ev_lag) cudaEventDestroy(ctx->ev_lag);
     if (ctx->ev_obs) cudaEventDestroy(ctx->ev_obs);
     if (ctx->obs) cudaStreamDestroy(ctx->obs);
+    if (ctx->copy) cudaStreamDestroy(ctx->copy);
+    if (ctx->ev_step) cudaEventDestroy(ctx->ev_step);
+    if (ctx->ev_copy) cudaEventDestroy(ctx->ev_copy);
     for (auto& e : ctx->pe)
         if (e) cudaEventDestroy(e);
     if (ctx->side) cudaStreamDestroy(ctx->side);

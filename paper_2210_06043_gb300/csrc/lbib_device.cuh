@@ -12,6 +12,14 @@
 namespace lbib {
 
 // D2Q9 weights printed after Eq. 3 (rest 4/9, axis 1/9, diagonal 1/36).
+// Programmatic dependent launch: pdl_wait blocks until the grids this one
+// depends on have completed and their writes are visible (it returns at once
+// when the launch had no programmatic dependency); pdl_trigger lets the
+// dependent grid be scheduled once every block of this one has issued it or
+// exited.  Every thread of a block issues both at the same point.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <typename R>
 __device__ __forceinline__ R wq(int q)
 {

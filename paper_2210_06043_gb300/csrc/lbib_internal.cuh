@@ -198,7 +198,9 @@ struct Dev {
 // (defined in lbib_lbm.cu and lbib_lag.cu; `prec` selects FP64 or FP32)
 // bulk update of lattice step m: parity = m & 1, slot = m % 3
 cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, int slot, cudaStream_t s);
-cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, cudaStream_t s);
+// pdl: k_spread and k_near_lbm are launched as programmatic dependents of the
+// kernel enqueued before them (the membrane update, then k_spread)
+cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, cudaStream_t s, bool pdl);
 cudaError_t launch_init_populations(const Dev& d, int prec, int buf, cudaStream_t s);
 // moments of one instance (node columns [x0, x0 + inx)) into [ny][inx] arrays
 cudaError_t launch_macro(const Dev& d, int prec, int buf, int64_t m, int x0, int inx, double* rho, double* ux,
@@ -207,7 +209,8 @@ cudaError_t launch_macro_typed(const Dev& d, int prec, int buf, int64_t m, int x
                                int dtype, cudaStream_t s);
 cudaError_t launch_lagrangian(const Dev& d, int prec, int parity, cudaStream_t s);
 // the observables record of the step the last membrane update completed
-cudaError_t launch_observables(const Dev& d, cudaStream_t s, bool urgent);
+// pdl: a programmatic dependent of the kernel enqueued before it
+cudaError_t launch_observables(const Dev& d, cudaStream_t s, bool urgent, bool pdl);
 cudaError_t launch_activate(const Dev& d, int prec, int64_t m, int which, cudaStream_t s);
 cudaError_t launch_rebuild_mask(const Dev& d, int prec, int64_t m, cudaStream_t s);
 size_t lagrangian_smem_bytes(int prec, int nv_max);

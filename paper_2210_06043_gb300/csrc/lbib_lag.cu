@@ -14,6 +14,7 @@ namespace lbib {
 // when the record is written.
 __global__ void k_observables(Dev d)
 {
+    pdl_wait();
     const int64_t n1 = *d.step;  // advanced by the membrane kernel
     const double* all = d.body_obs[n1 & 1];
     const double nan = __longlong_as_double(0x7ff8000000000000ULL);
@@ -49,19 +50,26 @@ __global__ void k_observables(Dev d)
     }
 }
 
-cudaError_t launch_observables(const Dev& d, cudaStream_t s, bool urgent)
+cudaError_t launch_observables(const Dev& d, cudaStream_t s, bool urgent, bool pdl)
 {
     // urgent: at the chain's priority (on the chain, queued behind the bulk
     // lattice blocks it would finish after them and hold up the end of the step)
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     cfg.gridDim = dim3(1);
     cfg.blockDim = dim3(128);
     cfg.stream = s;
-    attr[0].id = cudaLaunchAttributePriority;
-    attr[0].val.priority = d.chain_priority;
+    int na = 0;
+    if (urgent && d.chain_priority) {
+        attr[na].id = cudaLaunchAttributePriority;
+        attr[na++].val.priority = d.chain_priority;
+    }
+    if (pdl) {
+        attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[na++].val.programmaticStreamSerializationAllowed = 1;
+    }
     cfg.attrs = attr;
-    cfg.numAttrs = (urgent && d.chain_priority) ? 1 : 0;
+    cfg.numAttrs = na;
     return cudaLaunchKernelEx(&cfg, k_observables, d);
 }
 

@@ -970,6 +970,7 @@ __global__ void __launch_bounds__(T) k_lagrangian(Dev d, int p)
         xmax = -rv[3];
         ymax = -rv[4];
     }
+    pdl_trigger();  // the force gather may be scheduled; it waits for this grid to complete
     if (miss & 1u) bad |= ST_READ_MISS;
     if (miss & 2u) bad |= ST_SPREAD_MISS;
     if (bad) atomicOr(d.status, bad);

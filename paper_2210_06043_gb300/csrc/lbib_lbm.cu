@@ -204,6 +204,7 @@ constexpr int NEAR_STAGE = 64;    // markers a warp stages per pass
 template <typename R, bool MLS>
 __global__ void __launch_bounds__(32 * NEAR_WARPS) k_spread(Dev d, int p)
 {
+    pdl_wait();  // step counter, list and markers come from the membrane update
     const Lattice& L = d.L;
     const int64_t m = *d.step;  // lattice step (the Lagrangian counter has reached it)
     const int c = (int)(m % 3);
@@ -361,6 +362,7 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_spread(Dev d, int p)
             fy_o[base] = Fy[r];
         }
     }
+    pdl_trigger();
 }
 
 // Forced lattice update of the near tiles of step m: one block of TX x TY
@@ -370,6 +372,7 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_spread(Dev d, int p)
 template <typename S, typename R>
 __global__ void __launch_bounds__(TX* TY) k_near_lbm(Dev d, int p)
 {
+    pdl_wait();  // the force density comes from k_spread
     const Lattice& L = d.L;
     const int64_t m = *d.step;
     const int c = (int)(m % 3);
@@ -403,6 +406,7 @@ __global__ void __launch_bounds__(TX* TY) k_near_lbm(Dev d, int p)
         }
         if (threadIdx.x == 0 && threadIdx.y == 0) d.fresh[t] = (int32_t)m;  // cleared by the next membrane update
     }
+    pdl_trigger();
 }
 
 template <typename S, typename R>
@@ -566,18 +570,25 @@ cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, int slot, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, cudaStream_t s)
+cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, cudaStream_t s, bool pdl)
 {
     (void)prec;
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(32 * NEAR_WARPS);
     cfg.stream = s;
-    attr[0].id = cudaLaunchAttributePriority;
-    attr[0].val.priority = d.chain_priority;
+    int na = 0;
+    if (d.chain_priority) {
+        attr[na].id = cudaLaunchAttributePriority;
+        attr[na++].val.priority = d.chain_priority;
+    }
+    if (pdl) {
+        attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[na++].val.programmaticStreamSerializationAllowed = 1;
+    }
     cfg.attrs = attr;
-    cfg.numAttrs = d.chain_priority ? 1 : 0;
+    cfg.numAttrs = na;
     cudaError_t e = cudaSuccess;
     int nsm = 148;
     int dev = 0;

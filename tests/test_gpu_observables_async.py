@@ -55,3 +55,24 @@ def test_async_records_match_the_ring_and_keep_the_pipeline():
     assert host["step"][0] == K
     s.close()
     p.close()
+
+
+def test_async_copies_survive_a_wrapping_ring():
+    """With a ring of one record per instance every step overwrites the slot
+    the previous read copies from: the step must wait for that copy, so the
+    records equal those read through a ring that does not wrap."""
+    K = 30
+    bufs = []
+    for cap in (256, 1):
+        s = lbib.from_capillaries(_caps(), obs_capacity=cap)
+        buf = torch.zeros((K, 3 * lbib.Solver.OBS_DTYPE.itemsize), dtype=torch.uint8).pin_memory()
+        for k in range(K):
+            s.advance(1)
+            s.latest_observables_async(buf[k].data_ptr())
+        s.advance(3)  # steps after the last read overwrite its slot too
+        s.sync()
+        bufs.append(buf.numpy().copy())
+        s.close()
+    assert np.array_equal(bufs[0], bufs[1])
+    recs = bufs[1].view(lbib.Solver.OBS_DTYPE).reshape(K, 3)
+    assert recs[1:, 0]["step"].tolist() == list(range(1, K))
