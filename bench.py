@@ -331,8 +331,9 @@ def run_gpu(args):
         tuned = dict(s.launch_config())
         tuned_by = "--config"
     else:
-        tuned = s.autotune(steps_per_trial=args.tune_steps)  # leaves the state unchanged
-        tuned_by = f"lbib_autotune, {args.tune_steps} steps per trial"
+        tune_steps = args.tune_steps or (200 if args.workload == "production" else 50)
+        tuned = s.autotune(steps_per_trial=tune_steps)  # leaves the state unchanged
+        tuned_by = f"lbib_autotune, {tune_steps} steps per trial"
     # populations beyond L2 (sweep): no flush; else a 256 MiB buffer rewritten between steps
     pop_bytes = lbib.roofline_bytes_per_node(store) * nodes
     flush = None if pop_bytes > (256 << 20) else torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -477,7 +478,9 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=50, help="steps per capillary of the plain-solver timing")
     ap.add_argument("--cpu-nodes", type=float, default=1.0e8,
                     help="node updates of the CPU oracle sample (about 15 s at 7 MLUPS)")
-    ap.add_argument("--tune-steps", type=int, default=50, help="steps per autotuner trial")
+    ap.add_argument("--tune-steps", type=int, default=0,
+                    help="steps per autotuner trial (default: 50 for the sweep, 200 for the production capillary, "
+                         "whose steps are short enough for timing noise to decide between close candidates)")
     ap.add_argument("--storage", default="", choices=["", "fp32", "bf16", "fp16", "fp64"],
                     help="population storage (default: the workload's, FP32)")
     ap.add_argument("--profile-steps", type=int, default=50,

@@ -112,6 +112,7 @@ def test_sweep_full_size_fp32_sampled():
     compared bit-for-bit with lone runs and one with the oracle."""
     caps = wl.sweep_capillaries()
     batch = lbib.from_capillaries(caps)
+    batch.autotune(steps_per_trial=10)  # as the benchmark does before it times the sweep
     n = 40
     batch.advance(n)
     d = batch.describe()
