@@ -113,6 +113,9 @@ struct lbib_ctx {
     // still be in flight (its ring slot is written again ring_cap steps later)
     cudaStream_t copy = nullptr;
     cudaEvent_t ev_step = nullptr, ev_copy = nullptr;
+    // activation of the step after next: a branch of the step graph
+    cudaStream_t act = nullptr;
+    cudaEvent_t ev_act = nullptr;
     bool copy_pending = false;
     int64_t copy_first = 0;
     cudaEvent_t pe[6] = {};
@@ -201,6 +204,7 @@ lbib_status finish_pending(lbib_ctx* ctx)
         lbib_status s = guard_ring(ctx, ctx->s_l + 1);
         if (s != LBIB_OK) return s;
         CK(launch_lagrangian(ctx->d, ctx->prec, (int)((ctx->s_l + 1) & 1), ctx->stream));
+        CK(launch_activate_next(ctx->d, ctx->stream));
         CK(launch_observables(ctx->d, ctx->stream, true, ctx->chain_pdl != 0));  // after the membrane kernel
         ctx->s_l += 1;
     }
@@ -227,12 +231,17 @@ lbib_status capture_unit(lbib_ctx* ctx, int prof, int v)
     rec(2, ctx->cap);
     if (e == cudaSuccess) e = launch_lagrangian(d, ctx->prec, p, ctx->cap);
     rec(3, ctx->cap);
+    // near tiles of lattice step m + 1 on a branch of their own (first needed
+    // by the next graph)
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_lag, ctx->cap);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->act, ctx->ev_lag, 0);
+    if (e == cudaSuccess) e = launch_activate_next(d, ctx->act);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_act, ctx->act);
     // observables record on a branch of its own (the near update does not wait
     // for it; best when the chain sets the step) or after the near update
     // (best when the bulk update does: a lone block queued at normal priority
     // would wait behind the bulk blocks and end the step late)
     if (ctx->obs_branch) {
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_lag, ctx->cap);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->obs, ctx->ev_lag, 0);
         if (e == cudaSuccess) e = launch_observables(d, ctx->obs, false, false);
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_obs, ctx->obs);
@@ -252,6 +261,7 @@ lbib_status capture_unit(lbib_ctx* ctx, int prof, int v)
     if (!ctx->obs_branch && e == cudaSuccess) e = launch_observables(d, ctx->cap, true, pdl);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap, ctx->ev_join, 0);
     if (ctx->obs_branch && e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap, ctx->ev_obs, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap, ctx->ev_act, 0);
     cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &g);
     if (e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -741,6 +751,8 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     CKC(cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking));
     CKC(cudaStreamCreateWithFlags(&ctx->obs, cudaStreamNonBlocking));
     CKC(cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
+    CKC(cudaStreamCreateWithFlags(&ctx->act, cudaStreamNonBlocking));
+    CKC(cudaEventCreateWithFlags(&ctx->ev_act, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&ctx->ev_step, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&ctx->ev_copy, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
@@ -1589,7 +1601,7 @@ lbib_status lbib_describe(lbib_ctx* ctx, int32_t* kernels_per_step, int32_t* nea
     DeviceGuard guard(ctx->device);
     lbib_status s = finalize(ctx);
     if (s != LBIB_OK) return s;
-    if (kernels_per_step) *kernels_per_step = ctx->d.nbodies ? 5 : 1;
+    if (kernels_per_step) *kernels_per_step = ctx->d.nbodies ? 6 : 1;
     if (tiles) *tiles = ctx->d.L.ntiles;
     if (near_tiles) {
         int32_t c[3] = {0, 0, 0};
@@ -1614,6 +1626,8 @@ void lbib_destroy(lbib_ctx* ctx)
     if (ctx->ev_obs) cudaEventDestroy(ctx->ev_obs);
     if (ctx->obs) cudaStreamDestroy(ctx->obs);
     if (ctx->copy) cudaStreamDestroy(ctx->copy);
+    if (ctx->act) cudaStreamDestroy(ctx->act);
+    if (ctx->ev_act) cudaEventDestroy(ctx->ev_act);
     if (ctx->ev_step) cudaEventDestroy(ctx->ev_step);
     if (ctx->ev_copy) cudaEventDestroy(ctx->ev_copy);
     for (auto& e : ctx->pe)

@@ -211,6 +211,8 @@ cudaError_t launch_lagrangian(const Dev& d, int prec, int parity, cudaStream_t s
 // the observables record of the step the last membrane update completed
 // pdl: a programmatic dependent of the kernel enqueued before it
 cudaError_t launch_observables(const Dev& d, cudaStream_t s, bool urgent, bool pdl);
+// near tiles of the step after next, from the positions the membrane kernel stored
+cudaError_t launch_activate_next(const Dev& d, cudaStream_t s);
 cudaError_t launch_activate(const Dev& d, int prec, int64_t m, int which, cudaStream_t s);
 cudaError_t launch_rebuild_mask(const Dev& d, int prec, int64_t m, cudaStream_t s);
 size_t lagrangian_smem_bytes(int prec, int nv_max);

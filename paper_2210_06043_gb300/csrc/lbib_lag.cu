@@ -73,6 +73,75 @@ cudaError_t launch_observables(const Dev& d, cudaStream_t s, bool urgent, bool p
     return cudaLaunchKernelEx(&cfg, k_observables, d);
 }
 
+// Near tiles of lattice step m + 1, m = *d.step the step the membrane update
+// has just reached, from the X^m it stored: every stencil the membrane update
+// of step m + 1 reads (vertices, probes, the new element centroids) and the
+// spreading of step m + 1 writes lies, per element e, within the box of
+// half-width reach_e = max(l_e / 2, 1.2) + 2 around its centroid (vertex /
+// probe offset plus the stencil), widened by a quarter node for two steps of
+// motion (a stable lattice flow moves a marker by less than 0.1 dx per step;
+// a larger move shows up as a read or spread miss).  Every act_stride-th
+// element covers itself and the following ones up to the next activating
+// element, at their current distances; the box is taken around the stencil
+// origin (floor(x), floor(y - 1/2)), one node more.  One block per membrane,
+// a thread per activating element; unflagged tiles are claimed with an
+// exchange and appended to the list.  It runs on a branch of its own after
+// the membrane kernel: the tiles are first needed by the next step's graph.
+__global__ void __launch_bounds__(256) k_activate_next(Dev d)
+{
+    const Lattice& L = d.L;
+    const int64_t m = *d.step;
+    const int64_t s2 = m + 1;
+    uint32_t* flag = d.nearflag[s2 % 3];
+    const int c = (int)(s2 % 3);
+    const BodyConst& B = d.body[blockIdx.x];
+    const double* PX = d.pos[m & 1] + B.off;
+    const double* PY = d.pos[m & 1] + d.nmark + B.off;
+    const int nv = B.nv, stride = d.act_stride;
+    for (int l = threadIdx.x; l < nv; l += blockDim.x) {
+        if (l % stride != 0 && l != nv - 1) continue;
+        const int cover = (l % stride == 0) ? min(stride, nv - l) : 1;
+        const int w = (l + 1 == nv) ? 0 : l + 1;
+        const double cx = PX[l] + 0.5 * (PX[w] - PX[l]), cy = PY[l] + 0.5 * (PY[w] - PY[l]);
+        double reach = 0.0;
+        for (int j = 0; j < cover; ++j) {
+            const int e = l + j, e1 = (e + 1 == nv) ? 0 : e + 1;
+            const double ex = PX[e1] - PX[e], ey = PY[e1] - PY[e];
+            const double cxe = PX[e] + 0.5 * ex, cye = PY[e] + 0.5 * ey;
+            const double own = fmax(0.5 * sqrt(ex * ex + ey * ey), 1.2) + 2.0;
+            reach = fmax(reach, fmax(fabs(cxe - cx), fabs(cye - cy)) + own);
+        }
+        const int ra = (int)ceil(reach + 0.25) + 1;
+        const int ix = (int)floor(cx), jy = (int)floor(cy - 0.5);
+        const int i0 = B.x0 + max(0, ix - ra), i1 = B.x0 + min(B.nxi - 1, ix + ra);
+        const int j0 = max(0, jy - ra), j1 = min(L.ny - 1, jy + ra);
+        if (i0 > i1 || j0 > j1) continue;
+        for (int ty = j0 / TY; ty <= j1 / TY; ++ty)
+            for (int tx = i0 / TX; tx <= i1 / TX; ++tx) {
+                const int t = ty * L.ntx + tx;
+                if (flag[t] == 0u && atomicExch(&flag[t], 1u) == 0u) {
+                    const int pos = atomicAdd(&d.count[c], 1);
+                    if (pos < d.list_cap) d.list[c][pos] = t;
+                    else atomicOr(d.status, ST_LIST_OVERFLOW);
+                }
+            }
+    }
+}
+
+cudaError_t launch_activate_next(const Dev& d, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(d.nbodies);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = d.chain_priority;
+    cfg.attrs = attr;
+    cfg.numAttrs = d.chain_priority ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_activate_next, d);
+}
+
 size_t lagrangian_smem_bytes(int prec, int nv_max)
 {
     size_t r = (prec == PREC_F64) ? sizeof(double) : sizeof(float);

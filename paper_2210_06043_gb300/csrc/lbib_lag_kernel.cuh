@@ -753,14 +753,12 @@ __global__ void __launch_bounds__(T) k_lagrangian(Dev d, int p)
     }
     __syncthreads();
 
-    // 6. direct forcing at the new element centroids, spreading masks, activation
+    // 6. direct forcing at the new element centroids, spreading masks (the
+    //    near tiles of lattice step n + 2 are set by k_activate_next, off the
+    //    membrane -> near chain, from the X^{n+1} this kernel stores)
     int32_t* mki = d.mki[p];
     R* mkf = static_cast<R*>(d.mkf[p]);
-    const int64_t n2 = n + 2;
-    uint32_t* flag2 = d.nearflag[n2 % 3];
     const uint32_t* flag1 = d.nearflag[(n + 1) % 3];  // near tiles of lattice step n + 1
-    const int c2 = (int)(n2 % 3);
-    const int stride = d.act_stride;
     for (int l0 = tid / K; l0 < nvq; l0 += Q) {
         const bool valid = l0 < nv;
         const int l = valid ? l0 : nv - 1;
@@ -812,64 +810,6 @@ __global__ void __launch_bounds__(T) k_lagrangian(Dev d, int p)
                     const int t = tl[e];
                     if (!flag1[t]) miss |= 2u;
                     atomicOr(&d.mask[p][(size_t)t * d.mw + (gl >> 5)], 1u << (gl & 31));
-                }
-            }
-        }
-        if (l % stride == 0 || l == nv - 1) {
-            // Tiles the lattice step n + 2 must update as near: every stencil the
-            // membrane update of step n + 2 reads (vertices, probes, new element
-            // centroids) and the spreading of step n + 2 writes lies, per element
-            // e, within the box of half-width reach_e = max(l_e / 2, 1.2) + 2
-            // around its centroid (vertex / probe offset plus the stencil),
-            // widened by a quarter node for two steps of motion (a stable lattice
-            // flow moves a marker by less than 0.1 dx per step; a larger move
-            // shows up as a read or spread miss).  Each stride-th element
-            // covers itself and the following ones up to the next activating
-            // element, at their current distances; the box is taken around the
-            // stencil origin floor(c), one more node.  The lanes split the tiles.
-            const int cover = (l % stride == 0) ? min(stride, nv - l) : 1;
-            R reach = R(0);
-            for (int j = 0; j < cover; ++j) {
-                const int e = l + j, e1 = (e + 1 == nv) ? 0 : e + 1;
-                const R ex_ = p2_sub<R>(P2<R>{qxh[e1], qxl[e1]}, P2<R>{qxh[e], qxl[e]});
-                const R ey_ = p2_sub<R>(P2<R>{qyh[e1], qyl[e1]}, P2<R>{qyh[e], qyl[e]});
-                const P2<R> cxe = p2_add<R>(P2<R>{qxh[e], qxl[e]}, R(0.5) * ex_);
-                const P2<R> cye = p2_add<R>(P2<R>{qyh[e], qyl[e]}, R(0.5) * ey_);
-                const R dxe = fabs(p2_sub<R>(cxe, CX)), dye = fabs(p2_sub<R>(cye, CY));
-                const R own = fmax(R(0.5) * sqrt(ex_ * ex_ + ey_ * ey_), R(1.2)) + R(2);
-                reach = fmax(reach, fmax(dxe, dye) + own);
-            }
-            const int ra = (int)ceil(reach + R(0.25)) + 1;
-            const int i0 = max(0, sc.ix - ra), i1 = min(B.nxi - 1, sc.ix + ra);
-            const int j0 = max(0, sc.jy - ra), j1 = min(L.ny - 1, sc.jy + ra);
-            if (i0 <= i1 && j0 <= j1) {
-                for (int start = 0;; start += 8) {
-                    const int nt = box_tiles(L, B.x0 + i0, B.x0 + i1, j0, j1, start, tl);
-                    uint32_t fl[8 / K];
-#pragma unroll
-                    for (int k = 0; k < 8 / K; ++k) {
-                        const int e = lane4 + K * k;
-                        fl[k] = (e < nt) ? flag2[tl[e]] : 1u;
-                    }
-                    // claim the unflagged tiles, then append the claimed ones to the
-                    // list: each round's atomics are independent of one another, so
-                    // they are issued back to back instead of one round trip each
-                    uint32_t prev[8 / K];
-#pragma unroll
-                    for (int k = 0; k < 8 / K; ++k) {
-                        const int e = lane4 + K * k;
-                        prev[k] = (e < nt && fl[k] == 0u) ? atomicExch(&flag2[tl[e]], 1u) : 1u;
-                    }
-                    int pos[8 / K];
-#pragma unroll
-                    for (int k = 0; k < 8 / K; ++k) pos[k] = (prev[k] == 0u) ? atomicAdd(&d.count[c2], 1) : -1;
-#pragma unroll
-                    for (int k = 0; k < 8 / K; ++k) {
-                        if (pos[k] < 0) continue;
-                        if (pos[k] < d.list_cap) d.list[c2][pos[k]] = tl[lane4 + K * k];
-                        else bad |= ST_LIST_OVERFLOW;
-                    }
-                    if (nt < 8) break;
                 }
             }
         }

@@ -116,7 +116,7 @@ def test_sweep_full_size_fp32_sampled():
     n = 40
     batch.advance(n)
     d = batch.describe()
-    assert d["kernels_per_step"] == 5
+    assert d["kernels_per_step"] == 6
     latest = batch.latest_observables()
     records = [batch.observables(instance=inst) for inst in range(len(caps))]
     for inst, obs in enumerate(records):

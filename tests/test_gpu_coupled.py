@@ -188,7 +188,7 @@ def test_profiling_and_pipeline_bookkeeping():
     bulk, lag, near = s.kernel_times()
     assert bulk > 0 and lag > 0 and near > 0
     d = s.describe()
-    assert d["kernels_per_step"] == 5 and 0 < d["near_tiles"] < d["tiles"]
+    assert d["kernels_per_step"] == 6 and 0 < d["near_tiles"] < d["tiles"]
     assert s.step_count() == 4
     obs = s.observables()
     assert [o["step"] for o in obs] == [1, 2, 3, 4]
