@@ -305,7 +305,7 @@ lbib_status lbib_read_kernel_times(lbib_ctx* ctx, float* bulk_ms, float* lagr_ms
  * whatever its block size). */
 typedef struct {
     int32_t lagrangian_threads; /* threads per membrane block: 256 or 512 */
-    int32_t near_blocks;        /* blocks of the near-membrane lattice kernel, >= 1 */
+    int32_t near_blocks;        /* blocks of the near-membrane force gather, >= 1 */
     int32_t bulk_tiles_y;       /* 32 x 4 node tiles per bulk lattice block, stacked in y: 1, 2 or 4 */
     int32_t activation_stride;  /* every k-th element centroid schedules the near tiles around it
                                  * (over a radius grown to cover the k - 1 between): 1, 2 or 4 */
@@ -318,12 +318,15 @@ typedef struct {
                                  * kernel before them (scheduled while it finishes, so the launch
                                  * latency leaves the chain; their blocks then hold SM slots the
                                  * bulk update could use); 0: plain stream order */
+    int32_t near_update_blocks; /* blocks of the near-membrane lattice update (one tile at a time
+                                 * each), >= 1: at the chain's priority they take SM slots ahead of
+                                 * the bulk blocks, so fewer of them leave the bulk update more */
 } lbib_launch_config;
 
 /* Current configuration.  Like lbib_advance, the call completes the set-up
  * (no membranes can be added afterwards) and fills in the defaults: membrane
  * blocks of 256 threads when the bodies outnumber half the SMs (else 512),
- * near kernel 4 blocks per SM, one tile per bulk block and one node per bulk
+ * force gather 4 and near lattice update 16 blocks per SM, one tile per bulk block and one node per bulk
  * thread, activation stride 4, observables after the near update, plain
  * stream order on the chain. */
 lbib_status lbib_get_launch_config(lbib_ctx* ctx, lbib_launch_config* out);
@@ -339,7 +342,7 @@ lbib_status lbib_set_launch_config(lbib_ctx* ctx, const lbib_launch_config* cfg)
  * events (the faster run counts), the snapshot is restored, and the fastest
  * candidate is kept.  The search is coordinate-wise, in two rounds: bulk
  * tiles per block and nodes per thread, then membrane block size, then
- * activation stride, then near-kernel blocks (2, 4, 6, 8 or 12 per SM), then
+ * activation stride, then force-gather blocks (2, 4, 6, 8 or 12 per SM), then near-update blocks (4, 8 or 16 per SM), then
  * the observables branch, then programmatic launch on the chain, and the same again from the first round's optimum (the bulk and near kernels
  * share the SMs, so their best shapes depend on each other).  On return the
  * state, the step count and the

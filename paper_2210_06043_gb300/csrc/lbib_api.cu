@@ -120,7 +120,8 @@ struct lbib_ctx {
     int64_t copy_first = 0;
     cudaEvent_t pe[6] = {};
     bool profiling = false, profiled_last = false;
-    int near_grid = 0;  // 0: default, set at finalize
+    int near_grid = 0;         // force gather blocks; 0: default, set at finalize
+    int near_update_grid = 0;  // near lattice update blocks; 0: default, set at finalize
     std::vector<void*> allocs;
     double* macro_buf = nullptr;
     int device = 0;
@@ -256,7 +257,7 @@ lbib_status capture_unit(lbib_ctx* ctx, int prof, int v)
     // chain (launch latency hidden behind its tail), never in the profiling
     // graphs, whose timing events sit between the kernels
     const bool pdl = ctx->chain_pdl && !prof;
-    if (e == cudaSuccess) e = launch_lbm_near(d, ctx->prec, p, ctx->near_grid, ctx->cap, pdl);
+    if (e == cudaSuccess) e = launch_lbm_near(d, ctx->prec, p, ctx->near_grid, ctx->near_update_grid, ctx->cap, pdl);
     rec(5, ctx->cap);
     if (!ctx->obs_branch && e == cudaSuccess) e = launch_observables(d, ctx->cap, true, pdl);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap, ctx->ev_join, 0);
@@ -580,6 +581,7 @@ lbib_status finalize(lbib_ctx* ctx)
         d.chain_priority = greatest;  // numerically lowest = most urgent
     }
     if (!ctx->near_grid) ctx->near_grid = std::max(1, std::min(L.ntiles, 4 * nsm));
+    if (!ctx->near_update_grid) ctx->near_update_grid = std::max(1, std::min(L.ntiles, 16 * nsm));
     ctx->finalized = true;
     if (nb) {
         lbib_status s = ensure_graphs(ctx);
@@ -859,7 +861,7 @@ lbib_status lbib_advance(lbib_ctx* ctx, int64_t nsteps)
     if (ctx->s_l == ctx->s_f) {  // open the pipeline: lattice step s_f alone
         int p = (int)(ctx->s_f & 1);
         CK(launch_lbm_bulk(d, ctx->prec, p, (int)(ctx->s_f % 3), ctx->stream));
-        CK(launch_lbm_near(d, ctx->prec, p, ctx->near_grid, ctx->stream, false));
+        CK(launch_lbm_near(d, ctx->prec, p, ctx->near_grid, ctx->near_update_grid, ctx->stream, false));
         ctx->s_f += 1;
         nsteps -= 1;
         ctx->profiled_last = false;
@@ -1347,7 +1349,7 @@ bool valid_config(const lbib_launch_config& c)
            (c.activation_stride == 1 || c.activation_stride == 2 || c.activation_stride == 4) &&
            (c.bulk_nodes_per_thread == 1 || c.bulk_nodes_per_thread == 2) &&
            (c.observables_branch == 0 || c.observables_branch == 1) &&
-           (c.chain_programmatic == 0 || c.chain_programmatic == 1);
+           (c.chain_programmatic == 0 || c.chain_programmatic == 1) && c.near_update_blocks >= 1;
 }
 
 lbib_launch_config current_config(const lbib_ctx* ctx)
@@ -1360,6 +1362,7 @@ lbib_launch_config current_config(const lbib_ctx* ctx)
     c.bulk_nodes_per_thread = ctx->d.bulk_nodes_per_thread;
     c.observables_branch = ctx->obs_branch;
     c.chain_programmatic = ctx->chain_pdl;
+    c.near_update_blocks = ctx->near_update_grid;
     return c;
 }
 
@@ -1383,6 +1386,7 @@ void apply_config(lbib_ctx* ctx, const lbib_launch_config& c)
     ctx->d.bulk_nodes_per_thread = c.bulk_nodes_per_thread;
     ctx->obs_branch = c.observables_branch;
     ctx->chain_pdl = c.chain_programmatic;
+    ctx->near_update_grid = c.near_update_blocks;
 }
 
 }  // namespace
@@ -1502,7 +1506,7 @@ lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_co
         if (c.lagrangian_threads == best.lagrangian_threads && c.near_blocks == best.near_blocks &&
             c.bulk_tiles_y == best.bulk_tiles_y && c.activation_stride == best.activation_stride &&
             c.bulk_nodes_per_thread == best.bulk_nodes_per_thread && c.observables_branch == best.observables_branch &&
-            c.chain_programmatic == best.chain_programmatic)
+            c.chain_programmatic == best.chain_programmatic && c.near_update_blocks == best.near_update_blocks)
             return;
         float ms = 0.f;
         s = trial(c, &ms);
@@ -1540,6 +1544,12 @@ lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_co
             for (int per_sm : {2, 4, 6, 8, 12}) {
                 lbib_launch_config c = after_stride;
                 c.near_blocks = per_sm * nsm;
+                consider(c);
+            }
+            const lbib_launch_config after_gather = best;
+            for (int per_sm : {4, 8, 16}) {
+                lbib_launch_config c = after_gather;
+                c.near_update_blocks = per_sm * nsm;
                 consider(c);
             }
             const lbib_launch_config after_near = best;

@@ -200,7 +200,7 @@ struct Dev {
 cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, int slot, cudaStream_t s);
 // pdl: k_spread and k_near_lbm are launched as programmatic dependents of the
 // kernel enqueued before them (the membrane update, then k_spread)
-cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, cudaStream_t s, bool pdl);
+cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, int update_grid, cudaStream_t s, bool pdl);
 cudaError_t launch_init_populations(const Dev& d, int prec, int buf, cudaStream_t s);
 // moments of one instance (node columns [x0, x0 + inx)) into [ny][inx] arrays
 cudaError_t launch_macro(const Dev& d, int prec, int buf, int64_t m, int x0, int inx, double* rho, double* ux,

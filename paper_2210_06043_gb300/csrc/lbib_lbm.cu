@@ -570,7 +570,7 @@ cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, int slot, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, cudaStream_t s, bool pdl)
+cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, int update_grid, cudaStream_t s, bool pdl)
 {
     (void)prec;
     cudaLaunchConfig_t cfg = {};
@@ -590,17 +590,13 @@ cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, cudaSt
     cfg.attrs = attr;
     cfg.numAttrs = na;
     cudaError_t e = cudaSuccess;
-    int nsm = 148;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     by_store(d.store, [&](auto sp, auto rp) {
         LBIB_TYPES(sp, rp);
         if (d.L.transfer == LBIB_TRANSFER_MLS) e = cudaLaunchKernelEx(&cfg, k_spread<R, true>, d, parity);
         else e = cudaLaunchKernelEx(&cfg, k_spread<R, false>, d, parity);
         if (e != cudaSuccess) return;
-        // one tile per block at a time, up to 16 resident blocks of 128 threads per SM
-        cfg.gridDim = dim3((unsigned)std::max(1, std::min(d.list_cap, 16 * nsm)));
+        // one tile per block at a time, striding over the list
+        cfg.gridDim = dim3((unsigned)std::max(1, std::min(d.list_cap, update_grid)));
         cfg.blockDim = dim3(TX, TY);
         e = cudaLaunchKernelEx(&cfg, k_near_lbm<S, R>, d, parity);
     });
