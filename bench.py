@@ -487,7 +487,7 @@ def main():
                     help="steps of the separate profiled pass that gives the per-kernel times")
     ap.add_argument("--config", default="", help="fixed launch configuration "
                     "lagrangian_threads,near_blocks,bulk_tiles_y,activation_stride[,bulk_nodes_per_thread"
-                    "[,observables_branch[,chain_programmatic[,near_update_blocks]]]] "
+                    "[,observables_branch[,chain_programmatic[,near_update_blocks[,bulk_tma]]]]] "
                     "instead of the autotuner")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate inference timing")

@@ -321,6 +321,12 @@ typedef struct {
     int32_t near_update_blocks; /* blocks of the near-membrane lattice update (one tile at a time
                                  * each), >= 1: at the chain's priority they take SM slots ahead of
                                  * the bulk blocks, so fewer of them leave the bulk update more */
+    int32_t bulk_tma;           /* 1: the bulk update stages each 32 x 8 node box (nine planes, one
+                                 * halo row and 16 bytes of halo columns) in shared memory with one
+                                 * tensor copy, double-buffered, instead of nine loads per node (the
+                                 * tile and node-per-thread shape above then do not apply); 0: direct
+                                 * loads.  Where the driver offers no tensor-map encoder the direct
+                                 * kernel runs either way */
 } lbib_launch_config;
 
 /* Current configuration.  Like lbib_advance, the call completes the set-up
@@ -328,7 +334,7 @@ typedef struct {
  * blocks of 256 threads when the bodies outnumber half the SMs (else 512),
  * force gather 4 and near lattice update 16 blocks per SM, one tile per bulk block and one node per bulk
  * thread, activation stride 4, observables after the near update, plain
- * stream order on the chain. */
+ * stream order on the chain, direct loads in the bulk update. */
 lbib_status lbib_get_launch_config(lbib_ctx* ctx, lbib_launch_config* out);
 
 /* Sets the configuration used by the following steps (re-captures the step
@@ -341,7 +347,7 @@ lbib_status lbib_set_launch_config(lbib_ctx* ctx, const lbib_launch_config* cfg)
  * by two warm-up steps and twice steps_per_trial >= 1 steps, timed with CUDA
  * events (the faster run counts), the snapshot is restored, and the fastest
  * candidate is kept.  The search is coordinate-wise, in two rounds: bulk
- * tiles per block and nodes per thread, then membrane block size, then
+ * tiles per block and nodes per thread or the TMA-staged bulk update, then membrane block size, then
  * activation stride, then force-gather blocks (2, 4, 6, 8 or 12 per SM), then near-update blocks (4, 8 or 16 per SM), then
  * the observables branch, then programmatic launch on the chain, and the same again from the first round's optimum (the bulk and near kernels
  * share the SMs, so their best shapes depend on each other).  On return the

@@ -120,6 +120,7 @@ struct lbib_ctx {
     int64_t copy_first = 0;
     cudaEvent_t pe[6] = {};
     bool profiling = false, profiled_last = false;
+    alignas(64) unsigned char fmaps[256];  // tensor maps of the population buffers (two CUtensorMap)
     int near_grid = 0;         // force gather blocks; 0: default, set at finalize
     int near_update_grid = 0;  // near lattice update blocks; 0: default, set at finalize
     std::vector<void*> allocs;
@@ -182,6 +183,7 @@ lbib_status check_status(lbib_ctx* ctx)
         return fail(ctx, LBIB_ERR_STATE, "an interpolation stencil left the tiles updated as near-membrane");
     if (st & ST_SPREAD_MISS)
         return fail(ctx, LBIB_ERR_STATE, "a spreading stencil left the tiles scheduled as near-membrane");
+    if (st & ST_TMA_TIMEOUT) return fail(ctx, LBIB_ERR_TIMEOUT, "a bulk-update block gave up waiting for a tensor copy");
     return LBIB_OK;
 }
 
@@ -732,6 +734,13 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     CKC(cudaMemcpy(ctx->colinfo, cols.data(), cols.size() * sizeof(int4), cudaMemcpyHostToDevice));
     CKC(cudaMemset(d.f[0], 0, nq * ctx->ssz));
     CKC(cudaMemset(d.f[1], 0, nq * ctx->ssz));
+    // tensor maps for the TMA-staged bulk update (left out where the driver
+    // has no encoder: the direct-load kernel then runs whatever the option)
+    d.bulk_tma = 0;
+    d.fmaps = nullptr;
+    if (make_population_maps(d, ctx->fmaps) == cudaSuccess && configure_bulk_tma(d.store) == cudaSuccess)
+        d.fmaps = ctx->fmaps;
+    cudaGetLastError();
     CKC(cudaMemset(d.drho, 0, nn * ctx->rsz));
     CKC(cudaMemset(d.ux, 0, nn * ctx->rsz));
     CKC(cudaMemset(d.uy, 0, nn * ctx->rsz));
@@ -1349,7 +1358,8 @@ bool valid_config(const lbib_launch_config& c)
            (c.activation_stride == 1 || c.activation_stride == 2 || c.activation_stride == 4) &&
            (c.bulk_nodes_per_thread == 1 || c.bulk_nodes_per_thread == 2) &&
            (c.observables_branch == 0 || c.observables_branch == 1) &&
-           (c.chain_programmatic == 0 || c.chain_programmatic == 1) && c.near_update_blocks >= 1;
+           (c.chain_programmatic == 0 || c.chain_programmatic == 1) && c.near_update_blocks >= 1 &&
+           (c.bulk_tma == 0 || c.bulk_tma == 1);
 }
 
 lbib_launch_config current_config(const lbib_ctx* ctx)
@@ -1363,6 +1373,7 @@ lbib_launch_config current_config(const lbib_ctx* ctx)
     c.observables_branch = ctx->obs_branch;
     c.chain_programmatic = ctx->chain_pdl;
     c.near_update_blocks = ctx->near_update_grid;
+    c.bulk_tma = ctx->d.bulk_tma;
     return c;
 }
 
@@ -1387,6 +1398,7 @@ void apply_config(lbib_ctx* ctx, const lbib_launch_config& c)
     ctx->obs_branch = c.observables_branch;
     ctx->chain_pdl = c.chain_programmatic;
     ctx->near_update_grid = c.near_update_blocks;
+    ctx->d.bulk_tma = c.bulk_tma;
 }
 
 }  // namespace
@@ -1506,7 +1518,8 @@ lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_co
         if (c.lagrangian_threads == best.lagrangian_threads && c.near_blocks == best.near_blocks &&
             c.bulk_tiles_y == best.bulk_tiles_y && c.activation_stride == best.activation_stride &&
             c.bulk_nodes_per_thread == best.bulk_nodes_per_thread && c.observables_branch == best.observables_branch &&
-            c.chain_programmatic == best.chain_programmatic && c.near_update_blocks == best.near_update_blocks)
+            c.chain_programmatic == best.chain_programmatic && c.near_update_blocks == best.near_update_blocks &&
+            c.bulk_tma == best.bulk_tma)
             return;
         float ms = 0.f;
         s = trial(c, &ms);
@@ -1525,8 +1538,14 @@ lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_co
                 lbib_launch_config c = start;
                 c.bulk_tiles_y = rt;
                 c.bulk_nodes_per_thread = npt;
+                c.bulk_tma = 0;
                 consider(c);
             }
+        if (d.fmaps) {
+            lbib_launch_config c = start;
+            c.bulk_tma = 1;
+            consider(c);
+        }
         if (d.nbodies) {
             const lbib_launch_config after_bulk = best;
             for (int lt : {256, 512}) {

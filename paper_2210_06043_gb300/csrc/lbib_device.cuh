@@ -60,6 +60,23 @@ __device__ __forceinline__ void st<__half, float>(__half* p, float v)
     *p = __float2half_rn(v * HALF_SCALE);
 }
 
+// The same conversions from a stored value already loaded (from shared memory)
+template <typename S, typename R>
+__device__ __forceinline__ R from_store(S v)
+{
+    return static_cast<R>(v);
+}
+template <>
+__device__ __forceinline__ float from_store<__nv_bfloat16, float>(__nv_bfloat16 v)
+{
+    return __bfloat162float(v);
+}
+template <>
+__device__ __forceinline__ float from_store<__half, float>(__half v)
+{
+    return __half2float(v) * (1.0f / HALF_SCALE);
+}
+
 // ------------------------------------------------------- Peskin 4-point kernel
 // phi(a), a = |r|: (3 - 2a + sqrt(2 - 4 (a - 1/2)^2)) / 8 on [0, 1],
 // (5 - 2a - sqrt(2 - 4 (a - 3/2)^2)) / 8 on (1, 2], zero beyond (Peskin 2002).

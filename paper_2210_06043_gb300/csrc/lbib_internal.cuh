@@ -47,6 +47,7 @@ enum : uint32_t {
     ST_READ_MISS = 2u,      // an interpolation stencil reached a tile not updated as near
     ST_SPREAD_MISS = 4u,    // a spreading stencil reached a tile not scheduled as near
     ST_LIST_OVERFLOW = 8u,  // near-tile list capacity exceeded
+    ST_TMA_TIMEOUT = 16u,   // a bulk-update block gave up waiting for a tensor copy
 };
 
 enum { PREC_F64 = 0, PREC_F32 = 1 };  // compute type of the kernels
@@ -192,6 +193,9 @@ struct Dev {
     double dcut;               // repulsion cut-off (Eq. 12)
     double probe;              // probe length (Sec. 2.6)
     double uscale;             // observables: u_max / H
+    // fields added later go last
+    int bulk_tma;              // 1: the bulk update stages its populations with tensor copies
+    const void* fmaps;         // host copy of the two population tensor maps (parity 0, 1), or null
 };
 
 // ------------------------------------------------------------------ launchers
@@ -202,6 +206,10 @@ cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, int slot, cudaSt
 // kernel enqueued before them (the membrane update, then k_spread)
 cudaError_t launch_lbm_near(const Dev& d, int prec, int parity, int grid, int update_grid, cudaStream_t s, bool pdl);
 cudaError_t launch_init_populations(const Dev& d, int prec, int buf, cudaStream_t s);
+// tensor maps of the two population buffers for the TMA-staged bulk update
+// (out: two CUtensorMap, 64-byte aligned); and its kernel attributes
+cudaError_t make_population_maps(const Dev& d, void* out);
+cudaError_t configure_bulk_tma(int store);
 // moments of one instance (node columns [x0, x0 + inx)) into [ny][inx] arrays
 cudaError_t launch_macro(const Dev& d, int prec, int buf, int64_t m, int x0, int inx, double* rho, double* ux,
                          double* uy, cudaStream_t s);

@@ -16,7 +16,9 @@
 // x counted within the node's instance (a context may hold a batch of
 // capillaries side by side; each tile column carries its instance's origin
 // and width).
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <type_traits>
 
@@ -184,6 +186,163 @@ __global__ void __launch_bounds__(TX* TY* RT / NPT) k_bulk(Dev d, int p, int slo
         const int base = y * L.nxp + x;
 #pragma unroll
         for (int q = 0; q < 9; ++q) st<S, R>(fout + q * L.qstride + base, g[j][q]);
+    }
+}
+
+// TMA-staged bulk update.  A job is a 32 x 8 node box (two tiles of one tile
+// column); one 3-D tensor copy brings its nine population planes with a halo
+// of one row above and below and 16 bytes of columns on either side (the
+// copy's x must sit on a 16-byte boundary; rows outside the lattice arrive as
+// zeros) into one of TB_STAGES shared-memory stages, signalled on an mbarrier.
+// A block of 32 x 8 threads takes TB_JOBS consecutive jobs (neighbouring tile
+// columns): one warp first lists those with a tile the bulk update owns, with
+// their near flags and column records, in shared memory (so issuing a copy
+// needs no global read), and the copies run TB_STAGES jobs ahead of the
+// update.  Interior nodes read their nine pulls from the stage at
+// fixed offsets; wall, inlet and outlet nodes take the global path (pull).
+// Jobs whose two tiles are both near-membrane are skipped without a copy.
+// The node update is k_bulk's (same pull values, same collide_t), so every
+// node gets the same bits either way.  A launch option: on the 64-capillary
+// sweep it is slower than k_bulk (FP32 126 vs 106 us alone): the halo sectors
+// of the copies raise the DRAM reads from 367 to 445 MB per launch, and the
+// instructions per node do not fall (about 235 either way: the collision and
+// the stores, not the load addressing, make up most of them).
+constexpr int TB_ROWS = 8;
+constexpr int TB_STAGES = 3;
+constexpr int TB_JOBS = 8;  // at most 32 (one warp lists them)
+constexpr uint32_t TB_WAIT_LIMIT = 1u << 24;  // mbarrier polls before a block gives up
+template <typename S>
+__host__ __device__ constexpr int tb_hx() { return 16 / (int)sizeof(S); }
+template <typename S>
+__host__ __device__ constexpr int tb_w() { return TX + 2 * tb_hx<S>(); }
+template <typename S>
+__host__ __device__ constexpr uint32_t tb_copy_bytes() { return 9u * (TB_ROWS + 2) * tb_w<S>() * (uint32_t)sizeof(S); }
+template <typename S>
+__host__ __device__ constexpr uint32_t tb_stage_bytes() { return (tb_copy_bytes<S>() + 127u) & ~127u; }
+
+__device__ __forceinline__ uint32_t tb_smem(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ bool tb_wait(uint64_t* bar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < TB_WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(tb_smem(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// job = row pair * ntx + tile column: the jobs of a block are neighbouring
+// tile columns, so their halo columns are each other's (ordering the jobs down
+// a column instead raised the DRAM reads from 445 to 486 MB per launch)
+__device__ __forceinline__ void tb_issue(const CUtensorMap* tm, uint64_t* bar, void* dst, int job, int ntx, int hx,
+                                         uint32_t bytes)
+{
+    const int x = (job % ntx) * TX - hx, y = (job / ntx) * TB_ROWS - 1, z = 0;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tb_smem(bar)), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(tb_smem(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(tb_smem(bar))
+        : "memory");
+}
+
+template <typename S, typename R, bool FORCED>
+__global__ void __launch_bounds__(TX* TB_ROWS) k_bulk_tma(const __grid_constant__ CUtensorMap tm, Dev d, int p, int slot)
+{
+    extern __shared__ __align__(128) unsigned char tb_raw[];
+    __shared__ __align__(8) uint64_t full[TB_STAGES];
+    __shared__ int s_list[TB_JOBS];         // the block's jobs with a tile the bulk update owns
+    __shared__ uint32_t s_near[TB_JOBS][2]; // near flags of each listed job's two tiles
+    __shared__ int4 s_ci[TB_JOBS];          // column record of each listed job
+    __shared__ int s_n, s_abort;
+    const Lattice& L = d.L;
+    constexpr int HX = tb_hx<S>(), W = tb_w<S>(), H = TB_ROWS + 2;
+    constexpr uint32_t SB = tb_stage_bytes<S>(), CB = tb_copy_bytes<S>();
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    // stages on a 128-byte boundary of the shared window (tensor-copy destinations)
+    unsigned char* tb_stage = tb_raw + ((128u - (tb_smem(tb_raw) & 127u)) & 127u);
+    const int jy = (L.nty + 1) / 2;
+    const int njobs = L.ntx * jy;
+    const int first = blockIdx.x * TB_JOBS;
+    const S* __restrict__ fin = static_cast<const S*>(d.f[p]);
+    S* __restrict__ fout = static_cast<S*>(d.f[p ^ 1]);
+    // the block's jobs, their near flags and column records, read once (one warp)
+    if (threadIdx.y == 0) {
+        const int j = first + threadIdx.x;
+        uint32_t n0 = 1u, n1 = 1u;
+        int4 ci = make_int4(0, 0, 0, 0);
+        if (threadIdx.x < TB_JOBS && j < njobs) {
+            const int tx = j % L.ntx, t0 = (j / L.ntx) * 2;
+            n0 = d.nearflag[slot][t0 * L.ntx + tx];
+            n1 = (t0 + 1 < L.nty) ? d.nearflag[slot][(t0 + 1) * L.ntx + tx] : 1u;
+            ci = d.colinfo[tx];
+        }
+        const bool live = threadIdx.x < TB_JOBS && j < njobs && (!n0 || !n1);
+        const uint32_t m = __ballot_sync(0xffffffffu, live);
+        if (live) {
+            const int k = __popc(m & ((1u << threadIdx.x) - 1u));
+            s_list[k] = j;
+            s_near[k][0] = n0;
+            s_near[k][1] = n1;
+            s_ci[k] = ci;
+        }
+        if (threadIdx.x == 0) {
+            s_n = __popc(m);
+            s_abort = 0;
+            for (int i = 0; i < TB_STAGES; ++i)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tb_smem(&full[i])), "r"(1));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncwarp();
+        if (threadIdx.x == 0)
+            for (int k = 0; k < TB_STAGES && k < __popc(m); ++k)
+                tb_issue(&tm, &full[k], tb_stage + k * SB, s_list[k], L.ntx, HX, CB);
+    }
+    __syncthreads();
+    const int n = s_n;
+    // this thread's node within a job, and its place in a stage
+    const int cx0 = threadIdx.x + HX, cy0 = threadIdx.y + 1;
+    int k = 0;
+    for (; k < n; ++k) {
+        const int sg = k % TB_STAGES;
+        if (!tb_wait(&full[sg], (uint32_t)(k / TB_STAGES) & 1u)) s_abort = 1;
+        __syncthreads();
+        if (s_abort) break;
+        const int job = s_list[k];
+        const int tx = job % L.ntx;
+        const int x = tx * TX + threadIdx.x, y = (job / L.ntx) * TB_ROWS + threadIdx.y;
+        const int4 ci = s_ci[k];
+        const int xl = x - ci.x;
+        if (y < L.ny && xl < ci.y && !s_near[k][threadIdx.y / TY]) {
+            R g[9];
+            if (xl > 0 && xl < ci.y - 1 && y > 0 && y < L.ny - 1) {
+                const S* sp = reinterpret_cast<const S*>(tb_stage + sg * SB);
+#pragma unroll
+                for (int q = 0; q < 9; ++q) g[q] = from_store<S, R>(sp[(q * H + cy0 - cy(q)) * W + cx0 - cx(q)]);
+            } else {
+                pull<S, R>(L, fin, x, y, xl, ci.y, g);
+            }
+            R drho, ux, uy;
+            collide_t<R, FORCED>(g, lat_param<R>(L.gx, L.gx_f), lat_param<R>(L.gy, L.gy_f),
+                                 lat_param<R>(L.omega, L.omega_f), drho, ux, uy);
+            if (!(drho > R(-1)) || !isfinite(ux + uy)) atomicOr(d.status, ST_DIVERGED);
+            const int base = y * L.nxp + x;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) st<S, R>(fout + q * L.qstride + base, g[q]);
+        }
+        __syncthreads();  // every thread is done with stage sg
+        if (tid == 0 && k + TB_STAGES < n) tb_issue(&tm, &full[sg], tb_stage + sg * SB, s_list[k + TB_STAGES], L.ntx, HX, CB);
+    }
+    if (s_abort && tid == 0) {
+        atomicOr(d.status, ST_TMA_TIMEOUT);
+        // the copies still in flight land before the block's shared memory is released
+        for (int k2 = k; k2 < n && k2 < k + TB_STAGES; ++k2)
+            (void)tb_wait(&full[k2 % TB_STAGES], (uint32_t)(k2 / TB_STAGES) & 1u);
     }
 }
 
@@ -554,9 +713,75 @@ static void launch_bulk_rt(const Dev& d, int parity, int slot, cudaStream_t s)
     });
 }
 
+template <typename S>
+static CUtensorMapDataType tb_dtype()
+{
+    if (std::is_same<S, double>::value) return CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    if (std::is_same<S, float>::value) return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    if (std::is_same<S, __nv_bfloat16>::value) return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    return CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+}
+
+cudaError_t make_population_maps(const Dev& d, void* out)
+{
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (!fn || q != cudaDriverEntryPointSuccess) return cudaErrorNotSupported;
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    CUtensorMap* maps = static_cast<CUtensorMap*>(out);
+    CUresult r = CUDA_SUCCESS;
+    by_store(d.store, [&](auto sp, auto rp) {
+        LBIB_TYPES(sp, rp);
+        (void)sizeof(R);
+        const cuuint64_t es = sizeof(S);
+        // x (row pitch nxp), y (ny rows), plane q (stride ny nxp)
+        const cuuint64_t dims[3] = {(cuuint64_t)d.L.nxp, (cuuint64_t)d.L.ny, 9};
+        const cuuint64_t strides[2] = {(cuuint64_t)d.L.nxp * es, (cuuint64_t)d.L.qstride * es};
+        const cuuint32_t box[3] = {(cuuint32_t)tb_w<S>(), (cuuint32_t)(TB_ROWS + 2), 9};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        for (int b = 0; b < 2 && r == CUDA_SUCCESS; ++b)
+            r = encode(&maps[b], tb_dtype<S>(), 3, d.f[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    });
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t configure_bulk_tma(int store)
+{
+    cudaError_t e = cudaSuccess;
+    by_store(store, [&](auto sp, auto rp) {
+        LBIB_TYPES(sp, rp);
+        const int bytes = (int)(TB_STAGES * tb_stage_bytes<S>() + 128);
+        e = cudaFuncSetAttribute(k_bulk_tma<S, R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_bulk_tma<S, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    });
+    return e;
+}
+
+static void launch_bulk_tma(const Dev& d, int parity, int slot, cudaStream_t s)
+{
+    const int njobs = d.L.ntx * ((d.L.nty + 1) / 2);
+    const int grid = std::max(1, (njobs + TB_JOBS - 1) / TB_JOBS);
+    const bool forced = d.L.gx != 0.0 || d.L.gy != 0.0;
+    const CUtensorMap& tm = static_cast<const CUtensorMap*>(d.fmaps)[parity];
+    by_store(d.store, [&](auto sp, auto rp) {
+        LBIB_TYPES(sp, rp);
+        const size_t bytes = TB_STAGES * tb_stage_bytes<S>() + 128;
+        if (forced) k_bulk_tma<S, R, true><<<grid, dim3(TX, TB_ROWS), bytes, s>>>(tm, d, parity, slot);
+        else k_bulk_tma<S, R, false><<<grid, dim3(TX, TB_ROWS), bytes, s>>>(tm, d, parity, slot);
+    });
+}
+
 cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, int slot, cudaStream_t s)
 {
     (void)prec;  // the storage type fixes the compute type
+    if (d.bulk_tma && d.fmaps) {
+        launch_bulk_tma(d, parity, slot, s);
+        return cudaGetLastError();
+    }
     const int v = 10 * (d.bulk_tiles_y == 2 || d.bulk_tiles_y == 4 ? d.bulk_tiles_y : 1) +
                   (d.bulk_nodes_per_thread == 2 ? 2 : 1);
     switch (v) {

@@ -61,7 +61,8 @@ class lbib_launch_config(ctypes.Structure):
     _fields_ = [("lagrangian_threads", ctypes.c_int32), ("near_blocks", ctypes.c_int32),
                 ("bulk_tiles_y", ctypes.c_int32), ("activation_stride", ctypes.c_int32),
                 ("bulk_nodes_per_thread", ctypes.c_int32), ("observables_branch", ctypes.c_int32),
-                ("chain_programmatic", ctypes.c_int32), ("near_update_blocks", ctypes.c_int32)]
+                ("chain_programmatic", ctypes.c_int32), ("near_update_blocks", ctypes.c_int32),
+                ("bulk_tma", ctypes.c_int32)]
 
 
 class lbib_mlp_desc(ctypes.Structure):
@@ -226,7 +227,7 @@ def _config_dict(c: lbib_launch_config) -> dict:
     return dict(lagrangian_threads=c.lagrangian_threads, near_blocks=c.near_blocks, bulk_tiles_y=c.bulk_tiles_y,
                 activation_stride=c.activation_stride, bulk_nodes_per_thread=c.bulk_nodes_per_thread,
                 observables_branch=c.observables_branch, chain_programmatic=c.chain_programmatic,
-                near_update_blocks=c.near_update_blocks)
+                near_update_blocks=c.near_update_blocks, bulk_tma=c.bulk_tma)
 
 
 class Solver:
@@ -391,7 +392,7 @@ class Solver:
 
     def set_launch_config(self, lagrangian_threads, near_blocks, bulk_tiles_y, activation_stride=4,
                           bulk_nodes_per_thread=1, observables_branch=0, chain_programmatic=0,
-                          near_update_blocks=0):
+                          near_update_blocks=0, bulk_tma=0):
         """near_update_blocks 0 keeps the current grid of the near lattice update."""
         if not near_update_blocks:
             near_update_blocks = self.launch_config()["near_update_blocks"]
@@ -400,7 +401,7 @@ class Solver:
                                bulk_nodes_per_thread=int(bulk_nodes_per_thread),
                                observables_branch=int(observables_branch),
                                chain_programmatic=int(chain_programmatic),
-                               near_update_blocks=int(near_update_blocks))
+                               near_update_blocks=int(near_update_blocks), bulk_tma=int(bulk_tma))
         self._c(self.lib.lbib_set_launch_config(self.ctx, ctypes.byref(c)))
 
     def autotune(self, steps_per_trial=20) -> dict:

@@ -58,7 +58,7 @@ int main(void) {
   S(lbib_launch_config); O(lbib_launch_config, near_blocks); O(lbib_launch_config, bulk_tiles_y);
   O(lbib_launch_config, activation_stride); O(lbib_launch_config, bulk_nodes_per_thread);
   O(lbib_launch_config, observables_branch); O(lbib_launch_config, chain_programmatic);
-  O(lbib_launch_config, near_update_blocks);
+  O(lbib_launch_config, near_update_blocks); O(lbib_launch_config, bulk_tma);
   S(lbib_mlp_desc); O(lbib_mlp_desc, cuda_stream); O(lbib_mlp_desc, seed); O(lbib_mlp_desc, out_scale);
   return 0;
 }

@@ -15,8 +15,8 @@ from paper_2210_06043_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-CONFIGS = [(512, 608, 1, 4, 1, 0, 0, 2432), (256, 300, 2, 1, 2, 1, 1, 1), (256, 1, 4, 2, 1, 0, 1, 608),
-           (512, 2000, 4, 1, 2, 1, 0, 7), (512, 9, 1, 2, 2, 0, 1, 5000)]
+CONFIGS = [(512, 608, 1, 4, 1, 0, 0, 2432, 0), (256, 300, 2, 1, 2, 1, 1, 1, 1), (256, 1, 4, 2, 1, 0, 1, 608, 0),
+           (512, 2000, 4, 1, 2, 1, 0, 7, 1), (512, 9, 1, 2, 2, 0, 1, 5000, 0), (512, 608, 1, 1, 2, 0, 0, 2432, 1)]
 
 
 def _snapshot(s, caps):
@@ -41,18 +41,18 @@ def _equal(a, b):
             assert np.array_equal(x, y), k
 
 
-@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "bf16", "fp16"])
 def test_every_launch_configuration_gives_the_same_state(storage):
     caps = [wl.small_capillary(), wl.sweep_capillary(300, 60, 0.75, 5e-4, "biconcave", 1, storage="fp64",
                                                       cell_markers=300, particle_markers=64, n_lig=60)]
     caps = [dataclasses.replace(c, storage=storage) for c in caps]
     ref = None
-    for lt, nb, rt, st, npt, ob, pdl, nu in CONFIGS:
+    for lt, nb, rt, st, npt, ob, pdl, nu, tma in CONFIGS:
         s = lbib.from_capillaries(caps)
-        s.set_launch_config(lt, nb, rt, st, npt, ob, pdl, nu)
+        s.set_launch_config(lt, nb, rt, st, npt, ob, pdl, nu, tma)
         assert s.launch_config() == dict(lagrangian_threads=lt, near_blocks=nb, bulk_tiles_y=rt,
                                          activation_stride=st, bulk_nodes_per_thread=npt, observables_branch=ob,
-                                         chain_programmatic=pdl, near_update_blocks=nu)
+                                         chain_programmatic=pdl, near_update_blocks=nu, bulk_tma=tma)
         s.advance(30)
         snap = _snapshot(s, caps)
         obs = [s.observables(instance=k) for k in range(len(caps))]
@@ -94,7 +94,7 @@ def test_autotune_leaves_the_state_and_cursors_unchanged():
 def test_invalid_launch_configurations_are_rejected():
     s = lbib.from_capillary(wl.small_capillary())
     for bad in ((128, 100, 1, 4), (512, 0, 1, 4), (512, 100, 3, 4), (512, 100, 1, 3), (512, 100, 1, 4, 3),
-                (512, 100, 1, 4, 1, 2), (512, 100, 1, 4, 1, 0, 2), (512, 100, 1, 4, 1, 0, 0, -1)):
+                (512, 100, 1, 4, 1, 2), (512, 100, 1, 4, 1, 0, 2), (512, 100, 1, 4, 1, 0, 0, -1), (512, 100, 1, 4, 1, 0, 0, 100, 2)):
         with pytest.raises(lbib.LbibError) as e:
             s.set_launch_config(*bad)
         assert e.value.status == lbib.LBIB_ERR_INVALID_ARG
