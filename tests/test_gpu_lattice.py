@@ -104,3 +104,43 @@ def test_injected_nan_is_reported_as_divergence():
         s.sync()
     assert e.value.status == lbib.LBIB_ERR_DIVERGED
     s.close()
+
+
+# the TMA-staged bulk update (launch option bulk_tma): x-halo copies at both
+# ends of the row pitch, zero-filled rows beyond the walls, wall / inlet /
+# outlet nodes on the global path, and the forced variant (periodic mode)
+_TMA = dict(lagrangian_threads=512, near_blocks=1, bulk_tiles_y=1, activation_stride=4,
+            bulk_nodes_per_thread=1, observables_branch=0, chain_programmatic=0, near_update_blocks=1,
+            bulk_tma=1)
+
+
+@pytest.mark.parametrize("nx,ny", SHAPES)
+@pytest.mark.parametrize("bc", [lbib.LBIB_BC_INLET_OUTLET, lbib.LBIB_BC_PERIODIC_FORCE])
+def test_tma_staged_bulk_update_matches_oracle_fp64(nx, ny, bc):
+    f0 = wl.random_populations(nx, ny, seed=nx * 3 + ny, eps=1e-2)
+    g = (2e-5, -1e-5) if bc == lbib.LBIB_BC_PERIODIC_FORCE else (0.0, 0.0)
+    o, s = _pair(nx, ny, bc, lbib.LBIB_STORE_FP64, f0, g=g)
+    s.set_launch_config(**_TMA)
+    assert s.launch_config()["bulk_tma"] == 1
+    for n in (1, 4):
+        o.step(n)
+        s.advance(n)
+        assert np.abs(s.populations() - o.fpost()).max() < 1e-14
+    s.close()
+
+
+@pytest.mark.parametrize("storage", [lbib.LBIB_STORE_FP32, lbib.LBIB_STORE_BF16, lbib.LBIB_STORE_FP16])
+@pytest.mark.parametrize("bc", [lbib.LBIB_BC_INLET_OUTLET, lbib.LBIB_BC_PERIODIC_FORCE])
+def test_tma_staged_bulk_update_equals_direct_loads(storage, bc):
+    nx, ny = 100, 23
+    f0 = wl.random_populations(nx, ny, seed=11, eps=1e-2)
+    g = (2e-5, -1e-5) if bc == lbib.LBIB_BC_PERIODIC_FORCE else (0.0, 0.0)
+    out = []
+    for tma in (0, 1):
+        s = lbib.Solver(nx, ny, tau=0.8, re=5.0, bc=bc, g=g, storage=storage)
+        s.write_populations(f0)
+        s.set_launch_config(**dict(_TMA, bulk_tma=tma))
+        s.advance(6)
+        out.append(s.populations())
+        s.close()
+    assert np.array_equal(out[0], out[1])
