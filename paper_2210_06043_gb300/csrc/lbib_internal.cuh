@@ -143,7 +143,8 @@ struct Dev {
     void* fy;                  // Real [ny][nxp]
     int32_t* fresh;            // [ntiles]: lattice step whose near update wrote rho/u
     // nearflag[m % 3][t]: tile t is updated by the near kernel at lattice step m.
-    // Set by the membrane update of step m - 2 (or an activation), read by the
+    // Set by k_activate_next after the membrane update of step m - 2 (or by
+    // k_activate at set-up and restore), read by the
     // bulk and near updates of step m, cleared by the membrane update of step m;
     // three slots so that the bulk update of step m + 1, which runs alongside
     // the membrane update of step m, reads a slot nobody writes.

@@ -18,8 +18,9 @@
 //      nothing for a body fixed to the wall;
 //   6. direct forcing rho (U_struct - U*) at the new element centroids,
 //      written as markers for lattice step n + 1 together with the bit masks of
-//      the tiles their stencils touch; tiles within r_act of the new
-//      centroids are scheduled as near for lattice step n + 2;
+//      the tiles their stencils touch (the tiles around the new centroids are
+//      scheduled as near for lattice step n + 2 by k_activate_next, which runs
+//      after this kernel off the membrane -> near chain);
 //   7. area, perimeter change, centroid and extent of X^{n+1} (per body, for
 //      k_observables, which writes the record of step n + 1 right after); the
 //      last block to finish advances n.
