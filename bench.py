@@ -28,6 +28,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -85,11 +86,19 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _code_only(text):
+    """Source text without comments and blank lines: a comment edit does not
+    change the kernel the counters were taken on."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln.strip())
+
+
 def _kernel_source_hash():
     h = hashlib.sha256()
     for f in ("lbib_lbm.cu", "lbib_device.cuh", "lbib_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2210_06043_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2210_06043_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
