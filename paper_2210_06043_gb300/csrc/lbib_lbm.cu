@@ -101,7 +101,9 @@ __device__ __forceinline__ void pull(const Lattice& L, const S* __restrict__ fin
 // equilibrium, A = w (drho + rho (9/2 (e.u)^2 - 3/2 u.u)), and differ in the
 // sign of the odd part, B = 3 w rho e_q.u (Eq. 2); likewise the forcing term
 // of Eq. 4.  FORCED = false is the same update for F = 0 (it gives the same
-// values as FORCED = true with F = 0, without the source arithmetic).
+// values as FORCED = true with F = 0, without the source arithmetic).  The
+// near update (one node per thread) is held to 40 registers in FP32, like the
+// bulk update.
 template <typename R, bool FORCED>
 __device__ __forceinline__ void collide_t(R g[9], R Fx, R Fy, R omega, R& drho, R& ux, R& uy)
 {
@@ -119,10 +121,13 @@ __device__ __forceinline__ void collide_t(R g[9], R Fx, R Fy, R omega, R& drho, 
     const R u2 = R(1.5) * (ux * ux + uy * uy);
     const R uF = FORCED ? ux * Fx + uy * Fy : R(0);
     const R cf = R(1) - R(0.5) * omega;
+    // relaxation as g' = (1 - omega) g + omega f_eq, with omega folded into
+    // the equilibrium terms (one fused multiply-add per direction)
+    const R keep = R(1) - omega;
     // rest population
     {
-        const R geq = wq<R>(0) * (drho - rho * u2);
-        g[0] = g[0] - omega * (g[0] - geq);
+        const R oeq = (omega * wq<R>(0)) * (drho - rho * u2);
+        g[0] = keep * g[0] + oeq;
         if (FORCED) g[0] += cf * wq<R>(0) * (R(-3) * uF);
     }
 #pragma unroll
@@ -131,10 +136,10 @@ __device__ __forceinline__ void collide_t(R g[9], R Fx, R Fy, R omega, R& drho, 
         const int o = op(q);                    // 3, 4, 7, 8
         const R w = wq<R>(q);
         const R eu = R(cx(q)) * ux + R(cy(q)) * uy;
-        const R A = w * (drho + rho * (R(4.5) * eu * eu - u2));
-        const R B = w * rho * (R(3) * eu);
-        g[q] = g[q] - omega * (g[q] - (A + B));
-        g[o] = g[o] - omega * (g[o] - (A - B));
+        const R oA = (omega * w) * (drho + rho * (R(4.5) * eu * eu - u2));
+        const R oB = ((R(3) * omega * w) * rho) * eu;
+        g[q] = keep * g[q] + (oA + oB);
+        g[o] = keep * g[o] + (oA - oB);
         if (FORCED) {
             const R eF = R(cx(q)) * Fx + R(cy(q)) * Fy;
             const R even = cf * w * (R(9) * eu * eF - R(3) * uF);
@@ -529,7 +534,7 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_spread(Dev d, int p)
 // force density k_spread left in fx / fy; writes the populations, rho - 1 and
 // u for the membrane update, and marks the tile as holding step m.
 template <typename S, typename R>
-__global__ void __launch_bounds__(TX* TY) k_near_lbm(Dev d, int p)
+__global__ void __launch_bounds__(TX* TY, (std::is_same<R, float>::value ? 12 : 1)) k_near_lbm(Dev d, int p)
 {
     pdl_wait();  // the force density comes from k_spread
     const Lattice& L = d.L;
