@@ -54,7 +54,10 @@
  *     wall's bounce-back condition already holds the fluid there.
  *   - A traction probe that would cross a wall stops at the wall.
  *   - Bending: theta is the signed turning angle at the vertex of a
- *     counter-clockwise chain; the "t" in Eq. 10's denominators is "+".
+ *     counter-clockwise chain; the "t" in Eq. 10's denominators is "+";
+ *     l_right is the length of the edge on the left of the vertex and l_left
+ *     that of the edge on its right (the order in which Sec. 2.3 defines
+ *     them), which makes the three forces torque-free.
  *   - Area: shoelace formula (Green's theorem with the factor 1/2).
  *   - Bond laws (cited, not printed): P_f = 1 - exp(-k_f dt) when the gap to
  *     the nearest wall is below y_cr; P_r = 1 - exp(-k_r dt) with
@@ -563,16 +566,20 @@ void orc_membrane_forces(int nv, const double* x, const double* y, const double*
         fay[b] += 0.5 * fy;
     }
     for (int v = 0; v < nv; ++v) {
-        /* Eq. 10 for the vertex triple (v-1, v, v+1) */
+        /* Eq. 10 for the vertex triple (v-1, v, v+1).  Sec. 2.3 names l_right
+         * the length of the edge on the left of v and l_left that of the edge
+         * on its right; so the left vertex takes the right edge's share and
+         * the right vertex the left edge's, and the three forces have no net
+         * torque about any point. */
         int vl = (v + nv - 1) % nv, vr = (v + 1) % nv;
-        double lL = len[vl], lR = len[v];
+        double l_right = len[vl], l_left = len[v];
         double c = kb * (th[v] - th0[v]);
-        fbx[vl] += c * lL / (lL + lR) * nvx[v];
-        fby[vl] += c * lL / (lL + lR) * nvy[v];
+        fbx[vl] += c * l_left / (l_left + l_right) * nvx[v];
+        fby[vl] += c * l_left / (l_left + l_right) * nvy[v];
         fbx[v] += -c * nvx[v];
         fby[v] += -c * nvy[v];
-        fbx[vr] += c * lR / (lL + lR) * nvx[v];
-        fby[vr] += c * lR / (lL + lR) * nvy[v];
+        fbx[vr] += c * l_right / (l_left + l_right) * nvx[v];
+        fby[vr] += c * l_right / (l_left + l_right) * nvy[v];
     }
     free(len);
     free(nlx);

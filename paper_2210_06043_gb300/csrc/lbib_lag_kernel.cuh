@@ -635,13 +635,17 @@ __global__ void __launch_bounds__(T) k_lagrangian(Dev d, int p)
             const R cr = -ks * (len[v] - sl0[v]) * ilen[v];
             fsx = cl * ex[lm] - cr * ex[v];
             fsy = cl * ey[lm] - cr * ey[v];
-            // Eq. 10: triples centred at lm (v on its right), v, and w (v on its left)
+            // Eq. 10: triples centred at lm (v on its right), v, and w (v on its
+            // left).  Sec. 2.3 names l_right the length of the edge on the left
+            // of the centre and l_left that of the edge on its right, so an end
+            // vertex takes the share of the edge on the far side of the centre
+            // (the three forces then have no net torque).
             const int lmm = (lm == 0) ? nv - 1 : lm - 1;
             const R kl = kb * (th[lm] - sth0[lm]);
             const R kc = kb * (th[v] - sth0[v]);
             const R kr = kb * (th[w] - sth0[w]);
-            const R cR = kl * len[lm] / (len[lmm] + len[lm]);
-            const R cL = kr * len[v] / (len[v] + len[w]);
+            const R cR = kl * len[lmm] / (len[lmm] + len[lm]);
+            const R cL = kr * len[w] / (len[v] + len[w]);
             fbx = cR * vnx[lm] - kc * vnx[v] + cL * vnx[w];
             fby = cR * vny[lm] - kc * vny[v] + cL * vny[w];
         }
