@@ -381,9 +381,11 @@ lbib_status lbib_describe(lbib_ctx* ctx, int32_t* kernels_per_step, int32_t* nea
  * lattices that do not fit (about 233k nodes in FP32, 116k in FP64) give
  * LBIB_ERR_UNSUPPORTED before any work.  All calls on a device share that
  * array and leave their contents in it; each call clears what must start at
- * zero.  Calls whose GPU work overlaps race on it.  The first call on a device
- * looks up the array's device address (once per device, with that device
- * current), so make that first call before any stream capture.  The call
+ * zero.  Calls whose GPU work overlaps race on it.  Every call looks up the
+ * array's device address with the device current (a lookup allocates nothing
+ * and stays right after a device reset); the first call on a device also
+ * loads the library's device code there, so make it before any stream
+ * capture.  The call
  * waits for its stream and reports divergence as LBIB_ERR_DIVERGED; errors are
  * read with lbib_last_error(NULL). */
 lbib_status lbib_lattice_advance_noalloc(const lbib_fluid_params* params, double* f, int64_t nsteps);

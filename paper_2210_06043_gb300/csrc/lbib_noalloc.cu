@@ -20,7 +20,6 @@
 
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "lbib_internal.cuh"
@@ -30,27 +29,22 @@ using namespace lbib;
 namespace {
 
 constexpr size_t kScratchBytes = size_t(16) << 20;  // 16 MiB per device
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
 size_t up256(size_t n) { return (n + 255) & ~size_t(255); }
 
-// Device address of g_scratch on the current device (looked up once per device;
-// in host code the symbol's name is only a host-side stand-in).
-cudaError_t scratch_address(int dev, void** out)
+// Device address of g_scratch on the current device.  In host code the
+// symbol's name is only a host-side stand-in, so the address is looked up,
+// with the device current, on every call: the lookup allocates nothing, and a
+// cached address would go stale if the caller reset the device (the module is
+// then loaded again, possibly elsewhere).
+cudaError_t scratch_address(void** out)
 {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return e;
+    *out = p;
     return cudaSuccess;
 }
 
@@ -102,7 +96,7 @@ extern "C" lbib_status lbib_lattice_advance_noalloc(const lbib_fluid_params* P, 
     if (P->storage != LBIB_STORE_FP64 && P->storage != LBIB_STORE_FP32)
         return fail_noalloc(LBIB_ERR_UNSUPPORTED, "only FP64 and FP32 storage");
     if (nsteps < 0) return fail_noalloc(LBIB_ERR_INVALID_ARG, "nsteps < 0");
-    if (P->device < 0 || P->device >= kMaxDevices) return fail_noalloc(LBIB_ERR_INVALID_ARG, "device ordinal");
+    if (P->device < 0) return fail_noalloc(LBIB_ERR_INVALID_ARG, "device ordinal");
 
     Lattice L{};
     L.nx = P->nx;
@@ -140,7 +134,7 @@ extern "C" lbib_status lbib_lattice_advance_noalloc(const lbib_fluid_params* P, 
     std::string msg;
     unsigned char* base = nullptr;
     cudaStream_t stream = static_cast<cudaStream_t>(P->cuda_stream);
-    if (e == cudaSuccess) e = scratch_address(P->device, reinterpret_cast<void**>(&base));
+    if (e == cudaSuccess) e = scratch_address(reinterpret_cast<void**>(&base));
     if (e == cudaSuccess) {
         Dev d{};
         d.L = L;

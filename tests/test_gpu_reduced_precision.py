@@ -10,8 +10,7 @@ the last place plus the FP32 bound of the FP32 lattice test.
 The small capillary (240 x 60, biconcave cell + rigid adhering ellipse) run for
 its 2000 steps in each 16-bit storage is compared with the FP64 oracle on every
 quantity the library reports: velocity (relative L2), positions, delta p, r,
-N_L.  The bounds are the measured errors with a margin (the errors are stated
-in the design doc); they are much looser than FP32's because the storage rounding
+N_L.  The bounds are the measured errors with a margin; they are much looser than FP32's because the storage rounding
 of a slowly varying field repeats step after step."""
 import numpy as np
 import pytest

@@ -9,7 +9,7 @@ Parity bars as test_gpu_coupled.py (FP64: positions 1e-9 dx, velocity 1e-9
 relative L2; bond decisions identical up to logged ties).  The generated
 shapes are checked for what the paper says of them, not against numbers: the
 run converged, area is held (k_a = 1 keeps the membrane incompressible,
-P:118), the shape is symmetric about the channel's centre line, and the
+Sec. 2.3), the shape is symmetric about the channel's centre line, and the
 bullet leads with its nose while the parachute's rims trail."""
 import dataclasses
 import math
