@@ -455,7 +455,7 @@ def run_gpu(args):
             "roofline": roofline, "e2e": e2e, "gpu_launches": desc["kernels_per_step"] * K, "clocks": clk,
             "launch_config": dict(tuned, chosen_by=tuned_by),
             "wall_s_timed_region": wall}
-    if batch:
+    if batch and args.plain_steps > 0:
         t_plain = plain_solver(caps, local, args.plain_steps, 3)
         t_batch = dev_s / K
         line["sweep"] = {
@@ -486,7 +486,8 @@ def main():
     ap.add_argument("--impl", default="lbib", choices=["lbib", "reference"])
     ap.add_argument("--workload", default="sweep", choices=["sweep", "production"])
     ap.add_argument("--instances", type=int, default=64, help="first N capillaries of the sweep")
-    ap.add_argument("--plain-steps", type=int, default=50, help="steps per capillary of the plain-solver timing")
+    ap.add_argument("--plain-steps", type=int, default=50,
+                    help="steps per capillary of the plain-solver timing (0: skip it, for profiling runs)")
     ap.add_argument("--cpu-nodes", type=float, default=1.0e8,
                     help="node updates of the CPU oracle sample (about 15 s at 7 MLUPS)")
     ap.add_argument("--tune-steps", type=int, default=0,

@@ -306,10 +306,15 @@ lbib_status lbib_read_kernel_times(lbib_ctx* ctx, float* bulk_ms, float* lagr_ms
 typedef struct {
     int32_t lagrangian_threads; /* threads per membrane block: 256 or 512 */
     int32_t near_blocks;        /* blocks of the near-membrane force gather, >= 1 */
-    int32_t bulk_tiles_y;       /* 32 x 4 node tiles per bulk lattice block, stacked in y: 1, 2 or 4 */
+    int32_t bulk_tiles_y;       /* 32 x 4 node tiles per bulk lattice block, stacked in y: 1, 2 or 4
+                                 * (with 4 nodes per thread: 2, 4 or 8 tile rows of a 128-column
+                                 * strip, 64 columns in FP64 storage) */
     int32_t activation_stride;  /* every k-th element centroid schedules the near tiles around it
                                  * (over a radius grown to cover the k - 1 between): 1, 2 or 4 */
-    int32_t bulk_nodes_per_thread; /* nodes each bulk lattice thread updates: 1 or 2 */
+    int32_t bulk_nodes_per_thread; /* nodes each bulk lattice thread updates: 1 or 2 (of a column),
+                                    * or 4: consecutive nodes of a row (2 in FP64 storage), read and
+                                    * written as one 16-byte (8-byte for 16-bit storage) vector per
+                                    * population, the x shift of the pull done by warp shuffles */
     int32_t observables_branch; /* where the observables record of a step is written: 0 after the
                                  * near update (on the membrane -> near chain), 1 on a branch of its
                                  * own (off the chain, at normal priority) */

@@ -1356,7 +1356,7 @@ bool valid_config(const lbib_launch_config& c)
     return (c.lagrangian_threads == 256 || c.lagrangian_threads == 512) && c.near_blocks >= 1 &&
            (c.bulk_tiles_y == 1 || c.bulk_tiles_y == 2 || c.bulk_tiles_y == 4) &&
            (c.activation_stride == 1 || c.activation_stride == 2 || c.activation_stride == 4) &&
-           (c.bulk_nodes_per_thread == 1 || c.bulk_nodes_per_thread == 2) &&
+           (c.bulk_nodes_per_thread == 1 || c.bulk_nodes_per_thread == 2 || c.bulk_nodes_per_thread == 4) &&
            (c.observables_branch == 0 || c.observables_branch == 1) &&
            (c.chain_programmatic == 0 || c.chain_programmatic == 1) && c.near_update_blocks >= 1 &&
            (c.bulk_tma == 0 || c.bulk_tma == 1);
@@ -1533,7 +1533,7 @@ lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_co
     // revisits each coordinate from the first round's optimum
     for (int round = 0; round < 2; ++round) {
         const lbib_launch_config start = best;
-        for (int npt : {1, 2})
+        for (int npt : {1, 2, 4})
             for (int rt : {1, 2, 4}) {
                 lbib_launch_config c = start;
                 c.bulk_tiles_y = rt;

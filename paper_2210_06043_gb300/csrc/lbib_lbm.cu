@@ -96,58 +96,131 @@ __device__ __forceinline__ void pull(const Lattice& L, const S* __restrict__ fin
     }
 }
 
-// Moments with the half-force shift and the Guo-forced BGK collision, in place.
+// Moments with the half-force shift and the Guo-forced BGK collision.
 // Opposite directions q, o (e_o = -e_q) share the even part of the
 // equilibrium, A = w (drho + rho (9/2 (e.u)^2 - 3/2 u.u)), and differ in the
 // sign of the odd part, B = 3 w rho e_q.u (Eq. 2); likewise the forcing term
-// of Eq. 4.  FORCED = false is the same update for F = 0 (it gives the same
-// values as FORCED = true with F = 0, without the source arithmetic).  The
-// near update (one node per thread) is held to 40 registers in FP32, like the
-// bulk update.
+// of Eq. 4.  The relaxation is g' = (1 - omega) g + omega f_eq with omega
+// folded into the equilibrium terms.  FORCED = false is the same update for
+// F = 0 (it gives the same values as FORCED = true with F = 0, without the
+// source arithmetic).
+//
+// Every operation is explicitly rounded (fused multiply-adds where written,
+// nothing else fused or reordered): the lattice kernels inline these pieces
+// in different orders (a node at a time, or the moments of several nodes
+// first and then one population pair of all of them), and left to the
+// compiler's contraction the same expressions were fused differently in
+// different kernels.  Written out, every kernel gives every node the same
+// bits.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// 1 / rho.  FP32: the hardware's approximate reciprocal refined by one
+// Newton-Raphson step, x' = x + x (1 - rho x), which leaves it within an ulp
+// of the quotient for the densities a stable run has (rho is 1 to within a few
+// per cent; the step needs rho away from zero, infinity and subnormals, where
+// the divergence check has already stopped the run), without the division's
+// special-case branch.  FP64: the correctly rounded quotient.
+__device__ __forceinline__ float recip(float rho)
+{
+    float x;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(x) : "f"(rho));
+    return fma_rn(x, fma_rn(-rho, x, 1.0f), x);
+}
+__device__ __forceinline__ double recip(double rho) { return 1.0 / rho; }
+
+// relaxation constants of one omega (the same in every thread)
+template <typename R>
+struct Relax {
+    R omega, keep, cf;
+    __device__ __forceinline__ explicit Relax(R om)
+        : omega(om), keep(sub_rn(R(1), om)), cf(fma_rn(R(-0.5), om, R(1)))
+    {
+    }
+    __device__ __forceinline__ R ow(int q) const { return mul_rn(omega, wq<R>(q)); }
+    __device__ __forceinline__ R ow3(int q) const { return mul_rn(R(3), mul_rn(omega, wq<R>(q))); }
+    __device__ __forceinline__ R cfw(int q) const { return mul_rn(cf, wq<R>(q)); }
+};
+
+template <typename R>
+struct Mom {
+    R drho, rho, ux, uy, u2, uF;
+};
+
+// Eqs. 5-6: rho - 1, rho and u with the half-force shift
+template <typename R, bool FORCED>
+__device__ __forceinline__ Mom<R> moments(const R g[9], R Fx, R Fy)
+{
+    Mom<R> m;
+    // the x-moving populations' sums serve both the density and jx
+    const R east = add_rn(add_rn(g[1], g[5]), g[8]), west = add_rn(add_rn(g[3], g[6]), g[7]);
+    m.drho = add_rn(add_rn(add_rn(g[0], g[2]), g[4]), add_rn(east, west));
+    m.rho = add_rn(R(1), m.drho);
+    R jx = sub_rn(east, west);
+    R jy = sub_rn(add_rn(add_rn(g[2], g[5]), g[6]), add_rn(add_rn(g[4], g[7]), g[8]));
+    if (FORCED) {
+        jx = fma_rn(R(0.5), Fx, jx);
+        jy = fma_rn(R(0.5), Fy, jy);
+    }
+    const R inv = recip(m.rho);
+    m.ux = mul_rn(jx, inv);
+    m.uy = mul_rn(jy, inv);
+    m.u2 = mul_rn(R(1.5), fma_rn(m.ux, m.ux, mul_rn(m.uy, m.uy)));
+    m.uF = FORCED ? fma_rn(m.ux, Fx, mul_rn(m.uy, Fy)) : R(0);
+    return m;
+}
+
+// rest population after collision
+template <typename R, bool FORCED>
+__device__ __forceinline__ R relax_rest(const Relax<R>& X, R g0, const Mom<R>& m)
+{
+    R r = fma_rn(X.keep, g0, mul_rn(X.ow(0), fma_rn(-m.rho, m.u2, m.drho)));
+    if (FORCED) r = add_rn(r, mul_rn(X.cfw(0), mul_rn(R(-3), m.uF)));
+    return r;
+}
+
+// pair k = 0..3: q = 1, 2, 5, 6 and its opposite o = 3, 4, 7, 8
+__device__ __forceinline__ constexpr int pair_q(int k) { return (k < 2) ? 1 + k : 3 + k; }
+
+template <typename R, bool FORCED>
+__device__ __forceinline__ void relax_pair(const Relax<R>& X, int k, R& gq, R& go, const Mom<R>& m, R Fx, R Fy)
+{
+    const int q = pair_q(k);
+    // e_q . u and e_q . F for e_1 = (1, 0), e_2 = (0, 1), e_5 = (1, 1), e_6 = (-1, 1)
+    const R eu = q == 1 ? m.ux : (q == 2 ? m.uy : (q == 5 ? add_rn(m.ux, m.uy) : sub_rn(m.uy, m.ux)));
+    const R t = fma_rn(mul_rn(R(4.5), eu), eu, -m.u2);
+    const R oA = mul_rn(X.ow(q), fma_rn(m.rho, t, m.drho));
+    const R oB = mul_rn(mul_rn(X.ow3(q), m.rho), eu);
+    R a = fma_rn(X.keep, gq, add_rn(oA, oB));
+    R b = fma_rn(X.keep, go, sub_rn(oA, oB));
+    if (FORCED) {
+        const R eF = q == 1 ? Fx : (q == 2 ? Fy : (q == 5 ? add_rn(Fx, Fy) : sub_rn(Fy, Fx)));
+        const R even = mul_rn(X.cfw(q), fma_rn(mul_rn(R(9), eu), eF, mul_rn(R(-3), m.uF)));
+        const R odd = mul_rn(X.cfw(q), mul_rn(R(3), eF));
+        a = add_rn(a, add_rn(even, odd));
+        b = add_rn(b, sub_rn(even, odd));
+    }
+    gq = a;
+    go = b;
+}
+
 template <typename R, bool FORCED>
 __device__ __forceinline__ void collide_t(R g[9], R Fx, R Fy, R omega, R& drho, R& ux, R& uy)
 {
-    drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-    const R rho = R(1) + drho;
-    R jx = (g[1] + g[5] + g[8]) - (g[3] + g[6] + g[7]);
-    R jy = (g[2] + g[5] + g[6]) - (g[4] + g[7] + g[8]);
-    if (FORCED) {
-        jx += R(0.5) * Fx;
-        jy += R(0.5) * Fy;
-    }
-    const R inv = R(1) / rho;
-    ux = jx * inv;
-    uy = jy * inv;
-    const R u2 = R(1.5) * (ux * ux + uy * uy);
-    const R uF = FORCED ? ux * Fx + uy * Fy : R(0);
-    const R cf = R(1) - R(0.5) * omega;
-    // relaxation as g' = (1 - omega) g + omega f_eq, with omega folded into
-    // the equilibrium terms (one fused multiply-add per direction)
-    const R keep = R(1) - omega;
-    // rest population
-    {
-        const R oeq = (omega * wq<R>(0)) * (drho - rho * u2);
-        g[0] = keep * g[0] + oeq;
-        if (FORCED) g[0] += cf * wq<R>(0) * (R(-3) * uF);
-    }
+    const Relax<R> X(omega);
+    const Mom<R> m = moments<R, FORCED>(g, Fx, Fy);
+    drho = m.drho;
+    ux = m.ux;
+    uy = m.uy;
+    g[0] = relax_rest<R, FORCED>(X, g[0], m);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int q = (k < 2) ? 1 + k : 3 + k;  // 1, 2, 5, 6
-        const int o = op(q);                    // 3, 4, 7, 8
-        const R w = wq<R>(q);
-        const R eu = R(cx(q)) * ux + R(cy(q)) * uy;
-        const R oA = (omega * w) * (drho + rho * (R(4.5) * eu * eu - u2));
-        const R oB = ((R(3) * omega * w) * rho) * eu;
-        g[q] = keep * g[q] + (oA + oB);
-        g[o] = keep * g[o] + (oA - oB);
-        if (FORCED) {
-            const R eF = R(cx(q)) * Fx + R(cy(q)) * Fy;
-            const R even = cf * w * (R(9) * eu * eF - R(3) * uF);
-            const R odd = cf * w * (R(3) * eF);
-            g[q] += even + odd;
-            g[o] += even - odd;
-        }
-    }
+    for (int k = 0; k < 4; ++k) relax_pair<R, FORCED>(X, k, g[pair_q(k)], g[op(pair_q(k))], m, Fx, Fy);
 }
 
 template <typename R>
@@ -159,39 +232,405 @@ __device__ __forceinline__ void collide(R g[9], R Fx, R Fy, R omega, R& drho, R&
 // One block covers RT tiles stacked in y (a TX x RT TY node box) with
 // TX x (RT TY / NPT) threads; a thread updates NPT nodes of one column, NPT
 // rows apart, issuing all their loads before the first collision (more bytes
-// in flight per thread when fewer threads are resident).  A node is skipped
-// when the near kernel owns its tile.
+// in flight per thread when fewer threads are resident).  The block reads its
+// tiles' near flags once (a tile the near kernel owns is skipped) and decides
+// once whether its box touches a wall or an instance's first or last column:
+// an interior box pulls every node with one base offset plus the nine
+// per-plane offsets, which are the same for every thread, and needs no
+// per-node boundary test; a boundary box takes the general pull.
+// at most 40 registers a thread (48 resident warps): the lean address arithmetic let the
+// compiler take 48 at two nodes a thread, which cost a fifth of the resident
+// warps and, inside the step graph, more time than the instructions saved
 template <typename S, typename R, int RT, int NPT, bool FORCED>
-__global__ void __launch_bounds__(TX* TY* RT / NPT) k_bulk(Dev d, int p, int slot)
+__global__ void __launch_bounds__(TX* TY* RT / NPT, 1536 / (TX * TY * RT / NPT)) k_bulk(Dev d, int p, int slot)
 {
     const Lattice& L = d.L;
     constexpr int ROWS = TY * RT, STEP = ROWS / NPT;
     const int4 ci = d.colinfo[blockIdx.x];
+    uint32_t own = 0u;  // bit r: the bulk update owns tile row blockIdx.y RT + r
+#pragma unroll
+    for (int r = 0; r < RT; ++r) {
+        const int t = blockIdx.y * RT + r;
+        if (t < L.nty && !d.nearflag[slot][t * L.ntx + blockIdx.x]) own |= 1u << r;
+    }
+    if (!own) return;  // the whole block
     const int x = blockIdx.x * TX + threadIdx.x;
     const int xl = x - ci.x;
+    const int yb = blockIdx.y * ROWS;
+    const int xt = blockIdx.x * TX - ci.x;  // the tile column's first column within its instance
+    const bool interior = yb > 0 && yb + ROWS < L.ny && xt > 0 && xt + TX < ci.y;
     const S* __restrict__ fin = static_cast<const S*>(d.f[p]);
     S* __restrict__ fout = static_cast<S*>(d.f[p ^ 1]);
     R g[NPT][9];
     bool act[NPT];
+    if (interior) {
+        const int base = (yb + threadIdx.y) * L.nxp + x;
 #pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-        const int y = blockIdx.y * ROWS + threadIdx.y + j * STEP;
-        const int tyl = y / TY;
-        act[j] = (y < L.ny) && (xl < ci.y) && !d.nearflag[slot][tyl * L.ntx + blockIdx.x];
-        if (act[j]) pull<S, R>(L, fin, x, y, xl, ci.y, g[j]);
+        for (int j = 0; j < NPT; ++j) {
+            act[j] = (own >> ((threadIdx.y + j * STEP) / TY)) & 1u;
+            if (act[j])
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    g[j][q] = ld<S, R>(fin + base + j * STEP * L.nxp + (q * L.qstride - cy(q) * L.nxp - cx(q)));
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            const int y = yb + threadIdx.y + j * STEP;
+            act[j] = y < L.ny && xl < ci.y && ((own >> ((threadIdx.y + j * STEP) / TY)) & 1u);
+            if (act[j]) pull<S, R>(L, fin, x, y, xl, ci.y, g[j]);
+        }
     }
+    bool bad = false;
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
         if (!act[j]) continue;
-        const int y = blockIdx.y * ROWS + threadIdx.y + j * STEP;
         R drho, ux, uy;
         collide_t<R, FORCED>(g[j], lat_param<R>(L.gx, L.gx_f), lat_param<R>(L.gy, L.gy_f),
                              lat_param<R>(L.omega, L.omega_f), drho, ux, uy);
-        if (!(drho > R(-1)) || !isfinite(ux + uy)) atomicOr(d.status, ST_DIVERGED);
-        const int base = y * L.nxp + x;
+        if (!(drho > R(-1) && fabs(ux + uy) < R(INFINITY))) bad = true;
+        const int base = (yb + threadIdx.y + j * STEP) * L.nxp + x;
 #pragma unroll
         for (int q = 0; q < 9; ++q) st<S, R>(fout + q * L.qstride + base, g[j][q]);
     }
+    if (bad) atomicOr(d.status, ST_DIVERGED);
+}
+
+// Vectorised bulk update.  A thread updates BV consecutive nodes of a row
+// (BV = 16 bytes of FP32 or FP64 storage, 8 bytes of 16-bit storage) and
+// walks the four rows of its tile row; a warp spans 32 BV node columns and
+// each warp of a block takes one tile row.  The pull reads every population
+// plane as one aligned vector per thread at the row the plane streams from
+// (y - e_y, or the node's own row for a population bounced at a wall), so
+// no node needs its own load or address.  The plus-or-minus-one x shift of
+// the pull becomes a warp shuffle of the vector's end element: a lane takes
+// its left (right) neighbour's last (first) element, and a lane whose
+// neighbour did not load, or that sits at the warp's end, loads that one
+// value itself.  Zou-He then overrides the unknowns of inlet and outlet
+// nodes.  In the periodic mode the lanes holding an instance's first or last
+// column load the populations that wrap around to the other end.  The node update is k_bulk's
+// (same pulled values, same collide_t), so every node gets the same bits.
+template <typename S, typename R, int V>
+struct VecIO;
+template <>
+struct VecIO<float, float, 4> {
+    static __device__ __forceinline__ void ld_shared(const float* p, float o[4])
+    {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
+    }
+    static __device__ __forceinline__ void ld(const float* p, float o[4])
+    {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
+    }
+    static __device__ __forceinline__ void st(float* p, const float o[4])
+    {
+        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+};
+template <>
+struct VecIO<double, double, 2> {
+    static __device__ __forceinline__ void ld_shared(const double* p, double o[2])
+    {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        o[0] = v.x;
+        o[1] = v.y;
+    }
+    static __device__ __forceinline__ void ld(const double* p, double o[2])
+    {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+        o[0] = v.x;
+        o[1] = v.y;
+    }
+    static __device__ __forceinline__ void st(double* p, const double o[2])
+    {
+        *reinterpret_cast<double2*>(p) = make_double2(o[0], o[1]);
+    }
+};
+// bfloat16: element k of a 32-bit word pair sits in bits 16 (k & 1) .. of word
+// k / 2; widening is a shift, narrowing rounds to nearest even (as st<>)
+template <>
+struct VecIO<__nv_bfloat16, float, 4> {
+    static __device__ __forceinline__ void ld_shared(const __nv_bfloat16* p, float o[4])
+    {
+        const uint2 v = *reinterpret_cast<const uint2*>(p);
+        o[0] = __uint_as_float(v.x << 16);
+        o[1] = __uint_as_float(v.x & 0xffff0000u);
+        o[2] = __uint_as_float(v.y << 16);
+        o[3] = __uint_as_float(v.y & 0xffff0000u);
+    }
+    static __device__ __forceinline__ void ld(const __nv_bfloat16* p, float o[4])
+    {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+        o[0] = __uint_as_float(v.x << 16);
+        o[1] = __uint_as_float(v.x & 0xffff0000u);
+        o[2] = __uint_as_float(v.y << 16);
+        o[3] = __uint_as_float(v.y & 0xffff0000u);
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, const float o[4])
+    {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(o[0], o[1]), b = __floats2bfloat162_rn(o[2], o[3]);
+        uint2 v;
+        v.x = *reinterpret_cast<const uint32_t*>(&a);
+        v.y = *reinterpret_cast<const uint32_t*>(&b);
+        *reinterpret_cast<uint2*>(p) = v;
+    }
+};
+// binary16 scaled by HALF_SCALE, as ld<> / st<>
+template <>
+struct VecIO<__half, float, 4> {
+    static __device__ __forceinline__ void ld_shared(const __half* p, float o[4])
+    {
+        const uint2 v = *reinterpret_cast<const uint2*>(p);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+        o[0] = a.x * (1.0f / HALF_SCALE);
+        o[1] = a.y * (1.0f / HALF_SCALE);
+        o[2] = b.x * (1.0f / HALF_SCALE);
+        o[3] = b.y * (1.0f / HALF_SCALE);
+    }
+    static __device__ __forceinline__ void ld(const __half* p, float o[4])
+    {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+        o[0] = a.x * (1.0f / HALF_SCALE);
+        o[1] = a.y * (1.0f / HALF_SCALE);
+        o[2] = b.x * (1.0f / HALF_SCALE);
+        o[3] = b.y * (1.0f / HALF_SCALE);
+    }
+    static __device__ __forceinline__ void st(__half* p, const float o[4])
+    {
+        const __half2 a = __floats2half2_rn(o[0] * HALF_SCALE, o[1] * HALF_SCALE);
+        const __half2 b = __floats2half2_rn(o[2] * HALF_SCALE, o[3] * HALF_SCALE);
+        uint2 v;
+        v.x = *reinterpret_cast<const uint32_t*>(&a);
+        v.y = *reinterpret_cast<const uint32_t*>(&b);
+        *reinterpret_cast<uint2*>(p) = v;
+    }
+};
+
+#ifndef LBIB_VEC_NODES
+#define LBIB_VEC_NODES 4
+#endif
+#ifndef LBIB_VEC_MIN_BLOCKS
+#define LBIB_VEC_MIN_BLOCKS 3
+#endif
+constexpr int VEC_MIN_BLOCKS = LBIB_VEC_MIN_BLOCKS;
+template <>
+struct VecIO<float, float, 2> {
+    static __device__ __forceinline__ void ld(const float* p, float o[2])
+    {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+        o[0] = v.x;
+        o[1] = v.y;
+    }
+    static __device__ __forceinline__ void st(float* p, const float o[2])
+    {
+        *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
+    }
+};
+template <>
+struct VecIO<__nv_bfloat16, float, 2> {
+    static __device__ __forceinline__ void ld(const __nv_bfloat16* p, float o[2])
+    {
+        const uint32_t v = __ldg(reinterpret_cast<const unsigned int*>(p));
+        o[0] = __uint_as_float(v << 16);
+        o[1] = __uint_as_float(v & 0xffff0000u);
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, const float o[2])
+    {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(o[0], o[1]);
+        *reinterpret_cast<uint32_t*>(p) = *reinterpret_cast<const uint32_t*>(&a);
+    }
+};
+template <>
+struct VecIO<__half, float, 2> {
+    static __device__ __forceinline__ void ld(const __half* p, float o[2])
+    {
+        const uint32_t v = __ldg(reinterpret_cast<const unsigned int*>(p));
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v));
+        o[0] = a.x * (1.0f / HALF_SCALE);
+        o[1] = a.y * (1.0f / HALF_SCALE);
+    }
+    static __device__ __forceinline__ void st(__half* p, const float o[2])
+    {
+        const __half2 a = __floats2half2_rn(o[0] * HALF_SCALE, o[1] * HALF_SCALE);
+        *reinterpret_cast<uint32_t*>(p) = *reinterpret_cast<const uint32_t*>(&a);
+    }
+};
+
+template <typename S>
+__host__ __device__ constexpr int vec_width() { return sizeof(S) == 8 ? 2 : LBIB_VEC_NODES; }
+
+// One row of a vectorised bulk thread.  WALL: 0 interior row, 1 the row at
+// y = 0, 2 the row at y = ny - 1 (populations arriving through that wall are
+// bounced from the node's own opposite population: no shift at all).  The
+// moments of the V nodes come first; then each population pair is relaxed
+// for all V nodes and stored as two vectors, so that no node's whole output
+// waits in registers for the others.
+template <typename S, typename R, int V, int WALL, bool FORCED>
+__device__ __forceinline__ bool vec_row(const Lattice& L, const S* __restrict__ fin, S* __restrict__ fout, int x0,
+                                        int xs, int xl0, int nxi, int y, bool act, bool need_l, bool need_r,
+                                        bool bnd)
+{
+    R v[9][V];
+    constexpr bool bb[9] = {false,
+                            false,
+                            WALL == 1,
+                            false,
+                            WALL == 2,
+                            WALL == 1,
+                            WALL == 1,
+                            WALL == 2,
+                            WALL == 2};
+    const int row = y * L.nxp + x0;
+    // every lane loads (a lane that updates nothing reads the first updating
+    // lane's vectors: the requests merge, and the values go unused); loads
+    // under a lane predicate cost the kernel 40 more registers
+    const int rs = y * L.nxp + xs;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const int src = bb[q] ? op(q) * L.qstride + rs : q * L.qstride + rs - cy(q) * L.nxp;
+        VecIO<S, R, V>::ld(fin + src, v[q]);
+    }
+    // the value each shifted plane brings in at the lane's left or right end
+    R in[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        if (bb[q] || cx(q) == 0) continue;
+        const int src = q * L.qstride + row - cy(q) * L.nxp;
+        if (cx(q) == 1) {
+            in[q] = __shfl_up_sync(0xffffffffu, v[q][V - 1], 1);
+            if (need_l) in[q] = xl0 > 0 ? ld<S, R>(fin + src - 1) : R(0);
+        } else {
+            in[q] = __shfl_down_sync(0xffffffffu, v[q][0], 1);
+            if (need_r) in[q] = xl0 + V < nxi ? ld<S, R>(fin + src + V) : R(0);
+        }
+    }
+    if (!act) return false;
+    R g[V][9];
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            if (bb[q] || cx(q) == 0) g[i][q] = v[q][i];
+            else if (cx(q) == 1) g[i][q] = i > 0 ? v[q][i - 1] : in[q];
+            else g[i][q] = i < V - 1 ? v[q][i + 1] : in[q];
+        }
+    }
+    if (bnd) {
+        // lanes holding an instance's first or last column: the populations
+        // entering through the inlet or outlet are Zou-He's unknowns, or, in
+        // the periodic mode, come from the instance's other end
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            const int xl = xl0 + i;
+            if (L.bc == LBIB_BC_PERIODIC_FORCE) {
+                if (xl == 0) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q)
+                        if (!bb[q] && cx(q) == 1)
+                            g[i][q] = ld<S, R>(fin + q * L.qstride + row - cy(q) * L.nxp + i + nxi - 1);
+                }
+                if (xl == nxi - 1) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q)
+                        if (!bb[q] && cx(q) == -1)
+                            g[i][q] = ld<S, R>(fin + q * L.qstride + row - cy(q) * L.nxp + i - (nxi - 1));
+                }
+            } else if (xl == 0) {
+                zou_he_inlet<R>(g[i], inlet_profile<R>(L, y));
+            } else if (xl == nxi - 1) {
+                zou_he_outlet<R>(g[i], lat_param<R>(L.rho_out, L.rho_out_f));
+            }
+        }
+    }
+    const R Fx = lat_param<R>(L.gx, L.gx_f), Fy = lat_param<R>(L.gy, L.gy_f);
+    const Relax<R> X(lat_param<R>(L.omega, L.omega_f));
+    Mom<R> m[V];
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        m[i] = moments<R, FORCED>(g[i], Fx, Fy);
+        if (xl0 + i < nxi && !(m[i].drho > R(-1) && fabs(m[i].ux + m[i].uy) < R(INFINITY))) bad = true;
+    }
+    const bool full = xl0 + V <= nxi;
+    auto store = [&](int q, const R o[V]) {
+        if (full) {
+            VecIO<S, R, V>::st(fout + q * L.qstride + row, o);
+        } else {
+            // the instance ends inside the vector: only its own columns are written
+#pragma unroll
+            for (int i = 0; i < V; ++i)
+                if (xl0 + i < nxi) st<S, R>(fout + q * L.qstride + row + i, o[i]);
+        }
+    };
+    {
+        R o[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) o[i] = relax_rest<R, FORCED>(X, g[i][0], m[i]);
+        store(0, o);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int q = pair_q(k), o = op(q);
+        R a[V], b[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+            a[i] = g[i][q];
+            b[i] = g[i][o];
+            relax_pair<R, FORCED>(X, k, a[i], b[i], m[i], Fx, Fy);
+        }
+        store(q, a);
+        store(o, b);
+    }
+    return bad;
+}
+
+template <typename S, typename R, int V, bool FORCED>
+__global__ void __launch_bounds__(256, VEC_MIN_BLOCKS) k_bulk_vec(Dev d, int p, int slot)
+{
+    const Lattice& L = d.L;
+    const int lane = threadIdx.x;
+    const int x0 = (blockIdx.x * 32 + lane) * V;
+    const int ty = blockIdx.y * blockDim.y + threadIdx.y;  // the warp's tile row
+    if (ty >= L.nty) return;                                // whole warps
+    const int tx = x0 / TX;
+    bool act = false;
+    int xl0 = 0, nxi = 0;
+    if (x0 < L.nxp) {
+        const int4 ci = d.colinfo[tx];
+        xl0 = x0 - ci.x;
+        nxi = ci.y;
+        act = xl0 < nxi && !d.nearflag[slot][ty * L.ntx + tx];
+    }
+    const uint32_t am = __ballot_sync(0xffffffffu, act);
+    if (am == 0u) return;
+    const bool need_l = act && (lane == 0 || !((am >> (lane - 1)) & 1u));
+    const bool need_r = act && (lane == 31 || !((am >> (lane + 1)) & 1u));
+    const bool bnd = act && (xl0 == 0 || xl0 + V >= nxi);
+    const int xs = act ? x0 : (blockIdx.x * 32 + __ffs(am) - 1) * V;  // where this lane's vectors come from
+    const S* __restrict__ fin = static_cast<const S*>(d.f[p]);
+    S* __restrict__ fout = static_cast<S*>(d.f[p ^ 1]);
+    bool bad = false;
+    // interior rows first, then the wall rows (each in a code region of its
+    // own: one loop over the three row kinds needed twice the registers)
+    const int y0 = ty * TY, y1 = min(y0 + TY, L.ny);
+#pragma unroll 1
+    for (int y = max(y0, 1); y < min(y1, L.ny - 1); ++y)
+        bad |= vec_row<S, R, V, 0, FORCED>(L, fin, fout, x0, xs, xl0, nxi, y, act, need_l, need_r, bnd);
+    if (y0 == 0) bad |= vec_row<S, R, V, 1, FORCED>(L, fin, fout, x0, xs, xl0, nxi, 0, act, need_l, need_r, bnd);
+    if (y1 == L.ny)
+        bad |= vec_row<S, R, V, 2, FORCED>(L, fin, fout, x0, xs, xl0, nxi, L.ny - 1, act, need_l, need_r, bnd);
+    if (bad) atomicOr(d.status, ST_DIVERGED);
 }
 
 // TMA-staged bulk update.  A job is a 32 x 8 node box (two tiles of one tile
@@ -780,11 +1219,29 @@ static void launch_bulk_tma(const Dev& d, int parity, int slot, cudaStream_t s)
     });
 }
 
+static void launch_bulk_vec(const Dev& d, int parity, int slot, cudaStream_t s)
+{
+    const int rt = (d.bulk_tiles_y == 2 || d.bulk_tiles_y == 4) ? d.bulk_tiles_y : 1;
+    const dim3 block(32, 2 * rt);  // a warp per tile row
+    const bool forced = d.L.gx != 0.0 || d.L.gy != 0.0;
+    by_store(d.store, [&](auto sp, auto rp) {
+        LBIB_TYPES(sp, rp);
+        constexpr int V = vec_width<S>();
+        const dim3 grid((d.L.nxp + 32 * V - 1) / (32 * V), (d.L.nty + block.y - 1) / block.y);
+        if (forced) k_bulk_vec<S, R, V, true><<<grid, block, 0, s>>>(d, parity, slot);
+        else k_bulk_vec<S, R, V, false><<<grid, block, 0, s>>>(d, parity, slot);
+    });
+}
+
 cudaError_t launch_lbm_bulk(const Dev& d, int prec, int parity, int slot, cudaStream_t s)
 {
     (void)prec;  // the storage type fixes the compute type
     if (d.bulk_tma && d.fmaps) {
         launch_bulk_tma(d, parity, slot, s);
+        return cudaGetLastError();
+    }
+    if (d.bulk_nodes_per_thread == 4) {
+        launch_bulk_vec(d, parity, slot, s);
         return cudaGetLastError();
     }
     const int v = 10 * (d.bulk_tiles_y == 2 || d.bulk_tiles_y == 4 ? d.bulk_tiles_y : 1) +

@@ -144,3 +144,65 @@ def test_tma_staged_bulk_update_equals_direct_loads(storage, bc):
         out.append(s.populations())
         s.close()
     assert np.array_equal(out[0], out[1])
+
+
+# the vectorised bulk update (bulk_nodes_per_thread = 4): shuffled x shifts,
+# edge loads at warp ends, wall rows, Zou-He or periodic wrap in the lanes
+# holding an instance's end columns, partial vectors at a ragged end
+_VEC = dict(_TMA, bulk_tma=0, bulk_nodes_per_thread=4)
+
+
+@pytest.mark.parametrize("nx,ny", SHAPES + [(130, 6), (261, 13)])
+@pytest.mark.parametrize("bc", [lbib.LBIB_BC_INLET_OUTLET, lbib.LBIB_BC_PERIODIC_FORCE])
+@pytest.mark.parametrize("rt", [1, 4])
+def test_vector_bulk_update_matches_oracle_fp64(nx, ny, bc, rt):
+    f0 = wl.random_populations(nx, ny, seed=nx * 11 + ny, eps=1e-2)
+    g = (2e-5, -1e-5) if bc == lbib.LBIB_BC_PERIODIC_FORCE else (0.0, 0.0)
+    o, s = _pair(nx, ny, bc, lbib.LBIB_STORE_FP64, f0, g=g)
+    s.set_launch_config(**dict(_VEC, bulk_tiles_y=rt))
+    assert s.launch_config()["bulk_nodes_per_thread"] == 4
+    for n in (1, 4):
+        o.step(n)
+        s.advance(n)
+        assert np.abs(s.populations() - o.fpost()).max() < 1e-14
+    s.close()
+
+
+@pytest.mark.parametrize("storage", [lbib.LBIB_STORE_FP32, lbib.LBIB_STORE_BF16, lbib.LBIB_STORE_FP16])
+@pytest.mark.parametrize("bc", [lbib.LBIB_BC_INLET_OUTLET, lbib.LBIB_BC_PERIODIC_FORCE])
+@pytest.mark.parametrize("nx,ny", [(100, 23), (3, 2), (261, 13)])
+def test_vector_bulk_update_equals_one_node_per_thread(storage, bc, nx, ny):
+    f0 = wl.random_populations(nx, ny, seed=13 + nx, eps=1e-2)
+    g = (2e-5, -1e-5) if bc == lbib.LBIB_BC_PERIODIC_FORCE else (0.0, 0.0)
+    out = []
+    for npt in (1, 4):
+        s = lbib.Solver(nx, ny, tau=0.8, re=5.0, bc=bc, g=g, storage=storage)
+        s.write_populations(f0)
+        s.set_launch_config(**dict(_VEC, bulk_nodes_per_thread=npt))
+        s.advance(6)
+        out.append(s.populations())
+        s.close()
+    assert np.array_equal(out[0], out[1])
+
+
+def test_vector_bulk_update_in_a_ragged_batch_equals_lone_runs():
+    """Instances of 37, 3, 130 and 261 columns side by side (each starting on
+    a tile column): the vector lanes at an instance's end see the next
+    instance's columns as neighbours, and must not take their values."""
+    widths = [37, 3, 130, 261]
+    ny = 11
+    caps = [wl.Capillary(f"w{n}", n, ny, 0.9, 5.0, 0, "fp32", 0, []) for n in widths]
+    f0 = [wl.random_populations(n, ny, seed=n, eps=1e-2) for n in widths]
+    b = lbib.from_capillaries(caps)
+    for k, f in enumerate(f0):
+        b.write_populations(f, instance=k)
+    b.set_launch_config(**_VEC)
+    b.advance(5)
+    for k, c in enumerate(caps):
+        s = lbib.from_capillary(c)
+        s.write_populations(f0[k])
+        s.set_launch_config(**dict(_VEC, bulk_nodes_per_thread=1))
+        s.advance(5)
+        assert np.array_equal(b.populations(instance=k), s.populations()), c.name
+        s.close()
+    b.close()

@@ -16,7 +16,8 @@ from paper_2210_06043_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 CONFIGS = [(512, 608, 1, 4, 1, 0, 0, 2432, 0), (256, 300, 2, 1, 2, 1, 1, 1, 1), (256, 1, 4, 2, 1, 0, 1, 608, 0),
-           (512, 2000, 4, 1, 2, 1, 0, 7, 1), (512, 9, 1, 2, 2, 0, 1, 5000, 0), (512, 608, 1, 1, 2, 0, 0, 2432, 1)]
+           (512, 2000, 4, 1, 2, 1, 0, 7, 1), (512, 9, 1, 2, 2, 0, 1, 5000, 0), (512, 608, 1, 1, 2, 0, 0, 2432, 1),
+           (512, 608, 1, 1, 4, 0, 0, 2432, 0), (256, 300, 4, 2, 4, 1, 1, 16, 0), (512, 17, 2, 4, 4, 0, 0, 608, 0)]
 
 
 def _snapshot(s, caps):
@@ -94,6 +95,7 @@ def test_autotune_leaves_the_state_and_cursors_unchanged():
 def test_invalid_launch_configurations_are_rejected():
     s = lbib.from_capillary(wl.small_capillary())
     for bad in ((128, 100, 1, 4), (512, 0, 1, 4), (512, 100, 3, 4), (512, 100, 1, 3), (512, 100, 1, 4, 3),
+                (512, 100, 1, 4, 8),
                 (512, 100, 1, 4, 1, 2), (512, 100, 1, 4, 1, 0, 2), (512, 100, 1, 4, 1, 0, 0, -1), (512, 100, 1, 4, 1, 0, 0, 100, 2)):
         with pytest.raises(lbib.LbibError) as e:
             s.set_launch_config(*bad)
