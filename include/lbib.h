@@ -395,6 +395,29 @@ lbib_status lbib_describe(lbib_ctx* ctx, int32_t* kernels_per_step, int32_t* nea
  * read with lbib_last_error(NULL). */
 lbib_status lbib_lattice_advance_noalloc(const lbib_fluid_params* params, double* f, int64_t nsteps);
 
+/* Fault injection for failure-detection tests.  The paper has no
+ * counterpart; nothing here faults, traps or hangs a GPU.
+ *
+ * lbib_inject_fault(ctx, LBIB_FAULT_WAIT_TIMEOUT) sets, in stream order after
+ * the work enqueued so far, the device status bit that a kernel's bounded
+ * wait sets when it gives up (a bulk-update block waiting for a tensor copy).
+ * The next call that checks the device status (lbib_sync, any read) returns
+ * LBIB_ERR_TIMEOUT.  The context then refuses lbib_advance (LBIB_ERR_TIMEOUT)
+ * until lbib_load_state restores a saved state.  A real timeout behaves the
+ * same way: the blocks that gave up left nodes unupdated.  Other kinds give
+ * LBIB_ERR_INVALID_ARG.
+ *
+ * lbib_inject_alloc_failure(n) makes the (n + 1)-th device allocation the
+ * library makes in this process, from now on, fail as if the device were out
+ * of memory (n = 0: the next one), once; n < 0 cancels.  The call that
+ * allocates returns LBIB_ERR_OOM and keeps nothing it allocated:
+ * lbib_create frees everything itself; after a failed lbib_add_membrane,
+ * lbib_advance or lbib_mlp_create the caller destroys the object as usual.
+ * It applies to every context and thread of the process. */
+enum { LBIB_FAULT_WAIT_TIMEOUT = 1 };
+lbib_status lbib_inject_fault(lbib_ctx* ctx, int32_t kind);
+void lbib_inject_alloc_failure(int64_t after);
+
 /* Message of the last failed call on ctx (or of the last failed lbib_create
  * or lbib_lattice_advance_noalloc when ctx is NULL).  Valid until the next
  * call on ctx. */

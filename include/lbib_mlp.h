@@ -98,6 +98,17 @@ lbib_status lbib_mlp_param_count(lbib_mlp* net, size_t* n);
 lbib_status lbib_mlp_get_params(lbib_mlp* net, float* params, size_t n);
 lbib_status lbib_mlp_set_params(lbib_mlp* net, const float* params, size_t n);
 
+/* Waits for the context stream and reads the tensor-core kernels' status
+ * word: LBIB_ERR_TIMEOUT when one of their bounded waits gave up (that
+ * call's products are incomplete).  From then on the network refuses work
+ * (LBIB_ERR_TIMEOUT from forward, train_step, backward, apply_gradient and
+ * gradients; gradients and get_params also check the word) until
+ * lbib_mlp_set_params loads parameters again. */
+lbib_status lbib_mlp_sync(lbib_mlp* net);
+/* Fault injection for failure-detection tests (no counterpart in the paper;
+ * nothing faults or hangs a GPU): kind LBIB_FAULT_WAIT_TIMEOUT sets, in
+ * stream order, the status bit a bounded wait sets when it gives up. */
+lbib_status lbib_mlp_inject_fault(lbib_mlp* net, int32_t kind);
 /* Releases every resource of net (NULL is ignored). */
 void lbib_mlp_destroy(lbib_mlp* net);
 

@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -80,7 +81,7 @@ template <typename T>
 cudaError_t dalloc(std::vector<void*>& reg, T** p, size_t n)
 {
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+    cudaError_t e = device_malloc(&q, std::max<size_t>(n, 1) * sizeof(T));
     if (e == cudaSuccess) {
         reg.push_back(q);
         *p = static_cast<T*>(q);
@@ -91,6 +92,25 @@ cudaError_t dalloc(std::vector<void*>& reg, T** p, size_t n)
 }  // namespace
 
 void lbib::set_global_error(const char* msg) { g_create_error = msg; }
+
+namespace lbib {
+__global__ void k_raise_status(uint32_t* status, uint32_t bits) { atomicOr(status, bits); }
+}  // namespace lbib
+
+// allocations left before the injected failure (-1: none injected)
+static std::atomic<long long> g_alloc_countdown{-1};
+
+cudaError_t lbib::device_malloc(void** p, size_t bytes)
+{
+    long long c = g_alloc_countdown.load();
+    while (c >= 0) {
+        if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) {
+            if (c == 0) return cudaErrorMemoryAllocation;  // the injected failure (once)
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
 
 struct lbib_ctx {
     std::string err;
@@ -136,6 +156,10 @@ struct lbib_ctx {
     std::vector<int> mark_off, lig_off;    // body id -> first marker / first ligand site
     int4* colinfo = nullptr;
     InstConst* inst = nullptr;
+    // a fault after which the state cannot be trusted (a bounded device wait
+    // gave up, so some nodes or markers were not updated): lbib_advance refuses
+    // until lbib_load_state restores a saved state
+    lbib_status fault = LBIB_OK;
 };
 
 namespace {
@@ -183,7 +207,10 @@ lbib_status check_status(lbib_ctx* ctx)
         return fail(ctx, LBIB_ERR_STATE, "an interpolation stencil left the tiles updated as near-membrane");
     if (st & ST_SPREAD_MISS)
         return fail(ctx, LBIB_ERR_STATE, "a spreading stencil left the tiles scheduled as near-membrane");
-    if (st & ST_TMA_TIMEOUT) return fail(ctx, LBIB_ERR_TIMEOUT, "a bulk-update block gave up waiting for a tensor copy");
+    if (st & ST_TMA_TIMEOUT) {
+        ctx->fault = LBIB_ERR_TIMEOUT;
+        return fail(ctx, LBIB_ERR_TIMEOUT, "a bulk-update block gave up waiting for a tensor copy");
+    }
     return LBIB_OK;
 }
 
@@ -295,14 +322,15 @@ lbib_status upload_posf(lbib_ctx* ctx, int k)
     Dev& d = ctx->d;
     const size_t nm = std::max(d.nmark, 1);
     std::vector<double> pos(2 * nm);
-    CK(cudaMemcpy(pos.data(), d.pos[k], pos.size() * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(pos.data(), d.pos[k], pos.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     if (ctx->prec == PREC_F64) {
         std::vector<double> f(4 * nm, 0.0);
         for (size_t i = 0; i < nm; ++i) {
             f[i] = pos[i];
             f[2 * nm + i] = pos[nm + i];
         }
-        CK(cudaMemcpy(d.posf[k], f.data(), f.size() * 8, cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(d.posf[k], f.data(), f.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
     } else {
         std::vector<float> f(4 * nm, 0.f);
         for (size_t i = 0; i < nm; ++i) {
@@ -312,7 +340,7 @@ lbib_status upload_posf(lbib_ctx* ctx, int k)
             f[2 * nm + i] = hy;
             f[3 * nm + i] = (float)(pos[nm + i] - (double)hy);
         }
-        CK(cudaMemcpy(d.posf[k], f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(d.posf[k], f.data(), f.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
     }
     return LBIB_OK;
 }
@@ -525,46 +553,47 @@ lbib_status finalize(lbib_ctx* ctx)
     d.site_off = dsite;
 
     auto up_real = [&](void* dst, const std::vector<double>& src) -> cudaError_t {
-        if (ctx->prec == PREC_F64) return cudaMemcpy(dst, src.data(), src.size() * 8, cudaMemcpyHostToDevice);
+        if (ctx->prec == PREC_F64)
+            return cudaMemcpyAsync(dst, src.data(), src.size() * 8, cudaMemcpyHostToDevice, ctx->stream);
         std::vector<float> t(src.begin(), src.end());
-        return cudaMemcpy(dst, t.data(), t.size() * 4, cudaMemcpyHostToDevice);
+        return cudaMemcpyAsync(dst, t.data(), t.size() * 4, cudaMemcpyHostToDevice, ctx->stream);
     };
-    CK(cudaMemcpy(d.pos[0], pos.data(), pos.size() * 8, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d.pos[1], pos.data(), pos.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(d.pos[0], pos.data(), pos.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(d.pos[1], pos.data(), pos.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
     for (int k = 0; k < 2; ++k) {
         lbib_status st = upload_posf(ctx, k);
         if (st != LBIB_OK) return st;
     }
-    if (nb) CK(cudaMemcpy(dbody, bc.data(), bc.size() * sizeof(BodyConst), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->inst, ic.data(), ic.size() * sizeof(InstConst), cudaMemcpyHostToDevice));
+    if (nb) CK(cudaMemcpyAsync(dbody, bc.data(), bc.size() * sizeof(BodyConst), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->inst, ic.data(), ic.size() * sizeof(InstConst), cudaMemcpyHostToDevice, ctx->stream));
     {
         // tile-column table with the instances' first markers, now known
         std::vector<int4> cols;
         for (int i = 0; i < ni; ++i)
             for (int c = 0; c < (ic[i].nx + TX - 1) / TX; ++c)
                 cols.push_back(make_int4(ic[i].x0, ic[i].nx, ic[i].moff, i));
-        CK(cudaMemcpy(ctx->colinfo, cols.data(), cols.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(ctx->colinfo, cols.data(), cols.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
     }
-    CK(cudaMemcpy(d.rigid, rig.data(), rig.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(d.rigid, rig.data(), rig.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
     CK(up_real(dl0, l0));
     CK(up_real(dth0, th0));
-    CK(cudaMemcpy(drref, rref.data(), rref.size() * 8, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(dligel, lig_el.data(), lig_el.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(drref, rref.data(), rref.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(dligel, lig_el.data(), lig_el.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
     CK(up_real(dligt, lig_t));
-    CK(cudaMemcpy(d.bound, bound.data(), bound.size() * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d.anchor, anchor.data(), anchor.size() * 8, cudaMemcpyHostToDevice));
-    CK(cudaMemset(d.margin, 0, nl1 * rs));
-    CK(cudaMemcpy(dsite, site_off.data(), site_off.size() * 4, cudaMemcpyHostToDevice));
-    CK(cudaMemset(d.diag, 0, (size_t)NDIAG * nm1 * rs));
-    CK(cudaMemcpy(d.body_obs[0], bobs.data(), bobs.size() * 8, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d.body_obs[1], bobs.data(), bobs.size() * 8, cudaMemcpyHostToDevice));
-    CK(cudaMemset(d.ring, 0, (size_t)ni * d.ring_cap * sizeof(lbib_obs)));
+    CK(cudaMemcpyAsync(d.bound, bound.data(), bound.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(d.anchor, anchor.data(), anchor.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(d.margin, 0, nl1 * rs, ctx->stream));
+    CK(cudaMemcpyAsync(dsite, site_off.data(), site_off.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(d.diag, 0, (size_t)NDIAG * nm1 * rs, ctx->stream));
+    CK(cudaMemcpyAsync(d.body_obs[0], bobs.data(), bobs.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(d.body_obs[1], bobs.data(), bobs.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(d.ring, 0, (size_t)ni * d.ring_cap * sizeof(lbib_obs), ctx->stream));
     for (int k = 0; k < 2; ++k) {
-        CK(cudaMemset(d.mki[k], 0, 2 * nm1 * 4));
-        CK(cudaMemset(d.mkf[k], 0, 4 * nm1 * rs));
+        CK(cudaMemsetAsync(d.mki[k], 0, 2 * nm1 * 4, ctx->stream));
+        CK(cudaMemsetAsync(d.mkf[k], 0, 4 * nm1 * rs, ctx->stream));
     }
-    CK(cudaMemset(d.mask[0], 0, (size_t)L.ntiles * d.mw * 4));
-    CK(cudaMemset(d.mask[1], 0, (size_t)L.ntiles * d.mw * 4));
+    CK(cudaMemsetAsync(d.mask[0], 0, (size_t)L.ntiles * d.mw * 4, ctx->stream));
+    CK(cudaMemsetAsync(d.mask[1], 0, (size_t)L.ntiles * d.mw * 4, ctx->stream));
     if (nb) {
         if (lagrangian_smem_bytes(ctx->prec, d.nv_max) > 227 * 1024)
             return fail(ctx, LBIB_ERR_UNSUPPORTED, "membrane too large for one block's shared memory");
@@ -713,45 +742,10 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     } while (0)
     auto& reg = ctx->allocs;
     size_t nq = (size_t)9 * qs, nn = (size_t)qs;
-    CKC(dalloc(reg, reinterpret_cast<char**>(&d.f[0]), nq * ctx->ssz));
-    CKC(dalloc(reg, reinterpret_cast<char**>(&d.f[1]), nq * ctx->ssz));
-    CKC(dalloc(reg, reinterpret_cast<char**>(&d.drho), nn * ctx->rsz));
-    CKC(dalloc(reg, reinterpret_cast<char**>(&d.ux), nn * ctx->rsz));
-    CKC(dalloc(reg, reinterpret_cast<char**>(&d.uy), nn * ctx->rsz));
-    CKC(dalloc(reg, reinterpret_cast<char**>(&d.fx), nn * ctx->rsz));
-    CKC(dalloc(reg, reinterpret_cast<char**>(&d.fy), nn * ctx->rsz));
-    CKC(dalloc(reg, &d.fresh, L.ntiles));
-    for (int i = 0; i < 3; ++i) CKC(dalloc(reg, &d.nearflag[i], L.ntiles));
-    for (int i = 0; i < 3; ++i) CKC(dalloc(reg, &d.list[i], d.list_cap));
-    CKC(dalloc(reg, &d.count, 3));
-    CKC(dalloc(reg, &d.step, 1));
-    CKC(dalloc(reg, &d.status, 1));
-    CKC(dalloc(reg, &d.ticket, 1));
-    CKC(dalloc(reg, &ctx->colinfo, cols.size()));
-    CKC(dalloc(reg, &ctx->inst, (size_t)ninst));
-    d.colinfo = ctx->colinfo;
-    d.inst = ctx->inst;
-    CKC(cudaMemcpy(ctx->colinfo, cols.data(), cols.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    CKC(cudaMemset(d.f[0], 0, nq * ctx->ssz));
-    CKC(cudaMemset(d.f[1], 0, nq * ctx->ssz));
-    // tensor maps for the TMA-staged bulk update (left out where the driver
-    // has no encoder: the direct-load kernel then runs whatever the option)
-    d.bulk_tma = 0;
-    d.fmaps = nullptr;
-    if (make_population_maps(d, ctx->fmaps) == cudaSuccess && configure_bulk_tma(d.store) == cudaSuccess)
-        d.fmaps = ctx->fmaps;
-    cudaGetLastError();
-    CKC(cudaMemset(d.drho, 0, nn * ctx->rsz));
-    CKC(cudaMemset(d.ux, 0, nn * ctx->rsz));
-    CKC(cudaMemset(d.uy, 0, nn * ctx->rsz));
-    CKC(cudaMemset(d.fx, 0, nn * ctx->rsz));
-    CKC(cudaMemset(d.fy, 0, nn * ctx->rsz));
-    CKC(cudaMemset(d.fresh, 0x80, L.ntiles * 4));  // matches no step
-    for (int i = 0; i < 3; ++i) CKC(cudaMemset(d.nearflag[i], 0, L.ntiles * 4));
-    CKC(cudaMemset(d.count, 0, 12));
-    CKC(cudaMemset(d.step, 0, 8));
-    CKC(cudaMemset(d.status, 0, 4));
-    CKC(cudaMemset(d.ticket, 0, 4));
+    // streams first: every set-up copy and fill below is ordered on the
+    // context stream (a fill on the legacy default stream is not ordered with
+    // this non-blocking stream, and with other contexts' work in flight the
+    // initial populations were overwritten by their own zero fill)
     if (P->cuda_stream) {
         ctx->stream = static_cast<cudaStream_t>(P->cuda_stream);
     } else {
@@ -771,6 +765,45 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     CKC(cudaEventCreateWithFlags(&ctx->ev_lag, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&ctx->ev_obs, cudaEventDisableTiming));
     for (int i = 0; i < 6; ++i) CKC(cudaEventCreate(&ctx->pe[i]));
+    CKC(dalloc(reg, reinterpret_cast<char**>(&d.f[0]), nq * ctx->ssz));
+    CKC(dalloc(reg, reinterpret_cast<char**>(&d.f[1]), nq * ctx->ssz));
+    CKC(dalloc(reg, reinterpret_cast<char**>(&d.drho), nn * ctx->rsz));
+    CKC(dalloc(reg, reinterpret_cast<char**>(&d.ux), nn * ctx->rsz));
+    CKC(dalloc(reg, reinterpret_cast<char**>(&d.uy), nn * ctx->rsz));
+    CKC(dalloc(reg, reinterpret_cast<char**>(&d.fx), nn * ctx->rsz));
+    CKC(dalloc(reg, reinterpret_cast<char**>(&d.fy), nn * ctx->rsz));
+    CKC(dalloc(reg, &d.fresh, L.ntiles));
+    for (int i = 0; i < 3; ++i) CKC(dalloc(reg, &d.nearflag[i], L.ntiles));
+    for (int i = 0; i < 3; ++i) CKC(dalloc(reg, &d.list[i], d.list_cap));
+    CKC(dalloc(reg, &d.count, 3));
+    CKC(dalloc(reg, &d.step, 1));
+    CKC(dalloc(reg, &d.status, 1));
+    CKC(dalloc(reg, &d.ticket, 1));
+    CKC(dalloc(reg, &ctx->colinfo, cols.size()));
+    CKC(dalloc(reg, &ctx->inst, (size_t)ninst));
+    d.colinfo = ctx->colinfo;
+    d.inst = ctx->inst;
+    CKC(cudaMemcpyAsync(ctx->colinfo, cols.data(), cols.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+    CKC(cudaMemsetAsync(d.f[0], 0, nq * ctx->ssz, ctx->stream));
+    CKC(cudaMemsetAsync(d.f[1], 0, nq * ctx->ssz, ctx->stream));
+    // tensor maps for the TMA-staged bulk update (left out where the driver
+    // has no encoder: the direct-load kernel then runs whatever the option)
+    d.bulk_tma = 0;
+    d.fmaps = nullptr;
+    if (make_population_maps(d, ctx->fmaps) == cudaSuccess && configure_bulk_tma(d.store) == cudaSuccess)
+        d.fmaps = ctx->fmaps;
+    cudaGetLastError();
+    CKC(cudaMemsetAsync(d.drho, 0, nn * ctx->rsz, ctx->stream));
+    CKC(cudaMemsetAsync(d.ux, 0, nn * ctx->rsz, ctx->stream));
+    CKC(cudaMemsetAsync(d.uy, 0, nn * ctx->rsz, ctx->stream));
+    CKC(cudaMemsetAsync(d.fx, 0, nn * ctx->rsz, ctx->stream));
+    CKC(cudaMemsetAsync(d.fy, 0, nn * ctx->rsz, ctx->stream));
+    CKC(cudaMemsetAsync(d.fresh, 0x80, L.ntiles * 4, ctx->stream));  // matches no step
+    for (int i = 0; i < 3; ++i) CKC(cudaMemsetAsync(d.nearflag[i], 0, L.ntiles * 4, ctx->stream));
+    CKC(cudaMemsetAsync(d.count, 0, 12, ctx->stream));
+    CKC(cudaMemsetAsync(d.step, 0, 8, ctx->stream));
+    CKC(cudaMemsetAsync(d.status, 0, 4, ctx->stream));
+    CKC(cudaMemsetAsync(d.ticket, 0, 4, ctx->stream));
     CKC(launch_init_populations(d, ctx->prec, 0, ctx->stream));
     CKC(cudaStreamSynchronize(ctx->stream));
 #undef CKC
@@ -852,6 +885,8 @@ lbib_status lbib_advance(lbib_ctx* ctx, int64_t nsteps)
 {
     if (!ctx) return fail(ctx, LBIB_ERR_INVALID_ARG, "null context");
     if (nsteps < 0) return fail(ctx, LBIB_ERR_INVALID_ARG, "nsteps < 0");
+    if (ctx->fault != LBIB_OK)
+        return fail(ctx, ctx->fault, "a bounded device wait gave up earlier: restore a saved state (lbib_load_state)");
     DeviceGuard guard(ctx->device);
     lbib_status s = finalize(ctx);
     if (s != LBIB_OK) return s;
@@ -1035,8 +1070,9 @@ lbib_status lbib_write_instance_populations(lbib_ctx* ctx, int32_t instance, con
     CK(cudaStreamSynchronize(ctx->stream));
     char* dst = static_cast<char*>(ctx->d.f[0]);
     for (int q = 0; q < 9; ++q)
-        CK(cudaMemcpy2D(dst + ((size_t)q * L.qstride + x0) * es, (size_t)L.nxp * es, raw.data() + (size_t)q * nn * es,
-                        (size_t)inx * es, (size_t)inx * es, L.ny, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy2DAsync(dst + ((size_t)q * L.qstride + x0) * es, (size_t)L.nxp * es,
+                             raw.data() + (size_t)q * nn * es, (size_t)inx * es, (size_t)inx * es, L.ny,
+                             cudaMemcpyHostToDevice, ctx->stream));
     return LBIB_OK;
 }
 
@@ -1269,12 +1305,12 @@ lbib_status save_into(lbib_ctx* ctx, char* p, cudaMemcpyKind kind)
     const int64_t st = ctx->s_f;
     CkHeader h{kMagic, d.L.nx, d.L.ny, d.nbodies, d.nmark, d.nlig, ctx->prec, st, ctx->ninst, 0};
     if (kind == cudaMemcpyDeviceToHost) std::memcpy(p, &h, sizeof(h));
-    else CK(cudaMemcpy(p, &h, sizeof(h), cudaMemcpyHostToDevice));
+    else CK(cudaMemcpyAsync(p, &h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
     p += sizeof(h);
     size_t nq = (size_t)9 * d.L.qstride;
     size_t nm = std::max(d.nmark, 1), nl = std::max(d.nlig, 1), nb = std::max(d.nbodies, 1);
     auto put = [&](const void* src, size_t n) -> cudaError_t {
-        cudaError_t e = cudaMemcpy(p, src, n, kind);
+        cudaError_t e = cudaMemcpyAsync(p, src, n, kind, ctx->stream);
         p += n;
         return e;
     };
@@ -1303,7 +1339,10 @@ lbib_status load_from(lbib_ctx* ctx, const char* p, cudaMemcpyKind kind)
     Dev& d = ctx->d;
     CkHeader h;
     if (kind == cudaMemcpyHostToDevice) std::memcpy(&h, p, sizeof(h));
-    else CK(cudaMemcpy(&h, p, sizeof(h), cudaMemcpyDeviceToHost));
+    else {
+        CK(cudaMemcpyAsync(&h, p, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
     p += sizeof(h);
     if (h.magic != kMagic || h.nx != d.L.nx || h.ny != d.L.ny || h.nbodies != d.nbodies || h.nmark != d.nmark ||
         h.nlig != d.nlig || h.prec != ctx->prec || h.steps < 0 || h.ninst != ctx->ninst)
@@ -1312,7 +1351,7 @@ lbib_status load_from(lbib_ctx* ctx, const char* p, cudaMemcpyKind kind)
     size_t nq = (size_t)9 * d.L.qstride;
     size_t nm = std::max(d.nmark, 1), nl = std::max(d.nlig, 1), nb = std::max(d.nbodies, 1);
     auto get = [&](void* dst, size_t n) -> cudaError_t {
-        cudaError_t e = cudaMemcpy(dst, p, n, kind);
+        cudaError_t e = cudaMemcpyAsync(dst, p, n, kind, ctx->stream);
         p += n;
         return e;
     };
@@ -1334,13 +1373,13 @@ lbib_status load_from(lbib_ctx* ctx, const char* p, cudaMemcpyKind kind)
     CK(get(d.margin, nl * ctx->rsz));
     // scheduling state is rebuilt from the restored positions and markers
     const Lattice& L = d.L;
-    for (int i = 0; i < 3; ++i) CK(cudaMemset(d.nearflag[i], 0, L.ntiles * 4));
-    CK(cudaMemset(d.mask[0], 0, (size_t)L.ntiles * d.mw * 4));
-    CK(cudaMemset(d.mask[1], 0, (size_t)L.ntiles * d.mw * 4));
-    CK(cudaMemset(d.count, 0, 12));
-    CK(cudaMemset(d.status, 0, 4));
-    CK(cudaMemset(d.ticket, 0, 4));
-    CK(cudaMemcpy(d.step, &st, 8, cudaMemcpyHostToDevice));
+    for (int i = 0; i < 3; ++i) CK(cudaMemsetAsync(d.nearflag[i], 0, L.ntiles * 4, ctx->stream));
+    CK(cudaMemsetAsync(d.mask[0], 0, (size_t)L.ntiles * d.mw * 4, ctx->stream));
+    CK(cudaMemsetAsync(d.mask[1], 0, (size_t)L.ntiles * d.mw * 4, ctx->stream));
+    CK(cudaMemsetAsync(d.count, 0, 12, ctx->stream));
+    CK(cudaMemsetAsync(d.status, 0, 4, ctx->stream));
+    CK(cudaMemsetAsync(d.ticket, 0, 4, ctx->stream));
+    CK(cudaMemcpyAsync(d.step, &st, 8, cudaMemcpyHostToDevice, ctx->stream));
     ctx->s_f = ctx->s_l = st;
     ctx->obs_consumed.assign(ctx->ninst, st);
     if (d.nbodies) {
@@ -1420,10 +1459,28 @@ lbib_status lbib_load_state(lbib_ctx* ctx, const void* buf, size_t bytes)
     if (!ctx || !buf) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
     DeviceGuard guard(ctx->device);
     lbib_status s = pre_read(ctx);
-    if (s != LBIB_OK && s != LBIB_ERR_DIVERGED && s != LBIB_ERR_STATE) return s;
+    if (s != LBIB_OK && s != LBIB_ERR_DIVERGED && s != LBIB_ERR_STATE && s != LBIB_ERR_TIMEOUT) return s;
     if (bytes < state_bytes(ctx)) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than lbib_state_size");
-    return load_from(ctx, static_cast<const char*>(buf), cudaMemcpyHostToDevice);
+    s = load_from(ctx, static_cast<const char*>(buf), cudaMemcpyHostToDevice);
+    if (s == LBIB_OK) ctx->fault = LBIB_OK;  // a trusted state again
+    return s;
 }
+
+lbib_status lbib_inject_fault(lbib_ctx* ctx, int32_t kind)
+{
+    if (!ctx) return fail(ctx, LBIB_ERR_INVALID_ARG, "null context");
+    if (kind != LBIB_FAULT_WAIT_TIMEOUT) return fail(ctx, LBIB_ERR_INVALID_ARG, "unknown fault kind");
+    DeviceGuard guard(ctx->device);
+    lbib_status s = finalize(ctx);
+    if (s != LBIB_OK) return s;
+    // the status bit a bulk-update block sets when its bounded wait for a
+    // tensor copy gives up, raised in stream order after the work enqueued so far
+    k_raise_status<<<1, 1, 0, ctx->stream>>>(ctx->d.status, ST_TMA_TIMEOUT);
+    CK(cudaGetLastError());
+    return LBIB_OK;
+}
+
+void lbib_inject_alloc_failure(int64_t after) { g_alloc_countdown.store(after < 0 ? -1 : (long long)after); }
 
 lbib_status lbib_get_launch_config(lbib_ctx* ctx, lbib_launch_config* out)
 {
@@ -1462,8 +1519,8 @@ lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_co
     const size_t rb = (size_t)ctx->ninst * d.ring_cap * sizeof(lbib_obs);
     char* snap = nullptr;
     lbib_obs* ring = nullptr;
-    CK(cudaMalloc(&snap, sb));
-    cudaError_t e = cudaMalloc(&ring, std::max<size_t>(rb, 1));
+    CK(device_malloc(reinterpret_cast<void**>(&snap), sb));
+    cudaError_t e = device_malloc(reinterpret_cast<void**>(&ring), std::max<size_t>(rb, 1));
     if (e != cudaSuccess) {
         cudaFree(snap);
         return cuda_fail(ctx, e, "cudaMalloc");
@@ -1481,7 +1538,7 @@ lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_co
     };
     s = save_into(ctx, snap, cudaMemcpyDeviceToDevice);
     if (s == LBIB_OK && rb) {
-        e = cudaMemcpy(ring, d.ring, rb, cudaMemcpyDeviceToDevice);
+        e = cudaMemcpyAsync(ring, d.ring, rb, cudaMemcpyDeviceToDevice, ctx->stream);
         if (e != cudaSuccess) s = cuda_fail(ctx, e, "ring snapshot");
     }
     if (s == LBIB_OK && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess))
@@ -1591,7 +1648,8 @@ lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_co
         s = load_from(ctx, snap, cudaMemcpyDeviceToDevice);
     }
     if (s == LBIB_OK && rb) {
-        e = cudaMemcpy(d.ring, ring, rb, cudaMemcpyDeviceToDevice);
+        e = cudaMemcpyAsync(d.ring, ring, rb, cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) s = cuda_fail(ctx, e, "ring restore");
     }
     ctx->obs_consumed = cursors;

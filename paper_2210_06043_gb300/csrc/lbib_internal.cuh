@@ -227,6 +227,9 @@ cudaError_t launch_rebuild_mask(const Dev& d, int prec, int64_t m, cudaStream_t 
 size_t lagrangian_smem_bytes(int prec, int nv_max);
 // message returned by lbib_last_error(NULL) (calls that have no context)
 void set_global_error(const char* msg);
+// cudaMalloc through the allocation-failure countdown of
+// lbib_inject_alloc_failure (every device allocation of the library goes here)
+cudaError_t device_malloc(void** p, size_t bytes);
 cudaError_t configure_kernels(int prec, int nv_max);
 
 }  // namespace lbib

@@ -826,6 +826,8 @@ lbib_status mlp_fail(lbib_status s, const std::string& m)
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
+__global__ void k_or_word(uint32_t* w, uint32_t bits) { atomicOr(w, bits); }
+
 }  // namespace
 
 struct lbib_mlp {
@@ -855,6 +857,10 @@ struct lbib_mlp {
     int* pidx = nullptr;                    // padded position of each public parameter
     int64_t t = 0;                          // Adam steps
     uint32_t* status = nullptr;             // bounded-wait error word of the tensor-core kernels
+    // set when a sync found that a bounded wait gave up: the products of that
+    // call were not completed, so the network refuses work until its
+    // parameters are set again
+    lbib_status fault = LBIB_OK;
     bool tc = true;                         // forward products on tcgen05
     // fused inference (k_mlp_fused): packed weight chunks, refreshed after every update
     unsigned char* pw = nullptr;
@@ -867,11 +873,25 @@ struct lbib_mlp {
 
 namespace {
 
+// status word of the finished work: a bounded wait that gave up makes the
+// network refuse work (sticky) until lbib_mlp_set_params
+lbib_status mlp_check_status(lbib_mlp* net)
+{
+    uint32_t st = 0;
+    const cudaError_t e = cudaMemcpy(&st, net->status, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return mlp_fail(LBIB_ERR_CUDA, std::string("status read: ") + cudaGetErrorString(e));
+    if (st & 1u) {
+        net->fault = LBIB_ERR_TIMEOUT;
+        return mlp_fail(LBIB_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait (its products are incomplete)");
+    }
+    return LBIB_OK;
+}
+
 template <typename T>
 cudaError_t mlp_alloc(lbib_mlp* net, T** p, size_t n)
 {
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+    cudaError_t e = device_malloc(&q, std::max<size_t>(n, 1) * sizeof(T));
     if (e == cudaSuccess) {
         net->allocs.push_back(q);
         *p = static_cast<T*>(q);
@@ -1207,13 +1227,14 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
                 for (int i = 0; i < net->in_true[l]; ++i) idx.push_back((int)(net->woff[l] + (size_t)o * net->in[l] + i));
             for (int o = 0; o < net->out_true[l]; ++o) idx.push_back((int)(net->boff[l] + o));
         }
-        if ((e = cudaMemcpy(net->pidx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+        if ((e = cudaMemcpyAsync(net->pidx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                 net->stream)) != cudaSuccess)
             return bail(e, "cudaMemcpy");
     }
-    if ((e = cudaMemcpy(net->cin, cin.data(), 32 * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(net->sin, sin.data(), 32 * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(net->cout, cout.data(), 64 * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(net->sout, sout.data(), 64 * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(net->cin, cin.data(), 32 * 4, cudaMemcpyHostToDevice, net->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(net->sin, sin.data(), 32 * 4, cudaMemcpyHostToDevice, net->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(net->cout, cout.data(), 64 * 4, cudaMemcpyHostToDevice, net->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(net->sout, sout.data(), 64 * 4, cudaMemcpyHostToDevice, net->stream)) != cudaSuccess)
         return bail(e, "cudaMemcpy");
     // Glorot-uniform weights from a host generator (splitmix64), zero biases and padding
     std::vector<float> h(net->nparam, 0.f);
@@ -1232,11 +1253,11 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
             for (int i = 0; i < net->in_true[l]; ++i)
                 h[net->woff[l] + (size_t)o * net->in[l] + i] = (float)((2.0 * next() - 1.0) * lim);
     }
-    if ((e = cudaMemcpy(net->p, h.data(), net->nparam * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemset(net->m, 0, net->nparam * 4)) != cudaSuccess ||
-        (e = cudaMemset(net->v, 0, net->nparam * 4)) != cudaSuccess ||
-        (e = cudaMemset(net->g, 0, net->nparam * 4)) != cudaSuccess ||
-        (e = cudaMemset(net->status, 0, 4)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(net->p, h.data(), net->nparam * 4, cudaMemcpyHostToDevice, net->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(net->m, 0, net->nparam * 4, net->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(net->v, 0, net->nparam * 4, net->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(net->g, 0, net->nparam * 4, net->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(net->status, 0, 4, net->stream)) != cudaSuccess)
         return bail(e, "initialisation");
     k_to_bf16<<<(unsigned)((net->nparam + 255) / 256), 256, 0, net->stream>>>(net->p, net->pb, net->nparam);
     if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaStreamSynchronize(net->stream)) != cudaSuccess)
@@ -1248,6 +1269,7 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
 lbib_status lbib_mlp_forward(lbib_mlp* net, const float* x, int32_t batch, float* y)
 {
     if (!net || !x || !y) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
+    if (net->fault != LBIB_OK) return mlp_fail(net->fault, "a bounded device wait gave up earlier: set the parameters again");
     if (batch < 1 || batch > net->max_batch) return mlp_fail(LBIB_ERR_INVALID_ARG, "batch outside 1 .. max_batch");
     Guard guard(net->device);
     if (net->tc && net->fused) {
@@ -1274,6 +1296,7 @@ lbib_status lbib_mlp_forward(lbib_mlp* net, const float* x, int32_t batch, float
 lbib_status lbib_mlp_train_step(lbib_mlp* net, const float* x, const float* t, int32_t batch, float lr, float* loss)
 {
     if (!net || !x || !t) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
+    if (net->fault != LBIB_OK) return mlp_fail(net->fault, "a bounded device wait gave up earlier: set the parameters again");
     if (batch < 1 || batch > net->max_batch) return mlp_fail(LBIB_ERR_INVALID_ARG, "batch outside 1 .. max_batch");
     if (!(lr > 0.f) || !std::isfinite(lr)) return mlp_fail(LBIB_ERR_INVALID_ARG, "lr must be positive");
     Guard guard(net->device);
@@ -1297,6 +1320,7 @@ lbib_status lbib_mlp_backward(lbib_mlp* net, const float* x, const float* t, int
                               float* loss)
 {
     if (!net || !x || !t || !grad) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
+    if (net->fault != LBIB_OK) return mlp_fail(net->fault, "a bounded device wait gave up earlier: set the parameters again");
     if (n < net->ntrue) return mlp_fail(LBIB_ERR_INVALID_ARG, "buffer smaller than the parameter count");
     if (batch < 1 || batch > net->max_batch) return mlp_fail(LBIB_ERR_INVALID_ARG, "batch outside 1 .. max_batch");
     Guard guard(net->device);
@@ -1314,6 +1338,7 @@ lbib_status lbib_mlp_backward(lbib_mlp* net, const float* x, const float* t, int
 lbib_status lbib_mlp_apply_gradient(lbib_mlp* net, const float* grad, size_t n, float scale, float lr)
 {
     if (!net || !grad) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
+    if (net->fault != LBIB_OK) return mlp_fail(net->fault, "a bounded device wait gave up earlier: set the parameters again");
     if (n < net->ntrue) return mlp_fail(LBIB_ERR_INVALID_ARG, "buffer smaller than the parameter count");
     if (!std::isfinite(scale)) return mlp_fail(LBIB_ERR_INVALID_ARG, "scale must be finite");
     if (!(lr > 0.f) || !std::isfinite(lr)) return mlp_fail(LBIB_ERR_INVALID_ARG, "lr must be positive");
@@ -1360,6 +1385,7 @@ lbib_status lbib_mlp_gradients(lbib_mlp* net, const float* x, const float* t, in
                                float* loss)
 {
     if (!net || !x || !t || !grad) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
+    if (net->fault != LBIB_OK) return mlp_fail(net->fault, "a bounded device wait gave up earlier: set the parameters again");
     if (n < net->ntrue) return mlp_fail(LBIB_ERR_INVALID_ARG, "buffer smaller than the parameter count");
     if (batch < 1 || batch > net->max_batch) return mlp_fail(LBIB_ERR_INVALID_ARG, "batch outside 1 .. max_batch");
     Guard guard(net->device);
@@ -1371,6 +1397,8 @@ lbib_status lbib_mlp_gradients(lbib_mlp* net, const float* x, const float* t, in
     if (e == cudaSuccess) e = cudaMemcpy(h.data(), net->g, net->nparam * 4, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(&lh, net->loss_dev, 4, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_gradients: ") + cudaGetErrorString(e));
+    const lbib_status st = mlp_check_status(net);
+    if (st != LBIB_OK) return st;
     padded_to_host(net, h, grad);
     if (loss) *loss = lh;
     return LBIB_OK;
@@ -1385,6 +1413,8 @@ lbib_status lbib_mlp_get_params(lbib_mlp* net, float* params, size_t n)
     cudaError_t e = cudaStreamSynchronize(net->stream);
     if (e == cudaSuccess) e = cudaMemcpy(h.data(), net->p, net->nparam * 4, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_get_params: ") + cudaGetErrorString(e));
+    const lbib_status st = mlp_check_status(net);
+    if (st != LBIB_OK) return st;
     padded_to_host(net, h, params);
     return LBIB_OK;
 }
@@ -1404,17 +1434,40 @@ lbib_status lbib_mlp_set_params(lbib_mlp* net, const float* params, size_t n)
         for (int o = 0; o < net->out_true[l]; ++o) h[net->boff[l] + o] = params[k++];
     }
     cudaError_t e = cudaStreamSynchronize(net->stream);
-    if (e == cudaSuccess) e = cudaMemcpy(net->p, h.data(), net->nparam * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(net->m, 0, net->nparam * 4);
-    if (e == cudaSuccess) e = cudaMemset(net->v, 0, net->nparam * 4);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(net->p, h.data(), net->nparam * 4, cudaMemcpyHostToDevice, net->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(net->m, 0, net->nparam * 4, net->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(net->v, 0, net->nparam * 4, net->stream);
     if (e == cudaSuccess) {
         k_to_bf16<<<(unsigned)((net->nparam + 255) / 256), 256, 0, net->stream>>>(net->p, net->pb, net->nparam);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess) e = cudaMemsetAsync(net->status, 0, 4, net->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
     if (e != cudaSuccess) return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_set_params: ") + cudaGetErrorString(e));
     net->t = 0;
     net->pw_dirty = true;
+    net->fault = LBIB_OK;
+    return LBIB_OK;
+}
+
+lbib_status lbib_mlp_sync(lbib_mlp* net)
+{
+    if (!net) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
+    Guard guard(net->device);
+    cudaError_t e = cudaStreamSynchronize(net->stream);
+    if (e != cudaSuccess) return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_sync: ") + cudaGetErrorString(e));
+    return mlp_check_status(net);
+}
+
+lbib_status lbib_mlp_inject_fault(lbib_mlp* net, int32_t kind)
+{
+    if (!net) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
+    if (kind != LBIB_FAULT_WAIT_TIMEOUT) return mlp_fail(LBIB_ERR_INVALID_ARG, "unknown fault kind");
+    Guard guard(net->device);
+    // the bit the tensor-core kernels set when a bounded wait gives up, in stream order
+    k_or_word<<<1, 1, 0, net->stream>>>(net->status, 1u);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_inject_fault: ") + cudaGetErrorString(e));
     return LBIB_OK;
 }
 

@@ -24,6 +24,7 @@ LBIB_STORE_FP64, LBIB_STORE_FP32, LBIB_STORE_BF16, LBIB_STORE_FP16 = 0, 1, 2, 3
 STORAGE_CODES = {"fp64": LBIB_STORE_FP64, "fp32": LBIB_STORE_FP32, "bf16": LBIB_STORE_BF16, "fp16": LBIB_STORE_FP16}
 LBIB_CELL, LBIB_PARTICLE = 0, 1
 LBIB_DEFORMABLE, LBIB_RIGID, LBIB_FIXED = 0, 1, 2
+LBIB_FAULT_WAIT_TIMEOUT = 1
 FIELDS = ("x", "y", "xp", "yp", "uvx", "uvy", "fsx", "fsy", "fbx", "fby", "fax", "fay",
           "fpx", "fpy", "fwx", "fwy", "fhx", "fhy", "ftx", "fty", "vx", "vy",
           "mx", "my", "mfx", "mfy", "mds")
@@ -120,6 +121,9 @@ _SIGS = {
     "lbib_mlp_param_count": [_P, ctypes.POINTER(ctypes.c_size_t)],
     "lbib_mlp_get_params": [_P, _P, ctypes.c_size_t],
     "lbib_mlp_set_params": [_P, _P, ctypes.c_size_t],
+    "lbib_mlp_sync": [_P],
+    "lbib_mlp_inject_fault": [_P, ctypes.c_int32],
+    "lbib_inject_fault": [_P, ctypes.c_int32],
 }
 
 _lib = None
@@ -147,6 +151,8 @@ def load() -> ctypes.CDLL:
             lib.lbib_destroy.restype = None
             lib.lbib_mlp_destroy.argtypes = [_P]
             lib.lbib_mlp_destroy.restype = None
+            lib.lbib_inject_alloc_failure.argtypes = [ctypes.c_int64]
+            lib.lbib_inject_alloc_failure.restype = None
             _lib = lib
         return _lib
 
@@ -291,6 +297,10 @@ class Solver:
 
     def sync(self):
         lbib_sync(self.ctx)
+
+    def inject_fault(self, kind=LBIB_FAULT_WAIT_TIMEOUT):
+        """Failure-detection tests: raise a bounded-wait timeout in stream order."""
+        self._c(self.lib.lbib_inject_fault(self.ctx, int(kind)))
 
     def step_count(self) -> int:
         s = ctypes.c_int64()
@@ -468,6 +478,13 @@ class Mlp:
     def _c(self, st):
         _check(st, None)
 
+    def sync(self):
+        self._c(self.lib.lbib_mlp_sync(self.net))
+
+    def inject_fault(self, kind=LBIB_FAULT_WAIT_TIMEOUT):
+        """Failure-detection tests: raise a bounded-wait timeout in stream order."""
+        self._c(self.lib.lbib_mlp_inject_fault(self.net, int(kind)))
+
     def forward(self, x_ptr: int, batch: int, y_ptr: int):
         self._c(self.lib.lbib_mlp_forward(self.net, ctypes.c_void_p(x_ptr), int(batch), ctypes.c_void_p(y_ptr)))
 
@@ -550,6 +567,12 @@ def from_capillaries(caps, storage=None, device=0, stream=None, obs_capacity=0) 
     return s
 
 
+def inject_alloc_failure(after: int) -> None:
+    """Failure-detection tests: the (after + 1)-th device allocation the
+    library makes from now on fails as out of memory (once); after < 0 cancels."""
+    load().lbib_inject_alloc_failure(int(after))
+
+
 def roofline_bytes_per_node(storage: int) -> int:
     """Algorithmic DRAM bytes of one lattice-node update: 9 populations read and
     written once each."""
@@ -557,4 +580,5 @@ def roofline_bytes_per_node(storage: int) -> int:
 
 
 __all__ = [n for n in dir() if n.startswith("lbib_") or n.startswith("LBIB_")] + [
-    "Solver", "Mlp", "from_capillary", "from_capillaries", "load", "library_path", "LbibError", "roofline_bytes_per_node", "FIELDS"]
+    "Solver", "Mlp", "from_capillary", "from_capillaries", "load", "library_path", "LbibError", "roofline_bytes_per_node", "FIELDS",
+    "inject_alloc_failure"]

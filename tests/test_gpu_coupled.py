@@ -259,3 +259,33 @@ def test_largest_membrane():
         u.advance(1)
     assert e.value.status == lbib.LBIB_ERR_UNSUPPORTED
     u.close()
+
+
+def test_contexts_created_while_others_run_match_lone_runs():
+    """Every set-up copy and fill of a context is ordered on its own stream:
+    a context created and stepped while another context's steps are still in
+    flight computes exactly the lone trajectory.  (With the fills on the
+    legacy default stream, which is not ordered with the context's
+    non-blocking stream, a busy device let the zero fill of the populations
+    land after their initialisation.)"""
+    cap = wl.small_capillary()
+    lone = lbib.from_capillary(cap)
+    lone.advance(15)
+    x_lone, u_lone = lone.markers(0), lone.velocity()[0]
+    lone.close()
+    busy = lbib.from_capillary(cap)
+    busy.advance(40)  # in flight while the next context is set up
+    s = lbib.from_capillary(cap)
+    s.advance(15)
+    assert np.array_equal(s.markers(0), x_lone)
+    assert np.array_equal(s.velocity()[0], u_lone)
+    # a checkpoint written into a context while another one runs
+    busy.advance(40)
+    blob = s.save_state()
+    t = lbib.from_capillary(cap)
+    t.load_state(blob)
+    t.advance(5)
+    s.advance(5)
+    assert np.array_equal(t.markers(0), s.markers(0))
+    for c in (busy, s, t):
+        c.close()
