@@ -185,19 +185,39 @@ def _oracle_sample(caps, nodes_budget):
     return sample, max(1, int(round(nodes_budget / nodes)))
 
 
-def cpu_baseline(caps, nodes_budget):
-    """The oracle as it stands (single-threaded plain C, FP64) on a bounded
-    sample of the workload."""
-    sample, steps = _oracle_sample(caps, nodes_budget)
+def _time_oracle(sample, steps, threads):
+    import oracle
+    used = oracle.set_threads(threads)
     sims = [_oracle_sim(c) for c in sample]
     t0 = time.perf_counter()
     for s in sims:
         s.step(steps)
-    dt = time.perf_counter() - t0
+    return time.perf_counter() - t0, used
+
+
+def cpu_baseline(caps, nodes_budget):
+    """The oracle as it stands (plain C, FP64; its node loops on OpenMP
+    threads) on a bounded sample of the workload, on one thread and on every
+    host core; and the small capillary (240 x 60) for its full 2000 steps."""
+    from paper_2210_06043_gb300 import workloads as wl
+    host = os.cpu_count() or 1
+    sample, steps = _oracle_sample(caps, nodes_budget)
     nodes = sum(c.nodes for c in sample)
-    return {"value": nodes * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+    dt1, _ = _time_oracle(sample, steps, 1)
+    dtn, used = _time_oracle(sample, steps, host)
+    small = wl.small_capillary()
+    dts, _ = _time_oracle([small], small.steps, host)
+    return {"value": nodes * steps / dtn / 1e6, "unit": UNIT, "cores": used, "kind": "oracle",
+            "host_cores": host,
             "sample": f"{steps} steps from t = 0 of {len(sample)} of the {len(caps)} capillaries "
-                      f"({nodes} nodes), FP64 plain C, one thread", "seconds": dt}
+                      f"({nodes} nodes), FP64 plain C, node loops on {used} OpenMP threads",
+            "seconds": dtn,
+            "one_thread": {"value": nodes * steps / dt1 / 1e6, "seconds": dt1},
+            "small_capillary_full_run": {
+                "what": f"240 x 60 capillary, biconcave cell + rigid adhering ellipse, {small.steps} steps, "
+                        f"{used} threads",
+                "mlups": small.nodes * small.steps / dts / 1e6, "seconds": dts,
+                "marker_updates_per_s": small.markers * small.steps / dts}}
 
 
 def run_reference(args):
@@ -206,6 +226,8 @@ def run_reference(args):
         return 0
     caps, cfg = _workload(args.workload, args.instances)
     sample = caps[::32]  # every 32nd capillary of a sweep (the production capillary alone)
+    import oracle
+    threads = oracle.set_threads(os.cpu_count() or 1)  # the node loops on every host core
     sims = [_oracle_sim(c) for c in sample]
     nodes = sum(c.nodes for c in sample)
     for s in sims:
@@ -216,12 +238,13 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     v = nodes * args.steps / dt / 1e6
     what = (f"{args.steps} timed steps after {args.warmup} warm-up steps of {len(sample)} of the {len(caps)} "
-            f"capillaries ({nodes} nodes), FP64 plain C oracle, one thread")
+            f"capillaries ({nodes} nodes), FP64 plain C oracle, node loops on {threads} OpenMP threads")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": what},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": what,
+                             "host_cores": os.cpu_count()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     if len(caps) > 1:
         line["sims_per_hour"] = 3600.0 / (STEPS_PER_SIM * dt / args.steps * sum(c.nodes for c in caps) / nodes) \

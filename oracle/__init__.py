@@ -50,7 +50,7 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-std=gnu11", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+           "-fno-fast-math", "-fopenmp", _SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -103,6 +103,7 @@ def _load():
             "orc_body_traction": (None, [P, I, P, P]),
             "orc_step": (None, [P]),
             "orc_run": (None, [P, I64]),
+            "orc_set_threads": (I, [I]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -118,6 +119,12 @@ def _p(a: np.ndarray):
 
 def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the node loops (the results do not depend on it);
+    returns the count in use."""
+    return _load().orc_set_threads(int(n))
 
 
 # ------------------------------------------------------------ pieces (pins)

@@ -66,12 +66,20 @@
  *   - Vertex mass m_v = rho_body A_0 / nv; rigid mass rho_body A_0 and polar
  *     moment rho_body J_c of the polygon.
  *
+ * Host threads: the node loops of streaming and collision may run on several
+ * threads (OpenMP over rows and nodes, orc_set_threads); every node's
+ * arithmetic and every sum keep one order, so the results are the same bits
+ * for any thread count.  Everything else runs on one thread.
+ *
  * Parity status: every numbered piece above is pinned by the CPU tests
  * (closed forms, moment identities, brute force).  The coupled trajectory as a
  * whole has no printed numbers to pin it ("parity unpinned" for the full
  * trajectory beyond its pieces and invariants).
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -87,6 +95,18 @@ enum { ORC_CELL = 0, ORC_PARTICLE = 1 };
 enum { ORC_DEFORMABLE = 0, ORC_RIGID = 1, ORC_FIXED = 2 };
 
 /* ---------------------------------------------------------------- lattice */
+
+/* Host threads for the node loops (1: serial); returns the count in use. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* Eq. 3 evaluated literally: rest, four axis and four diagonal speeds. */
 static int EX[ORC_Q], EY[ORC_Q], OPP[ORC_Q];
@@ -187,6 +207,7 @@ void orc_stream_bc(int nx, int ny, int bc, double umax, double rho_out, const do
 {
     lattice_init();
     size_t n = (size_t)nx * ny;
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x)
             for (int q = 0; q < ORC_Q; ++q) {
@@ -205,6 +226,7 @@ void orc_stream_bc(int nx, int ny, int bc, double umax, double rho_out, const do
                 f[q * n + (size_t)y * nx + x] = v;
             }
     if (bc != ORC_BC_INLET_OUTLET) return;
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y) {
         double g[ORC_Q];
         for (int q = 0; q < ORC_Q; ++q) g[q] = f[q * n + (size_t)y * nx + 0];
@@ -1020,6 +1042,8 @@ void orc_step(orc_sim* s)
     /* 1. streaming + boundary conditions */
     orc_stream_bc(nx, ny, s->bc, s->umax, s->rho_out, s->f, s->fs);
     /* 2.-3. moments (Eqs. 5-6) and collision (Eqs. 1, 2, 4) */
+    int diverged = 0;
+#pragma omp parallel for schedule(static) reduction(| : diverged)
     for (size_t k = 0; k < n; ++k) {
         double fk[ORC_Q], feq[ORC_Q], gq[ORC_Q];
         double rho = 0.0, jx = 0.0, jy = 0.0;
@@ -1034,11 +1058,12 @@ void orc_step(orc_sim* s)
         s->rho[k] = rho;
         s->ux[k] = ux;
         s->uy[k] = uy;
-        if (!(rho > 0.0) || !isfinite(ux) || !isfinite(uy)) s->diverged = 1;
+        if (!(rho > 0.0) || !isfinite(ux) || !isfinite(uy)) diverged = 1;
         orc_equilibrium(rho, ux, uy, feq);
         orc_guo_term(ux, uy, Fx, Fy, s->tau, gq);
         for (int q = 0; q < ORC_Q; ++q) s->f[q * n + k] = fk[q] - (fk[q] - feq[q]) / s->tau + gq[q];
     }
+    if (diverged) s->diverged = 1;
     /* 4. Lagrangian update from (rho^n, u^n) at X^n */
     int nb = s->nb;
     double *len[ORC_MAX_BODIES], *nlx[ORC_MAX_BODIES], *nly[ORC_MAX_BODIES], *nvx[ORC_MAX_BODIES],

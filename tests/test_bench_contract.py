@@ -47,3 +47,17 @@ def test_traffic_hash_ignores_comments():
     code = "int a; // one\n/* two\n   lines */ int b;\n\n   \nint c;  \n"
     assert bench._code_only(code) == "int a;\n int b;\nint c;"
     assert bench._code_only("x = 1;  // note") == bench._code_only("// header\nx = 1;")
+
+
+def test_cpu_baseline_times_one_thread_and_every_host_core():
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2210_06043_gb300 import workloads as wl
+
+    caps = wl.sweep_capillaries()[:8]
+    cb = bench.cpu_baseline(caps, 2e6)
+    host = os.cpu_count()
+    assert cb["kind"] == "oracle" and cb["host_cores"] == host and cb["cores"] == host
+    assert cb["value"] > 0 and cb["one_thread"]["value"] > 0
+    full = cb["small_capillary_full_run"]
+    assert "2000 steps" in full["what"] and full["mlups"] > 0 and full["marker_updates_per_s"] > 0

@@ -104,3 +104,23 @@ def test_sweep_workload_covers_the_parameter_matrix():
     assert seen == {(ar, ca, cell, s) for ar in wl.SWEEP_AR for ca in wl.SWEEP_CA for cell in wl.SWEEP_CELLS
                     for s in wl.SWEEP_SEEDS}
     assert wl.sweep_capillaries()[5].nx == caps[5].nx  # seeded
+
+
+def test_threaded_node_loops_give_the_same_bits():
+    """The oracle's streaming and collision loops may run on several host
+    threads; every node's arithmetic and every sum keep one order, so the
+    small capillary after 40 steps is the same bits on 1 and 4 threads."""
+    cap = wl.small_capillary()
+    n0 = oracle.set_threads(0)
+    out = []
+    try:
+        for n in (1, 4):
+            assert oracle.set_threads(n) == n
+            s = build(cap)
+            s.step(40)
+            out.append((s.fpost(), s.body_xy(0), s.body_xy(1), s.macro()[1], s.obs()))
+    finally:
+        oracle.set_threads(n0)
+    (f1, a1, b1, u1, o1), (f4, a4, b4, u4, o4) = out
+    assert np.array_equal(f1, f4) and np.array_equal(a1, a4) and np.array_equal(b1, b4)
+    assert np.array_equal(u1, u4) and o1 == o4
