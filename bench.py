@@ -333,6 +333,51 @@ def surrogate_inference(local, stream, iters=50, batch=65536):
                     f"({sg.STEPS} solver steps); held-out accuracy of the trained network in the design notes"}
 
 
+def storage_16bit(caps, local, stream, steps, warmup, hbm):
+    """The same sweep with populations stored in 16 bits (FP16 deviations
+    scaled by 2^14, and BF16 deviations; FP32 arithmetic): autotuned, `steps`
+    steps timed with CUDA events on the launching stream, the bulk lattice
+    kernel's in-graph time from a profiled pass, both against the 16-bit
+    roofline (36 algorithmic bytes per node update)."""
+    import dataclasses
+
+    import torch
+
+    from paper_2210_06043_gb300 import lbib
+    out = {}
+    for st in ("fp16", "bf16"):
+        cs = [dataclasses.replace(c, storage=st) for c in caps]
+        s = lbib.from_capillaries(cs, device=local, stream=stream.cuda_stream)
+        cfg = s.autotune(steps_per_trial=50)
+        s.advance(max(warmup, 3))
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.advance(steps)
+        b.record(stream)
+        b.synchronize()
+        dt = a.elapsed_time(b) / 1e3
+        s.set_profiling(True)
+        kern = []
+        for _ in range(20):
+            s.advance(1)
+            kern.append(s.kernel_times())
+        s.set_profiling(False)
+        desc = s.describe()
+        s.close()
+        nodes = sum(c.nodes for c in cs)
+        bpn = lbib.roofline_bytes_per_node(lbib.STORAGE_CODES[st])
+        bulk_ms = statistics.mean(k[0] for k in kern)
+        bulk_nodes = nodes - desc["near_tiles"] * 32 * 4
+        out[st] = {"value": nodes * steps / dt / 1e6, "unit": UNIT, "ms_per_step": dt * 1e3 / steps,
+                   "bytes_per_node": bpn, "step_roofline_frac": nodes * bpn / (dt / steps) / 1e9 / hbm,
+                   "bulk_ms": bulk_ms, "bulk_roofline_frac": bulk_nodes * bpn / (bulk_ms * 1e-3) / 1e9 / hbm,
+                   "launch_config": cfg}
+    out["accuracy"] = ("against the FP64 oracle on the 240 x 60 capillary after 2000 steps "
+                       "(tests/test_gpu_reduced_precision.py): see the bounds stated there")
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -491,6 +536,8 @@ def run_gpu(args):
             "plain_solver": f"each capillary alone in its own context (same kernels, autotuned), "
                             f"{args.plain_steps} steps after 3 warm-up steps, warm L2, CUDA events",
             "accuracy": "every instance bit-identical to its lone run (tests/test_gpu_batch.py)"}
+    if batch and not args.storage and not args.no_16bit:
+        line["storage_16bit"] = storage_16bit(caps, local, stream, K, args.warmup, hbm)
     if batch and not args.no_surrogate:
         line["surrogate"] = surrogate_inference(local, stream)
     if ws == 1 and not args.no_cpu_baseline:
@@ -525,6 +572,7 @@ def main():
                     "[,observables_branch[,chain_programmatic[,near_update_blocks[,bulk_tma]]]]] "
                     "instead of the autotuner")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-16bit", action="store_true", help="skip the 16-bit storage timing of the sweep")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate inference timing")
     args = ap.parse_args()
     if args.impl == "reference":

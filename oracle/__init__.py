@@ -29,6 +29,7 @@ BC_INLET_OUTLET, BC_PERIODIC_FORCE = 0, 1
 CELL, PARTICLE = 0, 1
 DEFORMABLE, RIGID, FIXED = 0, 1, 2
 TRANSFER_PESKIN, TRANSFER_MLS = 0, 1
+STORE_EXACT, STORE_F32, STORE_BF16, STORE_F16 = 0, 1, 2, 3
 
 # order of the per-vertex arrays exposed by orc_get_body
 BODY_FIELDS = (
@@ -104,6 +105,8 @@ def _load():
             "orc_step": (None, [P]),
             "orc_run": (None, [P, I64]),
             "orc_set_threads": (I, [I]),
+            "orc_round_store": (D, [I, D]),
+            "orc_set_storage_rounding": (I, [P, I]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -203,6 +206,11 @@ def bond_uniform(seed, step, site):
     return _load().orc_bond_uniform(int(seed), int(step), int(site))
 
 
+def round_store(kind, g):
+    """A deviation as stored in precision `kind` (STORE_*)."""
+    return _load().orc_round_store(int(kind), float(g))
+
+
 def polygon(xy):
     """{A, P, cx, cy, Jc} of a closed chain given as an (nv, 2) array."""
     xy = _f64(xy)
@@ -272,6 +280,12 @@ class OracleSim:
 
     def set_repulsion_cutoff(self, d):
         self._lib.orc_set_repulsion_cutoff(self._h, float(d))
+
+    def set_storage_rounding(self, kind):
+        """Round the stored deviations to precision `kind` (STORE_*) after every
+        collision, and the current state at once."""
+        if self._lib.orc_set_storage_rounding(self._h, int(kind)) != 0:
+            raise ValueError("unknown storage kind")
 
     def set_transfer(self, kind):
         if self._lib.orc_set_transfer(self._h, int(kind)) != 0:

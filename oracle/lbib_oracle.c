@@ -623,6 +623,41 @@ double orc_rigid_bdf2(double u1, double u2, double acc)
     return (2.0 / 3.0) * (2.0 * u1 - 0.5 * u2 + acc);
 }
 
+/* ------------------------------------------------- storage of deviations */
+
+/* The precisions a library may store the post-collision deviations
+ * g = f* - w_i in: exact (FP64), binary32, bfloat16 (8 significant bits) and
+ * binary16 after scaling by 2^14 (11 significant bits).  The 16-bit kinds
+ * round the binary32 value of g, as a store from FP32 arithmetic would; every
+ * rounding is to nearest, ties to even (nearbyint in the default mode). */
+enum { ORC_STORE_EXACT = 0, ORC_STORE_F32 = 1, ORC_STORE_BF16 = 2, ORC_STORE_F16 = 3 };
+
+/* v rounded to `bits` significant bits; subnormal results below 2^emin keep
+ * the absolute quantum 2^(emin - bits + 1) */
+static double round_bits(double v, int bits, int emin)
+{
+    if (v == 0.0 || !isfinite(v)) return v;
+    int e;
+    frexp(v, &e); /* |v| = m 2^e, 1/2 <= m < 1: the leading bit has weight 2^(e-1) */
+    int lead = e - 1;
+    if (lead < emin) lead = emin;
+    const int sh = bits - 1 - lead; /* scale that puts the last kept bit at weight 1 */
+    return ldexp(nearbyint(ldexp(v, sh)), -sh);
+}
+
+double orc_round_store(int kind, double g)
+{
+    switch (kind) {
+    case ORC_STORE_F32: return (double)(float)g;
+    case ORC_STORE_BF16: return round_bits((double)(float)g, 8, -126);
+    case ORC_STORE_F16: {
+        const double v = round_bits((double)(float)g * 16384.0, 11, -14);
+        return fabs(v) > 65504.0 ? copysign(INFINITY, v) : v / 16384.0;
+    }
+    default: return g;
+    }
+}
+
 /* ------------------------------------------------------------ simulation */
 
 typedef struct {
@@ -649,6 +684,7 @@ typedef struct {
 
 typedef struct orc_sim {
     int nx, ny, bc, nb, diverged, transfer;
+    int store_round; /* ORC_STORE_*: rounding of the stored deviations after each collision */
     double tau, nu, umax, rho_out, gx, gy, dcut, probe;
     uint64_t seed;
     int64_t step;
@@ -727,6 +763,19 @@ void orc_destroy(orc_sim* s)
 }
 
 void orc_set_repulsion_cutoff(orc_sim* s, double d) { s->dcut = d; }
+
+/* Stores the post-collision deviations in the given precision from now on
+ * (the current state is rounded at once); -1 for an unknown kind. */
+int orc_set_storage_rounding(orc_sim* s, int kind)
+{
+    if (kind < ORC_STORE_EXACT || kind > ORC_STORE_F16) return -1;
+    lattice_init();
+    s->store_round = kind;
+    const size_t n = (size_t)s->nx * s->ny;
+    for (int q = 0; q < ORC_Q; ++q)
+        for (size_t k = 0; k < n; ++k) s->f[q * n + k] = WQ[q] + orc_round_store(kind, s->f[q * n + k] - WQ[q]);
+    return 0;
+}
 
 /* Selects the transfer kernel (ORC_TRANSFER_*) of the interpolation and the
  * spreading; returns -1 for an unknown kind. */
@@ -1062,6 +1111,9 @@ void orc_step(orc_sim* s)
         orc_equilibrium(rho, ux, uy, feq);
         orc_guo_term(ux, uy, Fx, Fy, s->tau, gq);
         for (int q = 0; q < ORC_Q; ++q) s->f[q * n + k] = fk[q] - (fk[q] - feq[q]) / s->tau + gq[q];
+        if (s->store_round)
+            for (int q = 0; q < ORC_Q; ++q)
+                s->f[q * n + k] = WQ[q] + orc_round_store(s->store_round, s->f[q * n + k] - WQ[q]);
     }
     if (diverged) s->diverged = 1;
     /* 4. Lagrangian update from (rho^n, u^n) at X^n */

@@ -8,10 +8,10 @@ for BF16, 2^-11 for FP16) plus FP32 arithmetic; the bound below is one unit in
 the last place plus the FP32 bound of the FP32 lattice test.
 
 The small capillary (240 x 60, biconcave cell + rigid adhering ellipse) run for
-its 2000 steps in each 16-bit storage is compared with the FP64 oracle on every
-quantity the library reports: velocity (relative L2), positions, delta p, r,
-N_L.  The bounds are the measured errors with a margin; they are much looser than FP32's because the storage rounding
-of a slowly varying field repeats step after step."""
+its 2000 steps in each 16-bit storage is compared on every quantity the
+library reports (velocity, positions, delta p, r, N_L) with the FP64 oracle
+and with the oracle storing its deviations in the same 16-bit format; the
+bounds are stated relative to the error the format causes in the oracle."""
 import numpy as np
 import pytest
 
@@ -24,15 +24,6 @@ pytestmark = pytest.mark.gpu
 
 W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
 STORES = {"bf16": (lbib.LBIB_STORE_BF16, 2.0**-8), "fp16": (lbib.LBIB_STORE_FP16, 2.0**-10)}
-
-# errors measured on GB300 for the small capillary after 2000 steps (BF16: u 4.1e-2,
-# x 1.9e-3, delta_p 5.0e-6, r 7.2e-4, N_L 0; FP16: u 3.2e-3, x 3.9e-5, delta_p 1.1e-7,
-# r 2.9e-6, N_L 0) times 3; N_L may differ by one bond of the ~20 engaged (0.05)
-C4_BOUNDS = {
-    "bf16": dict(u=0.12, x=6e-3, delta_p=1.5e-5, r=2.2e-3, n_l=0.05),
-    "fp16": dict(u=1e-2, x=1.2e-4, delta_p=3.5e-7, r=9e-6, n_l=0.05),
-}
-
 
 @pytest.mark.parametrize("store", sorted(STORES))
 @pytest.mark.parametrize("nx,ny", [(37, 9), (100, 23)])
@@ -58,23 +49,45 @@ def test_lattice_step_16bit_matches_oracle(store, nx, ny, bc):
     s.close()
 
 
+ROUNDING = {"bf16": oracle.STORE_BF16, "fp16": oracle.STORE_F16}
+
+
 @pytest.mark.parametrize("store", sorted(STORES))
-def test_small_capillary_16bit_against_fp64_oracle(store):
+def test_small_capillary_16bit_error_is_the_storage_rounding(store):
+    """The 240 x 60 capillary (biconcave cell, rigid adhering ellipse) for its
+    2000 steps in 16-bit storage, against the oracle run twice: exact, and
+    with its stored deviations rounded to the same 16-bit format after every
+    collision (oracle.set_storage_rounding).  The rounded oracle's distance
+    from the exact one is the error the format itself causes, computed
+    without the GPU.  The GPU must reproduce the rounded scheme to within a
+    quarter of that effect: its FP32 arithmetic lets a few roundings fall the
+    other way.  It must also sit within 1.25 times the effect of the exact
+    oracle.  Measured on GB300: the GPU is at 0.12 to 0.14 of the effect, and
+    the effect in u is 4.1e-2 for BF16 and 3.1e-3 for FP16."""
     code, _ = STORES[store]
     cap = wl.small_capillary()
-    o = oracle_from(cap)
+    exact = oracle_from(cap)
+    rounded = oracle_from(cap)
+    rounded.set_storage_rounding(ROUNDING[store])
     s = lbib.from_capillary(cap, storage=code)
-    o.step(cap.steps)
+    exact.step(cap.steps)
+    rounded.step(cap.steps)
     s.advance(cap.steps)
-    _, ux, uy = o.macro()
-    gux, guy = s.velocity()
-    errs = {"u": rel_l2(np.stack([gux, guy]), np.stack([ux, uy])),
-            "x": max(np.abs(o.body_xy(b) - s.markers(b)).max() for b in range(len(cap.bodies)))}
-    oo, go = o.obs(), s.observables()[-1]
+    u = {}
+    for name, sim in (("exact", exact), ("rounded", rounded)):
+        _, ux, uy = sim.macro()
+        u[name] = np.stack([ux, uy])
+    u["gpu"] = np.stack(s.velocity())
+    effect, repro, total = rel_l2(u["rounded"], u["exact"]), rel_l2(u["gpu"], u["rounded"]), rel_l2(u["gpu"], u["exact"])
+    print(store, f"u: storage effect {effect:.2e}, GPU - rounded {repro:.2e}, GPU - exact {total:.2e}")
+    assert repro <= 0.25 * effect and total <= 1.25 * effect
+    for b in range(len(cap.bodies)):
+        xs = rounded.body_xy(b)
+        fx = np.abs(xs - exact.body_xy(b)).max()
+        assert np.abs(s.markers(b) - xs).max() <= 0.25 * fx + 1e-9, b
+    go, ro, eo = s.observables()[-1], rounded.obs(), exact.obs()
     assert go["step"] == cap.steps and go["status"] == 0
-    for k in ("delta_p", "r", "n_l"):
-        errs[k] = abs(go[k] - oo[k])
-    print(store, {k: f"{v:.3e}" for k, v in errs.items()}, "oracle:", {k: oo[k] for k in ("delta_p", "r", "n_l")})
-    for k, v in errs.items():
-        assert v <= C4_BOUNDS[store][k], (store, k, v)
+    for k in ("delta_p", "r"):
+        assert abs(go[k] - ro[k]) <= 0.25 * abs(ro[k] - eo[k]) + 1e-12, k
+    assert go["n_l"] == ro["n_l"] == eo["n_l"]
     s.close()
