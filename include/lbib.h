@@ -239,6 +239,15 @@ lbib_status lbib_read_latest_observables_async(lbib_ctx* ctx, lbib_obs* out, siz
  * within y_cr of a wall start bound. */
 lbib_status lbib_set_adhesion(lbib_ctx* ctx, int32_t body, const lbib_adhesion_params* params);
 
+/* n membranes in one call (a sweep adds hundreds): body k is
+ * lbib_add_membrane_to(ctx, instance[k], &descs[k], ...) followed, when
+ * adhesion (may be NULL) has a non-NULL adhesion[k], by lbib_set_adhesion with
+ * it; ids_out (may be NULL, else n entries) receives the ids.  Host arrays,
+ * copied.  On an error the bodies before the failing one stay added and the
+ * call returns that error. */
+lbib_status lbib_add_membranes(lbib_ctx* ctx, int32_t n, const int32_t* instance, const lbib_membrane_desc* descs,
+                               const lbib_adhesion_params* const* adhesion, int32_t* ids_out);
+
 /* Enqueues nsteps >= 0 time steps on the context stream and returns without
  * waiting.  The last step's Lagrangian update may stay pending (overlapped
  * with the next call's lattice update); every read call completes it. */
@@ -417,6 +426,15 @@ lbib_status lbib_lattice_advance_noalloc(const lbib_fluid_params* params, double
 enum { LBIB_FAULT_WAIT_TIMEOUT = 1 };
 lbib_status lbib_inject_fault(lbib_ctx* ctx, int32_t kind);
 void lbib_inject_alloc_failure(int64_t after);
+
+/* Device memory of contexts comes from a pool the library keeps per device
+ * (allocated and freed in the order of the context's stream).  lbib_destroy
+ * returns a context's memory to that pool, which keeps up to 8 GiB of it for
+ * the next context instead of giving it back to the device (mapping and
+ * unmapping a 64-capillary sweep's 1.6 GB takes about 2 ms).
+ * lbib_release_cached_memory waits for the device and gives every unused
+ * byte of the device's pool back; LBIB_ERR_INVALID_ARG for a bad ordinal. */
+lbib_status lbib_release_cached_memory(int32_t device);
 
 /* Message of the last failed call on ctx (or of the last failed lbib_create
  * or lbib_lattice_advance_noalloc when ctx is NULL).  Valid until the next

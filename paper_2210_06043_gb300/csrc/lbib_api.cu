@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -89,6 +90,31 @@ cudaError_t dalloc(std::vector<void*>& reg, T** p, size_t n)
     return e;
 }
 
+// The arrays of one phase (creation, set-up) carved out of one device
+// allocation, each on a 256-byte boundary: one cudaMalloc and one cudaFree
+// instead of one per array (about 45 of each per context).
+struct Arena {
+    std::vector<std::pair<void**, size_t>> parts;  // where each pointer goes, byte offset
+    size_t bytes = 0;
+    template <typename T>
+    void add(T** p, size_t n)
+    {
+        parts.push_back({reinterpret_cast<void**>(p), bytes});
+        bytes += (std::max<size_t>(n, 1) * sizeof(T) + 255) & ~size_t(255);
+    }
+    // stream-ordered: allocated, and at lbib_destroy freed, in the order of
+    // the context stream's work, so neither waits for the device
+    cudaError_t commit(std::vector<void*>& reg, cudaStream_t stream)
+    {
+        void* base = nullptr;
+        cudaError_t e = device_malloc_async(&base, std::max<size_t>(bytes, 256), stream);
+        if (e != cudaSuccess) return e;
+        reg.push_back(base);
+        for (auto& pr : parts) *pr.first = static_cast<char*>(base) + pr.second;
+        return cudaSuccess;
+    }
+};
+
 }  // namespace
 
 void lbib::set_global_error(const char* msg) { g_create_error = msg; }
@@ -100,16 +126,64 @@ __global__ void k_raise_status(uint32_t* status, uint32_t bits) { atomicOr(statu
 // allocations left before the injected failure (-1: none injected)
 static std::atomic<long long> g_alloc_countdown{-1};
 
-cudaError_t lbib::device_malloc(void** p, size_t bytes)
+static bool injected_failure()
 {
     long long c = g_alloc_countdown.load();
     while (c >= 0) {
-        if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) {
-            if (c == 0) return cudaErrorMemoryAllocation;  // the injected failure (once)
-            break;
-        }
+        if (g_alloc_countdown.compare_exchange_weak(c, c - 1)) return c == 0;  // the injected failure (once)
     }
+    return false;
+}
+
+cudaError_t lbib::device_malloc(void** p, size_t bytes)
+{
+    if (injected_failure()) return cudaErrorMemoryAllocation;
     return cudaMalloc(p, bytes);
+}
+
+// The library's memory pool of each device: contexts' arenas come from it in
+// stream order and go back to it at lbib_destroy, and it keeps up to
+// kPoolKeep bytes of them for the next context (mapping and unmapping a
+// sweep's 1.6 GB cost about 2 ms per context otherwise);
+// lbib_release_cached_memory gives them back to the device.
+static constexpr uint64_t kPoolKeep = uint64_t(8) << 30;
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+static cudaError_t device_pool(cudaMemPool_t* out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = kPoolKeep;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_pool[dev] = pool;
+    }
+    *out = g_pool[dev];
+    return cudaSuccess;
+}
+
+cudaError_t lbib::device_malloc_async(void** p, size_t bytes, cudaStream_t s)
+{
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = device_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
 }
 
 struct lbib_ctx {
@@ -144,6 +218,7 @@ struct lbib_ctx {
     int near_grid = 0;         // force gather blocks; 0: default, set at finalize
     int near_update_grid = 0;  // near lattice update blocks; 0: default, set at finalize
     std::vector<void*> allocs;
+    std::vector<void*> stream_allocs;  // stream-ordered allocations (the arenas), freed on `stream`
     double* macro_buf = nullptr;
     int device = 0;
     // batch of instances
@@ -316,14 +391,12 @@ lbib_status ensure_graphs(lbib_ctx* ctx)
     return LBIB_OK;
 }
 
-// Positions of buffer k as float-float pairs (hi, lo) of the compute type.
-lbib_status upload_posf(lbib_ctx* ctx, int k)
+// Positions of buffer k as float-float pairs (hi, lo) of the compute type,
+// from the host copy of the positions (x block then y block) just uploaded.
+lbib_status upload_posf(lbib_ctx* ctx, int k, const std::vector<double>& pos)
 {
     Dev& d = ctx->d;
     const size_t nm = std::max(d.nmark, 1);
-    std::vector<double> pos(2 * nm);
-    CK(cudaMemcpyAsync(pos.data(), d.pos[k], pos.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
     if (ctx->prec == PREC_F64) {
         std::vector<double> f(4 * nm, 0.0);
         for (size_t i = 0; i < nm; ++i) {
@@ -424,13 +497,15 @@ lbib_status finalize(lbib_ctx* ctx)
         ctx->lig_off[order[b]] = loff;
         const std::vector<double>& ref = h.xy_ref.empty() ? h.xy : h.xy_ref;
         const int nv = h.nv;
-        // stress-free lengths and turning angles
+        // stress-free lengths and turning angles (the angles only where Eq. 10
+        // acts: a deformable membrane with k_b > 0; elsewhere they stay 0)
+        const bool bends = h.motion == LBIB_DEFORMABLE && h.beta != 0.0;
         for (int l = 0; l < nv; ++l) {
             int w = (l + 1) % nv, lm = (l + nv - 1) % nv;
             double dx = ref[2 * w] - ref[2 * l], dy = ref[2 * w + 1] - ref[2 * l + 1];
             l0[off + l] = std::sqrt(dx * dx + dy * dy);
             double ax = ref[2 * l] - ref[2 * lm], ay = ref[2 * l + 1] - ref[2 * lm + 1];
-            th0[off + l] = std::atan2(ax * dy - ay * dx, ax * dx + ay * dy);
+            th0[off + l] = bends ? std::atan2(ax * dy - ay * dx, ax * dx + ay * dy) : 0.0;
         }
         Poly pr = polygon(ref), pc = polygon(h.xy);
         B.A0 = pr.A;
@@ -519,31 +594,33 @@ lbib_status finalize(lbib_ctx* ctx)
     void *dl0 = nullptr, *dth0 = nullptr, *dligt = nullptr;
     double* drref = nullptr;
     int32_t *dligel = nullptr, *dsite = nullptr;
-    CK(dalloc(reg, &d.pos[0], 2 * nm1));
-    CK(dalloc(reg, &d.pos[1], 2 * nm1));
-    CK(dalloc(reg, reinterpret_cast<char**>(&d.posf[0]), 4 * nm1 * rs));
-    CK(dalloc(reg, reinterpret_cast<char**>(&d.posf[1]), 4 * nm1 * rs));
-    CK(dalloc(reg, &dbody, std::max(nb, 1)));
-    CK(dalloc(reg, &d.rigid, (size_t)std::max(nb, 1) * RG_N));
-    CK(dalloc(reg, reinterpret_cast<char**>(&dl0), nm1 * rs));
-    CK(dalloc(reg, reinterpret_cast<char**>(&dth0), nm1 * rs));
-    CK(dalloc(reg, &drref, 2 * nm1));
-    CK(dalloc(reg, &dligel, nl1));
-    CK(dalloc(reg, reinterpret_cast<char**>(&dligt), nl1 * rs));
-    CK(dalloc(reg, &d.bound, nl1));
-    CK(dalloc(reg, &d.anchor, 2 * nl1));
-    CK(dalloc(reg, reinterpret_cast<char**>(&d.margin), nl1 * rs));
-    CK(dalloc(reg, &dsite, (size_t)nmark + 1));
-    CK(dalloc(reg, reinterpret_cast<char**>(&d.diag), (size_t)NDIAG * nm1 * rs));
-    CK(dalloc(reg, &d.body_obs[0], (size_t)std::max(nb, 1) * BO_N));
-    CK(dalloc(reg, &d.body_obs[1], (size_t)std::max(nb, 1) * BO_N));
-    CK(dalloc(reg, &d.ring, (size_t)ni * d.ring_cap));
+    Arena ar;
+    ar.add(&d.pos[0], 2 * nm1);
+    ar.add(&d.pos[1], 2 * nm1);
+    ar.add(reinterpret_cast<char**>(&d.posf[0]), 4 * nm1 * rs);
+    ar.add(reinterpret_cast<char**>(&d.posf[1]), 4 * nm1 * rs);
+    ar.add(&dbody, std::max(nb, 1));
+    ar.add(&d.rigid, (size_t)std::max(nb, 1) * RG_N);
+    ar.add(reinterpret_cast<char**>(&dl0), nm1 * rs);
+    ar.add(reinterpret_cast<char**>(&dth0), nm1 * rs);
+    ar.add(&drref, 2 * nm1);
+    ar.add(&dligel, nl1);
+    ar.add(reinterpret_cast<char**>(&dligt), nl1 * rs);
+    ar.add(&d.bound, nl1);
+    ar.add(&d.anchor, 2 * nl1);
+    ar.add(reinterpret_cast<char**>(&d.margin), nl1 * rs);
+    ar.add(&dsite, (size_t)nmark + 1);
+    ar.add(reinterpret_cast<char**>(&d.diag), (size_t)NDIAG * nm1 * rs);
+    ar.add(&d.body_obs[0], (size_t)std::max(nb, 1) * BO_N);
+    ar.add(&d.body_obs[1], (size_t)std::max(nb, 1) * BO_N);
+    ar.add(&d.ring, (size_t)ni * d.ring_cap);
     for (int k = 0; k < 2; ++k) {
-        CK(dalloc(reg, &d.mki[k], 2 * nm1));
-        CK(dalloc(reg, reinterpret_cast<char**>(&d.mkf[k]), 4 * nm1 * rs));
+        ar.add(&d.mki[k], 2 * nm1);
+        ar.add(reinterpret_cast<char**>(&d.mkf[k]), 4 * nm1 * rs);
     }
-    CK(dalloc(reg, &d.mask[0], (size_t)L.ntiles * d.mw));
-    CK(dalloc(reg, &d.mask[1], (size_t)L.ntiles * d.mw));
+    ar.add(&d.mask[0], (size_t)L.ntiles * d.mw);
+    ar.add(&d.mask[1], (size_t)L.ntiles * d.mw);
+    CK(ar.commit(ctx->stream_allocs, ctx->stream));
     d.body = dbody;
     d.l0 = dl0;
     d.th0 = dth0;
@@ -561,7 +638,7 @@ lbib_status finalize(lbib_ctx* ctx)
     CK(cudaMemcpyAsync(d.pos[0], pos.data(), pos.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(d.pos[1], pos.data(), pos.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
     for (int k = 0; k < 2; ++k) {
-        lbib_status st = upload_posf(ctx, k);
+        lbib_status st = upload_posf(ctx, k, pos);
         if (st != LBIB_OK) return st;
     }
     if (nb) CK(cudaMemcpyAsync(dbody, bc.data(), bc.size() * sizeof(BodyConst), cudaMemcpyHostToDevice, ctx->stream));
@@ -613,11 +690,7 @@ lbib_status finalize(lbib_ctx* ctx)
     }
     if (!ctx->near_grid) ctx->near_grid = std::max(1, std::min(L.ntiles, 4 * nsm));
     if (!ctx->near_update_grid) ctx->near_update_grid = std::max(1, std::min(L.ntiles, 16 * nsm));
-    ctx->finalized = true;
-    if (nb) {
-        lbib_status s = ensure_graphs(ctx);
-        if (s != LBIB_OK) return s;
-    }
+    ctx->finalized = true;  // the step graphs are captured at the first step (after any launch configuration)
     CK(cudaStreamSynchronize(ctx->stream));
     return LBIB_OK;
 }
@@ -764,28 +837,31 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     CKC(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&ctx->ev_lag, cudaEventDisableTiming));
     CKC(cudaEventCreateWithFlags(&ctx->ev_obs, cudaEventDisableTiming));
-    for (int i = 0; i < 6; ++i) CKC(cudaEventCreate(&ctx->pe[i]));
-    CKC(dalloc(reg, reinterpret_cast<char**>(&d.f[0]), nq * ctx->ssz));
-    CKC(dalloc(reg, reinterpret_cast<char**>(&d.f[1]), nq * ctx->ssz));
-    CKC(dalloc(reg, reinterpret_cast<char**>(&d.drho), nn * ctx->rsz));
-    CKC(dalloc(reg, reinterpret_cast<char**>(&d.ux), nn * ctx->rsz));
-    CKC(dalloc(reg, reinterpret_cast<char**>(&d.uy), nn * ctx->rsz));
-    CKC(dalloc(reg, reinterpret_cast<char**>(&d.fx), nn * ctx->rsz));
-    CKC(dalloc(reg, reinterpret_cast<char**>(&d.fy), nn * ctx->rsz));
-    CKC(dalloc(reg, &d.fresh, L.ntiles));
-    for (int i = 0; i < 3; ++i) CKC(dalloc(reg, &d.nearflag[i], L.ntiles));
-    for (int i = 0; i < 3; ++i) CKC(dalloc(reg, &d.list[i], d.list_cap));
-    CKC(dalloc(reg, &d.count, 3));
-    CKC(dalloc(reg, &d.step, 1));
-    CKC(dalloc(reg, &d.status, 1));
-    CKC(dalloc(reg, &d.ticket, 1));
-    CKC(dalloc(reg, &ctx->colinfo, cols.size()));
-    CKC(dalloc(reg, &ctx->inst, (size_t)ninst));
+    Arena ar;
+    ar.add(reinterpret_cast<char**>(&d.f[0]), nq * ctx->ssz);
+    ar.add(reinterpret_cast<char**>(&d.f[1]), nq * ctx->ssz);
+    ar.add(reinterpret_cast<char**>(&d.drho), nn * ctx->rsz);
+    ar.add(reinterpret_cast<char**>(&d.ux), nn * ctx->rsz);
+    ar.add(reinterpret_cast<char**>(&d.uy), nn * ctx->rsz);
+    ar.add(reinterpret_cast<char**>(&d.fx), nn * ctx->rsz);
+    ar.add(reinterpret_cast<char**>(&d.fy), nn * ctx->rsz);
+    ar.add(&d.fresh, L.ntiles);
+    for (int i = 0; i < 3; ++i) ar.add(&d.nearflag[i], L.ntiles);
+    for (int i = 0; i < 3; ++i) ar.add(&d.list[i], d.list_cap);
+    ar.add(&d.count, 3);
+    ar.add(&d.step, 1);
+    ar.add(&d.status, 1);
+    ar.add(&d.ticket, 1);
+    ar.add(&ctx->colinfo, cols.size());
+    ar.add(&ctx->inst, (size_t)ninst);
+    CKC(ar.commit(ctx->stream_allocs, ctx->stream));
     d.colinfo = ctx->colinfo;
     d.inst = ctx->inst;
     CKC(cudaMemcpyAsync(ctx->colinfo, cols.data(), cols.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
-    CKC(cudaMemsetAsync(d.f[0], 0, nq * ctx->ssz, ctx->stream));
-    CKC(cudaMemsetAsync(d.f[1], 0, nq * ctx->ssz, ctx->stream));
+    // populations: the initial state is written whole (padding included) by
+    // the init kernel below; the second buffer needs no fill either: the first
+    // lattice step writes every node of it, and the row padding past an
+    // instance's end is never read as data by any kernel
     // tensor maps for the TMA-staged bulk update (left out where the driver
     // has no encoder: the direct-load kernel then runs whatever the option)
     d.bulk_tma = 0;
@@ -804,8 +880,7 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     CKC(cudaMemsetAsync(d.step, 0, 8, ctx->stream));
     CKC(cudaMemsetAsync(d.status, 0, 4, ctx->stream));
     CKC(cudaMemsetAsync(d.ticket, 0, 4, ctx->stream));
-    CKC(launch_init_populations(d, ctx->prec, 0, ctx->stream));
-    CKC(cudaStreamSynchronize(ctx->stream));
+    CKC(launch_init_populations(d, ctx->prec, 0, ctx->stream));  // the stream orders it before any use
 #undef CKC
     *out = ctx;
     return LBIB_OK;
@@ -865,6 +940,20 @@ lbib_status lbib_add_membrane_to(lbib_ctx* ctx, int32_t instance, const lbib_mem
 lbib_status lbib_add_membrane(lbib_ctx* ctx, const lbib_membrane_desc* m, int32_t* id_out)
 {
     return lbib_add_membrane_to(ctx, 0, m, id_out);
+}
+
+lbib_status lbib_add_membranes(lbib_ctx* ctx, int32_t n, const int32_t* instance, const lbib_membrane_desc* descs,
+                               const lbib_adhesion_params* const* adhesion, int32_t* ids_out)
+{
+    if (!ctx || n < 0 || (n > 0 && (!instance || !descs))) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
+    for (int32_t k = 0; k < n; ++k) {
+        int32_t id = -1;
+        lbib_status s = lbib_add_membrane_to(ctx, instance[k], &descs[k], &id);
+        if (s == LBIB_OK && adhesion && adhesion[k]) s = lbib_set_adhesion(ctx, id, adhesion[k]);
+        if (s != LBIB_OK) return s;  // bodies before k stay added
+        if (ids_out) ids_out[k] = id;
+    }
+    return LBIB_OK;
 }
 
 lbib_status lbib_set_adhesion(lbib_ctx* ctx, int32_t body, const lbib_adhesion_params* a)
@@ -951,7 +1040,11 @@ static lbib_status read_macro(lbib_ctx* ctx, int32_t inst, double* rho, double* 
     int max_nx = 0;
     for (int v : ctx->inst_nx) max_nx = std::max(max_nx, v);
     const size_t cap = (size_t)max_nx * L.ny;
-    if (!ctx->macro_buf) CK(dalloc(ctx->allocs, &ctx->macro_buf, 3 * cap));
+    if (!ctx->macro_buf) {
+        Arena ar;
+        ar.add(&ctx->macro_buf, 3 * cap);
+        CK(ar.commit(ctx->stream_allocs, ctx->stream));
+    }
     int64_t m = ctx->s_f - 1;
     CK(launch_macro(ctx->d, ctx->prec, (int)(ctx->s_f & 1), m, ctx->inst_x0[inst], inx, ctx->macro_buf,
                     ctx->macro_buf + cap, ctx->macro_buf + 2 * cap, ctx->stream));
@@ -1482,6 +1575,22 @@ lbib_status lbib_inject_fault(lbib_ctx* ctx, int32_t kind)
 
 void lbib_inject_alloc_failure(int64_t after) { g_alloc_countdown.store(after < 0 ? -1 : (long long)after); }
 
+lbib_status lbib_release_cached_memory(int32_t device)
+{
+    if (device < 0 || device >= 64) return fail(nullptr, LBIB_ERR_INVALID_ARG, "device ordinal");
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        pool = g_pool[device];
+    }
+    if (!pool) return LBIB_OK;  // nothing cached on that device
+    DeviceGuard guard(device);
+    cudaError_t e = cudaDeviceSynchronize();  // frees still in flight reach the pool first
+    if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "lbib_release_cached_memory");
+    return LBIB_OK;
+}
+
 lbib_status lbib_get_launch_config(lbib_ctx* ctx, lbib_launch_config* out)
 {
     if (!ctx || !out) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
@@ -1501,7 +1610,8 @@ lbib_status lbib_set_launch_config(lbib_ctx* ctx, const lbib_launch_config* cfg)
     if (s != LBIB_OK) return s;
     s = finish_pending(ctx);
     if (s != LBIB_OK) return s;
-    CK(cudaStreamSynchronize(ctx->stream));
+    // no wait: launches already enqueued keep the parameters they were given,
+    // and a step graph still in flight is freed when it completes
     apply_config(ctx, *cfg);
     return LBIB_OK;
 }
@@ -1661,6 +1771,10 @@ lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_co
 lbib_status lbib_set_profiling(lbib_ctx* ctx, int32_t enable)
 {
     if (!ctx) return fail(ctx, LBIB_ERR_INVALID_ARG, "null context");
+    if (enable && !ctx->pe[0]) {  // timing events only for contexts that profile
+        DeviceGuard guard(ctx->device);
+        for (int i = 0; i < 6; ++i) CK(cudaEventCreate(&ctx->pe[i]));
+    }
     ctx->profiling = enable != 0;
     return LBIB_OK;
 }
@@ -1703,9 +1817,13 @@ void lbib_destroy(lbib_ctx* ctx)
 {
     if (!ctx) return;
     DeviceGuard guard(ctx->device);
-    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    if (ctx->copy) cudaStreamSynchronize(ctx->copy);
+    // no wait for the device: graphs still in flight are freed when they
+    // complete, and the arenas are freed in the stream's order after them and
+    // after the last observables copy (which reads the ring)
+    if (ctx->stream && ctx->ev_copy) cudaStreamWaitEvent(ctx->stream, ctx->ev_copy, 0);
     destroy_graphs(ctx);
+    for (void* p : ctx->stream_allocs) cudaFreeAsync(p, ctx->stream);
+    if (!ctx->allocs.empty() && ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (void* p : ctx->allocs) cudaFree(p);
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);

@@ -230,6 +230,8 @@ void set_global_error(const char* msg);
 // cudaMalloc through the allocation-failure countdown of
 // lbib_inject_alloc_failure (every device allocation of the library goes here)
 cudaError_t device_malloc(void** p, size_t bytes);
+// the same through cudaMallocAsync on stream s (the device's default memory pool)
+cudaError_t device_malloc_async(void** p, size_t bytes, cudaStream_t s);
 cudaError_t configure_kernels(int prec, int nv_max);
 
 }  // namespace lbib

@@ -1012,13 +1012,21 @@ __global__ void __launch_bounds__(TX* TY, (std::is_same<R, float>::value ? 12 : 
     pdl_trigger();
 }
 
+// Initial post-collision populations: equilibrium at rho = 1 with the inlet
+// profile (or at rest); the columns past an instance's end (row padding) get
+// zeros, so the whole buffer is written and needs no fill beforehand.
 template <typename S, typename R>
 __global__ void k_init_populations(Dev d, int buf)
 {
     const Lattice& L = d.L;
     int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
-    if (x - d.colinfo[blockIdx.x].x >= d.colinfo[blockIdx.x].y || y >= L.ny) return;
+    if (y >= L.ny) return;
     S* f = static_cast<S*>(d.f[buf]);
+    if (x - d.colinfo[blockIdx.x].x >= d.colinfo[blockIdx.x].y) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) st<S, R>(f + q * L.qstride + y * L.nxp + x, R(0));
+        return;
+    }
     R u = (L.bc == LBIB_BC_INLET_OUTLET) ? inlet_profile<R>(L, y) : R(0);
 #pragma unroll
     for (int q = 0; q < 9; ++q) {

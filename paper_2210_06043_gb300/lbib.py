@@ -124,6 +124,8 @@ _SIGS = {
     "lbib_mlp_sync": [_P],
     "lbib_mlp_inject_fault": [_P, ctypes.c_int32],
     "lbib_inject_fault": [_P, ctypes.c_int32],
+    "lbib_release_cached_memory": [ctypes.c_int32],
+    "lbib_add_membranes": [_P, ctypes.c_int32, _P, _P, _P, _P],
 }
 
 _lib = None
@@ -539,12 +541,40 @@ class Mlp:
 
 
 def _add_bodies(s: Solver, cap, instance: int) -> None:
-    for b in cap.bodies:
-        i = s.add_membrane(b.kind, b.motion, b.xy, b.xy_ref, b.ca, b.beta, b.ka, b.density_ratio,
-                           instance=instance)
+    _add_all(s, [(instance, b) for b in cap.bodies])
+
+
+def _add_all(s: Solver, items) -> None:
+    """Every (instance, workloads.Body) of `items` in one lbib_add_membranes call."""
+    n = len(items)
+    if n == 0:
+        return
+    keep = []
+    descs = (lbib_membrane_desc * n)()
+    adh = (ctypes.POINTER(lbib_adhesion_params) * n)()
+    inst = (ctypes.c_int32 * n)()
+    for k, (i, b) in enumerate(items):
+        xy = np.ascontiguousarray(np.asarray(b.xy, dtype=np.float64).reshape(-1))
+        ref = None if b.xy_ref is None else np.ascontiguousarray(np.asarray(b.xy_ref, dtype=np.float64).reshape(-1))
+        keep += [xy, ref]
+        descs[k] = lbib_membrane_desc(kind=int(b.kind), motion=int(b.motion), nv=len(xy) // 2, xy=_dp(xy),
+                                      xy_ref=_dp(ref) if ref is not None else None, ca=float(b.ca),
+                                      beta=float(b.beta), ka=float(b.ka), density_ratio=float(b.density_ratio))
+        inst[k] = int(i)
         if b.adhesion is not None:
             a = b.adhesion
-            s.set_adhesion(i, a.n_lig, a.sigma, a.y_cr, a.y_eq, a.kf_dt, a.kr0_dt, a.xi)
+            p = lbib_adhesion_params(n_ligands=int(a.n_lig), sigma=float(a.sigma), y_cr=float(a.y_cr),
+                                     y_eq=float(a.y_eq), kf_dt=float(a.kf_dt), kr0_dt=float(a.kr0_dt),
+                                     xi=float(a.xi))
+            keep.append(p)
+            adh[k] = ctypes.pointer(p)
+    ids = (ctypes.c_int32 * n)()
+    s._c(s.lib.lbib_add_membranes(s.ctx, n, ctypes.cast(inst, _P), ctypes.cast(descs, _P), ctypes.cast(adh, _P),
+                                  ctypes.cast(ids, _P)))
+    for k, (i, b) in enumerate(items):
+        s.nv.append(np.asarray(b.xy).size // 2)
+        if b.adhesion is not None:
+            s.nlig[ids[k]] = int(b.adhesion.n_lig)
 
 
 def from_capillaries(caps, storage=None, device=0, stream=None, obs_capacity=0) -> Solver:
@@ -562,8 +592,7 @@ def from_capillaries(caps, storage=None, device=0, stream=None, obs_capacity=0) 
     s = Solver([c.nx for c in caps], c0.ny, tau=c0.tau, re=c0.re, rho_out=c0.rho_out, bc=c0.bc, g=c0.g,
                storage=st, device=device, stream=stream, obs_capacity=obs_capacity, seeds=[c.seed for c in caps],
                transfer=c0.transfer)
-    for k, c in enumerate(caps):
-        _add_bodies(s, c, k)
+    _add_all(s, [(k, b) for k, c in enumerate(caps) for b in c.bodies])
     return s
 
 
@@ -571,6 +600,12 @@ def inject_alloc_failure(after: int) -> None:
     """Failure-detection tests: the (after + 1)-th device allocation the
     library makes from now on fails as out of memory (once); after < 0 cancels."""
     load().lbib_inject_alloc_failure(int(after))
+
+
+def release_cached_memory(device: int = 0) -> None:
+    """Give the device memory the library keeps for the next context back
+    to the device (waits for the device)."""
+    _check(load().lbib_release_cached_memory(int(device)), None)
 
 
 def roofline_bytes_per_node(storage: int) -> int:
@@ -581,4 +616,4 @@ def roofline_bytes_per_node(storage: int) -> int:
 
 __all__ = [n for n in dir() if n.startswith("lbib_") or n.startswith("LBIB_")] + [
     "Solver", "Mlp", "from_capillary", "from_capillaries", "load", "library_path", "LbibError", "roofline_bytes_per_node", "FIELDS",
-    "inject_alloc_failure"]
+    "inject_alloc_failure", "release_cached_memory"]

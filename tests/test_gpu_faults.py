@@ -124,7 +124,7 @@ def test_failed_allocations_return_oom_and_leak_nothing():
             break  # k is past the last allocation: the run needed no more
     finally:
         lbib.inject_alloc_failure(-1)
-    assert failures > 20  # every allocation of creation and set-up was hit
+    assert failures >= 2  # creation and set-up (one allocation each) were both hit
     assert _free_bytes() == base
     _run_small(cap)  # the injection is spent: a normal run again
 
@@ -168,3 +168,26 @@ def test_failed_allocation_in_the_autotuner_leaves_the_context_usable():
     assert np.array_equal(a.markers(0), b.markers(0))
     a.close()
     b.close()
+
+
+def test_destroyed_contexts_memory_is_reused_then_released():
+    """lbib_destroy returns a context's device memory to the library's pool,
+    which keeps it for the next context of the process; a second context of
+    the same size allocates nothing new from the device, and
+    lbib_release_cached_memory gives the memory back to the device."""
+    cap = wl.Capillary("long", 6000, 150, 1.0, 1e-2, 0, "fp32", 0, [])  # ~65 MB of populations
+    lbib.release_cached_memory(0)
+    free0 = _free_bytes()
+    lbib.from_capillary(cap).close()
+    free1 = _free_bytes()
+    assert free0 - free1 > 60e6  # kept by the pool
+    s = lbib.from_capillary(cap)
+    s.advance(2)
+    s.sync()
+    assert _free_bytes() == free1  # the second context reused it
+    s.close()
+    lbib.release_cached_memory(0)
+    assert _free_bytes() >= free0 - (2 << 20)
+    with pytest.raises(lbib.LbibError) as e:
+        lbib.release_cached_memory(-1)
+    assert e.value.status == lbib.LBIB_ERR_INVALID_ARG
