@@ -11,7 +11,10 @@
  *   z_l = W_l a_{l-1} + b_l,  a_l = bf16(GELU(z_l))   (l = 1 .. n_hidden),
  *   y   = s_out * (W_out a_{n_hidden} + b_out) + c_out,
  * weights used in BF16 (FP32 master copies), products accumulated in FP32.
- * GELU(z) = z Phi(z), Phi the standard normal distribution function.
+ * GELU in the tanh form of Hendrycks & Gimpel (Gaussian Error Linear Units,
+ * 2016): GELU(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))), within
+ * 5e-4 of z Phi(z) (Phi the standard normal distribution function); the tanh
+ * is evaluated by the GPU's tanh approximation (relative error about 2^-11).
  * Training minimises the mean over the batch and the outputs of
  * ((y - t) / s_out)^2 (targets standardised by the same affine map) with Adam
  * (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).

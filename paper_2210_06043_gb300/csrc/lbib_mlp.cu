@@ -83,10 +83,102 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU in the tanh form of Hendrycks & Gimpel (Gaussian Error Linear Units,
+// 2016): GELU(z) = z/2 (1 + tanh(u)), u = sqrt(2/pi) (z + 0.044715 z^3).  The
+// tanh is the hardware approximation (tanh.approx.f32, relative error about
+// 2^-11; its packed FP16 form gives no more results per clock); every other
+// step is an explicitly rounded FP32 operation in a fixed order, so the packed
+// two-lane form (gelu2_bf16, f32x2 arithmetic) returns the same bits as the
+// scalar one.
+constexpr float GELU_K0 = 0.7978845608028654f;     // sqrt(2/pi)
+constexpr float GELU_K1 = 0.035677408136300125f;   // 0.044715 sqrt(2/pi)
+constexpr float GELU_K1X3 = 0.10703222440890037f;  // 3 * 0.044715 sqrt(2/pi)
+
+__device__ __forceinline__ float tanh_hw(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float gelu(float z)
+{
+    const float u = __fmul_rn(z, __fmaf_rn(__fmul_rn(z, z), GELU_K1, GELU_K0));
+    const float h = __fmul_rn(0.5f, z);
+    return __fmaf_rn(h, tanh_hw(u), h);
+}
+// d GELU / dz = (1 + tanh u)/2 + z/2 (1 - tanh^2 u) sqrt(2/pi) (1 + 3 * 0.044715 z^2)
 __device__ __forceinline__ float gelu_d(float z)
 {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+    const float zz = __fmul_rn(z, z);
+    const float th = tanh_hw(__fmul_rn(z, __fmaf_rn(zz, GELU_K1, GELU_K0)));
+    const float s = __fmaf_rn(-th, th, 1.0f);
+    return __fmaf_rn(__fmul_rn(__fmul_rn(0.5f, z), s), __fmaf_rn(zz, GELU_K1X3, GELU_K0), __fmaf_rn(0.5f, th, 0.5f));
+}
+
+// Two-lane FP32 arithmetic (add/mul/fma .rn .f32x2): one instruction for two
+// values, each lane rounded like the scalar operation.
+__device__ __forceinline__ uint64_t f2(float a, float b)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_split(uint64_t v, float& a, float& b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// GELU(v0 + b0), GELU(v1 + b1) rounded to a BF16 pair: gelu() on two lanes.
+__device__ __forceinline__ uint32_t gelu2_bf16(float v0, float v1, float b0, float b1)
+{
+    const uint64_t z = f2_add(f2(v0, v1), f2(b0, b1));
+    const uint64_t u = f2_mul(z, f2_fma(f2_mul(z, z), f2(GELU_K1, GELU_K1), f2(GELU_K0, GELU_K0)));
+    const uint64_t h = f2_mul(f2(0.5f, 0.5f), z);
+    float u0, u1, g0, g1;
+    f2_split(u, u0, u1);
+    f2_split(f2_fma(h, f2(tanh_hw(u0), tanh_hw(u1)), h), g0, g1);
+    const __nv_bfloat162 b2 = __floats2bfloat162_rn(g0, g1);
+    return *reinterpret_cast<const uint32_t*>(&b2);
+}
+
+// Tensor memory -> registers: 32 lanes x 16 consecutive 32-bit columns
+// (tcgen05.ld 32x32b.x16), and the wait for the loads issued so far.  The wait
+// names the destination registers as operands, so no use of them can be
+// scheduled above it.
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(addr));
+}
+__device__ __forceinline__ void tmem_wait(uint32_t (&v)[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                   "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]),
+                   "+r"(v[15])
+                 :
+                 : "memory");
 }
 
 // Shared tiles: A as [BM][BK+PAD] (K-major) or [BK][BM+PAD] (M-major), B likewise.
@@ -350,14 +442,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(GemmArgs g)
             for (int sub = 0; sub < SC / 16; ++sub) {
                 uint32_t r[16];
                 const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c0 + 16 * sub);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                    "%13, %14, %15}, [%16];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15])
-                    : "r"(ta));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                tmem_ld16(ta, r);
+                tmem_wait(r);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int col = 16 * sub + j;
@@ -402,22 +488,51 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(GemmArgs g)
 //     K slice in the same core-matrix layout, contiguous in global memory)
 //     through FZ_STAGES shared-memory stages with cp.async.bulk, each chunk
 //     completing a "full" barrier by its byte count;
-//   warps 4 .. 11: the epilogue.  Warp w reads tensor-memory lanes
-//     32 (w % 4) .. + 31 (its tile rows) over half of the columns, adds the
-//     bias, applies GELU and writes the BF16 operand of the next layer in
-//     place, or writes the output rows; they also load the inputs of the
-//     next tile of the slot.  Each step ends with an arrival on the slot's
-//     "epilogue done" barrier, which the MMA issuer waits for.
+//   warps 4 .. 19: the epilogue.  Warp w reads tensor-memory lanes
+//     32 (w % 4) .. + 31 (its tile rows) over a quarter of the columns, adds
+//     the bias, applies GELU (f32x2 arithmetic, hardware tanh) and writes the
+//     BF16 operand of the next layer in place, or writes the output rows;
+//     they also load the inputs of the next tile of the slot.  Each step ends
+//     with an arrival on the slot's "epilogue done" barrier, which the MMA
+//     issuer waits for.  Four epilogue warps per SM sub-partition keep the
+//     tanh unit (16 results per clock per SM, the epilogue's floor: 2048
+//     cycles per 128 x 256 layer, as long as the layer's MMAs) busy.
 // While the MMAs of one slot's layer run, the epilogue of the other slot's
-// previous layer runs.  Every wait is bounded: on timeout the CTA sets the
-// status word, the other roles leave their loops, the copies and MMAs still
-// in flight are waited for (bounded) and the tensor memory is freed.
-constexpr int FZ_THREADS = 384, FZ_STAGES = 3, FZ_MAXW = 256, FZ_MAXL = 9;
+// previous layer runs.  Both then share the SM's shared-memory bandwidth with
+// the weight stream: per 128 x 256 x 256 layer the MMAs read 192 KB of
+// operands, the stream writes 128 KB of weights and the epilogue 64 KB of
+// activations, about 3000 cycles at 128 B per clock against 2048 for the
+// MMAs alone.  Every wait is bounded: on timeout the CTA sets the status
+// word, the other roles leave their loops, the copies and MMAs still in
+// flight are waited for (bounded) and the tensor memory is freed.
+constexpr int FZ_STAGES = 3, FZ_MAXW = 256, FZ_MAXL = 9, FZ_EW = 16, FZ_THREADS = 128 + 32 * FZ_EW;
 constexpr size_t FZ_ACT = (size_t)TC_BM * FZ_MAXW * 2;        // 64 KB per slot
 constexpr size_t FZ_STAGE = (size_t)FZ_MAXW * TC_BK * 2;      // 32 KB per weight chunk
 constexpr size_t FZ_BAR = 2 * FZ_ACT + FZ_STAGES * FZ_STAGE;  // barriers after the buffers
 constexpr size_t FZ_SMEM = FZ_BAR + 256;
 static_assert(FZ_SMEM <= 227 * 1024, "fused kernel shared memory");
+
+// Epilogue of one hidden layer for 16 accumulator columns cb .. cb + 15 of
+// one tile row: bias, GELU, BF16, written as the next layer's A operand
+// (K-major core matrices: 64-column chunks of 16 KB, 8-row groups of 1 KB,
+// 8-column blocks of 128 B, one 16-byte row per block).
+__device__ __forceinline__ void fz_gelu16(const uint32_t (&v)[16], const float4 (&b)[4], int cb, unsigned char* arow)
+{
+    uint32_t pk[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        pk[2 * i] = gelu2_bf16(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1]), b[i].x, b[i].y);
+        pk[2 * i + 1] = gelu2_bf16(__uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3]), b[i].z, b[i].w);
+    }
+    unsigned char* dst = arow + (cb >> 6) * 16384 + ((cb & 63) >> 3) * 128;
+    *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    *reinterpret_cast<uint4*>(dst + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+}
+__device__ __forceinline__ void ld_bias16(float4 (&b)[4], const float4* p)
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = __ldg(p + i);
+}
 
 struct FusedArgs {
     const float* x;
@@ -455,13 +570,15 @@ __device__ __forceinline__ void fz_arrive(uint64_t* bar)
 }
 
 // inputs of a tile into the slot's first K chunk: a0 = bf16(s_in (x - c_in)),
-// zero beyond n_in and beyond the last row; 256 epilogue threads, two per row
+// zero beyond n_in and beyond the last row; 32 FZ_EW epilogue threads,
+// FZ_EW / 4 per row
 __device__ __forceinline__ void fz_prep(const FusedArgs& a, int tile, unsigned char* act, int e)
 {
-    const int r = e >> 1, part = e & 1, row = tile * TC_BM + r;
+    constexpr int PARTS = FZ_EW * 32 / TC_BM, COLS = 64 / PARTS;
+    const int r = e / PARTS, part = e % PARTS, row = tile * TC_BM + r;
 #pragma unroll
-    for (int g8 = 0; g8 < 4; ++g8) {
-        const int c0 = part * 32 + g8 * 8;
+    for (int g8 = 0; g8 < COLS / 8; ++g8) {
+        const int c0 = part * COLS + g8 * 8;
         uint32_t pk[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -496,6 +613,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
     const int ntiles = (a.M + TC_BM - 1) / TC_BM;
     // this CTA's tiles: blockIdx.x + k gridDim.x, k < nk; tile k uses slot k & 1
     const int nk = ((int)blockIdx.x < ntiles) ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto tile_of = [&](int k) { return (int)blockIdx.x + k * (int)gridDim.x; };
     if (tid == 0) {
         for (int i = 0; i < FZ_STAGES; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(1));
@@ -503,7 +621,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
         }
         for (int sl = 0; sl < 2; ++sl) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&accf[sl])), "r"(1));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&epid[sl])), "r"(256));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&epid[sl])), "r"(32 * FZ_EW));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(fin)), "r"(1));
         *abort_flag = 0u;
@@ -597,9 +715,10 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
         }
     } else if (warp >= 4) {
         // ---------------------------------------------------- epilogue
-        const int e = tid - 128, q4 = warp & 3, half = (warp - 4) >> 2, r = q4 * 32 + lane;
+        constexpr int NCG = FZ_EW / 4;  // column groups per tile row
+        const int e = tid - 128, q4 = warp & 3, cg = (warp - 4) >> 2, r = q4 * 32 + lane;
         for (int sl = 0; sl < 2 && sl < nk; ++sl) {
-            fz_prep(a, (int)blockIdx.x + sl * (int)gridDim.x, act[sl], e);
+            fz_prep(a, tile_of(sl), act[sl], e);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             fz_arrive(&epid[sl]);
         }
@@ -614,48 +733,29 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
                     apar[sl] ^= 1u;
                     if (!ok) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const int tile = (int)blockIdx.x + k * (int)gridDim.x;
+                    const int tile = tile_of(k);
                     const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(sl * 256);
                     if (l + 1 < a.L) {
-                        const int N = a.N[l], cbeg = half * (N >> 1), cend = cbeg + (N >> 1);
-                        const float* bias = a.bias + a.boff[l];
+                        // N is a multiple of 64: each column group is whole 16-column blocks
+                        const int N = a.N[l], cbeg = cg * (N / NCG), cend = cbeg + N / NCG;
+                        const float4* bias4 = reinterpret_cast<const float4*>(a.bias + a.boff[l]);
+                        unsigned char* arow = act[sl] + (r >> 3) * 1024 + (r & 7) * 16;
                         for (int cb = cbeg; cb < cend; cb += 16) {
                             uint32_t v[16];
-                            asm volatile(
-                                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
-                                "%10, %11, %12, %13, %14, %15}, [%16];"
-                                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-                                  "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                                : "r"(trow + (uint32_t)cb));
-                            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                            uint32_t pk[8];
-#pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                const float z0 = __uint_as_float(v[2 * i]) + bias[cb + 2 * i];
-                                const float z1 = __uint_as_float(v[2 * i + 1]) + bias[cb + 2 * i + 1];
-                                const __nv_bfloat162 b2 = __floats2bfloat162_rn(gelu(z0), gelu(z1));
-                                pk[i] = *reinterpret_cast<const uint32_t*>(&b2);
-                            }
-                            unsigned char* dst = act[sl] + (cb >> 6) * 16384 + (r >> 3) * 1024 +
-                                                 ((cb & 63) >> 3) * 128 + (r & 7) * 16;
-                            *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                            *reinterpret_cast<uint4*>(dst + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                            float4 b[4];
+                            tmem_ld16(trow + (uint32_t)cb, v);
+                            ld_bias16(b, bias4 + (cb >> 2));
+                            tmem_wait(v);
+                            fz_gelu16(v, b, cb, arow);
                         }
                     } else {
                         const float* bias = a.bias + a.boff[l];
                         const int row = tile * TC_BM + r;
-                        for (int cb = half * 32; cb < half * 32 + 32; cb += 16) {
+                        for (int cb = cg * (64 / NCG); cb < (cg + 1) * (64 / NCG); cb += 16) {
                             if (cb >= a.n_out) break;  // uniform across the warp
                             uint32_t v[16];
-                            asm volatile(
-                                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
-                                "%10, %11, %12, %13, %14, %15}, [%16];"
-                                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-                                  "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                                : "r"(trow + (uint32_t)cb));
-                            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                            tmem_ld16(trow + (uint32_t)cb, v);
+                            tmem_wait(v);
                             if (row < a.M)
 #pragma unroll
                                 for (int j = 0; j < 16; ++j) {
@@ -666,7 +766,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
                                 }
                         }
                         // the slot's next tile: the MMAs of this one have all completed
-                        if (k + 2 < nk) fz_prep(a, tile + 2 * (int)gridDim.x, act[sl], e);
+                        if (k + 2 < nk) fz_prep(a, tile_of(k + 2), act[sl], e);
                     }
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -823,8 +923,6 @@ lbib_status mlp_fail(lbib_status s, const std::string& m)
     set_global_error(m.c_str());
     return s;
 }
-
-int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 __global__ void k_or_word(uint32_t* w, uint32_t bits) { atomicOr(w, bits); }
 

@@ -1,8 +1,9 @@
 """GPU parity of the surrogate network's kernels (include/lbib_mlp.h) against
 the CPU oracle (oracle/mlp.py, quantize=True: the same bfloat16 roundings).
 
-Tolerances: the GPU accumulates products in FP32 and evaluates GELU in FP32,
-so an activation sitting on a bfloat16 rounding boundary can round the other
+Tolerances: the GPU accumulates products in FP32 and evaluates GELU in FP32
+with the hardware tanh approximation (relative error about 2^-11), so an
+activation sitting on a bfloat16 rounding boundary can round the other
 way (one unit, 2^-8 relative); such flips are rare and propagate as small
 noise, so outputs and gradients are compared in relative L2 (5e-3 and 2e-2),
 not element by element."""
