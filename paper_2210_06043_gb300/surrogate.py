@@ -4,7 +4,11 @@ solver itself generates, with the solver as fallback outside the training hull.
 
 Pieces (all numerical work in the library's kernels; this module only lays
 out inputs and drives the C ABI):
-  * the parameter space and its sampling (``Point``, ``sample_points``);
+  * the parameter space and its sampling (``Point``, ``sample_points``), and
+    bond-seed replicates of each point (``replicate``, ``seed_statistics``):
+    N_L counts stochastic bond events, so a point's trajectories differ from
+    seed to seed; the network is trained on replicate means, and that
+    seed-to-seed spread is the noise floor its N_L error is judged against;
   * the capillary each point runs in (``capillary_for``);
   * trajectory generation with batched solver contexts (``generate``);
   * training of ``lbib.Mlp`` on the trajectories (``train``), on one GPU or
@@ -42,7 +46,8 @@ STEPS, SAMPLES = 300000, 512
 AR_RANGE = (0.25, 1.0)
 LOGCA_RANGE = (-4.0, -3.0)
 DENSITY_RANGE = (10.0, 50.0)  # ligand sites per um of particle perimeter
-FEATURES = ("aspect_ratio", "log10_ca", "rigid", "globular", "biconcave", "ligand_density", "t_star")
+FEATURES = ("aspect_ratio", "log10_ca", "rigid", "globular", "biconcave", "ligand_density", "initial_bonds",
+            "inverse_initial_bonds", "t_star")
 OUTPUTS = ("n_l", "delta_p", "r")
 
 
@@ -72,12 +77,114 @@ def sample_points(n: int, seed: int = 0, rigid_fraction: float = 0.2) -> List[Po
                   seed=int(seed * 100003 + i)) for i in range(n)]
 
 
-def features(p: Point, t_star) -> np.ndarray:
-    """Feature rows [len(t_star), 7] for point p at the given times."""
+def replicate(points: Sequence[Point], replicates: int) -> List[Point]:
+    """Each point `replicates` times, consecutively, with bond seeds
+    seed * replicates + j (j < replicates): the same capillary under
+    independent Philox streams."""
+    return [dataclasses.replace(p, seed=p.seed * replicates + j) for p in points for j in range(replicates)]
+
+
+def seed_statistics(Y: np.ndarray, replicates: int):
+    """Y [n * replicates, samples, 3], the replicates of a point consecutive
+    (``replicate``).  Returns the replicate means [n, samples, 3] and, per
+    output, the seed-to-seed spread: the root mean square over points and
+    times of the sample standard deviation across replicates (the error floor
+    of predicting one trajectory), and that divided by sqrt(replicates) (the
+    floor of predicting a replicate mean, the uncertainty of the mean itself)."""
+    if replicates < 2:
+        raise ValueError("the spread needs at least two replicates")
+    Yr = Y.reshape(-1, replicates, *Y.shape[1:])
+    sd = np.sqrt(np.mean(Yr.var(1, ddof=1), axis=(0, 1)))
+    return Yr.mean(1), sd, sd / math.sqrt(replicates)
+
+
+_POLY = {}  # aspect-ratio nodes and the particle polygons (relative to the centre) at them
+
+
+def _particle_polygon(ar: np.ndarray) -> np.ndarray:
+    """The training particle's marker polygon relative to its centre
+    [len(ar), PARTICLE_MARKERS, 2] for aspect ratios inside AR_RANGE: a cubic
+    spline in the aspect ratio through the exact polygons (``wl.ellipse``,
+    equal arc spacing from 20000 samples) at 193 nodes; the vertices agree with
+    the exact construction to about 1e-9 dx."""
+    from scipy.interpolate import CubicSpline
+
+    if "spline" not in _POLY:
+        a = 0.5 * wl.PARTICLE_LENGTH_UM / (wl.H_UM / NY)
+        nodes = np.linspace(AR_RANGE[0], AR_RANGE[1], 193)
+        tab = np.stack([wl.ellipse(PARTICLE_MARKERS, 0.0, 0.0, a, r * a) for r in nodes])
+        _POLY["spline"] = CubicSpline(nodes, tab, axis=0)
+    return _POLY["spline"](ar)
+
+
+def initial_bonds(points: Sequence[Point]) -> np.ndarray:
+    """N_L's normalisation N0 for each point's training capillary: the number of
+    ligand sites bonded at t = 0 under the library's rule (include/lbib.h,
+    ``lbib_adhesion_params``): n_ligands sites at arc lengths (k + 1/2) P / n
+    along the particle's chain (P its polygon perimeter), a site bonded when
+    its gap to the nearer wall is below y_cr; n_ligands and y_cr as
+    ``capillary_for`` sets them.  N0 is a step function of the aspect ratio
+    and the ligand density (whole sites cross the y_cr line), which a smooth
+    network fits badly; as an input it lets the network predict N_L = N / N0
+    without learning the steps."""
+    dx = wl.H_UM / NY
+    a = 0.5 * wl.PARTICLE_LENGTH_UM / dx
+    y_cr = wl.Y_CR_UM / dx
+    ar = np.array([p.aspect_ratio for p in points], np.float64)
+    inside = (ar >= AR_RANGE[0]) & (ar <= AR_RANGE[1])
+    polys = np.zeros((len(points), PARTICLE_MARKERS, 2))
+    if inside.any():
+        polys[inside] = _particle_polygon(ar[inside])
+    for i in np.flatnonzero(~inside):  # outside the table: the exact construction
+        polys[i] = wl.ellipse(PARTICLE_MARKERS, 0.0, 0.0, a, ar[i] * a)
+    y = polys[:, :, 1] + (wl.PARTICLE_GAP_UM / dx + ar * a)[:, None]  # centre height as capillary_for places it
+    seg = np.hypot(*(np.roll(polys, -1, 1) - polys).transpose(2, 0, 1))
+    cum = np.concatenate([np.zeros((len(points), 1)), np.cumsum(seg, 1)], 1)  # [P, markers + 1]
+    dens = np.array([p.ligand_density for p in points], np.float64)
+    P = cum[:, -1]
+    n = np.maximum(4, np.rint(dens * P * dx)).astype(np.int64)
+    # Vertex 0 is the lowest point of the convex chain, so y rises from it to the top
+    # and falls back: only sites before the first vertex at or above y_cr (arc jf) or
+    # after the last one (arc jb) can be bonded.  Those candidates (with one site of
+    # margin on each side) go through the same position formula as every site.
+    high = y >= y_cr
+    jf = np.argmax(high[:, 1:], 1) + 1
+    jb = PARTICLE_MARKERS - 1 - np.argmax(high[:, ::-1], 1)
+    rows = np.arange(len(points))
+    kf = np.minimum(n, np.floor(cum[rows, jf] * n / P + 0.5).astype(np.int64) + 1)
+    kb = np.maximum(kf, np.floor(cum[rows, jb] * n / P - 0.5).astype(np.int64))
+    width = int(max(kf.max(initial=0), (n - kb).max(initial=0)))
+    j = np.arange(width)[None, :]
+    k = np.concatenate([np.broadcast_to(j, (len(points), width)), kb[:, None] + j], 1)  # forward, backward
+    valid = np.concatenate([j < kf[:, None], kb[:, None] + j < n[:, None]], 1)
+    k = np.where(valid, k, 0)
+    sk = (k + 0.5) * (P / n)[:, None]
+    # segment of each site: the first l with s <= cum[l + 1], at most markers - 1
+    l = np.minimum(np.sum(cum[:, None, 1:] < sk[:, :, None], -1), PARTICLE_MARKERS - 1)
+    c0 = np.take_along_axis(cum, l, 1)
+    c1 = np.take_along_axis(cum, l + 1, 1)
+    t = np.clip((sk - c0) / (c1 - c0), 0.0, 1.0)
+    y0 = np.take_along_axis(y, l, 1)
+    y1 = np.take_along_axis(y, (l + 1) % PARTICLE_MARKERS, 1)
+    py = y0 + t * (y1 - y0)
+    return np.count_nonzero(valid & (np.minimum(py, NY - py) < y_cr), 1).astype(np.int64)
+
+
+def features_many(points: Sequence[Point], t_star) -> np.ndarray:
+    """Feature rows [len(points) * len(t_star), len(FEATURES)], point-major."""
     t = np.atleast_1d(np.asarray(t_star, np.float64))
-    row = [p.aspect_ratio, LOGCA_RANGE[0] if p.rigid else p.log10_ca, float(p.rigid),
-           float(p.cell == "globular"), float(p.cell == "biconcave"), p.ligand_density]
-    return np.concatenate([np.tile(np.asarray(row, np.float64), (t.size, 1)), t[:, None]], 1).astype(np.float32)
+    n0 = initial_bonds(points).astype(np.float64)
+    rows = np.array([[p.aspect_ratio, LOGCA_RANGE[0] if p.rigid else p.log10_ca, float(p.rigid),
+                      float(p.cell == "globular"), float(p.cell == "biconcave"), p.ligand_density]
+                     for p in points], np.float64).reshape(len(points), 6)
+    rows = np.concatenate([rows, n0[:, None], 1.0 / np.maximum(n0, 1.0)[:, None]], 1)
+    X = np.concatenate([np.repeat(rows, t.size, 0), np.tile(t, len(points))[:, None]], 1)
+    return X.astype(np.float32)
+
+
+def features(p: Point, t_star) -> np.ndarray:
+    """Feature rows [len(t_star), len(FEATURES)] for point p at the given times."""
+    return features_many([p], t_star)
 
 
 def in_hull(p: Point, t_star_max: float) -> bool:
@@ -277,7 +384,7 @@ class Surrogate:
         Y = np.zeros((len(points), t_star.size, 3))
         idx_in = [i for i, ok in enumerate(inside) if ok]
         if idx_in:
-            X = np.concatenate([features(points[i], t_star) for i in idx_in])
+            X = features_many([points[i] for i in idx_in], t_star)
             Yn = predict_network(self.tr, X).reshape(len(idx_in), t_star.size, 3)
             for j, i in enumerate(idx_in):
                 Y[i] = Yn[j]
@@ -334,15 +441,18 @@ def plain_solver_seconds_per_step(points: Sequence[Point], steps: int = 2000, de
     return float(np.mean(out))
 
 
-def evaluate(tr: Trained, points: Sequence[Point], t_star: np.ndarray, Y: np.ndarray):
+def evaluate(tr: Trained, points: Sequence[Point], t_star: np.ndarray, Y: np.ndarray, floor=None):
     """Held-out errors of the network: per output, RMSE, mean absolute error,
     RMSE relative to the output's spread over the held-out set, and the
-    inference time of all (points x times) queries."""
+    time of all (points x times) queries: their features on the host and the
+    network on the GPU.  With ``floor`` (per output, the noise floor of the
+    targets Y, e.g. of replicate means from ``seed_statistics``) also the
+    floor and RMSE / floor."""
     import torch
 
-    X = np.concatenate([features(p, t_star) for p in points])
-    predict_network(tr, X[:65536])  # warm-up
+    predict_network(tr, features_many(points[:1], t_star))  # warm-up
     t0 = time.perf_counter()
+    X = features_many(points, t_star)
     P = predict_network(tr, X).reshape(len(points), t_star.size, 3)
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
@@ -350,9 +460,12 @@ def evaluate(tr: Trained, points: Sequence[Point], t_star: np.ndarray, Y: np.nda
     for j, name in enumerate(OUTPUTS):
         e = P[:, :, j] - Y[:, :, j]
         spread = float(Y[:, :, j].std())
-        err[name] = {"rmse": float(np.sqrt(np.mean(e * e))), "mae": float(np.mean(np.abs(e))),
-                     "rmse_over_std": float(np.sqrt(np.mean(e * e)) / spread) if spread > 0 else None,
-                     "std": spread}
+        rmse = float(np.sqrt(np.mean(e * e)))
+        err[name] = {"rmse": rmse, "mae": float(np.mean(np.abs(e))),
+                     "rmse_over_std": rmse / spread if spread > 0 else None, "std": spread}
+        if floor is not None:
+            err[name]["floor"] = float(floor[j])
+            err[name]["rmse_over_floor"] = rmse / float(floor[j]) if floor[j] > 0 else None
     return err, secs, P
 
 
@@ -364,7 +477,8 @@ def main(argv=None):
     import torch
 
     ap = argparse.ArgumentParser(description="generate solver trajectories, train the surrogate, evaluate it")
-    ap.add_argument("--points", type=int, default=2048)
+    ap.add_argument("--points", type=int, default=512)
+    ap.add_argument("--replicates", type=int, default=4, help="bond seeds per point (trajectories = points x this)")
     ap.add_argument("--holdout", type=float, default=0.1)
     ap.add_argument("--steps", type=int, default=STEPS)
     ap.add_argument("--samples", type=int, default=SAMPLES)
@@ -379,25 +493,31 @@ def main(argv=None):
     st = torch.cuda.Stream()
     torch.cuda.set_stream(st)
     pts = sample_points(args.points, seed=args.seed)
-    t_star, Y, gen_secs = generate(pts, steps=args.steps, samples=args.samples, batch=args.batch,
-                                   stream=st.cuda_stream, log=print)
-    np.savez_compressed(os.path.join(args.out, "trajectories.npz"), t_star=t_star, Y=Y,
+    runs = replicate(pts, args.replicates)
+    t_star, Yall, gen_secs = generate(runs, steps=args.steps, samples=args.samples, batch=args.batch,
+                                      stream=st.cuda_stream, log=print)
+    np.savez_compressed(os.path.join(args.out, "trajectories.npz"), t_star=t_star, Y=Yall,
                         P=np.array([[p.aspect_ratio, p.log10_ca, p.rigid, p.cell == "globular", p.ligand_density,
-                                     p.seed] for p in pts]))
+                                     p.seed] for p in runs]))
+    Y, seed_sd, floor = seed_statistics(Yall, args.replicates)
     n_hold = max(1, int(round(args.holdout * len(pts))))
     rng = np.random.default_rng(args.seed + 1)
     order = rng.permutation(len(pts))
     hold, fit = order[:n_hold], order[n_hold:]
-    X = np.concatenate([features(pts[i], t_star) for i in fit])
+    X = features_many([pts[i] for i in fit], t_star)
     T = Y[fit].reshape(-1, 3).astype(np.float32)
     t0 = time.perf_counter()
     tr = train(X, T, steps=args.train_steps, batch=args.train_batch, lr=args.lr, seed=args.seed, log=print)
     train_secs = time.perf_counter() - t0
-    err, inf_secs, P = evaluate(tr, [pts[i] for i in hold], t_star, Y[hold])
+    err, inf_secs, P = evaluate(tr, [pts[i] for i in hold], t_star, Y[hold], floor=floor)
+    # against the single held-out trajectories, whose floor is the seed-to-seed spread itself
+    Yh = Yall.reshape(len(pts), args.replicates, *Yall.shape[1:])[hold]
+    single = {name: {"rmse": float(np.sqrt(np.mean((P[:, None, :, j] - Yh[:, :, :, j]) ** 2))),
+                     "floor": float(seed_sd[j])} for j, name in enumerate(OUTPUTS)}
     # solver costs: the batched sweep that generated the data and the plain one-instance solver
     per_step_plain = plain_solver_seconds_per_step([pts[i] for i in hold[:8]])
     plain_per_traj = per_step_plain * args.steps
-    batched_per_traj = gen_secs / len(pts)
+    batched_per_traj = gen_secs / len(runs)
     surrogate_per_traj = inf_secs / len(hold)
     # fallback: a particle stiffer than the training range goes to the solver
     stiff = dataclasses.replace(pts[hold[0]], rigid=False, log10_ca=-4.5)
@@ -405,10 +525,11 @@ def main(argv=None):
     short = t_star[: max(2, args.samples // 64)]
     Yf, inside = sur.predict([pts[hold[0]], stiff], short)
     report = {
-        "points": len(pts), "holdout_points": int(n_hold), "samples_per_trajectory": int(args.samples),
+        "points": len(pts), "replicates": int(args.replicates), "trajectories": len(runs),
+        "holdout_points": int(n_hold), "samples_per_trajectory": int(args.samples),
         "steps_per_trajectory": int(args.steps), "t_star_max": float(t_star[-1]),
         "generation_gpu_seconds": gen_secs, "training_seconds": train_secs, "train_steps": args.train_steps,
-        "final_training_loss": tr.losses[-1], "holdout_errors": err,
+        "final_training_loss": tr.losses[-1], "holdout_errors": err, "holdout_single_trajectory_errors": single,
         "seconds_per_trajectory": {"plain_solver": plain_per_traj, "batched_solver": batched_per_traj,
                                    "surrogate": surrogate_per_traj},
         "sims_per_hour": {"plain_solver": 3600.0 / plain_per_traj, "batched_solver": 3600.0 / batched_per_traj,
