@@ -570,12 +570,15 @@ __device__ __forceinline__ void fz_arrive(uint64_t* bar)
 }
 
 // inputs of a tile into the slot's first K chunk: a0 = bf16(s_in (x - c_in)),
-// zero beyond n_in and beyond the last row; 32 FZ_EW epilogue threads,
-// FZ_EW / 4 per row
+// zero beyond n_in and beyond the last row; 32 FZ_EW epilogue threads, warp w
+// taking rows 8 w .. 8 w + 7 (lane % 8) and a quarter of the 64 columns
+// (lane / 8) each, so the eight lanes of a 16-byte store phase fill one
+// 128-byte row of core matrices (no bank conflicts)
 __device__ __forceinline__ void fz_prep(const FusedArgs& a, int tile, unsigned char* act, int e)
 {
-    constexpr int PARTS = FZ_EW * 32 / TC_BM, COLS = 64 / PARTS;
-    const int r = e / PARTS, part = e % PARTS, row = tile * TC_BM + r;
+    static_assert(FZ_EW * 8 == TC_BM, "one warp per 8 rows");
+    constexpr int COLS = 16;
+    const int r = (e >> 5) * 8 + (e & 7), part = (e >> 3) & 3, row = tile * TC_BM + r;
 #pragma unroll
     for (int g8 = 0; g8 < COLS / 8; ++g8) {
         const int c0 = part * COLS + g8 * 8;

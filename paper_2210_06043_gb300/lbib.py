@@ -544,37 +544,51 @@ def _add_bodies(s: Solver, cap, instance: int) -> None:
     _add_all(s, [(instance, b) for b in cap.bodies])
 
 
+# numpy images of lbib_membrane_desc and lbib_adhesion_params (same fields, same offsets),
+# so a batch's descriptors are filled as arrays rather than one ctypes object each
+_MEMBRANE_DT = np.dtype([("kind", "<i4"), ("motion", "<i4"), ("nv", "<i4"), ("reserved", "<i4"), ("xy", "<u8"),
+                         ("xy_ref", "<u8"), ("ca", "<f8"), ("beta", "<f8"), ("ka", "<f8"),
+                         ("density_ratio", "<f8")], align=True)
+_ADHESION_DT = np.dtype([("n_ligands", "<i4"), ("reserved", "<i4"), ("sigma", "<f8"), ("y_cr", "<f8"),
+                         ("y_eq", "<f8"), ("kf_dt", "<f8"), ("kr0_dt", "<f8"), ("xi", "<f8")], align=True)
+assert _MEMBRANE_DT.itemsize == ctypes.sizeof(lbib_membrane_desc)
+assert _ADHESION_DT.itemsize == ctypes.sizeof(lbib_adhesion_params)
+
+
+def _addr(a: np.ndarray) -> int:
+    return a.__array_interface__["data"][0]
+
+
 def _add_all(s: Solver, items) -> None:
     """Every (instance, workloads.Body) of `items` in one lbib_add_membranes call."""
     n = len(items)
     if n == 0:
         return
-    keep = []
-    descs = (lbib_membrane_desc * n)()
-    adh = (ctypes.POINTER(lbib_adhesion_params) * n)()
-    inst = (ctypes.c_int32 * n)()
-    for k, (i, b) in enumerate(items):
-        xy = np.ascontiguousarray(np.asarray(b.xy, dtype=np.float64).reshape(-1))
-        ref = None if b.xy_ref is None else np.ascontiguousarray(np.asarray(b.xy_ref, dtype=np.float64).reshape(-1))
+    keep, rows, adh_rows, adh_of = [], [], [], []
+    for i, b in items:
+        xy = np.ascontiguousarray(b.xy, dtype=np.float64)
+        ref = None if b.xy_ref is None else np.ascontiguousarray(b.xy_ref, dtype=np.float64)
         keep += [xy, ref]
-        descs[k] = lbib_membrane_desc(kind=int(b.kind), motion=int(b.motion), nv=len(xy) // 2, xy=_dp(xy),
-                                      xy_ref=_dp(ref) if ref is not None else None, ca=float(b.ca),
-                                      beta=float(b.beta), ka=float(b.ka), density_ratio=float(b.density_ratio))
-        inst[k] = int(i)
-        if b.adhesion is not None:
-            a = b.adhesion
-            p = lbib_adhesion_params(n_ligands=int(a.n_lig), sigma=float(a.sigma), y_cr=float(a.y_cr),
-                                     y_eq=float(a.y_eq), kf_dt=float(a.kf_dt), kr0_dt=float(a.kr0_dt),
-                                     xi=float(a.xi))
-            keep.append(p)
-            adh[k] = ctypes.pointer(p)
-    ids = (ctypes.c_int32 * n)()
-    s._c(s.lib.lbib_add_membranes(s.ctx, n, ctypes.cast(inst, _P), ctypes.cast(descs, _P), ctypes.cast(adh, _P),
-                                  ctypes.cast(ids, _P)))
+        rows.append((int(b.kind), int(b.motion), xy.size // 2, 0, _addr(xy), 0 if ref is None else _addr(ref),
+                     float(b.ca), float(b.beta), float(b.ka), float(b.density_ratio)))
+        a = b.adhesion
+        if a is None:
+            adh_of.append(-1)
+        else:
+            adh_of.append(len(adh_rows))
+            adh_rows.append((int(a.n_lig), 0, float(a.sigma), float(a.y_cr), float(a.y_eq), float(a.kf_dt),
+                             float(a.kr0_dt), float(a.xi)))
+    descs = np.array(rows, dtype=_MEMBRANE_DT)
+    adh = np.array(adh_rows, dtype=_ADHESION_DT)
+    idx = np.asarray(adh_of, np.int64)
+    adh_ptr = np.where(idx >= 0, (_addr(adh) if len(adh) else 0) + idx * _ADHESION_DT.itemsize, 0).astype(np.uint64)
+    inst = np.asarray([int(i) for i, _ in items], np.int32)
+    ids = np.zeros(n, np.int32)
+    s._c(s.lib.lbib_add_membranes(s.ctx, n, _vp(inst), _vp(descs), _vp(adh_ptr), _vp(ids)))
     for k, (i, b) in enumerate(items):
-        s.nv.append(np.asarray(b.xy).size // 2)
+        s.nv.append(rows[k][2])
         if b.adhesion is not None:
-            s.nlig[ids[k]] = int(b.adhesion.n_lig)
+            s.nlig[int(ids[k])] = int(b.adhesion.n_lig)
 
 
 def from_capillaries(caps, storage=None, device=0, stream=None, obs_capacity=0) -> Solver:
