@@ -40,13 +40,30 @@ struct GemmArgs {
     int M, N, K;              // M rows valid (ragged), N multiple of BN, K valid (ragged allowed on trans operands)
     int k_tiles_per_split;
     const float* bias;        // [N] (forward epilogues)
-    const float* Zin;         // [M][ldc] pre-activations (backward epilogue)
+    const float* Zin;         // pre-activations (backward epilogue): [M][ldc], or tiled (ztiled, see zt_index)
+    int ztiled;
+    int btiled;               // N-major B stored tiled (at_index) rather than [K][ldb]
     float* Zout;              // [M][ldc] pre-activations (forward GELU) or output (forward linear)
     __nv_bfloat16* Aout;      // [M][ldc] bf16 activations (forward GELU) or gradients (backward)
     float* part;              // [splits][M][ldc] (split-K partials)
     int ldc;
     uint32_t* status;         // error word: bit 0 set when a bounded wait gave up
 };
+
+// The fused forward pass stores pre-activations tile by tile, so that each
+// warp store is 512 contiguous bytes: for row m, column n of an N-column layer,
+// 128-row tile m / 128, 16-column block n / 16, 4-column group (n / 4) % 4,
+// then the tile's 128 rows of 4 values.
+__host__ __device__ __forceinline__ size_t zt_index(int m, int n, int N)
+{
+    return ((((size_t)(m >> 7) * (N >> 4) + (n >> 4)) * 4 + ((n >> 2) & 3)) * 128 + (m & 127)) * 4 + (n & 3);
+}
+// The activations likewise, in 16-byte groups of 8 BF16 columns: tile, 16-column
+// block, 8-column group (n / 8) % 2, then the tile's 128 rows of 8 values.
+__host__ __device__ __forceinline__ size_t at_index(int m, int n, int N)
+{
+    return ((((size_t)(m >> 7) * (N >> 4) + (n >> 4)) * 2 + ((n >> 3) & 1)) * 128 + (m & 127)) * 8 + (n & 7);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -145,10 +162,12 @@ __device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
     return r;
 }
-// GELU(v0 + b0), GELU(v1 + b1) rounded to a BF16 pair: gelu() on two lanes.
-__device__ __forceinline__ uint32_t gelu2_bf16(float v0, float v1, float b0, float b1)
+// GELU(v0 + b0), GELU(v1 + b1) rounded to a BF16 pair: gelu() on two lanes;
+// the pre-activations z = v + b in z0, z1.
+__device__ __forceinline__ uint32_t gelu2_bf16(float v0, float v1, float b0, float b1, float& z0, float& z1)
 {
     const uint64_t z = f2_add(f2(v0, v1), f2(b0, b1));
+    f2_split(z, z0, z1);
     const uint64_t u = f2_mul(z, f2_fma(f2_mul(z, z), f2(GELU_K1, GELU_K1), f2(GELU_K0, GELU_K0)));
     const uint64_t h = f2_mul(f2(0.5f, 0.5f), z);
     float u0, u1, g0, g1;
@@ -214,7 +233,9 @@ __device__ __forceinline__ void load_tiles(Tiles<TA, TB>& s, int buf, const Gemm
             const int r = ch >> 3, nc = (ch & 7) * 8;
             const int k = k0 + r;
             const bool v = k < g.K;
-            cp_async16(&s.b[buf][r][nc], g.B + (size_t)(v ? k : 0) * g.ldb + n0 + nc, v);
+            const __nv_bfloat16* src = g.btiled ? g.B + at_index(v ? k : 0, n0 + nc, g.ldb)
+                                                : g.B + (size_t)(v ? k : 0) * g.ldb + n0 + nc;
+            cp_async16(&s.b[buf][r][nc], src, v);
         }
     }
 }
@@ -293,8 +314,9 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_gemm(GemmArgs g)
                     g.Zout[o] = v0 + g.bias[n];
                     g.Zout[o + 1] = v1 + g.bias[n + 1];
                 } else if (EPI == EPI_BWD_GELU) {
-                    g.Aout[o] = __float2bfloat16_rn(v0 * gelu_d(g.Zin[o]));
-                    g.Aout[o + 1] = __float2bfloat16_rn(v1 * gelu_d(g.Zin[o + 1]));
+                    const float* zp = g.ztiled ? g.Zin + zt_index(m, n, g.ldc) : g.Zin + o;  // n even: both in one group
+                    g.Aout[o] = __float2bfloat16_rn(v0 * gelu_d(zp[0]));
+                    g.Aout[o + 1] = __float2bfloat16_rn(v1 * gelu_d(zp[1]));
                 } else {
                     float* pp = g.part + (size_t)blockIdx.z * g.M * g.ldc;
                     pp[o] = v0;
@@ -515,18 +537,38 @@ static_assert(FZ_SMEM <= 227 * 1024, "fused kernel shared memory");
 // Epilogue of one hidden layer for 16 accumulator columns cb .. cb + 15 of
 // one tile row: bias, GELU, BF16, written as the next layer's A operand
 // (K-major core matrices: 64-column chunks of 16 KB, 8-row groups of 1 KB,
-// 8-column blocks of 128 B, one 16-byte row per block).
-__device__ __forceinline__ void fz_gelu16(const uint32_t (&v)[16], const float4 (&b)[4], int cb, unsigned char* arow)
+// 8-column blocks of 128 B, one 16-byte row per block).  For a training
+// forward pass (zg, ag non-null: the entries of this row and column cb in the
+// tiled layouts of zt_index and at_index) the pre-activations (FP32) and
+// activations (BF16) also go to global memory, each warp store 512 contiguous
+// bytes.
+__device__ __forceinline__ void fz_gelu16(const uint32_t (&v)[16], const float4 (&b)[4], int cb, unsigned char* arow,
+                                          float* zg, __nv_bfloat16* ag)
 {
     uint32_t pk[8];
+    float z[16];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        pk[2 * i] = gelu2_bf16(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1]), b[i].x, b[i].y);
-        pk[2 * i + 1] = gelu2_bf16(__uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3]), b[i].z, b[i].w);
+        pk[2 * i] = gelu2_bf16(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1]), b[i].x, b[i].y, z[4 * i],
+                               z[4 * i + 1]);
+        pk[2 * i + 1] = gelu2_bf16(__uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3]), b[i].z, b[i].w,
+                                   z[4 * i + 2], z[4 * i + 3]);
     }
     unsigned char* dst = arow + (cb >> 6) * 16384 + ((cb & 63) >> 3) * 128;
     *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     *reinterpret_cast<uint4*>(dst + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    if (zg) {
+        // zg: the row's entry of column cb's 16-column block, tiled (zt_index): the
+        // four 4-column groups are 128 rows of 16 bytes apart
+        float4* zd = reinterpret_cast<float4*>(zg);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) zd[i * 128] = make_float4(z[4 * i], z[4 * i + 1], z[4 * i + 2], z[4 * i + 3]);
+        // ag: the row's entry of column cb, tiled (at_index): the second 8-column group
+        // is 128 rows of 16 bytes further
+        uint4* ad = reinterpret_cast<uint4*>(ag);
+        ad[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        ad[128] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    }
 }
 __device__ __forceinline__ void ld_bias16(float4 (&b)[4], const float4* p)
 {
@@ -544,6 +586,12 @@ struct FusedArgs {
     long long woff[FZ_MAXL];   // byte offset of layer l's first chunk in w
     const float *cin, *sin, *cout, *sout;
     uint32_t* status;
+    // a training forward pass (zout non-null): layer l's pre-activations and
+    // activations to zout[l], aout[l] ([M][N_l]), the output layer's raw values
+    // y_raw = W a + b to y ([M][N_{L-1}]) instead of the scaled outputs
+    float* zout[FZ_MAXL];
+    __nv_bfloat16* aout[FZ_MAXL];
+    int train;
 };
 
 __device__ __forceinline__ bool fz_wait(uint64_t* bar, uint32_t parity, volatile uint32_t* abort_flag,
@@ -743,13 +791,16 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
                         const int N = a.N[l], cbeg = cg * (N / NCG), cend = cbeg + N / NCG;
                         const float4* bias4 = reinterpret_cast<const float4*>(a.bias + a.boff[l]);
                         unsigned char* arow = act[sl] + (r >> 3) * 1024 + (r & 7) * 16;
+                        const int grow = tile * TC_BM + r;
+                        const bool st = a.train && grow < a.M;
                         for (int cb = cbeg; cb < cend; cb += 16) {
                             uint32_t v[16];
                             float4 b[4];
                             tmem_ld16(trow + (uint32_t)cb, v);
                             ld_bias16(b, bias4 + (cb >> 2));
                             tmem_wait(v);
-                            fz_gelu16(v, b, cb, arow);
+                            fz_gelu16(v, b, cb, arow, st ? a.zout[l] + zt_index(grow, cb, N) : nullptr,
+                                      st ? a.aout[l] + at_index(grow, cb, N) : nullptr);
                         }
                     } else {
                         const float* bias = a.bias + a.boff[l];
@@ -759,7 +810,13 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
                             uint32_t v[16];
                             tmem_ld16(trow + (uint32_t)cb, v);
                             tmem_wait(v);
-                            if (row < a.M)
+                            if (row < a.M && a.train) {
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) {
+                                    const int col = cb + j;
+                                    if (col < a.n_out) a.y[(size_t)row * a.N[l] + col] = __uint_as_float(v[j]) + bias[col];
+                                }
+                            } else if (row < a.M) {
 #pragma unroll
                                 for (int j = 0; j < 16; ++j) {
                                     const int col = cb + j;
@@ -767,6 +824,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
                                         a.y[(size_t)row * a.n_out + col] =
                                             a.sout[col] * (__uint_as_float(v[j]) + bias[col]) + a.cout[col];
                                 }
+                            }
                         }
                         // the slot's next tile: the MMAs of this one have all completed
                         if (k + 2 < nk) fz_prep(a, tile_of(k + 2), act[sl], e);
@@ -850,31 +908,73 @@ __global__ void k_sum_partials(const float* __restrict__ partial, int n, float d
     if (threadIdx.x == 0) *out = red[0] / div;
 }
 
-// bias gradient: per (column, batch chunk) partial sums of the bf16 gradients
-__global__ void k_bias_partial(const __nv_bfloat16* __restrict__ dZ, int ld, int batch, int rows_per_chunk,
-                               float* __restrict__ part)
+// bias gradient: partial column sums of the bf16 gradients over chunks of
+// BIAS_ROWS rows.  Block (32, 8): a warp reads 64 consecutive columns of a row
+// as bf16 pairs (coalesced); the 8 warps take every 8th row of the chunk and
+// their sums are added in warp order, so the result does not depend on timing.
+constexpr int BIAS_ROWS = 64;
+__global__ void k_bias_partial(const __nv_bfloat16* __restrict__ dZ, int ld, int batch, float* __restrict__ part)
 {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x, ch = blockIdx.y;
-    if (n >= ld) return;
-    const int b0 = ch * rows_per_chunk, b1 = min(batch, b0 + rows_per_chunk);
-    float s = 0.f;
-    for (int b = b0; b < b1; ++b) s += __bfloat162float(dZ[(size_t)b * ld + n]);
-    part[(size_t)ch * ld + n] = s;
+    __shared__ float2 red[8][32];
+    const int c = blockIdx.x * 64 + 2 * threadIdx.x, ch = blockIdx.y, w = threadIdx.y;
+    const int b0 = ch * BIAS_ROWS, b1 = min(batch, b0 + BIAS_ROWS);
+    float2 s = make_float2(0.f, 0.f);
+    if (c < ld)
+        for (int b = b0 + w; b < b1; b += 8) {
+            const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(dZ + (size_t)b * ld + c));
+            s.x += v.x;
+            s.y += v.y;
+        }
+    red[w][threadIdx.x] = s;
+    __syncthreads();
+    if (w == 0 && c < ld) {
+        float2 t = red[0][threadIdx.x];
+        for (int k = 1; k < 8; ++k) {
+            t.x += red[k][threadIdx.x].x;
+            t.y += red[k][threadIdx.x].y;
+        }
+        part[(size_t)ch * ld + c] = t.x;
+        part[(size_t)ch * ld + c + 1] = t.y;
+    }
 }
 
-// out[i] = sum over s < splits of part[s][i], in order
+// out[i] = sum over s < splits of part[s][i] in a fixed order: block (32, 8),
+// warp w adds s = w, w + 8, w + 16, ... for 32 consecutive i, then the eight
+// warp sums are added in warp order
 __global__ void k_reduce_splits(const float* __restrict__ part, int splits, size_t count, float* __restrict__ out)
 {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
+    __shared__ float red[8][32];
+    const size_t i = (size_t)blockIdx.x * 32 + threadIdx.x;
+    const int w = threadIdx.y;
     float s = 0.f;
-    for (int k = 0; k < splits; ++k) s += part[(size_t)k * count + i];
-    out[i] = s;
+    if (i < count)
+        for (int k = w; k < splits; k += 8) s += part[(size_t)k * count + i];
+    red[w][threadIdx.x] = s;
+    __syncthreads();
+    if (w == 0 && i < count) {
+        float t = red[0][threadIdx.x];
+        for (int k = 1; k < 8; ++k) t += red[k][threadIdx.x];
+        out[i] = t;
+    }
 }
+cudaError_t reduce_splits(const float* part, int splits, size_t count, float* out, cudaStream_t s)
+{
+    k_reduce_splits<<<(unsigned)((count + 31) / 32), dim3(32, 8), 0, s>>>(part, splits, count, out);
+    return cudaGetLastError();
+}
+
+// where the weights of each layer sit in the flat parameters and in the fused
+// kernel's packed chunks (pw null: no packed copy to refresh)
+struct PackTab {
+    unsigned char* pw;
+    int L;
+    int in[FZ_MAXL], out[FZ_MAXL];
+    long long woff[FZ_MAXL], pwoff[FZ_MAXL];
+};
 
 // Adam (bias-corrected) on the FP32 masters; refreshes the BF16 copies
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ gr, float* __restrict__ m, float* __restrict__ v,
-                       __nv_bfloat16* __restrict__ pb, size_t n, float lr, float c1, float c2)
+                       __nv_bfloat16* __restrict__ pb, size_t n, float lr, float c1, float c2, PackTab pk)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -885,7 +985,20 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ gr, floa
     const float upd = lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
     const float pn = p[i] - upd;
     p[i] = pn;
-    pb[i] = __float2bfloat16_rn(pn);
+    const __nv_bfloat16 q = __float2bfloat16_rn(pn);
+    pb[i] = q;
+    // the same value into the fused kernel's packed weight chunks (layout of k_pack_fused)
+    if (pk.pw)
+        for (int l = 0; l < pk.L; ++l) {
+            const long long j = (long long)i - pk.woff[l];
+            if (j >= 0 && j < (long long)pk.out[l] * pk.in[l]) {
+                const int nn = (int)(j / pk.in[l]), k = (int)(j % pk.in[l]);
+                const size_t o = (size_t)(k >> 6) * pk.out[l] * 128 + (nn >> 3) * 1024 + ((k & 63) >> 3) * 128 +
+                                 (nn & 7) * 16 + (k & 7) * 2;
+                *reinterpret_cast<__nv_bfloat16*>(pk.pw + pk.pwoff[l] + o) = q;
+                break;
+            }
+        }
 }
 
 // y = s_out y_raw + c_out over the first n_out columns
@@ -967,6 +1080,7 @@ struct lbib_mlp {
     unsigned char* pw = nullptr;
     long long pwoff[FZ_MAXL] = {};
     bool pw_dirty = true;
+    bool z_tiled = false;  // pre-activations stored tiled (zt_index) by the last forward pass
     bool fused = false;                     // network shape fits the fused kernel
     int nsm = 148;
     std::vector<void*> allocs;
@@ -1059,7 +1173,7 @@ cudaError_t forward_core(lbib_mlp* net, int batch, bool store_z = true)
 
 // inference through k_mlp_fused: weight chunks re-packed after an update,
 // one persistent CTA per SM (at most one per 128-row tile)
-cudaError_t forward_fused(lbib_mlp* net, const float* x, int batch, float* y)
+cudaError_t forward_fused(lbib_mlp* net, const float* x, int batch, float* y, bool train = false)
 {
     if (net->pw_dirty) {
         for (int l = 0; l < net->L; ++l) {
@@ -1091,6 +1205,12 @@ cudaError_t forward_fused(lbib_mlp* net, const float* x, int batch, float* y)
     a.cout = net->cout;
     a.sout = net->sout;
     a.status = net->status;
+    a.train = train ? 1 : 0;
+    if (train)
+        for (int l = 0; l + 1 < net->L; ++l) {
+            a.zout[l] = net->z[l];
+            a.aout[l] = net->act[l];
+        }
     const int ntiles = (batch + TC_BM - 1) / TC_BM;
     k_mlp_fused<<<std::min(ntiles, net->nsm), FZ_THREADS, FZ_SMEM, net->stream>>>(a);
     return cudaGetLastError();
@@ -1121,6 +1241,7 @@ cudaError_t backward_core(lbib_mlp* net, int batch)
         gw.M = net->out[l];
         gw.N = net->in[l];
         gw.K = batch;
+        gw.btiled = (l > 0 && net->z_tiled) ? 1 : 0;  // the fused forward pass tiles the activations
         gw.part = net->part;
         gw.ldc = net->in[l];
         e = gemm<true, true, EPI_PARTIAL>(gw, splits, net->stream);
@@ -1130,16 +1251,16 @@ cudaError_t backward_core(lbib_mlp* net, int batch)
             const int tps = (kt + std::min(splits, kt) - 1) / std::min(splits, kt);
             const int used = (kt + tps - 1) / tps;
             const size_t cnt = (size_t)net->out[l] * net->in[l];
-            k_reduce_splits<<<(unsigned)((cnt + 255) / 256), 256, 0, net->stream>>>(net->part, used, cnt,
-                                                                                     net->g + net->woff[l]);
+            e = reduce_splits(net->part, used, cnt, net->g + net->woff[l], net->stream);
+            if (e != cudaSuccess) break;
         }
         // db_l = column sums of dcur
         {
-            const int rows = 256, chunks = (batch + rows - 1) / rows;
+            const int chunks = (batch + BIAS_ROWS - 1) / BIAS_ROWS;
             dim3 grid((ldd + 63) / 64, chunks);
-            k_bias_partial<<<grid, 64, 0, net->stream>>>(dcur, ldd, batch, rows, net->part);
-            k_reduce_splits<<<(ldd + 255) / 256, 256, 0, net->stream>>>(net->part, chunks, (size_t)ldd,
-                                                                       net->g + net->boff[l]);
+            k_bias_partial<<<grid, dim3(32, 8), 0, net->stream>>>(dcur, ldd, batch, net->part);
+            e = reduce_splits(net->part, chunks, (size_t)ldd, net->g + net->boff[l], net->stream);
+            if (e != cudaSuccess) break;
         }
         e = cudaGetLastError();
         if (l == 0 || e != cudaSuccess) break;
@@ -1154,6 +1275,7 @@ cudaError_t backward_core(lbib_mlp* net, int batch)
         gx.N = net->in[l];
         gx.K = net->out[l];
         gx.Zin = net->z[l - 1];
+        gx.ztiled = net->z_tiled ? 1 : 0;
         gx.Aout = dnext;
         gx.ldc = net->in[l];
         e = gemm<false, true, EPI_BWD_GELU>(gx, 1, net->stream);
@@ -1163,13 +1285,32 @@ cudaError_t backward_core(lbib_mlp* net, int batch)
     return e;
 }
 
+// the packed weight chunks of the fused kernel, for the optimiser to keep
+// current (null when there are none, or when they are stale anyway)
+PackTab pack_tab(const lbib_mlp* net)
+{
+    PackTab t{};
+    t.pw = (net->fused && !net->pw_dirty) ? net->pw : nullptr;
+    t.L = net->L;
+    for (int l = 0; l < net->L; ++l) {
+        t.in[l] = net->in[l];
+        t.out[l] = net->out[l];
+        t.woff[l] = (long long)net->woff[l];
+        t.pwoff[l] = net->pwoff[l];
+    }
+    return t;
+}
+
 cudaError_t prep_and_loss(lbib_mlp* net, const float* x, const float* t, int batch)
 {
     dim3 blk(64, 4);
     k_prep_input<<<(batch + blk.y - 1) / blk.y, blk, 0, net->stream>>>(x, batch, net->desc.n_in, net->in[0], net->cin,
                                                                        net->sin, net->a0);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = forward_core(net, batch);
+    // the forward pass keeps every layer's pre-activations and activations for
+    // the backward pass: the fused kernel where the shape allows it
+    net->z_tiled = net->fused;  // the fused kernel stores the pre-activations tiled (zt_index)
+    if (e == cudaSuccess) e = net->fused ? forward_fused(net, x, batch, net->yraw, true) : forward_core(net, batch);
     if (e != cudaSuccess) return e;
     const int ldy = net->out[net->L - 1];
     dim3 lb(64, 4);
@@ -1262,8 +1403,8 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
     for (int l = 0; l + 1 < net->L; ++l) {
         __nv_bfloat16* a = nullptr;
         float* z = nullptr;
-        MA(a, B * d->width);
-        MA(z, B * d->width);
+        MA(a, (B + TC_BM - 1) / TC_BM * TC_BM * d->width);  // whole 128-row tiles (the tiled layouts)
+        MA(z, (B + TC_BM - 1) / TC_BM * TC_BM * d->width);
         net->act.push_back(a);
         net->z.push_back(z);
     }
@@ -1272,7 +1413,7 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
     MA(net->dZa, B * d->width);
     MA(net->dZb, B * d->width);
     const size_t wmax = (size_t)d->width * d->width;
-    const int chunks = (int)((B + 255) / 256);
+    const int chunks = (int)((B + BIAS_ROWS - 1) / BIAS_ROWS);  // bias-gradient partials
     net->part_floats = std::max((size_t)MAX_SPLITS * wmax, (size_t)chunks * d->width);
     MA(net->part, net->part_floats);
     MA(net->loss_part, (B + 3) / 4);
@@ -1407,10 +1548,10 @@ lbib_status lbib_mlp_train_step(lbib_mlp* net, const float* x, const float* t, i
         net->t += 1;
         const float c1 = 1.0f - (float)std::pow(0.9, (double)net->t);
         const float c2 = 1.0f - (float)std::pow(0.999, (double)net->t);
+        // a packed copy that is current stays current: the update writes it too
         k_adam<<<(unsigned)((net->nparam + 255) / 256), 256, 0, net->stream>>>(net->p, net->g, net->m, net->v, net->pb,
-                                                                               net->nparam, lr, c1, c2);
+                                                                               net->nparam, lr, c1, c2, pack_tab(net));
         e = cudaGetLastError();
-        net->pw_dirty = true;
     }
     if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, net->loss_dev, 4, cudaMemcpyDeviceToDevice, net->stream);
     if (e != cudaSuccess) return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_train_step: ") + cudaGetErrorString(e));
@@ -1455,10 +1596,10 @@ lbib_status lbib_mlp_apply_gradient(lbib_mlp* net, const float* grad, size_t n, 
         net->t += 1;
         const float c1 = 1.0f - (float)std::pow(0.9, (double)net->t);
         const float c2 = 1.0f - (float)std::pow(0.999, (double)net->t);
+        // a packed copy that is current stays current: the update writes it too
         k_adam<<<(unsigned)((net->nparam + 255) / 256), 256, 0, net->stream>>>(net->p, net->g, net->m, net->v, net->pb,
-                                                                               net->nparam, lr, c1, c2);
+                                                                               net->nparam, lr, c1, c2, pack_tab(net));
         e = cudaGetLastError();
-        net->pw_dirty = true;
     }
     if (e != cudaSuccess)
         return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_apply_gradient: ") + cudaGetErrorString(e));
