@@ -40,9 +40,7 @@ struct GemmArgs {
     int M, N, K;              // M rows valid (ragged), N multiple of BN, K valid (ragged allowed on trans operands)
     int k_tiles_per_split;
     const float* bias;        // [N] (forward epilogues)
-    const float* Zin;         // pre-activations (backward epilogue): [M][ldc], or tiled (ztiled, see zt_index)
-    int ztiled;
-    int btiled;               // N-major B stored tiled (at_index) rather than [K][ldb]
+    const float* Zin;         // [M][ldc] pre-activations (backward epilogue)
     float* Zout;              // [M][ldc] pre-activations (forward GELU) or output (forward linear)
     __nv_bfloat16* Aout;      // [M][ldc] bf16 activations (forward GELU) or gradients (backward)
     float* part;              // [splits][M][ldc] (split-K partials)
@@ -58,11 +56,13 @@ __host__ __device__ __forceinline__ size_t zt_index(int m, int n, int N)
 {
     return ((((size_t)(m >> 7) * (N >> 4) + (n >> 4)) * 4 + ((n >> 2) & 3)) * 128 + (m & 127)) * 4 + (n & 3);
 }
-// The activations likewise, in 16-byte groups of 8 BF16 columns: tile, 16-column
-// block, 8-column group (n / 8) % 2, then the tile's 128 rows of 8 values.
+// The activations (and their gradients) likewise, in 16-byte groups of 8 BF16
+// columns over 64-row blocks: block m / 64, 16-column block, 8-column group
+// (n / 8) % 2, then the block's 64 rows of 8 values.  A 64-row block of every
+// column is one contiguous range (N * 128 bytes).
 __host__ __device__ __forceinline__ size_t at_index(int m, int n, int N)
 {
-    return ((((size_t)(m >> 7) * (N >> 4) + (n >> 4)) * 2 + ((n >> 3) & 1)) * 128 + (m & 127)) * 8 + (n & 7);
+    return ((((size_t)(m >> 6) * (N >> 4) + (n >> 4)) * 2 + ((n >> 3) & 1)) * 64 + (m & 63)) * 8 + (n & 7);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -233,9 +233,7 @@ __device__ __forceinline__ void load_tiles(Tiles<TA, TB>& s, int buf, const Gemm
             const int r = ch >> 3, nc = (ch & 7) * 8;
             const int k = k0 + r;
             const bool v = k < g.K;
-            const __nv_bfloat16* src = g.btiled ? g.B + at_index(v ? k : 0, n0 + nc, g.ldb)
-                                                : g.B + (size_t)(v ? k : 0) * g.ldb + n0 + nc;
-            cp_async16(&s.b[buf][r][nc], src, v);
+            cp_async16(&s.b[buf][r][nc], g.B + (size_t)(v ? k : 0) * g.ldb + n0 + nc, v);
         }
     }
 }
@@ -314,9 +312,8 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_gemm(GemmArgs g)
                     g.Zout[o] = v0 + g.bias[n];
                     g.Zout[o + 1] = v1 + g.bias[n + 1];
                 } else if (EPI == EPI_BWD_GELU) {
-                    const float* zp = g.ztiled ? g.Zin + zt_index(m, n, g.ldc) : g.Zin + o;  // n even: both in one group
-                    g.Aout[o] = __float2bfloat16_rn(v0 * gelu_d(zp[0]));
-                    g.Aout[o + 1] = __float2bfloat16_rn(v1 * gelu_d(zp[1]));
+                    g.Aout[o] = __float2bfloat16_rn(v0 * gelu_d(g.Zin[o]));
+                    g.Aout[o + 1] = __float2bfloat16_rn(v1 * gelu_d(g.Zin[o + 1]));
                 } else {
                     float* pp = g.part + (size_t)blockIdx.z * g.M * g.ldc;
                     pp[o] = v0;
@@ -563,11 +560,13 @@ __device__ __forceinline__ void fz_gelu16(const uint32_t (&v)[16], const float4 
         float4* zd = reinterpret_cast<float4*>(zg);
 #pragma unroll
         for (int i = 0; i < 4; ++i) zd[i * 128] = make_float4(z[4 * i], z[4 * i + 1], z[4 * i + 2], z[4 * i + 3]);
+    }
+    if (ag) {
         // ag: the row's entry of column cb, tiled (at_index): the second 8-column group
-        // is 128 rows of 16 bytes further
+        // is 64 rows of 16 bytes further; zero for a row past the batch (zg null)
         uint4* ad = reinterpret_cast<uint4*>(ag);
-        ad[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        ad[128] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        ad[0] = zg ? make_uint4(pk[0], pk[1], pk[2], pk[3]) : make_uint4(0u, 0u, 0u, 0u);
+        ad[64] = zg ? make_uint4(pk[4], pk[5], pk[6], pk[7]) : make_uint4(0u, 0u, 0u, 0u);
     }
 }
 __device__ __forceinline__ void ld_bias16(float4 (&b)[4], const float4* p)
@@ -586,12 +585,16 @@ struct FusedArgs {
     long long woff[FZ_MAXL];   // byte offset of layer l's first chunk in w
     const float *cin, *sin, *cout, *sout;
     uint32_t* status;
-    // a training forward pass (zout non-null): layer l's pre-activations and
-    // activations to zout[l], aout[l] ([M][N_l]), the output layer's raw values
-    // y_raw = W a + b to y ([M][N_{L-1}]) instead of the scaled outputs
+    // a training forward pass (train): layer l's pre-activations and
+    // activations to zout[l], aout[l] (tiled: zt_index, at_index), the output
+    // layer's raw values y_raw = W a + b to y ([M][N_{L-1}]) instead of the
+    // scaled outputs.  The backward chain (k_mlp_fused<true>): step s reads the
+    // pre-activations zout[s] of its output width N[s] and writes the gradient
+    // aout[s] = bf16(acc * GELU'(z)) (tiled), starting from dy ([M][K[0]] BF16).
     float* zout[FZ_MAXL];
     __nv_bfloat16* aout[FZ_MAXL];
     int train;
+    const __nv_bfloat16* dy;
 };
 
 __device__ __forceinline__ bool fz_wait(uint64_t* bar, uint32_t parity, volatile uint32_t* abort_flag,
@@ -622,31 +625,86 @@ __device__ __forceinline__ void fz_arrive(uint64_t* bar)
 // taking rows 8 w .. 8 w + 7 (lane % 8) and a quarter of the 64 columns
 // (lane / 8) each, so the eight lanes of a 16-byte store phase fill one
 // 128-byte row of core matrices (no bank conflicts)
+template <bool BWD>
 __device__ __forceinline__ void fz_prep(const FusedArgs& a, int tile, unsigned char* act, int e)
 {
     static_assert(FZ_EW * 8 == TC_BM, "one warp per 8 rows");
     constexpr int COLS = 16;
     const int r = (e >> 5) * 8 + (e & 7), part = (e >> 3) & 3, row = tile * TC_BM + r;
+    if (BWD) {
+        // the output gradient rows (BF16, K[0] = 64 columns, tiled: at_index)
 #pragma unroll
-    for (int g8 = 0; g8 < COLS / 8; ++g8) {
-        const int c0 = part * COLS + g8 * 8;
-        uint32_t pk[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            float v[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int j = c0 + 2 * i + h;
-                v[h] = (row < a.M && j < a.n_in) ? a.sin[j] * (a.x[(size_t)row * a.n_in + j] - a.cin[j]) : 0.f;
-            }
-            const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[0], v[1]);
-            pk[i] = *reinterpret_cast<const uint32_t*>(&b2);
+        for (int g8 = 0; g8 < COLS / 8; ++g8) {
+            const int c0 = part * COLS + g8 * 8;
+            const uint4 v = (row < a.M) ? __ldg(reinterpret_cast<const uint4*>(a.dy + at_index(row, c0, a.K[0])))
+                                        : make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(act + (r >> 3) * 1024 + (c0 >> 3) * 128 + (r & 7) * 16) = v;
         }
-        *reinterpret_cast<uint4*>(act + (r >> 3) * 1024 + (c0 >> 3) * 128 + (r & 7) * 16) =
-            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    } else {
+#pragma unroll
+        for (int g8 = 0; g8 < COLS / 8; ++g8) {
+            const int c0 = part * COLS + g8 * 8;
+            uint32_t pk[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float v[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = c0 + 2 * i + h;
+                    v[h] = (row < a.M && j < a.n_in) ? a.sin[j] * (a.x[(size_t)row * a.n_in + j] - a.cin[j]) : 0.f;
+                }
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[0], v[1]);
+                pk[i] = *reinterpret_cast<const uint32_t*>(&b2);
+            }
+            *reinterpret_cast<uint4*>(act + (r >> 3) * 1024 + (c0 >> 3) * 128 + (r & 7) * 16) =
+                make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
     }
 }
 
+// Epilogue of a backward step for one tile row (its columns of group cg):
+// the accumulator (gradient before the activation) times GELU'(z), z the
+// forward pass's pre-activations, rounded to BF16; written as the next step's
+// A operand (except after the last step) and to the step's gradient output.
+__device__ __forceinline__ void fz_bwd_step(const FusedArgs& a, int l, int tile, uint32_t trow, unsigned char* arow,
+                                            int r, int cg)
+{
+    constexpr int NCG = FZ_EW / 4;
+    const int N = a.N[l], cbeg = cg * (N / NCG), cend = cbeg + N / NCG;
+    const bool last = (l + 1 == a.L);
+    const int grow = tile * TC_BM + r;
+    const bool st = grow < a.M;
+    for (int cb = cbeg; cb < cend; cb += 16) {
+        uint32_t v[16];
+        tmem_ld16(trow + (uint32_t)cb, v);
+        float4 z[4];
+        const float4* zp = reinterpret_cast<const float4*>(a.zout[l] + zt_index(st ? grow : 0, cb, N));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) z[i] = st ? __ldg(zp + i * 128) : make_float4(0.f, 0.f, 0.f, 0.f);
+        tmem_wait(v);
+        uint32_t pk[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __nv_bfloat162 p0 = __floats2bfloat162_rn(__uint_as_float(v[4 * i]) * gelu_d(z[i].x),
+                                                            __uint_as_float(v[4 * i + 1]) * gelu_d(z[i].y));
+            const __nv_bfloat162 p1 = __floats2bfloat162_rn(__uint_as_float(v[4 * i + 2]) * gelu_d(z[i].z),
+                                                            __uint_as_float(v[4 * i + 3]) * gelu_d(z[i].w));
+            pk[2 * i] = *reinterpret_cast<const uint32_t*>(&p0);
+            pk[2 * i + 1] = *reinterpret_cast<const uint32_t*>(&p1);
+        }
+        if (!last) {
+            unsigned char* dst = arow + (cb >> 6) * 16384 + ((cb & 63) >> 3) * 128;
+            *reinterpret_cast<uint4*>(dst) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            *reinterpret_cast<uint4*>(dst + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+        // (a row past the batch is written as zeros: the tiles are read whole)
+        uint4* ad = reinterpret_cast<uint4*>(a.aout[l] + at_index(grow, cb, N));
+        ad[0] = st ? make_uint4(pk[0], pk[1], pk[2], pk[3]) : make_uint4(0u, 0u, 0u, 0u);
+        ad[64] = st ? make_uint4(pk[4], pk[5], pk[6], pk[7]) : make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+template <bool BWD>
 __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
 {
     extern __shared__ __align__(1024) unsigned char fz[];
@@ -769,7 +827,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
         constexpr int NCG = FZ_EW / 4;  // column groups per tile row
         const int e = tid - 128, q4 = warp & 3, cg = (warp - 4) >> 2, r = q4 * 32 + lane;
         for (int sl = 0; sl < 2 && sl < nk; ++sl) {
-            fz_prep(a, tile_of(sl), act[sl], e);
+            fz_prep<BWD>(a, tile_of(sl), act[sl], e);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             fz_arrive(&epid[sl]);
         }
@@ -786,7 +844,12 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const int tile = tile_of(k);
                     const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(sl * 256);
-                    if (l + 1 < a.L) {
+                    if (BWD) {
+                        fz_bwd_step(a, l, tile, trow, act[sl] + (r >> 3) * 1024 + (r & 7) * 16, r, cg);
+                        // the slot's next tile once its last step is done (that step wrote
+                        // nothing to the slot's shared memory)
+                        if (l + 1 == a.L && k + 2 < nk) fz_prep<BWD>(a, tile_of(k + 2), act[sl], e);
+                    } else if (l + 1 < a.L) {
                         // N is a multiple of 64: each column group is whole 16-column blocks
                         const int N = a.N[l], cbeg = cg * (N / NCG), cend = cbeg + N / NCG;
                         const float4* bias4 = reinterpret_cast<const float4*>(a.bias + a.boff[l]);
@@ -800,7 +863,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
                             ld_bias16(b, bias4 + (cb >> 2));
                             tmem_wait(v);
                             fz_gelu16(v, b, cb, arow, st ? a.zout[l] + zt_index(grow, cb, N) : nullptr,
-                                      st ? a.aout[l] + at_index(grow, cb, N) : nullptr);
+                                      a.train ? a.aout[l] + at_index(grow, cb, N) : nullptr);
                         }
                     } else {
                         const float* bias = a.bias + a.boff[l];
@@ -827,7 +890,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
                             }
                         }
                         // the slot's next tile: the MMAs of this one have all completed
-                        if (k + 2 < nk) fz_prep(a, tile_of(k + 2), act[sl], e);
+                        if (k + 2 < nk) fz_prep<BWD>(a, tile_of(k + 2), act[sl], e);
                     }
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -840,39 +903,233 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
+// ------------------------------------------- weight gradients on tcgen05
+// dW = dZ^T A over a slice of the batch: M = out (64 or 256), N = in (64 or
+// 256), K = batch rows.  Both operands come from the tiled layout (at_index),
+// which holds, per 64-row block and 8-column group, 64 rows of 16 bytes, a
+// block of all columns contiguous: copied whole into shared memory (one bulk
+// copy per operand and K block) it is the MN-major no-swizzle core-matrix
+// layout (core matrix = 8 K-rows x 8 M/N elements; K-neighbours LBO = 128 B
+// apart, M/N-neighbours SBO = 1024 B apart; measured on GB300 against exact
+// small-integer products).  Each CTA streams its slice in 64-row K blocks
+// through DW_STAGES stages, multiplies with M 128 (the two halves of M 256
+// into tensor-memory columns [0, 256) and [256, 512)), N = in, K 16 per
+// instruction, and writes its FP32 partial (in the order k_reduce_splits_dw
+// reads) for a fixed-order reduction.  Rows past the batch in the last block
+// are zero in both layouts.
+// Roles: warp 0 lane 0 issues the MMAs, warp 1 streams the operands, warps
+// 4 .. 11 write the partial (warp w: lanes of quadrant w % 4, half (w - 4) / 4).
+constexpr int DW_STAGES = 6, DW_THREADS = 256, DW_KB = 64, DW_TN = 64;
+constexpr size_t DW_OPA = (size_t)TC_BM * DW_KB * 2;        // 16 KB of A (128 rows of M) per stage
+constexpr size_t DW_OPB = (size_t)DW_TN * DW_KB * 2;        // 8 KB of B (64 columns of N) per stage
+constexpr size_t DW_ST = DW_OPA + DW_OPB;
+constexpr size_t DW_BAR = (size_t)DW_STAGES * DW_ST;        // barriers after the stages
+constexpr size_t DW_SMEM = DW_BAR + 128;
+static_assert(DW_SMEM <= 227 * 1024, "weight-gradient kernel shared memory");
+
+struct DwArgs {
+    const __nv_bfloat16* dz;   // tiled, width M
+    const __nv_bfloat16* act;  // tiled, width N
+    int M, N, batch, rows_per_split;
+    float* part;               // [split][M x N] in the order k_reduce_splits_dw reads
+    uint32_t* status;
+};
+
+__device__ __forceinline__ uint32_t dw_idesc(int n)
+{
+    uint32_t d = 0;
+    d |= 1u << 4;                      // D format FP32
+    d |= 1u << 7;                      // A format BF16
+    d |= 1u << 10;                     // B format BF16
+    d |= 1u << 15;                     // A MN-major
+    d |= 1u << 16;                     // B MN-major
+    d |= (uint32_t)(n >> 3) << 17;     // N / 8
+    d |= (uint32_t)(TC_BM >> 4) << 24; // M / 16
+    return d;
+}
+__device__ __forceinline__ uint64_t dw_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);        // start address
+    d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;   // leading byte offset: next core matrix along K
+    d |= (uint64_t)((1024u >> 4) & 0x3FFF) << 32;  // stride byte offset: next 8 elements along M / N
+    d |= (uint64_t)1 << 46;                        // descriptor version (sm_100 family)
+    return d;                                      // no swizzle
+}
+
+// grid (M / 128 tiles x N / 64 tiles, splits): CTA (t, s) computes the 128 x 64
+// tile t of dW over batch rows [s rows_per_split, (s + 1) rows_per_split)
+__global__ void __launch_bounds__(DW_THREADS, 1) k_dw_tc(DwArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char dws[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(dws + DW_BAR);
+    uint64_t* full = bar;                  // [DW_STAGES]
+    uint64_t* empty = bar + DW_STAGES;     // [DW_STAGES]
+    uint64_t* accf = bar + 2 * DW_STAGES;  // the last MMA done
+    uint64_t* fin = accf + 1;              // MMAs drained on an abort
+    volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(fin + 1);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1) + 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tn = a.N / DW_TN, mt = (int)blockIdx.x / tn, nt = (int)blockIdx.x % tn;
+    const int mcols = min(TC_BM, a.M - mt * TC_BM);  // columns of M in this tile (64 or 128)
+    const int b0 = (int)blockIdx.y * a.rows_per_split, b1 = min(a.batch, b0 + a.rows_per_split);
+    const int nkb = (b1 > b0) ? (b1 - b0 + DW_KB - 1) / DW_KB : 0;
+    if (tid == 0) {
+        for (int i = 0; i < DW_STAGES; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(accf)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(fin)), "r"(1));
+        *abort_flag = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(DW_TN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+
+    if (tid == 0) {
+        // ---------------------------------------------------- MMA issuer
+        const uint32_t idesc = dw_idesc(DW_TN);
+        bool ok = true;
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+            const int st = kb % DW_STAGES;
+            ok = fz_wait(&full[st], (uint32_t)(kb / DW_STAGES) & 1u, abort_flag, a.status);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sA = smem_u32(dws + (size_t)st * DW_ST), sB = sA + (uint32_t)DW_OPA;
+#pragma unroll
+            for (int kk = 0; kk < DW_KB / 16; ++kk) {
+                const uint64_t da = dw_desc(sA + (uint32_t)(kk * 256));
+                const uint64_t db = dw_desc(sB + (uint32_t)(kk * 256));
+                const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&empty[st])));
+        }
+        if (ok)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(accf)));
+        else {
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(fin)));
+            fz_wait(fin, 0u, abort_flag, a.status, false);
+        }
+    } else if (tid == 32) {
+        // ---------------------------------------------------- operand stream
+        // a 64-row block of the tile's columns is one contiguous range of either
+        // operand (at_index): 128 (or 64) columns of M, 64 of N
+        const uint32_t ba = (uint32_t)mcols * DW_KB * 2, bb = (uint32_t)DW_OPB;
+        bool ok = true;
+        int issued = 0;
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+            const int st = kb % DW_STAGES;
+            ok = fz_wait(&empty[st], ((uint32_t)(kb / DW_STAGES) & 1u) ^ 1u, abort_flag, a.status);
+            if (!ok) break;
+            const int kr = b0 + kb * DW_KB;  // first row of the block, a multiple of 64
+            const uint32_t sA = smem_u32(dws + (size_t)st * DW_ST), sB = sA + (uint32_t)DW_OPA;
+            const uint32_t fb = smem_u32(&full[st]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(ba + bb) : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sA),
+                "l"(a.dz + at_index(kr, mt * TC_BM, a.M)), "r"(ba), "r"(fb)
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sB),
+                "l"(a.act + at_index(kr, nt * DW_TN, a.N)), "r"(bb), "r"(fb)
+                : "memory");
+            issued = kb + 1;
+        }
+        if (!ok) {
+            // copies still in flight land before the CTA leaves
+            for (int qq = (issued > DW_STAGES ? issued - DW_STAGES : 0); qq < issued; ++qq)
+                fz_wait(&full[qq % DW_STAGES], (uint32_t)(qq / DW_STAGES) & 1u, abort_flag, a.status, false);
+        }
+    } else if (warp >= 4) {
+        // ---------------------------------------------------- partial out
+        const int q4 = warp & 3, rl = q4 * 32 + lane, r = mt * TC_BM + rl;
+        bool ok = true;
+        if (nkb > 0) ok = fz_wait(accf, 0u, abort_flag, a.status);
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // the partial in k_reduce_splits_dw's order: a warp's 32 rows of 4 columns
+            // are 512 contiguous bytes
+            float4* dst = reinterpret_cast<float4*>(a.part + (size_t)blockIdx.y * a.M * a.N) +
+                          (size_t)(r >> 5) * (a.N >> 2) * 32 + (r & 31);
+            for (int cb = 0; cb < DW_TN; cb += 16) {
+                uint32_t v[16];
+                tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)cb, v);
+                tmem_wait(v);
+                if (rl < mcols)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        dst[(size_t)((nt * DW_TN + cb) / 4 + i) * 32] =
+                            nkb > 0 ? make_float4(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1]),
+                                                  __uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3]))
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(DW_TN));
+}
+
 // weights of every layer into the fused kernel's chunks: layer l, K chunk c
 // (columns 64 c .. 64 c + 63) as an N_l x 64 core-matrix image of N_l * 128
 // bytes, element (n, k) at (n / 8) * 1024 + (k % 64 / 8) * 128 + (n % 8) * 16 +
 // (k % 8) * 2 within it; one thread per element
-__global__ void k_pack_fused(const __nv_bfloat16* __restrict__ pb, size_t wsrc, int N, int K,
-                             unsigned char* __restrict__ dst)
+__device__ __forceinline__ size_t fz_chunk_offset(int n, int k, int N)
+{
+    return (size_t)(k >> 6) * N * 128 + (n >> 3) * 1024 + ((k & 63) >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+}
+// (out x in weights W: the forward pass's B has N = out, K = in; the backward
+// chain's B is the transpose, N = in, K = out, in the same layout)
+__global__ void k_pack_fused(const __nv_bfloat16* __restrict__ pb, size_t wsrc, int out, int in,
+                             unsigned char* __restrict__ dst, unsigned char* __restrict__ dstT)
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (size_t)N * K) return;
-    const int n = (int)(i / K), k = (int)(i % K);
-    const size_t o = (size_t)(k >> 6) * N * 128 + (n >> 3) * 1024 + ((k & 63) >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
-    *reinterpret_cast<__nv_bfloat16*>(dst + o) = pb[wsrc + i];
+    if (i >= (size_t)out * in) return;
+    const int o = (int)(i / in), j = (int)(i % in);
+    const __nv_bfloat16 w = pb[wsrc + i];
+    *reinterpret_cast<__nv_bfloat16*>(dst + fz_chunk_offset(o, j, out)) = w;
+    *reinterpret_cast<__nv_bfloat16*>(dstT + fz_chunk_offset(j, o, in)) = w;
 }
 
 // a0 = bf16(s_in (x - c_in)), zero beyond n_in (blockDim.x = the padded width ldo)
-__global__ void k_prep_input(const float* __restrict__ x, int batch, int n_in, int ldo, const float* __restrict__ c,
-                             const float* __restrict__ sc, __nv_bfloat16* __restrict__ a0)
+// (tiled: a0 in the at_index layout, rows up to `rows` (whole tiles), zero past the batch)
+__global__ void k_prep_input(const float* __restrict__ x, int batch, int rows, int n_in, int ldo,
+                             const float* __restrict__ c, const float* __restrict__ sc, __nv_bfloat16* __restrict__ a0,
+                             int tiled)
 {
     const int b = blockIdx.x * blockDim.y + threadIdx.y, j = threadIdx.x;
-    if (b >= batch || j >= ldo) return;
-    const float v = (j < n_in) ? sc[j] * (x[(size_t)b * n_in + j] - c[j]) : 0.f;
-    a0[(size_t)b * ldo + j] = __float2bfloat16_rn(v);
+    if (b >= rows || j >= ldo) return;
+    const float v = (b < batch && j < n_in) ? sc[j] * (x[(size_t)b * n_in + j] - c[j]) : 0.f;
+    a0[tiled ? at_index(b, j, ldo) : (size_t)b * ldo + j] = __float2bfloat16_rn(v);
 }
 
 // loss terms and output gradient: d = y_raw - (t - c_out) / s_out over the first
-// n_out columns; dY = bf16(2 d / (batch n_out)); per-block partial sums of d^2
-__global__ void k_loss_grad(const float* __restrict__ yraw, int ldy, const float* __restrict__ t, int batch, int n_out,
-                            const float* __restrict__ c, const float* __restrict__ sc, __nv_bfloat16* __restrict__ dY,
-                            float* __restrict__ partial)
+// n_out columns; dY = bf16(2 d / (batch n_out)); per-block partial sums of d^2.
+// Rows up to `rows` (zero past the batch); dY tiled (at_index) when `tiled`.
+__global__ void k_loss_grad(const float* __restrict__ yraw, int ldy, const float* __restrict__ t, int batch, int rows,
+                            int n_out, const float* __restrict__ c, const float* __restrict__ sc,
+                            __nv_bfloat16* __restrict__ dY, float* __restrict__ partial, int tiled)
 {
     __shared__ float red[256];
     const int b = blockIdx.x * blockDim.y + threadIdx.y, j = threadIdx.x;  // blockDim (64, 4)
     float d2 = 0.f;
+    if (b < rows && b >= batch) dY[tiled ? at_index(b, j, ldy) : (size_t)b * ldy + j] = __float2bfloat16_rn(0.f);
     if (b < batch) {
         float gval = 0.f;
         if (j < n_out) {
@@ -881,7 +1138,7 @@ __global__ void k_loss_grad(const float* __restrict__ yraw, int ldy, const float
             d2 = d * d;
             gval = 2.0f * d / ((float)batch * (float)n_out);
         }
-        dY[(size_t)b * ldy + j] = __float2bfloat16_rn(gval);
+        dY[tiled ? at_index(b, j, ldy) : (size_t)b * ldy + j] = __float2bfloat16_rn(gval);
     }
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     red[tid] = d2;
@@ -913,7 +1170,8 @@ __global__ void k_sum_partials(const float* __restrict__ partial, int n, float d
 // as bf16 pairs (coalesced); the 8 warps take every 8th row of the chunk and
 // their sums are added in warp order, so the result does not depend on timing.
 constexpr int BIAS_ROWS = 64;
-__global__ void k_bias_partial(const __nv_bfloat16* __restrict__ dZ, int ld, int batch, float* __restrict__ part)
+__global__ void k_bias_partial(const __nv_bfloat16* __restrict__ dZ, int ld, int batch, int tiled,
+                               float* __restrict__ part)
 {
     __shared__ float2 red[8][32];
     const int c = blockIdx.x * 64 + 2 * threadIdx.x, ch = blockIdx.y, w = threadIdx.y;
@@ -921,7 +1179,8 @@ __global__ void k_bias_partial(const __nv_bfloat16* __restrict__ dZ, int ld, int
     float2 s = make_float2(0.f, 0.f);
     if (c < ld)
         for (int b = b0 + w; b < b1; b += 8) {
-            const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(dZ + (size_t)b * ld + c));
+            const size_t o = tiled ? at_index(b, c, ld) : (size_t)b * ld + c;  // c even: the pair is adjacent
+            const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(dZ + o));
             s.x += v.x;
             s.y += v.y;
         }
@@ -957,6 +1216,30 @@ __global__ void k_reduce_splits(const float* __restrict__ part, int splits, size
         out[i] = t;
     }
 }
+// the same over partials stored in the weight-gradient kernel's order (an M x N
+// block as 32-row groups of 4-column groups, 32 rows x 4 values each): entry j
+// of a partial is element (m, n) of out, m = (j / (128 N/4)) * 32 + (j / 4) % 32,
+// n = ((j / 128) % (N / 4)) * 4 + j % 4; read in partial order, written to [M][N]
+__global__ void k_reduce_splits_dw(const float* __restrict__ part, int splits, int N, size_t count,
+                                   float* __restrict__ out)
+{
+    __shared__ float red[8][32];
+    const size_t j = (size_t)blockIdx.x * 32 + threadIdx.x;
+    const int w = threadIdx.y;
+    float s = 0.f;
+    if (j < count)
+        for (int k = w; k < splits; k += 8) s += part[(size_t)k * count + j];
+    red[w][threadIdx.x] = s;
+    __syncthreads();
+    if (w == 0 && j < count) {
+        float t = red[0][threadIdx.x];
+        for (int k = 1; k < 8; ++k) t += red[k][threadIdx.x];
+        const size_t grp = j / 128;  // (32-row group, 4-column group)
+        const int m = (int)(grp / (N / 4)) * 32 + (int)((j / 4) % 32), n = (int)(grp % (N / 4)) * 4 + (int)(j % 4);
+        out[(size_t)m * N + n] = t;
+    }
+}
+
 cudaError_t reduce_splits(const float* part, int splits, size_t count, float* out, cudaStream_t s)
 {
     k_reduce_splits<<<(unsigned)((count + 31) / 32), dim3(32, 8), 0, s>>>(part, splits, count, out);
@@ -966,7 +1249,7 @@ cudaError_t reduce_splits(const float* part, int splits, size_t count, float* ou
 // where the weights of each layer sit in the flat parameters and in the fused
 // kernel's packed chunks (pw null: no packed copy to refresh)
 struct PackTab {
-    unsigned char* pw;
+    unsigned char *pw, *pwT;  // forward chunks and the transposed (backward) ones, same offsets
     int L;
     int in[FZ_MAXL], out[FZ_MAXL];
     long long woff[FZ_MAXL], pwoff[FZ_MAXL];
@@ -993,9 +1276,8 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ gr, floa
             const long long j = (long long)i - pk.woff[l];
             if (j >= 0 && j < (long long)pk.out[l] * pk.in[l]) {
                 const int nn = (int)(j / pk.in[l]), k = (int)(j % pk.in[l]);
-                const size_t o = (size_t)(k >> 6) * pk.out[l] * 128 + (nn >> 3) * 1024 + ((k & 63) >> 3) * 128 +
-                                 (nn & 7) * 16 + (k & 7) * 2;
-                *reinterpret_cast<__nv_bfloat16*>(pk.pw + pk.pwoff[l] + o) = q;
+                *reinterpret_cast<__nv_bfloat16*>(pk.pw + pk.pwoff[l] + fz_chunk_offset(nn, k, pk.out[l])) = q;
+                *reinterpret_cast<__nv_bfloat16*>(pk.pwT + pk.pwoff[l] + fz_chunk_offset(k, nn, pk.in[l])) = q;
                 break;
             }
         }
@@ -1078,7 +1360,9 @@ struct lbib_mlp {
     bool tc = true;                         // forward products on tcgen05
     // fused inference (k_mlp_fused): packed weight chunks, refreshed after every update
     unsigned char* pw = nullptr;
+    unsigned char* pwT = nullptr;           // transposed chunks (backward chain), offsets pwoff
     long long pwoff[FZ_MAXL] = {};
+    std::vector<__nv_bfloat16*> dzs;        // dZ_l of the hidden layers (tiled), fused backward
     bool pw_dirty = true;
     bool z_tiled = false;  // pre-activations stored tiled (zt_index) by the last forward pass
     bool fused = false;                     // network shape fits the fused kernel
@@ -1179,7 +1463,8 @@ cudaError_t forward_fused(lbib_mlp* net, const float* x, int batch, float* y, bo
         for (int l = 0; l < net->L; ++l) {
             const size_t n = (size_t)net->out[l] * net->in[l];
             k_pack_fused<<<(unsigned)((n + 255) / 256), 256, 0, net->stream>>>(net->pb, net->woff[l], net->out[l],
-                                                                               net->in[l], net->pw + net->pwoff[l]);
+                                                                               net->in[l], net->pw + net->pwoff[l],
+                                                                               net->pwT + net->pwoff[l]);
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -1212,7 +1497,7 @@ cudaError_t forward_fused(lbib_mlp* net, const float* x, int batch, float* y, bo
             a.aout[l] = net->act[l];
         }
     const int ntiles = (batch + TC_BM - 1) / TC_BM;
-    k_mlp_fused<<<std::min(ntiles, net->nsm), FZ_THREADS, FZ_SMEM, net->stream>>>(a);
+    k_mlp_fused<false><<<std::min(ntiles, net->nsm), FZ_THREADS, FZ_SMEM, net->stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -1223,47 +1508,101 @@ int splits_for(int batch)
 }
 
 // backward pass after forward_core and the loss gradient in dY; gradients into net->g
+// the backward chain on tcgen05 (k_mlp_fused<true>): for l = L-1 .. 1,
+// dZ_{l-1} = bf16((dZ_l W_l) * GELU'(z_{l-1})), tile by tile through every layer,
+// from the output gradient dY; each dZ_{l-1} into dzs[l-1] (tiled)
+cudaError_t backward_chain(lbib_mlp* net, int batch)
+{
+    if (net->dzs.size() + 1 < (size_t)net->L || !net->pwT) return cudaErrorInvalidValue;
+    FusedArgs a{};
+    a.M = batch;
+    a.L = net->L - 1;
+    a.w = net->pwT;
+    a.status = net->status;
+    a.dy = net->dY;
+    for (int s = 0; s < a.L; ++s) {
+        const int l = net->L - 1 - s;
+        a.K[s] = net->out[l];
+        a.N[s] = net->in[l];
+        a.woff[s] = net->pwoff[l];
+        a.zout[s] = net->z[l - 1];
+        a.aout[s] = net->dzs[l - 1];
+    }
+    const int ntiles = (batch + TC_BM - 1) / TC_BM;
+    k_mlp_fused<true><<<std::min(ntiles, net->nsm), FZ_THREADS, FZ_SMEM, net->stream>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t backward_core(lbib_mlp* net, int batch)
 {
     cudaError_t e = cudaSuccess;
+    // after the fused forward pass (tiled pre-activations) the gradients of the
+    // pre-activations come from the tcgen05 chain, stored tiled
+    const bool chain = net->z_tiled;
+    if (chain && net->L > 1 && (e = backward_chain(net, batch)) != cudaSuccess) return e;
     const __nv_bfloat16* dcur = net->dY;  // gradient w.r.t. the current layer's output (pre-activation)
     int ldd = net->out[net->L - 1];
     const int splits = splits_for(batch);
     for (int l = net->L - 1; l >= 0 && e == cudaSuccess; --l) {
+        const int dtiled = chain ? 1 : 0;  // dY and the chain's gradients are tiled
         const __nv_bfloat16* ain = (l == 0) ? net->a0 : net->act[l - 1];
         const int ldin = net->in[l];
-        // dW_l = dcur^T ain: M = out, N = in, K = batch; both operands batch-major
-        GemmArgs gw{};
-        gw.A = dcur;
-        gw.lda = ldd;
-        gw.B = ain;
-        gw.ldb = ldin;
-        gw.M = net->out[l];
-        gw.N = net->in[l];
-        gw.K = batch;
-        gw.btiled = (l > 0 && net->z_tiled) ? 1 : 0;  // the fused forward pass tiles the activations
-        gw.part = net->part;
-        gw.ldc = net->in[l];
-        e = gemm<true, true, EPI_PARTIAL>(gw, splits, net->stream);
-        if (e != cudaSuccess) break;
-        {
-            const int kt = (batch + BK - 1) / BK;
-            const int tps = (kt + std::min(splits, kt) - 1) / std::min(splits, kt);
-            const int used = (kt + tps - 1) / tps;
-            const size_t cnt = (size_t)net->out[l] * net->in[l];
-            e = reduce_splits(net->part, used, cnt, net->g + net->woff[l], net->stream);
+        if (chain) {
+            // dW_l = dcur^T ain on tcgen05: 128 x 64 output tiles times batch slices of
+            // whole 64-row blocks (about 96 CTAs), FP32 partials summed in a fixed order
+            const int tiles = (net->out[l] + TC_BM - 1) / TC_BM * (net->in[l] / DW_TN);
+            const int nsplit =
+                std::max(1, std::min(std::min(MAX_SPLITS, (96 + tiles - 1) / tiles), (batch + DW_KB - 1) / DW_KB));
+            const int rps = ((batch + nsplit - 1) / nsplit + DW_KB - 1) / DW_KB * DW_KB;
+            const int used = (batch + rps - 1) / rps;
+            DwArgs da{dcur, ain, net->out[l], net->in[l], batch, rps, net->part, net->status};
+            k_dw_tc<<<dim3(tiles, used), DW_THREADS, DW_SMEM, net->stream>>>(da);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) {
+                const size_t cnt = (size_t)net->out[l] * net->in[l];
+                k_reduce_splits_dw<<<(unsigned)((cnt + 31) / 32), dim3(32, 8), 0, net->stream>>>(
+                    net->part, used, net->in[l], cnt, net->g + net->woff[l]);
+                e = cudaGetLastError();
+            }
             if (e != cudaSuccess) break;
+        } else {
+            // dW_l = dcur^T ain: M = out, N = in, K = batch; both operands batch-major
+            GemmArgs gw{};
+            gw.A = dcur;
+            gw.lda = ldd;
+            gw.B = ain;
+            gw.ldb = ldin;
+            gw.M = net->out[l];
+            gw.N = net->in[l];
+            gw.K = batch;
+            gw.part = net->part;
+            gw.ldc = net->in[l];
+            e = gemm<true, true, EPI_PARTIAL>(gw, splits, net->stream);
+            if (e != cudaSuccess) break;
+            {
+                const int kt = (batch + BK - 1) / BK;
+                const int tps = (kt + std::min(splits, kt) - 1) / std::min(splits, kt);
+                const int used = (kt + tps - 1) / tps;
+                const size_t cnt = (size_t)net->out[l] * net->in[l];
+                e = reduce_splits(net->part, used, cnt, net->g + net->woff[l], net->stream);
+                if (e != cudaSuccess) break;
+            }
         }
         // db_l = column sums of dcur
         {
             const int chunks = (batch + BIAS_ROWS - 1) / BIAS_ROWS;
             dim3 grid((ldd + 63) / 64, chunks);
-            k_bias_partial<<<grid, dim3(32, 8), 0, net->stream>>>(dcur, ldd, batch, net->part);
+            k_bias_partial<<<grid, dim3(32, 8), 0, net->stream>>>(dcur, ldd, batch, dtiled, net->part);
             e = reduce_splits(net->part, chunks, (size_t)ldd, net->g + net->boff[l], net->stream);
             if (e != cudaSuccess) break;
         }
         e = cudaGetLastError();
         if (l == 0 || e != cudaSuccess) break;
+        if (chain) {
+            dcur = net->dzs[l - 1];
+            ldd = net->in[l];
+            continue;
+        }
         // d pre-activation of layer l-1 = (dcur W_l) * GELU'(z_{l-1}): M = batch, N = in_l, K = out_l
         __nv_bfloat16* dnext = (dcur == net->dZa) ? net->dZb : net->dZa;
         GemmArgs gx{};
@@ -1275,7 +1614,6 @@ cudaError_t backward_core(lbib_mlp* net, int batch)
         gx.N = net->in[l];
         gx.K = net->out[l];
         gx.Zin = net->z[l - 1];
-        gx.ztiled = net->z_tiled ? 1 : 0;
         gx.Aout = dnext;
         gx.ldc = net->in[l];
         e = gemm<false, true, EPI_BWD_GELU>(gx, 1, net->stream);
@@ -1291,6 +1629,7 @@ PackTab pack_tab(const lbib_mlp* net)
 {
     PackTab t{};
     t.pw = (net->fused && !net->pw_dirty) ? net->pw : nullptr;
+    t.pwT = net->pwT;
     t.L = net->L;
     for (int l = 0; l < net->L; ++l) {
         t.in[l] = net->in[l];
@@ -1303,9 +1642,13 @@ PackTab pack_tab(const lbib_mlp* net)
 
 cudaError_t prep_and_loss(lbib_mlp* net, const float* x, const float* t, int batch)
 {
+    // the fused path keeps everything the backward pass reads in the tiled layouts
+    // (whole 128-row tiles, zero past the batch)
+    const int tiled = net->fused ? 1 : 0;
+    const int rows = tiled ? (batch + TC_BM - 1) / TC_BM * TC_BM : batch;
     dim3 blk(64, 4);
-    k_prep_input<<<(batch + blk.y - 1) / blk.y, blk, 0, net->stream>>>(x, batch, net->desc.n_in, net->in[0], net->cin,
-                                                                       net->sin, net->a0);
+    k_prep_input<<<(rows + blk.y - 1) / blk.y, blk, 0, net->stream>>>(x, batch, rows, net->desc.n_in, net->in[0],
+                                                                      net->cin, net->sin, net->a0, tiled);
     cudaError_t e = cudaGetLastError();
     // the forward pass keeps every layer's pre-activations and activations for
     // the backward pass: the fused kernel where the shape allows it
@@ -1314,10 +1657,10 @@ cudaError_t prep_and_loss(lbib_mlp* net, const float* x, const float* t, int bat
     if (e != cudaSuccess) return e;
     const int ldy = net->out[net->L - 1];
     dim3 lb(64, 4);
-    const int nblk = (batch + 3) / 4;
+    const int nblk = (rows + 3) / 4;
     // the output layer is padded to 64 columns: blockDim.x covers it
-    k_loss_grad<<<nblk, lb, 0, net->stream>>>(net->yraw, ldy, t, batch, net->desc.n_out, net->cout, net->sout,
-                                              net->dY, net->loss_part);
+    k_loss_grad<<<nblk, lb, 0, net->stream>>>(net->yraw, ldy, t, batch, rows, net->desc.n_out, net->cout, net->sout,
+                                              net->dY, net->loss_part, tiled);
     k_sum_partials<<<1, 256, 0, net->stream>>>(net->loss_part, nblk, (float)batch * (float)net->desc.n_out,
                                                net->loss_dev);
     return cudaGetLastError();
@@ -1399,7 +1742,8 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
     MA(net->sin, 32);
     MA(net->cout, 64);
     MA(net->sout, 64);
-    MA(net->a0, B * 64);
+    const size_t BT = (B + TC_BM - 1) / TC_BM * TC_BM;  // whole 128-row tiles (the tiled layouts)
+    MA(net->a0, BT * 64);
     for (int l = 0; l + 1 < net->L; ++l) {
         __nv_bfloat16* a = nullptr;
         float* z = nullptr;
@@ -1409,18 +1753,24 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
         net->z.push_back(z);
     }
     MA(net->yraw, B * 64);
-    MA(net->dY, B * 64);
+    MA(net->dY, BT * 64);
     MA(net->dZa, B * d->width);
     MA(net->dZb, B * d->width);
     const size_t wmax = (size_t)d->width * d->width;
     const int chunks = (int)((B + BIAS_ROWS - 1) / BIAS_ROWS);  // bias-gradient partials
     net->part_floats = std::max((size_t)MAX_SPLITS * wmax, (size_t)chunks * d->width);
     MA(net->part, net->part_floats);
-    MA(net->loss_part, (B + 3) / 4);
+    MA(net->loss_part, (BT + 3) / 4);
     MA(net->loss_dev, 1);
     MA(net->status, 1);
     MA(net->pidx, net->ntrue);
     net->fused = d->width <= FZ_MAXW && net->L <= FZ_MAXL;
+    if (net->fused)
+        for (int l = 0; l + 1 < net->L; ++l) {
+            __nv_bfloat16* dz = nullptr;
+            MA(dz, (B + TC_BM - 1) / TC_BM * TC_BM * d->width);
+            net->dzs.push_back(dz);
+        }
     if (net->fused) {
         size_t bytes = 0;
         for (int l = 0; l < net->L; ++l) {
@@ -1428,6 +1778,7 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
             bytes += (size_t)net->out[l] * net->in[l] * 2;
         }
         MA(net->pw, bytes);
+        MA(net->pwT, bytes);
     }
 #undef MA
     cudaDeviceGetAttribute(&net->nsm, cudaDevAttrMultiProcessorCount, net->device);
@@ -1436,7 +1787,10 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
                                   (int)TC_SMEM_REQUEST)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(k_gemm_tc<EPI_FWD_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)TC_SMEM_REQUEST)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FZ_SMEM)) !=
+        (e = cudaFuncSetAttribute(k_mlp_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FZ_SMEM)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_dw_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DW_SMEM)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_mlp_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FZ_SMEM)) !=
             cudaSuccess)
         return bail(e, "cudaFuncSetAttribute");
     if (d->cuda_stream) {
@@ -1521,8 +1875,8 @@ lbib_status lbib_mlp_forward(lbib_mlp* net, const float* x, int32_t batch, float
         return LBIB_OK;
     }
     dim3 blk(64, 4);
-    k_prep_input<<<(batch + 3) / 4, blk, 0, net->stream>>>(x, batch, net->desc.n_in, net->in[0], net->cin, net->sin,
-                                                           net->a0);
+    k_prep_input<<<(batch + 3) / 4, blk, 0, net->stream>>>(x, batch, batch, net->desc.n_in, net->in[0], net->cin,
+                                                           net->sin, net->a0, 0);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = forward_core(net, batch, false);
     if (e == cudaSuccess) {
