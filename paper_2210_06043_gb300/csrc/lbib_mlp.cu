@@ -932,6 +932,7 @@ struct DwArgs {
     const __nv_bfloat16* act;  // tiled, width N
     int M, N, batch, rows_per_split;
     float* part;               // [split][M x N] in the order k_reduce_splits_dw reads
+    float* bias_part;          // [split][M]: column sums of dz (the bias gradient), or null
     uint32_t* status;
 };
 
@@ -974,10 +975,13 @@ __global__ void __launch_bounds__(DW_THREADS, 1) k_dw_tc(DwArgs a)
     const int mcols = min(TC_BM, a.M - mt * TC_BM);  // columns of M in this tile (64 or 128)
     const int b0 = (int)blockIdx.y * a.rows_per_split, b1 = min(a.batch, b0 + a.rows_per_split);
     const int nkb = (b1 > b0) ? (b1 - b0 + DW_KB - 1) / DW_KB : 0;
+    // the CTAs of the first column tile also sum dz over their rows (warps 2, 3):
+    // a stage is then free once the MMAs and those 64 threads are done with it
+    const bool bsum = nt == 0 && a.bias_part != nullptr;
     if (tid == 0) {
         for (int i = 0; i < DW_STAGES; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(1));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(bsum ? 65 : 1));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(accf)), "r"(1));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(fin)), "r"(1));
@@ -1054,6 +1058,33 @@ __global__ void __launch_bounds__(DW_THREADS, 1) k_dw_tc(DwArgs a)
             // copies still in flight land before the CTA leaves
             for (int qq = (issued > DW_STAGES ? issued - DW_STAGES : 0); qq < issued; ++qq)
                 fz_wait(&full[qq % DW_STAGES], (uint32_t)(qq / DW_STAGES) & 1u, abort_flag, a.status, false);
+        }
+    } else if (warp == 2 || warp == 3) {
+        // ---------------------------------------------------- bias-gradient partial
+        // thread t sums columns 2t, 2t + 1 of the tile's dz block, rows in an order
+        // rotated by the column group (conflict-free shared-memory reads)
+        if (bsum) {
+            const int t = tid - 64, c = 2 * t, g = c >> 3;
+            float s0 = 0.f, s1 = 0.f;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int st = kb % DW_STAGES;
+                if (!fz_wait(&full[st], (uint32_t)(kb / DW_STAGES) & 1u, abort_flag, a.status)) break;
+                if (c < mcols) {
+                    const unsigned char* A = dws + (size_t)st * DW_ST + g * 1024 + (c & 7) * 2;
+                    for (int i = 0; i < DW_KB; ++i) {
+                        const int k = (i + g) & (DW_KB - 1);
+                        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(A + k * 16));
+                        s0 += v.x;
+                        s1 += v.y;
+                    }
+                }
+                fz_arrive(&empty[st]);
+            }
+            if (c < mcols) {
+                float* bp = a.bias_part + (size_t)blockIdx.y * a.M + mt * TC_BM + c;
+                bp[0] = s0;
+                bp[1] = s1;
+            }
         }
     } else if (warp >= 4) {
         // ---------------------------------------------------- partial out
@@ -1170,8 +1201,7 @@ __global__ void k_sum_partials(const float* __restrict__ partial, int n, float d
 // as bf16 pairs (coalesced); the 8 warps take every 8th row of the chunk and
 // their sums are added in warp order, so the result does not depend on timing.
 constexpr int BIAS_ROWS = 64;
-__global__ void k_bias_partial(const __nv_bfloat16* __restrict__ dZ, int ld, int batch, int tiled,
-                               float* __restrict__ part)
+__global__ void k_bias_partial(const __nv_bfloat16* __restrict__ dZ, int ld, int batch, float* __restrict__ part)
 {
     __shared__ float2 red[8][32];
     const int c = blockIdx.x * 64 + 2 * threadIdx.x, ch = blockIdx.y, w = threadIdx.y;
@@ -1179,8 +1209,7 @@ __global__ void k_bias_partial(const __nv_bfloat16* __restrict__ dZ, int ld, int
     float2 s = make_float2(0.f, 0.f);
     if (c < ld)
         for (int b = b0 + w; b < b1; b += 8) {
-            const size_t o = tiled ? at_index(b, c, ld) : (size_t)b * ld + c;  // c even: the pair is adjacent
-            const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(dZ + o));
+            const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(dZ + (size_t)b * ld + c));
             s.x += v.x;
             s.y += v.y;
         }
@@ -1363,6 +1392,7 @@ struct lbib_mlp {
     unsigned char* pwT = nullptr;           // transposed chunks (backward chain), offsets pwoff
     long long pwoff[FZ_MAXL] = {};
     std::vector<__nv_bfloat16*> dzs;        // dZ_l of the hidden layers (tiled), fused backward
+    float* bpart = nullptr;                 // [split][out] bias-gradient partials of k_dw_tc
     bool pw_dirty = true;
     bool z_tiled = false;  // pre-activations stored tiled (zt_index) by the last forward pass
     bool fused = false;                     // network shape fits the fused kernel
@@ -1544,7 +1574,6 @@ cudaError_t backward_core(lbib_mlp* net, int batch)
     int ldd = net->out[net->L - 1];
     const int splits = splits_for(batch);
     for (int l = net->L - 1; l >= 0 && e == cudaSuccess; --l) {
-        const int dtiled = chain ? 1 : 0;  // dY and the chain's gradients are tiled
         const __nv_bfloat16* ain = (l == 0) ? net->a0 : net->act[l - 1];
         const int ldin = net->in[l];
         if (chain) {
@@ -1555,7 +1584,7 @@ cudaError_t backward_core(lbib_mlp* net, int batch)
                 std::max(1, std::min(std::min(MAX_SPLITS, (96 + tiles - 1) / tiles), (batch + DW_KB - 1) / DW_KB));
             const int rps = ((batch + nsplit - 1) / nsplit + DW_KB - 1) / DW_KB * DW_KB;
             const int used = (batch + rps - 1) / rps;
-            DwArgs da{dcur, ain, net->out[l], net->in[l], batch, rps, net->part, net->status};
+            DwArgs da{dcur, ain, net->out[l], net->in[l], batch, rps, net->part, net->bpart, net->status};
             k_dw_tc<<<dim3(tiles, used), DW_THREADS, DW_SMEM, net->stream>>>(da);
             e = cudaGetLastError();
             if (e == cudaSuccess) {
@@ -1564,6 +1593,8 @@ cudaError_t backward_core(lbib_mlp* net, int batch)
                     net->part, used, net->in[l], cnt, net->g + net->woff[l]);
                 e = cudaGetLastError();
             }
+            // db_l: the column sums of dcur, summed by the same kernel per split
+            if (e == cudaSuccess) e = reduce_splits(net->bpart, used, (size_t)net->out[l], net->g + net->boff[l], net->stream);
             if (e != cudaSuccess) break;
         } else {
             // dW_l = dcur^T ain: M = out, N = in, K = batch; both operands batch-major
@@ -1589,10 +1620,10 @@ cudaError_t backward_core(lbib_mlp* net, int batch)
             }
         }
         // db_l = column sums of dcur
-        {
+        if (!chain) {
             const int chunks = (batch + BIAS_ROWS - 1) / BIAS_ROWS;
             dim3 grid((ldd + 63) / 64, chunks);
-            k_bias_partial<<<grid, dim3(32, 8), 0, net->stream>>>(dcur, ldd, batch, dtiled, net->part);
+            k_bias_partial<<<grid, dim3(32, 8), 0, net->stream>>>(dcur, ldd, batch, net->part);
             e = reduce_splits(net->part, chunks, (size_t)ldd, net->g + net->boff[l], net->stream);
             if (e != cudaSuccess) break;
         }
@@ -1765,12 +1796,14 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
     MA(net->status, 1);
     MA(net->pidx, net->ntrue);
     net->fused = d->width <= FZ_MAXW && net->L <= FZ_MAXL;
-    if (net->fused)
+    if (net->fused) {
         for (int l = 0; l + 1 < net->L; ++l) {
             __nv_bfloat16* dz = nullptr;
             MA(dz, (B + TC_BM - 1) / TC_BM * TC_BM * d->width);
             net->dzs.push_back(dz);
         }
+        MA(net->bpart, (size_t)MAX_SPLITS * std::max(d->width, 64));
+    }
     if (net->fused) {
         size_t bytes = 0;
         for (int l = 0; l < net->L; ++l) {
