@@ -595,6 +595,13 @@ struct FusedArgs {
     __nv_bfloat16* aout[FZ_MAXL];
     int train;
     const __nv_bfloat16* dy;
+    // training forward pass: the inputs a0 (tiled, 64 columns), and from the output
+    // layer the loss gradient dY = bf16(2 d / (M n_out)), d = y_raw - (t - c_out) /
+    // s_out (tiled, 64 columns), and per tile the sum of d^2 (loss_rows[tile], in a
+    // fixed order)
+    __nv_bfloat16 *a0_out, *dy_out;
+    const float* t;
+    float* loss_rows;
 };
 
 __device__ __forceinline__ bool fz_wait(uint64_t* bar, uint32_t parity, volatile uint32_t* abort_flag,
@@ -658,6 +665,8 @@ __device__ __forceinline__ void fz_prep(const FusedArgs& a, int tile, unsigned c
             }
             *reinterpret_cast<uint4*>(act + (r >> 3) * 1024 + (c0 >> 3) * 128 + (r & 7) * 16) =
                 make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            if (a.train)  // the backward pass's copy (zeros past the batch)
+                *reinterpret_cast<uint4*>(a.a0_out + at_index(row, c0, 64)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
     }
 }
@@ -718,6 +727,9 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
     uint64_t* fin = epid + 2;                // MMAs drained on an abort
     volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(fin + 1);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1) + 1;
+    uint64_t* lossb = fin + 2;                                 // [2] a tile's warp loss sums written
+    float* lsum = reinterpret_cast<float*>(lossb + 2);          // [2][FZ_EW]
+    static_assert(8 * 13 + 4 * 2 * FZ_EW <= 256, "barrier block");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ntiles = (a.M + TC_BM - 1) / TC_BM;
     // this CTA's tiles: blockIdx.x + k gridDim.x, k < nk; tile k uses slot k & 1
@@ -733,6 +745,8 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&epid[sl])), "r"(32 * FZ_EW));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(fin)), "r"(1));
+        for (int sl = 0; sl < 2; ++sl)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&lossb[sl])), "r"(FZ_EW));
         *abort_flag = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -831,7 +845,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             fz_arrive(&epid[sl]);
         }
-        uint32_t apar[2] = {0u, 0u};
+        uint32_t apar[2] = {0u, 0u}, lpar[2] = {0u, 0u};
         bool ok = true;
         for (int k0 = 0; k0 < nk && ok; k0 += 2)
             for (int l = 0; l < a.L && ok; ++l)
@@ -865,6 +879,55 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
                             fz_gelu16(v, b, cb, arow, st ? a.zout[l] + zt_index(grow, cb, N) : nullptr,
                                       a.train ? a.aout[l] + at_index(grow, cb, N) : nullptr);
                         }
+                    } else if (a.train) {
+                        // the loss gradient and squared errors of the row over its 16 of the
+                        // 64 (padded) output columns, straight from the accumulator
+                        static_assert(64 / NCG == 16, "one 16-column block per group");
+                        const float* bias = a.bias + a.boff[l];
+                        const int row = tile * TC_BM + r, cb = cg * 16;
+                        uint32_t v[16];
+                        tmem_ld16(trow + (uint32_t)cb, v);
+                        tmem_wait(v);
+                        float d2 = 0.f;
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int j = 0; j < 16; j += 2) {
+                            float gv[2] = {0.f, 0.f};
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const int col = cb + j + h;
+                                if (row < a.M && col < a.n_out) {
+                                    const float ts = (a.t[(size_t)row * a.n_out + col] - a.cout[col]) / a.sout[col];
+                                    const float d = (__uint_as_float(v[j + h]) + bias[col]) - ts;
+                                    d2 += d * d;
+                                    gv[h] = 2.0f * d / ((float)a.M * (float)a.n_out);
+                                }
+                            }
+                            const __nv_bfloat162 b2 = __floats2bfloat162_rn(gv[0], gv[1]);
+                            pk[j / 2] = *reinterpret_cast<const uint32_t*>(&b2);
+                        }
+                        uint4* ad = reinterpret_cast<uint4*>(a.dy_out + at_index(row, cb, 64));
+                        ad[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        ad[64] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                        // the tile's sum of d^2: a shuffle tree per warp, the warps' sums in
+                        // shared memory (one array and barrier per slot), added in warp order by
+                        // the first epilogue warp after a bounded wait
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+                        if (lane == 0) {
+                            lsum[sl * FZ_EW + (warp - 4)] = d2;
+                            fz_arrive(&lossb[sl]);
+                        }
+                        if (warp == 4) {
+                            const bool lok = fz_wait(&lossb[sl], lpar[sl], abort_flag, a.status);
+                            lpar[sl] ^= 1u;
+                            if (lok && lane == 0) {
+                                float ssum = 0.f;
+                                for (int i = 0; i < FZ_EW; ++i) ssum += lsum[sl * FZ_EW + i];
+                                a.loss_rows[tile] = ssum;
+                            }
+                        }
+                        if (k + 2 < nk) fz_prep<BWD>(a, tile_of(k + 2), act[sl], e);
                     } else {
                         const float* bias = a.bias + a.boff[l];
                         const int row = tile * TC_BM + r;
@@ -873,13 +936,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
                             uint32_t v[16];
                             tmem_ld16(trow + (uint32_t)cb, v);
                             tmem_wait(v);
-                            if (row < a.M && a.train) {
-#pragma unroll
-                                for (int j = 0; j < 16; ++j) {
-                                    const int col = cb + j;
-                                    if (col < a.n_out) a.y[(size_t)row * a.N[l] + col] = __uint_as_float(v[j]) + bias[col];
-                                }
-                            } else if (row < a.M) {
+                            if (row < a.M) {
 #pragma unroll
                                 for (int j = 0; j < 16; ++j) {
                                     const int col = cb + j;
@@ -1139,28 +1196,24 @@ __global__ void k_pack_fused(const __nv_bfloat16* __restrict__ pb, size_t wsrc, 
 }
 
 // a0 = bf16(s_in (x - c_in)), zero beyond n_in (blockDim.x = the padded width ldo)
-// (tiled: a0 in the at_index layout, rows up to `rows` (whole tiles), zero past the batch)
-__global__ void k_prep_input(const float* __restrict__ x, int batch, int rows, int n_in, int ldo,
-                             const float* __restrict__ c, const float* __restrict__ sc, __nv_bfloat16* __restrict__ a0,
-                             int tiled)
+__global__ void k_prep_input(const float* __restrict__ x, int batch, int n_in, int ldo, const float* __restrict__ c,
+                             const float* __restrict__ sc, __nv_bfloat16* __restrict__ a0)
 {
     const int b = blockIdx.x * blockDim.y + threadIdx.y, j = threadIdx.x;
-    if (b >= rows || j >= ldo) return;
-    const float v = (b < batch && j < n_in) ? sc[j] * (x[(size_t)b * n_in + j] - c[j]) : 0.f;
-    a0[tiled ? at_index(b, j, ldo) : (size_t)b * ldo + j] = __float2bfloat16_rn(v);
+    if (b >= batch || j >= ldo) return;
+    const float v = (j < n_in) ? sc[j] * (x[(size_t)b * n_in + j] - c[j]) : 0.f;
+    a0[(size_t)b * ldo + j] = __float2bfloat16_rn(v);
 }
 
 // loss terms and output gradient: d = y_raw - (t - c_out) / s_out over the first
-// n_out columns; dY = bf16(2 d / (batch n_out)); per-block partial sums of d^2.
-// Rows up to `rows` (zero past the batch); dY tiled (at_index) when `tiled`.
-__global__ void k_loss_grad(const float* __restrict__ yraw, int ldy, const float* __restrict__ t, int batch, int rows,
-                            int n_out, const float* __restrict__ c, const float* __restrict__ sc,
-                            __nv_bfloat16* __restrict__ dY, float* __restrict__ partial, int tiled)
+// n_out columns; dY = bf16(2 d / (batch n_out)); per-block partial sums of d^2
+__global__ void k_loss_grad(const float* __restrict__ yraw, int ldy, const float* __restrict__ t, int batch, int n_out,
+                            const float* __restrict__ c, const float* __restrict__ sc, __nv_bfloat16* __restrict__ dY,
+                            float* __restrict__ partial)
 {
     __shared__ float red[256];
     const int b = blockIdx.x * blockDim.y + threadIdx.y, j = threadIdx.x;  // blockDim (64, 4)
     float d2 = 0.f;
-    if (b < rows && b >= batch) dY[tiled ? at_index(b, j, ldy) : (size_t)b * ldy + j] = __float2bfloat16_rn(0.f);
     if (b < batch) {
         float gval = 0.f;
         if (j < n_out) {
@@ -1169,7 +1222,7 @@ __global__ void k_loss_grad(const float* __restrict__ yraw, int ldy, const float
             d2 = d * d;
             gval = 2.0f * d / ((float)batch * (float)n_out);
         }
-        dY[tiled ? at_index(b, j, ldy) : (size_t)b * ldy + j] = __float2bfloat16_rn(gval);
+        dY[(size_t)b * ldy + j] = __float2bfloat16_rn(gval);
     }
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     red[tid] = d2;
@@ -1487,8 +1540,9 @@ cudaError_t forward_core(lbib_mlp* net, int batch, bool store_z = true)
 
 // inference through k_mlp_fused: weight chunks re-packed after an update,
 // one persistent CTA per SM (at most one per 128-row tile)
-cudaError_t forward_fused(lbib_mlp* net, const float* x, int batch, float* y, bool train = false)
+cudaError_t forward_fused(lbib_mlp* net, const float* x, int batch, float* y, const float* t = nullptr)
 {
+    const bool train = t != nullptr;
     if (net->pw_dirty) {
         for (int l = 0; l < net->L; ++l) {
             const size_t n = (size_t)net->out[l] * net->in[l];
@@ -1521,11 +1575,16 @@ cudaError_t forward_fused(lbib_mlp* net, const float* x, int batch, float* y, bo
     a.sout = net->sout;
     a.status = net->status;
     a.train = train ? 1 : 0;
-    if (train)
+    if (train) {
         for (int l = 0; l + 1 < net->L; ++l) {
             a.zout[l] = net->z[l];
             a.aout[l] = net->act[l];
         }
+        a.a0_out = net->a0;
+        a.dy_out = net->dY;
+        a.t = t;
+        a.loss_rows = net->loss_part;
+    }
     const int ntiles = (batch + TC_BM - 1) / TC_BM;
     k_mlp_fused<false><<<std::min(ntiles, net->nsm), FZ_THREADS, FZ_SMEM, net->stream>>>(a);
     return cudaGetLastError();
@@ -1673,25 +1732,28 @@ PackTab pack_tab(const lbib_mlp* net)
 
 cudaError_t prep_and_loss(lbib_mlp* net, const float* x, const float* t, int batch)
 {
-    // the fused path keeps everything the backward pass reads in the tiled layouts
-    // (whole 128-row tiles, zero past the batch)
-    const int tiled = net->fused ? 1 : 0;
-    const int rows = tiled ? (batch + TC_BM - 1) / TC_BM * TC_BM : batch;
+    net->z_tiled = net->fused;  // the fused kernel stores what the backward pass reads tiled
+    if (net->fused) {
+        // one fused kernel: the inputs, every layer's pre-activations and activations,
+        // the loss gradient and the squared errors per row and column group
+        cudaError_t e = forward_fused(net, x, batch, net->yraw, t);
+        if (e != cudaSuccess) return e;
+        k_sum_partials<<<1, 256, 0, net->stream>>>(net->loss_part, (batch + TC_BM - 1) / TC_BM,
+                                                   (float)batch * (float)net->desc.n_out, net->loss_dev);
+        return cudaGetLastError();
+    }
     dim3 blk(64, 4);
-    k_prep_input<<<(rows + blk.y - 1) / blk.y, blk, 0, net->stream>>>(x, batch, rows, net->desc.n_in, net->in[0],
-                                                                      net->cin, net->sin, net->a0, tiled);
+    k_prep_input<<<(batch + blk.y - 1) / blk.y, blk, 0, net->stream>>>(x, batch, net->desc.n_in, net->in[0],
+                                                                       net->cin, net->sin, net->a0);
     cudaError_t e = cudaGetLastError();
-    // the forward pass keeps every layer's pre-activations and activations for
-    // the backward pass: the fused kernel where the shape allows it
-    net->z_tiled = net->fused;  // the fused kernel stores the pre-activations tiled (zt_index)
-    if (e == cudaSuccess) e = net->fused ? forward_fused(net, x, batch, net->yraw, true) : forward_core(net, batch);
+    if (e == cudaSuccess) e = forward_core(net, batch);
     if (e != cudaSuccess) return e;
     const int ldy = net->out[net->L - 1];
     dim3 lb(64, 4);
-    const int nblk = (rows + 3) / 4;
+    const int nblk = (batch + 3) / 4;
     // the output layer is padded to 64 columns: blockDim.x covers it
-    k_loss_grad<<<nblk, lb, 0, net->stream>>>(net->yraw, ldy, t, batch, rows, net->desc.n_out, net->cout, net->sout,
-                                              net->dY, net->loss_part, tiled);
+    k_loss_grad<<<nblk, lb, 0, net->stream>>>(net->yraw, ldy, t, batch, net->desc.n_out, net->cout, net->sout,
+                                              net->dY, net->loss_part);
     k_sum_partials<<<1, 256, 0, net->stream>>>(net->loss_part, nblk, (float)batch * (float)net->desc.n_out,
                                                net->loss_dev);
     return cudaGetLastError();
@@ -1791,7 +1853,7 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
     const int chunks = (int)((B + BIAS_ROWS - 1) / BIAS_ROWS);  // bias-gradient partials
     net->part_floats = std::max((size_t)MAX_SPLITS * wmax, (size_t)chunks * d->width);
     MA(net->part, net->part_floats);
-    MA(net->loss_part, (BT + 3) / 4);
+    MA(net->loss_part, BT * 4);  // per row and column group (fused), per block otherwise
     MA(net->loss_dev, 1);
     MA(net->status, 1);
     MA(net->pidx, net->ntrue);
@@ -1908,8 +1970,8 @@ lbib_status lbib_mlp_forward(lbib_mlp* net, const float* x, int32_t batch, float
         return LBIB_OK;
     }
     dim3 blk(64, 4);
-    k_prep_input<<<(batch + 3) / 4, blk, 0, net->stream>>>(x, batch, batch, net->desc.n_in, net->in[0], net->cin,
-                                                           net->sin, net->a0, 0);
+    k_prep_input<<<(batch + 3) / 4, blk, 0, net->stream>>>(x, batch, net->desc.n_in, net->in[0], net->cin, net->sin,
+                                                           net->a0);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = forward_core(net, batch, false);
     if (e == cudaSuccess) {
