@@ -1302,10 +1302,28 @@ __global__ void k_reduce_splits(const float* __restrict__ part, int splits, size
 // block as 32-row groups of 4-column groups, 32 rows x 4 values each): entry j
 // of a partial is element (m, n) of out, m = (j / (128 N/4)) * 32 + (j / 4) % 32,
 // n = ((j / 128) % (N / 4)) * 4 + j % 4; read in partial order, written to [M][N]
+// Blocks past those of the weights sum the bias partials bpart[split][M] into
+// bout[M] the same way (in order).
 __global__ void k_reduce_splits_dw(const float* __restrict__ part, int splits, int N, size_t count,
-                                   float* __restrict__ out)
+                                   float* __restrict__ out, const float* __restrict__ bpart, int M,
+                                   float* __restrict__ bout)
 {
     __shared__ float red[8][32];
+    const size_t wblocks = (count + 31) / 32;
+    if (blockIdx.x >= wblocks) {
+        const int i = (int)(blockIdx.x - wblocks) * 32 + threadIdx.x, w = threadIdx.y;
+        float s = 0.f;
+        if (i < M)
+            for (int k = w; k < splits; k += 8) s += bpart[(size_t)k * M + i];
+        red[w][threadIdx.x] = s;
+        __syncthreads();
+        if (w == 0 && i < M) {
+            float t = red[0][threadIdx.x];
+            for (int k = 1; k < 8; ++k) t += red[k][threadIdx.x];
+            bout[i] = t;
+        }
+        return;
+    }
     const size_t j = (size_t)blockIdx.x * 32 + threadIdx.x;
     const int w = threadIdx.y;
     float s = 0.f;
@@ -1647,13 +1665,14 @@ cudaError_t backward_core(lbib_mlp* net, int batch)
             k_dw_tc<<<dim3(tiles, used), DW_THREADS, DW_SMEM, net->stream>>>(da);
             e = cudaGetLastError();
             if (e == cudaSuccess) {
+                // dW_l and db_l (the column sums of dcur, per split from the same kernel)
                 const size_t cnt = (size_t)net->out[l] * net->in[l];
-                k_reduce_splits_dw<<<(unsigned)((cnt + 31) / 32), dim3(32, 8), 0, net->stream>>>(
-                    net->part, used, net->in[l], cnt, net->g + net->woff[l]);
+                const unsigned blocks = (unsigned)((cnt + 31) / 32 + (net->out[l] + 31) / 32);
+                k_reduce_splits_dw<<<blocks, dim3(32, 8), 0, net->stream>>>(net->part, used, net->in[l], cnt,
+                                                                           net->g + net->woff[l], net->bpart,
+                                                                           net->out[l], net->g + net->boff[l]);
                 e = cudaGetLastError();
             }
-            // db_l: the column sums of dcur, summed by the same kernel per split
-            if (e == cudaSuccess) e = reduce_splits(net->bpart, used, (size_t)net->out[l], net->g + net->boff[l], net->stream);
             if (e != cudaSuccess) break;
         } else {
             // dW_l = dcur^T ain: M = out, N = in, K = batch; both operands batch-major
