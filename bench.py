@@ -316,7 +316,7 @@ def surrogate_inference(local, stream, iters=50, batch=65536, accuracy=True):
     """Throughput of the surrogate network's inference (include/lbib_mlp.h:
     9 inputs, 3 x 256 GELU, 3 outputs; the fused tcgen05 kernel) on batches
     of 65 536 queries, CUDA events on the launching stream; one training step
-    (batch 8192, mma.sync backward); the host-side cost of a trajectory's
+    (batch 8192, tcgen05 forward and backward); the host-side cost of a trajectory's
     features (surrogate.features_many); and the held-out accuracy of a
     network trained here (``surrogate_accuracy``).  Weights of the timed
     network random: timing only."""

@@ -585,15 +585,14 @@ struct FusedArgs {
     long long woff[FZ_MAXL];   // byte offset of layer l's first chunk in w
     const float *cin, *sin, *cout, *sout;
     uint32_t* status;
-    // a training forward pass (train): layer l's pre-activations and
+    // a training forward pass (k_mlp_fused<FZ_TRAIN>): layer l's pre-activations and
     // activations to zout[l], aout[l] (tiled: zt_index, at_index), the output
     // layer's raw values y_raw = W a + b to y ([M][N_{L-1}]) instead of the
-    // scaled outputs.  The backward chain (k_mlp_fused<true>): step s reads the
+    // scaled outputs.  The backward chain (k_mlp_fused<FZ_BWD>): step s reads the
     // pre-activations zout[s] of its output width N[s] and writes the gradient
     // aout[s] = bf16(acc * GELU'(z)) (tiled), starting from dy ([M][K[0]] BF16).
     float* zout[FZ_MAXL];
     __nv_bfloat16* aout[FZ_MAXL];
-    int train;
     const __nv_bfloat16* dy;
     // training forward pass: the inputs a0 (tiled, 64 columns), and from the output
     // layer the loss gradient dY = bf16(2 d / (M n_out)), d = y_raw - (t - c_out) /
@@ -632,13 +631,17 @@ __device__ __forceinline__ void fz_arrive(uint64_t* bar)
 // taking rows 8 w .. 8 w + 7 (lane % 8) and a quarter of the 64 columns
 // (lane / 8) each, so the eight lanes of a 16-byte store phase fill one
 // 128-byte row of core matrices (no bank conflicts)
-template <bool BWD>
+// what an instantiation of k_mlp_fused computes (compile-time, so that the
+// inference kernel carries none of the training code)
+enum FzMode { FZ_INFER = 0, FZ_TRAIN = 1, FZ_BWD = 2 };
+
+template <int MODE>
 __device__ __forceinline__ void fz_prep(const FusedArgs& a, int tile, unsigned char* act, int e)
 {
     static_assert(FZ_EW * 8 == TC_BM, "one warp per 8 rows");
     constexpr int COLS = 16;
     const int r = (e >> 5) * 8 + (e & 7), part = (e >> 3) & 3, row = tile * TC_BM + r;
-    if (BWD) {
+    if (MODE == FZ_BWD) {
         // the output gradient rows (BF16, K[0] = 64 columns, tiled: at_index)
 #pragma unroll
         for (int g8 = 0; g8 < COLS / 8; ++g8) {
@@ -665,7 +668,7 @@ __device__ __forceinline__ void fz_prep(const FusedArgs& a, int tile, unsigned c
             }
             *reinterpret_cast<uint4*>(act + (r >> 3) * 1024 + (c0 >> 3) * 128 + (r & 7) * 16) =
                 make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            if (a.train)  // the backward pass's copy (zeros past the batch)
+            if (MODE == FZ_TRAIN)  // the backward pass's copy (zeros past the batch)
                 *reinterpret_cast<uint4*>(a.a0_out + at_index(row, c0, 64)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
     }
@@ -713,7 +716,7 @@ __device__ __forceinline__ void fz_bwd_step(const FusedArgs& a, int l, int tile,
     }
 }
 
-template <bool BWD>
+template <int MODE>
 __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
 {
     extern __shared__ __align__(1024) unsigned char fz[];
@@ -841,7 +844,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
         constexpr int NCG = FZ_EW / 4;  // column groups per tile row
         const int e = tid - 128, q4 = warp & 3, cg = (warp - 4) >> 2, r = q4 * 32 + lane;
         for (int sl = 0; sl < 2 && sl < nk; ++sl) {
-            fz_prep<BWD>(a, tile_of(sl), act[sl], e);
+            fz_prep<MODE>(a, tile_of(sl), act[sl], e);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             fz_arrive(&epid[sl]);
         }
@@ -858,18 +861,18 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const int tile = tile_of(k);
                     const uint32_t trow = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(sl * 256);
-                    if (BWD) {
+                    if (MODE == FZ_BWD) {
                         fz_bwd_step(a, l, tile, trow, act[sl] + (r >> 3) * 1024 + (r & 7) * 16, r, cg);
                         // the slot's next tile once its last step is done (that step wrote
                         // nothing to the slot's shared memory)
-                        if (l + 1 == a.L && k + 2 < nk) fz_prep<BWD>(a, tile_of(k + 2), act[sl], e);
+                        if (l + 1 == a.L && k + 2 < nk) fz_prep<MODE>(a, tile_of(k + 2), act[sl], e);
                     } else if (l + 1 < a.L) {
                         // N is a multiple of 64: each column group is whole 16-column blocks
                         const int N = a.N[l], cbeg = cg * (N / NCG), cend = cbeg + N / NCG;
                         const float4* bias4 = reinterpret_cast<const float4*>(a.bias + a.boff[l]);
                         unsigned char* arow = act[sl] + (r >> 3) * 1024 + (r & 7) * 16;
                         const int grow = tile * TC_BM + r;
-                        const bool st = a.train && grow < a.M;
+                        const bool st = MODE == FZ_TRAIN && grow < a.M;
                         for (int cb = cbeg; cb < cend; cb += 16) {
                             uint32_t v[16];
                             float4 b[4];
@@ -877,9 +880,9 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
                             ld_bias16(b, bias4 + (cb >> 2));
                             tmem_wait(v);
                             fz_gelu16(v, b, cb, arow, st ? a.zout[l] + zt_index(grow, cb, N) : nullptr,
-                                      a.train ? a.aout[l] + at_index(grow, cb, N) : nullptr);
+                                      MODE == FZ_TRAIN ? a.aout[l] + at_index(grow, cb, N) : nullptr);
                         }
-                    } else if (a.train) {
+                    } else if (MODE == FZ_TRAIN) {
                         // the loss gradient and squared errors of the row over its 16 of the
                         // 64 (padded) output columns, straight from the accumulator
                         static_assert(64 / NCG == 16, "one 16-column block per group");
@@ -927,7 +930,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
                                 a.loss_rows[tile] = ssum;
                             }
                         }
-                        if (k + 2 < nk) fz_prep<BWD>(a, tile_of(k + 2), act[sl], e);
+                        if (k + 2 < nk) fz_prep<MODE>(a, tile_of(k + 2), act[sl], e);
                     } else {
                         const float* bias = a.bias + a.boff[l];
                         const int row = tile * TC_BM + r;
@@ -947,7 +950,7 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
                             }
                         }
                         // the slot's next tile: the MMAs of this one have all completed
-                        if (k + 2 < nk) fz_prep<BWD>(a, tile_of(k + 2), act[sl], e);
+                        if (k + 2 < nk) fz_prep<MODE>(a, tile_of(k + 2), act[sl], e);
                     }
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1592,7 +1595,6 @@ cudaError_t forward_fused(lbib_mlp* net, const float* x, int batch, float* y, co
     a.cout = net->cout;
     a.sout = net->sout;
     a.status = net->status;
-    a.train = train ? 1 : 0;
     if (train) {
         for (int l = 0; l + 1 < net->L; ++l) {
             a.zout[l] = net->z[l];
@@ -1604,7 +1606,10 @@ cudaError_t forward_fused(lbib_mlp* net, const float* x, int batch, float* y, co
         a.loss_rows = net->loss_part;
     }
     const int ntiles = (batch + TC_BM - 1) / TC_BM;
-    k_mlp_fused<false><<<std::min(ntiles, net->nsm), FZ_THREADS, FZ_SMEM, net->stream>>>(a);
+    if (train)
+        k_mlp_fused<FZ_TRAIN><<<std::min(ntiles, net->nsm), FZ_THREADS, FZ_SMEM, net->stream>>>(a);
+    else
+        k_mlp_fused<FZ_INFER><<<std::min(ntiles, net->nsm), FZ_THREADS, FZ_SMEM, net->stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -1615,7 +1620,7 @@ int splits_for(int batch)
 }
 
 // backward pass after forward_core and the loss gradient in dY; gradients into net->g
-// the backward chain on tcgen05 (k_mlp_fused<true>): for l = L-1 .. 1,
+// the backward chain on tcgen05 (k_mlp_fused<FZ_BWD>): for l = L-1 .. 1,
 // dZ_{l-1} = bf16((dZ_l W_l) * GELU'(z_{l-1})), tile by tile through every layer,
 // from the output gradient dY; each dZ_{l-1} into dzs[l-1] (tiled)
 cudaError_t backward_chain(lbib_mlp* net, int batch)
@@ -1636,7 +1641,7 @@ cudaError_t backward_chain(lbib_mlp* net, int batch)
         a.aout[s] = net->dzs[l - 1];
     }
     const int ntiles = (batch + TC_BM - 1) / TC_BM;
-    k_mlp_fused<true><<<std::min(ntiles, net->nsm), FZ_THREADS, FZ_SMEM, net->stream>>>(a);
+    k_mlp_fused<FZ_BWD><<<std::min(ntiles, net->nsm), FZ_THREADS, FZ_SMEM, net->stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -1901,10 +1906,12 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
                                   (int)TC_SMEM_REQUEST)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(k_gemm_tc<EPI_FWD_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)TC_SMEM_REQUEST)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_mlp_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FZ_SMEM)) !=
+        (e = cudaFuncSetAttribute(k_mlp_fused<FZ_INFER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FZ_SMEM)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_mlp_fused<FZ_TRAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FZ_SMEM)) !=
             cudaSuccess ||
         (e = cudaFuncSetAttribute(k_dw_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DW_SMEM)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_mlp_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FZ_SMEM)) !=
+        (e = cudaFuncSetAttribute(k_mlp_fused<FZ_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FZ_SMEM)) !=
             cudaSuccess)
         return bail(e, "cudaFuncSetAttribute");
     if (d->cuda_stream) {
