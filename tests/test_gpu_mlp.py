@@ -63,11 +63,13 @@ def test_forward_matches_quantized_oracle():
     net.close()
 
 
-@pytest.mark.parametrize("B", [500, 1024])  # a ragged batch and one of whole 64-row tiles
+# a ragged batch, one of whole tiles, and one of 313 tiles (ragged): up to three 128-row tiles per
+# CTA of the fused training kernels, so both tile slots and the staging of a slot's next tile run
+@pytest.mark.parametrize("B", [500, 1024, 40000])
 def test_gradients_match_quantized_oracle_and_repeat_exactly(B):
     rng = np.random.default_rng(1)
     norm = _norm(rng)
-    net = _net(norm, seed=7)
+    net = _net(norm, max_batch=max(4096, B), seed=7)
     x = rng.uniform(-1, 1, (B, N_IN)).astype(np.float32)
     t = (rng.normal(0, 1, (B, N_OUT)) * norm["s_out"] + norm["c_out"]).astype(np.float32)
     xd, td = _dev(x), _dev(t)
