@@ -265,6 +265,7 @@ class Trained:
     t_star_max: float
     losses: List[float]
     stream: object = None  # torch stream the network enqueues on
+    seconds_per_step: float = float("nan")  # wall time per step after the first 100 (sampling included)
 
 
 def normalisation(X: np.ndarray, Y: np.ndarray):
@@ -334,6 +335,7 @@ def train(X: np.ndarray, Y: np.ndarray, steps: int = 3000, batch: int = 8192, lr
         loss = torch.zeros(1, device="cuda")
         grad = torch.zeros(net.param_count(), device="cuda") if world > 1 else None
         losses = []
+        t_warm, k_warm = None, None
         for k in range(steps):
             idx = torch.randint(0, X.shape[0], (batch,), device="cuda", generator=g)
             xb, yb = Xd[idx].contiguous(), Yd[idx].contiguous()
@@ -345,10 +347,13 @@ def train(X: np.ndarray, Y: np.ndarray, steps: int = 3000, batch: int = 8192, lr
             if k % 100 == 0 or k == steps - 1:
                 st.synchronize()
                 losses.append(float(loss.item()))
+                if k == min(100, steps - 1):  # first uses of every kernel are behind this point
+                    t_warm, k_warm = time.perf_counter(), k
                 if log:
                     log(f"step {k}: loss {losses[-1]:.4e}")
         st.synchronize()
-    return Trained(net, *norm, t_star_max=float(X[:, -1].max()), losses=losses, stream=st)
+        per_step = (time.perf_counter() - t_warm) / (steps - 1 - k_warm) if steps - 1 > k_warm else float("nan")
+    return Trained(net, *norm, t_star_max=float(X[:, -1].max()), losses=losses, stream=st, seconds_per_step=per_step)
 
 
 def predict_network(tr: Trained, X: np.ndarray) -> np.ndarray:
@@ -529,6 +534,7 @@ def main(argv=None):
         "holdout_points": int(n_hold), "samples_per_trajectory": int(args.samples),
         "steps_per_trajectory": int(args.steps), "t_star_max": float(t_star[-1]),
         "generation_gpu_seconds": gen_secs, "training_seconds": train_secs, "train_steps": args.train_steps,
+        "training_seconds_per_step": tr.seconds_per_step,
         "final_training_loss": tr.losses[-1], "holdout_errors": err, "holdout_single_trajectory_errors": single,
         "seconds_per_trajectory": {"plain_solver": plain_per_traj, "batched_solver": batched_per_traj,
                                    "surrogate": surrogate_per_traj},
