@@ -964,35 +964,44 @@ __global__ void __launch_bounds__(FZ_THREADS, 1) k_mlp_fused(FusedArgs a)
 }
 
 // ------------------------------------------- weight gradients on tcgen05
-// dW = dZ^T A over a slice of the batch: M = out (64 or 256), N = in (64 or
-// 256), K = batch rows.  Both operands come from the tiled layout (at_index),
-// which holds, per 64-row block and 8-column group, 64 rows of 16 bytes, a
-// block of all columns contiguous: copied whole into shared memory (one bulk
-// copy per operand and K block) it is the MN-major no-swizzle core-matrix
-// layout (core matrix = 8 K-rows x 8 M/N elements; K-neighbours LBO = 128 B
-// apart, M/N-neighbours SBO = 1024 B apart; measured on GB300 against exact
-// small-integer products).  Each CTA streams its slice in 64-row K blocks
-// through DW_STAGES stages, multiplies with M 128 (the two halves of M 256
-// into tensor-memory columns [0, 256) and [256, 512)), N = in, K 16 per
-// instruction, and writes its FP32 partial (in the order k_reduce_splits_dw
-// reads) for a fixed-order reduction.  Rows past the batch in the last block
-// are zero in both layouts.
-// Roles: warp 0 lane 0 issues the MMAs, warp 1 streams the operands, warps
-// 4 .. 11 write the partial (warp w: lanes of quadrant w % 4, half (w - 4) / 4).
-constexpr int DW_STAGES = 6, DW_THREADS = 256, DW_KB = 64, DW_TN = 64;
+// dW_l = dZ_l^T A_l over a slice of the batch for every layer l in one launch:
+// M = out (64 or 256), N = in (64 or 256), K = batch rows.  Both operands come
+// from the tiled layout (at_index), which holds, per 64-row block and 8-column
+// group, 64 rows of 16 bytes, a block of all columns contiguous: copied whole
+// into shared memory (one bulk copy per operand and K block) it is the MN-major
+// no-swizzle core-matrix layout (core matrix = 8 K-rows x 8 M/N elements;
+// K-neighbours LBO = 128 B apart, M/N-neighbours SBO = 1024 B apart; measured on
+// GB300 against exact small-integer products).  A CTA owns one 128 x 64 output
+// tile (64 x 64 where M is 64) of one layer and one slice of the batch: it
+// streams the slice in 64-row K blocks through DW_STAGES stages, accumulates in
+// 64 tensor-memory columns (M 128, N 64, K 16 per instruction), and writes its
+// FP32 partial (in the order k_reduce_dw reads) for a fixed-order reduction.
+// Rows past the batch in the last block are zero in both layouts.
+// Roles: warp 0 lane 0 issues the MMAs, warp 1 streams the operands, warps 2
+// and 3 sum the dZ blocks of the layer's first column tile (the bias gradient),
+// warps 4 .. 7 write the partial (warp w: the lanes of quadrant w % 4).
+constexpr int DW_STAGES = 4, DW_THREADS = 256, DW_KB = 64, DW_TN = 64;
 constexpr size_t DW_OPA = (size_t)TC_BM * DW_KB * 2;        // 16 KB of A (128 rows of M) per stage
 constexpr size_t DW_OPB = (size_t)DW_TN * DW_KB * 2;        // 8 KB of B (64 columns of N) per stage
 constexpr size_t DW_ST = DW_OPA + DW_OPB;
 constexpr size_t DW_BAR = (size_t)DW_STAGES * DW_ST;        // barriers after the stages
 constexpr size_t DW_SMEM = DW_BAR + 128;
-static_assert(DW_SMEM <= 227 * 1024, "weight-gradient kernel shared memory");
+static_assert(2 * (DW_SMEM + 1024) <= 228 * 1024, "two weight-gradient CTAs per SM");
 
-struct DwArgs {
+// one layer's share of the launch: its CTAs are cta0 .. cta0 + tiles * splits - 1,
+// CTA cta0 + s * tiles + t taking output tile t (row tile t / (N / 64), column
+// tile t % (N / 64)) over batch slice s
+struct DwLayer {
     const __nv_bfloat16* dz;   // tiled, width M
     const __nv_bfloat16* act;  // tiled, width N
-    int M, N, batch, rows_per_split;
-    float* part;               // [split][M x N] in the order k_reduce_splits_dw reads
-    float* bias_part;          // [split][M]: column sums of dz (the bias gradient), or null
+    long long part_off;        // [split][M x N] partials at part + part_off
+    int M, N, tiles, cta0, bpart_off;  // bias partials [split][M] at bias_part + bpart_off
+};
+struct DwArgs {
+    DwLayer ly[FZ_MAXL];
+    int nl, batch, rows_per_split;
+    float* part;
+    float* bias_part;
     uint32_t* status;
 };
 
@@ -1018,9 +1027,8 @@ __device__ __forceinline__ uint64_t dw_desc(uint32_t saddr)
     return d;                                      // no swizzle
 }
 
-// grid (M / 128 tiles x N / 64 tiles, splits): CTA (t, s) computes the 128 x 64
-// tile t of dW over batch rows [s rows_per_split, (s + 1) rows_per_split)
-__global__ void __launch_bounds__(DW_THREADS, 1) k_dw_tc(DwArgs a)
+// one CTA per (layer, output tile, batch slice); see DwLayer
+__global__ void __launch_bounds__(DW_THREADS, 2) k_dw_tc(DwArgs a)
 {
     extern __shared__ __align__(1024) unsigned char dws[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(dws + DW_BAR);
@@ -1031,9 +1039,26 @@ __global__ void __launch_bounds__(DW_THREADS, 1) k_dw_tc(DwArgs a)
     volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(fin + 1);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1) + 1;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tn = a.N / DW_TN, mt = (int)blockIdx.x / tn, nt = (int)blockIdx.x % tn;
-    const int mcols = min(TC_BM, a.M - mt * TC_BM);  // columns of M in this tile (64 or 128)
-    const int b0 = (int)blockIdx.y * a.rows_per_split, b1 = min(a.batch, b0 + a.rows_per_split);
+    // this CTA's layer (constant indices only: the table stays in parameter space)
+    const __nv_bfloat16 *dz = nullptr, *act = nullptr;
+    long long part_off = 0;
+    int M = 0, N = 0, tiles = 1, cta0 = 0, bpart_off = 0;
+#pragma unroll
+    for (int i = 0; i < FZ_MAXL; ++i)
+        if (i < a.nl && (int)blockIdx.x >= a.ly[i].cta0) {
+            dz = a.ly[i].dz;
+            act = a.ly[i].act;
+            part_off = a.ly[i].part_off;
+            M = a.ly[i].M;
+            N = a.ly[i].N;
+            tiles = a.ly[i].tiles;
+            cta0 = a.ly[i].cta0;
+            bpart_off = a.ly[i].bpart_off;
+        }
+    const int idx = (int)blockIdx.x - cta0, tile = idx % tiles, split = idx / tiles;
+    const int tn = N / DW_TN, mt = tile / tn, nt = tile % tn;
+    const int mcols = min(TC_BM, M - mt * TC_BM);  // columns of M in this tile (64 or 128)
+    const int b0 = split * a.rows_per_split, b1 = min(a.batch, b0 + a.rows_per_split);
     const int nkb = (b1 > b0) ? (b1 - b0 + DW_KB - 1) / DW_KB : 0;
     // the CTAs of the first column tile also sum dz over their rows (warps 2, 3):
     // a stage is then free once the MMAs and those 64 threads are done with it
@@ -1106,11 +1131,11 @@ __global__ void __launch_bounds__(DW_THREADS, 1) k_dw_tc(DwArgs a)
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(ba + bb) : "memory");
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sA),
-                "l"(a.dz + at_index(kr, mt * TC_BM, a.M)), "r"(ba), "r"(fb)
+                "l"(dz + at_index(kr, mt * TC_BM, M)), "r"(ba), "r"(fb)
                 : "memory");
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sB),
-                "l"(a.act + at_index(kr, nt * DW_TN, a.N)), "r"(bb), "r"(fb)
+                "l"(act + at_index(kr, nt * DW_TN, N)), "r"(bb), "r"(fb)
                 : "memory");
             issued = kb + 1;
         }
@@ -1141,7 +1166,7 @@ __global__ void __launch_bounds__(DW_THREADS, 1) k_dw_tc(DwArgs a)
                 fz_arrive(&empty[st]);
             }
             if (c < mcols) {
-                float* bp = a.bias_part + (size_t)blockIdx.y * a.M + mt * TC_BM + c;
+                float* bp = a.bias_part + bpart_off + (size_t)split * M + mt * TC_BM + c;
                 bp[0] = s0;
                 bp[1] = s1;
             }
@@ -1153,10 +1178,10 @@ __global__ void __launch_bounds__(DW_THREADS, 1) k_dw_tc(DwArgs a)
         if (nkb > 0) ok = fz_wait(accf, 0u, abort_flag, a.status);
         if (ok) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // the partial in k_reduce_splits_dw's order: a warp's 32 rows of 4 columns
+            // the partial in k_reduce_dw's order: a warp's 32 rows of 4 columns
             // are 512 contiguous bytes
-            float4* dst = reinterpret_cast<float4*>(a.part + (size_t)blockIdx.y * a.M * a.N) +
-                          (size_t)(r >> 5) * (a.N >> 2) * 32 + (r & 31);
+            float4* dst = reinterpret_cast<float4*>(a.part + part_off + (size_t)split * M * N) +
+                          (size_t)(r >> 5) * (N >> 2) * 32 + (r & 31);
             for (int cb = 0; cb < DW_TN; cb += 16) {
                 uint32_t v[16];
                 tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)cb, v);
@@ -1301,42 +1326,91 @@ __global__ void k_reduce_splits(const float* __restrict__ part, int splits, size
         out[i] = t;
     }
 }
-// the same over partials stored in the weight-gradient kernel's order (an M x N
-// block as 32-row groups of 4-column groups, 32 rows x 4 values each): entry j
-// of a partial is element (m, n) of out, m = (j / (128 N/4)) * 32 + (j / 4) % 32,
-// n = ((j / 128) % (N / 4)) * 4 + j % 4; read in partial order, written to [M][N]
-// Blocks past those of the weights sum the bias partials bpart[split][M] into
-// bout[M] the same way (in order).
-__global__ void k_reduce_splits_dw(const float* __restrict__ part, int splits, int N, size_t count,
-                                   float* __restrict__ out, const float* __restrict__ bpart, int M,
-                                   float* __restrict__ bout)
+// the weight and bias gradients of every layer from k_dw_tc's partials, in one
+// launch.  A layer's weight partial j (of M N, per split) is element (m, n) of
+// its gradient, m = (j / (128 N/4)) * 32 + (j / 4) % 32, n = ((j / 128) % (N / 4))
+// * 4 + j % 4 (32-row groups of 4-column groups, 32 rows x 4 values each); its
+// bias partials are [split][M].  Block (32, 8) over 32 consecutive entries: warp
+// w adds the splits s = w, w + 8, w + 16, ... in order, then the eight warp sums
+// are added in warp order, so the result does not depend on timing.  With
+// loss_n > 0 the last block also sums the per-tile squared errors of the
+// training forward pass into the loss (in k_sum_partials' order).
+struct RedLayer {
+    long long part_off;  // weight partials at part + part_off, [split][M x N]
+    float* out;          // [M][N] weight gradient
+    float* bout;         // [M] bias gradient
+    int M, N, blk0, bpart_off;  // blocks blk0 .. : weights, then bias
+};
+struct RedArgs {
+    RedLayer ly[FZ_MAXL];
+    int nl, splits, nblk;
+    const float* part;
+    const float* bpart;
+    const float* loss_part;  // per-tile sums of squares, or null
+    int loss_n;
+    float loss_div;
+    float* loss_out;
+};
+
+__global__ void k_reduce_dw(RedArgs a)
 {
     __shared__ float red[8][32];
+    const int w = threadIdx.y, x = threadIdx.x;
+    if ((int)blockIdx.x >= a.nblk) {
+        // the loss: the same strided sums and tree as k_sum_partials
+        float* r = &red[0][0];
+        const int t = w * 32 + x;
+        float s = 0.f;
+        for (int i = t; i < a.loss_n; i += 256) s += a.loss_part[i];
+        r[t] = s;
+        __syncthreads();
+        for (int s2 = 128; s2 > 0; s2 >>= 1) {
+            if (t < s2) r[t] += r[t + s2];
+            __syncthreads();
+        }
+        if (t == 0) *a.loss_out = r[0] / a.loss_div;
+        return;
+    }
+    long long part_off = 0;
+    float *out = nullptr, *bout = nullptr;
+    int M = 0, N = 64, blk0 = 0, bpart_off = 0;
+#pragma unroll
+    for (int i = 0; i < FZ_MAXL; ++i)
+        if (i < a.nl && (int)blockIdx.x >= a.ly[i].blk0) {
+            part_off = a.ly[i].part_off;
+            out = a.ly[i].out;
+            bout = a.ly[i].bout;
+            M = a.ly[i].M;
+            N = a.ly[i].N;
+            blk0 = a.ly[i].blk0;
+            bpart_off = a.ly[i].bpart_off;
+        }
+    const size_t count = (size_t)M * N;
     const size_t wblocks = (count + 31) / 32;
-    if (blockIdx.x >= wblocks) {
-        const int i = (int)(blockIdx.x - wblocks) * 32 + threadIdx.x, w = threadIdx.y;
+    const size_t b = (size_t)blockIdx.x - blk0;
+    if (b >= wblocks) {
+        const int i = (int)(b - wblocks) * 32 + x;
         float s = 0.f;
         if (i < M)
-            for (int k = w; k < splits; k += 8) s += bpart[(size_t)k * M + i];
-        red[w][threadIdx.x] = s;
+            for (int k = w; k < a.splits; k += 8) s += a.bpart[bpart_off + (size_t)k * M + i];
+        red[w][x] = s;
         __syncthreads();
         if (w == 0 && i < M) {
-            float t = red[0][threadIdx.x];
-            for (int k = 1; k < 8; ++k) t += red[k][threadIdx.x];
+            float t = red[0][x];
+            for (int k = 1; k < 8; ++k) t += red[k][x];
             bout[i] = t;
         }
         return;
     }
-    const size_t j = (size_t)blockIdx.x * 32 + threadIdx.x;
-    const int w = threadIdx.y;
+    const size_t j = b * 32 + x;
     float s = 0.f;
     if (j < count)
-        for (int k = w; k < splits; k += 8) s += part[(size_t)k * count + j];
-    red[w][threadIdx.x] = s;
+        for (int k = w; k < a.splits; k += 8) s += a.part[part_off + (size_t)k * count + j];
+    red[w][x] = s;
     __syncthreads();
     if (w == 0 && j < count) {
-        float t = red[0][threadIdx.x];
-        for (int k = 1; k < 8; ++k) t += red[k][threadIdx.x];
+        float t = red[0][x];
+        for (int k = 1; k < 8; ++k) t += red[k][x];
         const size_t grp = j / 128;  // (32-row group, 4-column group)
         const int m = (int)(grp / (N / 4)) * 32 + (int)((j / 4) % 32), n = (int)(grp % (N / 4)) * 4 + (int)(j % 4);
         out[(size_t)m * N + n] = t;
@@ -1466,7 +1540,8 @@ struct lbib_mlp {
     unsigned char* pwT = nullptr;           // transposed chunks (backward chain), offsets pwoff
     long long pwoff[FZ_MAXL] = {};
     std::vector<__nv_bfloat16*> dzs;        // dZ_l of the hidden layers (tiled), fused backward
-    float* bpart = nullptr;                 // [split][out] bias-gradient partials of k_dw_tc
+    float* bpart = nullptr;                 // [split][out] bias-gradient partials of k_dw_tc, every layer
+    size_t bpart_floats = 0;
     bool pw_dirty = true;
     bool z_tiled = false;  // pre-activations stored tiled (zt_index) by the last forward pass
     bool fused = false;                     // network shape fits the fused kernel
@@ -1645,65 +1720,95 @@ cudaError_t backward_chain(lbib_mlp* net, int batch)
     return cudaGetLastError();
 }
 
+// every layer's weight and bias gradients on tcgen05 after the gradient chain,
+// with the loss of the fused forward pass: one k_dw_tc launch (all layers' 128 x
+// 64 output tiles times batch slices of whole 64-row blocks, about two CTAs per
+// SM) and one k_reduce_dw launch (the partials summed in a fixed order)
+cudaError_t gradients_tc(lbib_mlp* net, int batch)
+{
+    int T = 0;  // output tiles over all layers
+    for (int l = 0; l < net->L; ++l) T += (net->out[l] + TC_BM - 1) / TC_BM * (net->in[l] / DW_TN);
+    const int nsplit =
+        std::max(1, std::min(std::min(MAX_SPLITS, 2 * net->nsm / T), (batch + DW_KB - 1) / DW_KB));
+    const int rps = ((batch + nsplit - 1) / nsplit + DW_KB - 1) / DW_KB * DW_KB;
+    const int used = (batch + rps - 1) / rps;
+    DwArgs da{};
+    RedArgs ra{};
+    da.nl = ra.nl = net->L;
+    da.batch = batch;
+    da.rows_per_split = rps;
+    da.part = net->part;
+    da.bias_part = net->bpart;
+    da.status = net->status;
+    long long poff = 0;
+    int cta = 0, boff = 0, blk = 0;
+    for (int l = 0; l < net->L; ++l) {
+        const int M = net->out[l], N = net->in[l], tiles = (M + TC_BM - 1) / TC_BM * (N / DW_TN);
+        // dZ of the layer's pre-activation: the loss gradient for the output layer,
+        // the chain's result for the hidden ones
+        da.ly[l] = DwLayer{l + 1 == net->L ? net->dY : net->dzs[l], l == 0 ? net->a0 : net->act[l - 1], poff, M, N,
+                           tiles, cta, boff};
+        ra.ly[l] = RedLayer{poff, net->g + net->woff[l], net->g + net->boff[l], M, N, blk, boff};
+        poff += (long long)used * M * N;
+        boff += used * M;
+        cta += tiles * used;
+        blk += (int)(((size_t)M * N + 31) / 32 + (M + 31) / 32);
+    }
+    if ((size_t)poff > net->part_floats || (size_t)boff > net->bpart_floats) return cudaErrorInvalidValue;
+    k_dw_tc<<<cta, DW_THREADS, DW_SMEM, net->stream>>>(da);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ra.splits = used;
+    ra.nblk = blk;
+    ra.part = net->part;
+    ra.bpart = net->bpart;
+    ra.loss_part = net->loss_part;
+    ra.loss_n = (batch + TC_BM - 1) / TC_BM;
+    ra.loss_div = (float)batch * (float)net->desc.n_out;
+    ra.loss_out = net->loss_dev;
+    k_reduce_dw<<<blk + 1, dim3(32, 8), 0, net->stream>>>(ra);
+    return cudaGetLastError();
+}
+
 cudaError_t backward_core(lbib_mlp* net, int batch)
 {
     cudaError_t e = cudaSuccess;
     // after the fused forward pass (tiled pre-activations) the gradients of the
-    // pre-activations come from the tcgen05 chain, stored tiled
-    const bool chain = net->z_tiled;
-    if (chain && net->L > 1 && (e = backward_chain(net, batch)) != cudaSuccess) return e;
+    // pre-activations come from the tcgen05 chain, stored tiled, and the weight
+    // gradients from tensor-core products over batch slices
+    if (net->z_tiled) {
+        if (net->L > 1 && (e = backward_chain(net, batch)) != cudaSuccess) return e;
+        return gradients_tc(net, batch);
+    }
     const __nv_bfloat16* dcur = net->dY;  // gradient w.r.t. the current layer's output (pre-activation)
     int ldd = net->out[net->L - 1];
     const int splits = splits_for(batch);
     for (int l = net->L - 1; l >= 0 && e == cudaSuccess; --l) {
         const __nv_bfloat16* ain = (l == 0) ? net->a0 : net->act[l - 1];
         const int ldin = net->in[l];
-        if (chain) {
-            // dW_l = dcur^T ain on tcgen05: 128 x 64 output tiles times batch slices of
-            // whole 64-row blocks (about 96 CTAs), FP32 partials summed in a fixed order
-            const int tiles = (net->out[l] + TC_BM - 1) / TC_BM * (net->in[l] / DW_TN);
-            const int nsplit =
-                std::max(1, std::min(std::min(MAX_SPLITS, (96 + tiles - 1) / tiles), (batch + DW_KB - 1) / DW_KB));
-            const int rps = ((batch + nsplit - 1) / nsplit + DW_KB - 1) / DW_KB * DW_KB;
-            const int used = (batch + rps - 1) / rps;
-            DwArgs da{dcur, ain, net->out[l], net->in[l], batch, rps, net->part, net->bpart, net->status};
-            k_dw_tc<<<dim3(tiles, used), DW_THREADS, DW_SMEM, net->stream>>>(da);
-            e = cudaGetLastError();
-            if (e == cudaSuccess) {
-                // dW_l and db_l (the column sums of dcur, per split from the same kernel)
-                const size_t cnt = (size_t)net->out[l] * net->in[l];
-                const unsigned blocks = (unsigned)((cnt + 31) / 32 + (net->out[l] + 31) / 32);
-                k_reduce_splits_dw<<<blocks, dim3(32, 8), 0, net->stream>>>(net->part, used, net->in[l], cnt,
-                                                                           net->g + net->woff[l], net->bpart,
-                                                                           net->out[l], net->g + net->boff[l]);
-                e = cudaGetLastError();
-            }
+        // dW_l = dcur^T ain: M = out, N = in, K = batch; both operands batch-major
+        GemmArgs gw{};
+        gw.A = dcur;
+        gw.lda = ldd;
+        gw.B = ain;
+        gw.ldb = ldin;
+        gw.M = net->out[l];
+        gw.N = net->in[l];
+        gw.K = batch;
+        gw.part = net->part;
+        gw.ldc = net->in[l];
+        e = gemm<true, true, EPI_PARTIAL>(gw, splits, net->stream);
+        if (e != cudaSuccess) break;
+        {
+            const int kt = (batch + BK - 1) / BK;
+            const int tps = (kt + std::min(splits, kt) - 1) / std::min(splits, kt);
+            const int used = (kt + tps - 1) / tps;
+            const size_t cnt = (size_t)net->out[l] * net->in[l];
+            e = reduce_splits(net->part, used, cnt, net->g + net->woff[l], net->stream);
             if (e != cudaSuccess) break;
-        } else {
-            // dW_l = dcur^T ain: M = out, N = in, K = batch; both operands batch-major
-            GemmArgs gw{};
-            gw.A = dcur;
-            gw.lda = ldd;
-            gw.B = ain;
-            gw.ldb = ldin;
-            gw.M = net->out[l];
-            gw.N = net->in[l];
-            gw.K = batch;
-            gw.part = net->part;
-            gw.ldc = net->in[l];
-            e = gemm<true, true, EPI_PARTIAL>(gw, splits, net->stream);
-            if (e != cudaSuccess) break;
-            {
-                const int kt = (batch + BK - 1) / BK;
-                const int tps = (kt + std::min(splits, kt) - 1) / std::min(splits, kt);
-                const int used = (kt + tps - 1) / tps;
-                const size_t cnt = (size_t)net->out[l] * net->in[l];
-                e = reduce_splits(net->part, used, cnt, net->g + net->woff[l], net->stream);
-                if (e != cudaSuccess) break;
-            }
         }
         // db_l = column sums of dcur
-        if (!chain) {
+        {
             const int chunks = (batch + BIAS_ROWS - 1) / BIAS_ROWS;
             dim3 grid((ldd + 63) / 64, chunks);
             k_bias_partial<<<grid, dim3(32, 8), 0, net->stream>>>(dcur, ldd, batch, net->part);
@@ -1712,11 +1817,6 @@ cudaError_t backward_core(lbib_mlp* net, int batch)
         }
         e = cudaGetLastError();
         if (l == 0 || e != cudaSuccess) break;
-        if (chain) {
-            dcur = net->dzs[l - 1];
-            ldd = net->in[l];
-            continue;
-        }
         // d pre-activation of layer l-1 = (dcur W_l) * GELU'(z_{l-1}): M = batch, N = in_l, K = out_l
         __nv_bfloat16* dnext = (dcur == net->dZa) ? net->dZb : net->dZa;
         GemmArgs gx{};
@@ -1759,12 +1859,9 @@ cudaError_t prep_and_loss(lbib_mlp* net, const float* x, const float* t, int bat
     net->z_tiled = net->fused;  // the fused kernel stores what the backward pass reads tiled
     if (net->fused) {
         // one fused kernel: the inputs, every layer's pre-activations and activations,
-        // the loss gradient and the squared errors per row and column group
-        cudaError_t e = forward_fused(net, x, batch, net->yraw, t);
-        if (e != cudaSuccess) return e;
-        k_sum_partials<<<1, 256, 0, net->stream>>>(net->loss_part, (batch + TC_BM - 1) / TC_BM,
-                                                   (float)batch * (float)net->desc.n_out, net->loss_dev);
-        return cudaGetLastError();
+        // the loss gradient and the squared errors per tile (every caller runs
+        // backward_core next: its reduction launch sums the loss)
+        return forward_fused(net, x, batch, net->yraw, t);
     }
     dim3 blk(64, 4);
     k_prep_input<<<(batch + blk.y - 1) / blk.y, blk, 0, net->stream>>>(x, batch, net->desc.n_in, net->in[0],
@@ -1876,8 +1973,19 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
     const size_t wmax = (size_t)d->width * d->width;
     const int chunks = (int)((B + BIAS_ROWS - 1) / BIAS_ROWS);  // bias-gradient partials
     net->part_floats = std::max((size_t)MAX_SPLITS * wmax, (size_t)chunks * d->width);
+    cudaDeviceGetAttribute(&net->nsm, cudaDevAttrMultiProcessorCount, net->device);
+    {
+        // gradients_tc: at most max(2 SMs, output tiles) CTAs' 128 x 64 partials
+        size_t tiles = 0, outs = 0;
+        for (int l = 0; l < net->L; ++l) {
+            tiles += (size_t)(net->out[l] + TC_BM - 1) / TC_BM * (net->in[l] / DW_TN);
+            outs += (size_t)net->out[l];
+        }
+        net->part_floats = std::max(net->part_floats, std::max((size_t)2 * net->nsm, tiles) * TC_BM * DW_TN);
+        net->bpart_floats = (size_t)MAX_SPLITS * outs;
+    }
     MA(net->part, net->part_floats);
-    MA(net->loss_part, BT * 4);  // per row and column group (fused), per block otherwise
+    MA(net->loss_part, BT * 4);  // per tile (fused), per block of 4 rows otherwise
     MA(net->loss_dev, 1);
     MA(net->status, 1);
     MA(net->pidx, net->ntrue);
@@ -1888,7 +1996,7 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
             MA(dz, (B + TC_BM - 1) / TC_BM * TC_BM * d->width);
             net->dzs.push_back(dz);
         }
-        MA(net->bpart, (size_t)MAX_SPLITS * std::max(d->width, 64));
+        MA(net->bpart, net->bpart_floats);
     }
     if (net->fused) {
         size_t bytes = 0;
@@ -1900,7 +2008,6 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
         MA(net->pwT, bytes);
     }
 #undef MA
-    cudaDeviceGetAttribute(&net->nsm, cudaDevAttrMultiProcessorCount, net->device);
     // shared-memory opt-ins are per device: set them here, with the net's device current
     if ((e = cudaFuncSetAttribute(k_gemm_tc<EPI_FWD_GELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)TC_SMEM_REQUEST)) != cudaSuccess ||
