@@ -1327,18 +1327,39 @@ __global__ void k_reduce_splits(const float* __restrict__ part, int splits, size
     }
 }
 // the weight and bias gradients of every layer from k_dw_tc's partials, in one
-// launch.  A layer's weight partial j (of M N, per split) is element (m, n) of
-// its gradient, m = (j / (128 N/4)) * 32 + (j / 4) % 32, n = ((j / 128) % (N / 4))
-// * 4 + j % 4 (32-row groups of 4-column groups, 32 rows x 4 values each); its
-// bias partials are [split][M].  Block (32, 8) over 32 consecutive entries: warp
-// w adds the splits s = w, w + 8, w + 16, ... in order, then the eight warp sums
-// are added in warp order, so the result does not depend on timing.  With
-// loss_n > 0 the last block also sums the per-tile squared errors of the
-// training forward pass into the loss (in k_sum_partials' order).
+// launch of 256-thread blocks.  A layer's weight partial j (of M N, per split) is
+// element (m, n) of its gradient, m = (j / (128 N/4)) * 32 + (j / 4) % 32,
+// n = ((j / 128) % (N / 4)) * 4 + j % 4 (32-row groups of 4-column groups, 32
+// rows x 4 values each); its bias partials are [split][M].  Thread j adds the
+// splits s = 0, 1, 2, ... in order (consecutive threads read consecutive
+// partials), so the result does not depend on timing.  With loss_n > 0 the last
+// block also sums the per-tile squared errors of the training forward pass into
+// the loss (in k_sum_partials' order).
+// one Adam step (bias-corrected, beta 0.9 / 0.999, eps 1e-8) of parameter i on the
+// FP32 masters with gradient g, every operation explicitly rounded so that every
+// kernel that applies it gives the same bits; returns the new BF16 copy
+__device__ __forceinline__ __nv_bfloat16 adam_update(float* __restrict__ p, float* __restrict__ m,
+                                                     float* __restrict__ v, __nv_bfloat16* __restrict__ pb, size_t i,
+                                                     float g, float lr, float c1, float c2)
+{
+    const float mi = __fmaf_rn(0.9f, m[i], __fmul_rn(0.1f, g));
+    const float vi = __fmaf_rn(0.999f, v[i], __fmul_rn(__fmul_rn(0.001f, g), g));
+    m[i] = mi;
+    v[i] = vi;
+    const float upd =
+        __fdiv_rn(__fmul_rn(lr, __fdiv_rn(mi, c1)), __fadd_rn(__fsqrt_rn(__fdiv_rn(vi, c2)), 1e-8f));
+    const float pn = __fsub_rn(p[i], upd);
+    p[i] = pn;
+    const __nv_bfloat16 q = __float2bfloat16_rn(pn);
+    pb[i] = q;
+    return q;
+}
+
+constexpr int RED_THREADS = 256;
 struct RedLayer {
-    long long part_off;  // weight partials at part + part_off, [split][M x N]
-    float* out;          // [M][N] weight gradient
-    float* bout;         // [M] bias gradient
+    long long part_off;       // weight partials at part + part_off, [split][M x N]
+    long long woff, boff;     // the layer's weights ([M][N]) and biases in the flat parameters
+    long long pwoff;          // its chunks in the packed copies
     int M, N, blk0, bpart_off;  // blocks blk0 .. : weights, then bias
 };
 struct RedArgs {
@@ -1346,74 +1367,82 @@ struct RedArgs {
     int nl, splits, nblk;
     const float* part;
     const float* bpart;
+    float* g;                // gradients (flat parameter layout)
     const float* loss_part;  // per-tile sums of squares, or null
     int loss_n;
     float loss_div;
     float* loss_out;
+    // with p set, the Adam step of every parameter follows its gradient
+    // (adam_update), and with pw set the packed weight copies (forward pw,
+    // transposed pwT, layout of k_pack_fused) get the new BF16 values too
+    float *p, *m, *v;
+    __nv_bfloat16* pb;
+    float lr, c1, c2;
+    unsigned char *pw, *pwT;
 };
 
-__global__ void k_reduce_dw(RedArgs a)
+__global__ void __launch_bounds__(RED_THREADS) k_reduce_dw(RedArgs a)
 {
-    __shared__ float red[8][32];
-    const int w = threadIdx.y, x = threadIdx.x;
+    const int t = threadIdx.x;
     if ((int)blockIdx.x >= a.nblk) {
         // the loss: the same strided sums and tree as k_sum_partials
-        float* r = &red[0][0];
-        const int t = w * 32 + x;
+        __shared__ float r[RED_THREADS];
         float s = 0.f;
-        for (int i = t; i < a.loss_n; i += 256) s += a.loss_part[i];
+        for (int i = t; i < a.loss_n; i += RED_THREADS) s += a.loss_part[i];
         r[t] = s;
         __syncthreads();
-        for (int s2 = 128; s2 > 0; s2 >>= 1) {
+        for (int s2 = RED_THREADS / 2; s2 > 0; s2 >>= 1) {
             if (t < s2) r[t] += r[t + s2];
             __syncthreads();
         }
         if (t == 0) *a.loss_out = r[0] / a.loss_div;
         return;
     }
-    long long part_off = 0;
-    float *out = nullptr, *bout = nullptr;
+    long long part_off = 0, woff = 0, boff = 0, pwoff = 0;
     int M = 0, N = 64, blk0 = 0, bpart_off = 0;
 #pragma unroll
     for (int i = 0; i < FZ_MAXL; ++i)
         if (i < a.nl && (int)blockIdx.x >= a.ly[i].blk0) {
             part_off = a.ly[i].part_off;
-            out = a.ly[i].out;
-            bout = a.ly[i].bout;
+            woff = a.ly[i].woff;
+            boff = a.ly[i].boff;
+            pwoff = a.ly[i].pwoff;
             M = a.ly[i].M;
             N = a.ly[i].N;
             blk0 = a.ly[i].blk0;
             bpart_off = a.ly[i].bpart_off;
         }
     const size_t count = (size_t)M * N;
-    const size_t wblocks = (count + 31) / 32;
+    const size_t wblocks = (count + RED_THREADS - 1) / RED_THREADS;
     const size_t b = (size_t)blockIdx.x - blk0;
     if (b >= wblocks) {
-        const int i = (int)(b - wblocks) * 32 + x;
-        float s = 0.f;
-        if (i < M)
-            for (int k = w; k < a.splits; k += 8) s += a.bpart[bpart_off + (size_t)k * M + i];
-        red[w][x] = s;
-        __syncthreads();
-        if (w == 0 && i < M) {
-            float t = red[0][x];
-            for (int k = 1; k < 8; ++k) t += red[k][x];
-            bout[i] = t;
+        const int i = (int)(b - wblocks) * RED_THREADS + t;
+        if (i < M) {
+            const float* q = a.bpart + bpart_off + i;
+            float s = 0.f;
+            for (int k = 0; k < a.splits; ++k) s += q[(size_t)k * M];
+            a.g[boff + i] = s;
+            if (a.p) adam_update(a.p, a.m, a.v, a.pb, (size_t)(boff + i), s, a.lr, a.c1, a.c2);
         }
         return;
     }
-    const size_t j = b * 32 + x;
-    float s = 0.f;
-    if (j < count)
-        for (int k = w; k < a.splits; k += 8) s += a.part[part_off + (size_t)k * count + j];
-    red[w][x] = s;
-    __syncthreads();
-    if (w == 0 && j < count) {
-        float t = red[0][x];
-        for (int k = 1; k < 8; ++k) t += red[k][x];
+    const size_t j = b * RED_THREADS + t;
+    if (j < count) {
+        const float* q = a.part + part_off + j;
+        float s = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < a.splits; ++k) s += q[(size_t)k * count];
         const size_t grp = j / 128;  // (32-row group, 4-column group)
         const int m = (int)(grp / (N / 4)) * 32 + (int)((j / 4) % 32), n = (int)(grp % (N / 4)) * 4 + (int)(j % 4);
-        out[(size_t)m * N + n] = t;
+        const size_t i = (size_t)woff + (size_t)m * N + n;
+        a.g[i] = s;
+        if (a.p) {
+            const __nv_bfloat16 q = adam_update(a.p, a.m, a.v, a.pb, i, s, a.lr, a.c1, a.c2);
+            if (a.pw) {
+                *reinterpret_cast<__nv_bfloat16*>(a.pw + pwoff + fz_chunk_offset(m, n, M)) = q;
+                *reinterpret_cast<__nv_bfloat16*>(a.pwT + pwoff + fz_chunk_offset(n, m, N)) = q;
+            }
+        }
     }
 }
 
@@ -1438,15 +1467,7 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ gr, floa
 {
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float g = gr[i];
-    const float mi = 0.9f * m[i] + 0.1f * g, vi = 0.999f * v[i] + 0.001f * g * g;
-    m[i] = mi;
-    v[i] = vi;
-    const float upd = lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
-    const float pn = p[i] - upd;
-    p[i] = pn;
-    const __nv_bfloat16 q = __float2bfloat16_rn(pn);
-    pb[i] = q;
+    const __nv_bfloat16 q = adam_update(p, m, v, pb, i, gr[i], lr, c1, c2);
     // the same value into the fused kernel's packed weight chunks (layout of k_pack_fused)
     if (pk.pw)
         for (int l = 0; l < pk.L; ++l) {
@@ -1720,11 +1741,17 @@ cudaError_t backward_chain(lbib_mlp* net, int batch)
     return cudaGetLastError();
 }
 
+// an optimiser step to apply with the gradients (lr, bias corrections)
+struct AdamStep {
+    float lr, c1, c2;
+};
+
 // every layer's weight and bias gradients on tcgen05 after the gradient chain,
 // with the loss of the fused forward pass: one k_dw_tc launch (all layers' 128 x
 // 64 output tiles times batch slices of whole 64-row blocks, about two CTAs per
-// SM) and one k_reduce_dw launch (the partials summed in a fixed order)
-cudaError_t gradients_tc(lbib_mlp* net, int batch)
+// SM) and one k_reduce_dw launch (the partials summed in a fixed order, and the
+// Adam step when st is given)
+cudaError_t gradients_tc(lbib_mlp* net, int batch, const AdamStep* st)
 {
     int T = 0;  // output tiles over all layers
     for (int l = 0; l < net->L; ++l) T += (net->out[l] + TC_BM - 1) / TC_BM * (net->in[l] / DW_TN);
@@ -1748,11 +1775,11 @@ cudaError_t gradients_tc(lbib_mlp* net, int batch)
         // the chain's result for the hidden ones
         da.ly[l] = DwLayer{l + 1 == net->L ? net->dY : net->dzs[l], l == 0 ? net->a0 : net->act[l - 1], poff, M, N,
                            tiles, cta, boff};
-        ra.ly[l] = RedLayer{poff, net->g + net->woff[l], net->g + net->boff[l], M, N, blk, boff};
+        ra.ly[l] = RedLayer{poff, (long long)net->woff[l], (long long)net->boff[l], net->pwoff[l], M, N, blk, boff};
         poff += (long long)used * M * N;
         boff += used * M;
         cta += tiles * used;
-        blk += (int)(((size_t)M * N + 31) / 32 + (M + 31) / 32);
+        blk += (int)(((size_t)M * N + RED_THREADS - 1) / RED_THREADS + (M + RED_THREADS - 1) / RED_THREADS);
     }
     if ((size_t)poff > net->part_floats || (size_t)boff > net->bpart_floats) return cudaErrorInvalidValue;
     k_dw_tc<<<cta, DW_THREADS, DW_SMEM, net->stream>>>(da);
@@ -1766,11 +1793,28 @@ cudaError_t gradients_tc(lbib_mlp* net, int batch)
     ra.loss_n = (batch + TC_BM - 1) / TC_BM;
     ra.loss_div = (float)batch * (float)net->desc.n_out;
     ra.loss_out = net->loss_dev;
-    k_reduce_dw<<<blk + 1, dim3(32, 8), 0, net->stream>>>(ra);
+    ra.g = net->g;
+    if (st) {
+        ra.p = net->p;
+        ra.m = net->m;
+        ra.v = net->v;
+        ra.pb = net->pb;
+        ra.lr = st->lr;
+        ra.c1 = st->c1;
+        ra.c2 = st->c2;
+        // a packed copy that is current stays current: the update writes it too
+        ra.pw = (net->fused && !net->pw_dirty) ? net->pw : nullptr;
+        ra.pwT = net->pwT;
+    }
+    k_reduce_dw<<<blk + 1, RED_THREADS, 0, net->stream>>>(ra);
     return cudaGetLastError();
 }
 
-cudaError_t backward_core(lbib_mlp* net, int batch)
+PackTab pack_tab(const lbib_mlp* net);
+
+// the gradients of the loss of the last prep_and_loss into net->g, then, with
+// st, the Adam step
+cudaError_t backward_core(lbib_mlp* net, int batch, const AdamStep* st = nullptr)
 {
     cudaError_t e = cudaSuccess;
     // after the fused forward pass (tiled pre-activations) the gradients of the
@@ -1778,7 +1822,7 @@ cudaError_t backward_core(lbib_mlp* net, int batch)
     // gradients from tensor-core products over batch slices
     if (net->z_tiled) {
         if (net->L > 1 && (e = backward_chain(net, batch)) != cudaSuccess) return e;
-        return gradients_tc(net, batch);
+        return gradients_tc(net, batch, st);
     }
     const __nv_bfloat16* dcur = net->dY;  // gradient w.r.t. the current layer's output (pre-activation)
     int ldd = net->out[net->L - 1];
@@ -1833,6 +1877,11 @@ cudaError_t backward_core(lbib_mlp* net, int batch)
         e = gemm<false, true, EPI_BWD_GELU>(gx, 1, net->stream);
         dcur = dnext;
         ldd = net->in[l];
+    }
+    if (e == cudaSuccess && st) {
+        k_adam<<<(unsigned)((net->nparam + 255) / 256), 256, 0, net->stream>>>(
+            net->p, net->g, net->m, net->v, net->pb, net->nparam, st->lr, st->c1, st->c2, pack_tab(net));
+        e = cudaGetLastError();
     }
     return e;
 }
@@ -2125,16 +2174,10 @@ lbib_status lbib_mlp_train_step(lbib_mlp* net, const float* x, const float* t, i
     if (!(lr > 0.f) || !std::isfinite(lr)) return mlp_fail(LBIB_ERR_INVALID_ARG, "lr must be positive");
     Guard guard(net->device);
     cudaError_t e = prep_and_loss(net, x, t, batch);
-    if (e == cudaSuccess) e = backward_core(net, batch);
-    if (e == cudaSuccess) {
-        net->t += 1;
-        const float c1 = 1.0f - (float)std::pow(0.9, (double)net->t);
-        const float c2 = 1.0f - (float)std::pow(0.999, (double)net->t);
-        // a packed copy that is current stays current: the update writes it too
-        k_adam<<<(unsigned)((net->nparam + 255) / 256), 256, 0, net->stream>>>(net->p, net->g, net->m, net->v, net->pb,
-                                                                               net->nparam, lr, c1, c2, pack_tab(net));
-        e = cudaGetLastError();
-    }
+    const int64_t step = net->t + 1;
+    const AdamStep st{lr, 1.0f - (float)std::pow(0.9, (double)step), 1.0f - (float)std::pow(0.999, (double)step)};
+    if (e == cudaSuccess) e = backward_core(net, batch, &st);
+    if (e == cudaSuccess) net->t = step;
     if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, net->loss_dev, 4, cudaMemcpyDeviceToDevice, net->stream);
     if (e != cudaSuccess) return mlp_fail(LBIB_ERR_CUDA, std::string("lbib_mlp_train_step: ") + cudaGetErrorString(e));
     return LBIB_OK;
