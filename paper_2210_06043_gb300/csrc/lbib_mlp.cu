@@ -1430,7 +1430,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_dw(RedArgs a)
     if (j < count) {
         const float* q = a.part + part_off + j;
         float s = 0.f;
-#pragma unroll 4
+#pragma unroll 8
         for (int k = 0; k < a.splits; ++k) s += q[(size_t)k * count];
         const size_t grp = j / 128;  // (32-row group, 4-column group)
         const int m = (int)(grp / (N / 4)) * 32 + (int)((j / 4) % 32), n = (int)(grp % (N / 4)) * 4 + (int)(j % 4);

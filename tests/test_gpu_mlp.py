@@ -89,6 +89,38 @@ def test_gradients_match_quantized_oracle_and_repeat_exactly(B):
     net.close()
 
 
+# other shapes through the same tensor-core training path: width 64 (one output
+# tile per layer), 192 (a 64-row second tile and three column tiles), eight
+# hidden layers; a batch of one row, and ragged ones
+@pytest.mark.parametrize("width,hidden,B", [(64, 1, 1), (192, 2, 333), (128, 8, 2500)])
+def test_gradients_of_other_shapes(width, hidden, B):
+    rng = np.random.default_rng(width + hidden)
+    norm = _norm(rng)
+    net = lbib.Mlp(N_IN, N_OUT, width=width, n_hidden=hidden, max_batch=4096, seed=3,
+                   stream=torch.cuda.current_stream().cuda_stream,
+                   in_shift=norm["c_in"], in_scale=norm["s_in"], out_shift=norm["c_out"], out_scale=norm["s_out"])
+    x = rng.uniform(-1, 1, (B, N_IN)).astype(np.float32)
+    t = (rng.normal(0, 1, (B, N_OUT)) * norm["s_out"] + norm["c_out"]).astype(np.float32)
+    xd, td = _dev(x), _dev(t)
+    g1, l1 = net.gradients(xd.data_ptr(), td.data_ptr(), B)
+    g2, l2 = net.gradients(xd.data_ptr(), td.data_ptr(), B)
+    assert np.array_equal(g1, g2) and l1 == l2
+    layers = omlp.split_params(net.get_params(), N_IN, width, hidden, N_OUT)
+    lo, go = omlp.gradients(layers, x, t, quantize=True, **norm)
+    assert abs(l1 - lo) <= 1e-3 * lo
+    k = 0
+    for (dW, db) in go:
+        gw = g1[k:k + dW.size].reshape(dW.shape)
+        k += dW.size
+        gb = g1[k:k + db.size]
+        k += db.size
+        # one row: a flipped bf16 rounding is not averaged out over the batch
+        tol = 6e-2 if B == 1 else 2e-2
+        assert _rel(gw, dW) < tol and _rel(gb, db) < tol
+    assert k == g1.size
+    net.close()
+
+
 def test_training_fits_a_smooth_function():
     rng = np.random.default_rng(2)
     norm = dict(c_in=np.zeros(N_IN, np.float32), s_in=np.ones(N_IN, np.float32),
