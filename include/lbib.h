@@ -11,7 +11,7 @@
  *   2. moments with the half-force shift (Eqs. 5-6) and BGK collision with the
  *      Hermite equilibrium and Guo's forcing term (Eqs. 1, 2, 4);
  *   3. the Lagrangian update of every membrane from that velocity: Peskin or
- *      moving-least-squares interpolation (Sec. 2.2, Sec. 2.9; lbib_transfer),
+ *      moving-least-squares interpolation (Sec. 2.2, Sec. 2.8; lbib_transfer),
  *      ligand-receptor kinetics and force
  *      (Sec. 2.5, Eq. 13), membrane forces (Eqs. 8, 10, 11), repulsion
  *      (Eq. 12), probe tractions (Eqs. 14-15), Verlet + BDF2 (Eqs. 17-18) or

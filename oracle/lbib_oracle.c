@@ -19,7 +19,7 @@
  *   3. BGK collision with the Hermite equilibrium and Guo's forcing term
  *      (Eqs. 1, 2, 4);
  *   4. the Lagrangian update from the velocity of step 2: interpolation at
- *      the vertices (Sec. 2.9), probes for pressure and velocity gradients
+ *      the vertices (Sec. 2.8), probes for pressure and velocity gradients
  *      (Sec. 2.6), ligand-receptor kinetics and force (Eq. 13), membrane
  *      forces (Eqs. 8, 10, 11), repulsion (Eq. 12), tractions (Eqs. 14-15),
  *      Verlet + BDF2 (Eqs. 17-18) or rigid BDF2 (Eq. 19);
@@ -824,7 +824,7 @@ int orc_add_body(orc_sim* s, int kind, int motion, int nv, const double* xy, con
     b->kb = beta * b->ks;
     b->ka = ka;
     b->rho_b = density_ratio;
-    b->mv = density_ratio * b->A0 / nv; /* Sec. 2.9: mass spread evenly on the vertices */
+    b->mv = density_ratio * b->A0 / nv; /* Sec. 2.8: mass spread evenly on the vertices */
     orc_polygon(nv, b->x, b->y, poly);
     b->mass = density_ratio * poly[0];
     b->inertia = density_ratio * poly[4];

@@ -6,7 +6,7 @@
 // its near tiles), for the block's body, in this order:
 //   1. chain geometry at X^n: edges, lengths, outward element normals, vertex
 //      normals and signed turning angles; shoelace area in FP64;
-//   2. fluid velocity at the vertices (Sec. 2.9) with the truncated Peskin
+//   2. fluid velocity at the vertices (Sec. 2.8) with the truncated Peskin
 //      stencil; pressure and velocity gradient at a probe 1.2 dx along each
 //      element normal, stopped at a wall it would cross (Sec. 2.6);
 //   3. ligand-receptor kinetics from Philox4x32-10 draws keyed on (seed;

@@ -1,5 +1,5 @@
 """Pins of the oracle's immersed-boundary pieces: Peskin's discrete delta,
-interpolation and spreading (Sec. 2.2, Sec. 2.9) and the element tractions of
+interpolation and spreading (Sec. 2.2, Sec. 2.8) and the element tractions of
 Eqs. 14-15 with the 1.2 dx probe of Sec. 2.6.  CPU only."""
 import os
 

@@ -1,5 +1,5 @@
 """Pins of three oracle pieces that the GPU comparison alone cannot vouch for:
-the deformable vertex update (Eqs. 17-18, Sec. 2.9), explicit direct forcing
+the deformable vertex update (Eqs. 17-18, Sec. 2.8), explicit direct forcing
 (Sec. 2.2, the reading: F_L = rho (U_struct - U*) / dt at the element
 centroids, spread with weight ds = element length) and the distribution of
 the bending force over a hinge (Eq. 10, Sec. 2.3).  Every expected value is
@@ -25,7 +25,7 @@ def _polygon_area(xy):
     return 0.5 * float(np.sum(x * np.roll(y, -1) - np.roll(x, -1) * y))
 
 
-# ------------------------------------------------------- Eqs. 17-18 (Sec. 2.9)
+# ------------------------------------------------------- Eqs. 17-18 (Sec. 2.8)
 
 def _displaced_cell(nx=64, ny=64, nv=32, R=10.0, delta=0.05, tau=1.0, re=0.5, ca=1e-3, rho_b=1.0):
     """A stress-free regular polygon in fluid at rest with vertex 0 pushed out
@@ -38,7 +38,7 @@ def _displaced_cell(nx=64, ny=64, nv=32, R=10.0, delta=0.05, tau=1.0, re=0.5, ca
     s = oracle.OracleSim(nx, ny, tau=tau, re=re, bc=oracle.BC_PERIODIC_FORCE)
     s.add_body(oracle.CELL, oracle.DEFORMABLE, xy, xy_ref=ref, ca=ca, beta=0.0, ka=0.0, density_ratio=rho_b)
     # hand-computed constants: u_max = Re nu / H (Sec. 3.1), k_s = rho nu u_max / Ca
-    # (Sec. 3.1), m_v = rho_body A_0 / nv (Sec. 2.9) with A_0 the regular polygon's area
+    # (Sec. 3.1), m_v = rho_body A_0 / nv (Sec. 2.8) with A_0 the regular polygon's area
     nu = _nu(tau)
     umax = re * nu / ny
     ks = nu * umax / ca
