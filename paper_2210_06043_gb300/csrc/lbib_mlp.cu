@@ -586,9 +586,9 @@ struct FusedArgs {
     const float *cin, *sin, *cout, *sout;
     uint32_t* status;
     // a training forward pass (k_mlp_fused<FZ_TRAIN>): layer l's pre-activations and
-    // activations to zout[l], aout[l] (tiled: zt_index, at_index), the output
-    // layer's raw values y_raw = W a + b to y ([M][N_{L-1}]) instead of the
-    // scaled outputs.  The backward chain (k_mlp_fused<FZ_BWD>): step s reads the
+    // activations to zout[l], aout[l] (tiled: zt_index, at_index); the output
+    // layer's raw values y_raw = W a + b go only into the loss gradient and the
+    // squared errors below (nothing is written to y).  The backward chain (k_mlp_fused<FZ_BWD>): step s reads the
     // pre-activations zout[s] of its output width N[s] and writes the gradient
     // aout[s] = bf16(acc * GELU'(z)) (tiled), starting from dy ([M][K[0]] BF16).
     float* zout[FZ_MAXL];
