@@ -3,6 +3,12 @@
 Each translation unit is compiled in parallel; the result is linked as a
 shared library with the static CUDA runtime, so it loads into any process
 (PyTorch's or not) that has the driver.
+
+``build(checked=True)`` makes the bounds-checked debug build
+``liblbib_checked.so`` (``-DLBIB_CHECKED``): the kernels' population, node,
+tile and marker indices are checked against their arrays, an index outside
+sets a status bit that the next sync reports as LBIB_ERR_STATE, and the access
+is redirected to the array's first element (nothing traps).
 """
 from __future__ import annotations
 
@@ -15,6 +21,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbib.so")
+LIB_CHECKED = os.path.join(OUT_DIR, "liblbib_checked.so")
 SOURCES = ("lbib_api.cu", "lbib_lbm.cu", "lbib_lag.cu", "lbib_lag_mls.cu", "lbib_noalloc.cu", "lbib_mlp.cu")
 HEADERS = ("lbib_internal.cuh", "lbib_device.cuh", "lbib_lag_kernel.cuh")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
@@ -27,10 +34,10 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found (CUDA toolkit required to build liblbib)")
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
     deps.append(os.path.join(HERE, "..", "include", "lbib.h"))
     deps.append(os.path.join(HERE, "..", "include", "lbib_mlp.h"))
@@ -42,13 +49,17 @@ def flags(extra=()):
     return ["-O3", ARCH, "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-O3", *extra]
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile (if stale) and return the path of liblbib.so."""
-    if not force and not _stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+    """Compile (if stale) and return the path of liblbib.so (liblbib_checked.so
+    with ``checked``)."""
+    lib = LIB_CHECKED if checked else LIB
+    if checked:
+        extra = (*extra, "-DLBIB_CHECKED")
+    if not force and not _stale(lib):
+        return lib
     os.makedirs(OUT_DIR, exist_ok=True)
     cc = nvcc()
-    tag = f"{os.getpid()}"
+    tag = f"{os.getpid()}{'c' if checked else ''}"
     objs = []
 
     def compile_one(src):
@@ -73,17 +84,17 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
                 o = os.path.join(OUT_DIR, src.replace(".cu", f".{tag}.o"))
                 if os.path.exists(o):
                     os.remove(o)
-    tmp = LIB + f".{tag}.tmp"
+    tmp = lib + f".{tag}.tmp"
     r = subprocess.run([cc, "-shared", ARCH, "-o", tmp, *objs], capture_output=True, text=True)
     for o in objs:
         os.remove(o)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
 
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -282,6 +282,7 @@ lbib_status check_status(lbib_ctx* ctx)
         return fail(ctx, LBIB_ERR_STATE, "an interpolation stencil left the tiles updated as near-membrane");
     if (st & ST_SPREAD_MISS)
         return fail(ctx, LBIB_ERR_STATE, "a spreading stencil left the tiles scheduled as near-membrane");
+    if (st & ST_BOUNDS) return fail(ctx, LBIB_ERR_STATE, "an index left its array (bounds-checked build)");
     if (st & ST_TMA_TIMEOUT) {
         ctx->fault = LBIB_ERR_TIMEOUT;
         return fail(ctx, LBIB_ERR_TIMEOUT, "a bulk-update block gave up waiting for a tensor copy");
@@ -855,6 +856,9 @@ lbib_status create_impl(const lbib_fluid_params* P, int32_t ninst, const int32_t
     ar.add(&ctx->colinfo, cols.size());
     ar.add(&ctx->inst, (size_t)ninst);
     CKC(ar.commit(ctx->stream_allocs, ctx->stream));
+#ifdef LBIB_CHECKED
+    L.chk_status = d.status;
+#endif
     d.colinfo = ctx->colinfo;
     d.inst = ctx->inst;
     CKC(cudaMemcpyAsync(ctx->colinfo, cols.data(), cols.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));

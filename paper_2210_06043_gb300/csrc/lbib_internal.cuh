@@ -48,7 +48,25 @@ enum : uint32_t {
     ST_SPREAD_MISS = 4u,    // a spreading stencil reached a tile not scheduled as near
     ST_LIST_OVERFLOW = 8u,  // near-tile list capacity exceeded
     ST_TMA_TIMEOUT = 16u,   // a bulk-update block gave up waiting for a tensor copy
+    ST_BOUNDS = 32u,        // bounds-checked build only: an index left its array
 };
+
+// Bounds-checked debug build (compiled with -DLBIB_CHECKED): LBIB_IDX(i, n, st)
+// is i when 0 <= i < n; otherwise it sets ST_BOUNDS in the status word st and
+// gives 0, so the access lands on the array's first element instead of outside
+// it (nothing traps: the host reads the bit at the next sync).  In the normal
+// build it is i, and st is not evaluated.
+#ifdef LBIB_CHECKED
+__device__ __forceinline__ long long lbib_idx(long long i, long long n, uint32_t* st)
+{
+    if (i >= 0 && i < n) return i;
+    atomicOr(st, (uint32_t)ST_BOUNDS);
+    return 0;
+}
+#define LBIB_IDX(i, n, st) lbib_idx((long long)(i), (long long)(n), (st))
+#else
+#define LBIB_IDX(i, n, st) (i)
+#endif
 
 enum { PREC_F64 = 0, PREC_F32 = 1 };  // compute type of the kernels
 
@@ -77,6 +95,9 @@ struct Lattice {
     // kernel's register allocation (40 -> 48 at two nodes per thread), which
     // cost 3.5 % of the step
     int transfer;             // lbib_transfer
+#ifdef LBIB_CHECKED
+    uint32_t* chk_status;     // the context's status word (LBIB_IDX)
+#endif
 };
 
 // Lattice parameter in the compute type R: the double for R = double, the

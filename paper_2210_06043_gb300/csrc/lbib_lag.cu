@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256) k_activate_next(Dev d)
         if (i0 > i1 || j0 > j1) continue;
         for (int ty = j0 / TY; ty <= j1 / TY; ++ty)
             for (int tx = i0 / TX; tx <= i1 / TX; ++tx) {
-                const int t = ty * L.ntx + tx;
+                const int t = (int)LBIB_IDX(ty * L.ntx + tx, L.ntiles, L.chk_status);
                 if (flag[t] == 0u && atomicExch(&flag[t], 1u) == 0u) {
                     const int pos = atomicAdd(&d.count[c], 1);
                     if (pos < d.list_cap) d.list[c][pos] = t;

@@ -245,11 +245,11 @@ __device__ __forceinline__ void sample_group(const Dev& d, const Spot<R>& sp, in
         else py[k] = peskin<R>(ry);
         if (!vj) py[k] = dpy[k] = R(0);
         // the row's nodes lie in at most two tiles: both must hold step m
-        fr[2 * k] = d.fresh[tile_of(L, ic[0], jc[k])];
-        fr[2 * k + 1] = d.fresh[tile_of(L, ic[3], jc[k])];
+        fr[2 * k] = d.fresh[LBIB_IDX(tile_of(L, ic[0], jc[k]), L.ntiles, L.chk_status)];
+        fr[2 * k + 1] = d.fresh[LBIB_IDX(tile_of(L, ic[3], jc[k]), L.ntiles, L.chk_status)];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            const int idx = jc[k] * L.nxp + ic[a];
+            const int idx = (int)LBIB_IDX(jc[k] * L.nxp + ic[a], L.qstride, L.chk_status);
             a_u[4 * k + a] = ux[idx];
             a_v[4 * k + a] = uy[idx];
             a_r[4 * k + a] = dr[idx];
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(T) k_lagrangian(Dev d, int p)
         const int cnt = min(d.count[c0], d.list_cap);
         uint32_t* f0 = d.nearflag[c0];
         const int32_t* l0 = d.list[c0];
-        for (int k = blockIdx.x * T + tid; k < cnt; k += gridDim.x * T) f0[l0[k]] = 0u;
+        for (int k = blockIdx.x * T + tid; k < cnt; k += gridDim.x * T) f0[LBIB_IDX(l0[k], L.ntiles, L.chk_status)] = 0u;
     }
 
     // 0. one round of global loads; positions to float-float pairs; the FP64
@@ -786,7 +786,7 @@ __global__ void __launch_bounds__(T) k_lagrangian(Dev d, int p)
             Fx = rho * (usx - o.u);
             Fy = rho * (usy - o.v);
         }
-        const int g = off + l;
+        const int g = (int)LBIB_IDX(off + l, NM, L.chk_status);
         if (lane4 == 0) {
             mki[g] = B.x0 + sc.ix;  // lattice column of the stencil origin
             mki[NM + g] = sc.jy;

@@ -71,23 +71,24 @@ __device__ __forceinline__ void pull(const Lattice& L, const S* __restrict__ fin
     const int qs = L.qstride, nxp = L.nxp;
     if (xl > 0 && xl < nxi - 1 && y > 0 && y < L.ny - 1) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) g[q] = ld<S, R>(fin + q * qs + (y - cy(q)) * nxp + (x - cx(q)));
+        for (int q = 0; q < 9; ++q)
+            g[q] = ld<S, R>(fin + LBIB_IDX(q * qs + (y - cy(q)) * nxp + (x - cx(q)), 9LL * qs, L.chk_status));
         return;
     }
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
         int xs = xl - cx(q), ys = y - cy(q);
         if (ys < 0 || ys >= L.ny) {
-            g[q] = ld<S, R>(fin + op(q) * qs + y * nxp + x);  // halfway bounce-back
+            g[q] = ld<S, R>(fin + LBIB_IDX(op(q) * qs + y * nxp + x, 9LL * qs, L.chk_status));  // halfway bounce-back
         } else if (xs < 0 || xs >= nxi) {
             if (L.bc == LBIB_BC_PERIODIC_FORCE) {
                 xs = xs < 0 ? xs + nxi : xs - nxi;
-                g[q] = ld<S, R>(fin + q * qs + ys * nxp + (x - xl) + xs);
+                g[q] = ld<S, R>(fin + LBIB_IDX(q * qs + ys * nxp + (x - xl) + xs, 9LL * qs, L.chk_status));
             } else {
                 g[q] = R(0);  // unknown, set by Zou-He
             }
         } else {
-            g[q] = ld<S, R>(fin + q * qs + ys * nxp + (x - cx(q)));
+            g[q] = ld<S, R>(fin + LBIB_IDX(q * qs + ys * nxp + (x - cx(q)), 9LL * qs, L.chk_status));
         }
     }
     if (L.bc == LBIB_BC_INLET_OUTLET) {
@@ -271,7 +272,8 @@ __global__ void __launch_bounds__(TX* TY* RT / NPT, 1536 / (TX * TY * RT / NPT))
             if (act[j])
 #pragma unroll
                 for (int q = 0; q < 9; ++q)
-                    g[j][q] = ld<S, R>(fin + base + j * STEP * L.nxp + (q * L.qstride - cy(q) * L.nxp - cx(q)));
+                    g[j][q] = ld<S, R>(fin + LBIB_IDX(base + j * STEP * L.nxp + (q * L.qstride - cy(q) * L.nxp - cx(q)),
+                                                      9LL * L.qstride, L.chk_status));
         }
     } else {
 #pragma unroll
@@ -291,7 +293,8 @@ __global__ void __launch_bounds__(TX* TY* RT / NPT, 1536 / (TX * TY * RT / NPT))
         if (!(drho > R(-1) && fabs(ux + uy) < R(INFINITY))) bad = true;
         const int base = (yb + threadIdx.y + j * STEP) * L.nxp + x;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) st<S, R>(fout + q * L.qstride + base, g[j][q]);
+        for (int q = 0; q < 9; ++q)
+            st<S, R>(fout + LBIB_IDX(q * L.qstride + base, 9LL * L.qstride, L.chk_status), g[j][q]);
     }
     if (bad) atomicOr(d.status, ST_DIVERGED);
 }
@@ -499,7 +502,7 @@ __device__ __forceinline__ bool vec_row(const Lattice& L, const S* __restrict__ 
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
         const int src = bb[q] ? op(q) * L.qstride + rs : q * L.qstride + rs - cy(q) * L.nxp;
-        VecIO<S, R, V>::ld(fin + src, v[q]);
+        VecIO<S, R, V>::ld(fin + LBIB_IDX(src, 9LL * L.qstride - (V - 1), L.chk_status), v[q]);
     }
     // the value each shifted plane brings in at the lane's left or right end
     R in[9];
@@ -509,10 +512,11 @@ __device__ __forceinline__ bool vec_row(const Lattice& L, const S* __restrict__ 
         const int src = q * L.qstride + row - cy(q) * L.nxp;
         if (cx(q) == 1) {
             in[q] = __shfl_up_sync(0xffffffffu, v[q][V - 1], 1);
-            if (need_l) in[q] = xl0 > 0 ? ld<S, R>(fin + src - 1) : R(0);
+            if (need_l) in[q] = xl0 > 0 ? ld<S, R>(fin + LBIB_IDX(src - 1, 9LL * L.qstride, L.chk_status)) : R(0);
         } else {
             in[q] = __shfl_down_sync(0xffffffffu, v[q][0], 1);
-            if (need_r) in[q] = xl0 + V < nxi ? ld<S, R>(fin + src + V) : R(0);
+            if (need_r)
+                in[q] = xl0 + V < nxi ? ld<S, R>(fin + LBIB_IDX(src + V, 9LL * L.qstride, L.chk_status)) : R(0);
         }
     }
     if (!act) return false;
@@ -538,13 +542,15 @@ __device__ __forceinline__ bool vec_row(const Lattice& L, const S* __restrict__ 
 #pragma unroll
                     for (int q = 0; q < 9; ++q)
                         if (!bb[q] && cx(q) == 1)
-                            g[i][q] = ld<S, R>(fin + q * L.qstride + row - cy(q) * L.nxp + i + nxi - 1);
+                            g[i][q] = ld<S, R>(fin + LBIB_IDX(q * L.qstride + row - cy(q) * L.nxp + i + nxi - 1,
+                                                              9LL * L.qstride, L.chk_status));
                 }
                 if (xl == nxi - 1) {
 #pragma unroll
                     for (int q = 0; q < 9; ++q)
                         if (!bb[q] && cx(q) == -1)
-                            g[i][q] = ld<S, R>(fin + q * L.qstride + row - cy(q) * L.nxp + i - (nxi - 1));
+                            g[i][q] = ld<S, R>(fin + LBIB_IDX(q * L.qstride + row - cy(q) * L.nxp + i - (nxi - 1),
+                                                              9LL * L.qstride, L.chk_status));
                 }
             } else if (xl == 0) {
                 zou_he_inlet<R>(g[i], inlet_profile<R>(L, y));
@@ -565,12 +571,13 @@ __device__ __forceinline__ bool vec_row(const Lattice& L, const S* __restrict__ 
     const bool full = xl0 + V <= nxi;
     auto store = [&](int q, const R o[V]) {
         if (full) {
-            VecIO<S, R, V>::st(fout + q * L.qstride + row, o);
+            VecIO<S, R, V>::st(fout + LBIB_IDX(q * L.qstride + row, 9LL * L.qstride - (V - 1), L.chk_status), o);
         } else {
             // the instance ends inside the vector: only its own columns are written
 #pragma unroll
             for (int i = 0; i < V; ++i)
-                if (xl0 + i < nxi) st<S, R>(fout + q * L.qstride + row + i, o[i]);
+                if (xl0 + i < nxi)
+                    st<S, R>(fout + LBIB_IDX(q * L.qstride + row + i, 9LL * L.qstride, L.chk_status), o[i]);
         }
     };
     {
@@ -775,7 +782,7 @@ __global__ void __launch_bounds__(TX* TB_ROWS) k_bulk_tma(const __grid_constant_
             collide_t<R, FORCED>(g, lat_param<R>(L.gx, L.gx_f), lat_param<R>(L.gy, L.gy_f),
                                  lat_param<R>(L.omega, L.omega_f), drho, ux, uy);
             if (!(drho > R(-1)) || !isfinite(ux + uy)) atomicOr(d.status, ST_DIVERGED);
-            const int base = y * L.nxp + x;
+            const int base = (int)LBIB_IDX(y * L.nxp + x, L.qstride, L.chk_status);
 #pragma unroll
             for (int q = 0; q < 9; ++q) st<S, R>(fout + q * L.qstride + base, g[q]);
         }
@@ -960,7 +967,7 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_spread(Dev d, int p)
 #pragma unroll
         for (int r = 0; r < TY; ++r) {
             if (!live[r]) continue;
-            const int base = (y0 + r) * L.nxp + x;
+            const int base = (int)LBIB_IDX((y0 + r) * L.nxp + x, L.qstride, L.chk_status);
             fx_o[base] = Fx[r];
             fy_o[base] = Fy[r];
         }
@@ -997,7 +1004,7 @@ __global__ void __launch_bounds__(TX* TY, (std::is_same<R, float>::value ? 12 : 
         if (xl < ci.y && y < L.ny) {
             R g[9];
             pull<S, R>(L, fin, x, y, xl, ci.y, g);
-            const int base = y * L.nxp + x;
+            const int base = (int)LBIB_IDX(y * L.nxp + x, L.qstride, L.chk_status);
             R drho, ux, uy;
             collide<R>(g, fx_i[base], fy_i[base], omega, drho, ux, uy);
             if (!(drho > R(-1)) || !isfinite(ux + uy)) atomicOr(d.status, ST_DIVERGED);
@@ -1024,14 +1031,16 @@ __global__ void k_init_populations(Dev d, int buf)
     S* f = static_cast<S*>(d.f[buf]);
     if (x - d.colinfo[blockIdx.x].x >= d.colinfo[blockIdx.x].y) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) st<S, R>(f + q * L.qstride + y * L.nxp + x, R(0));
+        for (int q = 0; q < 9; ++q)
+            st<S, R>(f + LBIB_IDX(q * L.qstride + y * L.nxp + x, 9LL * L.qstride, L.chk_status), R(0));
         return;
     }
     R u = (L.bc == LBIB_BC_INLET_OUTLET) ? inlet_profile<R>(L, y) : R(0);
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
         R eu = R(cx(q)) * u;
-        st<S, R>(f + q * L.qstride + y * L.nxp + x, wq<R>(q) * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * u * u));
+        st<S, R>(f + LBIB_IDX(q * L.qstride + y * L.nxp + x, 9LL * L.qstride, L.chk_status),
+                 wq<R>(q) * (R(3) * eu + R(4.5) * eu * eu - R(1.5) * u * u));
     }
 }
 
@@ -1048,7 +1057,7 @@ __global__ void k_macro(Dev d, int buf, int64_t m, int x0, int inx, O* rho_o, O*
     if (xl >= inx || y >= L.ny) return;
     const int x = x0 + xl;
     int t = blockIdx.y * L.ntx + x / TX;
-    int base = y * L.nxp + x, ob = y * inx + xl;
+    int base = (int)LBIB_IDX(y * L.nxp + x, L.qstride, L.chk_status), ob = y * inx + xl;
     R Fx = lat_param<R>(L.gx, L.gx_f), Fy = lat_param<R>(L.gy, L.gy_f);
     if (d.fresh[t] == (int32_t)m) {
         Fx = static_cast<const R*>(d.fx)[base];

@@ -140,6 +140,9 @@ extern "C" lbib_status lbib_lattice_advance_noalloc(const lbib_fluid_params* P, 
         d.L = L;
         d.store = (prec == PREC_F64) ? STORE_F64 : STORE_F32;
         d.status = reinterpret_cast<uint32_t*>(base);
+#ifdef LBIB_CHECKED
+        d.L.chk_status = d.status;
+#endif
         d.nearflag[0] = d.nearflag[1] = d.nearflag[2] = reinterpret_cast<uint32_t*>(base + 256);
         int4* cols = reinterpret_cast<int4*>(base + 256 + need_flags);
         d.colinfo = cols;
@@ -176,6 +179,10 @@ extern "C" lbib_status lbib_lattice_advance_noalloc(const lbib_fluid_params* P, 
         if (e == cudaSuccess && (status & ST_DIVERGED)) {
             st = LBIB_ERR_DIVERGED;
             msg = "non-finite or non-positive state on the device";
+        }
+        if (e == cudaSuccess && (status & ST_BOUNDS)) {
+            st = LBIB_ERR_STATE;
+            msg = "an index left its array (bounds-checked build)";
         }
     }
     if (e != cudaSuccess) {

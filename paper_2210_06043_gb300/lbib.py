@@ -6,6 +6,7 @@ is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import os
 import threading
 from typing import Optional
 
@@ -132,16 +133,23 @@ _lib = None
 _lock = threading.Lock()
 
 
+def checked() -> bool:
+    """True when LBIB_CHECKED=1 in the environment: the process loads the
+    bounds-checked debug build (liblbib_checked.so) instead of liblbib.so."""
+    return os.environ.get("LBIB_CHECKED", "0") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_CHECKED if checked() else _build.LIB
 
 
 def load() -> ctypes.CDLL:
-    """Build (if stale) and load liblbib.so; raises if either fails."""
+    """Build (if stale) and load liblbib.so (the checked build with
+    LBIB_CHECKED=1); raises if either fails."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            path = _build.build(checked=checked())
             lib = ctypes.CDLL(path)
             for name, args in _SIGS.items():
                 fn = getattr(lib, name)

@@ -122,3 +122,23 @@ def test_create_batch_reports_errors_through_the_boundary():
     big = np.full(4, 1 << 23, dtype=np.int32)
     assert lib.lbib_create_batch(ctypes.byref(p), 4, big.ctypes.data, None, ctypes.byref(h)) == \
         lbib.LBIB_ERR_UNSUPPORTED
+
+
+def test_bounds_checked_build_compiles_and_exports_every_declared_symbol():
+    """The debug build with the index checks compiled in (-DLBIB_CHECKED) is a
+    separate library with the same boundary; lbib picks it with LBIB_CHECKED=1."""
+    path = build.build(checked=True)
+    assert path.endswith("liblbib_checked.so") and os.path.exists(path)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    assert set(declared_functions()) <= set(re.findall(r"\bT (lbib_\w+)", out))
+    env_before = os.environ.get("LBIB_CHECKED")
+    try:
+        os.environ["LBIB_CHECKED"] = "1"
+        assert lbib.library_path() == path
+        os.environ["LBIB_CHECKED"] = "0"
+        assert lbib.library_path() == build.LIB
+    finally:
+        if env_before is None:
+            os.environ.pop("LBIB_CHECKED", None)
+        else:
+            os.environ["LBIB_CHECKED"] = env_before
