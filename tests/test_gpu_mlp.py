@@ -121,6 +121,54 @@ def test_gradients_of_other_shapes(width, hidden, B):
     net.close()
 
 
+def test_wide_network_on_the_general_path():
+    """Width 320 (above the fused kernels' 256): every product on the general
+    tensor-core GEMM path.  Outputs and gradients against the quantized
+    oracle, gradients repeat exactly, and backward + apply(1) equals
+    train_step bit for bit over two steps."""
+    rng = np.random.default_rng(9)
+    norm = _norm(rng)
+    width, hidden, B = 320, 2, 700
+
+    def make(seed):
+        return lbib.Mlp(N_IN, N_OUT, width=width, n_hidden=hidden, max_batch=1024, seed=seed,
+                        stream=torch.cuda.current_stream().cuda_stream,
+                        in_shift=norm["c_in"], in_scale=norm["s_in"], out_shift=norm["c_out"],
+                        out_scale=norm["s_out"])
+
+    a, b = make(5), make(5)
+    x = rng.uniform(-1, 1, (B, N_IN)).astype(np.float32)
+    t = (rng.normal(0, 1, (B, N_OUT)) * norm["s_out"] + norm["c_out"]).astype(np.float32)
+    xd, td, yd = _dev(x), _dev(t), torch.zeros(B, N_OUT, device="cuda")
+    a.forward(xd.data_ptr(), B, yd.data_ptr())
+    torch.cuda.synchronize()
+    layers = omlp.split_params(a.get_params(), N_IN, width, hidden, N_OUT)
+    y, _, _ = omlp.forward(layers, x, quantize=True, **norm)
+    assert _rel(yd.cpu().numpy(), y) < 5e-3
+    g1, l1 = a.gradients(xd.data_ptr(), td.data_ptr(), B)
+    g2, l2 = a.gradients(xd.data_ptr(), td.data_ptr(), B)
+    assert np.array_equal(g1, g2) and l1 == l2
+    lo, go = omlp.gradients(layers, x, t, quantize=True, **norm)
+    assert abs(l1 - lo) <= 1e-3 * lo
+    k = 0
+    for (dW, db) in go:
+        gw = g1[k:k + dW.size].reshape(dW.shape)
+        k += dW.size
+        gb = g1[k:k + db.size]
+        k += db.size
+        assert _rel(gw, dW) < 2e-2 and _rel(gb, db) < 2e-2
+    n = a.param_count()
+    grad = torch.zeros(n, device="cuda")
+    for lr in (1e-3, 5e-4):
+        a.backward(xd.data_ptr(), td.data_ptr(), B, grad.data_ptr(), n, None)
+        a.apply_gradient(grad.data_ptr(), n, 1.0, lr)
+        b.train_step(xd.data_ptr(), td.data_ptr(), B, lr)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.get_params(), b.get_params())
+    a.close()
+    b.close()
+
+
 def test_training_fits_a_smooth_function():
     rng = np.random.default_rng(2)
     norm = dict(c_in=np.zeros(N_IN, np.float32), s_in=np.ones(N_IN, np.float32),
