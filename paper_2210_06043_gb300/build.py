@@ -23,7 +23,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbib.so")
 LIB_CHECKED = os.path.join(OUT_DIR, "liblbib_checked.so")
 SOURCES = ("lbib_api.cu", "lbib_lbm.cu", "lbib_lag.cu", "lbib_lag_mls.cu", "lbib_noalloc.cu", "lbib_mlp.cu")
-HEADERS = ("lbib_internal.cuh", "lbib_device.cuh", "lbib_lag_kernel.cuh")
+HEADERS = ("lbib_internal.cuh", "lbib_device.cuh", "lbib_lag_kernel.cuh", "lbib_trace.h")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "lbib_internal.cuh"
+#include "lbib_trace.h"
 
 using namespace lbib;
 
@@ -422,6 +423,7 @@ lbib_status upload_posf(lbib_ctx* ctx, int k, const std::vector<double>& pos)
 // Builds the device Lagrangian arrays from the host bodies (first advance).
 lbib_status finalize(lbib_ctx* ctx)
 {
+    LBIB_TRACE("lbib set-up (first advance)");
     if (ctx->finalized) return LBIB_OK;
     Dev& d = ctx->d;
     const Lattice& L = d.L;
@@ -896,6 +898,7 @@ extern "C" {
 
 lbib_status lbib_create(const lbib_fluid_params* P, lbib_ctx** out)
 {
+    LBIB_TRACE("lbib_create");
     if (!P || !out) return fail(nullptr, LBIB_ERR_INVALID_ARG, "null argument");
     const uint64_t seed = P->seed;
     return create_impl(P, 1, &P->nx, &seed, out);
@@ -904,11 +907,13 @@ lbib_status lbib_create(const lbib_fluid_params* P, lbib_ctx** out)
 lbib_status lbib_create_batch(const lbib_fluid_params* P, int32_t n_instances, const int32_t* nx,
                               const uint64_t* seeds, lbib_ctx** out)
 {
+    LBIB_TRACE("lbib_create_batch");
     return create_impl(P, n_instances, nx, seeds, out);
 }
 
 lbib_status lbib_add_membrane_to(lbib_ctx* ctx, int32_t instance, const lbib_membrane_desc* m, int32_t* id_out)
 {
+    LBIB_TRACE("lbib_add_membrane_to");
     if (!ctx || !m) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
     if (!valid_instance(ctx, instance)) return fail(ctx, LBIB_ERR_INVALID_ARG, "no such instance");
     if (ctx->finalized) return fail(ctx, LBIB_ERR_STATE, "membranes must be added before the first advance");
@@ -949,6 +954,7 @@ lbib_status lbib_add_membrane(lbib_ctx* ctx, const lbib_membrane_desc* m, int32_
 lbib_status lbib_add_membranes(lbib_ctx* ctx, int32_t n, const int32_t* instance, const lbib_membrane_desc* descs,
                                const lbib_adhesion_params* const* adhesion, int32_t* ids_out)
 {
+    LBIB_TRACE("lbib_add_membranes");
     if (!ctx || n < 0 || (n > 0 && (!instance || !descs))) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
     for (int32_t k = 0; k < n; ++k) {
         int32_t id = -1;
@@ -962,6 +968,7 @@ lbib_status lbib_add_membranes(lbib_ctx* ctx, int32_t n, const int32_t* instance
 
 lbib_status lbib_set_adhesion(lbib_ctx* ctx, int32_t body, const lbib_adhesion_params* a)
 {
+    LBIB_TRACE("lbib_set_adhesion");
     if (!ctx || !a) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
     if (ctx->finalized) return fail(ctx, LBIB_ERR_STATE, "adhesion must be set before the first advance");
     if (body < 0 || body >= (int)ctx->bodies.size()) return fail(ctx, LBIB_ERR_INVALID_ARG, "no such body");
@@ -976,6 +983,7 @@ lbib_status lbib_set_adhesion(lbib_ctx* ctx, int32_t body, const lbib_adhesion_p
 
 lbib_status lbib_advance(lbib_ctx* ctx, int64_t nsteps)
 {
+    LBIB_TRACE("lbib_advance");
     if (!ctx) return fail(ctx, LBIB_ERR_INVALID_ARG, "null context");
     if (nsteps < 0) return fail(ctx, LBIB_ERR_INVALID_ARG, "nsteps < 0");
     if (ctx->fault != LBIB_OK)
@@ -1017,6 +1025,7 @@ lbib_status lbib_advance(lbib_ctx* ctx, int64_t nsteps)
 
 lbib_status lbib_sync(lbib_ctx* ctx)
 {
+    LBIB_TRACE("lbib_sync");
     if (!ctx) return fail(ctx, LBIB_ERR_INVALID_ARG, "null context");
     DeviceGuard guard(ctx->device);
     return pre_read(ctx);
@@ -1061,6 +1070,7 @@ static lbib_status read_macro(lbib_ctx* ctx, int32_t inst, double* rho, double* 
 
 lbib_status lbib_read_instance_velocity(lbib_ctx* ctx, int32_t instance, double* ux, double* uy, size_t n)
 {
+    LBIB_TRACE("lbib_read_instance_velocity");
     if (!ctx || !ux || !uy) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
     return read_macro(ctx, instance, nullptr, ux, uy, n);
 }
@@ -1072,12 +1082,14 @@ lbib_status lbib_read_velocity(lbib_ctx* ctx, double* ux, double* uy, size_t n)
 
 lbib_status lbib_read_density(lbib_ctx* ctx, double* rho, size_t n)
 {
+    LBIB_TRACE("lbib_read_density");
     if (!ctx || !rho) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
     return read_macro(ctx, 0, rho, nullptr, nullptr, n);
 }
 
 lbib_status lbib_read_velocity_device(lbib_ctx* ctx, void* dux, void* duy, size_t n, int32_t dtype)
 {
+    LBIB_TRACE("lbib_read_velocity_device");
     if (!ctx || !dux || !duy) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
     if (dtype != 0 && dtype != 1) return fail(ctx, LBIB_ERR_INVALID_ARG, "dtype must be 0 (float) or 1 (double)");
     const Lattice& L = ctx->d.L;
@@ -1118,6 +1130,7 @@ static void double_to_stored(const lbib_ctx* ctx, char* raw, size_t k, double v)
 
 lbib_status lbib_read_instance_populations(lbib_ctx* ctx, int32_t instance, double* f, size_t n)
 {
+    LBIB_TRACE("lbib_read_instance_populations");
     if (!ctx || !f) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
     if (!valid_instance(ctx, instance)) return fail(ctx, LBIB_ERR_INVALID_ARG, "no such instance");
     const Lattice& L = ctx->d.L;
@@ -1149,6 +1162,7 @@ lbib_status lbib_read_populations(lbib_ctx* ctx, double* f, size_t n)
 
 lbib_status lbib_write_instance_populations(lbib_ctx* ctx, int32_t instance, const double* f, size_t n)
 {
+    LBIB_TRACE("lbib_write_instance_populations");
     if (!ctx || !f) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
     if (!valid_instance(ctx, instance)) return fail(ctx, LBIB_ERR_INVALID_ARG, "no such instance");
     const Lattice& L = ctx->d.L;
@@ -1181,6 +1195,7 @@ lbib_status lbib_write_populations(lbib_ctx* ctx, const double* f, size_t n)
 lbib_status lbib_read_instance_observables(lbib_ctx* ctx, int32_t instance, lbib_obs* out, size_t cap,
                                            size_t* n_out)
 {
+    LBIB_TRACE("lbib_read_instance_observables");
     if (!ctx || !n_out || (cap && !out)) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
     if (!valid_instance(ctx, instance)) return fail(ctx, LBIB_ERR_INVALID_ARG, "no such instance");
     *n_out = 0;
@@ -1207,6 +1222,7 @@ lbib_status lbib_read_instance_observables(lbib_ctx* ctx, int32_t instance, lbib
 
 lbib_status lbib_read_latest_observables(lbib_ctx* ctx, lbib_obs* out, size_t n)
 {
+    LBIB_TRACE("lbib_read_latest_observables");
     if (!ctx || !out) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
     if (n < (size_t)ctx->ninst) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than n_instances");
     DeviceGuard guard(ctx->device);
@@ -1228,6 +1244,7 @@ lbib_status lbib_read_latest_observables(lbib_ctx* ctx, lbib_obs* out, size_t n)
 
 lbib_status lbib_read_latest_observables_async(lbib_ctx* ctx, lbib_obs* out, size_t n)
 {
+    LBIB_TRACE("lbib_read_latest_observables_async");
     if (!ctx || !out) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
     if (n < (size_t)ctx->ninst) return fail(ctx, LBIB_ERR_INVALID_ARG, "buffer smaller than n_instances");
     DeviceGuard guard(ctx->device);
@@ -1274,6 +1291,7 @@ lbib_status lbib_read_observables(lbib_ctx* ctx, lbib_obs* out, size_t cap, size
 
 lbib_status lbib_read_markers(lbib_ctx* ctx, int32_t id, double* xy, size_t n)
 {
+    LBIB_TRACE("lbib_read_markers");
     if (!ctx || !xy) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
     if (id < 0 || id >= (int)ctx->bodies.size()) return fail(ctx, LBIB_ERR_INVALID_ARG, "no such body");
     const int nv = ctx->bodies[id].nv;
@@ -1296,6 +1314,7 @@ lbib_status lbib_read_markers(lbib_ctx* ctx, int32_t id, double* xy, size_t n)
 
 lbib_status lbib_read_body_field(lbib_ctx* ctx, int32_t id, int32_t field, double* out, size_t n)
 {
+    LBIB_TRACE("lbib_read_body_field");
     if (!ctx || !out) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
     if (id < 0 || id >= (int)ctx->bodies.size()) return fail(ctx, LBIB_ERR_INVALID_ARG, "no such body");
     if (field < 0 || field >= LBIB_FIELD_COUNT) return fail(ctx, LBIB_ERR_INVALID_ARG, "unknown field");
@@ -1327,6 +1346,7 @@ lbib_status lbib_read_body_field(lbib_ctx* ctx, int32_t id, int32_t field, doubl
 lbib_status lbib_read_bonds(lbib_ctx* ctx, int32_t id, int32_t* bound, double* ax, double* ay, double* margin,
                             size_t n)
 {
+    LBIB_TRACE("lbib_read_bonds");
     if (!ctx) return fail(ctx, LBIB_ERR_INVALID_ARG, "null context");
     if (id < 0 || id >= (int)ctx->bodies.size()) return fail(ctx, LBIB_ERR_INVALID_ARG, "no such body");
     const HostBody& h = ctx->bodies[id];
@@ -1543,6 +1563,7 @@ extern "C" {
 
 lbib_status lbib_save_state(lbib_ctx* ctx, void* buf, size_t bytes)
 {
+    LBIB_TRACE("lbib_save_state");
     if (!ctx || !buf) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
     DeviceGuard guard(ctx->device);
     lbib_status s = pre_read(ctx);
@@ -1553,6 +1574,7 @@ lbib_status lbib_save_state(lbib_ctx* ctx, void* buf, size_t bytes)
 
 lbib_status lbib_load_state(lbib_ctx* ctx, const void* buf, size_t bytes)
 {
+    LBIB_TRACE("lbib_load_state");
     if (!ctx || !buf) return fail(ctx, LBIB_ERR_INVALID_ARG, "null argument");
     DeviceGuard guard(ctx->device);
     lbib_status s = pre_read(ctx);
@@ -1622,6 +1644,7 @@ lbib_status lbib_set_launch_config(lbib_ctx* ctx, const lbib_launch_config* cfg)
 
 lbib_status lbib_autotune(lbib_ctx* ctx, int32_t steps_per_trial, lbib_launch_config* chosen)
 {
+    LBIB_TRACE("lbib_autotune");
     if (!ctx) return fail(ctx, LBIB_ERR_INVALID_ARG, "null context");
     if (steps_per_trial < 1) return fail(ctx, LBIB_ERR_INVALID_ARG, "steps_per_trial < 1");
     DeviceGuard guard(ctx->device);
@@ -1819,6 +1842,7 @@ lbib_status lbib_describe(lbib_ctx* ctx, int32_t* kernels_per_step, int32_t* nea
 
 void lbib_destroy(lbib_ctx* ctx)
 {
+    LBIB_TRACE("lbib_destroy");
     if (!ctx) return;
     DeviceGuard guard(ctx->device);
     // no wait for the device: graphs still in flight are freed when they

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "lbib_internal.cuh"
+#include "lbib_trace.h"
 #include "../../include/lbib_mlp.h"
 
 using namespace lbib;
@@ -1948,6 +1949,7 @@ extern "C" {
 
 lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
 {
+    LBIB_TRACE("lbib_mlp_create");
     if (!d || !out) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
     if (d->n_in < 1 || d->n_in > 32 || d->width < 64 || d->width % 64 || d->width > 1024 || d->n_hidden < 1 ||
@@ -2141,6 +2143,7 @@ lbib_status lbib_mlp_create(const lbib_mlp_desc* d, lbib_mlp** out)
 
 lbib_status lbib_mlp_forward(lbib_mlp* net, const float* x, int32_t batch, float* y)
 {
+    LBIB_TRACE("lbib_mlp_forward");
     if (!net || !x || !y) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
     if (net->fault != LBIB_OK) return mlp_fail(net->fault, "a bounded device wait gave up earlier: set the parameters again");
     if (batch < 1 || batch > net->max_batch) return mlp_fail(LBIB_ERR_INVALID_ARG, "batch outside 1 .. max_batch");
@@ -2168,6 +2171,7 @@ lbib_status lbib_mlp_forward(lbib_mlp* net, const float* x, int32_t batch, float
 
 lbib_status lbib_mlp_train_step(lbib_mlp* net, const float* x, const float* t, int32_t batch, float lr, float* loss)
 {
+    LBIB_TRACE("lbib_mlp_train_step");
     if (!net || !x || !t) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
     if (net->fault != LBIB_OK) return mlp_fail(net->fault, "a bounded device wait gave up earlier: set the parameters again");
     if (batch < 1 || batch > net->max_batch) return mlp_fail(LBIB_ERR_INVALID_ARG, "batch outside 1 .. max_batch");
@@ -2186,6 +2190,7 @@ lbib_status lbib_mlp_train_step(lbib_mlp* net, const float* x, const float* t, i
 lbib_status lbib_mlp_backward(lbib_mlp* net, const float* x, const float* t, int32_t batch, float* grad, size_t n,
                               float* loss)
 {
+    LBIB_TRACE("lbib_mlp_backward");
     if (!net || !x || !t || !grad) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
     if (net->fault != LBIB_OK) return mlp_fail(net->fault, "a bounded device wait gave up earlier: set the parameters again");
     if (n < net->ntrue) return mlp_fail(LBIB_ERR_INVALID_ARG, "buffer smaller than the parameter count");
@@ -2204,6 +2209,7 @@ lbib_status lbib_mlp_backward(lbib_mlp* net, const float* x, const float* t, int
 
 lbib_status lbib_mlp_apply_gradient(lbib_mlp* net, const float* grad, size_t n, float scale, float lr)
 {
+    LBIB_TRACE("lbib_mlp_apply_gradient");
     if (!net || !grad) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
     if (net->fault != LBIB_OK) return mlp_fail(net->fault, "a bounded device wait gave up earlier: set the parameters again");
     if (n < net->ntrue) return mlp_fail(LBIB_ERR_INVALID_ARG, "buffer smaller than the parameter count");
@@ -2251,6 +2257,7 @@ static void padded_to_host(const lbib_mlp* net, const std::vector<float>& pad, f
 lbib_status lbib_mlp_gradients(lbib_mlp* net, const float* x, const float* t, int32_t batch, float* grad, size_t n,
                                float* loss)
 {
+    LBIB_TRACE("lbib_mlp_gradients");
     if (!net || !x || !t || !grad) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
     if (net->fault != LBIB_OK) return mlp_fail(net->fault, "a bounded device wait gave up earlier: set the parameters again");
     if (n < net->ntrue) return mlp_fail(LBIB_ERR_INVALID_ARG, "buffer smaller than the parameter count");
@@ -2273,6 +2280,7 @@ lbib_status lbib_mlp_gradients(lbib_mlp* net, const float* x, const float* t, in
 
 lbib_status lbib_mlp_get_params(lbib_mlp* net, float* params, size_t n)
 {
+    LBIB_TRACE("lbib_mlp_get_params");
     if (!net || !params) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
     if (n < net->ntrue) return mlp_fail(LBIB_ERR_INVALID_ARG, "buffer smaller than the parameter count");
     Guard guard(net->device);
@@ -2288,6 +2296,7 @@ lbib_status lbib_mlp_get_params(lbib_mlp* net, float* params, size_t n)
 
 lbib_status lbib_mlp_set_params(lbib_mlp* net, const float* params, size_t n)
 {
+    LBIB_TRACE("lbib_mlp_set_params");
     if (!net || !params) return mlp_fail(LBIB_ERR_INVALID_ARG, "null argument");
     if (n < net->ntrue) return mlp_fail(LBIB_ERR_INVALID_ARG, "buffer smaller than the parameter count");
     for (size_t i = 0; i < net->ntrue; ++i)
