@@ -567,36 +567,66 @@ def _addr(a: np.ndarray) -> int:
     return a.__array_interface__["data"][0]
 
 
+class _Records:
+    """lbib_add_membranes' arguments for a list of (instance, workloads.Body):
+    the descriptors (one array, filled a field at a time), every body's
+    vertices (and stress-free vertices) copied into one array the descriptors
+    point into, the adhesion records and a pointer per body (0: none).  The
+    library copies what the pointers reach during the call; `keep` holds the
+    arrays until then."""
+
+    def __init__(self, items):
+        n = len(items)
+        bodies = [b for _, b in items]
+        self.inst = np.fromiter((int(i) for i, _ in items), np.int32, n)
+        xys = [np.ascontiguousarray(b.xy, dtype=np.float64).reshape(-1) for b in bodies]
+        sizes = np.fromiter((x.size for x in xys), np.int64, n)
+        self.nv = sizes // 2
+        d = np.zeros(n, _MEMBRANE_DT)
+        d["kind"] = [int(b.kind) for b in bodies]
+        d["motion"] = [int(b.motion) for b in bodies]
+        d["nv"] = self.nv
+        flat = np.concatenate(xys) if n else np.zeros(0)
+        d["xy"] = _addr(flat) + 8 * (np.cumsum(sizes) - sizes)
+        with_ref = [k for k, b in enumerate(bodies) if b.xy_ref is not None]
+        flat_ref = np.zeros(0)
+        if with_ref:
+            refs = [np.ascontiguousarray(bodies[k].xy_ref, dtype=np.float64).reshape(-1) for k in with_ref]
+            rsz = np.fromiter((r.size for r in refs), np.int64, len(refs))
+            flat_ref = np.concatenate(refs)
+            d["xy_ref"][with_ref] = _addr(flat_ref) + 8 * (np.cumsum(rsz) - rsz)
+        d["ca"] = [float(b.ca) for b in bodies]
+        d["beta"] = [float(b.beta) for b in bodies]
+        d["ka"] = [float(b.ka) for b in bodies]
+        d["density_ratio"] = [float(b.density_ratio) for b in bodies]
+        self.descs = d
+        self.with_adh = [k for k, b in enumerate(bodies) if b.adhesion is not None]
+        ads = [bodies[k].adhesion for k in self.with_adh]
+        adh = np.zeros(len(ads), _ADHESION_DT)
+        if ads:
+            adh["n_ligands"] = [int(a.n_lig) for a in ads]
+            for f, attr in (("sigma", "sigma"), ("y_cr", "y_cr"), ("y_eq", "y_eq"), ("kf_dt", "kf_dt"),
+                            ("kr0_dt", "kr0_dt"), ("xi", "xi")):
+                adh[f] = [float(getattr(a, attr)) for a in ads]
+        self.adh = adh
+        self.n_lig = [int(a.n_lig) for a in ads]
+        self.adh_ptr = np.zeros(n, np.uint64)
+        if ads:
+            self.adh_ptr[self.with_adh] = _addr(adh) + _ADHESION_DT.itemsize * np.arange(len(ads), dtype=np.uint64)
+        self.keep = (flat, flat_ref, adh)
+
+
 def _add_all(s: Solver, items) -> None:
     """Every (instance, workloads.Body) of `items` in one lbib_add_membranes call."""
     n = len(items)
     if n == 0:
         return
-    keep, rows, adh_rows, adh_of = [], [], [], []
-    for i, b in items:
-        xy = np.ascontiguousarray(b.xy, dtype=np.float64)
-        ref = None if b.xy_ref is None else np.ascontiguousarray(b.xy_ref, dtype=np.float64)
-        keep += [xy, ref]
-        rows.append((int(b.kind), int(b.motion), xy.size // 2, 0, _addr(xy), 0 if ref is None else _addr(ref),
-                     float(b.ca), float(b.beta), float(b.ka), float(b.density_ratio)))
-        a = b.adhesion
-        if a is None:
-            adh_of.append(-1)
-        else:
-            adh_of.append(len(adh_rows))
-            adh_rows.append((int(a.n_lig), 0, float(a.sigma), float(a.y_cr), float(a.y_eq), float(a.kf_dt),
-                             float(a.kr0_dt), float(a.xi)))
-    descs = np.array(rows, dtype=_MEMBRANE_DT)
-    adh = np.array(adh_rows, dtype=_ADHESION_DT)
-    idx = np.asarray(adh_of, np.int64)
-    adh_ptr = np.where(idx >= 0, (_addr(adh) if len(adh) else 0) + idx * _ADHESION_DT.itemsize, 0).astype(np.uint64)
-    inst = np.asarray([int(i) for i, _ in items], np.int32)
+    r = _Records(items)
     ids = np.zeros(n, np.int32)
-    s._c(s.lib.lbib_add_membranes(s.ctx, n, _vp(inst), _vp(descs), _vp(adh_ptr), _vp(ids)))
-    for k, (i, b) in enumerate(items):
-        s.nv.append(rows[k][2])
-        if b.adhesion is not None:
-            s.nlig[int(ids[k])] = int(b.adhesion.n_lig)
+    s._c(s.lib.lbib_add_membranes(s.ctx, n, _vp(r.inst), _vp(r.descs), _vp(r.adh_ptr), _vp(ids)))
+    s.nv.extend(int(v) for v in r.nv)
+    for k, nl in zip(r.with_adh, r.n_lig):
+        s.nlig[int(ids[k])] = nl
 
 
 def from_capillaries(caps, storage=None, device=0, stream=None, obs_capacity=0) -> Solver:
